@@ -1,0 +1,470 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each one checks it against an
+independent definition (dense KKT solve, SVD projections, closed forms worked
+out by hand, invariants stated in the paper, brute force on tiny instances).
+A final test plants mistakes in separately built oracle variants and checks
+that some pin here catches every one of them.
+"""
+import os
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.dense import constraint_matrix, multiplier_vector, brute_suffix_domain
+from paper_2407_05433_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def amax(a):
+    a = np.asarray(a, float)
+    return float(np.abs(a).max()) if a.size else 0.0
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    if b.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b))))
+
+
+def _scalar(case):
+    N, n, m = 1, 1, 1
+    p = np.array([1 if case == "B" else 0], np.int32)
+    q = np.array([0, 1 if case == "C" else 0], np.int32)
+    pb = synth.ECLQRProblem(
+        N=N, n=n, m=m, p=p, q=q,
+        A=np.array([[[1.5]]]), B=np.array([[[2.0]]]), c=np.array([[0.5]]),
+        C=np.array([[1.0]]) if case == "B" else np.zeros((0, 1)),
+        D=np.array([[2.0]]) if case == "B" else np.zeros((0, 1)),
+        d=np.array([-1.0]) if case == "B" else np.zeros(0),
+        E=np.array([[1.0]]) if case == "C" else np.zeros((0, 1)),
+        e=np.array([-1.0]) if case == "C" else np.zeros(0),
+        Q=np.array([[[2.0]], [[3.0]]]), M=np.zeros((1, 1, 1)), R=np.array([[[1.0]]]),
+        qv=np.array([[0.25], [0.5]]), rv=np.array([[-1.0]]), s0=np.array([1.0]))
+    return pb
+
+
+def _golden_scalar():
+    rows = {}
+    with open(os.path.join(HERE, "golden", "scalar_closed_form.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, *vals = line.split()
+            rows[k] = [float(v) for v in vals]
+    return rows
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("case", ["A", "B", "C"])
+def test_scalar_closed_form(case):
+    """Hand-derived one-stage solutions (tests/golden/scalar_closed_form.txt)."""
+    u, x1, lam1, alpha, mu, etaN = _golden_scalar()[case]
+    pb = _scalar(case)
+    s = oracle.solve(pb)
+    assert s.ok
+    assert abs(s.u[0, 0] - u) < 1e-13
+    assert abs(s.x[1, 0] - x1) < 1e-13
+    assert abs(s.lam[1, 0] - lam1) < 1e-13
+    assert abs(s.alpha[0] - alpha) < 1e-13
+    assert abs(s.x[0, 0] - 1.0) < 1e-15
+    if not np.isnan(mu):
+        assert abs(s.mu[0] - mu) < 1e-13
+    if not np.isnan(etaN):
+        assert abs(s.eta[0] - etaN) < 1e-13
+
+
+def test_table1_reduced_dims():
+    """Sec. 9: the Table 1 workload has min nbar = 6 and min mbar = 2."""
+    g = {}
+    with open(os.path.join(HERE, "golden", "table1_reduced_dims.txt")) as f:
+        for line in f:
+            if not line.startswith("#") and line.strip():
+                k, v = line.split()
+                g[k] = float(v)
+    pb = synth.config("table1", N=32)
+    assert pb.n == g["n"] and pb.m == g["m"] and pb.q[0] == g["state_only_rows_per_nonterminal_stage"]
+    s = oracle.solve(pb, debug=True)
+    assert s.ok
+    assert s.debug["nbar"].min() == g["min_nbar"]
+    assert s.debug["mbar"].min() == g["min_mbar"]
+    r = oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha)
+    assert r <= g["max_gpu_residual"]
+
+
+# ---------------------------------------------------------------- Lemma 1 and the null-space solve
+def _row_space_projector(H):
+    if H.shape[0] == 0:
+        return np.zeros((H.shape[1], H.shape[1]))
+    U, s, Vt = np.linalg.svd(H)
+    r = int(np.sum(s > 1e-9 * s[0]))
+    return Vt[:r].T @ Vt[:r]
+
+
+def _same_affine_set(H1, h1, H2, h2, tol=1e-9):
+    """{H1 x + h1 = 0} == {H2 x + h2 = 0} (both consistent)."""
+    n = H1.shape[1]
+    P1, P2 = _row_space_projector(H1), _row_space_projector(H2)
+    if np.abs(P1 - P2).max() > tol:
+        return False
+    if H1.shape[0] == 0:
+        return True
+    x1 = -np.linalg.pinv(H1) @ h1
+    x2 = -np.linalg.pinv(H2) @ h2
+    return np.abs(x1 - x2).max() <= tol * max(1.0, np.abs(x1).max())
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_project_matches_svd_projection(seed):
+    """Lemma 1: {z : exists y, F y + G z + g = 0} computed by the oracle equals
+    the SVD null-space projection W^T (G z + g) = 0, also with rank-deficient F."""
+    rng = np.random.default_rng(seed)
+    r, ky, kz = 9, 4, 5
+    F = rng.standard_normal((r, ky))
+    if seed % 2:
+        F[:, 3] = F[:, 0] - 2 * F[:, 1]          # rank-deficient eliminated block
+    G = rng.standard_normal((r, kz))
+    if seed % 3 == 0:
+        G[7] = G[2]; F[7] = F[2]                  # duplicated row
+    z0, y0 = rng.standard_normal(kz), rng.standard_normal(ky)
+    g = -(F @ y0 + G @ z0)                        # consistent
+    M = np.hstack([F, G, g[:, None]])
+    gr, rows, inc = oracle.project_rows(M, [ky], kz)
+    assert not inc
+    assert gr[0] == np.linalg.matrix_rank(F)
+    U, s, _ = np.linalg.svd(F)
+    W = U[:, int(np.sum(s > 1e-10 * s[0])):]
+    assert _same_affine_set(rows[:, :kz], rows[:, kz], W.T @ G, W.T @ g)
+    # every kept row has unit coefficient norm and z0 satisfies it
+    assert np.allclose(np.linalg.norm(rows[:, :kz], axis=1), 1.0)
+    assert np.abs(rows[:, :kz] @ z0 + rows[:, kz]).max() < 1e-12
+
+
+def test_project_detects_inconsistency():
+    """Lemma 1: a row reduced to 0 = gamma with gamma != 0 marks an empty set;
+    a redundant row 0 = 0 is dropped (Sec. 8, item 4)."""
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal((4, 2)); G = rng.standard_normal((4, 2))
+    F[3] = F[0]; G[3] = G[0]
+    z, y = rng.standard_normal(2), rng.standard_normal(2)
+    g = -(F @ y + G @ z)
+    _, rows, inc = oracle.project_rows(np.hstack([F, G, g[:, None]]), [2], 2)
+    assert not inc and rows.shape[0] == 1      # null(F^T) is 2-dim; e_0 - e_3 gives 0 = 0
+    g2 = g.copy(); g2[3] += 1e-3
+    _, _, inc = oracle.project_rows(np.hstack([F, G, g2[:, None]]), [2], 2)
+    assert inc
+
+
+@pytest.mark.parametrize("shape", [(3, 7), (5, 5), (6, 4), (0, 4)])
+def test_tqr_solve(shape):
+    """Null space and min-norm solutions agree with numpy's pseudo-inverse."""
+    rng = np.random.default_rng(shape[0] * 10 + shape[1])
+    rk, nk = shape
+    K = rng.standard_normal((rk, nk))
+    if rk >= 3:
+        K[-1] = K[0] + K[1]                       # one dependent row
+    x0 = rng.standard_normal((nk, 2))
+    b = -K @ x0
+    rank, Q, X, res = oracle.tqr_solve(K, b)
+    assert rank == (np.linalg.matrix_rank(K) if rk else 0)
+    assert np.allclose(Q.T @ Q, np.eye(nk), atol=1e-13)
+    if rank < nk:
+        assert np.abs(K @ Q[:, rank:]).max() < 1e-12 if rk else True
+    assert np.abs(X + np.linalg.pinv(K) @ b).max() < 1e-11 if rk else np.abs(X).max() == 0
+    assert res < 1e-12
+
+
+# ---------------------------------------------------------------- Prop. 1 associativity (composition by Lemma 1)
+def _compose(R1, R2, na, nb, nc):
+    """compose relations on (a,b) and (b,c), rows [L | R | l], eliminating b."""
+    r1, r2 = R1.shape[0], R2.shape[0]
+    M = np.zeros((r1 + r2, nb + na + nc + 1))
+    M[:r1, :nb] = R1[:, na:na + nb]; M[:r1, nb:nb + na] = R1[:, :na]; M[:r1, -1] = R1[:, -1]
+    M[r1:, :nb] = R2[:, :nb]; M[r1:, nb + na:nb + na + nc] = R2[:, nb:nb + nc]; M[r1:, -1] = R2[:, -1]
+    _, rows, inc = oracle.project_rows(M, [nb], na + nc)
+    assert not inc
+    return rows
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_composition_associative(seed):
+    """Prop. 1: (R_ab o R_bc) o R_cd and R_ab o (R_bc o R_cd) are the same set."""
+    rng = np.random.default_rng(100 + seed)
+    n = 3
+    pts = [rng.standard_normal(n) for _ in range(4)]   # a consistent chain point
+    rels = []
+    for k in range(3):
+        r = rng.integers(1, 2 * n + 1)
+        L = rng.standard_normal((r, n)); Rm = rng.standard_normal((r, n))
+        if seed % 2:
+            Rm[:, 0] = 0.0
+        l = -(L @ pts[k] + Rm @ pts[k + 1])
+        rels.append(np.hstack([L, Rm, l[:, None]]))
+    left = _compose(_compose(rels[0], rels[1], n, n, n), rels[2], n, n, n)
+    right = _compose(rels[0], _compose(rels[1], rels[2], n, n, n), n, n, n)
+    assert _same_affine_set(left[:, :2 * n], left[:, -1], right[:, :2 * n], right[:, -1])
+
+
+# ---------------------------------------------------------------- Thm 3 by brute force
+def _tiny(seed, kind):
+    rng = np.random.default_rng(seed)
+    N, n, m = 4, 3, 2
+    p = rng.integers(0, 3, size=N)
+    q = rng.integers(0, 2, size=N + 1)
+    if kind == "terminal":
+        q[N] = 2
+    pb = synth.make_problem(seed, N, n, m, p, q, degenerate_frac=0.5 if kind == "degenerate" else 0.0)
+    return pb
+
+
+@pytest.mark.parametrize("seed,kind", list(itertools.product(range(5), ["plain", "terminal", "degenerate"])))
+def test_suffix_domains_brute_force(seed, kind):
+    """Thm 3: X_i is the projection onto x_i of every constraint from stage i on;
+    checked against a brute-force SVD projection of the stacked suffix system."""
+    pb = _tiny(seed, kind)
+    s = oracle.solve(pb, debug=True)
+    assert s.ok
+    for i in range(pb.N + 1):
+        r = s.debug["hrows"][i]
+        H, h = s.debug["H"][i, :r, :pb.n], s.debug["H"][i, :r, pb.n]
+        Hb, hb, cons = brute_suffix_domain(pb, i)
+        assert cons
+        assert _same_affine_set(H, h, Hb, hb), f"stage {i}"
+        assert s.debug["nbar"][i] == pb.n - Hb.shape[0]
+
+
+# ---------------------------------------------------------------- closed-form invariants of Sec. 4-5
+@pytest.mark.parametrize("name,N", [("single_n4", 40), ("degenerate_n12", 40), ("table1", 30), ("long_n16", 20)])
+def test_parameterisation_invariants(name, N):
+    """eqs. state-param / left-inverse: H T = 0, H t + h = 0, S T = I with S = T^T;
+    Lemma 4: Gamma Z = 0, Gamma Y + Phi = 0, Gamma y + gamma = 0."""
+    pb = synth.config(name, N=N)
+    s = oracle.solve(pb, debug=True)
+    assert s.ok
+    D, n, m = s.debug, pb.n, pb.m
+    po = np.concatenate([[0], np.cumsum(pb.p)])
+    for i in range(pb.N + 1):
+        r, nb = D["hrows"][i], D["nbar"][i]
+        H, h = D["H"][i, :r, :n], D["H"][i, :r, n]
+        T, t = D["T"][i, :, :nb], D["t"][i]
+        assert amax(T.T @ T - np.eye(nb)) < 1e-12
+        if r:
+            assert amax(H @ T) < 1e-12
+            assert amax(H @ t + h) < 1e-10 * max(1, amax(h))
+    for i in range(pb.N):
+        r1 = D["hrows"][i + 1]
+        Hn, hn = D["H"][i + 1, :r1, :n], D["H"][i + 1, :r1, n]
+        nb, mb = D["nbar"][i], D["mbar"][i]
+        T, t = D["T"][i, :, :nb], D["t"][i]
+        Cc, Dd, dd = pb.C[po[i]:po[i + 1]], pb.D[po[i]:po[i + 1]], pb.d[po[i]:po[i + 1]]
+        Gam = np.vstack([Dd, Hn @ pb.B[i]])
+        Phi = np.vstack([Cc @ T, Hn @ pb.A[i] @ T])
+        gam = np.concatenate([Cc @ t + dd, Hn @ (pb.A[i] @ t + pb.c[i]) + hn])
+        Y, Z, y = D["Y"][i, :, :nb], D["Z"][i, :, :mb], D["y"][i]
+        assert mb == (m - np.linalg.matrix_rank(Gam) if Gam.shape[0] else m)
+        if Gam.shape[0]:
+            assert amax(Gam @ Z) < 1e-11
+            assert amax(Gam @ Y + Phi) < 1e-9
+            assert amax(Gam @ y + gam) < 1e-9 * max(1, amax(gam))
+
+
+@pytest.mark.parametrize("name,N,cross", [("single_n4", 30, False), ("degenerate_n12", 20, False), ("long_n16", 12, True)])
+def test_equivalence_and_convexity(name, N, cross):
+    """Thm 5: for reduced trajectories, the original objective equals the reduced
+    objective plus sum kappa, and the recovered (x, u) are feasible.
+    Prop. 6: reduced stage Hessians PSD, Rbar PD, Qbar_N PSD."""
+    pb = synth.config(name, N=N)
+    if cross:
+        base = synth.make_problem(7, pb.N, pb.n, pb.m, pb.p, pb.q, cross=True)
+        pb = base
+    s = oracle.solve(pb, debug=True)
+    assert s.ok
+    D, Nn = s.debug, pb.N
+    nb, mb = D["nbar"], D["mbar"]
+    rng = np.random.default_rng(5)
+    for trial in range(3):
+        z = [rng.standard_normal(nb[0]) * 0.1]
+        v = []
+        for i in range(Nn):
+            v.append(rng.standard_normal(mb[i]) * 0.1)
+            z.append(D["Abar"][i, :nb[i + 1], :nb[i]] @ z[i] + D["Bbar"][i, :nb[i + 1], :mb[i]] @ v[i]
+                     + D["cbar"][i, :nb[i + 1]])
+        x = np.stack([D["T"][i, :, :nb[i]] @ z[i] + D["t"][i] for i in range(Nn + 1)])
+        u = np.stack([D["Y"][i, :, :nb[i]] @ z[i] + D["Z"][i, :, :mb[i]] @ v[i] + D["y"][i] for i in range(Nn)])
+        scale = max(1.0, amax(x), amax(u))
+        for i in range(Nn):
+            assert amax(pb.A[i] @ x[i] + pb.B[i] @ u[i] + pb.c[i] - x[i + 1]) < 1e-10 * scale
+        f = oracle.objective(pb, x, u)
+        fr = sum(0.5 * z[i] @ D["Qbar"][i, :nb[i], :nb[i]] @ z[i] + z[i] @ D["Mbar"][i, :nb[i], :mb[i]] @ v[i]
+                 + 0.5 * v[i] @ D["Rbar"][i, :mb[i], :mb[i]] @ v[i] + D["qbar"][i, :nb[i]] @ z[i]
+                 + D["rbar"][i, :mb[i]] @ v[i] for i in range(Nn))
+        fr += 0.5 * z[Nn] @ D["Qbar"][Nn, :nb[Nn], :nb[Nn]] @ z[Nn] + D["qbar"][Nn, :nb[Nn]] @ z[Nn]
+        assert abs(f - fr - D["kappa"].sum()) <= 1e-9 * max(1.0, abs(f))
+    for i in range(Nn):
+        Hs = np.block([[D["Qbar"][i, :nb[i], :nb[i]], D["Mbar"][i, :nb[i], :mb[i]]],
+                       [D["Mbar"][i, :nb[i], :mb[i]].T, D["Rbar"][i, :mb[i], :mb[i]]]])
+        if Hs.size:
+            assert np.linalg.eigvalsh(0.5 * (Hs + Hs.T)).min() > -1e-9 * max(1, amax(Hs))
+        if mb[i]:
+            assert np.linalg.eigvalsh(D["Rbar"][i, :mb[i], :mb[i]]).min() > 0
+    if nb[Nn]:
+        assert np.linalg.eigvalsh(D["Qbar"][Nn, :nb[Nn], :nb[Nn]]).min() > -1e-9
+
+
+# ---------------------------------------------------------------- against the dense KKT definition
+CLASSES = [
+    ("mixed", lambda: synth.config("single_n4", N=48)),
+    ("state_only", lambda: synth.config("table1", N=24)),
+    ("degenerate", lambda: synth.config("degenerate_n12", N=32)),
+    ("long_orthogonal", lambda: synth.config("long_n16", N=24)),
+    ("batched_n24", lambda: synth.config("batched_uneven", N=24, index=3)),
+    ("cross_terms", lambda: synth.make_problem(11, 20, 5, 3, 2, np.r_[np.zeros(20, np.int32), 2], cross=True)),
+    ("unconstrained", lambda: synth.make_problem(12, 25, 4, 2, 0, 0)),
+    ("redundant", lambda: synth.make_problem(13, 16, 4, 3, 3, np.r_[np.ones(16, np.int32), 3],
+                                             dup_rows=[(0, 1), (6, 7)], zero_D_rows=[12])),
+    ("one_stage", lambda: synth.make_problem(14, 1, 3, 2, 1, np.array([0, 1], np.int32))),
+]
+
+
+@pytest.mark.parametrize("name,make", CLASSES, ids=[c[0] for c in CLASSES])
+def test_oracle_matches_dense_kkt(name, make):
+    """x, u equal the unique minimiser of the QP; multipliers equal the dense
+    solution when J has full row rank, otherwise they satisfy KKT and differ from
+    the dense min-norm multiplier by a vector of null(J^T) (Prop. 7)."""
+    pb = make()
+    s = oracle.solve(pb)
+    assert s.ok, oracle.STATUS_NAMES[s.status]
+    d = oracle.dense_kkt(pb)
+    assert rel(s.x, d["x"]) < 1e-9 and rel(s.u, d["u"]) < 1e-9
+    r = oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha)
+    assert r < 1e-9
+    y = multiplier_vector(pb, s.lam, s.mu, s.eta, s.alpha)
+    yd = multiplier_vector(pb, d["lam"], d["mu"], d["eta"], d["alpha"])
+    if d["rank_J"] == d["rows_J"]:
+        assert rel(y, yd) < 1e-9
+    else:
+        # y - yd must lie in null(J^T): both are multipliers of the same KKT point
+        assert amax(d["J"].T @ (y - yd)) < 1e-9 * max(1.0, amax(y))
+
+
+def test_unconstrained_matches_textbook_lqr():
+    """With no constraint rows the reduction is the identity (T = I, Z = I) and the
+    result is the plain LQR solution from an independent textbook Riccati in numpy."""
+    pb = synth.make_problem(21, 30, 4, 2, 0, 0, cross=True)
+    s = oracle.solve(pb, debug=True)
+    assert (s.debug["nbar"] == 4).all() and (s.debug["mbar"] == 2).all()
+    N = pb.N
+    P, p = pb.Q[N].copy(), pb.qv[N].copy()
+    Ks, ks = [None] * N, [None] * N
+    for i in range(N - 1, -1, -1):
+        A, B, c = pb.A[i], pb.B[i], pb.c[i]
+        Huu = pb.R[i] + B.T @ P @ B
+        Hux = pb.M[i].T + B.T @ P @ A
+        hu = pb.rv[i] + B.T @ (P @ c + p)
+        Ks[i] = -np.linalg.solve(Huu, Hux)
+        ks[i] = -np.linalg.solve(Huu, hu)
+        P, p = pb.Q[i] + A.T @ P @ A + Hux.T @ Ks[i], pb.qv[i] + A.T @ (P @ c + p) + Hux.T @ ks[i]
+    x = pb.s0.copy()
+    for i in range(N):
+        u = Ks[i] @ x + ks[i]
+        assert np.abs(u - s.u[i]).max() < 1e-9 * max(1, np.abs(u).max())
+        x = pb.A[i] @ x + pb.B[i] @ u + pb.c[i]
+
+
+# ---------------------------------------------------------------- failure detection (Alg. 1)
+def test_infeasible_suffix_detected():
+    """Alg. 1: an inconsistent suffix relation returns infeasible."""
+    pb = synth.config("single_n4", N=16)
+    pb.q[-1] = 0
+    pb.E = np.zeros((0, 4)); pb.e = np.zeros(0)
+    # two copies of one terminal row with different offsets
+    pb.q[-1] = 2
+    pb.E = np.array([[1.0, 0, 0, 0], [1.0, 0, 0, 0]]); pb.e = np.array([0.0, 1.0])
+    s = oracle.solve(pb)
+    assert oracle.STATUS_NAMES[s.status] == "infeasible_suffix" and s.fail_stage == pb.N
+
+
+def test_infeasible_initial_state_detected():
+    """eq. initial-feasibility: s_0 outside X_0 returns infeasible."""
+    pb = synth.config("table1", N=8)          # E_0 rows restrict x_0
+    pb.s0 = pb.s0 + 0.1
+    s = oracle.solve(pb)
+    assert oracle.STATUS_NAMES[s.status] == "infeasible_x0"
+
+
+def test_kkt_residual_definition():
+    """Sec. 9: equality rows are divided by max(1, |coefficients|, |offset|); the
+    other blocks are plain; the norm is the maximum over all of them."""
+    pb = synth.make_problem(31, 3, 2, 1, 1, 0)
+    d = oracle.dense_kkt(pb)
+    base = oracle.kkt_residual(pb, d["x"], d["u"], d["lam"], d["mu"], d["eta"], d["alpha"])
+    assert base < 1e-12
+    pb2 = pb.copy()
+    pb2.C, pb2.D = 3 * pb.C, 3 * pb.D   # same rows scaled by 3: every row's scale exceeds 1
+    pb2.d = 3 * pb.d + 0.5              # shifts the mixed-row residual of every stage by 0.5
+    r, parts = oracle.kkt_residual(pb2, d["x"], d["u"], d["lam"], d["mu"], d["eta"], d["alpha"], parts=True)
+    sc = [max(1.0, np.abs(pb2.C[j]).max(), np.abs(pb2.D[j]).max(), abs(pb2.d[j])) for j in range(pb2.C.shape[0])]
+    assert abs(parts[2] - max(0.5 / s for s in sc)) < 1e-12
+    x = d["x"].copy(); x[0, 0] += 1e-3
+    _, parts = oracle.kkt_residual(pb, x, d["u"], d["lam"], d["mu"], d["eta"], d["alpha"], parts=True)
+    assert abs(parts[0] - 1e-3) < 1e-15
+
+
+def test_rank_tolerance_sweep_keeps_dimensions():
+    """Sec. 8 tolerance policy: reduced dimensions do not change for tau_rank in
+    1e-13..1e-8 on the degenerate workload (rank gaps are wide)."""
+    pb = synth.config("degenerate_n12", N=64)
+    ref = oracle.solve(pb, debug=True)
+    for tau in (1e-13, 1e-12, 1e-11, 1e-9, 1e-8):
+        s = oracle.solve(pb, tau_rank=tau, debug=True)
+        assert (s.debug["nbar"] == ref.debug["nbar"]).all() and (s.debug["mbar"] == ref.debug["mbar"]).all()
+
+
+# ---------------------------------------------------------------- planted mistakes are caught
+def _pins_pass(lib):
+    """The subset of the pins above that runs against an arbitrary oracle build."""
+    try:
+        for case in ("A", "B", "C"):
+            u, x1, lam1, alpha, mu, etaN = _golden_scalar()[case]
+            s = oracle.solve(_scalar(case), lib=lib)
+            if not s.ok or abs(s.u[0, 0] - u) > 1e-12 or abs(s.lam[1, 0] - lam1) > 1e-12 \
+                    or abs(s.alpha[0] - alpha) > 1e-12:
+                return False
+        for name, make in CLASSES:
+            pb = make()
+            s = oracle.solve(pb, lib=lib)
+            if not s.ok:
+                return False
+            d = oracle.dense_kkt(pb)
+            if rel(s.x, d["x"]) > 1e-9 or rel(s.u, d["u"]) > 1e-9:
+                return False
+            if oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha, lib=lib) > 1e-9:
+                return False
+            if oracle.kkt_residual(pb, d["x"], d["u"], d["lam"], d["mu"], d["eta"], d["alpha"], lib=lib) > 1e-9:
+                return False
+        pb2 = synth.make_problem(31, 3, 2, 1, 1, 0)
+        d = oracle.dense_kkt(pb2)
+        pb2.C, pb2.D, pb2.d = 3 * pb2.C, 3 * pb2.D, 3 * pb2.d + 0.5
+        _, parts = oracle.kkt_residual(pb2, d["x"], d["u"], d["lam"], d["mu"], d["eta"], d["alpha"],
+                                       parts=True, lib=lib)
+        sc = [max(1.0, np.abs(pb2.C[j]).max(), np.abs(pb2.D[j]).max(), abs(pb2.d[j])) for j in range(pb2.C.shape[0])]
+        if abs(parts[2] - max(0.5 / s for s in sc)) > 1e-12:
+            return False
+    except Exception:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("plant", range(1, 11))
+def test_planted_mistakes_are_caught(plant, tmp_path):
+    lib = oracle.load_mutant(plant, str(tmp_path))
+    assert not _pins_pass(lib), f"planted mistake {plant} slipped through the pins"
+
+
+def test_unplanted_build_passes_pin_subset(tmp_path):
+    lib = oracle.load_mutant(0, str(tmp_path))
+    assert _pins_pass(lib)
