@@ -1,0 +1,158 @@
+/*
+ * eclqr.h -- C ABI of the GB300 solver for linear equality-constrained LQR
+ * problems, following Sousa-Pinto & Orban, "An Efficient Algorithm for Solving
+ * Linear Equality-Constrained LQR Problems" (arXiv 2407.05433).
+ *
+ * Problem (Sec. 2, eq. problem), for each problem j of a batch:
+ *
+ *   min  sum_{i<N} 1/2 x_i'Q_i x_i + x_i'M_i u_i + 1/2 u_i'R_i u_i + q_i'x_i + r_i'u_i
+ *        + 1/2 x_N'Q_N x_N + q_N'x_N
+ *   s.t. x_0 = s_0,   x_{i+1} = A_i x_i + B_i u_i + c_i,
+ *        C_i x_i + D_i u_i + d_i = 0 (p_i rows),   E_i x_i + e_i = 0 (q_i rows, i = 0..N).
+ *
+ * The library runs Algorithm 1: base relations and their associative suffix
+ * scan (Sec. 3-4), domain parameterisations (eq. state-param), stage-parallel
+ * elimination (Sec. 5), the reduced unconstrained LQR (Sec. 6), recovery
+ * (eq. recovery-maps) and multipliers (Sec. 7), all in CUDA kernels for sm_103a.
+ *
+ * Layout.  All problem arrays are FP64, row-major, packed problem after
+ * problem and, inside a problem, stage after stage:
+ *   A  N*n*n    B  N*n*m    c  N*n
+ *   C  (sum_i p_i)*n   D  (sum_i p_i)*m   d  sum_i p_i      (rows of stage i after stage i-1)
+ *   E  (sum_{i<=N} q_i)*n   e  sum_{i<=N} q_i                (stage N = terminal rows)
+ *   Q  (N+1)*n*n   qv (N+1)*n          (block N is Q_N, q_N)
+ *   M  N*n*m       R  N*m*m     rv N*m
+ *   s0 n;  outputs x (N+1)*n, u N*m, lam (N+1)*n, mu sum p_i, eta sum q_i, alpha n.
+ * State and control dimensions are uniform inside one problem and may differ
+ * between problems; constraint row counts vary per stage and may be zero; rows
+ * may be dependent or redundant (Sec. 2).  eclqr_layout() returns the total
+ * element count of every array.
+ *
+ * Ownership.  Descriptor arrays are host memory, read during eclqr_create
+ * and eclqr_layout only.  Data, s0 and every output are device pointers owned
+ * by the caller; the data must stay unchanged from eclqr_build until the last
+ * call that uses the handle.  The handle owns its device workspace (the
+ * factors T, Y, Z, the reduced problem, the Riccati factors, the scan slots).
+ * Every call is asynchronous on the caller's stream (a cudaStream_t passed as
+ * void*; NULL = legacy default stream); a handle serves one stream at a time.
+ *
+ * Errors.  Return values: ECLQR_OK or a negative ECLQR_E* code for API
+ * errors detected on the host (bad arguments, allocation or launch failure).
+ * Numerical outcomes are per problem, written asynchronously to the caller's
+ * device int32 array status[num_problems] (ECLQR_STATUS_*): the first failure
+ * seen for a problem is kept.
+ */
+#ifndef ECLQR_H
+#define ECLQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define ECLQR_OK 0
+#define ECLQR_EINVAL (-1)    /* bad descriptor, option or pointer                  */
+#define ECLQR_ENOMEM (-2)    /* device allocation failed                           */
+#define ECLQR_ECUDA (-3)     /* a CUDA call or kernel launch failed                */
+#define ECLQR_ESTATE (-4)    /* call order violated (e.g. solve before build)      */
+
+/* per-problem status codes (device array) */
+#define ECLQR_STATUS_OK 0
+#define ECLQR_STATUS_INFEASIBLE_SUFFIX 1 /* a suffix relation reads 0 = gamma != 0 (Alg. 1)      */
+#define ECLQR_STATUS_INFEASIBLE_X0 2     /* s_0 violates H_0 s_0 + h_0 = 0 (eq. initial-feasibility) */
+#define ECLQR_STATUS_RANK_INCONSISTENT 3 /* nonzero residual row in Gamma u = -(Phi z + gamma) (Lemma 4 remark) */
+#define ECLQR_STATUS_NONCONVEX 4         /* Cholesky of Rbar + Bbar'P Bbar failed (Prop. 6 violated) */
+#define ECLQR_STATUS_DUAL_INCONSISTENT 5 /* a dual relation reads 0 = gamma != 0 (Sec. 7)         */
+
+typedef struct eclqr_handle eclqr_handle;
+
+/* Batch structure (host memory). */
+typedef struct {
+  int32_t num_problems;  /* P >= 1                                                    */
+  const int32_t *N;      /* [P] horizons, N_j >= 1                                    */
+  const int32_t *n;      /* [P] state dimensions, 1 <= n_j <= ECLQR_MAX_N             */
+  const int32_t *m;      /* [P] control dimensions, 1 <= m_j <= ECLQR_MAX_M           */
+  const int32_t *p;      /* [sum_j N_j] mixed rows per stage, 0 <= p_i <= ECLQR_MAX_ROWS */
+  const int32_t *q;      /* [sum_j (N_j+1)] state-only rows per stage, 0..ECLQR_MAX_ROWS */
+} eclqr_desc;
+
+#define ECLQR_MAX_N 32
+#define ECLQR_MAX_M 16
+#define ECLQR_MAX_ROWS 32
+
+/* Problem data (device memory), layout in the header comment. */
+typedef struct {
+  const double *A, *B, *c;
+  const double *C, *D, *d;
+  const double *E, *e;
+  const double *Q, *M, *R, *qv, *rv;
+} eclqr_data;
+
+typedef struct {
+  double tau_rank;   /* relative rank cut after row scaling (Sec. 8 items 1-2); default 1e-10 */
+  double tau_inc;    /* inconsistency cut on a scaled offset (Sec. 8 item 4); default 1e-8    */
+  int32_t refine;    /* refinement passes on the reduced LQR KKT residual; default 2          */
+  int32_t chunk;     /* stages per scan chunk; 0 = chosen from N and the SM count             */
+} eclqr_options;
+
+/* element counts of every packed array (for allocation) */
+typedef struct {
+  int64_t A, B, c, C, D, d, E, e, Q, M, R, qv, rv, s0;
+  int64_t x, u, lam, mu, eta, alpha;
+  int64_t stages;    /* sum_j N_j */
+} eclqr_layout_info;
+
+/* Fills *opt with the defaults above. */
+void eclqr_default_options(eclqr_options *opt);
+
+/* Validates the descriptor and returns array sizes.  Host only. */
+int eclqr_layout(const eclqr_desc *desc, eclqr_layout_info *out);
+
+/* Plans the batch and allocates the device workspace (cudaMalloc) on the
+ * current device.  opt may be NULL (defaults).  Host-synchronous. */
+int eclqr_create(const eclqr_desc *desc, const eclqr_options *opt, eclqr_handle **out);
+
+/* Feasible-domain scan and stagewise elimination of Algorithm 1 (Sec. 3-5)
+ * plus the coefficient part of the reduced Riccati solve (Sec. 6): everything
+ * that does not depend on s_0.  status: device int32[P], overwritten. */
+int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *stream);
+
+/* Checks s_0 (eq. initial-feasibility), forms z_0 (eq. reduced-initial), rolls
+ * the reduced LQR out with refinement on its KKT residual, and recovers
+ * x (N+1)*n and u N*m (eq. recovery-maps).  s0, x, u: device.  status is
+ * updated (not cleared). */
+int eclqr_solve(eclqr_handle *h, const double *s0, double *x, double *u, int32_t *status,
+                void *stream);
+
+/* Multipliers of the original problem (Sec. 7) at the last solve: lambda
+ * (N+1)*n with lambda_0 = -alpha, mu, eta, alpha.  x, u: the solve's output.
+ * Selects the min-norm representative (min-norm lambda_0, then min-norm
+ * lambda_{i+1} given lambda_i, then min-norm (mu_i, eta_i)).  Device pointers. */
+int eclqr_multipliers(eclqr_handle *h, const double *x, const double *u, double *lam,
+                      double *mu, double *eta, double *alpha, int32_t *status, void *stream);
+
+/* Infinity-norm KKT residual of the original problem (Sec. 9 residual
+ * definition): x_0 - s_0, dynamics, equality rows divided by max(1, largest
+ * |coefficient|, |offset|) of the row, and stationarity.  resid: device
+ * double[P]. */
+int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const double *u,
+                       const double *lam, const double *mu, const double *eta,
+                       const double *alpha, double *resid, void *stream);
+
+/* Reduced dimensions nbar_i (sum_j (N_j+1)) and mbar_i (sum_j N_j) of the last
+ * build, into device int32 arrays. */
+int eclqr_reduced_dims(eclqr_handle *h, int32_t *nbar, int32_t *mbar, void *stream);
+
+/* Kernel launches issued by the last build/solve/multipliers/residual calls
+ * of this handle (host counters, for launch accounting). */
+int64_t eclqr_launch_count(const eclqr_handle *h);
+
+void eclqr_destroy(eclqr_handle *h);
+const char *eclqr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ECLQR_H */

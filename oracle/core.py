@@ -45,7 +45,7 @@ class _Problem(ct.Structure):
 class _Debug(ct.Structure):
     _fields_ = [(k, ct.c_void_p) for k in ("nbar", "mbar", "hrows", "H", "T", "t", "Y", "Z", "y",
                                            "Abar", "Bbar", "cbar", "Qbar", "Mbar", "Rbar", "qbar",
-                                           "rbar", "kappa", "z", "v", "lrows", "L")]
+                                           "rbar", "kappa", "z", "v", "lrows", "L", "pi", "UT")]
 
 
 class _Options(ct.Structure):
@@ -147,7 +147,7 @@ def solve(pb, tau_rank=1e-10, tau_inc=1e-8, multipliers=True, debug=False, refin
             Qbar=np.zeros((N + 1, n, n)), Mbar=np.zeros((N, n, m)), Rbar=np.zeros((N, m, m)),
             qbar=np.zeros((N + 1, n)), rbar=np.zeros((N, m)), kappa=np.zeros(N + 1),
             z=np.zeros((N + 1, n)), v=np.zeros((N, m)), lrows=np.zeros(N + 1, np.int32),
-            L=np.zeros((N + 1, n, n + 1)))
+            L=np.zeros((N + 1, n, n + 1)), pi=np.zeros((N + 1, n)), UT=np.zeros((N + 1, n, n)))
         dbgp = ct.byref(_Debug(*[dbg_arrays[k].ctypes.data for k, _ in _Debug._fields_]))
     opt = _Options(tau_rank, tau_inc, refine)
     st = lib.orc_solve(ct.byref(s), ct.byref(opt), x.ctypes.data, u.ctypes.data,

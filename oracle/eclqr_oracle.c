@@ -382,6 +382,8 @@ typedef struct {
   double *v;      /* N x m */
   int *lrows;     /* [N+1] rows of the admissible costate sets */
   double *L;      /* (N+1) x n x (n+1) */
+  double *pi;     /* (N+1) x n: reduced costates P_i z_i + p_i (refined) */
+  double *UT;     /* (N+1) x n x n: [U_i | T_i] */
 } orc_debug;
 
 typedef struct {
@@ -704,58 +706,146 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
     free(Gm); free(Rhs); free(Sol); free(Qf); free(AT); free(tmp); free(tmp2);
     free(rz); free(qz); free(Mz); free(RY); free(RZ); free(Ry); free(BZ);
   }
-  /* ---- 7. sequential Riccati on the reduced LQR (textbook recursion, cross term kept) ----
-   * Coefficient pass: P_N = Qbar_N; H_uu = Rbar + Bbar^T P Bbar, H_ux = Mbar^T + Bbar^T P Abar,
-   * K = -H_uu^{-1} H_ux, P_i = Qbar + Abar^T P Abar + H_ux^T K.  The linear pass (p, k) and
-   * the rollout are functions of the offsets (qbar, rbar, cbar, z_0) only, so the same
-   * factors serve the refinement solves below. */
+  /* ---- 7. square-root (information form) Riccati on the reduced LQR ----
+   * The paper leaves the unconstrained LQR solver open (Sec. 6).  The textbook
+   * recursion P_i = Qbar + Abar'P Abar - H_ux' H_uu^{-1} H_ux cancels large
+   * terms when P grows through stretches without control authority, so the
+   * value functions are carried in square-root form V_i(z) = 1/2 ||R_i z + s_i||^2
+   * (R_i upper triangular): with L L' the Cholesky factor of the stage Hessian
+   * [[Qbar, Mbar], [Mbar', Rbar]] (order z, v), the rows
+   *     [ L'_v | L'_z | L^{-1}[qbar; rbar] ]     (stage cost)
+   *     [ R_{i+1} Bbar | R_{i+1} Abar | R_{i+1} cbar + s_{i+1} ]   (cost to go)
+   * over the columns (v | z | 1) are reduced by Householder QR; the first mbar
+   * rows give R_vv v + R_vz z + o_v = 0 at the minimiser (K, k), the next nbar
+   * rows give R_i, s_i.  P_i = R_i'R_i, H_uu = R_vv'R_vv, H_ux = R_vv'R_vz. */
   {
-    double *Pm = dalloc((size_t)n * n), *PA = dalloc((size_t)n * n), *PB = dalloc((size_t)n * m);
-    double *Pn = dalloc((size_t)n * n);
+    double *Rn = dalloc((size_t)n * n), *sn = dalloc(n), *St = dalloc((size_t)(2 * n + m) * (n + m + 1));
+    double *Hs = dalloc((size_t)(n + m) * (n + m)), *lv = dalloc(n + m), *vv2 = dalloc(2 * n + m);
     int nN = nb[N];
+    /* R_N = chol(Qbar_N)', s_N = R_N^{-T} qbar_N */
     for (int a = 0; a < nN; a++)
-      for (int j = 0; j < nN; j++) Pm[a * n + j] = Qb[(size_t)N * n * n + a * n + j];
-    memcpy(Pst + (size_t)N * n * n, Pm, sizeof(double) * n * n);
-    for (int i = N - 1; i >= 0; i--) {
-      int ni = nb[i], nn = nb[i + 1], mi = mb[i];
-      const double *Abi = Ab + (size_t)i * n * n, *Bbi = Bb + (size_t)i * n * m;
-      double *Lh = Lhs + (size_t)i * m * m, *Hx = Hxs + (size_t)i * m * n, *Ki = Kg + (size_t)i * m * n;
-      gemm(0, 0, nn, ni, nn, 1.0, Pm, n, Abi, n, 0.0, PA, n);
-      if (mi > 0) {
-        gemm(0, 0, nn, mi, nn, 1.0, Pm, n, Bbi, m, 0.0, PB, m);
-        gemm(1, 0, mi, mi, nn, 1.0, Bbi, m, PB, m, 0.0, Lh, mi);
-        for (int a = 0; a < mi; a++)
-          for (int j = 0; j < mi; j++) Lh[a * mi + j] += Rb[(size_t)i * m * m + a * m + j];
-        for (int a = 0; a < mi; a++)
-          for (int j = 0; j < ni; j++) {
-            double s = Mb[(size_t)i * n * m + j * m + a];
-            for (int l = 0; l < nn; l++) s += Bbi[l * m + a] * PA[l * n + j];
-            Hx[a * n + j] = s;
-          }
-        g_flops += 2.0 * mi * nn * ni;
-        if (cholesky(Lh, mi)) { status = ORC_NONCONVEX; *fail_stage = i; break; }
-        double *G = dalloc((size_t)mi * (ni ? ni : 1));
-        for (int a = 0; a < mi; a++)
-          for (int j = 0; j < ni; j++) G[a * ni + j] = Hx[a * n + j];
-        if (ni) chol_solve(Lh, mi, G, ni);
-        for (int a = 0; a < mi; a++)
-          for (int j = 0; j < ni; j++) Ki[a * n + j] = -G[a * ni + j];
-        free(G);
-      }
-      for (int a = 0; a < ni; a++)
-        for (int j = 0; j < ni; j++) {
-          double s = Qb[(size_t)i * n * n + a * n + j];
-          for (int l = 0; l < nn; l++) s += Abi[l * n + a] * PA[l * n + j];
-          if (ORC_PLANT != 4)
-            for (int l = 0; l < mi; l++) s += Hx[l * n + a] * Ki[l * n + j];
-          Pn[a * n + j] = s;
-        }
-      g_flops += 2.0 * ni * ni * (nn + mi);
-      for (int a = 0; a < ni; a++)
-        for (int j = 0; j < ni; j++) Pm[a * n + j] = 0.5 * (Pn[a * n + j] + Pn[j * n + a]);
-      memcpy(Pst + (size_t)i * n * n, Pm, sizeof(double) * n * n);
+      for (int j = 0; j < nN; j++) Hs[a * nN + j] = Qb[(size_t)N * n * n + a * n + j];
+    if (nN && cholesky(Hs, nN)) { status = ORC_NONCONVEX; *fail_stage = N; }
+    for (int a = 0; a < nN; a++) {
+      for (int j = 0; j < nN; j++) Rn[a * n + j] = Hs[j * nN + a];
+      double s = qb[(size_t)N * n + a];
+      for (int l = 0; l < a; l++) s -= Hs[a * nN + l] * sn[l];
+      sn[a] = s / Hs[a * nN + a];
     }
-    free(Pm); free(PA); free(PB); free(Pn);
+    for (int a = 0; a < nN; a++) {
+      for (int j = 0; j < nN; j++) {
+        double s = 0.0;
+        for (int l = 0; l < nN; l++) s += Rn[l * n + a] * Rn[l * n + j];
+        Pst[(size_t)N * n * n + a * n + j] = s;
+      }
+      pst[(size_t)N * n + a] = qb[(size_t)N * n + a];
+    }
+    for (int i = N - 1; i >= 0 && status == ORC_OK; i--) {
+      int ni = nb[i], nn = nb[i + 1], mi = mb[i];
+      int k = ni + mi, rows = k + nn, ld = k + 1;
+      const double *Abi = Ab + (size_t)i * n * n, *Bbi = Bb + (size_t)i * n * m, *cbi = cb + (size_t)i * n;
+      /* stage Hessian in (z, v) order, Cholesky */
+      for (int a = 0; a < k; a++)
+        for (int j = 0; j < k; j++) {
+          double h;
+          if (a < ni && j < ni) h = Qb[(size_t)i * n * n + a * n + j];
+          else if (a < ni) h = Mb[(size_t)i * n * m + a * m + (j - ni)];
+          else if (j < ni) h = Mb[(size_t)i * n * m + j * m + (a - ni)];
+          else h = Rb[(size_t)i * m * m + (a - ni) * m + (j - ni)];
+          Hs[a * k + j] = h;
+        }
+      if (cholesky(Hs, k)) { status = ORC_NONCONVEX; *fail_stage = i; break; }
+      /* l = L^{-1} [qbar; rbar] */
+      for (int a = 0; a < k; a++) {
+        double s = (a < ni) ? qb[(size_t)i * n + a] : rb[(size_t)i * m + (a - ni)];
+        for (int l = 0; l < a; l++) s -= Hs[a * k + l] * lv[l];
+        lv[a] = s / Hs[a * k + a];
+      }
+      /* stacked rows, columns (v | z | 1) */
+      memset(St, 0, sizeof(double) * rows * ld);
+      for (int a = 0; a < k; a++) {
+        for (int j = 0; j < ni; j++) St[a * ld + mi + j] = Hs[j * k + a];        /* (L')_{a, z_j} */
+        for (int j = 0; j < mi; j++) St[a * ld + j] = Hs[(ni + j) * k + a];     /* (L')_{a, v_j} */
+        St[a * ld + k] = lv[a];
+      }
+      for (int a = 0; a < nn; a++) {
+        int row = k + a;
+        for (int j = 0; j < mi; j++) {
+          double s = 0.0;
+          for (int l = 0; l < nn; l++) s += ((ORC_PLANT == 4) ? Rn[l * n + a] : Rn[a * n + l]) * Bbi[l * m + j];
+          St[row * ld + j] = s;
+        }
+        for (int j = 0; j < ni; j++) {
+          double s = 0.0;
+          for (int l = 0; l < nn; l++) s += ((ORC_PLANT == 4) ? Rn[l * n + a] : Rn[a * n + l]) * Abi[l * n + j];
+          St[row * ld + mi + j] = s;
+        }
+        double s = sn[a];
+        for (int l = 0; l < nn; l++) s += Rn[a * n + l] * cbi[l];
+        St[row * ld + k] = s;
+      }
+      g_flops += 2.0 * nn * nn * (mi + ni + 1) + (double)k * k * k / 3.0;
+      /* Householder QR over the first k columns, no pivoting */
+      for (int c = 0; c < k; c++) {
+        double nrm = 0.0;
+        for (int r = c; r < rows; r++) nrm += St[r * ld + c] * St[r * ld + c];
+        nrm = sqrt(nrm);
+        if (nrm == 0.0) continue;
+        double xk = St[c * ld + c], sg = xk >= 0.0 ? 1.0 : -1.0;
+        for (int r = c; r < rows; r++) vv2[r] = St[r * ld + c];
+        vv2[c] = xk + sg * nrm;
+        double beta = 1.0 / (nrm * (nrm + fabs(xk)));
+        for (int j = c + 1; j < ld; j++) {
+          double w = 0.0;
+          for (int r = c; r < rows; r++) w += vv2[r] * St[r * ld + j];
+          w *= beta;
+          for (int r = c; r < rows; r++) St[r * ld + j] -= w * vv2[r];
+        }
+        St[c * ld + c] = -sg * nrm;
+        for (int r = c + 1; r < rows; r++) St[r * ld + c] = 0.0;
+        g_flops += 4.0 * (rows - c) * (ld - c);
+      }
+      /* K, k: R_vv v = -(R_vz z + o_v) */
+      double *Ki = Kg + (size_t)i * m * n, *ki = kg + (size_t)i * m;
+      for (int col = 0; col <= ni; col++) {
+        /* back substitution for column col of -[R_vz | o_v] */
+        for (int a = mi - 1; a >= 0; a--) {
+          double s = -St[a * ld + mi + col];
+          for (int l = a + 1; l < mi; l++) s -= St[a * ld + l] * ((col < ni) ? Ki[l * n + col] : ki[l]);
+          s /= St[a * ld + a];
+          if (col < ni) Ki[a * n + col] = s; else ki[a] = s;
+        }
+      }
+      /* H_uu = R_vv'R_vv -> Cholesky factor with positive diagonal; H_ux = R_vv'R_vz */
+      double *Lh = Lhs + (size_t)i * m * m, *Hx = Hxs + (size_t)i * m * n;
+      for (int a = 0; a < mi; a++) {
+        double sga = St[a * ld + a] >= 0.0 ? 1.0 : -1.0;
+        for (int j = 0; j < mi; j++) Lh[j * mi + a] = (j >= a) ? sga * St[a * ld + j] : 0.0;
+      }
+      for (int a = 0; a < mi; a++)
+        for (int j = 0; j < ni; j++) {
+          double s = 0.0;
+          for (int l = 0; l <= a && l < mi; l++) s += St[l * ld + a] * St[l * ld + mi + j];
+          Hx[a * n + j] = s;
+        }
+      /* R_i, s_i and P_i = R_i'R_i */
+      for (int a = 0; a < ni; a++) {
+        for (int j = 0; j < ni; j++) Rn[a * n + j] = (j >= a) ? St[(mi + a) * ld + mi + j] : 0.0;
+        sn[a] = St[(mi + a) * ld + k];
+      }
+      for (int a = 0; a < ni; a++) {
+        for (int j = 0; j < ni; j++) {
+          double s = 0.0;
+          for (int l = 0; l < ni; l++) s += Rn[l * n + a] * Rn[l * n + j];
+          Pst[(size_t)i * n * n + a * n + j] = s;
+        }
+        double s = 0.0;
+        for (int l = 0; l < ni; l++) s += Rn[l * n + a] * sn[l];
+        pst[(size_t)i * n + a] = s;                         /* p_i = R_i' s_i */
+      }
+      g_flops += 2.0 * ni * ni * ni + 2.0 * mi * mi * ni;
+    }
+    free(Rn); free(sn); free(St); free(Hs); free(lv); free(vv2);
     if (status != ORC_OK) goto done;
   }
   /* ---- 8. linear pass, rollout (eq. reduced-initial) and refinement on the reduced KKT ----
@@ -780,8 +870,9 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
     }
     for (int pass = 0; pass <= opt->refine; pass++) {
       double *Z_ = pass ? dz : zz, *V_ = pass ? dv : vv, *PI_ = pass ? dpi : pis;
-      /* linear pass */
+      /* linear pass (pass 0 takes p_i, k_i from the square-root recursion) */
       int nN = nb[N];
+      if (pass) {
       for (int a = 0; a < nN; a++) pv[a] = qo_[(size_t)N * n + a];
       memcpy(pst + (size_t)N * n, pv, sizeof(double) * n);
       for (int i = N - 1; i >= 0; i--) {
@@ -809,6 +900,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         }
         memcpy(pst + (size_t)i * n, pv, sizeof(double) * n);
         g_flops += 2.0 * nn * nn + 2.0 * mi * nn + 2.0 * ni * (nn + mi);
+      }
       }
       /* rollout v = K z + k, z+ = Abar z + Bbar v + cbar; costates pi = P z + p */
       for (int a = 0; a < nb[0]; a++) Z_[a] = pass ? 0.0 : z0[a];
@@ -1205,6 +1297,8 @@ done:
     if (dbg->rbar) memcpy(dbg->rbar, rb, sizeof(double) * N * m);
     if (dbg->kappa) memcpy(dbg->kappa, kap, sizeof(double) * (N + 1));
     if (dbg->z) memcpy(dbg->z, zz, sizeof(double) * (N + 1) * n);
+    if (dbg->pi) memcpy(dbg->pi, pis, sizeof(double) * (N + 1) * n);
+    if (dbg->UT) memcpy(dbg->UT, Ux, sizeof(double) * (N + 1) * n * n);
     if (dbg->v) memcpy(dbg->v, vv, sizeof(double) * N * m);
   }
   if (flops) *flops = g_flops;

@@ -1,0 +1,427 @@
+// api.cu -- host orchestration behind the C ABI of include/eclqr.h.
+//
+// eclqr_create plans the batch (groups of equal (n, m), stage and chunk
+// descriptors, workspace layout) and allocates one device block per group.
+// The other calls only enqueue kernels on the caller's stream: no host
+// synchronisation, no allocation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/eclqr.h"
+#include "kernels.cuh"
+
+using namespace eclqr;
+
+namespace {
+
+constexpr int kMaxSmemBytes = 227 * 1024;
+
+struct GroupHost {
+  Group g;
+  int maxnch = 0;
+  int levels = 0;
+  void *dmem = nullptr;
+  std::vector<int> ids;  // batch indices of the problems in this group
+};
+
+int ilog2ceil(int x) {
+  int k = 0;
+  while ((1 << k) < x) k++;
+  return k;
+}
+
+}  // namespace
+
+struct eclqr_handle {
+  int P = 0;
+  eclqr_options opt;
+  eclqr_layout_info lay;
+  std::vector<GroupHost> groups;
+  long long launches = 0;
+  bool built = false, solved = false;
+  int device = 0;
+};
+
+namespace {
+
+// one warp per task, W warps per CTA chosen from the shared memory each warp needs
+template <typename... KArgs, typename... Args>
+int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_warp, cudaStream_t st, Args... args) {
+  if (ntasks <= 0) return ECLQR_OK;
+  const size_t wbytes = (size_t)per_warp * sizeof(double);
+  int W = 4;
+  if (wbytes > 0) W = (int)std::max<size_t>(1, std::min<size_t>(4, kMaxSmemBytes / wbytes));
+  if (wbytes * W > (size_t)kMaxSmemBytes) return ECLQR_EINVAL;
+  const size_t smem = wbytes * W;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return ECLQR_ECUDA;
+  }
+  const int grid = (ntasks + W - 1) / W;
+  kern<<<grid, 32 * W, smem, st>>>(args...);
+  h->launches++;
+  return cudaPeekAtLastError() == cudaSuccess ? ECLQR_OK : ECLQR_ECUDA;
+}
+
+#define TRY(x)                 \
+  do {                         \
+    int _rc = (x);             \
+    if (_rc != ECLQR_OK) return _rc; \
+  } while (0)
+
+int validate(const eclqr_desc *d) {
+  if (!d || d->num_problems < 1 || !d->N || !d->n || !d->m || !d->p || !d->q) return ECLQR_EINVAL;
+  long long ps = 0, qs = 0;
+  for (int j = 0; j < d->num_problems; j++) {
+    if (d->N[j] < 1 || d->n[j] < 1 || d->n[j] > ECLQR_MAX_N || d->m[j] < 1 || d->m[j] > ECLQR_MAX_M)
+      return ECLQR_EINVAL;
+    for (int i = 0; i < d->N[j]; i++)
+      if (d->p[ps + i] < 0 || d->p[ps + i] > ECLQR_MAX_ROWS) return ECLQR_EINVAL;
+    for (int i = 0; i <= d->N[j]; i++)
+      if (d->q[qs + i] < 0 || d->q[qs + i] > ECLQR_MAX_ROWS) return ECLQR_EINVAL;
+    ps += d->N[j];
+    qs += d->N[j] + 1;
+  }
+  return ECLQR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void eclqr_default_options(eclqr_options *opt) {
+  if (!opt) return;
+  opt->tau_rank = 1e-10;
+  opt->tau_inc = 1e-8;
+  opt->refine = 2;
+  opt->chunk = 0;
+}
+
+int eclqr_layout(const eclqr_desc *d, eclqr_layout_info *out) {
+  if (!out) return ECLQR_EINVAL;
+  TRY(validate(d));
+  eclqr_layout_info L;
+  std::memset(&L, 0, sizeof(L));
+  long long ps = 0, qs = 0;
+  for (int j = 0; j < d->num_problems; j++) {
+    const long long N = d->N[j], n = d->n[j], m = d->m[j];
+    long long Pj = 0, Qj = 0;
+    for (int i = 0; i < N; i++) Pj += d->p[ps + i];
+    for (int i = 0; i <= N; i++) Qj += d->q[qs + i];
+    ps += N;
+    qs += N + 1;
+    L.A += N * n * n; L.B += N * n * m; L.c += N * n;
+    L.C += Pj * n; L.D += Pj * m; L.d += Pj;
+    L.E += Qj * n; L.e += Qj;
+    L.Q += (N + 1) * n * n; L.M += N * n * m; L.R += N * m * m; L.qv += (N + 1) * n; L.rv += N * m;
+    L.s0 += n; L.x += (N + 1) * n; L.u += N * m; L.lam += (N + 1) * n; L.mu += Pj; L.eta += Qj; L.alpha += n;
+    L.stages += N;
+  }
+  *out = L;
+  return ECLQR_OK;
+}
+
+int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **out) {
+  if (!out) return ECLQR_EINVAL;
+  *out = nullptr;
+  TRY(validate(d));
+  eclqr_handle *h = new (std::nothrow) eclqr_handle();
+  if (!h) return ECLQR_ENOMEM;
+  eclqr_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0)) {
+    delete h;
+    return ECLQR_EINVAL;
+  }
+  eclqr_layout(d, &h->lay);
+  h->P = d->num_problems;
+  cudaGetDevice(&h->device);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+
+  // batch offsets of every problem
+  const int P = d->num_problems;
+  std::vector<ProbInfo> pinfo(P);
+  std::vector<long long> pstage(P + 1, 0), qstage(P + 1, 0);
+  {
+    long long oA = 0, oB = 0, oc = 0, oC = 0, oD = 0, od = 0, oE = 0, oe = 0, oQ = 0, oM = 0, oR = 0, oqv = 0,
+              orv = 0, os0 = 0, ox = 0, ou = 0, olam = 0, omu = 0, oeta = 0, oal = 0;
+    for (int j = 0; j < P; j++) {
+      const long long N = d->N[j], n = d->n[j], m = d->m[j];
+      pstage[j + 1] = pstage[j] + N;
+      qstage[j + 1] = qstage[j] + N + 1;
+      long long Pj = 0, Qj = 0;
+      for (long long i = 0; i < N; i++) Pj += d->p[pstage[j] + i];
+      for (long long i = 0; i <= N; i++) Qj += d->q[qstage[j] + i];
+      ProbInfo &pi = pinfo[j];
+      std::memset(&pi, 0, sizeof(pi));
+      pi.N = (int)N;
+      pi.id = j;
+      pi.oA = oA; pi.oB = oB; pi.oc = oc; pi.oC = oC; pi.oD = oD; pi.od = od; pi.oE = oE; pi.oe = oe;
+      pi.oQ = oQ; pi.oM = oM; pi.oR = oR; pi.oqv = oqv; pi.orv = orv;
+      pi.os0 = os0; pi.ox = ox; pi.ou = ou; pi.olam = olam; pi.omu = omu; pi.oeta = oeta; pi.oalpha = oal;
+      oA += N * n * n; oB += N * n * m; oc += N * n; oC += Pj * n; oD += Pj * m; od += Pj; oE += Qj * n; oe += Qj;
+      oQ += (N + 1) * n * n; oM += N * n * m; oR += N * m * m; oqv += (N + 1) * n; orv += N * m;
+      os0 += n; ox += (N + 1) * n; ou += N * m; olam += (N + 1) * n; omu += Pj; oeta += Qj; oal += n;
+    }
+  }
+  // groups of equal (n, m)
+  std::map<std::pair<int, int>, std::vector<int>> by_dims;
+  for (int j = 0; j < P; j++) by_dims[{d->n[j], d->m[j]}].push_back(j);
+  long long total_stages = h->lay.stages;
+  for (auto &kv : by_dims) {
+    GroupHost gh;
+    Group &g = gh.g;
+    std::memset(&g, 0, sizeof(g));
+    g.n = kv.first.first;
+    g.m = kv.first.second;
+    gh.ids = kv.second;
+    int pmax = 0, qmax = 0;
+    for (int j : gh.ids) {
+      for (long long i = 0; i < d->N[j]; i++) pmax = std::max(pmax, d->p[pstage[j] + i]);
+      for (long long i = 0; i <= d->N[j]; i++) qmax = std::max(qmax, d->q[qstage[j] + i]);
+    }
+    g.pmax = pmax;
+    g.qmax = qmax;
+    std::vector<ProbInfo> gp;
+    std::vector<StageInfo> gs;
+    std::vector<ChunkInfo> gc;
+    for (int j : gh.ids) {
+      ProbInfo pi = pinfo[j];
+      int L = h->opt.chunk;
+      if (L <= 0) {
+        // enough chunks to give every SM sub-partition work, short chunks for short horizons
+        long long target = std::max<long long>(1, total_stages / (4LL * sms));
+        L = (int)std::min<long long>(64, std::max<long long>(4, target));
+        if (pi.N < 4 * L) L = std::max(2, pi.N / 8);
+        L = std::max(1, std::min(L, pi.N));
+      }
+      pi.L = L;
+      pi.nch = (pi.N + L - 1) / L;
+      pi.ch0 = (int)gc.size();
+      pi.st0 = (int)gs.size();
+      const int local = (int)gp.size();
+      int prow = 0, qrow = 0;
+      for (int i = 0; i <= pi.N; i++) {
+        StageInfo si;
+        si.prob = local;
+        si.i = i;
+        si.p = (i < pi.N) ? d->p[pstage[j] + i] : 0;
+        si.q = d->q[qstage[j] + i];
+        si.prow = prow;
+        si.qrow = qrow;
+        prow += si.p;
+        qrow += si.q;
+        gs.push_back(si);
+      }
+      for (int c = 0; c <= pi.nch; c++) gc.push_back(ChunkInfo{local, c});
+      gh.maxnch = std::max(gh.maxnch, pi.nch);
+      gp.push_back(pi);
+    }
+    g.nprob = (int)gp.size();
+    g.nstage = (int)gs.size();
+    g.nslot = (int)gc.size();
+    gh.levels = ilog2ceil(gh.maxnch + 1);
+    g.ws = make_ws_layout(g.n, g.m, pmax, qmax);
+    g.cs_stride = ((8 * g.n * g.n + 4 * g.n) + 3) & ~3;  // cost relations: 2n constraint + 2n cost rows
+    g.cr_stride = 0;
+    g.tau_rank = h->opt.tau_rank;
+    g.tau_inc = h->opt.tau_inc;
+    // one allocation: descriptors, stage workspace, chunk slots
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t r = off; off += (bytes + 255) & ~size_t(255); return r; };
+    size_t o_prob = take(sizeof(ProbInfo) * gp.size()), o_st = take(sizeof(StageInfo) * gs.size()),
+           o_ch = take(sizeof(ChunkInfo) * gc.size());
+    size_t o_W = take(sizeof(double) * (size_t)g.ws.stride * g.nstage);
+    size_t o_WI = take(sizeof(int) * (size_t)SI_STRIDE * g.nstage);
+    size_t o_CS0 = take(sizeof(double) * (size_t)g.cs_stride * g.nslot);
+    size_t o_CS1 = take(sizeof(double) * (size_t)g.cs_stride * g.nslot);
+    size_t o_CI0 = take(sizeof(int) * CI_STRIDE * g.nslot), o_CI1 = take(sizeof(int) * CI_STRIDE * g.nslot);
+    if (cudaMalloc(&gh.dmem, off) != cudaSuccess) {
+      for (auto &x : h->groups) cudaFree(x.dmem);
+      delete h;
+      return ECLQR_ENOMEM;
+    }
+    char *base = (char *)gh.dmem;
+    cudaMemset(gh.dmem, 0, off);
+    cudaMemcpy(base + o_prob, gp.data(), sizeof(ProbInfo) * gp.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(base + o_st, gs.data(), sizeof(StageInfo) * gs.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(base + o_ch, gc.data(), sizeof(ChunkInfo) * gc.size(), cudaMemcpyHostToDevice);
+    g.prob = (const ProbInfo *)(base + o_prob);
+    g.st = (const StageInfo *)(base + o_st);
+    g.chunk = (const ChunkInfo *)(base + o_ch);
+    g.W = (double *)(base + o_W);
+    g.WI = (int *)(base + o_WI);
+    g.CS[0] = (double *)(base + o_CS0);
+    g.CS[1] = (double *)(base + o_CS1);
+    g.CI[0] = (int *)(base + o_CI0);
+    g.CI[1] = (int *)(base + o_CI1);
+    // every kernel's shared memory must fit one warp
+    const int n = g.n, m = g.m;
+    const int need = std::max({smem_primal_sweep(n, m, pmax, qmax), smem_rel_level(n, pmax, qmax), smem_param(n),
+                               smem_elim(n, m, pmax), smem_lqr_up(n, m), smem_lqr_level(n), smem_riccati(n, m),
+                               smem_aff(n), smem_dual_stage(n, m), smem_dual_sweep(n, m, pmax, qmax),
+                               smem_dual_leaf(n, m, pmax, qmax)});
+    if ((size_t)need * sizeof(double) > (size_t)kMaxSmemBytes) {
+      cudaFree(gh.dmem);
+      for (auto &x : h->groups) cudaFree(x.dmem);
+      delete h;
+      return ECLQR_EINVAL;
+    }
+    h->groups.push_back(gh);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    for (auto &x : h->groups) cudaFree(x.dmem);
+    delete h;
+    return ECLQR_ECUDA;
+  }
+  *out = h;
+  return ECLQR_OK;
+}
+
+int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *stream) {
+  if (!h || !data || !status) return ECLQR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
+  for (auto &gh : h->groups) {
+    Group &g = gh.g;
+    g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
+    g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
+    g.status = status;
+    const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
+    const int sw = smem_primal_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
+    TRY(launch(h, k_terminal, g.nprob, sw, st, g, sw));
+    TRY(launch(h, k_primal_up, g.nslot, sw, st, g, sw));
+    int src = 0;
+    for (int k = 0; k < gh.levels; k++, src ^= 1)
+      TRY(launch(h, k_rel_level, g.nslot, sl, st, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
+    TRY(launch(h, k_primal_down, g.nslot, sw, st, g, src, sw));
+    const int sp = smem_param(n), se = smem_elim(n, m, pm);
+    TRY(launch(h, k_param, g.nstage, sp, st, g, sp));
+    TRY(launch(h, k_elim, g.nstage, se, st, g, se));
+    const int su = smem_lqr_up(n, m), slv = smem_lqr_level(n), sr = smem_riccati(n, m);
+    TRY(launch(h, k_lqr_up, g.nslot, su, st, g, su));
+    src = 0;
+    for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_lqr_level, g.nslot, slv, st, g, src, 1 << k, slv));
+    TRY(launch(h, k_riccati_down, g.nslot, sr, st, g, src, sr));
+  }
+  h->built = true;
+  h->solved = false;
+  return ECLQR_OK;
+}
+
+namespace {
+int aff_scan(eclqr_handle *h, GroupHost &gh, int mode, cudaStream_t st) {
+  Group &g = gh.g;
+  const int sa = smem_aff(g.n);
+  const int fwd = (mode == AFF_CLIN_) ? 0 : 1;
+  TRY(launch(h, k_aff_up, g.nslot, sa, st, g, mode, sa));
+  int src = 0;
+  for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_aff_level, g.nslot, sa, st, g, src, 1 << k, fwd, sa));
+  TRY(launch(h, k_aff_down, g.nslot, sa, st, g, mode, src, sa));
+  return ECLQR_OK;
+}
+}  // namespace
+
+int eclqr_solve(eclqr_handle *h, const double *s0, double *x, double *u, int32_t *status, void *stream) {
+  if (!h || !s0 || !x || !u || !status) return ECLQR_EINVAL;
+  if (!h->built) return ECLQR_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (auto &gh : h->groups) {
+    Group &g = gh.g;
+    g.status = status;
+    TRY(launch(h, k_solve_init, g.nprob, 0, st, g, s0));
+    TRY(aff_scan(h, gh, AFF_ROLL_, st));
+    TRY(launch(h, k_post_roll, g.nstage, 0, st, g, 0));
+    for (int r = 0; r < h->opt.refine; r++) {
+      TRY(launch(h, k_resid, g.nstage, 0, st, g));
+      TRY(aff_scan(h, gh, AFF_CLIN_, st));
+      TRY(launch(h, k_kcorr, g.nstage, 0, st, g));
+      TRY(aff_scan(h, gh, AFF_CROLL_, st));
+      TRY(launch(h, k_post_roll, g.nstage, 0, st, g, 1));
+    }
+    TRY(launch(h, k_recover, g.nstage, 0, st, g, x, u));
+  }
+  h->solved = true;
+  return ECLQR_OK;
+}
+
+int eclqr_multipliers(eclqr_handle *h, const double *x, const double *u, double *lam, double *mu, double *eta,
+                      double *alpha, int32_t *status, void *stream) {
+  if (!h || !x || !u || !lam || !alpha || !status) return ECLQR_EINVAL;
+  if (h->lay.mu > 0 && !mu) return ECLQR_EINVAL;
+  if (h->lay.eta > 0 && !eta) return ECLQR_EINVAL;
+  if (!h->solved) return ECLQR_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (auto &gh : h->groups) {
+    Group &g = gh.g;
+    g.status = status;
+    const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
+    const int sd = smem_dual_stage(n, m), sw = smem_dual_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
+    const int sf = smem_dual_leaf(n, m, pm, qm);
+    TRY(launch(h, k_dual_stage, g.nstage, sd, st, g, x, u, sd));
+    TRY(launch(h, k_dual_terminal, g.nprob, sw, st, g, sw));
+    TRY(launch(h, k_dual_up, g.nslot, sw, st, g, sw));
+    int src = 0;
+    for (int k = 0; k < gh.levels; k++, src ^= 1)
+      TRY(launch(h, k_rel_level, g.nslot, sl, st, g, src, 1 << k, (int)ST_DUAL_INCONSISTENT, sl));
+    TRY(launch(h, k_dual_down, g.nslot, sw, st, g, src, sw));
+    TRY(launch(h, k_dual_root, g.nprob, sw, st, g, sw));
+    TRY(aff_scan(h, gh, AFF_NU_, st));
+    TRY(launch(h, k_dual_leaf, g.nstage, sf, st, g, lam, mu, eta, alpha, sf));
+  }
+  return ECLQR_OK;
+}
+
+int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const double *u, const double *lam,
+                       const double *mu, const double *eta, const double *alpha, double *resid, void *stream) {
+  if (!h || !s0 || !x || !u || !lam || !alpha || !resid) return ECLQR_EINVAL;
+  if (!h->built) return ECLQR_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(resid, 0, sizeof(double) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
+  for (auto &gh : h->groups) {
+    Group &g = gh.g;
+    TRY(launch(h, k_kkt_residual, g.nstage, 0, st, g, s0, x, u, lam, mu, eta, alpha, resid));
+  }
+  return ECLQR_OK;
+}
+
+int eclqr_reduced_dims(eclqr_handle *h, int32_t *nbar, int32_t *mbar, void *stream) {
+  if (!h || !nbar || !mbar) return ECLQR_EINVAL;
+  if (!h->built) return ECLQR_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (auto &gh : h->groups) {
+    const int blocks = (gh.g.nstage + 255) / 256;
+    k_dims<<<blocks, 256, 0, st>>>(gh.g, nbar, mbar);
+    h->launches++;
+    if (cudaPeekAtLastError() != cudaSuccess) return ECLQR_ECUDA;
+  }
+  return ECLQR_OK;
+}
+
+int64_t eclqr_launch_count(const eclqr_handle *h) { return h ? h->launches : 0; }
+
+void eclqr_destroy(eclqr_handle *h) {
+  if (!h) return;
+  for (auto &gh : h->groups) cudaFree(gh.dmem);
+  delete h;
+}
+
+const char *eclqr_strerror(int code) {
+  switch (code) {
+    case ECLQR_OK: return "ok";
+    case ECLQR_EINVAL: return "invalid argument";
+    case ECLQR_ENOMEM: return "device allocation failed";
+    case ECLQR_ECUDA: return "CUDA error";
+    case ECLQR_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

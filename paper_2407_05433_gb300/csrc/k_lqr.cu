@@ -1,0 +1,778 @@
+// k_lqr.cu -- the reduced unconstrained LQR (Sec. 6) and the recovery maps
+// (eq. recovery-maps) on sm_103a.
+//
+// Riccati factors.  The paper obtains log depth from an associative LQR scan
+// [ref-AS-LQR].  Here the scan elements are conditional costs V(z_a | z_b) of
+// a chunk kept in square-root form, as "cost relations": constraint rows that
+// hold exactly (states z_b reachable from z_a) and least-squares cost rows on
+// (z_a, z_b).  Composition eliminates the shared state by equality-constrained
+// least squares (wlse_elim: orthogonal and pivoted), so value functions whose
+// Hessians grow without bound through stretches without control authority
+// turn into constraints instead of cancelling.  Chunks compose their own
+// stages, a log-depth scan over chunks gives V at every chunk boundary, and
+// each chunk then runs the square-root Riccati recursion inward, storing P_i,
+// K_i, the Cholesky factor of Rbar + Bbar'P Bbar and Phi_i = Abar + Bbar K_i.
+//
+// Linear passes.  With those factors the remaining recursions are affine
+// chains: p_i = Phi_i' (P_{i+1} c_i + p_{i+1}) + q_i + K_i' r_i backwards and
+// z_{i+1} = Phi_i z_i + Bbar k_i + c_i forwards.  They run as chunked affine
+// scans (k_aff_*), also used for the refinement passes on the reduced KKT
+// residual and for the forward costate expansion of Sec. 7.
+#include "kernels.cuh"
+
+namespace eclqr {
+
+__host__ int smem_lqr_up(int n, int m) {
+  const int ldr = 2 * n + 1, rows = 5 * n + m, ldm = m + 2 * n + 1;
+  return 2 * (2 * n) * ldr + rows * ldm + 2 * rows + 2 * (ldm + rows) + m + 16;
+}
+__host__ int smem_lqr_level(int n) {
+  const int rows = 8 * n, ldm = 3 * n + 1;
+  return rows * ldm + 2 * rows + 2 * (ldm + rows) + n + 16;
+}
+__host__ int smem_riccati(int n, int m) {
+  const int rows = 2 * n + m, ld = n + m + 1;
+  return n * (n + 1) + rows * ld + rows + ld + 4 * n * n + 2 * m * n + 8;
+}
+__host__ int smem_aff(int n) { return 2 * (n * n + n) + n * n + 2 * n + 8; }
+
+// Cost-relation slot layout (ld 2n + 1): constraint rows at 0 (CI_ROWS of them),
+// cost rows at offset 2n (2n + 1) (CI_ROWS2 of them); CI_NA / CI_NB are the
+// endpoint dimensions, CI_NB = 0 marks a value function (unary, cost only).
+__device__ __forceinline__ double *crel_cost(double *slot, int n) { return slot + 2 * n * (2 * n + 1); }
+
+// ----------------------------------------------------------- chunk conditional costs
+// Up-sweep over stages b-1 .. a of the conditional cost V(z_i | z_b): a cost
+// relation on (z_i, z_b).  Stage i substitutes the reduced dynamics
+// z_{i+1} = Abar z_i + Bbar v + cbar into the rows on (z_{i+1}, z_b), stacks the
+// stage cost rows L'[z; v] + l and eliminates v (wlse_elim).
+__global__ void k_lqr_up(Group g, int per_warp) {
+  const int t = warp_task();
+  if (t >= g.nslot) return;
+  const ChunkInfo ci = g.chunk[t];
+  const ProbInfo &P = g.prob[ci.prob];
+  const int n = g.n, m = g.m, lane = lane_id();
+  const int ldr = 2 * n + 1;
+  double *slot = g.CS[0] + (size_t)t * g.cs_stride;
+  int *cm = g.CI[0] + (size_t)t * CI_STRIDE;
+  double *sm = warp_smem(per_warp);
+  if (ci.c == P.nch) {
+    // terminal value: rows [L' | L^{-1} qbar_N], L L' = Qbar_N (eq. terminal-cost-data)
+    const int sN = P.st0 + P.N;
+    const double *ws = stage_ws(g, sN);
+    const int nN = stage_wi(g, sN)[SI_NBAR];
+    double *Hh = sm, *l = sm + n * n;
+    for (int idx = lane; idx < nN * nN; idx += 32) {
+      int a = idx / nN, j = idx - a * nN;
+      Hh[idx] = ws[g.ws.Qb + a * n + j];
+    }
+    __syncwarp();
+    const int fail = wcholesky(Hh, nN, nN);
+    if (lane == 0) {
+      for (int a = 0; a < nN; a++) {
+        double s0 = ws[g.ws.qb + a];
+        for (int k = 0; k < a; k++) s0 = fma(-Hh[a * nN + k], l[k], s0);
+        l[a] = s0 / Hh[a * nN + a];
+      }
+    }
+    __syncwarp();
+    double *cost = crel_cost(slot, n);
+    for (int idx = lane; idx < nN * (nN + 1); idx += 32) {
+      int a = idx / (nN + 1), j = idx - a * (nN + 1);
+      cost[a * ldr + j] = (j < nN) ? Hh[j * nN + a] : l[a];
+    }
+    if (lane == 0) {
+      cm[CI_ROWS] = 0; cm[CI_NA] = nN; cm[CI_NB] = 0; cm[CI_ROWS2] = nN;
+      if (fail) set_status(g, ci.prob, ST_NONCONVEX);
+    }
+    return;
+  }
+  const int a = ci.c * P.L, b = min(a + P.L, P.N);
+  const int nbz = stage_wi(g, P.st0 + b)[SI_NBAR];
+  const int rows_max = 5 * n + m, ldm_max = m + 2 * n + 1;
+  double *Cons = sm, *Cost = Cons + 2 * n * ldr, *M = Cost + 2 * n * ldr, *scr = M + rows_max * ldm_max;
+  // z_b' = z_b on (z_b', z_b)
+  for (int idx = lane; idx < nbz * ldr; idx += 32) {
+    int i = idx / ldr, j = idx - i * ldr;
+    Cons[idx] = (j == i) ? 1.0 : ((j == nbz + i) ? -1.0 : 0.0);
+  }
+  __syncwarp();
+  int rc = nbz, rq = 0;
+  int fail = 0;
+  for (int i = b - 1; i >= a; --i) {
+    const int s = P.st0 + i;
+    const double *ws = stage_ws(g, s);
+    const int *wi = stage_wi(g, s);
+    const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
+    const int ldm = mu + nx + nbz + 1, kh = nx + mu;
+    const double *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb, *cb = ws + g.ws.cb, *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
+    // columns v (mu) | z_i (nx) | z_b (nbz) | 1
+    // rows: constraints (rc) then stage cost (kh) then old cost (rq)
+    const int rtot = rc + kh + rq;
+    for (int idx = lane; idx < rtot * ldm; idx += 32) {
+      int r = idx / ldm, j = idx - r * ldm;
+      double val = 0.0;
+      if (r < rc || r >= rc + kh) {
+        const double *row = (r < rc) ? Cons + r * ldr : Cost + (r - rc - kh) * ldr;  // [K1 (n1) | Kb (nbz) | k]
+        if (j < mu) {
+          for (int l = 0; l < n1; l++) val = fma(row[l], Bb[l * m + j], val);
+        } else if (j < mu + nx) {
+          for (int l = 0; l < n1; l++) val = fma(row[l], Ab[l * n + (j - mu)], val);
+        } else if (j < mu + nx + nbz) {
+          val = row[n1 + (j - mu - nx)];
+        } else {
+          val = row[n1 + nbz];
+          for (int l = 0; l < n1; l++) val = fma(row[l], cb[l], val);
+        }
+      } else {
+        const int q = r - rc;  // stage cost row q of L' (columns z then v)
+        if (j < mu) val = LT[q * (n + m) + nx + j];
+        else if (j < mu + nx) val = LT[q * (n + m) + (j - mu)];
+        else if (j == ldm - 1) val = lt[q];
+      }
+      M[idx] = val;
+    }
+    __syncwarp();
+    LseResult lr = wlse_elim(M, ldm, rc, kh + rq, mu, nx + nbz, g.tau_rank, g.tau_inc, Cons, Cost, ldr, scr);
+    rc = lr.kc;
+    rq = lr.kq;
+    fail |= lr.inconsistent;
+  }
+  for (int idx = lane; idx < rc * ldr; idx += 32) slot[idx] = Cons[idx];
+  double *cost = crel_cost(slot, n);
+  for (int idx = lane; idx < rq * ldr; idx += 32) cost[idx] = Cost[idx];
+  if (lane == 0) {
+    cm[CI_ROWS] = rc; cm[CI_NA] = stage_wi(g, P.st0 + a)[SI_NBAR]; cm[CI_NB] = nbz; cm[CI_ROWS2] = rq;
+    if (fail) set_status(g, ci.prob, ST_NONCONVEX);
+  }
+}
+
+// One level of the chunk suffix scan on cost relations: slot t <- slot t o slot t + d,
+// eliminating the shared state (wlse_elim); a value on the right gives a value.
+__global__ void k_lqr_level(Group g, int src, int d, int per_warp) {
+  const int t = warp_task();
+  if (t >= g.nslot) return;
+  const ChunkInfo ci = g.chunk[t];
+  const ProbInfo &P = g.prob[ci.prob];
+  const int n = g.n, lane = lane_id(), ldr = 2 * n + 1;
+  double *S1 = g.CS[src] + (size_t)t * g.cs_stride;
+  const int *I1 = g.CI[src] + (size_t)t * CI_STRIDE;
+  double *Dst = g.CS[src ^ 1] + (size_t)t * g.cs_stride;
+  int *J = g.CI[src ^ 1] + (size_t)t * CI_STRIDE;
+  const int rc1 = I1[CI_ROWS], na = I1[CI_NA], nm = I1[CI_NB], rq1 = I1[CI_ROWS2];
+  if (ci.c + d > P.nch || nm == 0) {
+    for (int idx = lane; idx < rc1 * ldr; idx += 32) Dst[idx] = S1[idx];
+    for (int idx = lane; idx < rq1 * ldr; idx += 32) crel_cost(Dst, n)[idx] = crel_cost(S1, n)[idx];
+    if (lane == 0) { J[CI_ROWS] = rc1; J[CI_NA] = na; J[CI_NB] = nm; J[CI_ROWS2] = rq1; }
+    return;
+  }
+  double *S2 = g.CS[src] + (size_t)(t + d) * g.cs_stride;
+  const int *I2 = g.CI[src] + (size_t)(t + d) * CI_STRIDE;
+  const int rc2 = I2[CI_ROWS], nb = I2[CI_NB], rq2 = I2[CI_ROWS2];
+  double *sm = warp_smem(per_warp);
+  const int ldm = nm + na + nb + 1;
+  const int rc = rc1 + rc2, rq = rq1 + rq2;
+  double *M = sm, *scr = sm + (rc + rq) * ldm;
+  // columns z_m | z_a | z_b | 1 ; rows: constraints of e1, e2, then costs of e1, e2
+  for (int idx = lane; idx < (rc + rq) * ldm; idx += 32) {
+    int r = idx / ldm, j = idx - r * ldm;
+    bool left;
+    const double *row;
+    if (r < rc1) { left = true; row = S1 + r * ldr; }
+    else if (r < rc) { left = false; row = S2 + (r - rc1) * ldr; }
+    else if (r < rc + rq1) { left = true; row = crel_cost(S1, n) + (r - rc) * ldr; }
+    else { left = false; row = crel_cost(S2, n) + (r - rc - rq1) * ldr; }
+    double val = 0.0;
+    if (left) {          // [z_a (na) | z_m (nm) | 1]
+      if (j < nm) val = row[na + j];
+      else if (j < nm + na) val = row[j - nm];
+      else if (j == ldm - 1) val = row[na + nm];
+    } else {             // [z_m (nm) | z_b (nb) | 1]
+      if (j < nm) val = row[j];
+      else if (j >= nm + na && j < nm + na + nb) val = row[nm + (j - nm - na)];
+      else if (j == ldm - 1) val = row[nm + nb];
+    }
+    M[idx] = val;
+  }
+  __syncwarp();
+  LseResult lr = wlse_elim(M, ldm, rc, rq, nm, na + nb, g.tau_rank, g.tau_inc, Dst, crel_cost(Dst, n), ldr, scr);
+  if (lane == 0) {
+    J[CI_ROWS] = lr.kc; J[CI_NA] = na; J[CI_NB] = nb; J[CI_ROWS2] = lr.kq;
+    if (lr.inconsistent) set_status(g, ci.prob, ST_NONCONVEX);
+  }
+}
+
+// ----------------------------------------------------------- chunk down-sweep: square-root Riccati
+// From V_b = 1/2 ||C z_b + c||^2 (the scan's value at the chunk end), each stage
+// stacks [L'_v | L'_z | l] and [C Bbar | C Abar | C cbar + c] over (v | z | 1) and
+// triangularises them by Householder QR: R_vv v + R_vz z + o_v = 0 at the
+// minimiser (K, k) and V_i = 1/2 ||R_zz z + o_z||^2.  P_i = R_zz'R_zz, p_i = R_zz'o_z,
+// H_uu = R_vv'R_vv, H_ux = R_vv'R_vz and Phi_i = Abar + Bbar K are stored for the
+// linear passes.
+__global__ void k_riccati_down(Group g, int fin, int per_warp) {
+  const int t = warp_task();
+  if (t >= g.nslot) return;
+  const ChunkInfo ci = g.chunk[t];
+  const ProbInfo &P = g.prob[ci.prob];
+  if (ci.c >= P.nch) return;
+  const int n = g.n, m = g.m, lane = lane_id();
+  const int a = ci.c * P.L, b = min(a + P.L, P.N);
+  const int ldr = 2 * n + 1;
+  double *sm = warp_smem(per_warp);
+  const int rows_max = 2 * n + m, ldst = n + m + 1;
+  double *V = sm, *St = V + n * (n + 1), *v = St + rows_max * ldst, *w = v + rows_max;
+  double *Kt = w + ldst;  // m x (n + 1)
+  // V_b
+  int rv;
+  {
+    const double *src = crel_cost(g.CS[fin] + (size_t)(t + 1) * g.cs_stride, n);
+    const int *I = g.CI[fin] + (size_t)(t + 1) * CI_STRIDE;
+    const int nbz = I[CI_NA];
+    rv = I[CI_ROWS2];
+    for (int idx = lane; idx < rv * (nbz + 1); idx += 32) {
+      int r = idx / (nbz + 1), j = idx - r * (nbz + 1);
+      V[r * (n + 1) + j] = src[r * ldr + j];
+    }
+    __syncwarp();
+    if (b == P.N) {  // P_N = C'C, p_N = C'c
+      double *wsN = stage_ws(g, P.st0 + b);
+      for (int idx = lane; idx < nbz * (nbz + 1); idx += 32) {
+        int r = idx / (nbz + 1), j = idx - r * (nbz + 1);
+        double s0 = 0.0;
+        for (int l = 0; l < rv; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + j], s0);
+        if (j < nbz) wsN[g.ws.P + r * n + j] = s0; else wsN[g.ws.p + r] = s0;
+      }
+    }
+  }
+  for (int i = b - 1; i >= a; --i) {
+    const int s = P.st0 + i;
+    double *ws = stage_ws(g, s);
+    const int *wi = stage_wi(g, s);
+    const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
+    const int kh = nx + mu, rows = kh + rv, ld = kh + 1;
+    const double *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb, *cb = ws + g.ws.cb, *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
+    for (int idx = lane; idx < rows * ld; idx += 32) {
+      int r = idx / ld, j = idx - r * ld;
+      double val = 0.0;
+      if (r < kh) {
+        if (j < mu) val = LT[r * (n + m) + nx + j];
+        else if (j < kh) val = LT[r * (n + m) + (j - mu)];
+        else val = lt[r];
+      } else {
+        const double *row = V + (r - kh) * (n + 1);
+        if (j < mu) {
+          for (int l = 0; l < n1; l++) val = fma(row[l], Bb[l * m + j], val);
+        } else if (j < kh) {
+          for (int l = 0; l < n1; l++) val = fma(row[l], Ab[l * n + (j - mu)], val);
+        } else {
+          val = row[n1];
+          for (int l = 0; l < n1; l++) val = fma(row[l], cb[l], val);
+        }
+      }
+      St[idx] = val;
+    }
+    __syncwarp();
+    // Householder QR over the first kh columns, in order
+    for (int col = 0; col < kh && col < rows; col++) {
+      double s0 = 0.0;
+      for (int r = col + lane; r < rows; r += 32) s0 = fma(St[r * ld + col], St[r * ld + col], s0);
+      s0 = sqrt(warp_sum(s0));
+      if (s0 == 0.0) continue;
+      whouse_apply(St, ld, col, rows, col, col + 1, ld, nullptr, v, w, s0);
+    }
+    // K, k:  R_vv [K | k] = -[R_vz | o_v]  (lanes over the nx + 1 columns)
+    for (int c = lane; c <= nx; c += 32) {
+      for (int r = mu - 1; r >= 0; r--) {
+        double s0 = -St[r * ld + mu + c];
+        for (int l = r + 1; l < mu; l++) s0 = fma(-St[r * ld + l], Kt[l * (n + 1) + c], s0);
+        Kt[r * (n + 1) + c] = s0 / St[r * ld + r];
+      }
+    }
+    __syncwarp();
+    // stores: K, k, Lh (lower Cholesky factor of H_uu with positive diagonal), Hx, P, p, Phi
+    for (int idx = lane; idx < mu * (nx + 1); idx += 32) {
+      int r = idx / (nx + 1), c = idx - r * (nx + 1);
+      if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
+    }
+    for (int idx = lane; idx < mu * mu; idx += 32) {
+      int r = idx / mu, j = idx - r * mu;  // Lh[r][j] = sign_j * R_vv[j][r] for j <= r
+      double sg = St[j * ld + j] >= 0.0 ? 1.0 : -1.0;
+      ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * St[j * ld + r] : 0.0;
+    }
+    for (int idx = lane; idx < mu * nx; idx += 32) {
+      int r = idx / nx, c = idx - r * nx;
+      double s0 = 0.0;
+      for (int l = 0; l <= r; l++) s0 = fma(St[l * ld + r], St[l * ld + mu + c], s0);
+      ws[g.ws.Hx + r * n + c] = s0;
+    }
+    for (int idx = lane; idx < n1 * nx; idx += 32) {
+      int r = idx / nx, c = idx - r * nx;
+      double s0 = Ab[r * n + c];
+      for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
+      ws[g.ws.Phi + r * n + c] = s0;
+    }
+    // new value rows [R_zz | o_z]
+    __syncwarp();
+    for (int idx = lane; idx < nx * (nx + 1); idx += 32) {
+      int r = idx / (nx + 1), c = idx - r * (nx + 1);
+      V[r * (n + 1) + c] = (c < nx) ? ((c >= r) ? St[(mu + r) * ld + mu + c] : 0.0) : St[(mu + r) * ld + kh];
+    }
+    __syncwarp();
+    rv = nx;
+    for (int idx = lane; idx < nx * (nx + 1); idx += 32) {
+      int r = idx / (nx + 1), c = idx - r * (nx + 1);
+      double s0 = 0.0;
+      for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
+      if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
+    }
+    __syncwarp();
+  }
+}
+
+// ----------------------------------------------------------- affine chain scans
+// Per-stage maps by mode (d_i = dimension of the chained vector at stage i):
+//   AFF_ROLL  forward  z_{i+1} = Phi_i z_i + Bbar k_i + cbar_i        -> z
+//   AFF_CROLL forward  dz_{i+1} = Phi_i dz_i + Bbar k'_i + rc_i       -> dz (k' held in dv)
+//   AFF_CLIN  backward p'_i = Phi_i'(P_{i+1} rc_i + p'_{i+1}) + rq_i + K_i' rr_i -> pp
+//   AFF_NU    forward  nu_{i+1} = Pnu_i nu_i + pnu_i                  -> nu
+enum { AFF_ROLL = 0, AFF_CROLL = 1, AFF_CLIN = 2, AFF_NU = 3 };
+
+__device__ __forceinline__ int aff_dim(const Group &g, int s, int mode) {
+  return (mode == AFF_NU) ? stage_wi(g, s)[SI_UR] : stage_wi(g, s)[SI_NBAR];
+}
+__device__ __forceinline__ bool aff_forward(int mode) { return mode != AFF_CLIN; }
+__device__ __forceinline__ int aff_out(const Group &g, int mode) {
+  return mode == AFF_ROLL ? g.ws.z : mode == AFF_CROLL ? g.ws.dz : mode == AFF_CLIN ? g.ws.pp : g.ws.nu;
+}
+
+// map of stage i: y_out = G y_in + gv.  Forward: in = stage i, out = stage i+1;
+// backward: in = stage i+1, out = stage i.  G (dout x din, ld n) and gv into smem.
+__device__ void aff_stage_map(const Group &g, int s, int mode, double *G, double *gv, double *tmp) {
+  const int n = g.n, m = g.m, lane = lane_id();
+  const double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);
+  const int *wi = stage_wi(g, s);
+  if (mode == AFF_NU) {
+    const int din = wi[SI_UR], dout = stage_wi(g, s + 1)[SI_UR];
+    for (int idx = lane; idx < dout * din; idx += 32) {
+      int i = idx / din, j = idx - i * din;
+      G[i * n + j] = ws[g.ws.Pnu + i * n + j];
+    }
+    for (int i = lane; i < dout; i += 32) gv[i] = ws[g.ws.pnu + i];
+    __syncwarp();
+    return;
+  }
+  const int nx = wi[SI_NBAR], ny = stage_wi(g, s + 1)[SI_NBAR], mu = wi[SI_MBAR];
+  const double *Phi = ws + g.ws.Phi, *Bb = ws + g.ws.Bb;
+  if (mode == AFF_ROLL || mode == AFF_CROLL) {
+    const double *kk = ws + (mode == AFF_ROLL ? g.ws.k : g.ws.dv);
+    const double *cc = ws + (mode == AFF_ROLL ? g.ws.cb : g.ws.rc);
+    for (int idx = lane; idx < ny * nx; idx += 32) {
+      int i = idx / nx, j = idx - i * nx;
+      G[i * n + j] = Phi[i * n + j];
+    }
+    for (int i = lane; i < ny; i += 32) {
+      double s0 = cc[i];
+      for (int l = 0; l < mu; l++) s0 = fma(Bb[i * m + l], kk[l], s0);
+      gv[i] = s0;
+    }
+    __syncwarp();
+    return;
+  }
+  // AFF_CLIN: G = Phi' (nx x ny), gv = Phi' P_{i+1} rc + rq + K' rr
+  const double *Pn = wn + g.ws.P, *rc = ws + g.ws.rc, *rq = ws + g.ws.rq, *rr = ws + g.ws.rr, *K = ws + g.ws.K;
+  for (int idx = lane; idx < nx * ny; idx += 32) {
+    int i = idx / ny, j = idx - i * ny;
+    G[i * n + j] = Phi[j * n + i];
+  }
+  for (int i = lane; i < ny; i += 32) {
+    double s0 = 0.0;
+    for (int l = 0; l < ny; l++) s0 = fma(Pn[i * n + l], rc[l], s0);
+    tmp[i] = s0;
+  }
+  __syncwarp();
+  for (int i = lane; i < nx; i += 32) {
+    double s0 = rq[i];
+    for (int l = 0; l < ny; l++) s0 = fma(Phi[l * n + i], tmp[l], s0);
+    for (int l = 0; l < mu; l++) s0 = fma(K[l * n + i], rr[l], s0);
+    gv[i] = s0;
+  }
+  __syncwarp();
+}
+
+// chunk aggregates; also the boundary value slot (forward: slot 0 of the
+// problem holds y_0, backward: slot nch holds y_N).
+__global__ void k_aff_up(Group g, int mode, int per_warp) {
+  const int t = warp_task();
+  if (t >= g.nslot) return;
+  const ChunkInfo ci = g.chunk[t];
+  const ProbInfo &P = g.prob[ci.prob];
+  const int n = g.n, lane = lane_id();
+  const bool fwd = aff_forward(mode);
+  double *cs0 = g.CS[0];
+  if (ci.c == P.nch) {
+    // boundary value
+    const int s = fwd ? P.st0 : P.st0 + P.N;
+    const int slot = fwd ? P.ch0 : P.ch0 + P.nch;
+    const int dim = aff_dim(g, s, mode);
+    double *gv = cs0 + (size_t)slot * g.cs_stride + n * n;
+    const double *src = stage_ws(g, s);
+    for (int i = lane; i < dim; i += 32) {
+      double v;
+      if (mode == AFF_ROLL) v = src[g.ws.z + i];
+      else if (mode == AFF_CROLL) v = 0.0;
+      else if (mode == AFF_CLIN) v = src[g.ws.rq + i];
+      else v = src[g.ws.nu + i];
+      gv[i] = v;
+    }
+    if (lane == 0) {
+      int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
+      cm[CI_ROWS] = 1; cm[CI_NA] = dim; cm[CI_NB] = 0;
+    }
+    return;
+  }
+  const int a = ci.c * P.L, b = min(a + P.L, P.N);
+  const int slot = fwd ? P.ch0 + ci.c + 1 : P.ch0 + ci.c;
+  double *sm = warp_smem(per_warp);
+  double *Gm = sm, *gm = Gm + n * n, *Gs = gm + n, *gs = Gs + n * n, *Tm = gs + n, *tmp = Tm + n * n;
+  const int d0 = fwd ? aff_dim(g, P.st0 + a, mode) : aff_dim(g, P.st0 + b, mode);
+  for (int idx = lane; idx < n * n; idx += 32) {
+    int i = idx / n, j = idx - i * n;
+    Gm[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int i = lane; i < n; i += 32) gm[i] = 0.0;
+  __syncwarp();
+  int dcur = d0;  // rows of the aggregate (current output dimension)
+  for (int k = 0; k < b - a; k++) {
+    const int i = fwd ? a + k : b - 1 - k;
+    const int s = P.st0 + i;
+    aff_stage_map(g, s, mode, Gs, gs, tmp);
+    const int dout = fwd ? aff_dim(g, s + 1, mode) : aff_dim(g, s, mode);
+    // Tm = Gs Gm (dout x d0), tmp = Gs gm + gs
+    wgemm<false, false>(dout, d0, dcur, 1.0, Gs, n, Gm, n, 0.0, Tm, n);
+    for (int r = lane; r < dout; r += 32) {
+      double s0 = gs[r];
+      for (int l = 0; l < dcur; l++) s0 = fma(Gs[r * n + l], gm[l], s0);
+      tmp[r] = s0;
+    }
+    __syncwarp();
+    for (int idx = lane; idx < dout * d0; idx += 32) {
+      int r = idx / d0, j = idx - r * d0;
+      Gm[r * n + j] = Tm[r * n + j];
+    }
+    for (int r = lane; r < dout; r += 32) gm[r] = tmp[r];
+    __syncwarp();
+    dcur = dout;
+  }
+  double *cs = cs0 + (size_t)slot * g.cs_stride;
+  for (int idx = lane; idx < n * n; idx += 32) cs[idx] = Gm[idx];
+  for (int i = lane; i < n; i += 32) cs[n * n + i] = gm[i];
+  if (lane == 0) {
+    int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
+    cm[CI_ROWS] = 0; cm[CI_NA] = d0; cm[CI_NB] = dcur;
+  }
+}
+
+// slot t <- slot t o slot t' (t' = t - d forward, t + d backward) inside one problem.
+__global__ void k_aff_level(Group g, int src, int d, int fwd, int per_warp) {
+  const int t = warp_task();
+  if (t >= g.nslot) return;
+  const ChunkInfo ci = g.chunk[t];
+  const ProbInfo &P = g.prob[ci.prob];
+  const int n = g.n, lane = lane_id();
+  const int j = t - P.ch0;  // slot index 0..nch
+  const double *S1 = g.CS[src] + (size_t)t * g.cs_stride;
+  const int *I1 = g.CI[src] + (size_t)t * CI_STRIDE;
+  double *Dst = g.CS[src ^ 1] + (size_t)t * g.cs_stride;
+  int *J = g.CI[src ^ 1] + (size_t)t * CI_STRIDE;
+  const int na = I1[CI_NA], nb = I1[CI_NB];
+  const bool value1 = I1[CI_ROWS] == 1;
+  const int j2 = fwd ? j - d : j + d;
+  if (value1 || j2 < 0 || j2 > P.nch) {
+    for (int idx = lane; idx < n * n + n; idx += 32) Dst[idx] = S1[idx];
+    if (lane == 0) { J[CI_ROWS] = I1[CI_ROWS]; J[CI_NA] = na; J[CI_NB] = nb; }
+    return;
+  }
+  const int t2 = P.ch0 + j2;
+  const double *S2 = g.CS[src] + (size_t)t2 * g.cs_stride;
+  const int *I2 = g.CI[src] + (size_t)t2 * CI_STRIDE;
+  double *sm = warp_smem(per_warp);
+  double *Tm = sm, *tv = Tm + n * n;
+  if (I2[CI_ROWS] == 1) {
+    // value: y = G1 v + g1
+    const int dv = I2[CI_NA];
+    for (int r = lane; r < nb; r += 32) {
+      double s0 = S1[n * n + r];
+      for (int l = 0; l < dv; l++) s0 = fma(S1[r * n + l], S2[n * n + l], s0);
+      Dst[n * n + r] = s0;
+    }
+    if (lane == 0) { J[CI_ROWS] = 1; J[CI_NA] = nb; J[CI_NB] = 0; }
+    return;
+  }
+  const int na2 = I2[CI_NA];
+  // (G1 G2, G1 g2 + g1): input dim na2, output nb
+  wgemm<false, false>(nb, na2, na, 1.0, S1, n, S2, n, 0.0, Tm, n);
+  for (int r = lane; r < nb; r += 32) {
+    double s0 = S1[n * n + r];
+    for (int l = 0; l < na; l++) s0 = fma(S1[r * n + l], S2[n * n + l], s0);
+    tv[r] = s0;
+  }
+  __syncwarp();
+  for (int idx = lane; idx < n * n; idx += 32) Dst[idx] = Tm[idx];
+  for (int r = lane; r < n; r += 32) Dst[n * n + r] = tv[r];
+  if (lane == 0) { J[CI_ROWS] = 0; J[CI_NA] = na2; J[CI_NB] = nb; }
+}
+
+__global__ void k_aff_down(Group g, int mode, int fin, int per_warp) {
+  const int t = warp_task();
+  if (t >= g.nslot) return;
+  const ChunkInfo ci = g.chunk[t];
+  const ProbInfo &P = g.prob[ci.prob];
+  if (ci.c >= P.nch) return;
+  const int n = g.n, lane = lane_id();
+  const bool fwd = aff_forward(mode);
+  const int a = ci.c * P.L, b = min(a + P.L, P.N);
+  const int off = aff_out(g, mode);
+  double *sm = warp_smem(per_warp);
+  double *Gs = sm, *gs = Gs + n * n, *y = gs + n, *y2 = y + n, *tmp = y2 + n;
+  // boundary value after the scan: forward slot (ch0 + c) = y_a; backward slot (ch0 + c + 1) = y_b
+  const int slot = fwd ? P.ch0 + ci.c : P.ch0 + ci.c + 1;
+  const double *sv = g.CS[fin] + (size_t)slot * g.cs_stride + n * n;
+  int dcur = fwd ? aff_dim(g, P.st0 + a, mode) : aff_dim(g, P.st0 + b, mode);
+  for (int i = lane; i < n; i += 32) y[i] = (i < dcur) ? sv[i] : 0.0;
+  __syncwarp();
+  if (fwd) {
+    for (int i = a; i < b; i++) {
+      const int s = P.st0 + i;
+      double *o = stage_ws(g, s) + off;
+      for (int r = lane; r < n; r += 32) o[r] = (r < dcur) ? y[r] : 0.0;
+      aff_stage_map(g, s, mode, Gs, gs, tmp);
+      const int dout = aff_dim(g, s + 1, mode);
+      for (int r = lane; r < dout; r += 32) {
+        double s0 = gs[r];
+        for (int l = 0; l < dcur; l++) s0 = fma(Gs[r * n + l], y[l], s0);
+        y2[r] = s0;
+      }
+      __syncwarp();
+      for (int r = lane; r < n; r += 32) y[r] = (r < dout) ? y2[r] : 0.0;
+      __syncwarp();
+      dcur = dout;
+    }
+    if (b == P.N) {
+      double *o = stage_ws(g, P.st0 + b) + off;
+      for (int r = lane; r < n; r += 32) o[r] = (r < dcur) ? y[r] : 0.0;
+    }
+  } else {
+    if (b == P.N) {
+      double *o = stage_ws(g, P.st0 + b) + off;
+      for (int r = lane; r < n; r += 32) o[r] = (r < dcur) ? y[r] : 0.0;
+    }
+    for (int i = b - 1; i >= a; i--) {
+      const int s = P.st0 + i;
+      aff_stage_map(g, s, mode, Gs, gs, tmp);
+      const int dout = aff_dim(g, s, mode);
+      for (int r = lane; r < dout; r += 32) {
+        double s0 = gs[r];
+        for (int l = 0; l < dcur; l++) s0 = fma(Gs[r * n + l], y[l], s0);
+        y2[r] = s0;
+      }
+      __syncwarp();
+      for (int r = lane; r < n; r += 32) y[r] = (r < dout) ? y2[r] : 0.0;
+      __syncwarp();
+      dcur = dout;
+      double *o = stage_ws(g, s) + off;
+      for (int r = lane; r < n; r += 32) o[r] = y[r];
+    }
+  }
+}
+
+// ----------------------------------------------------------- stage-parallel helpers of the solve
+// z_0 = T_0'(s_0 - t_0) and the check H_0 s_0 + h_0 = 0 (eqs. initial-feasibility, reduced-initial)
+__global__ void k_solve_init(Group g, const double *s0) {
+  const int t = warp_task();
+  if (t >= g.nprob) return;
+  const ProbInfo &P = g.prob[t];
+  const int n = g.n, lane = lane_id();
+  const int s = P.st0;
+  double *ws = stage_ws(g, s);
+  const int *wi = stage_wi(g, s);
+  const int r = wi[SI_HROWS], ur = wi[SI_UR], nb = n - ur;
+  const double *x0 = s0 + P.os0;
+  const double *H = ws + g.ws.H, *T = ws + g.ws.UT + ur, *tt = ws + g.ws.t;
+  double worst = 0.0, om = 0.0;
+  for (int a = lane; a < r; a += 32) {
+    double v = H[a * (n + 1) + n];
+    om = fmax(om, fabs(v));
+    for (int l = 0; l < n; l++) v = fma(H[a * (n + 1) + l], x0[l], v);
+    worst = fmax(worst, fabs(v));
+  }
+  for (int l = lane; l < n; l += 32) om = fmax(om, fabs(x0[l]));
+  worst = warp_max(worst);
+  om = fmax(1.0, warp_max(om));
+  if (lane == 0 && worst > g.tau_inc * om) set_status(g, t, ST_INFEASIBLE_X0);
+  for (int a = lane; a < n; a += 32) {
+    double v = 0.0;
+    if (a < nb)
+      for (int l = 0; l < n; l++) v = fma(T[l * n + a], x0[l] - tt[l], v);
+    ws[g.ws.z + a] = v;
+  }
+}
+
+// pass 0: v_i = K z + k, pi_i = P z + p.  correction passes: dv = K dz + k', dpi = P dz + p',
+// then z += dz, v += dv, pi += dpi.
+__global__ void k_post_roll(Group g, int corr) {
+  const int s = warp_task();
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  const int n = g.n, m = g.m, lane = lane_id();
+  double *ws = stage_ws(g, s);
+  const int *wi = stage_wi(g, s);
+  const int nx = wi[SI_NBAR], mu = (S.i < P.N) ? wi[SI_MBAR] : 0;
+  const double *zz = ws + (corr ? g.ws.dz : g.ws.z);
+  const double *kk = ws + (corr ? g.ws.dv : g.ws.k);
+  const double *pp = ws + (corr ? g.ws.pp : g.ws.p);
+  // v (or dv) -- computed into registers of the lanes then written
+  double myv = 0.0, mypi = 0.0;
+  const int r = lane;
+  if (r < mu) {
+    myv = kk[r];
+    for (int l = 0; l < nx; l++) myv = fma(ws[g.ws.K + r * n + l], zz[l], myv);
+  }
+  if (r < nx) {
+    mypi = pp[r];
+    for (int l = 0; l < nx; l++) mypi = fma(ws[g.ws.P + r * n + l], zz[l], mypi);
+  }
+  __syncwarp();
+  if (!corr) {
+    if (r < m) ws[g.ws.v + r] = (r < mu) ? myv : 0.0;
+    if (r < n) ws[g.ws.pi + r] = (r < nx) ? mypi : 0.0;
+  } else {
+    if (r < mu) ws[g.ws.v + r] += myv;
+    if (r < nx) { ws[g.ws.pi + r] += mypi; ws[g.ws.z + r] += zz[r]; }
+  }
+}
+
+// residual of the reduced KKT system at (z, v, pi):
+//   rq_i = Qbar z + Mbar v + qbar - pi_i + Abar' pi_{i+1}   (i < N),  rq_N = Qbar_N z + qbar_N - pi_N
+//   rr_i = Mbar' z + Rbar v + rbar + Bbar' pi_{i+1}
+//   rc_i = Abar z + Bbar v + cbar - z_{i+1}
+__global__ void k_resid(Group g) {
+  const int s = warp_task();
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  const int n = g.n, m = g.m, lane = lane_id();
+  double *ws = stage_ws(g, s);
+  const int *wi = stage_wi(g, s);
+  const bool last = S.i == P.N;
+  const double *wn = last ? ws : stage_ws(g, s + 1);
+  const int nx = wi[SI_NBAR], mu = last ? 0 : wi[SI_MBAR], ny = last ? 0 : stage_wi(g, s + 1)[SI_NBAR];
+  const double *z = ws + g.ws.z, *v = ws + g.ws.v, *pi = ws + g.ws.pi, *pin = wn + g.ws.pi, *zn = wn + g.ws.z;
+  const double *Qb = ws + g.ws.Qb, *Mb = ws + g.ws.Mb, *Rb = ws + g.ws.Rb, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
+  for (int r = lane; r < nx; r += 32) {
+    double s0 = ws[g.ws.qb + r] - pi[r];
+    for (int l = 0; l < nx; l++) s0 = fma(Qb[r * n + l], z[l], s0);
+    for (int l = 0; l < mu; l++) s0 = fma(Mb[r * m + l], v[l], s0);
+    for (int l = 0; l < ny; l++) s0 = fma(Ab[l * n + r], pin[l], s0);
+    ws[g.ws.rq + r] = s0;
+  }
+  for (int r = lane; r < mu; r += 32) {
+    double s0 = ws[g.ws.rb + r];
+    for (int l = 0; l < nx; l++) s0 = fma(Mb[l * m + r], z[l], s0);
+    for (int l = 0; l < mu; l++) s0 = fma(Rb[r * m + l], v[l], s0);
+    for (int l = 0; l < ny; l++) s0 = fma(Bb[l * m + r], pin[l], s0);
+    ws[g.ws.rr + r] = s0;
+  }
+  for (int r = lane; r < ny; r += 32) {
+    double s0 = ws[g.ws.cb + r] - zn[r];
+    for (int l = 0; l < nx; l++) s0 = fma(Ab[r * n + l], z[l], s0);
+    for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], v[l], s0);
+    ws[g.ws.rc + r] = s0;
+  }
+}
+
+// k'_i = -H_uu^{-1} (rr + Bbar' (P_{i+1} rc + p'_{i+1}))  -> dv (temporarily)
+__global__ void k_kcorr(Group g) {
+  const int s = warp_task();
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  if (S.i >= P.N) return;
+  const int n = g.n, m = g.m, lane = lane_id();
+  double *ws = stage_ws(g, s);
+  const double *wn = stage_ws(g, s + 1);
+  const int mu = stage_wi(g, s)[SI_MBAR], ny = stage_wi(g, s + 1)[SI_NBAR];
+  const double *Bb = ws + g.ws.Bb, *Pn = wn + g.ws.P, *rc = ws + g.ws.rc, *ppn = wn + g.ws.pp;
+  const double *Lh = ws + g.ws.Lh;
+  double w = 0.0;
+  if (lane < ny) {
+    w = ppn[lane];
+    for (int l = 0; l < ny; l++) w = fma(Pn[lane * n + l], rc[l], w);
+  }
+  double h = 0.0;
+  for (int l = 0; l < ny; l++) {
+    double wl = __shfl_sync(kFull, w, l);
+    if (lane < mu) h = fma(Bb[l * m + lane], wl, h);
+  }
+  if (lane < mu) h += ws[g.ws.rr + lane];
+  // solve L L' k = -h (lane 0 sequential over the tiny system)
+  double hv[16];
+  for (int r = 0; r < 16; r++) hv[r] = __shfl_sync(kFull, h, r);
+  if (lane == 0) {
+    for (int i = 0; i < mu; i++) {
+      double s0 = hv[i];
+      for (int l = 0; l < i; l++) s0 -= Lh[i * m + l] * hv[l];
+      hv[i] = s0 / Lh[i * m + i];
+    }
+    for (int i = mu - 1; i >= 0; i--) {
+      double s0 = hv[i];
+      for (int l = i + 1; l < mu; l++) s0 -= Lh[l * m + i] * hv[l];
+      hv[i] = s0 / Lh[i * m + i];
+    }
+    for (int i = 0; i < mu; i++) ws[g.ws.dv + i] = -hv[i];
+  }
+}
+
+// x_i = T z + t, u_i = Y z + Z v + y (eq. recovery-maps)
+__global__ void k_recover(Group g, double *x, double *u) {
+  const int s = warp_task();
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  const int n = g.n, m = g.m, lane = lane_id();
+  const double *ws = stage_ws(g, s);
+  const int *wi = stage_wi(g, s);
+  const int ur = wi[SI_UR], nb = n - ur;
+  const double *T = ws + g.ws.UT + ur, *z = ws + g.ws.z;
+  for (int a = lane; a < n; a += 32) {
+    double v = ws[g.ws.t + a];
+    for (int j = 0; j < nb; j++) v = fma(T[a * n + j], z[j], v);
+    x[P.ox + (size_t)S.i * n + a] = v;
+  }
+  if (S.i < P.N) {
+    const int mb = wi[SI_MBAR];
+    const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *vv = ws + g.ws.v;
+    for (int a = lane; a < m; a += 32) {
+      double v = ws[g.ws.y + a];
+      for (int j = 0; j < nb; j++) v = fma(Y[a * n + j], z[j], v);
+      for (int j = 0; j < mb; j++) v = fma(Z[a * m + j], vv[j], v);
+      u[P.ou + (size_t)S.i * m + a] = v;
+    }
+  }
+}
+
+}  // namespace eclqr
+
+namespace eclqr {
+// reduced dimensions into batch-ordered arrays: nbar has N_j + 1 entries per
+// problem (same prefix as x / n), mbar N_j entries (same prefix as u / m)
+__global__ void k_dims(Group g, int *nbar, int *mbar) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  const int *wi = stage_wi(g, s);
+  nbar[P.ox / g.n + S.i] = wi[SI_NBAR];
+  if (S.i < P.N) mbar[P.ou / g.m + S.i] = wi[SI_MBAR];
+}
+}  // namespace eclqr

@@ -1,0 +1,54 @@
+// kernels.cuh -- kernel and shared-memory-size declarations shared by the
+// kernel translation units and the host orchestration (api.cu).
+#pragma once
+#include "plan.cuh"
+
+namespace eclqr {
+
+// shared memory per warp, in doubles
+__host__ int smem_primal_sweep(int n, int m, int pmax, int qmax);
+__host__ int smem_rel_level(int n, int pmax, int qmax);
+__host__ int smem_param(int n);
+__host__ int smem_elim(int n, int m, int pmax);
+__host__ int smem_lqr_up(int n, int m);
+__host__ int smem_lqr_level(int n);
+__host__ int smem_riccati(int n, int m);
+__host__ int smem_aff(int n);
+__host__ int smem_dual_stage(int n, int m);
+__host__ int smem_dual_sweep(int n, int m, int pmax, int qmax);
+__host__ int smem_dual_leaf(int n, int m, int pmax, int qmax);
+
+// primal scan and elimination (k_primal.cu)
+__global__ void k_terminal(Group g, int per_warp);
+__global__ void k_primal_up(Group g, int per_warp);
+__global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_warp);
+__global__ void k_primal_down(Group g, int fin, int per_warp);
+__global__ void k_param(Group g, int per_warp);
+__global__ void k_elim(Group g, int per_warp);
+
+// reduced LQR, affine chains, recovery (k_lqr.cu)
+enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_CLIN_ = 2, AFF_NU_ = 3 };
+__global__ void k_lqr_up(Group g, int per_warp);
+__global__ void k_lqr_level(Group g, int src, int d, int per_warp);
+__global__ void k_riccati_down(Group g, int fin, int per_warp);
+__global__ void k_aff_up(Group g, int mode, int per_warp);
+__global__ void k_aff_level(Group g, int src, int d, int fwd, int per_warp);
+__global__ void k_aff_down(Group g, int mode, int fin, int per_warp);
+__global__ void k_solve_init(Group g, const double *s0);
+__global__ void k_post_roll(Group g, int corr);
+__global__ void k_resid(Group g);
+__global__ void k_kcorr(Group g);
+__global__ void k_recover(Group g, double *x, double *u);
+__global__ void k_dims(Group g, int *nbar, int *mbar);
+
+// multipliers and residual (k_dual.cu)
+__global__ void k_dual_stage(Group g, const double *x, const double *u, int per_warp);
+__global__ void k_dual_terminal(Group g, int per_warp);
+__global__ void k_dual_up(Group g, int per_warp);
+__global__ void k_dual_down(Group g, int fin, int per_warp);
+__global__ void k_dual_root(Group g, int per_warp);
+__global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_warp);
+__global__ void k_kkt_residual(Group g, const double *s0, const double *x, const double *u, const double *lam,
+                               const double *mu, const double *eta, const double *alpha, double *resid);
+
+}  // namespace eclqr

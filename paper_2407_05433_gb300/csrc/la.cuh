@@ -1,0 +1,689 @@
+// la.cuh -- warp-level FP64 dense linear algebra on small matrices held in
+// shared memory.  Every routine is called by all 32 lanes of one warp, with
+// the warp converged; matrices are row-major with explicit leading dimensions.
+//
+// Cost model on sm_103a: an FP64 instruction occupies the SM sub-partition's
+// FP64 pipe for the whole warp whatever its active mask, so loops hand each
+// lane an independent output element (element-parallel updates, lane-per-
+// column dot products) instead of reducing across lanes wherever possible.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eclqr {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// arg-max over non-negative values; ties resolve to the lowest index.  The
+// bit pattern of a non-negative double orders like the value, so the
+// comparison runs on the integer pipe.
+__device__ __forceinline__ void warp_argmax(double v, int idx, double &bv, int &bi) {
+  long long key = __double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    long long k2 = __shfl_xor_sync(kFull, key, o);
+    int i2 = __shfl_xor_sync(kFull, idx, o);
+    if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+  }
+  bv = __longlong_as_double(key);
+  bi = idx;
+}
+
+__device__ __forceinline__ void wzero(double *p, int n) {
+  for (int i = lane_id(); i < n; i += 32) p[i] = 0.0;
+  __syncwarp();
+}
+
+__device__ __forceinline__ void wcopy(double *dst, int ldd, const double *src, int lds, int rows,
+                                      int cols) {
+  for (int idx = lane_id(); idx < rows * cols; idx += 32) {
+    int i = idx / cols, j = idx - i * cols;
+    dst[i * ldd + j] = src[i * lds + j];
+  }
+  __syncwarp();
+}
+
+// C (m x n) = alpha * op(A) op(B) + beta * C; op(A) is m x k, op(B) is k x n.
+// C must not alias A or B.
+template <bool TA, bool TB>
+static __device__ void wgemm(int m, int n, int k, double alpha, const double *A, int lda, const double *B,
+                      int ldb, double beta, double *C, int ldc) {
+  for (int idx = lane_id(); idx < m * n; idx += 32) {
+    int i = idx / n, j = idx - i * n;
+    double s0 = 0.0, s1 = 0.0;
+    int l = 0;
+    for (; l + 1 < k; l += 2) {
+      double a0 = TA ? A[l * lda + i] : A[i * lda + l];
+      double a1 = TA ? A[(l + 1) * lda + i] : A[i * lda + l + 1];
+      double b0 = TB ? B[j * ldb + l] : B[l * ldb + j];
+      double b1 = TB ? B[j * ldb + l + 1] : B[(l + 1) * ldb + j];
+      s0 = fma(a0, b0, s0);
+      s1 = fma(a1, b1, s1);
+    }
+    if (l < k) {
+      double a0 = TA ? A[l * lda + i] : A[i * lda + l];
+      double b0 = TB ? B[j * ldb + l] : B[l * ldb + j];
+      s0 = fma(a0, b0, s0);
+    }
+    double s = alpha * (s0 + s1);
+    C[i * ldc + j] = (beta == 0.0) ? s : fma(beta, C[i * ldc + j], s);
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Lemma 1 by ordered column-pivoted Householder row reduction.
+//
+// M (r x nc, ld) holds, column-wise: ng groups of columns to eliminate (sizes
+// gsz[]), then nkeep kept columns, then one offset column.  Tolerance policy
+// (Sec. 8): every row is scaled to unit 2-norm over its coefficient columns;
+// a pivot is accepted when its column norm over the remaining rows exceeds
+// tau_rank * nu (nu = largest column norm of the scaled matrix); groups are
+// pivoted in order, the eliminated variables first; a leftover row whose
+// offset exceeds tau_inc * max(1, largest scaled offset) is inconsistent.
+// On return rows [k0, k0 + krank) hold the kept relation in the kept columns
+// (upper-trapezoidal in pivot order); they are also written, each renormalised
+// to unit coefficient norm, to out (krank x (nkeep + 1), ldo) when out != 0.
+// scr: >= 2 * nc + r + nc/2 + 1 doubles of scratch private to the warp.
+// ---------------------------------------------------------------------------
+struct ProjResult {
+  int grank[3];
+  int krank;
+  int k0;
+  int inconsistent;
+};
+
+static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const int *gsz, int nkeep,
+                               double tau_rank, double tau_inc, double *out, int ldo,
+                               double *scr) {
+  const int lane = lane_id();
+  int ncoef = nkeep;
+  for (int g = 0; g < ng; g++) ncoef += gsz[g];
+  const int nc = ncoef + 1, off = ncoef;
+  double *v = scr;                 // r
+  double *w = scr + r;             // nc
+  int *done = (int *)(scr + r + nc);  // nc ints
+  ProjResult res;
+  res.grank[0] = res.grank[1] = res.grank[2] = 0;
+  res.krank = 0;
+  res.k0 = 0;
+  res.inconsistent = 0;
+
+  // row scaling
+  for (int i = lane; i < r; i += 32) {
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+    for (; j + 1 < ncoef; j += 2) {
+      double a = M[i * ld + j], b = M[i * ld + j + 1];
+      s0 = fma(a, a, s0);
+      s1 = fma(b, b, s1);
+    }
+    if (j < ncoef) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
+    double s = s0 + s1;
+    if (s > 0.0) {
+      double inv = 1.0 / sqrt(s);
+      for (j = 0; j < nc; j++) M[i * ld + j] *= inv;
+    }
+  }
+  for (int j = lane; j < nc; j += 32) done[j] = 0;
+  __syncwarp();
+  // nu and omega
+  double nu = 0.0, om = 0.0;
+  for (int j = lane; j < ncoef; j += 32) {
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < r; i += 2) {
+      s0 = fma(M[i * ld + j], M[i * ld + j], s0);
+      s1 = fma(M[(i + 1) * ld + j], M[(i + 1) * ld + j], s1);
+    }
+    if (i < r) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
+    nu = fmax(nu, s0 + s1);
+  }
+  for (int i = lane; i < r; i += 32) om = fmax(om, fabs(M[i * ld + off]));
+  nu = sqrt(warp_max(nu));
+  om = fmax(1.0, warp_max(om));
+  const double thr = tau_rank * nu;
+
+  int k = 0, c0 = 0;
+  for (int g = 0; g <= ng; g++) {
+    const int c1 = c0 + (g < ng ? gsz[g] : nkeep);
+    int rk = 0;
+    while (k < r) {
+      double mybest = -1.0;
+      int mypiv = 0x7fffffff;
+      for (int j = c0 + lane; j < c1; j += 32) {
+        if (done[j]) continue;
+        double s0 = 0.0, s1 = 0.0;
+        int i = k;
+        for (; i + 1 < r; i += 2) {
+          s0 = fma(M[i * ld + j], M[i * ld + j], s0);
+          s1 = fma(M[(i + 1) * ld + j], M[(i + 1) * ld + j], s1);
+        }
+        if (i < r) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
+        double s = s0 + s1;
+        if (s > mybest) { mybest = s; mypiv = j; }
+      }
+      double best2;
+      int piv;
+      warp_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, best2, piv);
+      if (piv == 0x7fffffff) break;
+      const double best = sqrt(best2);
+      if (!(best > thr)) break;
+      const double xk = M[k * ld + piv];
+      const double sg = xk >= 0.0 ? 1.0 : -1.0;
+      for (int i = k + lane; i < r; i += 32) v[i] = (i == k) ? xk + sg * best : M[i * ld + piv];
+      const double beta = 1.0 / (best * (best + fabs(xk)));
+      __syncwarp();
+      for (int j = lane; j < nc; j += 32) {
+        if (done[j] || j == piv) continue;
+        double s0 = 0.0, s1 = 0.0;
+        int i = k;
+        for (; i + 1 < r; i += 2) {
+          s0 = fma(v[i], M[i * ld + j], s0);
+          s1 = fma(v[i + 1], M[(i + 1) * ld + j], s1);
+        }
+        if (i < r) s0 = fma(v[i], M[i * ld + j], s0);
+        w[j] = beta * (s0 + s1);
+      }
+      __syncwarp();
+      const int rows = r - k;
+      for (int idx = lane; idx < rows * nc; idx += 32) {
+        int i = k + idx / nc, j = idx % nc;
+        if (done[j] || j == piv) continue;
+        M[i * ld + j] = fma(-w[j], v[i], M[i * ld + j]);
+      }
+      __syncwarp();
+      for (int i = k + lane; i < r; i += 32) M[i * ld + piv] = (i == k) ? -sg * best : 0.0;
+      if (lane == 0) done[piv] = 1;
+      __syncwarp();
+      k++;
+      rk++;
+    }
+    if (g < ng) res.grank[g] = rk; else res.krank = rk;
+    c0 = c1;
+  }
+  res.k0 = k - res.krank;
+  int bad = 0;
+  for (int i = k + lane; i < r; i += 32)
+    if (fabs(M[i * ld + off]) > tau_inc * om) bad = 1;
+  res.inconsistent = __any_sync(kFull, bad);
+  if (out) {
+    const int kc0 = ncoef - nkeep;
+    for (int a = lane; a < res.krank; a += 32) {
+      const double *row = M + (res.k0 + a) * ld;
+      double s = 0.0;
+      for (int j = 0; j < nkeep; j++) s = fma(row[kc0 + j], row[kc0 + j], s);
+      double inv = 1.0 / sqrt(s);
+      for (int j = 0; j < nkeep; j++) out[a * ldo + j] = row[kc0 + j] * inv;
+      out[a * ldo + nkeep] = row[off] * inv;
+    }
+  }
+  __syncwarp();
+  return res;
+}
+
+// ---------------------------------------------------------------------------
+// Null space and minimum-norm solutions of K X = -B through the column-
+// pivoted Householder QR of K^T (pivoting over the rows of K):
+//   K^T Pi = Q R,   rank = accepted pivots (tau_rank * largest row norm).
+// W (nk x rk, ldw) receives K^T and is overwritten by R; Q (nk x nk, ldq) is
+// formed explicitly: its first `rank` columns span range(K^T), the last
+// nk - rank are an orthonormal basis of null(K).  perm: rk ints.
+// ---------------------------------------------------------------------------
+static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_rank, double *W, int ldw,
+                    double *Q, int ldq, int *perm, double *scr /* >= nk + max(nk, rk) */) {
+  const int lane = lane_id();
+  double *v = scr, *w = scr + nk;
+  for (int idx = lane; idx < nk * rk; idx += 32) {
+    int i = idx / rk, j = idx - i * rk;
+    W[i * ldw + j] = K[j * ldk + i];
+  }
+  for (int idx = lane; idx < nk * nk; idx += 32) {
+    int i = idx / nk, j = idx - i * nk;
+    Q[i * ldq + j] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int j = lane; j < rk; j += 32) perm[j] = j;
+  __syncwarp();
+  double nu = 0.0;
+  for (int j = lane; j < rk; j += 32) {
+    double s = 0.0;
+    for (int i = 0; i < nk; i++) s = fma(W[i * ldw + j], W[i * ldw + j], s);
+    nu = fmax(nu, s);
+  }
+  nu = sqrt(warp_max(nu));
+  const double thr = tau_rank * nu;
+  int rank = 0;
+  for (int s = 0; s < rk && s < nk; s++) {
+    double mybest = -1.0;
+    int mypiv = 0x7fffffff;
+    for (int j = s + lane; j < rk; j += 32) {
+      double t = 0.0;
+      for (int i = s; i < nk; i++) t = fma(W[i * ldw + j], W[i * ldw + j], t);
+      if (t > mybest) { mybest = t; mypiv = j; }
+    }
+    double b2;
+    int piv;
+    warp_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
+    if (piv == 0x7fffffff) break;
+    const double best = sqrt(b2);
+    if (!(best > thr)) break;
+    if (piv != s) {
+      for (int i = lane; i < nk; i += 32) {
+        double t = W[i * ldw + s];
+        W[i * ldw + s] = W[i * ldw + piv];
+        W[i * ldw + piv] = t;
+      }
+      if (lane == 0) {
+        int t = perm[s]; perm[s] = perm[piv]; perm[piv] = t;
+      }
+      __syncwarp();
+    }
+    const double xk = W[s * ldw + s];
+    const double sg = xk >= 0.0 ? 1.0 : -1.0;
+    for (int i = s + lane; i < nk; i += 32) v[i] = (i == s) ? xk + sg * best : W[i * ldw + s];
+    const double beta = 1.0 / (best * (best + fabs(xk)));
+    __syncwarp();
+    // W columns > s
+    for (int j = s + 1 + lane; j < rk; j += 32) {
+      double t = 0.0;
+      for (int i = s; i < nk; i++) t = fma(v[i], W[i * ldw + j], t);
+      w[j] = beta * t;
+    }
+    __syncwarp();
+    const int cols = rk - s - 1, rows = nk - s;
+    for (int idx = lane; idx < rows * cols; idx += 32) {
+      int i = s + idx / cols, j = s + 1 + idx % cols;
+      W[i * ldw + j] = fma(-w[j], v[i], W[i * ldw + j]);
+    }
+    __syncwarp();
+    for (int i = s + lane; i < nk; i += 32) W[i * ldw + s] = (i == s) ? -sg * best : 0.0;
+    // Q <- Q H on columns [s, nk)
+    for (int i = lane; i < nk; i += 32) {
+      double t = 0.0;
+      for (int l = s; l < nk; l++) t = fma(Q[i * ldq + l], v[l], t);
+      w[i] = beta * t;
+    }
+    __syncwarp();
+    for (int idx = lane; idx < nk * rows; idx += 32) {
+      int i = idx / rows, l = s + idx % rows;
+      Q[i * ldq + l] = fma(-w[i], v[l], Q[i * ldq + l]);
+    }
+    __syncwarp();
+    rank++;
+  }
+  return rank;
+}
+
+// After wtqr: X (nk x nb, ldx) = -Q1 R11^{-T} (Pi^T B)_1 for B (rk x nb, ldb),
+// the min-norm solutions of K X = -B.  Returns the largest residual of the
+// dependent rows relative to max(1, |B|_max) (a consistency check).
+// Y: rank x nb scratch (ldy).  X must not alias B.
+static __device__ double wtqr_solve(const double *W, int ldw, const double *Q, int ldq, const int *perm,
+                             int rk, int nk, int rank, const double *B, int ldb, int nb, double *X,
+                             int ldx, double *Y, int ldy) {
+  const int lane = lane_id();
+  double bmax = 0.0;
+  for (int idx = lane; idx < rk * nb; idx += 32) {
+    int i = idx / nb, j = idx - i * nb;
+    bmax = fmax(bmax, fabs(B[i * ldb + j]));
+  }
+  bmax = fmax(1.0, warp_max(bmax));
+  double rmax = 0.0;
+  for (int c = lane; c < nb; c += 32) {
+    for (int i = 0; i < rank; i++) {
+      double s = B[perm[i] * ldb + c];
+      for (int l = 0; l < i; l++) s = fma(-W[l * ldw + i], Y[l * ldy + c], s);
+      Y[i * ldy + c] = s / W[i * ldw + i];
+    }
+    for (int j = rank; j < rk; j++) {
+      double s = B[perm[j] * ldb + c];
+      for (int l = 0; l < rank; l++) s = fma(-W[l * ldw + j], Y[l * ldy + c], s);
+      rmax = fmax(rmax, fabs(s));
+    }
+  }
+  __syncwarp();
+  for (int idx = lane; idx < nk * nb; idx += 32) {
+    int i = idx / nb, c = idx - i * nb;
+    double s = 0.0;
+    for (int l = 0; l < rank; l++) s = fma(Q[i * ldq + l], Y[l * ldy + c], s);
+    X[i * ldx + c] = -s;
+  }
+  __syncwarp();
+  return warp_max(rmax) / bmax;
+}
+
+// In-place Cholesky L L^T of an SPD n x n matrix (lower triangle, upper set
+// to zero).  Returns 0 on success, 1 if a pivot is not positive.
+static __device__ int wcholesky(double *Hm, int ld, int n) {
+  const int lane = lane_id();
+  int fail = 0;
+  for (int j = 0; j < n; j++) {
+    // diagonal
+    double s = Hm[j * ld + j];
+    for (int l = 0; l < j; l++) s = fma(-Hm[j * ld + l], Hm[j * ld + l], s);
+    if (!(s > 0.0)) fail = 1;
+    const double d = sqrt(fmax(s, 1e-300));
+    const double inv = 1.0 / d;
+    for (int i = j + 1 + lane; i < n; i += 32) {
+      double t = Hm[i * ld + j];
+      for (int l = 0; l < j; l++) t = fma(-Hm[i * ld + l], Hm[j * ld + l], t);
+      Hm[i * ld + j] = t * inv;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      Hm[j * ld + j] = d;
+      for (int i = 0; i < j; i++) Hm[i * ld + j] = 0.0;
+    }
+    __syncwarp();
+  }
+  return fail;
+}
+
+// Solve (L L^T) X = B in place, B n x nb (ld ldb); lanes over right-hand sides.
+static __device__ void wchol_solve(const double *L, int ldl, int n, double *B, int ldb, int nb) {
+  for (int c = lane_id(); c < nb; c += 32) {
+    for (int i = 0; i < n; i++) {
+      double s = B[i * ldb + c];
+      for (int l = 0; l < i; l++) s = fma(-L[i * ldl + l], B[l * ldb + c], s);
+      B[i * ldb + c] = s / L[i * ldl + i];
+    }
+    for (int i = n - 1; i >= 0; i--) {
+      double s = B[i * ldb + c];
+      for (int l = i + 1; l < n; l++) s = fma(-L[l * ldl + i], B[l * ldb + c], s);
+      B[i * ldb + c] = s / L[i * ldl + i];
+    }
+  }
+  __syncwarp();
+}
+
+// In-place LU with partial pivoting of an n x n matrix; piv: n ints.
+static __device__ void wlu(double *A, int ld, int n, int *piv) {
+  const int lane = lane_id();
+  for (int j = 0; j < n; j++) {
+    double mybest = -1.0;
+    int myi = 0x7fffffff;
+    for (int i = j + lane; i < n; i += 32) {
+      double a = fabs(A[i * ld + j]);
+      if (a > mybest) { mybest = a; myi = i; }
+    }
+    double b;
+    int p;
+    warp_argmax(mybest < 0.0 ? 0.0 : mybest, myi, b, p);
+    if (p == 0x7fffffff) p = j;
+    if (p != j) {
+      for (int c = lane; c < n; c += 32) {
+        double t = A[j * ld + c]; A[j * ld + c] = A[p * ld + c]; A[p * ld + c] = t;
+      }
+    }
+    if (lane == 0) piv[j] = p;
+    __syncwarp();
+    const double inv = 1.0 / A[j * ld + j];
+    for (int i = j + 1 + lane; i < n; i += 32) A[i * ld + j] *= inv;
+    __syncwarp();
+    const int rows = n - j - 1, cols = n - j - 1;
+    for (int idx = lane; idx < rows * cols; idx += 32) {
+      int i = j + 1 + idx / cols, c = j + 1 + idx % cols;
+      A[i * ld + c] = fma(-A[i * ld + j], A[j * ld + c], A[i * ld + c]);
+    }
+    __syncwarp();
+  }
+}
+
+// Solve A X = B (trans = 0) or A^T X = B (trans = 1) with the LU of wlu; B is
+// n x nb, overwritten with X; lanes over right-hand sides.
+static __device__ void wlu_solve(const double *LU, int ld, int n, const int *piv, double *B, int ldb, int nb,
+                          int trans) {
+  for (int c = lane_id(); c < nb; c += 32) {
+    if (!trans) {
+      for (int i = 0; i < n; i++)
+        if (piv[i] != i) { double t = B[i * ldb + c]; B[i * ldb + c] = B[piv[i] * ldb + c]; B[piv[i] * ldb + c] = t; }
+      for (int i = 0; i < n; i++) {
+        double s = B[i * ldb + c];
+        for (int l = 0; l < i; l++) s = fma(-LU[i * ld + l], B[l * ldb + c], s);
+        B[i * ldb + c] = s;
+      }
+      for (int i = n - 1; i >= 0; i--) {
+        double s = B[i * ldb + c];
+        for (int l = i + 1; l < n; l++) s = fma(-LU[i * ld + l], B[l * ldb + c], s);
+        B[i * ldb + c] = s / LU[i * ld + i];
+      }
+    } else {
+      // A^T = U^T L^T P
+      for (int i = 0; i < n; i++) {
+        double s = B[i * ldb + c];
+        for (int l = 0; l < i; l++) s = fma(-LU[l * ld + i], B[l * ldb + c], s);
+        B[i * ldb + c] = s / LU[i * ld + i];
+      }
+      for (int i = n - 1; i >= 0; i--) {
+        double s = B[i * ldb + c];
+        for (int l = i + 1; l < n; l++) s = fma(-LU[l * ld + i], B[l * ldb + c], s);
+        B[i * ldb + c] = s;
+      }
+      for (int i = n - 1; i >= 0; i--)
+        if (piv[i] != i) { double t = B[i * ldb + c]; B[i * ldb + c] = B[piv[i] * ldb + c]; B[piv[i] * ldb + c] = t; }
+    }
+  }
+  __syncwarp();
+}
+
+}  // namespace eclqr
+
+namespace eclqr {
+
+// ---------------------------------------------------------------------------
+// Elimination in a cost relation: rows [0, rc) are constraints (hold exactly),
+// rows [rc, rc + rq) are least-squares cost rows (1/2 ||row . (vars, 1)||^2).
+// Columns: ne eliminated | nk kept | 1 offset.  Minimises the cost over the
+// eliminated variables subject to the constraints and returns the induced
+// relation on the kept variables (equality-constrained least squares by
+// direct elimination):
+//   A. column-pivoted Householder on the (row-scaled) constraint rows over the
+//      eliminated columns;
+//   B. the constraint pivot rows remove their pivot variables from the cost
+//      rows (adding multiples of an exact equation leaves the cost unchanged
+//      on the constraint set);
+//   C. column-pivoted Householder on the cost rows over the remaining
+//      eliminated columns (their pivot rows vanish at the minimiser);
+//   D. remaining constraint rows reduced to an independent basis over the kept
+//      columns, leftover rows checked for 0 = gamma (tau_inc);
+//   E. remaining cost rows compressed by Householder QR over the kept columns.
+// Outputs: kc constraint rows (unit coefficient norm) to outC and kq cost rows
+// to outQ, each (nk + 1) wide with leading dimension ldo.
+// scr: >= 2 (rc + rq) + 2 (ne + nk + 1) + ne / 2 + 4 doubles.
+// ---------------------------------------------------------------------------
+struct LseResult {
+  int k1, k2, kc, kq, inconsistent;
+};
+
+static __device__ void whouse_apply(double *M, int ld, int r0, int r1, int piv, int c0, int c1, const int *done,
+                                    double *v, double *w, double nrm) {
+  // reflector from column piv on rows [r0, r1) applied to columns [c0, c1) not done (piv excluded)
+  const int lane = lane_id();
+  const double xk = M[r0 * ld + piv];
+  const double sg = xk >= 0.0 ? 1.0 : -1.0;
+  for (int i = r0 + lane; i < r1; i += 32) v[i] = (i == r0) ? xk + sg * nrm : M[i * ld + piv];
+  const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
+  __syncwarp();
+  for (int j = c0 + lane; j < c1; j += 32) {
+    if ((done && done[j]) || j == piv) continue;
+    double s0 = 0.0, s1 = 0.0;
+    int i = r0;
+    for (; i + 1 < r1; i += 2) {
+      s0 = fma(v[i], M[i * ld + j], s0);
+      s1 = fma(v[i + 1], M[(i + 1) * ld + j], s1);
+    }
+    if (i < r1) s0 = fma(v[i], M[i * ld + j], s0);
+    w[j] = beta * (s0 + s1);
+  }
+  __syncwarp();
+  const int rows = r1 - r0, cols = c1 - c0;
+  for (int idx = lane; idx < rows * cols; idx += 32) {
+    int i = r0 + idx / cols, j = c0 + idx % cols;
+    if ((done && done[j]) || j == piv) continue;
+    M[i * ld + j] = fma(-w[j], v[i], M[i * ld + j]);
+  }
+  __syncwarp();
+  for (int i = r0 + lane; i < r1; i += 32) M[i * ld + piv] = (i == r0) ? -sg * nrm : 0.0;
+  __syncwarp();
+}
+
+// pivot search: largest column norm (squared) among columns [c0, c1) not done over rows [r0, r1)
+static __device__ void wpivot(const double *M, int ld, int r0, int r1, int c0, int c1, const int *done,
+                              double &best, int &piv) {
+  double mybest = -1.0;
+  int mypiv = 0x7fffffff;
+  for (int j = c0 + lane_id(); j < c1; j += 32) {
+    if (done && done[j]) continue;
+    double s0 = 0.0, s1 = 0.0;
+    int i = r0;
+    for (; i + 1 < r1; i += 2) {
+      s0 = fma(M[i * ld + j], M[i * ld + j], s0);
+      s1 = fma(M[(i + 1) * ld + j], M[(i + 1) * ld + j], s1);
+    }
+    if (i < r1) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
+    double s = s0 + s1;
+    if (s > mybest) { mybest = s; mypiv = j; }
+  }
+  double b2;
+  warp_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
+  best = sqrt(b2);
+}
+
+static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne, int nk, double tau_rank,
+                                      double tau_inc, double *outC, double *outQ, int ldo, double *scr) {
+  const int lane = lane_id();
+  const int nc = ne + nk + 1, off = ne + nk, r = rc + rq;
+  double *v = scr;
+  double *w = v + r;
+  int *done = (int *)(w + (nc > r ? nc : r));
+  int *pc = done + nc;
+  LseResult res;
+  res.k1 = res.k2 = res.kc = res.kq = res.inconsistent = 0;
+  // scale constraint rows to unit coefficient norm
+  for (int i = lane; i < rc; i += 32) {
+    double s = 0.0;
+    for (int j = 0; j < off; j++) s = fma(M[i * ld + j], M[i * ld + j], s);
+    if (s > 0.0) {
+      double inv = 1.0 / sqrt(s);
+      for (int j = 0; j < nc; j++) M[i * ld + j] *= inv;
+    }
+  }
+  for (int j = lane; j < nc; j += 32) done[j] = 0;
+  __syncwarp();
+  double nu = 0.0, om = 0.0;
+  for (int j = lane; j < off; j += 32) {
+    double s = 0.0;
+    for (int i = 0; i < rc; i++) s = fma(M[i * ld + j], M[i * ld + j], s);
+    nu = fmax(nu, s);
+  }
+  for (int i = lane; i < rc; i += 32) om = fmax(om, fabs(M[i * ld + off]));
+  nu = sqrt(warp_max(nu));
+  om = fmax(1.0, warp_max(om));
+  const double thr = tau_rank * nu;
+  // A
+  int k = 0;
+  while (k < rc) {
+    double best;
+    int piv;
+    wpivot(M, ld, k, rc, 0, ne, done, best, piv);
+    if (piv == 0x7fffffff || !(best > thr)) break;
+    whouse_apply(M, ld, k, rc, piv, 0, nc, done, v, w, best);
+    if (lane == 0) { done[piv] = 1; pc[k] = piv; }
+    __syncwarp();
+    k++;
+  }
+  res.k1 = k;
+  // B
+  for (int p = 0; p < res.k1; p++) {
+    const int col = pc[p];
+    const double inv = 1.0 / M[p * ld + col];
+    for (int q = lane; q < rq; q += 32) w[q] = M[(rc + q) * ld + col] * inv;
+    __syncwarp();
+    for (int idx = lane; idx < rq * nc; idx += 32) {
+      int q = idx / nc, j = idx - q * nc;
+      double val = (j == col) ? 0.0 : fma(-w[q], M[p * ld + j], M[(rc + q) * ld + j]);
+      M[(rc + q) * ld + j] = val;
+    }
+    __syncwarp();
+  }
+  // C
+  double nuq = 0.0;
+  for (int j = lane; j < ne; j += 32) {
+    if (done[j]) continue;
+    double s = 0.0;
+    for (int i = rc; i < r; i++) s = fma(M[i * ld + j], M[i * ld + j], s);
+    nuq = fmax(nuq, s);
+  }
+  nuq = sqrt(warp_max(nuq));
+  int kk = rc;
+  while (kk < r) {
+    double best;
+    int piv;
+    wpivot(M, ld, kk, r, 0, ne, done, best, piv);
+    if (piv == 0x7fffffff || !(best > tau_rank * nuq) || best == 0.0) break;
+    whouse_apply(M, ld, kk, r, piv, 0, nc, done, v, w, best);
+    if (lane == 0) done[piv] = 1;
+    __syncwarp();
+    kk++;
+  }
+  res.k2 = kk - rc;
+  // D
+  int kd = res.k1;
+  while (kd < rc) {
+    double best;
+    int piv;
+    wpivot(M, ld, kd, rc, ne, off, done, best, piv);
+    if (piv == 0x7fffffff || !(best > thr)) break;
+    whouse_apply(M, ld, kd, rc, piv, ne, nc, done, v, w, best);
+    if (lane == 0) done[piv] = 1;
+    __syncwarp();
+    kd++;
+  }
+  res.kc = kd - res.k1;
+  int bad = 0;
+  for (int i = kd + lane; i < rc; i += 32)
+    if (fabs(M[i * ld + off]) > tau_inc * om) bad = 1;
+  res.inconsistent = __any_sync(kFull, bad);
+  for (int a = lane; a < res.kc; a += 32) {
+    const double *row = M + (res.k1 + a) * ld;
+    double s = 0.0;
+    for (int j = 0; j < nk; j++) s = fma(row[ne + j], row[ne + j], s);
+    double inv = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+    for (int j = 0; j < nk; j++) outC[a * ldo + j] = row[ne + j] * inv;
+    outC[a * ldo + nk] = row[off] * inv;
+  }
+  __syncwarp();
+  // E: compress the remaining cost rows over the kept columns (no pivoting)
+  int ke = kk;
+  for (int col = ne; col < off && ke < r; col++) {
+    double s = 0.0;
+    for (int i = ke + lane; i < r; i += 32) s = fma(M[i * ld + col], M[i * ld + col], s);
+    s = sqrt(warp_sum(s));
+    if (s == 0.0) continue;
+    whouse_apply(M, ld, ke, r, col, col + 1, nc, nullptr, v, w, s);
+    ke++;
+  }
+  res.kq = ke - kk;
+  for (int idx = lane; idx < res.kq * (nk + 1); idx += 32) {
+    int a = idx / (nk + 1), j = idx - a * (nk + 1);
+    outQ[a * ldo + j] = M[(kk + a) * ld + ne + j];
+  }
+  __syncwarp();
+  return res;
+}
+
+}  // namespace eclqr

@@ -1,0 +1,141 @@
+// plan.cuh -- batch plan shared by the kernels and the host orchestration.
+//
+// A batch is split into groups of problems with equal (n, m).  Inside a
+// group every stage owns a fixed-stride workspace slot (doubles) and a few
+// ints; every problem owns nch + 1 chunk slots (nch scan chunks plus the
+// terminal element), double-buffered for the log-depth chunk scans.
+#pragma once
+#include <stdint.h>
+#include "la.cuh"
+
+namespace eclqr {
+
+struct ProbInfo {
+  int N;        // horizon
+  int L;        // stages per chunk
+  int nch;      // number of chunks, ceil(N / L)
+  int ch0;      // first chunk slot of this problem (nch + 1 slots)
+  int st0;      // first stage slot (N + 1 slots: stages 0..N)
+  int id;       // index in the batch (status, residual)
+  long long oA, oB, oc, oC, oD, od, oE, oe, oQ, oM, oR, oqv, orv;  // element offsets of the problem's data
+  long long os0, ox, ou, olam, omu, oeta, oalpha;                // element offsets of s0 and outputs
+};
+
+struct StageInfo {
+  int prob;     // problem index inside the group
+  int i;        // stage index 0..N
+  int p, q;     // mixed / state-only rows
+  int prow, qrow;  // first row of this stage in the problem's C/D/d and E/e blocks
+};
+
+struct ChunkInfo {
+  int prob;     // problem index inside the group
+  int c;        // chunk index 0..nch (nch = terminal element)
+};
+
+// ---- per-stage workspace layout (offsets in doubles) ----
+struct WsLayout {
+  int H, UT, t, Y, Z, y, Ab, Bb, cb, Qb, Mb, Rb, qb, rb;
+  int P, p, K, k, Lh, Hx, Phi;
+  int z, v, pi, dz, dv, dpi, rq, rr, rc, pp;
+  int nu, NH, Pnu, pnu, UA, BU, UC, Ux, ru;
+  int LT, lt;   // Cholesky factor L' of the reduced stage Hessian (order z, v) and L^{-1}[qbar; rbar]
+  int stride;
+};
+
+__host__ __device__ inline WsLayout make_ws_layout(int n, int m, int pmax, int qmax) {
+  WsLayout L;
+  int o = 0;
+  auto take = [&](int sz) { int r = o; o += sz; return r; };
+  L.H = take(n * (n + 1));
+  L.UT = take(n * n);
+  L.t = take(n);
+  L.Y = take(m * n);
+  L.Z = take(m * m);
+  L.y = take(m);
+  L.Ab = take(n * n);
+  L.Bb = take(n * m);
+  L.cb = take(n);
+  L.Qb = take(n * n);
+  L.Mb = take(n * m);
+  L.Rb = take(m * m);
+  L.qb = take(n);
+  L.rb = take(m);
+  L.P = take(n * n);
+  L.p = take(n);
+  L.K = take(m * n);
+  L.k = take(m);
+  L.Lh = take(m * m);
+  L.Hx = take(m * n);
+  L.Phi = take(n * n);
+  L.z = take(n);
+  L.v = take(m);
+  L.pi = take(n);
+  L.dz = take(n);
+  L.dv = take(m);
+  L.dpi = take(n);
+  L.rq = take(n);
+  L.rr = take(m);
+  L.rc = take(n);
+  L.pp = take(n);
+  L.nu = take(n);
+  L.NH = take(n * (n + 1));
+  L.Pnu = take(n * n);
+  L.pnu = take(n);
+  L.UA = take(n * n);
+  L.BU = take(m * n);
+  L.UC = take(n * (pmax + qmax + 1));
+  L.Ux = take(n);
+  L.ru = take(m);
+  L.LT = take((n + m) * (n + m));
+  L.lt = take(n + m);
+  L.stride = (o + 3) & ~3;
+  return L;
+}
+
+// per-stage ints
+enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_STRIDE = 8 };
+// per-chunk-slot ints: rows, left dim, right dim (0 = unary/value)
+enum { CI_ROWS = 0, CI_NA = 1, CI_NB = 2, CI_ROWS2 = 3, CI_STRIDE = 4 };
+
+struct Group {
+  int n, m, pmax, qmax;
+  int nprob, nstage, nslot;
+  const ProbInfo *prob;
+  const StageInfo *st;
+  const ChunkInfo *chunk;
+  // problem data (device, batch-global packed arrays)
+  const double *A, *B, *c, *C, *D, *d, *E, *e, *Q, *M, *R, *qv, *rv;
+  // workspace
+  WsLayout ws;
+  double *W;      // nstage * ws.stride
+  int *WI;        // nstage * SI_STRIDE
+  double *CS[2];  // nslot * cs_stride
+  int *CI[2];     // nslot * CI_STRIDE
+  int cs_stride;
+  double *CR;     // nslot * cr_stride: per-slot scan results kept across kernels
+  int cr_stride;
+  int *status;    // batch-global, indexed by ProbInfo::id
+  double tau_rank, tau_inc;
+};
+
+__device__ __forceinline__ void set_status(const Group &g, int prob, int code) {
+  atomicCAS(g.status + g.prob[prob].id, 0, code);
+}
+
+__device__ __forceinline__ double *stage_ws(const Group &g, int s) { return g.W + (size_t)s * g.ws.stride; }
+__device__ __forceinline__ int *stage_wi(const Group &g, int s) { return g.WI + (size_t)s * SI_STRIDE; }
+
+// task index of the calling warp, and its shared-memory window
+__device__ __forceinline__ int warp_task() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+
+extern __shared__ double g_smem[];
+__device__ __forceinline__ double *warp_smem(int per_warp) { return g_smem + (size_t)(threadIdx.x >> 5) * per_warp; }
+
+// status codes (mirror include/eclqr.h)
+enum {
+  ST_OK = 0, ST_INFEASIBLE_SUFFIX = 1, ST_INFEASIBLE_X0 = 2, ST_RANK_INCONSISTENT = 3,
+  ST_NONCONVEX = 4, ST_DUAL_INCONSISTENT = 5
+};
+
+}  // namespace eclqr

@@ -1,0 +1,153 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Tolerance: 1e-9 relative per block (||delta||_inf / max(1, ||oracle||_inf)) on
+x, u, lambda, mu, eta and alpha; reduced dimensions nbar_i, mbar_i exactly;
+the GPU-computed KKT residual (Sec. 9 definition) at most 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_05433_gb300 import eclqr, synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+KEYS = ("x", "u", "lam", "mu", "eta", "alpha")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2407_05433_gb300 import build as b
+    b.build()
+    eclqr.load()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    if b.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b))))
+
+
+def gpu_run(problems, **kw):
+    b = eclqr.Batch(problems, **kw)
+    try:
+        b.run()
+        res = b.results()
+        dims = b.reduced_dims()
+    finally:
+        b.close()
+    return res, dims
+
+
+def check(pb, r, dims, tol=TOL, orc=None):
+    s = orc or oracle.solve(pb, debug=True)
+    assert s.ok, oracle.STATUS_NAMES[s.status]
+    assert eclqr.STATUS_NAMES[r["status"]] == "ok"
+    nb, mb = dims
+    assert (nb == s.debug["nbar"]).all(), (nb, s.debug["nbar"])
+    assert (mb == s.debug["mbar"]).all(), (mb, s.debug["mbar"])
+    for k in KEYS:
+        e = rel(r[k], getattr(s, k))
+        assert e <= tol, f"{k}: rel err {e:.3e}"
+    assert r["resid"] <= 1e-9, r["resid"]
+    assert oracle.kkt_residual(pb, r["x"], r["u"], r["lam"], r["mu"], r["eta"], r["alpha"]) <= 1e-9
+
+
+def test_scalar_closed_forms():
+    from test_oracle_pins import _scalar
+    for case in "ABC":
+        pb = _scalar(case)
+        (r,), (d,) = gpu_run([pb])
+        check(pb, r, d)
+
+
+CLASSES = [
+    ("mixed", lambda: synth.config("single_n4", N=48)),
+    ("state_only", lambda: synth.config("table1", N=24)),
+    ("degenerate", lambda: synth.config("degenerate_n12", N=32)),
+    ("long_orthogonal", lambda: synth.config("long_n16", N=24)),
+    ("batched_n24", lambda: synth.config("batched_uneven", N=24, index=3)),
+    ("cross_terms", lambda: synth.make_problem(11, 20, 5, 3, 2, np.r_[np.zeros(20, np.int32), 2], cross=True)),
+    ("unconstrained", lambda: synth.make_problem(12, 25, 4, 2, 0, 0)),
+    ("redundant", lambda: synth.make_problem(13, 16, 4, 3, 3, np.r_[np.ones(16, np.int32), 3],
+                                             dup_rows=[(0, 1), (6, 7)], zero_D_rows=[12])),
+    ("one_stage", lambda: synth.make_problem(14, 1, 3, 2, 1, np.array([0, 1], np.int32))),
+    ("two_stage", lambda: synth.make_problem(15, 2, 3, 2, 1, np.array([1, 0, 2], np.int32))),
+]
+
+
+@pytest.mark.parametrize("name,make", CLASSES, ids=[c[0] for c in CLASSES])
+def test_classes(name, make):
+    pb = make()
+    (r,), (d,) = gpu_run([pb])
+    check(pb, r, d)
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 3, 5, 7, 16, 64])
+def test_chunk_lengths_and_ragged_tails(chunk):
+    pb = synth.config("degenerate_n12", N=61)
+    (r,), (d,) = gpu_run([pb], chunk=chunk)
+    check(pb, r, d)
+
+
+def test_single_n4_full():
+    pb = synth.config("single_n4")
+    (r,), (d,) = gpu_run([pb])
+    check(pb, r, d)
+
+
+def test_degenerate_n12_full():
+    pb = synth.config("degenerate_n12")
+    (r,), (d,) = gpu_run([pb])
+    check(pb, r, d)
+
+
+def test_table1_n1024():
+    pb = synth.config("table1", N=1024)
+    (r,), (d,) = gpu_run([pb])
+    check(pb, r, d)
+
+
+def test_long_n16_shrunk():
+    pb = synth.config("long_n16", N=4096)
+    (r,), (d,) = gpu_run([pb])
+    check(pb, r, d)
+
+
+def test_batched_uneven_subset():
+    pbs = [synth.config("batched_uneven", index=j, N=None) for j in range(24)]
+    res, dims = gpu_run(pbs)
+    for pb, r, d in zip(pbs, res, dims):
+        check(pb, r, d)
+
+
+def test_diff_batch_subset():
+    pbs = [synth.config("diff_batch", index=j) for j in range(8)]
+    res, dims = gpu_run(pbs)
+    for pb, r, d in zip(pbs, res, dims):
+        check(pb, r, d)
+
+
+def test_infeasible_suffix_status():
+    pb = synth.config("single_n4", N=16)
+    pb.q[-1] = 2
+    pb.E = np.array([[1.0, 0, 0, 0], [1.0, 0, 0, 0]])
+    pb.e = np.array([0.0, 1.0])
+    b = eclqr.Batch([pb])
+    b.build()
+    b.solve()
+    st = int(b.status.cpu()[0])
+    b.close()
+    assert eclqr.STATUS_NAMES[st] == "infeasible_suffix"
+
+
+def test_infeasible_initial_state_status():
+    pb = synth.config("table1", N=8)
+    pb.s0 = pb.s0 + 0.1
+    b = eclqr.Batch([pb])
+    b.build()
+    b.solve()
+    st = int(b.status.cpu()[0])
+    b.close()
+    assert eclqr.STATUS_NAMES[st] == "infeasible_x0"
