@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput benchmark: equality-constrained LQR stages solved per second.
+
+One step is one pass of the whole path of Algorithm 1 over one problem
+instance through the C ABI: eclqr_build (suffix-domain scan, stage
+elimination, Riccati factors), eclqr_solve (rollout with refinement and
+recovery of x, u), eclqr_multipliers (Sec. 7) and eclqr_kkt_residual (the
+Sec. 9 residual, the gate of the metric).  The workload is the degenerate
+n = 12 instance (N = 1024, m = 6, mixed rows U{0..8} per stage, 20% of stages
+with duplicated or D = 0 rows, full-rank terminal rows), seeded and synthetic.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun every rank solves its own copy (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.  ``--impl reference`` times the
+CPU oracle on the host instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ECLQR stages solved/s at KKT resid≤1e-9 (FP64), batched vs plain, % FP64 peak"
+WORKLOAD = "degenerate_n12"
+WORKLOAD_DESC = ("degenerate_n12: one instance, N=1024, n=12, m=6, mixed rows U{0..8} per stage, 20% of stages "
+                 "with duplicated or D=0 rows, full-rank terminal rows, A=I+0.1 randn, seed 0")
+KKT_GATE = 1e-9
+KERNELS = ["k_terminal", "k_primal_up", "k_rel_level", "k_primal_down", "k_param", "k_elim", "k_lqr_up",
+           "k_lqr_level", "k_riccati_down", "k_aff_up", "k_aff_level", "k_aff_down", "k_solve_init",
+           "k_post_roll", "k_resid", "k_scorr", "k_recover", "k_dual_stage", "k_dual_terminal", "k_dual_up",
+           "k_dual_down", "k_dual_root", "k_dual_leaf", "k_kkt_residual"]
+# phase of Algorithm 1 each kernel implements (index into the oracle's per-phase flop counts)
+KERNEL_PHASE = {"k_terminal": 0, "k_primal_up": 0, "k_rel_level": 0, "k_primal_down": 0, "k_param": 1,
+                "k_elim": 2, "k_lqr_up": 3, "k_lqr_level": 3, "k_riccati_down": 3, "k_aff_up": 4,
+                "k_aff_level": 4, "k_aff_down": 4, "k_solve_init": 4, "k_post_roll": 4, "k_resid": 4,
+                "k_scorr": 4, "k_recover": 4, "k_dual_stage": 5, "k_dual_terminal": 5, "k_dual_up": 5,
+                "k_dual_down": 5, "k_dual_root": 5, "k_dual_leaf": 5, "k_kkt_residual": 6}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(pb, seconds):
+    """The CPU oracle as it stands, one thread, repeated over the workload for ~seconds."""
+    import oracle
+    oracle.build_oracle()
+    oracle.solve(pb)  # warm
+    n, t0 = 0, time.perf_counter()
+    times = []
+    while True:
+        t = time.perf_counter()
+        s = oracle.solve(pb)
+        oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha)
+        times.append(time.perf_counter() - t)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    return pb.N / statistics.median(times), n, statistics.median(times)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2407_05433_gb300 import synth
+    import oracle
+    oracle.build_oracle()
+    pb = synth.config(WORKLOAD)
+    for _ in range(args.warmup):
+        oracle.solve(pb)
+    times, resid = [], None
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        s = oracle.solve(pb)
+        resid = oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * statistics.mean(times)
+    value = pb.N / (ms * 1e-3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "stages/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "stages": pb.N, "kkt_resid": resid, "status": s.status},
+            "cpu_baseline": {"value": value, "unit": "stages/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the full workload ({pb.N} stages) per step, one thread"},
+            "e2e": {"value": value, "unit": "stages/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    from paper_2407_05433_gb300 import eclqr, synth
+    from paper_2407_05433_gb300 import build as build_mod
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        build_mod.build()
+    if world > 1:
+        torch.distributed.barrier()
+    build_mod.build()
+    eclqr.load()
+
+    pb = synth.config(WORKLOAD)
+    batch = eclqr.Batch([pb], device=dev, refine=args.refine, chunk=args.chunk)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        batch.build()
+        batch.solve()
+        batch.multipliers()
+        batch.residual()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # which kernel dominates the step: bracket each kernel in turn over one untimed step
+    per_kernel = {}
+    for name in KERNELS:
+        eclqr.eclqr_time_kernel(batch.h, name)
+        step()
+        nl, tms = eclqr.eclqr_kernel_time(batch.h)
+        per_kernel[name] = (nl, tms)
+    eclqr.eclqr_time_kernel(batch.h, None)
+    dominant = max(per_kernel, key=lambda k: per_kernel[k][1])
+
+    # timed region: per-step events, L2 flushed between steps (outside the events)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    eclqr.eclqr_time_kernel(batch.h, dominant)
+    launches0 = batch.launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = batch.launches() - launches0
+    nl_dom, t_dom = eclqr.eclqr_kernel_time(batch.h)
+    eclqr.eclqr_time_kernel(batch.h, None)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    (res,) = batch.results()
+    ok = res["status"] == 0 and res["resid"] <= KKT_GATE
+
+    # end to end through the C ABI with host buffers: pinned H2D of the inputs,
+    # the four calls, D2H of every output, all inside the timed region
+    host_in = {k: torch.from_numpy(batch.host[k]).pin_memory() for k in eclqr.DATA_KEYS + ("s0",)}
+    outs = ("x", "u", "lam", "mu", "eta", "alpha", "resid", "status")
+    host_out = {k: torch.empty_like(getattr(batch, k), device="cpu").pin_memory() for k in outs}
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+    e2e_steps = max(5, args.steps // 4)
+
+    def e2e_step():
+        for k, t in host_in.items():
+            batch.d[k].copy_(t, non_blocking=True)
+        step()
+        for k in outs:
+            host_out[k].copy_(getattr(batch, k), non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for _ in range(e2e_steps):
+        flush.zero_()
+        ev0.record(stream)
+        e2e_step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms += ev0.elapsed_time(ev1)
+    e2e_ms /= e2e_steps
+    e2e_ok = int(host_out["status"][0]) == 0 and float(host_out["resid"][0]) <= KKT_GATE
+
+    if rank != 0:
+        batch.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    import oracle
+    oracle.build_oracle()
+    sref = oracle.solve(pb)
+    phase = sref.phase_flops
+    step_flops = float(np.sum(phase[:6]))
+    ms = total_ms / args.steps
+    value = world * pb.N / (ms * 1e-3)
+    peak = eclqr.eclqr_probe_fp64_peak()
+    dom_ms = t_dom / max(1, nl_dom)
+    launches_per_step_dom = nl_dom / args.steps
+    dom_flops = phase[KERNEL_PHASE[dominant]] / max(1.0, launches_per_step_dom)
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tinfo = json.load(open(tpath))
+            if tinfo.get("kernel") == dominant and tinfo.get("workload") == WORKLOAD:
+                traffic = tinfo.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    cpu = None
+    if args.cpu_seconds > 0:
+        rate, nrun, med = oracle_rate(pb, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "stages/s", "cores": 1, "kind": "oracle",
+               "sample": f"full workload ({pb.N} stages) solved {nrun} times in ~{args.cpu_seconds:.0f} s, "
+                         f"median {med * 1e3:.1f} ms per solve, one thread"}
+    line = {
+        "metric": METRIC, "value": value if ok else 0.0, "unit": "stages/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "stages_per_gpu": pb.N, "refine": args.refine,
+                   "chunk": args.chunk or "auto", "l2": "256 MB buffer written between timed steps",
+                   "kkt_resid": res["resid"], "status": res["status"], "gate_passed": ok,
+                   "step": "eclqr_build + eclqr_solve + eclqr_multipliers + eclqr_kkt_residual"},
+        "e2e": {"value": (world * pb.N / (e2e_ms * 1e-3)) if e2e_ok else 0.0, "unit": "stages/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "avg_launch_ms": dom_ms, "launches_per_step": launches_per_step_dom,
+                     "algorithmic_flops_per_launch": dom_flops,
+                     "peak_source": "FP64 FMA probe (eclqr_probe_fp64_peak) on this GPU",
+                     "step_achieved": step_flops / (ms * 1e-3) / 1e12,
+                     "step_frac": step_flops / (ms * 1e-3) / 1e12 / peak},
+        "kernel_ms_per_step": {k: round(v[1], 4) for k, v in per_kernel.items()},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--refine", type=int, default=4)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -81,6 +81,8 @@ typedef struct {
 #define ECLQR_MAX_N 32
 #define ECLQR_MAX_M 16
 #define ECLQR_MAX_ROWS 32
+/* Combinations whose largest kernel needs more than 227 KB of shared memory
+ * per warp are rejected by eclqr_create with ECLQR_EINVAL. */
 
 /* Problem data (device memory), layout in the header comment. */
 typedef struct {
@@ -93,7 +95,7 @@ typedef struct {
 typedef struct {
   double tau_rank;   /* relative rank cut after row scaling (Sec. 8 items 1-2); default 1e-10 */
   double tau_inc;    /* inconsistency cut on a scaled offset (Sec. 8 item 4); default 1e-8    */
-  int32_t refine;    /* refinement passes on the reduced LQR KKT residual; default 2          */
+  int32_t refine;    /* refinement passes on the reduced LQR KKT residual; default 4          */
   int32_t chunk;     /* stages per scan chunk; 0 = chosen from N and the SM count             */
 } eclqr_options;
 
@@ -145,9 +147,24 @@ int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const
  * build, into device int32 arrays. */
 int eclqr_reduced_dims(eclqr_handle *h, int32_t *nbar, int32_t *mbar, void *stream);
 
-/* Kernel launches issued by the last build/solve/multipliers/residual calls
- * of this handle (host counters, for launch accounting). */
+/* Kernel launches issued through this handle since eclqr_create (host counter,
+ * for launch accounting). */
 int64_t eclqr_launch_count(const eclqr_handle *h);
+
+/* Measurement hooks (not part of the method).
+ * eclqr_time_kernel: when name names one of the library's kernels (e.g.
+ * "k_primal_up"), every later launch of that kernel through this handle is
+ * bracketed by CUDA events recorded on the launching stream (at most 4096
+ * launches are kept); NULL switches it off.  Returns ECLQR_EINVAL for an
+ * unknown name.  eclqr_kernel_time reports the launches bracketed since the
+ * last eclqr_time_kernel call and their summed duration in milliseconds; it
+ * synchronises on the recorded events.
+ * eclqr_probe_fp64_peak measures the device's FP64 FMA throughput (TFLOP/s)
+ * with a kernel of independent FMA chains on every SM (the roofline
+ * denominator for this FP64 path); host-synchronous, allocates 8 MB. */
+int eclqr_time_kernel(eclqr_handle *h, const char *name);
+int eclqr_kernel_time(eclqr_handle *h, int64_t *launches, double *total_ms);
+int eclqr_probe_fp64_peak(double *tflops);
 
 void eclqr_destroy(eclqr_handle *h);
 const char *eclqr_strerror(int code);

@@ -59,6 +59,8 @@ def _bind(path):
         [ct.POINTER(ct.c_int), ct.POINTER(ct.c_double), ct.c_void_p]
     lib.orc_kkt_residual.restype = ct.c_double
     lib.orc_kkt_residual.argtypes = [ct.POINTER(_Problem)] + [ct.c_void_p] * 7
+    lib.orc_phase_flops.restype = None
+    lib.orc_phase_flops.argtypes = [ct.c_void_p]
     return lib
 
 
@@ -86,6 +88,8 @@ def _load():
             lib.orc_tqr_solve.restype = ct.c_int
             lib.orc_tqr_solve.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_double, ct.c_void_p,
                                           ct.c_int, ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_double)]
+            lib.orc_phase_flops.restype = None
+            lib.orc_phase_flops.argtypes = [ct.c_void_p]
             _lib = lib
     return _lib
 
@@ -121,6 +125,7 @@ class OracleSolution:
     alpha: np.ndarray
     flops: float
     debug: dict | None = None
+    phase_flops: np.ndarray | None = None
 
     @property
     def ok(self):
@@ -154,7 +159,10 @@ def solve(pb, tau_rank=1e-10, tau_inc=1e-8, multipliers=True, debug=False, refin
                        lam.ctypes.data if multipliers else None, _ptr(mu) or mu.ctypes.data,
                        _ptr(eta) or eta.ctypes.data, alpha.ctypes.data, ct.byref(fail), ct.byref(fl), dbgp)
     del keep
-    return OracleSolution(st, fail.value, x, u, lam, mu, eta, alpha, fl.value, dbg_arrays)
+    ph = np.zeros(8)
+    lib.orc_phase_flops(ph.ctypes.data)
+    sol = OracleSolution(st, fail.value, x, u, lam, mu, eta, alpha, fl.value, dbg_arrays, ph[:7].copy())
+    return sol
 
 
 def kkt_residual(pb, x, u, lam, mu, eta, alpha, parts=False, lib=None):

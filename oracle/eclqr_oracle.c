@@ -62,6 +62,12 @@
 #define ORC_BAD_INPUT 6
 
 static double g_flops = 0.0;
+/* flops per phase of Algorithm 1: 0 suffix domains, 1 parameterisation,
+   2 stage elimination, 3 Riccati factors, 4 linear passes/rollout/refinement/
+   recovery, 5 multipliers, 6 KKT residual */
+static double g_phase[8];
+static int g_cur = 0;
+#define ADDF(x) do { double _f = (x); g_flops += _f; g_phase[g_cur] += _f; } while (0)
 
 /* ------------------------------------------------------------------ */
 /* small dense helpers, row-major, explicit leading dimensions          */
@@ -81,7 +87,7 @@ static void gemm(int ta, int tb, int m, int n, int k, double alpha,
       }
       C[i * ldc + j] = alpha * s + (beta == 0.0 ? 0.0 : beta * C[i * ldc + j]);
     }
-  g_flops += 2.0 * m * n * k;
+  ADDF(2.0 * m * n * k);
 }
 
 static double *dalloc(size_t n) {
@@ -163,7 +169,7 @@ static void project(double *M, int r, int nc, int ngroups, const int *gsz,
         w *= beta;
         for (int i = k; i < r; i++) M[i * nc + j] -= w * v[i];
       }
-      g_flops += 4.0 * (r - k) * (nc - k);
+      ADDF(4.0 * (r - k) * (nc - k));
       M[k * nc + piv] = -sg * best;
       for (int i = k + 1; i < r; i++) M[i * nc + piv] = 0.0;
       done[piv] = 1;
@@ -260,7 +266,7 @@ static int tqr_solve(const double *K, int rk, int nk, double tau_rank,
       w *= beta;
       for (int l = s; l < nk; l++) Q[i * nk + l] -= w * v[l];
     }
-    g_flops += 4.0 * (nk - s) * (rk - s) + 4.0 * nk * (nk - s);
+    ADDF(4.0 * (nk - s) * (rk - s) + 4.0 * nk * (nk - s));
     rank++;
   }
   double rmax = 0.0;
@@ -282,7 +288,7 @@ static int tqr_solve(const double *K, int rk, int nk, double tau_rank,
         if (fabs(s) / bmax > rmax) rmax = fabs(s) / bmax;
       }
     }
-    g_flops += (double)nb * rank * rank + 2.0 * nb * rank * (rk - rank);
+    ADDF((double)nb * rank * rank + 2.0 * nb * rank * (rk - rank));
     /* X = -Q1 y */
     for (int i = 0; i < nk; i++)
       for (int c = 0; c < nb; c++) {
@@ -290,7 +296,7 @@ static int tqr_solve(const double *K, int rk, int nk, double tau_rank,
         for (int l = 0; l < rank; l++) s += Q[i * nk + l] * y[l * nb + c];
         X[i * nb + c] = -s;
       }
-    g_flops += 2.0 * nk * rank * nb;
+    ADDF(2.0 * nk * rank * nb);
     free(y);
   }
   if (resid) *resid = rmax;
@@ -314,7 +320,7 @@ static int cholesky(double *Hm, int n) {
     }
     for (int i = 0; i < j; i++) Hm[i * n + j] = 0.0;
   }
-  g_flops += (double)n * n * n / 3.0;
+  ADDF((double)n * n * n / 3.0);
   return 0;
 }
 
@@ -332,7 +338,7 @@ static void chol_solve(const double *L, int n, double *Bm, int nb) {
       Bm[i * nb + c] = s / L[i * n + i];
     }
   }
-  g_flops += 2.0 * n * n * nb;
+  ADDF(2.0 * n * n * nb);
 }
 
 /* ------------------------------------------------------------------ */
@@ -401,6 +407,8 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
   const double tr = opt->tau_rank, ti = opt->tau_inc;
   if (N < 1 || n < 1 || m < 1) return ORC_BAD_INPUT;
   g_flops = 0.0;
+  for (int k = 0; k < 8; k++) g_phase[k] = 0.0;
+  g_cur = 0;
   *fail_stage = -1;
   int status = ORC_OK;
 
@@ -478,7 +486,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
       for (int l = 0; l < n; l++) s += Hn[a * hld + l] * ci[l] * ((ORC_PLANT == 2) ? -1.0 : 1.0);
       Wm[a * cmax + m + n] = s;
     }
-    g_flops += 2.0 * rn * n * (m + n + 1);
+    ADDF(2.0 * rn * n * (m + n + 1));
     /* C x + D u + d = 0 */
     for (int a = 0; a < pi; a++) {
       int row = rn + a, src = po[i] + a;
@@ -510,6 +518,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
     if (worst > ti * om) { status = ORC_INFEASIBLE_X0; *fail_stage = 0; goto done; }
   }
   /* ---- 4. T_i, t_i (eqs. state-param, left-inverse; S_i = T_i^T) ---- */
+  g_cur = 1;
   {
     double *Kb = dalloc((size_t)n * n), *bb = dalloc(n), *Qf = dalloc((size_t)n * n), *tx = dalloc(n);
     for (int i = 0; i <= N; i++) {
@@ -531,6 +540,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
     free(Kb); free(bb); free(Qf); free(tx);
   }
   /* ---- 5-6. stage elimination (Sec. 5) ---- */
+  g_cur = 2;
   {
     int gr = pmax + n;
     double *Gm = dalloc((size_t)gr * (m ? m : 1));
@@ -562,7 +572,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int l = 0; l < n; l++) s += P->C[(size_t)src * n + l] * ti_[l];
         Rhs[a * (n + 1) + ni] = s;
       }
-      g_flops += 2.0 * pi * n * (ni + 1);
+      ADDF(2.0 * pi * n * (ni + 1));
       /* A T and A t + c */
       gemm(0, 0, n, ni, n, 1.0, Ai, n, Ti, n, 0.0, AT, n);
       for (int l = 0; l < n; l++) {
@@ -570,7 +580,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int j = 0; j < n; j++) s += Ai[l * n + j] * ti_[j];
         tmp[l] = s;
       }
-      g_flops += 2.0 * n * n;
+      ADDF(2.0 * n * n);
       for (int a = 0; a < rn; a++) {
         const double *hrow = Hn + a * hld;
         for (int j = 0; j < m; j++) {
@@ -587,7 +597,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int l = 0; l < n; l++) s += hrow[l] * tmp[l];
         Rhs[(pi + a) * (n + 1) + ni] = s;
       }
-      g_flops += 2.0 * rn * n * (m + ni + 1);
+      ADDF(2.0 * rn * n * (m + ni + 1));
       /* compact Rhs to ld = ni + 1 */
       double *Rc = dalloc((size_t)(rows ? rows : 1) * (ni + 1));
       for (int a = 0; a < rows; a++)
@@ -615,7 +625,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int j = 0; j < m; j++) s += Bi[l * m + j] * yi[j];
         tmp2[l] = s;
       }
-      g_flops += 2.0 * n * m;
+      ADDF(2.0 * n * m);
       gemm(1, 0, nn, 1, n, 1.0, Tn, n, tmp2, 1, 0.0, cbi, 1);
       /* state substitution (eq. state-cost-data) */
       const double *Qi = P->Q + (size_t)i * n * n, *Mi = P->M + (size_t)i * n * m;
@@ -629,14 +639,14 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int j = 0; j < n; j++) s += Qi[l * n + j] * ti_[j];
         tmp2[l] = s;                                                    /* Q t + q */
       }
-      g_flops += 2.0 * n * n;
+      ADDF(2.0 * n * n);
       gemm(1, 0, ni, 1, n, 1.0, Ti, n, tmp2, 1, 0.0, qz, 1);            /* q^z */
       for (int j = 0; j < m; j++) {
         double s = ri[j];
         for (int l = 0; l < n; l++) s += Mi[l * m + j] * ti_[l];
         rz[j] = s;                                                      /* r^z = M^T t + r */
       }
-      g_flops += 2.0 * n * m;
+      ADDF(2.0 * n * m);
       /* reduced cost (eq. reduced-cost-data) */
       gemm(0, 0, m, ni, m, 1.0, Ri, m, Yi, n, 0.0, RY, n);             /* R Y */
       gemm(0, 0, m, mi, m, 1.0, Ri, m, Zi, m, 0.0, RZ, m);             /* R Z */
@@ -645,7 +655,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int j = 0; j < m; j++) s += Ri[a * m + j] * yi[j];
         Ry[a] = s;                                                      /* R y + r^z */
       }
-      g_flops += 2.0 * m * m;
+      ADDF(2.0 * m * m);
       /* Qbar = Q^z + M^z Y + Y^T M^z^T + Y^T R Y */
       gemm(0, 0, ni, ni, m, 1.0, Mz, m, Yi, n, 1.0, Qbi, n);
       gemm(1, 1, ni, ni, m, 1.0, Yi, n, Mz, m, 1.0, Qbi, n);
@@ -667,7 +677,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int j = 0; j < m; j++) s += Zi[j * m + a] * Ry[j];
         rbi[a] = s;
       }
-      g_flops += 4.0 * ni * m + 2.0 * mi * m;
+      ADDF(4.0 * ni * m + 2.0 * mi * m);
       /* kappa_i (eq. stage-constant) */
       {
         double s = 0.0;
@@ -706,6 +716,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
     free(Gm); free(Rhs); free(Sol); free(Qf); free(AT); free(tmp); free(tmp2);
     free(rz); free(qz); free(Mz); free(RY); free(RZ); free(Ry); free(BZ);
   }
+  g_cur = 3;
   /* ---- 7. square-root (information form) Riccati on the reduced LQR ----
    * The paper leaves the unconstrained LQR solver open (Sec. 6).  The textbook
    * recursion P_i = Qbar + Abar'P Abar - H_ux' H_uu^{-1} H_ux cancels large
@@ -784,7 +795,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int l = 0; l < nn; l++) s += Rn[a * n + l] * cbi[l];
         St[row * ld + k] = s;
       }
-      g_flops += 2.0 * nn * nn * (mi + ni + 1) + (double)k * k * k / 3.0;
+      ADDF(2.0 * nn * nn * (mi + ni + 1) + (double)k * k * k / 3.0);
       /* Householder QR over the first k columns, no pivoting */
       for (int c = 0; c < k; c++) {
         double nrm = 0.0;
@@ -803,7 +814,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         }
         St[c * ld + c] = -sg * nrm;
         for (int r = c + 1; r < rows; r++) St[r * ld + c] = 0.0;
-        g_flops += 4.0 * (rows - c) * (ld - c);
+        ADDF(4.0 * (rows - c) * (ld - c));
       }
       /* K, k: R_vv v = -(R_vz z + o_v) */
       double *Ki = Kg + (size_t)i * m * n, *ki = kg + (size_t)i * m;
@@ -843,11 +854,12 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int l = 0; l < ni; l++) s += Rn[l * n + a] * sn[l];
         pst[(size_t)i * n + a] = s;                         /* p_i = R_i' s_i */
       }
-      g_flops += 2.0 * ni * ni * ni + 2.0 * mi * mi * ni;
+      ADDF(2.0 * ni * ni * ni + 2.0 * mi * mi * ni);
     }
     free(Rn); free(sn); free(St); free(Hs); free(lv); free(vv2);
     if (status != ORC_OK) goto done;
   }
+  g_cur = 4;
   /* ---- 8. linear pass, rollout (eq. reduced-initial) and refinement on the reduced KKT ----
    * lqr_offsets(qb', rb', cb', z0') -> (z, v, pi) solves the reduced LQR with the factors above.
    * Refinement: the residual of the reduced KKT system (reduced dynamics, stationarity in z and
@@ -899,7 +911,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
           pv[a] = s;
         }
         memcpy(pst + (size_t)i * n, pv, sizeof(double) * n);
-        g_flops += 2.0 * nn * nn + 2.0 * mi * nn + 2.0 * ni * (nn + mi);
+        ADDF(2.0 * nn * nn + 2.0 * mi * nn + 2.0 * ni * (nn + mi));
       }
       }
       /* rollout v = K z + k, z+ = Abar z + Bbar v + cbar; costates pi = P z + p */
@@ -918,7 +930,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
           for (int j = 0; j < mi; j++) s += Bb[(size_t)i * n * m + a * m + j] * vi[j];
           zn[a] = s;
         }
-        g_flops += 2.0 * mi * ni + 2.0 * nn * (ni + mi);
+        ADDF(2.0 * mi * ni + 2.0 * nn * (ni + mi));
       }
       for (int i = 0; i <= N; i++)
         for (int a = 0; a < nb[i]; a++) {
@@ -962,7 +974,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
           }
         }
       }
-      g_flops += 2.0 * N * (double)(n * n + n * m) * 3.0;
+      ADDF(2.0 * N * (double)(n * n + n * m) * 3.0);
     }
     free(qo_); free(ro_); free(co_); free(dz); free(dv); free(dpi); free(pv); free(w); free(hu); free(z0);
   }
@@ -975,7 +987,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int j = 0; j < ni; j++) s += T[(size_t)i * n * n + a * n + j] * zz[(size_t)i * n + j];
         x[(size_t)i * n + a] = s;
       }
-      g_flops += 2.0 * n * ni;
+      ADDF(2.0 * n * ni);
     }
     for (int i = 0; i < N; i++) {
       int ni = nb[i], mi = mb[i];
@@ -985,9 +997,10 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int j = 0; j < mi; j++) s += Z[(size_t)i * m * m + a * m + j] * vv[(size_t)i * m + j];
         u[(size_t)i * m + a] = s;
       }
-      g_flops += 2.0 * m * (ni + mi);
+      ADDF(2.0 * m * (ni + mi));
     }
   }
+  g_cur = 5;
   /* ---- 9. multipliers (Sec. 7), in the normal coordinates of the domains ----
    * For any KKT multiplier, the chain rule through x = T z + t, u = Y z + Z v + y
    * turns the original Lagrangian into the reduced one with costates
@@ -1031,7 +1044,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int j = 0; j < m; j++) s += P->R[(size_t)i * m * m + a * m + j] * u[(size_t)i * m + j];
         gu[(size_t)i * m + a] = s;
       }
-    g_flops += 2.0 * (N + 1) * n * (n + m) + 2.0 * N * m * (n + m);
+    ADDF(2.0 * (N + 1) * n * (n + m) + 2.0 * N * m * (n + m));
     /* reduced costates pi_i: refined above */
     /* rho^x_i = g^x_i + A_i^T T_{i+1} pi_{i+1}, rho^u_i = g^u_i + B_i^T T_{i+1} pi_{i+1} */
     {
@@ -1055,7 +1068,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
           ru[(size_t)i * m + a] = s;
         }
       }
-      g_flops += (double)N * (2.0 * n * n + 2.0 * n * (n + m));
+      ADDF((double)N * (2.0 * n * n + 2.0 * n * (n + m)));
       free(tp);
     }
     int wr = n + m + n;
@@ -1102,7 +1115,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (int l = 0; l < n; l++) s += UX(i, l, a) * rx[(size_t)(i) * n + l];      \
         Ux_[a] = s;                                                                  \
       }                                                                              \
-      g_flops += 2.0 * r0 * r1 * n * (n + 1) + 2.0 * m * r1 * n + 2.0 * r0 * n * (pi + qi + 1); \
+      ADDF(2.0 * r0 * r1 * n * (n + 1) + 2.0 * m * r1 * n + 2.0 * r0 * n * (pi + qi + 1)); \
     } while (0)
     /* terminal relation (N): project eta_N */
     {
@@ -1230,7 +1243,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
             for (int b = 0; b < r1; b++) s += BU[a * n + b] * nu1[b];
             rhs[r0 + a] = s;
           }
-          g_flops += 2.0 * (r0 + m) * r1;
+          ADDF(2.0 * (r0 + m) * r1);
           tqr_solve(Fl, r0 + m, nw, tr, rhs, 1, wsol, NULL, &rs);
           for (int j = 0; j < pi; j++) mu[po[i] + j] = wsol[j];
           for (int j = 0; j < qi; j++) eta[qo[i] + j] = wsol[pi + j];
@@ -1264,7 +1277,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
           for (int a = 0; a < ur[i]; a++) s += UX(i, l, a) * nus[(size_t)i * n + a];
           lam[(size_t)i * n + l] = s;
         }
-      g_flops += 2.0 * (N + 1) * n * n;
+      ADDF(2.0 * (N + 1) * n * n);
       for (int l = 0; l < n; l++) alpha[l] = -lam[l];
     }
 #undef STAGE_BLOCKS
@@ -1388,6 +1401,11 @@ double orc_kkt_residual(const orc_problem *P, const double *x, const double *u,
 
 /* exported helpers so tests can exercise Lemma 1 and the null-space solve
    on their own, against independent numpy computations */
+/* flops of the last orc_solve per phase (see g_phase) */
+void orc_phase_flops(double *out) {
+  for (int k = 0; k < 8; k++) out[k] = g_phase[k];
+}
+
 int orc_project(double *M, int r, int nc, int ngroups, const int *gsz, int nkeep,
                 double tau_rank, double tau_inc, int *grank, int *krank, double *out) {
   int inc = 0;

@@ -45,6 +45,10 @@ struct eclqr_handle {
   long long launches = 0;
   bool built = false, solved = false;
   int device = 0;
+  // optional event bracket around one kernel (measurement hook)
+  const void *timed = nullptr;
+  std::vector<cudaEvent_t> ev;
+  int nev = 0;
 };
 
 namespace {
@@ -64,7 +68,13 @@ int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_warp, cu
       return ECLQR_ECUDA;
   }
   const int grid = (ntasks + W - 1) / W;
+  const bool timed = h->timed == (const void *)kern && h->nev + 2 <= (int)h->ev.size();
+  if (timed) cudaEventRecord(h->ev[h->nev], st);
   kern<<<grid, 32 * W, smem, st>>>(args...);
+  if (timed) {
+    cudaEventRecord(h->ev[h->nev + 1], st);
+    h->nev += 2;
+  }
   h->launches++;
   return cudaPeekAtLastError() == cudaSuccess ? ECLQR_OK : ECLQR_ECUDA;
 }
@@ -93,13 +103,56 @@ int validate(const eclqr_desc *d) {
 
 }  // namespace
 
+namespace {
+// eight independent FMA chains per thread: throughput, not latency, bound
+__global__ void k_fp64_probe(double *out, int iters, double a, double b) {
+  double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; i++) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+}  // namespace
+
 extern "C" {
+
+int eclqr_probe_fp64_peak(double *tflops) {
+  if (!tflops) return ECLQR_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ECLQR_ECUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  double *buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * (size_t)blocks * threads) != cudaSuccess) return ECLQR_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fp64_probe<<<blocks, threads>>>(buf, 64, 1.0000001, 1e-9);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; rep++) {
+    cudaEventRecord(e0);
+    k_fp64_probe<<<blocks, threads>>>(buf, iters, 1.0000001, 1e-9);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  const cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (err != cudaSuccess) return ECLQR_ECUDA;
+  *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+  return ECLQR_OK;
+}
 
 void eclqr_default_options(eclqr_options *opt) {
   if (!opt) return;
   opt->tau_rank = 1e-10;
   opt->tau_inc = 1e-8;
-  opt->refine = 2;
+  opt->refine = 4;
   opt->chunk = 0;
 }
 
@@ -166,6 +219,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       pi.oA = oA; pi.oB = oB; pi.oc = oc; pi.oC = oC; pi.oD = oD; pi.od = od; pi.oE = oE; pi.oe = oe;
       pi.oQ = oQ; pi.oM = oM; pi.oR = oR; pi.oqv = oqv; pi.orv = orv;
       pi.os0 = os0; pi.ox = ox; pi.ou = ou; pi.olam = olam; pi.omu = omu; pi.oeta = oeta; pi.oalpha = oal;
+      pi.ost = qstage[j];
       oA += N * n * n; oB += N * n * m; oc += N * n; oC += Pj * n; oD += Pj * m; od += Pj; oE += Qj * n; oe += Qj;
       oQ += (N + 1) * n * n; oM += N * n * m; oR += N * m * m; oqv += (N + 1) * n; orv += N * m;
       os0 += n; ox += (N + 1) * n; ou += N * m; olam += (N + 1) * n; omu += Pj; oeta += Qj; oal += n;
@@ -196,10 +250,11 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       ProbInfo pi = pinfo[j];
       int L = h->opt.chunk;
       if (L <= 0) {
-        // enough chunks to give every SM sub-partition work, short chunks for short horizons
-        long long target = std::max<long long>(1, total_stages / (4LL * sms));
-        L = (int)std::min<long long>(64, std::max<long long>(4, target));
-        if (pi.N < 4 * L) L = std::max(2, pi.N / 8);
+        // enough chunks to give every SM work, but never shorter than 8 stages:
+        // chunk boundaries right after ill-conditioned stages cost accuracy in the
+        // composed dual relations, and short chunks place more boundaries
+        long long target = std::max<long long>(1, total_stages / (2LL * sms));
+        L = (int)std::min<long long>(64, std::max<long long>(8, target));
         L = std::max(1, std::min(L, pi.N));
       }
       pi.L = L;
@@ -266,7 +321,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     const int n = g.n, m = g.m;
     const int need = std::max({smem_primal_sweep(n, m, pmax, qmax), smem_rel_level(n, pmax, qmax), smem_param(n),
                                smem_elim(n, m, pmax), smem_lqr_up(n, m), smem_lqr_level(n), smem_riccati(n, m),
-                               smem_aff(n), smem_dual_stage(n, m), smem_dual_sweep(n, m, pmax, qmax),
+                               smem_aff(n, m), smem_dual_stage(n, m), smem_dual_sweep(n, m, pmax, qmax),
                                smem_dual_leaf(n, m, pmax, qmax)});
     if ((size_t)need * sizeof(double) > (size_t)kMaxSmemBytes) {
       cudaFree(gh.dmem);
@@ -319,8 +374,8 @@ int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *
 namespace {
 int aff_scan(eclqr_handle *h, GroupHost &gh, int mode, cudaStream_t st) {
   Group &g = gh.g;
-  const int sa = smem_aff(g.n);
-  const int fwd = (mode == AFF_CLIN_) ? 0 : 1;
+  const int sa = smem_aff(g.n, g.m);
+  const int fwd = (mode == AFF_SLIN_) ? 0 : 1;
   TRY(launch(h, k_aff_up, g.nslot, sa, st, g, mode, sa));
   int src = 0;
   for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_aff_level, g.nslot, sa, st, g, src, 1 << k, fwd, sa));
@@ -341,8 +396,9 @@ int eclqr_solve(eclqr_handle *h, const double *s0, double *x, double *u, int32_t
     TRY(launch(h, k_post_roll, g.nstage, 0, st, g, 0));
     for (int r = 0; r < h->opt.refine; r++) {
       TRY(launch(h, k_resid, g.nstage, 0, st, g));
-      TRY(aff_scan(h, gh, AFF_CLIN_, st));
-      TRY(launch(h, k_kcorr, g.nstage, 0, st, g));
+      TRY(aff_scan(h, gh, AFF_SLIN_, st));
+      const int sc = 3 * (g.n + g.m) + 8;
+      TRY(launch(h, k_scorr, g.nstage, sc, st, g, sc));
       TRY(aff_scan(h, gh, AFF_CROLL_, st));
       TRY(launch(h, k_post_roll, g.nstage, 0, st, g, 1));
     }
@@ -410,7 +466,55 @@ int64_t eclqr_launch_count(const eclqr_handle *h) { return h ? h->launches : 0; 
 void eclqr_destroy(eclqr_handle *h) {
   if (!h) return;
   for (auto &gh : h->groups) cudaFree(gh.dmem);
+  for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
+}
+
+int eclqr_time_kernel(eclqr_handle *h, const char *name) {
+  if (!h) return ECLQR_EINVAL;
+  h->nev = 0;
+  if (!name) {
+    h->timed = nullptr;
+    return ECLQR_OK;
+  }
+  static const struct { const char *name; const void *fn; } table[] = {
+      {"k_terminal", (const void *)k_terminal}, {"k_primal_up", (const void *)k_primal_up},
+      {"k_rel_level", (const void *)k_rel_level}, {"k_primal_down", (const void *)k_primal_down},
+      {"k_param", (const void *)k_param}, {"k_elim", (const void *)k_elim},
+      {"k_lqr_up", (const void *)k_lqr_up}, {"k_lqr_level", (const void *)k_lqr_level},
+      {"k_riccati_down", (const void *)k_riccati_down}, {"k_aff_up", (const void *)k_aff_up},
+      {"k_aff_level", (const void *)k_aff_level}, {"k_aff_down", (const void *)k_aff_down},
+      {"k_solve_init", (const void *)k_solve_init}, {"k_post_roll", (const void *)k_post_roll},
+      {"k_resid", (const void *)k_resid}, {"k_scorr", (const void *)k_scorr},
+      {"k_recover", (const void *)k_recover}, {"k_dual_stage", (const void *)k_dual_stage},
+      {"k_dual_terminal", (const void *)k_dual_terminal}, {"k_dual_up", (const void *)k_dual_up},
+      {"k_dual_down", (const void *)k_dual_down}, {"k_dual_root", (const void *)k_dual_root},
+      {"k_dual_leaf", (const void *)k_dual_leaf}, {"k_kkt_residual", (const void *)k_kkt_residual}};
+  for (const auto &e : table)
+    if (std::strcmp(e.name, name) == 0) {
+      if (h->ev.empty()) {
+        h->ev.resize(2 * 4096);
+        for (auto &x : h->ev)
+          if (cudaEventCreate(&x) != cudaSuccess) return ECLQR_ECUDA;
+      }
+      h->timed = e.fn;
+      return ECLQR_OK;
+    }
+  return ECLQR_EINVAL;
+}
+
+int eclqr_kernel_time(eclqr_handle *h, int64_t *launches, double *total_ms) {
+  if (!h || !launches || !total_ms) return ECLQR_EINVAL;
+  double t = 0.0;
+  for (int k = 0; k + 1 < h->nev; k += 2) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(h->ev[k + 1]) != cudaSuccess) return ECLQR_ECUDA;
+    if (cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]) != cudaSuccess) return ECLQR_ECUDA;
+    t += ms;
+  }
+  *launches = h->nev / 2;
+  *total_ms = t;
+  return ECLQR_OK;
 }
 
 const char *eclqr_strerror(int code) {

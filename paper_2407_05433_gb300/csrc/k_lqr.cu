@@ -31,10 +31,10 @@ __host__ int smem_lqr_level(int n) {
   return rows * ldm + 2 * rows + 2 * (ldm + rows) + n + 16;
 }
 __host__ int smem_riccati(int n, int m) {
-  const int rows = 2 * n + m, ld = n + m + 1;
-  return n * (n + 1) + rows * ld + rows + ld + 4 * n * n + 2 * m * n + 8;
+  const int rows = 2 * n + m, ld = n + m + 1 + rows;
+  return n * (n + 1) + rows * ld + rows + ld + 2 * m * (n + 1) + 8;
 }
-__host__ int smem_aff(int n) { return 2 * (n * n + n) + n * n + 2 * n + 8; }
+__host__ int smem_aff(int n, int m) { return 2 * (n * n + n) + n * n + 5 * n + 2 * m + 8; }
 
 // Cost-relation slot layout (ld 2n + 1): constraint rows at 0 (CI_ROWS of them),
 // cost rows at offset 2n (2n + 1) (CI_ROWS2 of them); CI_NA / CI_NB are the
@@ -205,10 +205,13 @@ __global__ void k_lqr_level(Group g, int src, int d, int per_warp) {
 // ----------------------------------------------------------- chunk down-sweep: square-root Riccati
 // From V_b = 1/2 ||C z_b + c||^2 (the scan's value at the chunk end), each stage
 // stacks [L'_v | L'_z | l] and [C Bbar | C Abar | C cbar + c] over (v | z | 1) and
-// triangularises them by Householder QR: R_vv v + R_vz z + o_v = 0 at the
-// minimiser (K, k) and V_i = 1/2 ||R_zz z + o_z||^2.  P_i = R_zz'R_zz, p_i = R_zz'o_z,
-// H_uu = R_vv'R_vv, H_ux = R_vv'R_vz and Phi_i = Abar + Bbar K are stored for the
-// linear passes.
+// triangularises them by Householder QR, carrying an identity block so that
+// Q' is formed too: R_vv v + R_vz z + o_v = 0 at the minimiser (K, k) and
+// V_i = 1/2 ||R_i z + s_i||^2 with R_i upper triangular, rows signed so that
+// its diagonal is positive (the unique such square root of P_i, so chunks
+// meeting at a boundary use the same frame).  Stored per stage: P_i = R_i'R_i,
+// p_i = R_i's_i, K, k, H_uu (Cholesky factor), H_ux = R_vv'R_vz, Phi = Abar + Bbar K,
+// and for the refinement passes R_i, R_vv and the top rows of Q'.
 __global__ void k_riccati_down(Group g, int fin, int per_warp) {
   const int t = warp_task();
   if (t >= g.nslot) return;
@@ -217,12 +220,12 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, lane = lane_id();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
-  const int ldr = 2 * n + 1;
+  const int ldr = 2 * n + 1, ldq = 2 * n + m;
   double *sm = warp_smem(per_warp);
-  const int rows_max = 2 * n + m, ldst = n + m + 1;
+  const int rows_max = 2 * n + m, ldst = n + m + 1 + rows_max;
   double *V = sm, *St = V + n * (n + 1), *v = St + rows_max * ldst, *w = v + rows_max;
   double *Kt = w + ldst;  // m x (n + 1)
-  // V_b
+  // V_b, rows signed to a positive diagonal
   int rv;
   {
     const double *src = crel_cost(g.CS[fin] + (size_t)(t + 1) * g.cs_stride, n);
@@ -231,10 +234,11 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
     rv = I[CI_ROWS2];
     for (int idx = lane; idx < rv * (nbz + 1); idx += 32) {
       int r = idx / (nbz + 1), j = idx - r * (nbz + 1);
-      V[r * (n + 1) + j] = src[r * ldr + j];
+      const double sg = (src[r * ldr + r] >= 0.0) ? 1.0 : -1.0;
+      V[r * (n + 1) + j] = sg * src[r * ldr + j];
     }
     __syncwarp();
-    if (b == P.N) {  // P_N = C'C, p_N = C'c
+    if (b == P.N) {  // P_N = C'C, p_N = C'c, value factor for the refinement
       double *wsN = stage_ws(g, P.st0 + b);
       for (int idx = lane; idx < nbz * (nbz + 1); idx += 32) {
         int r = idx / (nbz + 1), j = idx - r * (nbz + 1);
@@ -242,19 +246,25 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
         for (int l = 0; l < rv; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + j], s0);
         if (j < nbz) wsN[g.ws.P + r * n + j] = s0; else wsN[g.ws.p + r] = s0;
       }
+      for (int idx = lane; idx < rv * nbz; idx += 32) {
+        int r = idx / nbz, j = idx - r * nbz;
+        wsN[g.ws.RV + r * n + j] = V[r * (n + 1) + j];
+      }
     }
   }
   for (int i = b - 1; i >= a; --i) {
     const int s = P.st0 + i;
     double *ws = stage_ws(g, s);
-    const int *wi = stage_wi(g, s);
+    int *wi = stage_wi(g, s);
     const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
-    const int kh = nx + mu, rows = kh + rv, ld = kh + 1;
+    const int kh = nx + mu, rows = kh + rv, ld = kh + 1 + rows;
     const double *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb, *cb = ws + g.ws.cb, *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
     for (int idx = lane; idx < rows * ld; idx += 32) {
       int r = idx / ld, j = idx - r * ld;
       double val = 0.0;
-      if (r < kh) {
+      if (j > kh) {
+        val = (j - kh - 1 == r) ? 1.0 : 0.0;  // identity block: becomes Q'
+      } else if (r < kh) {
         if (j < mu) val = LT[r * (n + m) + nx + j];
         else if (j < kh) val = LT[r * (n + m) + (j - mu)];
         else val = lt[r];
@@ -272,7 +282,6 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
       St[idx] = val;
     }
     __syncwarp();
-    // Householder QR over the first kh columns, in order
     for (int col = 0; col < kh && col < rows; col++) {
       double s0 = 0.0;
       for (int r = col + lane; r < rows; r += 32) s0 = fma(St[r * ld + col], St[r * ld + col], s0);
@@ -280,7 +289,15 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
       if (s0 == 0.0) continue;
       whouse_apply(St, ld, col, rows, col, col + 1, ld, nullptr, v, w, s0);
     }
-    // K, k:  R_vv [K | k] = -[R_vz | o_v]  (lanes over the nx + 1 columns)
+    // sign the z rows to a positive diagonal (rows mu .. kh - 1, all columns)
+    for (int idx = lane; idx < nx * ld; idx += 32) {
+      int r = mu + idx / ld, j = idx % ld;
+      if (St[r * ld + r] < 0.0 && j != r) St[r * ld + j] = -St[r * ld + j];
+    }
+    __syncwarp();
+    for (int r = mu + lane; r < kh; r += 32) St[r * ld + r] = fabs(St[r * ld + r]);
+    __syncwarp();
+    // K, k:  R_vv [K | k] = -[R_vz | o_v]
     for (int c = lane; c <= nx; c += 32) {
       for (int r = mu - 1; r >= 0; r--) {
         double s0 = -St[r * ld + mu + c];
@@ -289,15 +306,15 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
       }
     }
     __syncwarp();
-    // stores: K, k, Lh (lower Cholesky factor of H_uu with positive diagonal), Hx, P, p, Phi
     for (int idx = lane; idx < mu * (nx + 1); idx += 32) {
       int r = idx / (nx + 1), c = idx - r * (nx + 1);
       if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
     }
     for (int idx = lane; idx < mu * mu; idx += 32) {
-      int r = idx / mu, j = idx - r * mu;  // Lh[r][j] = sign_j * R_vv[j][r] for j <= r
+      int r = idx / mu, j = idx - r * mu;
       double sg = St[j * ld + j] >= 0.0 ? 1.0 : -1.0;
       ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * St[j * ld + r] : 0.0;
+      ws[g.ws.RVV + r * m + j] = (j >= r) ? St[r * ld + j] : 0.0;
     }
     for (int idx = lane; idx < mu * nx; idx += 32) {
       int r = idx / nx, c = idx - r * nx;
@@ -311,7 +328,13 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
       for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
       ws[g.ws.Phi + r * n + c] = s0;
     }
-    // new value rows [R_zz | o_z]
+    // top kh rows of Q' (columns: kh stage-cost offsets, then rv value offsets)
+    for (int idx = lane; idx < kh * rows; idx += 32) {
+      int r = idx / rows, c = idx - r * rows;
+      ws[g.ws.Qs + r * ldq + c] = St[r * ld + kh + 1 + c];
+    }
+    if (lane == 0) wi[SI_RV] = rv;
+    // new value rows [R_i | s_i]
     __syncwarp();
     for (int idx = lane; idx < nx * (nx + 1); idx += 32) {
       int r = idx / (nx + 1), c = idx - r * (nx + 1);
@@ -324,25 +347,50 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
       double s0 = 0.0;
       for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
       if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
+      if (c < nx) ws[g.ws.RV + r * n + c] = V[r * (n + 1) + c];
     }
     __syncwarp();
   }
+}
+
+// Offsets of the refinement's square-root linear pass at stage s:
+// lq = L^{-1} [rq; rr] (stage cost rows) and u = R_{i+1} rc (value rows).
+__device__ void slin_offsets(const Group &g, int s, double *lq, double *u) {
+  const int n = g.n, m = g.m, lane = lane_id();
+  const double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);
+  const int *wi = stage_wi(g, s);
+  const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], kh = nx + mu, rv = wi[SI_RV];
+  const double *LT = ws + g.ws.LT;
+  if (lane == 0) {
+    for (int a = 0; a < kh; a++) {
+      double s0 = (a < nx) ? ws[g.ws.rq + a] : ws[g.ws.rr + (a - nx)];
+      for (int l = 0; l < a; l++) s0 = fma(-LT[l * (n + m) + a], lq[l], s0);
+      lq[a] = s0 / LT[a * (n + m) + a];
+    }
+  }
+  for (int r = lane; r < rv; r += 32) {
+    double s0 = 0.0;
+    for (int l = r; l < rv; l++) s0 = fma(wn[g.ws.RV + r * n + l], ws[g.ws.rc + l], s0);
+    u[r] = s0;
+  }
+  __syncwarp();
 }
 
 // ----------------------------------------------------------- affine chain scans
 // Per-stage maps by mode (d_i = dimension of the chained vector at stage i):
 //   AFF_ROLL  forward  z_{i+1} = Phi_i z_i + Bbar k_i + cbar_i        -> z
 //   AFF_CROLL forward  dz_{i+1} = Phi_i dz_i + Bbar k'_i + rc_i       -> dz (k' held in dv)
-//   AFF_CLIN  backward p'_i = Phi_i'(P_{i+1} rc_i + p'_{i+1}) + rq_i + K_i' rr_i -> pp
+//   AFF_SLIN  backward s'_i = G_i s'_{i+1} + g_i, the refinement's linear pass in square-root form:
+//             G_i = rows of Q' (norm <= 1), g_i from L^{-1}[rq; rr] and R_{i+1} rc     -> sp
 //   AFF_NU    forward  nu_{i+1} = Pnu_i nu_i + pnu_i                  -> nu
-enum { AFF_ROLL = 0, AFF_CROLL = 1, AFF_CLIN = 2, AFF_NU = 3 };
+enum { AFF_ROLL = 0, AFF_CROLL = 1, AFF_SLIN = 2, AFF_NU = 3 };
 
 __device__ __forceinline__ int aff_dim(const Group &g, int s, int mode) {
   return (mode == AFF_NU) ? stage_wi(g, s)[SI_UR] : stage_wi(g, s)[SI_NBAR];
 }
-__device__ __forceinline__ bool aff_forward(int mode) { return mode != AFF_CLIN; }
+__device__ __forceinline__ bool aff_forward(int mode) { return mode != AFF_SLIN; }
 __device__ __forceinline__ int aff_out(const Group &g, int mode) {
-  return mode == AFF_ROLL ? g.ws.z : mode == AFF_CROLL ? g.ws.dz : mode == AFF_CLIN ? g.ws.pp : g.ws.nu;
+  return mode == AFF_ROLL ? g.ws.z : mode == AFF_CROLL ? g.ws.dz : mode == AFF_SLIN ? g.ws.sp : g.ws.nu;
 }
 
 // map of stage i: y_out = G y_in + gv.  Forward: in = stage i, out = stage i+1;
@@ -378,25 +426,23 @@ __device__ void aff_stage_map(const Group &g, int s, int mode, double *G, double
     __syncwarp();
     return;
   }
-  // AFF_CLIN: G = Phi' (nx x ny), gv = Phi' P_{i+1} rc + rq + K' rr
-  const double *Pn = wn + g.ws.P, *rc = ws + g.ws.rc, *rq = ws + g.ws.rq, *rr = ws + g.ws.rr, *K = ws + g.ws.K;
-  for (int idx = lane; idx < nx * ny; idx += 32) {
-    int i = idx / ny, j = idx - i * ny;
-    G[i * n + j] = Phi[j * n + i];
+  // AFF_SLIN: G = rows mu.. of Q' on the value offsets (nx x rv), gv = Q'[z rows] [L^{-1}[rq; rr]; R_{i+1} rc]
+  const int kh = nx + mu, rv = wi[SI_RV], ldq = 2 * n + m;
+  const double *Qs = ws + g.ws.Qs;
+  double *lq = tmp, *u = tmp + (n + m);
+  slin_offsets(g, s, lq, u);
+  for (int idx = lane; idx < nx * rv; idx += 32) {
+    int i = idx / rv, j = idx - i * rv;
+    G[i * n + j] = Qs[(mu + i) * ldq + kh + j];
   }
-  for (int i = lane; i < ny; i += 32) {
-    double s0 = 0.0;
-    for (int l = 0; l < ny; l++) s0 = fma(Pn[i * n + l], rc[l], s0);
-    tmp[i] = s0;
-  }
-  __syncwarp();
   for (int i = lane; i < nx; i += 32) {
-    double s0 = rq[i];
-    for (int l = 0; l < ny; l++) s0 = fma(Phi[l * n + i], tmp[l], s0);
-    for (int l = 0; l < mu; l++) s0 = fma(K[l * n + i], rr[l], s0);
+    double s0 = 0.0;
+    for (int l = 0; l < kh; l++) s0 = fma(Qs[(mu + i) * ldq + l], lq[l], s0);
+    for (int l = 0; l < rv; l++) s0 = fma(Qs[(mu + i) * ldq + kh + l], u[l], s0);
     gv[i] = s0;
   }
   __syncwarp();
+  (void)ny;
 }
 
 // chunk aggregates; also the boundary value slot (forward: slot 0 of the
@@ -420,9 +466,16 @@ __global__ void k_aff_up(Group g, int mode, int per_warp) {
       double v;
       if (mode == AFF_ROLL) v = src[g.ws.z + i];
       else if (mode == AFF_CROLL) v = 0.0;
-      else if (mode == AFF_CLIN) v = src[g.ws.rq + i];
+      else if (mode == AFF_SLIN) v = 0.0;  // set below: s'_N = R_N^{-T} rq_N
       else v = src[g.ws.nu + i];
       gv[i] = v;
+    }
+    if (mode == AFF_SLIN && lane == 0) {
+      for (int a = 0; a < dim; a++) {
+        double s0 = src[g.ws.rq + a];
+        for (int l = 0; l < a; l++) s0 = fma(-src[g.ws.RV + l * n + a], gv[l], s0);
+        gv[a] = s0 / src[g.ws.RV + a * n + a];
+      }
     }
     if (lane == 0) {
       int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
@@ -691,45 +744,43 @@ __global__ void k_resid(Group g) {
   }
 }
 
-// k'_i = -H_uu^{-1} (rr + Bbar' (P_{i+1} rc + p'_{i+1}))  -> dv (temporarily)
-__global__ void k_kcorr(Group g) {
+// From the square-root linear pass s': k'_i = -R_vv^{-1} o_v with
+// o_v = Q'[v rows] [L^{-1}[rq; rr]; R_{i+1} rc + s'_{i+1}]  (-> dv), and p'_i = R_i's'_i (-> pp).
+__global__ void k_scorr(Group g, int per_warp) {
   const int s = warp_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  if (S.i >= P.N) return;
   const int n = g.n, m = g.m, lane = lane_id();
   double *ws = stage_ws(g, s);
-  const double *wn = stage_ws(g, s + 1);
-  const int mu = stage_wi(g, s)[SI_MBAR], ny = stage_wi(g, s + 1)[SI_NBAR];
-  const double *Bb = ws + g.ws.Bb, *Pn = wn + g.ws.P, *rc = ws + g.ws.rc, *ppn = wn + g.ws.pp;
-  const double *Lh = ws + g.ws.Lh;
-  double w = 0.0;
-  if (lane < ny) {
-    w = ppn[lane];
-    for (int l = 0; l < ny; l++) w = fma(Pn[lane * n + l], rc[l], w);
+  const int *wi = stage_wi(g, s);
+  const int nx = wi[SI_NBAR];
+  const double *sp = ws + g.ws.sp, *RV = ws + g.ws.RV;
+  for (int r = lane; r < nx; r += 32) {
+    double s0 = 0.0;
+    for (int l = 0; l <= r; l++) s0 = fma(RV[l * n + r], sp[l], s0);
+    ws[g.ws.pp + r] = s0;
   }
-  double h = 0.0;
-  for (int l = 0; l < ny; l++) {
-    double wl = __shfl_sync(kFull, w, l);
-    if (lane < mu) h = fma(Bb[l * m + lane], wl, h);
+  if (S.i >= P.N) return;
+  const int mu = wi[SI_MBAR], kh = nx + mu, rv = wi[SI_RV], ldq = 2 * n + m;
+  double *sm = warp_smem(per_warp);
+  double *lq = sm, *u = sm + (n + m), *ov = u + n;
+  slin_offsets(g, s, lq, u);
+  const double *Qs = ws + g.ws.Qs, *sn = stage_ws(g, s + 1) + g.ws.sp;
+  for (int r = lane; r < mu; r += 32) {
+    double s0 = 0.0;
+    for (int l = 0; l < kh; l++) s0 = fma(Qs[r * ldq + l], lq[l], s0);
+    for (int l = 0; l < rv; l++) s0 = fma(Qs[r * ldq + kh + l], u[l] + sn[l], s0);
+    ov[r] = s0;
   }
-  if (lane < mu) h += ws[g.ws.rr + lane];
-  // solve L L' k = -h (lane 0 sequential over the tiny system)
-  double hv[16];
-  for (int r = 0; r < 16; r++) hv[r] = __shfl_sync(kFull, h, r);
+  __syncwarp();
   if (lane == 0) {
-    for (int i = 0; i < mu; i++) {
-      double s0 = hv[i];
-      for (int l = 0; l < i; l++) s0 -= Lh[i * m + l] * hv[l];
-      hv[i] = s0 / Lh[i * m + i];
+    const double *Rvv = ws + g.ws.RVV;
+    for (int r = mu - 1; r >= 0; r--) {
+      double s0 = -ov[r];
+      for (int l = r + 1; l < mu; l++) s0 = fma(-Rvv[r * m + l], ws[g.ws.dv + l], s0);
+      ws[g.ws.dv + r] = s0 / Rvv[r * m + r];
     }
-    for (int i = mu - 1; i >= 0; i--) {
-      double s0 = hv[i];
-      for (int l = i + 1; l < mu; l++) s0 -= Lh[l * m + i] * hv[l];
-      hv[i] = s0 / Lh[i * m + i];
-    }
-    for (int i = 0; i < mu; i++) ws[g.ws.dv + i] = -hv[i];
   }
 }
 
@@ -765,14 +816,14 @@ __global__ void k_recover(Group g, double *x, double *u) {
 
 namespace eclqr {
 // reduced dimensions into batch-ordered arrays: nbar has N_j + 1 entries per
-// problem (same prefix as x / n), mbar N_j entries (same prefix as u / m)
+// problem, mbar N_j entries (the prefix of N_j + 1 minus one per earlier problem)
 __global__ void k_dims(Group g, int *nbar, int *mbar) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
   const int *wi = stage_wi(g, s);
-  nbar[P.ox / g.n + S.i] = wi[SI_NBAR];
-  if (S.i < P.N) mbar[P.ou / g.m + S.i] = wi[SI_MBAR];
+  nbar[P.ost + S.i] = wi[SI_NBAR];
+  if (S.i < P.N) mbar[P.ost - P.id + S.i] = wi[SI_MBAR];
 }
 }  // namespace eclqr

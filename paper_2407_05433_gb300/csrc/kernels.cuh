@@ -13,7 +13,7 @@ __host__ int smem_elim(int n, int m, int pmax);
 __host__ int smem_lqr_up(int n, int m);
 __host__ int smem_lqr_level(int n);
 __host__ int smem_riccati(int n, int m);
-__host__ int smem_aff(int n);
+__host__ int smem_aff(int n, int m);
 __host__ int smem_dual_stage(int n, int m);
 __host__ int smem_dual_sweep(int n, int m, int pmax, int qmax);
 __host__ int smem_dual_leaf(int n, int m, int pmax, int qmax);
@@ -27,7 +27,7 @@ __global__ void k_param(Group g, int per_warp);
 __global__ void k_elim(Group g, int per_warp);
 
 // reduced LQR, affine chains, recovery (k_lqr.cu)
-enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_CLIN_ = 2, AFF_NU_ = 3 };
+enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_SLIN_ = 2, AFF_NU_ = 3 };
 __global__ void k_lqr_up(Group g, int per_warp);
 __global__ void k_lqr_level(Group g, int src, int d, int per_warp);
 __global__ void k_riccati_down(Group g, int fin, int per_warp);
@@ -37,7 +37,7 @@ __global__ void k_aff_down(Group g, int mode, int fin, int per_warp);
 __global__ void k_solve_init(Group g, const double *s0);
 __global__ void k_post_roll(Group g, int corr);
 __global__ void k_resid(Group g);
-__global__ void k_kcorr(Group g);
+__global__ void k_scorr(Group g, int per_warp);
 __global__ void k_recover(Group g, double *x, double *u);
 __global__ void k_dims(Group g, int *nbar, int *mbar);
 

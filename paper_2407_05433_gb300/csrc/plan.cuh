@@ -19,6 +19,7 @@ struct ProbInfo {
   int id;       // index in the batch (status, residual)
   long long oA, oB, oc, oC, oD, od, oE, oe, oQ, oM, oR, oqv, orv;  // element offsets of the problem's data
   long long os0, ox, ou, olam, omu, oeta, oalpha;                // element offsets of s0 and outputs
+  long long ost;  // sum over earlier problems of (N + 1): batch stage offset
 };
 
 struct StageInfo {
@@ -40,6 +41,7 @@ struct WsLayout {
   int z, v, pi, dz, dv, dpi, rq, rr, rc, pp;
   int nu, NH, Pnu, pnu, UA, BU, UC, Ux, ru;
   int LT, lt;   // Cholesky factor L' of the reduced stage Hessian (order z, v) and L^{-1}[qbar; rbar]
+  int Qs, RV, RVV, sp;  // square-root Riccati: top rows of Q', value factor R_i, R_vv, linear term s'
   int stride;
 };
 
@@ -89,12 +91,16 @@ __host__ __device__ inline WsLayout make_ws_layout(int n, int m, int pmax, int q
   L.ru = take(m);
   L.LT = take((n + m) * (n + m));
   L.lt = take(n + m);
+  L.Qs = take((n + m) * (2 * n + m));
+  L.RV = take(n * n);
+  L.RVV = take(m * m);
+  L.sp = take(n);
   L.stride = (o + 3) & ~3;
   return L;
 }
 
 // per-stage ints
-enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_STRIDE = 8 };
+enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_RV = 5, SI_STRIDE = 8 };
 // per-chunk-slot ints: rows, left dim, right dim (0 = unary/value)
 enum { CI_ROWS = 0, CI_NA = 1, CI_NB = 2, CI_ROWS2 = 3, CI_STRIDE = 4 };
 

@@ -74,6 +74,12 @@ def load():
     lib.eclqr_reduced_dims.restype = i32
     lib.eclqr_launch_count.argtypes = [vp]
     lib.eclqr_launch_count.restype = ct.c_int64
+    lib.eclqr_time_kernel.argtypes = [vp, ct.c_char_p]
+    lib.eclqr_time_kernel.restype = i32
+    lib.eclqr_kernel_time.argtypes = [vp, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]
+    lib.eclqr_kernel_time.restype = i32
+    lib.eclqr_probe_fp64_peak.argtypes = [ct.POINTER(ct.c_double)]
+    lib.eclqr_probe_fp64_peak.restype = i32
     lib.eclqr_destroy.argtypes = [vp]
     lib.eclqr_destroy.restype = None
     lib.eclqr_strerror.argtypes = [i32]
@@ -134,6 +140,23 @@ def eclqr_destroy(h):
     load().eclqr_destroy(h)
 
 
+def eclqr_time_kernel(h, name):
+    return load().eclqr_time_kernel(h, name.encode() if name else None)
+
+
+def eclqr_kernel_time(h):
+    n, t = ct.c_int64(0), ct.c_double(0.0)
+    rc = load().eclqr_kernel_time(h, ct.byref(n), ct.byref(t))
+    _check(rc, "eclqr_kernel_time")
+    return int(n.value), float(t.value)
+
+
+def eclqr_probe_fp64_peak():
+    t = ct.c_double(0.0)
+    _check(load().eclqr_probe_fp64_peak(ct.byref(t)), "eclqr_probe_fp64_peak")
+    return float(t.value)
+
+
 def eclqr_strerror(code):
     return load().eclqr_strerror(code).decode()
 
@@ -167,7 +190,7 @@ def make_desc(h):
 class Batch:
     """A batch of problems resident on one CUDA device, solved through the C ABI."""
 
-    def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=2, chunk=0):
+    def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=4, chunk=0):
         import torch
         self.torch = torch
         self.problems = list(problems)
