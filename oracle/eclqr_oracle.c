@@ -870,6 +870,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
     double *qo_ = dalloc((size_t)(N + 1) * n), *ro_ = dalloc((size_t)N * m), *co_ = dalloc((size_t)N * n);
     double *dz = dalloc((size_t)(N + 1) * n), *dv = dalloc((size_t)N * m), *dpi = dalloc((size_t)(N + 1) * n);
     double *pv = dalloc(n), *w = dalloc(n), *hu = dalloc(m);
+    double *xr_ = dalloc(n), *uu_ = dalloc(m), *lh_ = dalloc(n), *ga_ = dalloc(n), *gb_ = dalloc(m);
     memcpy(qo_, qb, sizeof(double) * (N + 1) * n);
     memcpy(ro_, rb, sizeof(double) * N * m);
     memcpy(co_, cb, sizeof(double) * N * n);
@@ -943,27 +944,63 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         for (size_t k = 0; k < (size_t)N * m; k++) vv[k] += dv[k];
       }
       if (pass == opt->refine) break;
-      /* residual of the reduced KKT system with the true reduced data */
+      /* residual of the reduced KKT system, evaluated through the original data.
+       * Under x_i = T_i z_i + t_i, u_i = Y_i z_i + Z_i v_i + y_i (Thm 5 substitution) the
+       * z- and v-gradients of the reduced Lagrangian are T_i'a_i + Y_i'b_i - pi_i and Z_i'b_i,
+       * with a_i = g^x_i + A_i' T_{i+1} pi_{i+1} and b_i = g^u_i + B_i' T_{i+1} pi_{i+1}.
+       * Forming Qbar z + qbar instead sums terms of size |Y_i|^2, which cancel down to
+       * pi_i: where the mixed rows leave D_i ill-conditioned |Y_i| is large and that
+       * cancellation, not the solve, sets the accuracy of the multipliers. */
       for (int i = 0; i <= N; i++) {
-        int ni = nb[i];
-        const double *zi = zz + (size_t)i * n, *pii = pis + (size_t)i * n;
-        for (int a = 0; a < ni; a++) {
-          double s = qb[(size_t)i * n + a] - pii[a];
-          for (int j = 0; j < ni; j++) s += Qb[(size_t)i * n * n + a * n + j] * zi[j];
-          if (i < N) {
-            int nn = nb[i + 1], mi = mb[i];
-            for (int j = 0; j < mi; j++) s += Mb[(size_t)i * n * m + a * m + j] * vv[(size_t)i * m + j];
-            for (int l = 0; l < nn; l++) s += Ab[(size_t)i * n * n + l * n + a] * pis[(size_t)(i + 1) * n + l];
+        int ni = nb[i], nn = (i < N) ? nb[i + 1] : 0, mi = (i < N) ? mb[i] : 0;
+        const double *zi = zz + (size_t)i * n, *pii = pis + (size_t)i * n, *Ti = T + (size_t)i * n * n;
+        for (int a = 0; a < n; a++) {
+          double s = t[(size_t)i * n + a];
+          for (int j = 0; j < ni; j++) s += Ti[a * n + j] * zi[j];
+          xr_[a] = s;
+        }
+        if (i < N) {
+          const double *Tn = T + (size_t)(i + 1) * n * n, *pn = pis + (size_t)(i + 1) * n;
+          for (int a = 0; a < m; a++) {
+            double s = yv[(size_t)i * m + a];
+            for (int j = 0; j < ni; j++) s += Y[(size_t)i * m * n + a * n + j] * zi[j];
+            for (int j = 0; j < mi; j++) s += Z[(size_t)i * m * m + a * m + j] * vv[(size_t)i * m + j];
+            uu_[a] = s;
           }
+          for (int l = 0; l < n; l++) {
+            double s = 0.0;
+            for (int j = 0; j < nn; j++) s += Tn[l * n + j] * pn[j];
+            lh_[l] = s;                                   /* T_{i+1} pi_{i+1} */
+          }
+        }
+        for (int a = 0; a < n; a++) {
+          double s = P->qv[(size_t)i * n + a];
+          for (int j = 0; j < n; j++) s += P->Q[(size_t)i * n * n + a * n + j] * xr_[j];
+          if (i < N) {
+            for (int j = 0; j < m; j++) s += P->M[(size_t)i * n * m + a * m + j] * uu_[j];
+            for (int l = 0; l < n; l++) s += P->A[(size_t)i * n * n + l * n + a] * lh_[l];
+          }
+          ga_[a] = s;
+        }
+        if (i < N)
+          for (int a = 0; a < m; a++) {
+            double s = P->rv[(size_t)i * m + a];
+            for (int j = 0; j < n; j++) s += P->M[(size_t)i * n * m + j * m + a] * xr_[j];
+            for (int j = 0; j < m; j++) s += P->R[(size_t)i * m * m + a * m + j] * uu_[j];
+            for (int l = 0; l < n; l++) s += P->B[(size_t)i * n * m + l * m + a] * lh_[l];
+            gb_[a] = s;
+          }
+        for (int a = 0; a < ni; a++) {
+          double s = -pii[a];
+          for (int l = 0; l < n; l++) s += Ti[l * n + a] * ga_[l];
+          if (i < N)
+            for (int l = 0; l < m; l++) s += Y[(size_t)i * m * n + l * n + a] * gb_[l];
           qo_[(size_t)i * n + a] = s;
         }
         if (i < N) {
-          int nn = nb[i + 1], mi = mb[i];
           for (int a = 0; a < mi; a++) {
-            double s = rb[(size_t)i * m + a];
-            for (int j = 0; j < ni; j++) s += Mb[(size_t)i * n * m + j * m + a] * zi[j];
-            for (int j = 0; j < mi; j++) s += Rb[(size_t)i * m * m + a * m + j] * vv[(size_t)i * m + j];
-            for (int l = 0; l < nn; l++) s += Bb[(size_t)i * n * m + l * m + a] * pis[(size_t)(i + 1) * n + l];
+            double s = 0.0;
+            for (int l = 0; l < m; l++) s += Z[(size_t)i * m * m + l * m + a] * gb_[l];
             ro_[(size_t)i * m + a] = s;
           }
           for (int a = 0; a < nn; a++) {
@@ -973,10 +1010,12 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
             co_[(size_t)i * n + a] = s;
           }
         }
+        ADDF(2.0 * n * ni + 2.0 * m * (ni + mi) + 2.0 * n * nn + 2.0 * n * (2 * n + m) + 2.0 * m * (2 * n + m) +
+             2.0 * ni * (n + m) + 2.0 * mi * m + 2.0 * nn * (ni + mi));
       }
-      ADDF(2.0 * N * (double)(n * n + n * m) * 3.0);
     }
     free(qo_); free(ro_); free(co_); free(dz); free(dv); free(dpi); free(pv); free(w); free(hu); free(z0);
+    free(xr_); free(uu_); free(lh_); free(ga_); free(gb_);
   }
   /* recovery (eq. recovery-maps) */
   {

@@ -395,7 +395,8 @@ int eclqr_solve(eclqr_handle *h, const double *s0, double *x, double *u, int32_t
     TRY(aff_scan(h, gh, AFF_ROLL_, st));
     TRY(launch(h, k_post_roll, g.nstage, 0, st, g, 0));
     for (int r = 0; r < h->opt.refine; r++) {
-      TRY(launch(h, k_resid, g.nstage, 0, st, g));
+      const int sres = 3 * g.n + 2 * g.m;
+      TRY(launch(h, k_resid, g.nstage, sres, st, g, sres));
       TRY(aff_scan(h, gh, AFF_SLIN_, st));
       const int sc = 3 * (g.n + g.m) + 8;
       TRY(launch(h, k_scorr, g.nstage, sc, st, g, sc));

@@ -705,35 +705,82 @@ __global__ void k_post_roll(Group g, int corr) {
   }
 }
 
-// residual of the reduced KKT system at (z, v, pi):
-//   rq_i = Qbar z + Mbar v + qbar - pi_i + Abar' pi_{i+1}   (i < N),  rq_N = Qbar_N z + qbar_N - pi_N
-//   rr_i = Mbar' z + Rbar v + rbar + Bbar' pi_{i+1}
-//   rc_i = Abar z + Bbar v + cbar - z_{i+1}
-__global__ void k_resid(Group g) {
+// Residual of the reduced KKT system, evaluated through the original data.
+// Under x_i = T z + t, u_i = Y z + Z v + y (Thm 5 substitution), with
+// a = g^x + A'T_{i+1}pi_{i+1} and b = g^u + B'T_{i+1}pi_{i+1} at that point,
+// the z-rows are T'a + Y'b - pi, the v-rows Z'b, and the costate rows
+// cbar + Abar z + Bbar v - z_{i+1}.  Forming Qbar z + qbar instead would sum
+// terms of size |Y|^2 that cancel down to pi: where the mixed rows leave D_i
+// ill-conditioned |Y| is large, and that cancellation would set the accuracy
+// of the costates and so of the multipliers.  Per warp: 3n + 2m doubles.
+__global__ void k_resid(Group g, int per_warp) {
   const int s = warp_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, lane = lane_id(), i = S.i;
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
-  const bool last = S.i == P.N;
+  const bool last = i == P.N;
   const double *wn = last ? ws : stage_ws(g, s + 1);
   const int nx = wi[SI_NBAR], mu = last ? 0 : wi[SI_MBAR], ny = last ? 0 : stage_wi(g, s + 1)[SI_NBAR];
+  const int ur = wi[SI_UR], ur1 = last ? 0 : stage_wi(g, s + 1)[SI_UR];
   const double *z = ws + g.ws.z, *v = ws + g.ws.v, *pi = ws + g.ws.pi, *pin = wn + g.ws.pi, *zn = wn + g.ws.z;
-  const double *Qb = ws + g.ws.Qb, *Mb = ws + g.ws.Mb, *Rb = ws + g.ws.Rb, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
+  const double *T = ws + g.ws.UT + ur, *Tn = wn + g.ws.UT + ur1;
+  const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
+  double *sm = warp_smem(per_warp);
+  double *xs = sm, *us = xs + n, *lh = us + m, *ga = lh + n, *gb = ga + n;
+  for (int a = lane; a < n; a += 32) {
+    double s0 = ws[g.ws.t + a];
+    for (int j = 0; j < nx; j++) s0 = fma(T[a * n + j], z[j], s0);
+    xs[a] = s0;
+  }
+  if (!last) {
+    for (int a = lane; a < m; a += 32) {
+      double s0 = ws[g.ws.y + a];
+      for (int j = 0; j < nx; j++) s0 = fma(Y[a * n + j], z[j], s0);
+      for (int j = 0; j < mu; j++) s0 = fma(Z[a * m + j], v[j], s0);
+      us[a] = s0;
+    }
+    for (int l = lane; l < n; l += 32) {
+      double s0 = 0.0;
+      for (int j = 0; j < ny; j++) s0 = fma(Tn[l * n + j], pin[j], s0);
+      lh[l] = s0;                                               // T_{i+1} pi_{i+1}
+    }
+  }
+  __syncwarp();
+  const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
+  const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
+  const double *Mm = g.M + P.oM + (size_t)i * n * m, *R = g.R + P.oR + (size_t)i * m * m;
+  const double *rv = g.rv + P.orv + (size_t)i * m;
+  for (int a = lane; a < n; a += 32) {
+    double s0 = q[a];
+    for (int j = 0; j < n; j++) s0 = fma(Q[a * n + j], xs[j], s0);
+    if (!last) {
+      for (int j = 0; j < m; j++) s0 = fma(Mm[a * m + j], us[j], s0);
+      for (int l = 0; l < n; l++) s0 = fma(A[l * n + a], lh[l], s0);
+    }
+    ga[a] = s0;
+  }
+  if (!last)
+    for (int a = lane; a < m; a += 32) {
+      double s0 = rv[a];
+      for (int j = 0; j < n; j++) s0 = fma(Mm[j * m + a], xs[j], s0);
+      for (int j = 0; j < m; j++) s0 = fma(R[a * m + j], us[j], s0);
+      for (int l = 0; l < n; l++) s0 = fma(B[l * m + a], lh[l], s0);
+      gb[a] = s0;
+    }
+  __syncwarp();
   for (int r = lane; r < nx; r += 32) {
-    double s0 = ws[g.ws.qb + r] - pi[r];
-    for (int l = 0; l < nx; l++) s0 = fma(Qb[r * n + l], z[l], s0);
-    for (int l = 0; l < mu; l++) s0 = fma(Mb[r * m + l], v[l], s0);
-    for (int l = 0; l < ny; l++) s0 = fma(Ab[l * n + r], pin[l], s0);
+    double s0 = -pi[r];
+    for (int l = 0; l < n; l++) s0 = fma(T[l * n + r], ga[l], s0);
+    if (!last)
+      for (int l = 0; l < m; l++) s0 = fma(Y[l * n + r], gb[l], s0);
     ws[g.ws.rq + r] = s0;
   }
   for (int r = lane; r < mu; r += 32) {
-    double s0 = ws[g.ws.rb + r];
-    for (int l = 0; l < nx; l++) s0 = fma(Mb[l * m + r], z[l], s0);
-    for (int l = 0; l < mu; l++) s0 = fma(Rb[r * m + l], v[l], s0);
-    for (int l = 0; l < ny; l++) s0 = fma(Bb[l * m + r], pin[l], s0);
+    double s0 = 0.0;
+    for (int l = 0; l < m; l++) s0 = fma(Z[l * m + r], gb[l], s0);
     ws[g.ws.rr + r] = s0;
   }
   for (int r = lane; r < ny; r += 32) {

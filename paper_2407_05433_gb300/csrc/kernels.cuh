@@ -36,7 +36,7 @@ __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_warp);
 __global__ void k_aff_down(Group g, int mode, int fin, int per_warp);
 __global__ void k_solve_init(Group g, const double *s0);
 __global__ void k_post_roll(Group g, int corr);
-__global__ void k_resid(Group g);
+__global__ void k_resid(Group g, int per_warp);
 __global__ void k_scorr(Group g, int per_warp);
 __global__ void k_recover(Group g, double *x, double *u);
 __global__ void k_dims(Group g, int *nbar, int *mbar);

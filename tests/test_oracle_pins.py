@@ -351,6 +351,19 @@ def test_oracle_matches_dense_kkt(name, make):
         assert amax(d["J"].T @ (y - yd)) < 1e-9 * max(1.0, amax(y))
 
 
+@pytest.mark.parametrize("name,make", CLASSES, ids=[c[0] for c in CLASSES])
+def test_unrefined_pass_matches_dense_primal(name, make):
+    """Without refinement the reduced data (Lemma 4, Thm 5) and the square-root
+    Riccati alone give the primal minimiser to 1e-6: refinement evaluates its
+    residual on the original data, so it would mask a wrong reduced cost or
+    offset that this check still sees."""
+    pb = make()
+    s = oracle.solve(pb, refine=0)
+    assert s.ok
+    d = oracle.dense_kkt(pb)
+    assert rel(s.x, d["x"]) < 1e-6 and rel(s.u, d["u"]) < 1e-6
+
+
 def test_unconstrained_matches_textbook_lqr():
     """With no constraint rows the reduction is the identity (T = I, Z = I) and the
     result is the plain LQR solution from an independent textbook Riccati in numpy."""
@@ -441,6 +454,9 @@ def _pins_pass(lib):
                 return False
             d = oracle.dense_kkt(pb)
             if rel(s.x, d["x"]) > 1e-9 or rel(s.u, d["u"]) > 1e-9:
+                return False
+            s0 = oracle.solve(pb, refine=0, lib=lib)
+            if not s0.ok or rel(s0.x, d["x"]) > 1e-6 or rel(s0.u, d["u"]) > 1e-6:
                 return False
             if oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha, lib=lib) > 1e-9:
                 return False
