@@ -57,6 +57,7 @@ extern "C" {
 #define ECLQR_ENOMEM (-2)    /* device allocation failed                           */
 #define ECLQR_ECUDA (-3)     /* a CUDA call or kernel launch failed                */
 #define ECLQR_ESTATE (-4)    /* call order violated (e.g. solve before build)      */
+#define ECLQR_ETOOBIG (-5)   /* batch larger than the fixed array of eclqr_kkt_residual_noalloc */
 
 /* per-problem status codes (device array) */
 #define ECLQR_STATUS_OK 0
@@ -168,6 +169,35 @@ int eclqr_probe_fp64_peak(double *tflops);
 
 void eclqr_destroy(eclqr_handle *h);
 const char *eclqr_strerror(int code);
+
+/* Residual without allocating.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory at the moment they need
+ * the check -- real-time control loops that forbid allocation after start-up,
+ * or processes whose device memory is fully reserved by another allocator so
+ * that cudaMalloc fails.  It computes exactly what eclqr_kkt_residual computes
+ * (Sec. 9 residual definition), for the batch described by desc and data, with
+ * no handle: the per-problem and per-stage descriptors that the handle keeps in
+ * its workspace are written instead into one fixed device array of
+ * ECLQR_NOALLOC_MAX_PROBLEMS problem and ECLQR_NOALLOC_MAX_STAGES stage records
+ * (about 4 MB, held by every GPU that loads the library until the process
+ * exits).  The call performs no cudaMalloc, cudaFree or other allocation.
+ *   - desc: host memory, as for eclqr_create; data, s0, x, u, lam, mu, eta,
+ *     alpha: device, laid out as for eclqr_kkt_residual; resid: device
+ *     double[num_problems], zeroed by the call and then written.
+ *   - Batches with more than ECLQR_NOALLOC_MAX_PROBLEMS problems or more than
+ *     ECLQR_NOALLOC_MAX_STAGES stage records (sum_j (N_j + 1)) are rejected
+ *     with ECLQR_ETOOBIG before anything is enqueued.
+ *   - The first call on a device looks up the device address of the array
+ *     (cudaGetSymbolAddress) with that device current; make this first call
+ *     before any stream capture on that device.
+ *   - Every call rewrites the array (and a host staging array of the same
+ *     size) in full for its batch; calls that overlap -- on the GPU, or from
+ *     several host threads -- race and must be serialised by the caller. */
+#define ECLQR_NOALLOC_MAX_PROBLEMS 4096
+#define ECLQR_NOALLOC_MAX_STAGES 131072
+int eclqr_kkt_residual_noalloc(const eclqr_desc *desc, const eclqr_data *data, const double *s0,
+                               const double *x, const double *u, const double *lam, const double *mu,
+                               const double *eta, const double *alpha, double *resid, void *stream);
 
 #ifdef __cplusplus
 }

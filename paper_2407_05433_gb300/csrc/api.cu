@@ -525,6 +525,7 @@ const char *eclqr_strerror(int code) {
     case ECLQR_ENOMEM: return "device allocation failed";
     case ECLQR_ECUDA: return "CUDA error";
     case ECLQR_ESTATE: return "call out of order";
+    case ECLQR_ETOOBIG: return "batch exceeds the fixed array of eclqr_kkt_residual_noalloc";
     default: return "unknown error";
   }
 }

@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libeclqr.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, -1, -2, -3, -4
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5
 STATUS_NAMES = {0: "ok", 1: "infeasible_suffix", 2: "infeasible_x0", 3: "rank_inconsistent",
                 4: "nonconvex", 5: "dual_inconsistent"}
 
@@ -80,6 +80,8 @@ def load():
     lib.eclqr_kernel_time.restype = i32
     lib.eclqr_probe_fp64_peak.argtypes = [ct.POINTER(ct.c_double)]
     lib.eclqr_probe_fp64_peak.restype = i32
+    lib.eclqr_kkt_residual_noalloc.argtypes = [ct.POINTER(eclqr_desc), ct.POINTER(eclqr_data)] + [vp] * 9
+    lib.eclqr_kkt_residual_noalloc.restype = i32
     lib.eclqr_destroy.argtypes = [vp]
     lib.eclqr_destroy.restype = None
     lib.eclqr_strerror.argtypes = [i32]
@@ -126,6 +128,11 @@ def eclqr_multipliers(h, x, u, lam, mu, eta, alpha, status, stream):
 
 def eclqr_kkt_residual(h, s0, x, u, lam, mu, eta, alpha, resid, stream):
     return load().eclqr_kkt_residual(h, s0, x, u, lam, mu, eta, alpha, resid, stream)
+
+
+def eclqr_kkt_residual_noalloc(desc, data, s0, x, u, lam, mu, eta, alpha, resid, stream):
+    return load().eclqr_kkt_residual_noalloc(ct.byref(desc), ct.byref(data), s0, x, u, lam, mu, eta, alpha,
+                                             resid, stream)
 
 
 def eclqr_reduced_dims(h, nbar, mbar, stream):
