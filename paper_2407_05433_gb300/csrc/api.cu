@@ -19,7 +19,10 @@ using namespace eclqr;
 
 namespace {
 
-constexpr int kMaxSmemBytes = 227 * 1024;
+// dynamic shared memory per task: the 227 KB opt-in limit less room for the
+// team reductions' static arrays
+constexpr int kMaxSmemBytes = 226 * 1024;
+constexpr int kTeamWarps = 4;
 
 struct GroupHost {
   Group g;
@@ -53,24 +56,22 @@ struct eclqr_handle {
 
 namespace {
 
-// one warp per task, W warps per CTA chosen from the shared memory each warp needs
+// one CTA (a team of kTeamWarps warps, one per SM sub-partition) per task,
+// with per_task doubles of dynamic shared memory
 template <typename... KArgs, typename... Args>
-int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_warp, cudaStream_t st, Args... args) {
+int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cudaStream_t st, Args... args) {
   if (ntasks <= 0) return ECLQR_OK;
-  const size_t wbytes = (size_t)per_warp * sizeof(double);
-  int W = 4;
-  if (wbytes > 0) W = (int)std::max<size_t>(1, std::min<size_t>(4, kMaxSmemBytes / wbytes));
-  if (wbytes * W > (size_t)kMaxSmemBytes) return ECLQR_EINVAL;
-  const size_t smem = wbytes * W;
+  const size_t smem = (size_t)per_task * sizeof(double);
+  if (smem > (size_t)kMaxSmemBytes) return ECLQR_EINVAL;
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return ECLQR_ECUDA;
   }
-  const int grid = (ntasks + W - 1) / W;
+  const int grid = ntasks;
   const bool timed = h->timed == (const void *)kern && h->nev + 2 <= (int)h->ev.size();
   if (timed) cudaEventRecord(h->ev[h->nev], st);
-  kern<<<grid, 32 * W, smem, st>>>(args...);
+  kern<<<grid, 32 * kTeamWarps, smem, st>>>(args...);
   if (timed) {
     cudaEventRecord(h->ev[h->nev + 1], st);
     h->nev += 2;
@@ -317,7 +318,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     g.CS[1] = (double *)(base + o_CS1);
     g.CI[0] = (int *)(base + o_CI0);
     g.CI[1] = (int *)(base + o_CI1);
-    // every kernel's shared memory must fit one warp
+    // every kernel's shared memory must fit one task (one CTA)
     const int n = g.n, m = g.m;
     const int need = std::max({smem_primal_sweep(n, m, pmax, qmax), smem_rel_level(n, pmax, qmax), smem_param(n),
                                smem_elim(n, m, pmax), smem_lqr_up(n, m), smem_lqr_level(n), smem_riccati(n, m),

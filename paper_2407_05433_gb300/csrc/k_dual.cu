@@ -35,12 +35,12 @@ __host__ int smem_dual_leaf(int n, int m, int pmax, int qmax) {
 }
 
 // ---------------------------------------------------------------- per-stage blocks
-__global__ void k_dual_stage(Group g, const double *x, const double *u, int per_warp) {
-  const int s = warp_task();
+__global__ void k_dual_stage(Group g, const double *x, const double *u, int per_task) {
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, m = g.m, lane = lane_id(), i = S.i;
+  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
   const int r0 = wi[SI_UR];
@@ -48,21 +48,21 @@ __global__ void k_dual_stage(Group g, const double *x, const double *u, int per_
   const double *xi = x + P.ox + (size_t)i * n;
   const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
   const int ldc = g.pmax + g.qmax + 1;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *X = sm, *gx = X + n * n, *tp = gx + n, *rx = tp + n, *gu = rx + n;
   if (i == P.N) {
-    for (int a = lane; a < n; a += 32) {
+    for (int a = tid; a < n; a += TEAM) {
       double v = q[a];
       for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
       gx[a] = v;
     }
-    __syncwarp();
-    for (int a = lane; a < r0; a += 32) {
+    tsync();
+    for (int a = tid; a < r0; a += TEAM) {
       double v = 0.0;
       for (int l = 0; l < n; l++) v = fma(U[l * n + a], gx[l], v);
       ws[g.ws.Ux + a] = v;
     }
-    for (int idx = lane; idx < r0 * S.q; idx += 32) {
+    for (int idx = tid; idx < r0 * S.q; idx += TEAM) {
       int a = idx / S.q, j = idx - a * S.q;
       double v = 0.0;
       for (int l = 0; l < n; l++) v = fma(U[l * n + a], g.E[P.oE + (size_t)(S.qrow + j) * n + l], v);
@@ -78,7 +78,7 @@ __global__ void k_dual_stage(Group g, const double *x, const double *u, int per_
   const int r1 = win[SI_UR], nb1 = n - r1;
   const double *U1 = wn + g.ws.UT, *T1 = wn + g.ws.UT + r1, *pi1 = wn + g.ws.pi;
   // objective gradients (eq. objective-gradients) and T_{i+1} pi_{i+1}
-  for (int a = lane; a < n; a += 32) {
+  for (int a = tid; a < n; a += TEAM) {
     double v = q[a];
     for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
     for (int j = 0; j < m; j++) v = fma(Mm[a * m + j], ui[j], v);
@@ -87,46 +87,46 @@ __global__ void k_dual_stage(Group g, const double *x, const double *u, int per_
     for (int j = 0; j < nb1; j++) t = fma(T1[a * n + j], pi1[j], t);
     tp[a] = t;
   }
-  for (int a = lane; a < m; a += 32) {
+  for (int a = tid; a < m; a += TEAM) {
     double v = r[a];
     for (int j = 0; j < n; j++) v = fma(Mm[j * m + a], xi[j], v);
     for (int j = 0; j < m; j++) v = fma(R[a * m + j], ui[j], v);
     gu[a] = v;
   }
-  __syncwarp();
-  for (int a = lane; a < n; a += 32) {
+  tsync();
+  for (int a = tid; a < n; a += TEAM) {
     double v = gx[a];
     for (int l = 0; l < n; l++) v = fma(A[l * n + a], tp[l], v);
     rx[a] = v;
   }
-  for (int a = lane; a < m; a += 32) {
+  for (int a = tid; a < m; a += TEAM) {
     double v = gu[a];
     for (int l = 0; l < n; l++) v = fma(B[l * m + a], tp[l], v);
     ws[g.ws.ru + a] = v;
   }
   // X = A' U_{i+1} (n x r1)
-  for (int idx = lane; idx < n * r1; idx += 32) {
+  for (int idx = tid; idx < n * r1; idx += TEAM) {
     int l = idx / r1, b = idx - l * r1;
     double v = 0.0;
     for (int k = 0; k < n; k++) v = fma(A[k * n + l], U1[k * n + b], v);
     X[l * n + b] = v;
   }
-  __syncwarp();
+  tsync();
   wgemm<true, false>(r0, r1, n, 1.0, U, n, X, n, 0.0, ws + g.ws.UA, n);   // U' A' U1
-  for (int idx = lane; idx < m * r1; idx += 32) {
+  for (int idx = tid; idx < m * r1; idx += TEAM) {
     int a = idx / r1, b = idx - a * r1;
     double v = 0.0;
     for (int k = 0; k < n; k++) v = fma(B[k * m + a], U1[k * n + b], v);
     ws[g.ws.BU + a * n + b] = v;                                         // B' U1
   }
-  for (int idx = lane; idx < r0 * (S.p + S.q); idx += 32) {
+  for (int idx = tid; idx < r0 * (S.p + S.q); idx += TEAM) {
     int a = idx / (S.p + S.q), j = idx - a * (S.p + S.q);
     const double *row = (j < S.p) ? g.C + P.oC + (size_t)(S.prow + j) * n : g.E + P.oE + (size_t)(S.qrow + j - S.p) * n;
     double v = 0.0;
     for (int l = 0; l < n; l++) v = fma(U[l * n + a], row[l], v);
     ws[g.ws.UC + a * ldc + j] = v;                                       // U' [C' E']
   }
-  for (int a = lane; a < r0; a += 32) {
+  for (int a = tid; a < r0; a += TEAM) {
     double v = 0.0;
     for (int l = 0; l < n; l++) v = fma(U[l * n + a], rx[l], v);
     ws[g.ws.Ux + a] = v;                                                 // U' rho^x
@@ -137,14 +137,14 @@ __global__ void k_dual_stage(Group g, const double *x, const double *u, int per_
 // layout  mu,eta (w) | nu_{i+1} (r1) | nu_i (r0) | [extra zero block (ext)] | 1.
 // Returns the number of rows written (r0 + m).
 __device__ int dual_stage_rows(const Group &g, int s, double *M, int ldm, int ext) {
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
   const double *ws = stage_ws(g, s);
   const int r0 = stage_wi(g, s)[SI_UR], r1 = stage_wi(g, s + 1)[SI_UR];
   const int w = S.p + S.q, ldc = g.pmax + g.qmax + 1;
   const int rows = r0 + m;
-  for (int idx = lane; idx < rows * ldm; idx += 32) {
+  for (int idx = tid; idx < rows * ldm; idx += TEAM) {
     int r = idx / ldm, j = idx - r * ldm;
     double val = 0.0;
     if (r < r0) {
@@ -161,25 +161,25 @@ __device__ int dual_stage_rows(const Group &g, int s, double *M, int ldm, int ex
     M[idx] = val;
   }
   (void)ext;
-  __syncwarp();
+  tsync();
   return rows;
 }
 
 // ---------------------------------------------------------------- terminal relation on nu_N
-__global__ void k_dual_terminal(Group g, int per_warp) {
-  const int t = warp_task();
+__global__ void k_dual_terminal(Group g, int per_task) {
+  const int t = team_task();
   if (t >= g.nprob) return;
   const ProbInfo &P = g.prob[t];
-  const int n = g.n, lane = lane_id();
+  const int n = g.n, tid = team_rank();
   const int s = P.st0 + P.N;
   const StageInfo S = g.st[s];
   double *ws = stage_ws(g, s);
   int *wi = stage_wi(g, s);
   const int rN = wi[SI_UR], qN = S.q, ldc = g.pmax + g.qmax + 1;
   const int ldm = qN + rN + 1;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *M = sm, *out = M + n * ldm, *scr = out + n * (n + 1);
-  for (int idx = lane; idx < rN * ldm; idx += 32) {
+  for (int idx = tid; idx < rN * ldm; idx += TEAM) {
     int r = idx / ldm, j = idx - r * ldm;
     double val = 0.0;
     if (j < qN) val = ws[g.ws.UC + r * ldc + j];
@@ -187,18 +187,18 @@ __global__ void k_dual_terminal(Group g, int per_warp) {
     else if (j == ldm - 1) val = ws[g.ws.Ux + r];
     M[idx] = val;
   }
-  __syncwarp();
+  tsync();
   const int gs[1] = {qN};
   ProjResult pr = wproject(M, ldm, rN, 1, gs, rN, g.tau_rank, g.tau_inc, out, rN + 1, scr);
   double *NH = ws + g.ws.NH;
   const int slot = P.ch0 + P.nch, ldr = 2 * n + 1;
   double *cs = g.CS[0] + (size_t)slot * g.cs_stride;
-  for (int idx = lane; idx < pr.krank * (rN + 1); idx += 32) {
+  for (int idx = tid; idx < pr.krank * (rN + 1); idx += TEAM) {
     int r = idx / (rN + 1), j = idx - r * (rN + 1);
     NH[r * (n + 1) + j] = out[idx];
     cs[r * ldr + j] = out[idx];
   }
-  if (lane == 0) {
+  if (tid == 0) {
     wi[SI_NUROWS] = pr.krank;
     int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
     cm[CI_ROWS] = pr.krank; cm[CI_NA] = rN; cm[CI_NB] = 0;
@@ -207,25 +207,25 @@ __global__ void k_dual_terminal(Group g, int per_warp) {
 }
 
 // ---------------------------------------------------------------- chunk up-sweep on (nu_a, nu_b)
-__global__ void k_dual_up(Group g, int per_warp) {
-  const int t = warp_task();
+__global__ void k_dual_up(Group g, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
   if (ci.c >= P.nch) return;
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int rb = stage_wi(g, P.st0 + b)[SI_UR];
   const int ldr = 2 * n + 1;
   const int ldm_max = g.pmax + g.qmax + 3 * n + 1, rows_max = 3 * n + m;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *Rel = sm, *M = Rel + 2 * n * ldr, *scr = M + rows_max * ldm_max;
   // identity on (nu_b', nu_b)
-  for (int idx = lane; idx < rb * ldr; idx += 32) {
+  for (int idx = tid; idx < rb * ldr; idx += TEAM) {
     int i = idx / ldr, j = idx - i * ldr;
     Rel[idx] = (j == i) ? 1.0 : ((j == rb + i) ? -1.0 : 0.0);
   }
-  __syncwarp();
+  tsync();
   int rr = rb;
   for (int i = b - 1; i >= a; --i) {
     const int s = P.st0 + i;
@@ -235,7 +235,7 @@ __global__ void k_dual_up(Group g, int per_warp) {
     const int ldm = w + r1 + r0 + rb + 1;
     int rows = dual_stage_rows(g, s, M, ldm, rb);
     // the stage rows were written with offset column ldm - 1 and a zero nu_b block
-    for (int idx = lane; idx < rr * ldm; idx += 32) {
+    for (int idx = tid; idx < rr * ldm; idx += TEAM) {
       int r = idx / ldm, j = idx - r * ldm;
       const double *row = Rel + r * ldr;  // [L (r1) | R (rb) | l]
       double val = 0.0;
@@ -244,33 +244,33 @@ __global__ void k_dual_up(Group g, int per_warp) {
       else if (j == ldm - 1) val = row[r1 + rb];
       M[(rows + r) * ldm + j] = val;
     }
-    __syncwarp();
+    tsync();
     const int gs[2] = {w, r1};
     ProjResult pr = wproject(M, ldm, rows + rr, 2, gs, r0 + rb, g.tau_rank, g.tau_inc, Rel, ldr, scr);
     rr = pr.krank;
-    if (pr.inconsistent && lane == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
-    __syncwarp();
+    if (pr.inconsistent && tid == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
+    tsync();
   }
   double *cs = g.CS[0] + (size_t)t * g.cs_stride;
-  for (int idx = lane; idx < rr * ldr; idx += 32) cs[idx] = Rel[idx];
-  if (lane == 0) {
+  for (int idx = tid; idx < rr * ldr; idx += TEAM) cs[idx] = Rel[idx];
+  if (tid == 0) {
     int *cm = g.CI[0] + (size_t)t * CI_STRIDE;
     cm[CI_ROWS] = rr; cm[CI_NA] = stage_wi(g, P.st0 + a)[SI_UR]; cm[CI_NB] = rb;
   }
 }
 
 // ---------------------------------------------------------------- chunk down-sweep: sets N_i and forward maps
-__global__ void k_dual_down(Group g, int fin, int per_warp) {
-  const int t = warp_task();
+__global__ void k_dual_down(Group g, int fin, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
   if (ci.c >= P.nch) return;
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int ldr = 2 * n + 1;
   const int ldm_max = g.pmax + g.qmax + 3 * n + 1, rows_max = 3 * n + m;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *Ns = sm;                          // n x (2n+1): current set on nu_{i+1}
   double *M = Ns + 2 * n * ldr;             // rows_max x ldm_max
   double *K = M + rows_max * ldm_max;       // rows_max x (2n+1): rows after eliminating mu,eta
@@ -285,8 +285,8 @@ __global__ void k_dual_down(Group g, int fin, int per_warp) {
   {
     const double *src = g.CS[fin] + (size_t)(t + 1) * g.cs_stride;
     const int rows = g.CI[fin][(size_t)(t + 1) * CI_STRIDE + CI_ROWS];
-    for (int idx = lane; idx < rows * ldr; idx += 32) Ns[idx] = src[idx];
-    __syncwarp();
+    for (int idx = tid; idx < rows * ldr; idx += TEAM) Ns[idx] = src[idx];
+    tsync();
     if (b == P.N) { /* stage N's set was stored by k_dual_terminal */ }
     int rr = rows;
     for (int i = b - 1; i >= a; --i) {
@@ -296,7 +296,7 @@ __global__ void k_dual_down(Group g, int fin, int per_warp) {
       const int r0 = stage_wi(g, s)[SI_UR], r1 = stage_wi(g, s + 1)[SI_UR], w = S.p + S.q;
       const int ldm = w + r1 + r0 + 1;
       int rows2 = dual_stage_rows(g, s, M, ldm, 0);
-      for (int idx = lane; idx < rr * ldm; idx += 32) {
+      for (int idx = tid; idx < rr * ldm; idx += TEAM) {
         int r = idx / ldm, j = idx - r * ldm;
         const double *row = Ns + r * ldr;  // [H (r1) | h]
         double val = 0.0;
@@ -304,79 +304,79 @@ __global__ void k_dual_down(Group g, int fin, int per_warp) {
         else if (j == ldm - 1) val = row[r1];
         M[(rows2 + r) * ldm + j] = val;
       }
-      __syncwarp();
+      tsync();
       // eliminate (mu, eta): rows [Kn (r1) | L (r0) | l]
       const int gs1[1] = {w};
       ProjResult p1 = wproject(M, ldm, rows2 + rr, 1, gs1, r1 + r0, g.tau_rank, g.tau_inc, K, ldr, scr);
       const int kr = p1.krank;
-      if (p1.inconsistent && lane == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
+      if (p1.inconsistent && tid == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
       // forward map: nu_{i+1} = -Kn^+ (L nu_i + l)
       double *Pnu = ws + g.ws.Pnu, *pnu = ws + g.ws.pnu;
       {
         const int rank = wtqr(K, ldr, kr, r1, g.tau_rank, Wt, (kr > 0 ? kr : 1), Qf, n, perm, tq);
         wtqr_solve(Wt, (kr > 0 ? kr : 1), Qf, n, perm, kr, r1, rank, K + r1, ldr, r0 + 1, X, n + 1, Ys, n + 1);
-        for (int idx = lane; idx < r1 * (r0 + 1); idx += 32) {
+        for (int idx = tid; idx < r1 * (r0 + 1); idx += TEAM) {
           int r = idx / (r0 + 1), j = idx - r * (r0 + 1);
           if (j < r0) Pnu[r * n + j] = X[r * (n + 1) + j]; else pnu[r] = X[r * (n + 1) + j];
         }
       }
       // N_i: project nu_{i+1} out of the same rows
-      for (int idx = lane; idx < kr * (r1 + r0 + 1); idx += 32) {
+      for (int idx = tid; idx < kr * (r1 + r0 + 1); idx += TEAM) {
         int r = idx / (r1 + r0 + 1), j = idx - r * (r1 + r0 + 1);
         M[idx] = K[r * ldr + j];
       }
-      __syncwarp();
+      tsync();
       const int gs2[1] = {r1};
       ProjResult p2 = wproject(M, r1 + r0 + 1, kr, 1, gs2, r0, g.tau_rank, g.tau_inc, Ns, ldr, scr);
       rr = p2.krank;
-      if (p2.inconsistent && lane == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
+      if (p2.inconsistent && tid == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
       double *NH = ws + g.ws.NH;
-      for (int idx = lane; idx < rr * (r0 + 1); idx += 32) {
+      for (int idx = tid; idx < rr * (r0 + 1); idx += TEAM) {
         int r = idx / (r0 + 1), j = idx - r * (r0 + 1);
         NH[r * (n + 1) + j] = Ns[r * ldr + j];
       }
-      if (lane == 0) stage_wi(g, s)[SI_NUROWS] = rr;
-      __syncwarp();
+      if (tid == 0) stage_wi(g, s)[SI_NUROWS] = rr;
+      tsync();
     }
   }
 }
 
 // ---------------------------------------------------------------- root: min-norm nu_0 in N_0
-__global__ void k_dual_root(Group g, int per_warp) {
-  const int t = warp_task();
+__global__ void k_dual_root(Group g, int per_task) {
+  const int t = team_task();
   if (t >= g.nprob) return;
   const ProbInfo &P = g.prob[t];
-  const int n = g.n, lane = lane_id();
+  const int n = g.n, tid = team_rank();
   const int s = P.st0;
   double *ws = stage_ws(g, s);
   const int r0 = stage_wi(g, s)[SI_UR], rr = stage_wi(g, s)[SI_NUROWS];
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *Hs = sm, *hb = Hs + n * (n + 1), *Wt = hb + n, *Qf = Wt + n * n, *X = Qf + n * n, *Ys = X + n;
   double *tq = Ys + n;
   int *perm = (int *)(tq + 4 * n);
   const double *NH = ws + g.ws.NH;
-  for (int idx = lane; idx < rr * (n + 1); idx += 32) Hs[idx] = NH[idx];
-  for (int r = lane; r < rr; r += 32) hb[r] = NH[r * (n + 1) + r0];
-  __syncwarp();
+  for (int idx = tid; idx < rr * (n + 1); idx += TEAM) Hs[idx] = NH[idx];
+  for (int r = tid; r < rr; r += TEAM) hb[r] = NH[r * (n + 1) + r0];
+  tsync();
   const int rank = wtqr(Hs, n + 1, rr, r0, g.tau_rank, Wt, (rr > 0 ? rr : 1), Qf, n, perm, tq);
   wtqr_solve(Wt, (rr > 0 ? rr : 1), Qf, n, perm, rr, r0, rank, hb, 1, 1, X, 1, Ys, 1);
-  for (int a = lane; a < n; a += 32) ws[g.ws.nu + a] = (a < r0) ? X[a] : 0.0;
+  for (int a = tid; a < n; a += TEAM) ws[g.ws.nu + a] = (a < r0) ? X[a] : 0.0;
 }
 
 // ---------------------------------------------------------------- leaves: mu_i, eta_i, lambda_i, alpha, eta_N
-__global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_warp) {
-  const int s = warp_task();
+__global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task) {
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, m = g.m, lane = lane_id(), i = S.i;
+  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   const double *ws = stage_ws(g, s);
   const int r0 = stage_wi(g, s)[SI_UR], nb = n - r0;
   const int ldc = g.pmax + g.qmax + 1;
   const double *nu0 = ws + g.ws.nu;
   // lambda_i = T_i pi_i + U_i nu_i
   const double *UT = ws + g.ws.UT, *pi = ws + g.ws.pi;
-  for (int a = lane; a < n; a += 32) {
+  for (int a = tid; a < n; a += TEAM) {
     double v = 0.0;
     for (int j = 0; j < r0; j++) v = fma(UT[a * n + j], nu0[j], v);
     for (int j = 0; j < nb; j++) v = fma(UT[a * n + r0 + j], pi[j], v);
@@ -385,7 +385,7 @@ __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, doubl
   }
   const int w = (i < P.N) ? S.p + S.q : S.q;
   if (w == 0) return;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   const int wmax = g.pmax + g.qmax, rmax = n + m;
   double *F = sm, *rhs = F + rmax * wmax, *Wt = rhs + rmax, *Qf = Wt + wmax * rmax, *X = Qf + wmax * wmax;
   double *Ys = X + wmax, *tq = Ys + rmax;
@@ -396,14 +396,14 @@ __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, doubl
     const int r1 = stage_wi(g, s + 1)[SI_UR];
     const double *nu1 = wn + g.ws.nu;
     rows = r0 + m;
-    for (int idx = lane; idx < rows * w; idx += 32) {
+    for (int idx = tid; idx < rows * w; idx += TEAM) {
       int r = idx / w, j = idx - r * w;
       double val;
       if (r < r0) val = ws[g.ws.UC + r * ldc + j];
       else val = (j < S.p) ? g.D[P.oD + (size_t)(S.prow + j) * m + (r - r0)] : 0.0;
       F[idx] = val;
     }
-    for (int r = lane; r < rows; r += 32) {
+    for (int r = tid; r < rows; r += TEAM) {
       double v;
       if (r < r0) {
         v = ws[g.ws.Ux + r] - nu0[r];
@@ -416,20 +416,20 @@ __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, doubl
     }
   } else {
     rows = r0;
-    for (int idx = lane; idx < rows * w; idx += 32) {
+    for (int idx = tid; idx < rows * w; idx += TEAM) {
       int r = idx / w, j = idx - r * w;
       F[idx] = ws[g.ws.UC + r * ldc + j];
     }
-    for (int r = lane; r < rows; r += 32) rhs[r] = ws[g.ws.Ux + r] - nu0[r];
+    for (int r = tid; r < rows; r += TEAM) rhs[r] = ws[g.ws.Ux + r] - nu0[r];
   }
-  __syncwarp();
+  tsync();
   const int rank = wtqr(F, w, rows, w, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qf, wmax, perm, tq);
   wtqr_solve(Wt, (rows > 0 ? rows : 1), Qf, wmax, perm, rows, w, rank, rhs, 1, 1, X, 1, Ys, 1);
   if (i < P.N) {
-    for (int j = lane; j < S.p; j += 32) mu[P.omu + S.prow + j] = X[j];
-    for (int j = lane; j < S.q; j += 32) eta[P.oeta + S.qrow + j] = X[S.p + j];
+    for (int j = tid; j < S.p; j += TEAM) mu[P.omu + S.prow + j] = X[j];
+    for (int j = tid; j < S.q; j += TEAM) eta[P.oeta + S.qrow + j] = X[S.p + j];
   } else {
-    for (int j = lane; j < S.q; j += 32) eta[P.oeta + S.qrow + j] = X[j];
+    for (int j = tid; j < S.q; j += TEAM) eta[P.oeta + S.qrow + j] = X[j];
   }
 }
 
@@ -440,18 +440,18 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
 
 __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const double *u, const double *lam,
                                const double *mu, const double *eta, const double *alpha, double *resid) {
-  const int s = warp_task();
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, m = g.m, lane = lane_id(), i = S.i;
+  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   const double *xi = x + P.ox + (size_t)i * n, *li = lam + P.olam + (size_t)i * n;
   const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
   double r = 0.0;
   if (i == 0)
-    for (int a = lane; a < n; a += 32) r = fmax(r, fabs(xi[a] - s0[P.os0 + a]));
+    for (int a = tid; a < n; a += TEAM) r = fmax(r, fabs(xi[a] - s0[P.os0 + a]));
   // state-only rows, normalised
-  for (int k = lane; k < S.q; k += 32) {
+  for (int k = tid; k < S.q; k += TEAM) {
     const double *Ek = g.E + P.oE + (size_t)(S.qrow + k) * n;
     double e = g.e[P.oe + S.qrow + k], v = e, sc = fmax(1.0, fabs(e));
     for (int j = 0; j < n; j++) { v = fma(Ek[j], xi[j], v); sc = fmax(sc, fabs(Ek[j])); }
@@ -465,20 +465,20 @@ __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const
     const double *rv = g.rv + P.orv + (size_t)i * m;
     const double *ui = u + P.ou + (size_t)i * m, *xn = x + P.ox + (size_t)(i + 1) * n;
     const double *ln = lam + P.olam + (size_t)(i + 1) * n, *mui = mu + P.omu + S.prow;
-    for (int a = lane; a < n; a += 32) {
+    for (int a = tid; a < n; a += TEAM) {
       double v = c[a] - xn[a];
       for (int j = 0; j < n; j++) v = fma(A[a * n + j], xi[j], v);
       for (int j = 0; j < m; j++) v = fma(B[a * m + j], ui[j], v);
       r = fmax(r, fabs(v));
     }
-    for (int k = lane; k < S.p; k += 32) {
+    for (int k = tid; k < S.p; k += TEAM) {
       const double *Ck = g.C + P.oC + (size_t)(S.prow + k) * n, *Dk = g.D + P.oD + (size_t)(S.prow + k) * m;
       double dd = g.d[P.od + S.prow + k], v = dd, sc = fmax(1.0, fabs(dd));
       for (int j = 0; j < n; j++) { v = fma(Ck[j], xi[j], v); sc = fmax(sc, fabs(Ck[j])); }
       for (int j = 0; j < m; j++) { v = fma(Dk[j], ui[j], v); sc = fmax(sc, fabs(Dk[j])); }
       r = fmax(r, fabs(v) / sc);
     }
-    for (int a = lane; a < m; a += 32) {
+    for (int a = tid; a < m; a += TEAM) {
       double v = rv[a];
       for (int j = 0; j < n; j++) v = fma(Mm[j * m + a], xi[j], v);
       for (int j = 0; j < m; j++) v = fma(R[a * m + j], ui[j], v);
@@ -486,7 +486,7 @@ __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const
       for (int k = 0; k < S.p; k++) v = fma(g.D[P.oD + (size_t)(S.prow + k) * m + a], mui[k], v);
       r = fmax(r, fabs(v));
     }
-    for (int a = lane; a < n; a += 32) {
+    for (int a = tid; a < n; a += TEAM) {
       double v = q[a] + ((i == 0) ? alpha[P.oalpha + a] : -li[a]);
       for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
       for (int j = 0; j < m; j++) v = fma(Mm[a * m + j], ui[j], v);
@@ -496,15 +496,15 @@ __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const
       r = fmax(r, fabs(v));
     }
   } else {
-    for (int a = lane; a < n; a += 32) {
+    for (int a = tid; a < n; a += TEAM) {
       double v = q[a] - li[a];
       for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
       for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
       r = fmax(r, fabs(v));
     }
   }
-  r = warp_max(r);
-  if (lane == 0) atomic_max_nonneg(resid + P.id, r);
+  r = team_max(r);
+  if (tid == 0) atomic_max_nonneg(resid + P.id, r);
 }
 
 }  // namespace eclqr

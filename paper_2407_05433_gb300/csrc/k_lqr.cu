@@ -46,42 +46,42 @@ __device__ __forceinline__ double *crel_cost(double *slot, int n) { return slot 
 // relation on (z_i, z_b).  Stage i substitutes the reduced dynamics
 // z_{i+1} = Abar z_i + Bbar v + cbar into the rows on (z_{i+1}, z_b), stacks the
 // stage cost rows L'[z; v] + l and eliminates v (wlse_elim).
-__global__ void k_lqr_up(Group g, int per_warp) {
-  const int t = warp_task();
+__global__ void k_lqr_up(Group g, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const int ldr = 2 * n + 1;
   double *slot = g.CS[0] + (size_t)t * g.cs_stride;
   int *cm = g.CI[0] + (size_t)t * CI_STRIDE;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   if (ci.c == P.nch) {
     // terminal value: rows [L' | L^{-1} qbar_N], L L' = Qbar_N (eq. terminal-cost-data)
     const int sN = P.st0 + P.N;
     const double *ws = stage_ws(g, sN);
     const int nN = stage_wi(g, sN)[SI_NBAR];
     double *Hh = sm, *l = sm + n * n;
-    for (int idx = lane; idx < nN * nN; idx += 32) {
+    for (int idx = tid; idx < nN * nN; idx += TEAM) {
       int a = idx / nN, j = idx - a * nN;
       Hh[idx] = ws[g.ws.Qb + a * n + j];
     }
-    __syncwarp();
+    tsync();
     const int fail = wcholesky(Hh, nN, nN);
-    if (lane == 0) {
+    if (tid == 0) {
       for (int a = 0; a < nN; a++) {
         double s0 = ws[g.ws.qb + a];
         for (int k = 0; k < a; k++) s0 = fma(-Hh[a * nN + k], l[k], s0);
         l[a] = s0 / Hh[a * nN + a];
       }
     }
-    __syncwarp();
+    tsync();
     double *cost = crel_cost(slot, n);
-    for (int idx = lane; idx < nN * (nN + 1); idx += 32) {
+    for (int idx = tid; idx < nN * (nN + 1); idx += TEAM) {
       int a = idx / (nN + 1), j = idx - a * (nN + 1);
       cost[a * ldr + j] = (j < nN) ? Hh[j * nN + a] : l[a];
     }
-    if (lane == 0) {
+    if (tid == 0) {
       cm[CI_ROWS] = 0; cm[CI_NA] = nN; cm[CI_NB] = 0; cm[CI_ROWS2] = nN;
       if (fail) set_status(g, ci.prob, ST_NONCONVEX);
     }
@@ -92,11 +92,11 @@ __global__ void k_lqr_up(Group g, int per_warp) {
   const int rows_max = 5 * n + m, ldm_max = m + 2 * n + 1;
   double *Cons = sm, *Cost = Cons + 2 * n * ldr, *M = Cost + 2 * n * ldr, *scr = M + rows_max * ldm_max;
   // z_b' = z_b on (z_b', z_b)
-  for (int idx = lane; idx < nbz * ldr; idx += 32) {
+  for (int idx = tid; idx < nbz * ldr; idx += TEAM) {
     int i = idx / ldr, j = idx - i * ldr;
     Cons[idx] = (j == i) ? 1.0 : ((j == nbz + i) ? -1.0 : 0.0);
   }
-  __syncwarp();
+  tsync();
   int rc = nbz, rq = 0;
   int fail = 0;
   for (int i = b - 1; i >= a; --i) {
@@ -109,7 +109,7 @@ __global__ void k_lqr_up(Group g, int per_warp) {
     // columns v (mu) | z_i (nx) | z_b (nbz) | 1
     // rows: constraints (rc) then stage cost (kh) then old cost (rq)
     const int rtot = rc + kh + rq;
-    for (int idx = lane; idx < rtot * ldm; idx += 32) {
+    for (int idx = tid; idx < rtot * ldm; idx += TEAM) {
       int r = idx / ldm, j = idx - r * ldm;
       double val = 0.0;
       if (r < rc || r >= rc + kh) {
@@ -132,16 +132,16 @@ __global__ void k_lqr_up(Group g, int per_warp) {
       }
       M[idx] = val;
     }
-    __syncwarp();
+    tsync();
     LseResult lr = wlse_elim(M, ldm, rc, kh + rq, mu, nx + nbz, g.tau_rank, g.tau_inc, Cons, Cost, ldr, scr);
     rc = lr.kc;
     rq = lr.kq;
     fail |= lr.inconsistent;
   }
-  for (int idx = lane; idx < rc * ldr; idx += 32) slot[idx] = Cons[idx];
+  for (int idx = tid; idx < rc * ldr; idx += TEAM) slot[idx] = Cons[idx];
   double *cost = crel_cost(slot, n);
-  for (int idx = lane; idx < rq * ldr; idx += 32) cost[idx] = Cost[idx];
-  if (lane == 0) {
+  for (int idx = tid; idx < rq * ldr; idx += TEAM) cost[idx] = Cost[idx];
+  if (tid == 0) {
     cm[CI_ROWS] = rc; cm[CI_NA] = stage_wi(g, P.st0 + a)[SI_NBAR]; cm[CI_NB] = nbz; cm[CI_ROWS2] = rq;
     if (fail) set_status(g, ci.prob, ST_NONCONVEX);
   }
@@ -149,32 +149,32 @@ __global__ void k_lqr_up(Group g, int per_warp) {
 
 // One level of the chunk suffix scan on cost relations: slot t <- slot t o slot t + d,
 // eliminating the shared state (wlse_elim); a value on the right gives a value.
-__global__ void k_lqr_level(Group g, int src, int d, int per_warp) {
-  const int t = warp_task();
+__global__ void k_lqr_level(Group g, int src, int d, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
-  const int n = g.n, lane = lane_id(), ldr = 2 * n + 1;
+  const int n = g.n, tid = team_rank(), ldr = 2 * n + 1;
   double *S1 = g.CS[src] + (size_t)t * g.cs_stride;
   const int *I1 = g.CI[src] + (size_t)t * CI_STRIDE;
   double *Dst = g.CS[src ^ 1] + (size_t)t * g.cs_stride;
   int *J = g.CI[src ^ 1] + (size_t)t * CI_STRIDE;
   const int rc1 = I1[CI_ROWS], na = I1[CI_NA], nm = I1[CI_NB], rq1 = I1[CI_ROWS2];
   if (ci.c + d > P.nch || nm == 0) {
-    for (int idx = lane; idx < rc1 * ldr; idx += 32) Dst[idx] = S1[idx];
-    for (int idx = lane; idx < rq1 * ldr; idx += 32) crel_cost(Dst, n)[idx] = crel_cost(S1, n)[idx];
-    if (lane == 0) { J[CI_ROWS] = rc1; J[CI_NA] = na; J[CI_NB] = nm; J[CI_ROWS2] = rq1; }
+    for (int idx = tid; idx < rc1 * ldr; idx += TEAM) Dst[idx] = S1[idx];
+    for (int idx = tid; idx < rq1 * ldr; idx += TEAM) crel_cost(Dst, n)[idx] = crel_cost(S1, n)[idx];
+    if (tid == 0) { J[CI_ROWS] = rc1; J[CI_NA] = na; J[CI_NB] = nm; J[CI_ROWS2] = rq1; }
     return;
   }
   double *S2 = g.CS[src] + (size_t)(t + d) * g.cs_stride;
   const int *I2 = g.CI[src] + (size_t)(t + d) * CI_STRIDE;
   const int rc2 = I2[CI_ROWS], nb = I2[CI_NB], rq2 = I2[CI_ROWS2];
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   const int ldm = nm + na + nb + 1;
   const int rc = rc1 + rc2, rq = rq1 + rq2;
   double *M = sm, *scr = sm + (rc + rq) * ldm;
   // columns z_m | z_a | z_b | 1 ; rows: constraints of e1, e2, then costs of e1, e2
-  for (int idx = lane; idx < (rc + rq) * ldm; idx += 32) {
+  for (int idx = tid; idx < (rc + rq) * ldm; idx += TEAM) {
     int r = idx / ldm, j = idx - r * ldm;
     bool left;
     const double *row;
@@ -194,9 +194,9 @@ __global__ void k_lqr_level(Group g, int src, int d, int per_warp) {
     }
     M[idx] = val;
   }
-  __syncwarp();
+  tsync();
   LseResult lr = wlse_elim(M, ldm, rc, rq, nm, na + nb, g.tau_rank, g.tau_inc, Dst, crel_cost(Dst, n), ldr, scr);
-  if (lane == 0) {
+  if (tid == 0) {
     J[CI_ROWS] = lr.kc; J[CI_NA] = na; J[CI_NB] = nb; J[CI_ROWS2] = lr.kq;
     if (lr.inconsistent) set_status(g, ci.prob, ST_NONCONVEX);
   }
@@ -212,16 +212,16 @@ __global__ void k_lqr_level(Group g, int src, int d, int per_warp) {
 // meeting at a boundary use the same frame).  Stored per stage: P_i = R_i'R_i,
 // p_i = R_i's_i, K, k, H_uu (Cholesky factor), H_ux = R_vv'R_vz, Phi = Abar + Bbar K,
 // and for the refinement passes R_i, R_vv and the top rows of Q'.
-__global__ void k_riccati_down(Group g, int fin, int per_warp) {
-  const int t = warp_task();
+__global__ void k_riccati_down(Group g, int fin, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
   if (ci.c >= P.nch) return;
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int ldr = 2 * n + 1, ldq = 2 * n + m;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   const int rows_max = 2 * n + m, ldst = n + m + 1 + rows_max;
   double *V = sm, *St = V + n * (n + 1), *v = St + rows_max * ldst, *w = v + rows_max;
   double *Kt = w + ldst;  // m x (n + 1)
@@ -232,21 +232,21 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
     const int *I = g.CI[fin] + (size_t)(t + 1) * CI_STRIDE;
     const int nbz = I[CI_NA];
     rv = I[CI_ROWS2];
-    for (int idx = lane; idx < rv * (nbz + 1); idx += 32) {
+    for (int idx = tid; idx < rv * (nbz + 1); idx += TEAM) {
       int r = idx / (nbz + 1), j = idx - r * (nbz + 1);
       const double sg = (src[r * ldr + r] >= 0.0) ? 1.0 : -1.0;
       V[r * (n + 1) + j] = sg * src[r * ldr + j];
     }
-    __syncwarp();
+    tsync();
     if (b == P.N) {  // P_N = C'C, p_N = C'c, value factor for the refinement
       double *wsN = stage_ws(g, P.st0 + b);
-      for (int idx = lane; idx < nbz * (nbz + 1); idx += 32) {
+      for (int idx = tid; idx < nbz * (nbz + 1); idx += TEAM) {
         int r = idx / (nbz + 1), j = idx - r * (nbz + 1);
         double s0 = 0.0;
         for (int l = 0; l < rv; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + j], s0);
         if (j < nbz) wsN[g.ws.P + r * n + j] = s0; else wsN[g.ws.p + r] = s0;
       }
-      for (int idx = lane; idx < rv * nbz; idx += 32) {
+      for (int idx = tid; idx < rv * nbz; idx += TEAM) {
         int r = idx / nbz, j = idx - r * nbz;
         wsN[g.ws.RV + r * n + j] = V[r * (n + 1) + j];
       }
@@ -259,7 +259,7 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
     const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
     const int kh = nx + mu, rows = kh + rv, ld = kh + 1 + rows;
     const double *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb, *cb = ws + g.ws.cb, *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
-    for (int idx = lane; idx < rows * ld; idx += 32) {
+    for (int idx = tid; idx < rows * ld; idx += TEAM) {
       int r = idx / ld, j = idx - r * ld;
       double val = 0.0;
       if (j > kh) {
@@ -281,99 +281,99 @@ __global__ void k_riccati_down(Group g, int fin, int per_warp) {
       }
       St[idx] = val;
     }
-    __syncwarp();
+    tsync();
     for (int col = 0; col < kh && col < rows; col++) {
       double s0 = 0.0;
-      for (int r = col + lane; r < rows; r += 32) s0 = fma(St[r * ld + col], St[r * ld + col], s0);
-      s0 = sqrt(warp_sum(s0));
+      for (int r = col + tid; r < rows; r += TEAM) s0 = fma(St[r * ld + col], St[r * ld + col], s0);
+      s0 = sqrt(team_sum(s0));
       if (s0 == 0.0) continue;
       whouse_apply(St, ld, col, rows, col, col + 1, ld, nullptr, v, w, s0);
     }
     // sign the z rows to a positive diagonal (rows mu .. kh - 1, all columns)
-    for (int idx = lane; idx < nx * ld; idx += 32) {
+    for (int idx = tid; idx < nx * ld; idx += TEAM) {
       int r = mu + idx / ld, j = idx % ld;
       if (St[r * ld + r] < 0.0 && j != r) St[r * ld + j] = -St[r * ld + j];
     }
-    __syncwarp();
-    for (int r = mu + lane; r < kh; r += 32) St[r * ld + r] = fabs(St[r * ld + r]);
-    __syncwarp();
+    tsync();
+    for (int r = mu + tid; r < kh; r += TEAM) St[r * ld + r] = fabs(St[r * ld + r]);
+    tsync();
     // K, k:  R_vv [K | k] = -[R_vz | o_v]
-    for (int c = lane; c <= nx; c += 32) {
+    for (int c = tid; c <= nx; c += TEAM) {
       for (int r = mu - 1; r >= 0; r--) {
         double s0 = -St[r * ld + mu + c];
         for (int l = r + 1; l < mu; l++) s0 = fma(-St[r * ld + l], Kt[l * (n + 1) + c], s0);
         Kt[r * (n + 1) + c] = s0 / St[r * ld + r];
       }
     }
-    __syncwarp();
-    for (int idx = lane; idx < mu * (nx + 1); idx += 32) {
+    tsync();
+    for (int idx = tid; idx < mu * (nx + 1); idx += TEAM) {
       int r = idx / (nx + 1), c = idx - r * (nx + 1);
       if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
     }
-    for (int idx = lane; idx < mu * mu; idx += 32) {
+    for (int idx = tid; idx < mu * mu; idx += TEAM) {
       int r = idx / mu, j = idx - r * mu;
       double sg = St[j * ld + j] >= 0.0 ? 1.0 : -1.0;
       ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * St[j * ld + r] : 0.0;
       ws[g.ws.RVV + r * m + j] = (j >= r) ? St[r * ld + j] : 0.0;
     }
-    for (int idx = lane; idx < mu * nx; idx += 32) {
+    for (int idx = tid; idx < mu * nx; idx += TEAM) {
       int r = idx / nx, c = idx - r * nx;
       double s0 = 0.0;
       for (int l = 0; l <= r; l++) s0 = fma(St[l * ld + r], St[l * ld + mu + c], s0);
       ws[g.ws.Hx + r * n + c] = s0;
     }
-    for (int idx = lane; idx < n1 * nx; idx += 32) {
+    for (int idx = tid; idx < n1 * nx; idx += TEAM) {
       int r = idx / nx, c = idx - r * nx;
       double s0 = Ab[r * n + c];
       for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
       ws[g.ws.Phi + r * n + c] = s0;
     }
     // top kh rows of Q' (columns: kh stage-cost offsets, then rv value offsets)
-    for (int idx = lane; idx < kh * rows; idx += 32) {
+    for (int idx = tid; idx < kh * rows; idx += TEAM) {
       int r = idx / rows, c = idx - r * rows;
       ws[g.ws.Qs + r * ldq + c] = St[r * ld + kh + 1 + c];
     }
-    if (lane == 0) wi[SI_RV] = rv;
+    if (tid == 0) wi[SI_RV] = rv;
     // new value rows [R_i | s_i]
-    __syncwarp();
-    for (int idx = lane; idx < nx * (nx + 1); idx += 32) {
+    tsync();
+    for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
       int r = idx / (nx + 1), c = idx - r * (nx + 1);
       V[r * (n + 1) + c] = (c < nx) ? ((c >= r) ? St[(mu + r) * ld + mu + c] : 0.0) : St[(mu + r) * ld + kh];
     }
-    __syncwarp();
+    tsync();
     rv = nx;
-    for (int idx = lane; idx < nx * (nx + 1); idx += 32) {
+    for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
       int r = idx / (nx + 1), c = idx - r * (nx + 1);
       double s0 = 0.0;
       for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
       if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
       if (c < nx) ws[g.ws.RV + r * n + c] = V[r * (n + 1) + c];
     }
-    __syncwarp();
+    tsync();
   }
 }
 
 // Offsets of the refinement's square-root linear pass at stage s:
 // lq = L^{-1} [rq; rr] (stage cost rows) and u = R_{i+1} rc (value rows).
 __device__ void slin_offsets(const Group &g, int s, double *lq, double *u) {
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);
   const int *wi = stage_wi(g, s);
   const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], kh = nx + mu, rv = wi[SI_RV];
   const double *LT = ws + g.ws.LT;
-  if (lane == 0) {
+  if (tid == 0) {
     for (int a = 0; a < kh; a++) {
       double s0 = (a < nx) ? ws[g.ws.rq + a] : ws[g.ws.rr + (a - nx)];
       for (int l = 0; l < a; l++) s0 = fma(-LT[l * (n + m) + a], lq[l], s0);
       lq[a] = s0 / LT[a * (n + m) + a];
     }
   }
-  for (int r = lane; r < rv; r += 32) {
+  for (int r = tid; r < rv; r += TEAM) {
     double s0 = 0.0;
     for (int l = r; l < rv; l++) s0 = fma(wn[g.ws.RV + r * n + l], ws[g.ws.rc + l], s0);
     u[r] = s0;
   }
-  __syncwarp();
+  tsync();
 }
 
 // ----------------------------------------------------------- affine chain scans
@@ -396,17 +396,17 @@ __device__ __forceinline__ int aff_out(const Group &g, int mode) {
 // map of stage i: y_out = G y_in + gv.  Forward: in = stage i, out = stage i+1;
 // backward: in = stage i+1, out = stage i.  G (dout x din, ld n) and gv into smem.
 __device__ void aff_stage_map(const Group &g, int s, int mode, double *G, double *gv, double *tmp) {
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);
   const int *wi = stage_wi(g, s);
   if (mode == AFF_NU) {
     const int din = wi[SI_UR], dout = stage_wi(g, s + 1)[SI_UR];
-    for (int idx = lane; idx < dout * din; idx += 32) {
+    for (int idx = tid; idx < dout * din; idx += TEAM) {
       int i = idx / din, j = idx - i * din;
       G[i * n + j] = ws[g.ws.Pnu + i * n + j];
     }
-    for (int i = lane; i < dout; i += 32) gv[i] = ws[g.ws.pnu + i];
-    __syncwarp();
+    for (int i = tid; i < dout; i += TEAM) gv[i] = ws[g.ws.pnu + i];
+    tsync();
     return;
   }
   const int nx = wi[SI_NBAR], ny = stage_wi(g, s + 1)[SI_NBAR], mu = wi[SI_MBAR];
@@ -414,16 +414,16 @@ __device__ void aff_stage_map(const Group &g, int s, int mode, double *G, double
   if (mode == AFF_ROLL || mode == AFF_CROLL) {
     const double *kk = ws + (mode == AFF_ROLL ? g.ws.k : g.ws.dv);
     const double *cc = ws + (mode == AFF_ROLL ? g.ws.cb : g.ws.rc);
-    for (int idx = lane; idx < ny * nx; idx += 32) {
+    for (int idx = tid; idx < ny * nx; idx += TEAM) {
       int i = idx / nx, j = idx - i * nx;
       G[i * n + j] = Phi[i * n + j];
     }
-    for (int i = lane; i < ny; i += 32) {
+    for (int i = tid; i < ny; i += TEAM) {
       double s0 = cc[i];
       for (int l = 0; l < mu; l++) s0 = fma(Bb[i * m + l], kk[l], s0);
       gv[i] = s0;
     }
-    __syncwarp();
+    tsync();
     return;
   }
   // AFF_SLIN: G = rows mu.. of Q' on the value offsets (nx x rv), gv = Q'[z rows] [L^{-1}[rq; rr]; R_{i+1} rc]
@@ -431,28 +431,28 @@ __device__ void aff_stage_map(const Group &g, int s, int mode, double *G, double
   const double *Qs = ws + g.ws.Qs;
   double *lq = tmp, *u = tmp + (n + m);
   slin_offsets(g, s, lq, u);
-  for (int idx = lane; idx < nx * rv; idx += 32) {
+  for (int idx = tid; idx < nx * rv; idx += TEAM) {
     int i = idx / rv, j = idx - i * rv;
     G[i * n + j] = Qs[(mu + i) * ldq + kh + j];
   }
-  for (int i = lane; i < nx; i += 32) {
+  for (int i = tid; i < nx; i += TEAM) {
     double s0 = 0.0;
     for (int l = 0; l < kh; l++) s0 = fma(Qs[(mu + i) * ldq + l], lq[l], s0);
     for (int l = 0; l < rv; l++) s0 = fma(Qs[(mu + i) * ldq + kh + l], u[l], s0);
     gv[i] = s0;
   }
-  __syncwarp();
+  tsync();
   (void)ny;
 }
 
 // chunk aggregates; also the boundary value slot (forward: slot 0 of the
 // problem holds y_0, backward: slot nch holds y_N).
-__global__ void k_aff_up(Group g, int mode, int per_warp) {
-  const int t = warp_task();
+__global__ void k_aff_up(Group g, int mode, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
-  const int n = g.n, lane = lane_id();
+  const int n = g.n, tid = team_rank();
   const bool fwd = aff_forward(mode);
   double *cs0 = g.CS[0];
   if (ci.c == P.nch) {
@@ -462,7 +462,7 @@ __global__ void k_aff_up(Group g, int mode, int per_warp) {
     const int dim = aff_dim(g, s, mode);
     double *gv = cs0 + (size_t)slot * g.cs_stride + n * n;
     const double *src = stage_ws(g, s);
-    for (int i = lane; i < dim; i += 32) {
+    for (int i = tid; i < dim; i += TEAM) {
       double v;
       if (mode == AFF_ROLL) v = src[g.ws.z + i];
       else if (mode == AFF_CROLL) v = 0.0;
@@ -470,14 +470,15 @@ __global__ void k_aff_up(Group g, int mode, int per_warp) {
       else v = src[g.ws.nu + i];
       gv[i] = v;
     }
-    if (mode == AFF_SLIN && lane == 0) {
+    tsync();
+    if (mode == AFF_SLIN && tid == 0) {
       for (int a = 0; a < dim; a++) {
         double s0 = src[g.ws.rq + a];
         for (int l = 0; l < a; l++) s0 = fma(-src[g.ws.RV + l * n + a], gv[l], s0);
         gv[a] = s0 / src[g.ws.RV + a * n + a];
       }
     }
-    if (lane == 0) {
+    if (tid == 0) {
       int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
       cm[CI_ROWS] = 1; cm[CI_NA] = dim; cm[CI_NB] = 0;
     }
@@ -485,15 +486,15 @@ __global__ void k_aff_up(Group g, int mode, int per_warp) {
   }
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int slot = fwd ? P.ch0 + ci.c + 1 : P.ch0 + ci.c;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *Gm = sm, *gm = Gm + n * n, *Gs = gm + n, *gs = Gs + n * n, *Tm = gs + n, *tmp = Tm + n * n;
   const int d0 = fwd ? aff_dim(g, P.st0 + a, mode) : aff_dim(g, P.st0 + b, mode);
-  for (int idx = lane; idx < n * n; idx += 32) {
+  for (int idx = tid; idx < n * n; idx += TEAM) {
     int i = idx / n, j = idx - i * n;
     Gm[idx] = (i == j) ? 1.0 : 0.0;
   }
-  for (int i = lane; i < n; i += 32) gm[i] = 0.0;
-  __syncwarp();
+  for (int i = tid; i < n; i += TEAM) gm[i] = 0.0;
+  tsync();
   int dcur = d0;  // rows of the aggregate (current output dimension)
   for (int k = 0; k < b - a; k++) {
     const int i = fwd ? a + k : b - 1 - k;
@@ -502,36 +503,36 @@ __global__ void k_aff_up(Group g, int mode, int per_warp) {
     const int dout = fwd ? aff_dim(g, s + 1, mode) : aff_dim(g, s, mode);
     // Tm = Gs Gm (dout x d0), tmp = Gs gm + gs
     wgemm<false, false>(dout, d0, dcur, 1.0, Gs, n, Gm, n, 0.0, Tm, n);
-    for (int r = lane; r < dout; r += 32) {
+    for (int r = tid; r < dout; r += TEAM) {
       double s0 = gs[r];
       for (int l = 0; l < dcur; l++) s0 = fma(Gs[r * n + l], gm[l], s0);
       tmp[r] = s0;
     }
-    __syncwarp();
-    for (int idx = lane; idx < dout * d0; idx += 32) {
+    tsync();
+    for (int idx = tid; idx < dout * d0; idx += TEAM) {
       int r = idx / d0, j = idx - r * d0;
       Gm[r * n + j] = Tm[r * n + j];
     }
-    for (int r = lane; r < dout; r += 32) gm[r] = tmp[r];
-    __syncwarp();
+    for (int r = tid; r < dout; r += TEAM) gm[r] = tmp[r];
+    tsync();
     dcur = dout;
   }
   double *cs = cs0 + (size_t)slot * g.cs_stride;
-  for (int idx = lane; idx < n * n; idx += 32) cs[idx] = Gm[idx];
-  for (int i = lane; i < n; i += 32) cs[n * n + i] = gm[i];
-  if (lane == 0) {
+  for (int idx = tid; idx < n * n; idx += TEAM) cs[idx] = Gm[idx];
+  for (int i = tid; i < n; i += TEAM) cs[n * n + i] = gm[i];
+  if (tid == 0) {
     int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
     cm[CI_ROWS] = 0; cm[CI_NA] = d0; cm[CI_NB] = dcur;
   }
 }
 
 // slot t <- slot t o slot t' (t' = t - d forward, t + d backward) inside one problem.
-__global__ void k_aff_level(Group g, int src, int d, int fwd, int per_warp) {
-  const int t = warp_task();
+__global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
-  const int n = g.n, lane = lane_id();
+  const int n = g.n, tid = team_rank();
   const int j = t - P.ch0;  // slot index 0..nch
   const double *S1 = g.CS[src] + (size_t)t * g.cs_stride;
   const int *I1 = g.CI[src] + (size_t)t * CI_STRIDE;
@@ -541,99 +542,99 @@ __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_warp) {
   const bool value1 = I1[CI_ROWS] == 1;
   const int j2 = fwd ? j - d : j + d;
   if (value1 || j2 < 0 || j2 > P.nch) {
-    for (int idx = lane; idx < n * n + n; idx += 32) Dst[idx] = S1[idx];
-    if (lane == 0) { J[CI_ROWS] = I1[CI_ROWS]; J[CI_NA] = na; J[CI_NB] = nb; }
+    for (int idx = tid; idx < n * n + n; idx += TEAM) Dst[idx] = S1[idx];
+    if (tid == 0) { J[CI_ROWS] = I1[CI_ROWS]; J[CI_NA] = na; J[CI_NB] = nb; }
     return;
   }
   const int t2 = P.ch0 + j2;
   const double *S2 = g.CS[src] + (size_t)t2 * g.cs_stride;
   const int *I2 = g.CI[src] + (size_t)t2 * CI_STRIDE;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *Tm = sm, *tv = Tm + n * n;
   if (I2[CI_ROWS] == 1) {
     // value: y = G1 v + g1
     const int dv = I2[CI_NA];
-    for (int r = lane; r < nb; r += 32) {
+    for (int r = tid; r < nb; r += TEAM) {
       double s0 = S1[n * n + r];
       for (int l = 0; l < dv; l++) s0 = fma(S1[r * n + l], S2[n * n + l], s0);
       Dst[n * n + r] = s0;
     }
-    if (lane == 0) { J[CI_ROWS] = 1; J[CI_NA] = nb; J[CI_NB] = 0; }
+    if (tid == 0) { J[CI_ROWS] = 1; J[CI_NA] = nb; J[CI_NB] = 0; }
     return;
   }
   const int na2 = I2[CI_NA];
   // (G1 G2, G1 g2 + g1): input dim na2, output nb
   wgemm<false, false>(nb, na2, na, 1.0, S1, n, S2, n, 0.0, Tm, n);
-  for (int r = lane; r < nb; r += 32) {
+  for (int r = tid; r < nb; r += TEAM) {
     double s0 = S1[n * n + r];
     for (int l = 0; l < na; l++) s0 = fma(S1[r * n + l], S2[n * n + l], s0);
     tv[r] = s0;
   }
-  __syncwarp();
-  for (int idx = lane; idx < n * n; idx += 32) Dst[idx] = Tm[idx];
-  for (int r = lane; r < n; r += 32) Dst[n * n + r] = tv[r];
-  if (lane == 0) { J[CI_ROWS] = 0; J[CI_NA] = na2; J[CI_NB] = nb; }
+  tsync();
+  for (int idx = tid; idx < n * n; idx += TEAM) Dst[idx] = Tm[idx];
+  for (int r = tid; r < n; r += TEAM) Dst[n * n + r] = tv[r];
+  if (tid == 0) { J[CI_ROWS] = 0; J[CI_NA] = na2; J[CI_NB] = nb; }
 }
 
-__global__ void k_aff_down(Group g, int mode, int fin, int per_warp) {
-  const int t = warp_task();
+__global__ void k_aff_down(Group g, int mode, int fin, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
   if (ci.c >= P.nch) return;
-  const int n = g.n, lane = lane_id();
+  const int n = g.n, tid = team_rank();
   const bool fwd = aff_forward(mode);
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int off = aff_out(g, mode);
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *Gs = sm, *gs = Gs + n * n, *y = gs + n, *y2 = y + n, *tmp = y2 + n;
   // boundary value after the scan: forward slot (ch0 + c) = y_a; backward slot (ch0 + c + 1) = y_b
   const int slot = fwd ? P.ch0 + ci.c : P.ch0 + ci.c + 1;
   const double *sv = g.CS[fin] + (size_t)slot * g.cs_stride + n * n;
   int dcur = fwd ? aff_dim(g, P.st0 + a, mode) : aff_dim(g, P.st0 + b, mode);
-  for (int i = lane; i < n; i += 32) y[i] = (i < dcur) ? sv[i] : 0.0;
-  __syncwarp();
+  for (int i = tid; i < n; i += TEAM) y[i] = (i < dcur) ? sv[i] : 0.0;
+  tsync();
   if (fwd) {
     for (int i = a; i < b; i++) {
       const int s = P.st0 + i;
       double *o = stage_ws(g, s) + off;
-      for (int r = lane; r < n; r += 32) o[r] = (r < dcur) ? y[r] : 0.0;
+      for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? y[r] : 0.0;
       aff_stage_map(g, s, mode, Gs, gs, tmp);
       const int dout = aff_dim(g, s + 1, mode);
-      for (int r = lane; r < dout; r += 32) {
+      for (int r = tid; r < dout; r += TEAM) {
         double s0 = gs[r];
         for (int l = 0; l < dcur; l++) s0 = fma(Gs[r * n + l], y[l], s0);
         y2[r] = s0;
       }
-      __syncwarp();
-      for (int r = lane; r < n; r += 32) y[r] = (r < dout) ? y2[r] : 0.0;
-      __syncwarp();
+      tsync();
+      for (int r = tid; r < n; r += TEAM) y[r] = (r < dout) ? y2[r] : 0.0;
+      tsync();
       dcur = dout;
     }
     if (b == P.N) {
       double *o = stage_ws(g, P.st0 + b) + off;
-      for (int r = lane; r < n; r += 32) o[r] = (r < dcur) ? y[r] : 0.0;
+      for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? y[r] : 0.0;
     }
   } else {
     if (b == P.N) {
       double *o = stage_ws(g, P.st0 + b) + off;
-      for (int r = lane; r < n; r += 32) o[r] = (r < dcur) ? y[r] : 0.0;
+      for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? y[r] : 0.0;
     }
     for (int i = b - 1; i >= a; i--) {
       const int s = P.st0 + i;
       aff_stage_map(g, s, mode, Gs, gs, tmp);
       const int dout = aff_dim(g, s, mode);
-      for (int r = lane; r < dout; r += 32) {
+      for (int r = tid; r < dout; r += TEAM) {
         double s0 = gs[r];
         for (int l = 0; l < dcur; l++) s0 = fma(Gs[r * n + l], y[l], s0);
         y2[r] = s0;
       }
-      __syncwarp();
-      for (int r = lane; r < n; r += 32) y[r] = (r < dout) ? y2[r] : 0.0;
-      __syncwarp();
+      tsync();
+      for (int r = tid; r < n; r += TEAM) y[r] = (r < dout) ? y2[r] : 0.0;
+      tsync();
       dcur = dout;
       double *o = stage_ws(g, s) + off;
-      for (int r = lane; r < n; r += 32) o[r] = y[r];
+      for (int r = tid; r < n; r += TEAM) o[r] = y[r];
     }
   }
 }
@@ -641,10 +642,10 @@ __global__ void k_aff_down(Group g, int mode, int fin, int per_warp) {
 // ----------------------------------------------------------- stage-parallel helpers of the solve
 // z_0 = T_0'(s_0 - t_0) and the check H_0 s_0 + h_0 = 0 (eqs. initial-feasibility, reduced-initial)
 __global__ void k_solve_init(Group g, const double *s0) {
-  const int t = warp_task();
+  const int t = team_task();
   if (t >= g.nprob) return;
   const ProbInfo &P = g.prob[t];
-  const int n = g.n, lane = lane_id();
+  const int n = g.n, tid = team_rank();
   const int s = P.st0;
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
@@ -652,17 +653,17 @@ __global__ void k_solve_init(Group g, const double *s0) {
   const double *x0 = s0 + P.os0;
   const double *H = ws + g.ws.H, *T = ws + g.ws.UT + ur, *tt = ws + g.ws.t;
   double worst = 0.0, om = 0.0;
-  for (int a = lane; a < r; a += 32) {
+  for (int a = tid; a < r; a += TEAM) {
     double v = H[a * (n + 1) + n];
     om = fmax(om, fabs(v));
     for (int l = 0; l < n; l++) v = fma(H[a * (n + 1) + l], x0[l], v);
     worst = fmax(worst, fabs(v));
   }
-  for (int l = lane; l < n; l += 32) om = fmax(om, fabs(x0[l]));
-  worst = warp_max(worst);
-  om = fmax(1.0, warp_max(om));
-  if (lane == 0 && worst > g.tau_inc * om) set_status(g, t, ST_INFEASIBLE_X0);
-  for (int a = lane; a < n; a += 32) {
+  for (int l = tid; l < n; l += TEAM) om = fmax(om, fabs(x0[l]));
+  worst = team_max(worst);
+  om = fmax(1.0, team_max(om));
+  if (tid == 0 && worst > g.tau_inc * om) set_status(g, t, ST_INFEASIBLE_X0);
+  for (int a = tid; a < n; a += TEAM) {
     double v = 0.0;
     if (a < nb)
       for (int l = 0; l < n; l++) v = fma(T[l * n + a], x0[l] - tt[l], v);
@@ -673,11 +674,11 @@ __global__ void k_solve_init(Group g, const double *s0) {
 // pass 0: v_i = K z + k, pi_i = P z + p.  correction passes: dv = K dz + k', dpi = P dz + p',
 // then z += dz, v += dv, pi += dpi.
 __global__ void k_post_roll(Group g, int corr) {
-  const int s = warp_task();
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
   const int nx = wi[SI_NBAR], mu = (S.i < P.N) ? wi[SI_MBAR] : 0;
@@ -686,7 +687,7 @@ __global__ void k_post_roll(Group g, int corr) {
   const double *pp = ws + (corr ? g.ws.pp : g.ws.p);
   // v (or dv) -- computed into registers of the lanes then written
   double myv = 0.0, mypi = 0.0;
-  const int r = lane;
+  const int r = tid;
   if (r < mu) {
     myv = kk[r];
     for (int l = 0; l < nx; l++) myv = fma(ws[g.ws.K + r * n + l], zz[l], myv);
@@ -695,7 +696,7 @@ __global__ void k_post_roll(Group g, int corr) {
     mypi = pp[r];
     for (int l = 0; l < nx; l++) mypi = fma(ws[g.ws.P + r * n + l], zz[l], mypi);
   }
-  __syncwarp();
+  tsync();
   if (!corr) {
     if (r < m) ws[g.ws.v + r] = (r < mu) ? myv : 0.0;
     if (r < n) ws[g.ws.pi + r] = (r < nx) ? mypi : 0.0;
@@ -712,13 +713,13 @@ __global__ void k_post_roll(Group g, int corr) {
 // cbar + Abar z + Bbar v - z_{i+1}.  Forming Qbar z + qbar instead would sum
 // terms of size |Y|^2 that cancel down to pi: where the mixed rows leave D_i
 // ill-conditioned |Y| is large, and that cancellation would set the accuracy
-// of the costates and so of the multipliers.  Per warp: 3n + 2m doubles.
-__global__ void k_resid(Group g, int per_warp) {
-  const int s = warp_task();
+// of the costates and so of the multipliers.  Per task: 3n + 2m doubles.
+__global__ void k_resid(Group g, int per_task) {
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, m = g.m, lane = lane_id(), i = S.i;
+  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
   const bool last = i == P.N;
@@ -728,32 +729,32 @@ __global__ void k_resid(Group g, int per_warp) {
   const double *z = ws + g.ws.z, *v = ws + g.ws.v, *pi = ws + g.ws.pi, *pin = wn + g.ws.pi, *zn = wn + g.ws.z;
   const double *T = ws + g.ws.UT + ur, *Tn = wn + g.ws.UT + ur1;
   const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *xs = sm, *us = xs + n, *lh = us + m, *ga = lh + n, *gb = ga + n;
-  for (int a = lane; a < n; a += 32) {
+  for (int a = tid; a < n; a += TEAM) {
     double s0 = ws[g.ws.t + a];
     for (int j = 0; j < nx; j++) s0 = fma(T[a * n + j], z[j], s0);
     xs[a] = s0;
   }
   if (!last) {
-    for (int a = lane; a < m; a += 32) {
+    for (int a = tid; a < m; a += TEAM) {
       double s0 = ws[g.ws.y + a];
       for (int j = 0; j < nx; j++) s0 = fma(Y[a * n + j], z[j], s0);
       for (int j = 0; j < mu; j++) s0 = fma(Z[a * m + j], v[j], s0);
       us[a] = s0;
     }
-    for (int l = lane; l < n; l += 32) {
+    for (int l = tid; l < n; l += TEAM) {
       double s0 = 0.0;
       for (int j = 0; j < ny; j++) s0 = fma(Tn[l * n + j], pin[j], s0);
       lh[l] = s0;                                               // T_{i+1} pi_{i+1}
     }
   }
-  __syncwarp();
+  tsync();
   const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
   const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
   const double *Mm = g.M + P.oM + (size_t)i * n * m, *R = g.R + P.oR + (size_t)i * m * m;
   const double *rv = g.rv + P.orv + (size_t)i * m;
-  for (int a = lane; a < n; a += 32) {
+  for (int a = tid; a < n; a += TEAM) {
     double s0 = q[a];
     for (int j = 0; j < n; j++) s0 = fma(Q[a * n + j], xs[j], s0);
     if (!last) {
@@ -763,27 +764,27 @@ __global__ void k_resid(Group g, int per_warp) {
     ga[a] = s0;
   }
   if (!last)
-    for (int a = lane; a < m; a += 32) {
+    for (int a = tid; a < m; a += TEAM) {
       double s0 = rv[a];
       for (int j = 0; j < n; j++) s0 = fma(Mm[j * m + a], xs[j], s0);
       for (int j = 0; j < m; j++) s0 = fma(R[a * m + j], us[j], s0);
       for (int l = 0; l < n; l++) s0 = fma(B[l * m + a], lh[l], s0);
       gb[a] = s0;
     }
-  __syncwarp();
-  for (int r = lane; r < nx; r += 32) {
+  tsync();
+  for (int r = tid; r < nx; r += TEAM) {
     double s0 = -pi[r];
     for (int l = 0; l < n; l++) s0 = fma(T[l * n + r], ga[l], s0);
     if (!last)
       for (int l = 0; l < m; l++) s0 = fma(Y[l * n + r], gb[l], s0);
     ws[g.ws.rq + r] = s0;
   }
-  for (int r = lane; r < mu; r += 32) {
+  for (int r = tid; r < mu; r += TEAM) {
     double s0 = 0.0;
     for (int l = 0; l < m; l++) s0 = fma(Z[l * m + r], gb[l], s0);
     ws[g.ws.rr + r] = s0;
   }
-  for (int r = lane; r < ny; r += 32) {
+  for (int r = tid; r < ny; r += TEAM) {
     double s0 = ws[g.ws.cb + r] - zn[r];
     for (int l = 0; l < nx; l++) s0 = fma(Ab[r * n + l], z[l], s0);
     for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], v[l], s0);
@@ -793,35 +794,35 @@ __global__ void k_resid(Group g, int per_warp) {
 
 // From the square-root linear pass s': k'_i = -R_vv^{-1} o_v with
 // o_v = Q'[v rows] [L^{-1}[rq; rr]; R_{i+1} rc + s'_{i+1}]  (-> dv), and p'_i = R_i's'_i (-> pp).
-__global__ void k_scorr(Group g, int per_warp) {
-  const int s = warp_task();
+__global__ void k_scorr(Group g, int per_task) {
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
   const int nx = wi[SI_NBAR];
   const double *sp = ws + g.ws.sp, *RV = ws + g.ws.RV;
-  for (int r = lane; r < nx; r += 32) {
+  for (int r = tid; r < nx; r += TEAM) {
     double s0 = 0.0;
     for (int l = 0; l <= r; l++) s0 = fma(RV[l * n + r], sp[l], s0);
     ws[g.ws.pp + r] = s0;
   }
   if (S.i >= P.N) return;
   const int mu = wi[SI_MBAR], kh = nx + mu, rv = wi[SI_RV], ldq = 2 * n + m;
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *lq = sm, *u = sm + (n + m), *ov = u + n;
   slin_offsets(g, s, lq, u);
   const double *Qs = ws + g.ws.Qs, *sn = stage_ws(g, s + 1) + g.ws.sp;
-  for (int r = lane; r < mu; r += 32) {
+  for (int r = tid; r < mu; r += TEAM) {
     double s0 = 0.0;
     for (int l = 0; l < kh; l++) s0 = fma(Qs[r * ldq + l], lq[l], s0);
     for (int l = 0; l < rv; l++) s0 = fma(Qs[r * ldq + kh + l], u[l] + sn[l], s0);
     ov[r] = s0;
   }
-  __syncwarp();
-  if (lane == 0) {
+  tsync();
+  if (tid == 0) {
     const double *Rvv = ws + g.ws.RVV;
     for (int r = mu - 1; r >= 0; r--) {
       double s0 = -ov[r];
@@ -833,16 +834,16 @@ __global__ void k_scorr(Group g, int per_warp) {
 
 // x_i = T z + t, u_i = Y z + Z v + y (eq. recovery-maps)
 __global__ void k_recover(Group g, double *x, double *u) {
-  const int s = warp_task();
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
   const int ur = wi[SI_UR], nb = n - ur;
   const double *T = ws + g.ws.UT + ur, *z = ws + g.ws.z;
-  for (int a = lane; a < n; a += 32) {
+  for (int a = tid; a < n; a += TEAM) {
     double v = ws[g.ws.t + a];
     for (int j = 0; j < nb; j++) v = fma(T[a * n + j], z[j], v);
     x[P.ox + (size_t)S.i * n + a] = v;
@@ -850,7 +851,7 @@ __global__ void k_recover(Group g, double *x, double *u) {
   if (S.i < P.N) {
     const int mb = wi[SI_MBAR];
     const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *vv = ws + g.ws.v;
-    for (int a = lane; a < m; a += 32) {
+    for (int a = tid; a < m; a += TEAM) {
       double v = ws[g.ws.y + a];
       for (int j = 0; j < nb; j++) v = fma(Y[a * n + j], z[j], v);
       for (int j = 0; j < mb; j++) v = fma(Z[a * m + j], vv[j], v);

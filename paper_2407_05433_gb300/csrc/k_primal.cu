@@ -1,6 +1,6 @@
 // k_primal.cu -- feasible-domain scan (Sec. 3-4) and stage-parallel
-// elimination (Sec. 5) on sm_103a.  One warp per task; small matrices live in
-// the warp's shared-memory window.
+// elimination (Sec. 5) on sm_103a.  One CTA per task; small matrices live in
+// the task's shared-memory window.
 //
 // Scan schedule.  A problem's stages are cut into chunks of L stages.  Each
 // chunk first composes its own base relations (eq. base-system) into one
@@ -17,7 +17,7 @@
 
 namespace eclqr {
 
-// ----------------------------------------------------------- shared memory sizes (doubles per warp)
+// ----------------------------------------------------------- shared memory sizes (doubles per task)
 __host__ int smem_primal_sweep(int n, int m, int pmax, int qmax) {
   int rows = 2 * n + pmax + qmax, ldm = m + 2 * n + 1;
   return 2 * n * (2 * n + 1) + rows * ldm + rows + 2 * ldm + 8;
@@ -36,32 +36,32 @@ __host__ int smem_elim(int n, int m, int pmax) {
 }
 
 // ----------------------------------------------------------- terminal domain X_N
-__global__ void k_terminal(Group g, int per_warp) {
-  const int t = warp_task();
+__global__ void k_terminal(Group g, int per_task) {
+  const int t = team_task();
   if (t >= g.nprob) return;
   const ProbInfo &P = g.prob[t];
-  const int n = g.n, lane = lane_id();
+  const int n = g.n, tid = team_rank();
   const int s = P.st0 + P.N;
   const StageInfo S = g.st[s];
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   const int ld = n + 1;
   double *M = sm, *scr = sm + g.qmax * ld;
-  for (int idx = lane; idx < S.q * ld; idx += 32) {
+  for (int idx = tid; idx < S.q * ld; idx += TEAM) {
     int i = idx / ld, j = idx - i * ld;
     M[idx] = (j < n) ? g.E[P.oE + (size_t)(S.qrow + i) * n + j] : g.e[P.oe + S.qrow + i];
   }
-  __syncwarp();
+  tsync();
   double *H = stage_ws(g, s) + g.ws.H;
   ProjResult r = wproject(M, ld, S.q, 0, nullptr, n, g.tau_rank, g.tau_inc, H, ld, scr);
   // terminal element of the chunk scan: unary relation on x_N
   const int slot = P.ch0 + P.nch;
   double *cs = g.CS[0] + (size_t)slot * g.cs_stride;
   const int ldr = 2 * n + 1;
-  for (int idx = lane; idx < r.krank * ld; idx += 32) {
+  for (int idx = tid; idx < r.krank * ld; idx += TEAM) {
     int i = idx / ld, j = idx - i * ld;
     cs[i * ldr + j] = H[i * ld + j];
   }
-  if (lane == 0) {
+  if (tid == 0) {
     stage_wi(g, s)[SI_HROWS] = r.krank;
     int *ci = g.CI[0] + (size_t)slot * CI_STRIDE;
     ci[CI_ROWS] = r.krank; ci[CI_NA] = n; ci[CI_NB] = 0;
@@ -72,24 +72,24 @@ __global__ void k_terminal(Group g, int per_warp) {
 // ----------------------------------------------------------- chunk up-sweep
 // Relation on (x_i, x_b) built from stage b-1 down to a.  Columns of the
 // projected system: u_i (m) | x_i (n) | x_b (n) | 1.
-__global__ void k_primal_up(Group g, int per_warp) {
-  const int t = warp_task();
+__global__ void k_primal_up(Group g, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
   if (ci.c >= P.nch) return;
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   const int ldr = 2 * n + 1, ldm = m + 2 * n + 1;
   const int rows_max = 2 * n + g.pmax + g.qmax;
   double *Rel = sm, *M = Rel + 2 * n * ldr, *scr = M + rows_max * ldm;
   // identity relation x_{b}' - x_b = 0 on (x_{b}', x_b)
-  for (int idx = lane; idx < n * ldr; idx += 32) {
+  for (int idx = tid; idx < n * ldr; idx += TEAM) {
     int i = idx / ldr, j = idx - i * ldr;
     Rel[idx] = (j == i) ? 1.0 : ((j == n + i) ? -1.0 : 0.0);
   }
-  __syncwarp();
+  tsync();
   int rr = n;
   for (int i = b - 1; i >= a; --i) {
     const StageInfo S = g.st[P.st0 + i];
@@ -98,7 +98,7 @@ __global__ void k_primal_up(Group g, int per_warp) {
     // [L B | L A | R | L c + l]
     wgemm<false, false>(rr, m, n, 1.0, Rel, ldr, B, m, 0.0, M, ldm);
     wgemm<false, false>(rr, n, n, 1.0, Rel, ldr, A, n, 0.0, M + m, ldm);
-    for (int idx = lane; idx < rr * (n + 1); idx += 32) {
+    for (int idx = tid; idx < rr * (n + 1); idx += TEAM) {
       int r = idx / (n + 1), j = idx - r * (n + 1);
       if (j < n) {
         M[r * ldm + m + n + j] = Rel[r * ldr + n + j];
@@ -109,7 +109,7 @@ __global__ void k_primal_up(Group g, int per_warp) {
       }
     }
     // [D | C | 0 | d] and [0 | E | 0 | e]
-    for (int idx = lane; idx < (S.p + S.q) * ldm; idx += 32) {
+    for (int idx = tid; idx < (S.p + S.q) * ldm; idx += TEAM) {
       int r = idx / ldm, j = idx - r * ldm;
       double val = 0.0;
       if (r < S.p) {
@@ -124,16 +124,16 @@ __global__ void k_primal_up(Group g, int per_warp) {
       }
       M[(rr + r) * ldm + j] = val;
     }
-    __syncwarp();
+    tsync();
     const int gs[1] = {m};
     ProjResult pr = wproject(M, ldm, rr + S.p + S.q, 1, gs, 2 * n, g.tau_rank, g.tau_inc, Rel, ldr, scr);
     rr = pr.krank;
-    if (pr.inconsistent && lane == 0) set_status(g, ci.prob, ST_INFEASIBLE_SUFFIX);
-    __syncwarp();
+    if (pr.inconsistent && tid == 0) set_status(g, ci.prob, ST_INFEASIBLE_SUFFIX);
+    tsync();
   }
   double *cs = g.CS[0] + (size_t)t * g.cs_stride;
-  for (int idx = lane; idx < rr * ldr; idx += 32) cs[idx] = Rel[idx];
-  if (lane == 0) {
+  for (int idx = tid; idx < rr * ldr; idx += TEAM) cs[idx] = Rel[idx];
+  if (tid == 0) {
     int *cm = g.CI[0] + (size_t)t * CI_STRIDE;
     cm[CI_ROWS] = rr; cm[CI_NA] = n; cm[CI_NB] = n;
   }
@@ -142,12 +142,12 @@ __global__ void k_primal_up(Group g, int per_warp) {
 // ----------------------------------------------------------- one level of the chunk suffix scan
 // slot t <- slot t o slot t+d when both belong to the same problem, else copied.
 // Works for any endpoint dimensions recorded in the slot ints (primal and dual).
-__global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_warp) {
-  const int t = warp_task();
+__global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
-  const int lane = lane_id();
+  const int tid = team_rank();
   const int ldr = 2 * g.n + 1;
   const double *S1 = g.CS[src] + (size_t)t * g.cs_stride;
   const int *I1 = g.CI[src] + (size_t)t * CI_STRIDE;
@@ -155,18 +155,18 @@ __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_warp
   int *J = g.CI[src ^ 1] + (size_t)t * CI_STRIDE;
   const int r1 = I1[CI_ROWS], na = I1[CI_NA], nb = I1[CI_NB];
   if (ci.c + d > P.nch || nb == 0) {
-    for (int idx = lane; idx < r1 * ldr; idx += 32) Dst[idx] = S1[idx];
-    if (lane == 0) { J[CI_ROWS] = r1; J[CI_NA] = na; J[CI_NB] = nb; }
+    for (int idx = tid; idx < r1 * ldr; idx += TEAM) Dst[idx] = S1[idx];
+    if (tid == 0) { J[CI_ROWS] = r1; J[CI_NA] = na; J[CI_NB] = nb; }
     return;
   }
   const double *S2 = g.CS[src] + (size_t)(t + d) * g.cs_stride;
   const int *I2 = g.CI[src] + (size_t)(t + d) * CI_STRIDE;
   const int r2 = I2[CI_ROWS], nd = I2[CI_NB];
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   const int ldm = nb + na + nd + 1;
   double *M = sm, *scr = sm + (r1 + r2) * ldm;
   // columns: b | a | d | 1
-  for (int idx = lane; idx < (r1 + r2) * ldm; idx += 32) {
+  for (int idx = tid; idx < (r1 + r2) * ldm; idx += TEAM) {
     int r = idx / ldm, j = idx - r * ldm;
     double val = 0.0;
     if (r < r1) {
@@ -182,36 +182,36 @@ __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_warp
     }
     M[idx] = val;
   }
-  __syncwarp();
+  tsync();
   const int gs[1] = {nb};
   ProjResult pr = wproject(M, ldm, r1 + r2, 1, gs, na + nd, g.tau_rank, g.tau_inc, Dst, ldr, scr);
-  if (lane == 0) {
+  if (tid == 0) {
     J[CI_ROWS] = pr.krank; J[CI_NA] = na; J[CI_NB] = nd;
     if (pr.inconsistent) set_status(g, ci.prob, fail_code);
   }
 }
 
 // ----------------------------------------------------------- chunk down-sweep: every X_i
-__global__ void k_primal_down(Group g, int fin, int per_warp) {
-  const int t = warp_task();
+__global__ void k_primal_down(Group g, int fin, int per_task) {
+  const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
   if (ci.c >= P.nch) return;
-  const int n = g.n, m = g.m, lane = lane_id();
+  const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   const int ldh = n + 1, ldr = 2 * n + 1, ldm = m + n + 1;
   const int rows_max = n + g.pmax + g.qmax;
   double *Hs = sm, *M = Hs + n * ldh, *scr = M + rows_max * ldm;
   // X_b from the scan (unary relation held by slot t + 1)
   const double *xb = g.CS[fin] + (size_t)(t + 1) * g.cs_stride;
   int rr = g.CI[fin][(size_t)(t + 1) * CI_STRIDE + CI_ROWS];
-  for (int idx = lane; idx < rr * ldh; idx += 32) {
+  for (int idx = tid; idx < rr * ldh; idx += TEAM) {
     int i = idx / ldh, j = idx - i * ldh;
     Hs[idx] = xb[i * ldr + j];
   }
-  __syncwarp();
+  tsync();
   for (int i = b - 1; i >= a; --i) {
     const int s = P.st0 + i;
     const StageInfo S = g.st[s];
@@ -219,12 +219,12 @@ __global__ void k_primal_down(Group g, int fin, int per_warp) {
     const double *c = g.c + P.oc + (size_t)i * n;
     wgemm<false, false>(rr, m, n, 1.0, Hs, ldh, B, m, 0.0, M, ldm);
     wgemm<false, false>(rr, n, n, 1.0, Hs, ldh, A, n, 0.0, M + m, ldm);
-    for (int r = lane; r < rr; r += 32) {
+    for (int r = tid; r < rr; r += TEAM) {
       double s0 = Hs[r * ldh + n];
       for (int l = 0; l < n; l++) s0 = fma(Hs[r * ldh + l], c[l], s0);
       M[r * ldm + m + n] = s0;
     }
-    for (int idx = lane; idx < (S.p + S.q) * ldm; idx += 32) {
+    for (int idx = tid; idx < (S.p + S.q) * ldm; idx += TEAM) {
       int r = idx / ldm, j = idx - r * ldm;
       double val = 0.0;
       if (r < S.p) {
@@ -239,48 +239,48 @@ __global__ void k_primal_down(Group g, int fin, int per_warp) {
       }
       M[(rr + r) * ldm + j] = val;
     }
-    __syncwarp();
+    tsync();
     const int gs[1] = {m};
     ProjResult pr = wproject(M, ldm, rr + S.p + S.q, 1, gs, n, g.tau_rank, g.tau_inc, Hs, ldh, scr);
     rr = pr.krank;
     double *H = stage_ws(g, s) + g.ws.H;
-    for (int idx = lane; idx < rr * ldh; idx += 32) H[idx] = Hs[idx];
-    if (lane == 0) {
+    for (int idx = tid; idx < rr * ldh; idx += TEAM) H[idx] = Hs[idx];
+    if (tid == 0) {
       stage_wi(g, s)[SI_HROWS] = rr;
       if (pr.inconsistent) set_status(g, ci.prob, ST_INFEASIBLE_SUFFIX);
     }
-    __syncwarp();
+    tsync();
   }
 }
 
 // ----------------------------------------------------------- T_i, t_i, U_i (eq. state-param)
 // QR of H_i^T: Q = [U_i | T_i], U_i spans range(H_i^T), T_i = orthonormal basis
 // of null(H_i); t_i = min-norm solution of H_i t = -h_i; S_i = T_i^T.
-__global__ void k_param(Group g, int per_warp) {
-  const int s = warp_task();
+__global__ void k_param(Group g, int per_task) {
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
-  const int n = g.n, lane = lane_id();
+  const int n = g.n, tid = team_rank();
   double *ws = stage_ws(g, s);
   int *wi = stage_wi(g, s);
   const int r = wi[SI_HROWS];
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   double *Hs = sm, *Wt = Hs + n * (n + 1), *Qf = Wt + n * n, *hb = Qf + n * n, *X = hb + n;
   double *scr = X + n;
   int *perm = (int *)(scr + 4 * n);
   const double *H = ws + g.ws.H;
-  for (int idx = lane; idx < r * (n + 1); idx += 32) Hs[idx] = H[idx];
-  for (int i = lane; i < r; i += 32) hb[i] = H[i * (n + 1) + n];
-  __syncwarp();
+  for (int idx = tid; idx < r * (n + 1); idx += TEAM) Hs[idx] = H[idx];
+  for (int i = tid; i < r; i += TEAM) hb[i] = H[i * (n + 1) + n];
+  tsync();
   const int rank = wtqr(Hs, n + 1, r, n, g.tau_rank, Wt, (r > 0 ? r : 1), Qf, n, perm, scr);
   double *Ys = scr + 2 * n;  // rank x 1
   wtqr_solve(Wt, (r > 0 ? r : 1), Qf, n, perm, r, n, rank, hb, 1, 1, X, 1, Ys, 1);
   double *UT = ws + g.ws.UT, *tt = ws + g.ws.t;
-  for (int idx = lane; idx < n * n; idx += 32) UT[idx] = Qf[idx];
-  for (int i = lane; i < n; i += 32) tt[i] = X[i];
-  if (lane == 0) { wi[SI_UR] = rank; wi[SI_NBAR] = n - rank; }
-  __syncwarp();
+  for (int idx = tid; idx < n * n; idx += TEAM) UT[idx] = Qf[idx];
+  for (int i = tid; i < n; i += TEAM) tt[i] = X[i];
+  if (tid == 0) { wi[SI_UR] = rank; wi[SI_NBAR] = n - rank; }
+  tsync();
   if (S.i == P.N) {
     // terminal cost (eq. terminal-cost-data): Qbar_N = T' Q_N T, qbar_N = T'(Q_N t + q_N)
     const int nb = n - rank;
@@ -289,24 +289,24 @@ __global__ void k_param(Group g, int per_warp) {
     double *T = Qf + rank;  // columns rank.. of Qf, ld n
     wgemm<false, false>(n, nb, n, 1.0, QN, n, T, n, 0.0, QT, n);
     wgemm<true, false>(nb, nb, n, 1.0, T, n, QT, n, 0.0, ws + g.ws.Qb, n);
-    for (int l = lane; l < n; l += 32) {
+    for (int l = tid; l < n; l += TEAM) {
       double s0 = qN[l];
       for (int j = 0; j < n; j++) s0 = fma(QN[l * n + j], X[j], s0);
       Hs[l] = s0;
     }
-    __syncwarp();
+    tsync();
     wgemm<true, false>(nb, 1, n, 1.0, T, n, Hs, 1, 0.0, ws + g.ws.qb, 1);
   }
 }
 
 // ----------------------------------------------------------- stage elimination (Sec. 5)
-__global__ void k_elim(Group g, int per_warp) {
-  const int s = warp_task();
+__global__ void k_elim(Group g, int per_task) {
+  const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
   if (S.i >= P.N) return;
-  const int n = g.n, m = g.m, lane = lane_id(), i = S.i;
+  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);
   int *wi = stage_wi(g, s), *win = stage_wi(g, s + 1);
   const int ur = wi[SI_UR], nb = n - ur, ur1 = win[SI_UR], nn = n - ur1, r1 = win[SI_HROWS];
@@ -319,7 +319,7 @@ __global__ void k_elim(Group g, int per_warp) {
   const double *T = ws + g.ws.UT + ur, *t = ws + g.ws.t;        // ld n
   const double *Tn = wn + g.ws.UT + ur1, *tn = wn + g.ws.t;     // ld n
   const double *Hn = wn + g.ws.H;                                 // ld n + 1
-  double *sm = warp_smem(per_warp);
+  double *sm = team_smem(per_task);
   const int rmax = g.pmax + n;
   double *AT = sm;                       // n x n (ld n)
   double *QT = AT + n * n;               // n x n
@@ -342,20 +342,20 @@ __global__ void k_elim(Group g, int per_warp) {
   int *perm = (int *)(scr + 4 * n + 2 * m + 2 * rmax);
   // A T, A t + c
   wgemm<false, false>(n, nb, n, 1.0, A, n, T, n, 0.0, AT, n);
-  for (int l = lane; l < n; l += 32) {
+  for (int l = tid; l < n; l += TEAM) {
     double s0 = c[l];
     for (int j = 0; j < n; j++) s0 = fma(A[l * n + j], t[j], s0);
     Atc[l] = s0;
   }
-  for (int idx = lane; idx < r1 * (n + 1); idx += 32) Hs[idx] = Hn[idx];
-  __syncwarp();
+  for (int idx = tid; idx < r1 * (n + 1); idx += TEAM) Hs[idx] = Hn[idx];
+  tsync();
   // Gamma = [D; Hn B],  [Phi | gamma] = [C T | C t + d; Hn A T | Hn (A t + c) + hn]
-  for (int idx = lane; idx < S.p * m; idx += 32) {
+  for (int idx = tid; idx < S.p * m; idx += TEAM) {
     int a = idx / m, j = idx - a * m;
     Gm[a * m + j] = g.D[P.oD + (size_t)(S.prow + a) * m + j];
   }
   wgemm<false, false>(r1, m, n, 1.0, Hs, n + 1, B, m, 0.0, Gm + S.p * m, m);
-  for (int idx = lane; idx < S.p * (nb + 1); idx += 32) {
+  for (int idx = tid; idx < S.p * (nb + 1); idx += TEAM) {
     int a = idx / (nb + 1), j = idx - a * (nb + 1);
     const double *Cr = g.C + P.oC + (size_t)(S.prow + a) * n;
     double s0 = 0.0;
@@ -367,7 +367,7 @@ __global__ void k_elim(Group g, int per_warp) {
     }
     Rh[a * (nb + 1) + j] = s0;
   }
-  for (int idx = lane; idx < r1 * (nb + 1); idx += 32) {
+  for (int idx = tid; idx < r1 * (nb + 1); idx += TEAM) {
     int a = idx / (nb + 1), j = idx - a * (nb + 1);
     const double *hr = Hs + a * (n + 1);
     double s0 = 0.0;
@@ -379,98 +379,98 @@ __global__ void k_elim(Group g, int per_warp) {
     }
     Rh[(S.p + a) * (nb + 1) + j] = s0;
   }
-  __syncwarp();
+  tsync();
   // Lemma 4: Z = null(Gamma), [Y | y] = -Gamma^- [Phi | gamma] (min norm)
   const int rank = wtqr(Gm, m, rows, m, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qm, m, perm, scr);
   const double rs = wtqr_solve(Wt, (rows > 0 ? rows : 1), Qm, m, perm, rows, m, rank, Rh, nb + 1, nb + 1,
                                Sol, nb + 1, X1, nb + 1);
-  if (lane == 0 && rs > g.tau_inc) set_status(g, S.prob, ST_RANK_INCONSISTENT);
+  if (tid == 0 && rs > g.tau_inc) set_status(g, S.prob, ST_RANK_INCONSISTENT);
   const int mb = m - rank;
   const double *Z = Qm + rank;  // ld m
   // Y (m x nb, ld n), y (m)
-  for (int idx = lane; idx < m * nb; idx += 32) {
+  for (int idx = tid; idx < m * nb; idx += TEAM) {
     int a = idx / nb, j = idx - a * nb;
     Yw[a * n + j] = Sol[a * (nb + 1) + j];
   }
-  for (int a = lane; a < m; a += 32) ys[a] = Sol[a * (nb + 1) + nb];
-  __syncwarp();
+  for (int a = tid; a < m; a += TEAM) ys[a] = Sol[a * (nb + 1) + nb];
+  tsync();
   // reduced dynamics (eq. reduced-dynamics-data), S_{i+1} = T_{i+1}^T
   wgemm<false, false>(n, nb, m, 1.0, B, m, Yw, n, 1.0, AT, n);            // A T + B Y
   wgemm<true, false>(nn, nb, n, 1.0, Tn, n, AT, n, 0.0, ws + g.ws.Ab, n);
   wgemm<false, false>(n, mb, m, 1.0, B, m, Z, m, 0.0, BZ, m);             // B Z
   wgemm<true, false>(nn, mb, n, 1.0, Tn, n, BZ, m, 0.0, ws + g.ws.Bb, m);
-  for (int l = lane; l < n; l += 32) {
+  for (int l = tid; l < n; l += TEAM) {
     double s0 = Atc[l] - tn[l];
     for (int j = 0; j < m; j++) s0 = fma(B[l * m + j], ys[j], s0);
     cv[l] = s0;
   }
-  __syncwarp();
+  tsync();
   wgemm<true, false>(nn, 1, n, 1.0, Tn, n, cv, 1, 0.0, ws + g.ws.cb, 1);
   // state substitution (eq. state-cost-data)
   wgemm<false, false>(n, nb, n, 1.0, Q, n, T, n, 0.0, QT, n);             // Q T
   double *Qb = ws + g.ws.Qb, *Mb = ws + g.ws.Mb, *Rb = ws + g.ws.Rb;
   wgemm<true, false>(nb, nb, n, 1.0, T, n, QT, n, 0.0, Qb, n);            // Q^z
   wgemm<true, false>(nb, m, n, 1.0, T, n, Mm, m, 0.0, Mz, m);             // M^z
-  for (int l = lane; l < n; l += 32) {
+  for (int l = tid; l < n; l += TEAM) {
     double s0 = q[l];
     for (int j = 0; j < n; j++) s0 = fma(Q[l * n + j], t[j], s0);
     Qtq[l] = s0;
   }
-  for (int a = lane; a < m; a += 32) {
+  for (int a = tid; a < m; a += TEAM) {
     double s0 = r[a];
     for (int l = 0; l < n; l++) s0 = fma(Mm[l * m + a], t[l], s0);
     rz[a] = s0;                                                           // r^z
   }
-  __syncwarp();
+  tsync();
   wgemm<true, false>(nb, 1, n, 1.0, T, n, Qtq, 1, 0.0, qz, 1);            // q^z
   // reduced cost (eq. reduced-cost-data)
   wgemm<false, false>(m, nb, m, 1.0, R, m, Yw, n, 0.0, RY, n);            // R Y
   wgemm<false, false>(m, mb, m, 1.0, R, m, Z, m, 0.0, RZ, m);             // R Z
-  for (int a = lane; a < m; a += 32) {
+  for (int a = tid; a < m; a += TEAM) {
     double s0 = rz[a];
     for (int j = 0; j < m; j++) s0 = fma(R[a * m + j], ys[j], s0);
     Ry[a] = s0;                                                           // R y + r^z
   }
-  __syncwarp();
+  tsync();
   wgemm<false, false>(nb, nb, m, 1.0, Mz, m, Yw, n, 0.0, X2, n);          // M^z Y
-  for (int idx = lane; idx < nb * nb; idx += 32) {
+  for (int idx = tid; idx < nb * nb; idx += TEAM) {
     int a = idx / nb, j = idx - a * nb;
     Qb[a * n + j] += X2[a * n + j] + X2[j * n + a];
   }
-  __syncwarp();
+  tsync();
   wgemm<true, false>(nb, nb, m, 1.0, Yw, n, RY, n, 1.0, Qb, n);           // + Y' R Y
   wgemm<false, false>(nb, mb, m, 1.0, Mz, m, Z, m, 0.0, Mb, m);           // M^z Z
   wgemm<true, false>(nb, mb, m, 1.0, Yw, n, RZ, m, 1.0, Mb, m);           // + Y' R Z
   wgemm<true, false>(mb, mb, m, 1.0, Z, m, RZ, m, 0.0, Rb, m);            // Z' R Z
   double *qb = ws + g.ws.qb, *rb = ws + g.ws.rb;
-  for (int a = lane; a < nb; a += 32) {
+  for (int a = tid; a < nb; a += TEAM) {
     double s0 = qz[a];
     for (int j = 0; j < m; j++) s0 = fma(Mz[a * m + j], ys[j], s0);
     for (int j = 0; j < m; j++) s0 = fma(Yw[j * n + a], Ry[j], s0);
     qb[a] = s0;
   }
-  for (int a = lane; a < mb; a += 32) {
+  for (int a = tid; a < mb; a += TEAM) {
     double s0 = 0.0;
     for (int j = 0; j < m; j++) s0 = fma(Z[j * m + a], Ry[j], s0);
     rb[a] = s0;
   }
   // Y, Z, y for recovery (eq. recovery-maps)
   double *Yo = ws + g.ws.Y, *Zo = ws + g.ws.Z, *yo = ws + g.ws.y;
-  for (int idx = lane; idx < m * n; idx += 32) Yo[idx] = Yw[idx];
-  for (int idx = lane; idx < m * m; idx += 32) {
+  for (int idx = tid; idx < m * n; idx += TEAM) Yo[idx] = Yw[idx];
+  for (int idx = tid; idx < m * m; idx += TEAM) {
     int a = idx / m, j = idx - a * m;
     Zo[idx] = (j < mb) ? Z[a * m + j] : 0.0;
   }
-  for (int a = lane; a < m; a += 32) yo[a] = ys[a];
-  if (lane == 0) wi[SI_MBAR] = mb;
-  __syncwarp();
+  for (int a = tid; a < m; a += TEAM) yo[a] = ys[a];
+  if (tid == 0) wi[SI_MBAR] = mb;
+  tsync();
   // square root of the reduced stage Hessian [[Qbar, Mbar], [Mbar', Rbar]] (order z, v):
   // L L' = H, stored as L' (upper) with l = L^{-1} [qbar; rbar], for the square-root LQR
   {
     const int kh = nb + mb, ldh = n + m;
     double *Hh = (double *)(perm + rmax + 2);  // past the permutation scratch
     Hh = (double *)(((uintptr_t)Hh + 7) & ~(uintptr_t)7);
-    for (int idx = lane; idx < kh * kh; idx += 32) {
+    for (int idx = tid; idx < kh * kh; idx += TEAM) {
       int a = idx / kh, j = idx - a * kh;
       double h;
       if (a < nb && j < nb) h = Qb[a * n + j];
@@ -479,16 +479,16 @@ __global__ void k_elim(Group g, int per_warp) {
       else h = Rb[(a - nb) * m + (j - nb)];
       Hh[idx] = h;
     }
-    __syncwarp();
+    tsync();
     const int fail = wcholesky(Hh, kh, kh);
-    if (fail && lane == 0) set_status(g, S.prob, ST_NONCONVEX);
+    if (fail && tid == 0) set_status(g, S.prob, ST_NONCONVEX);
     double *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
-    for (int idx = lane; idx < kh * kh; idx += 32) {
+    for (int idx = tid; idx < kh * kh; idx += TEAM) {
       int a = idx / kh, j = idx - a * kh;
       LT[a * ldh + j] = Hh[j * kh + a];
     }
-    // l = L^{-1} [qbar; rbar] (one lane, small)
-    if (lane == 0) {
+    // l = L^{-1} [qbar; rbar] (one tid, small)
+    if (tid == 0) {
       for (int a = 0; a < kh; a++) {
         double s0 = (a < nb) ? qb[a] : rb[a - nb];
         for (int l = 0; l < a; l++) s0 = fma(-Hh[a * kh + l], lt[l], s0);

@@ -5,7 +5,7 @@
 
 namespace eclqr {
 
-// shared memory per warp, in doubles
+// shared memory per task, in doubles
 __host__ int smem_primal_sweep(int n, int m, int pmax, int qmax);
 __host__ int smem_rel_level(int n, int pmax, int qmax);
 __host__ int smem_param(int n);
@@ -19,35 +19,35 @@ __host__ int smem_dual_sweep(int n, int m, int pmax, int qmax);
 __host__ int smem_dual_leaf(int n, int m, int pmax, int qmax);
 
 // primal scan and elimination (k_primal.cu)
-__global__ void k_terminal(Group g, int per_warp);
-__global__ void k_primal_up(Group g, int per_warp);
-__global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_warp);
-__global__ void k_primal_down(Group g, int fin, int per_warp);
-__global__ void k_param(Group g, int per_warp);
-__global__ void k_elim(Group g, int per_warp);
+__global__ void k_terminal(Group g, int per_task);
+__global__ void k_primal_up(Group g, int per_task);
+__global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task);
+__global__ void k_primal_down(Group g, int fin, int per_task);
+__global__ void k_param(Group g, int per_task);
+__global__ void k_elim(Group g, int per_task);
 
 // reduced LQR, affine chains, recovery (k_lqr.cu)
 enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_SLIN_ = 2, AFF_NU_ = 3 };
-__global__ void k_lqr_up(Group g, int per_warp);
-__global__ void k_lqr_level(Group g, int src, int d, int per_warp);
-__global__ void k_riccati_down(Group g, int fin, int per_warp);
-__global__ void k_aff_up(Group g, int mode, int per_warp);
-__global__ void k_aff_level(Group g, int src, int d, int fwd, int per_warp);
-__global__ void k_aff_down(Group g, int mode, int fin, int per_warp);
+__global__ void k_lqr_up(Group g, int per_task);
+__global__ void k_lqr_level(Group g, int src, int d, int per_task);
+__global__ void k_riccati_down(Group g, int fin, int per_task);
+__global__ void k_aff_up(Group g, int mode, int per_task);
+__global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task);
+__global__ void k_aff_down(Group g, int mode, int fin, int per_task);
 __global__ void k_solve_init(Group g, const double *s0);
 __global__ void k_post_roll(Group g, int corr);
-__global__ void k_resid(Group g, int per_warp);
-__global__ void k_scorr(Group g, int per_warp);
+__global__ void k_resid(Group g, int per_task);
+__global__ void k_scorr(Group g, int per_task);
 __global__ void k_recover(Group g, double *x, double *u);
 __global__ void k_dims(Group g, int *nbar, int *mbar);
 
 // multipliers and residual (k_dual.cu)
-__global__ void k_dual_stage(Group g, const double *x, const double *u, int per_warp);
-__global__ void k_dual_terminal(Group g, int per_warp);
-__global__ void k_dual_up(Group g, int per_warp);
-__global__ void k_dual_down(Group g, int fin, int per_warp);
-__global__ void k_dual_root(Group g, int per_warp);
-__global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_warp);
+__global__ void k_dual_stage(Group g, const double *x, const double *u, int per_task);
+__global__ void k_dual_terminal(Group g, int per_task);
+__global__ void k_dual_up(Group g, int per_task);
+__global__ void k_dual_down(Group g, int fin, int per_task);
+__global__ void k_dual_root(Group g, int per_task);
+__global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task);
 __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const double *u, const double *lam,
                                const double *mu, const double *eta, const double *alpha, double *resid);
 

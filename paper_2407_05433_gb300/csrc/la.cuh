@@ -1,11 +1,14 @@
-// la.cuh -- warp-level FP64 dense linear algebra on small matrices held in
-// shared memory.  Every routine is called by all 32 lanes of one warp, with
-// the warp converged; matrices are row-major with explicit leading dimensions.
+// la.cuh -- FP64 dense linear algebra on small matrices held in shared
+// memory, executed by a team: all threads of one CTA work on one task.  Every
+// routine is called by the whole team, converged; matrices are row-major with
+// explicit leading dimensions.
 //
-// Cost model on sm_103a: an FP64 instruction occupies the SM sub-partition's
-// FP64 pipe for the whole warp whatever its active mask, so loops hand each
-// lane an independent output element (element-parallel updates, lane-per-
-// column dot products) instead of reducing across lanes wherever possible.
+// Cost model on sm_103a: an FP64 instruction occupies its SM sub-partition's
+// FP64 pipe for the whole warp whatever its active mask, and each of the four
+// sub-partitions has its own pipe.  A team of four warps therefore has four
+// times the FP64 issue rate of one warp; loops hand each thread an independent
+// output element (element-parallel updates, thread-per-column dot products)
+// instead of reducing across threads wherever possible.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -14,7 +17,10 @@ namespace eclqr {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+// rank of the calling thread in its team, the team size, and the team barrier
+__device__ __forceinline__ int team_rank() { return threadIdx.x; }
+#define TEAM ((int)blockDim.x)
+__device__ __forceinline__ void tsync() { __syncthreads(); }
 
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
@@ -31,30 +37,73 @@ __device__ __forceinline__ double warp_sum(double v) {
 // arg-max over non-negative values; ties resolve to the lowest index.  The
 // bit pattern of a non-negative double orders like the value, so the
 // comparison runs on the integer pipe.
-__device__ __forceinline__ void warp_argmax(double v, int idx, double &bv, int &bi) {
-  long long key = __double_as_longlong(v);
+__device__ __forceinline__ void warp_argmax(long long &key, int &idx) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     long long k2 = __shfl_xor_sync(kFull, key, o);
     int i2 = __shfl_xor_sync(kFull, idx, o);
     if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
   }
+}
+
+// Team reductions: warp shuffles, then one partial per warp through shared
+// memory.  The trailing barrier lets the next reduction reuse the slots.
+__device__ __forceinline__ double team_max(double v) {
+  __shared__ double red_max[32];
+  v = warp_max(v);
+  if ((threadIdx.x & 31) == 0) red_max[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = red_max[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) r = fmax(r, red_max[w]);
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double team_sum(double v) {
+  __shared__ double red_sum[32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red_sum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = red_sum[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) r += red_sum[w];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void team_argmax(double v, int idx, double &bv, int &bi) {
+  __shared__ long long red_key[32];
+  __shared__ int red_idx[32];
+  long long key = __double_as_longlong(v);
+  warp_argmax(key, idx);
+  if ((threadIdx.x & 31) == 0) {
+    red_key[threadIdx.x >> 5] = key;
+    red_idx[threadIdx.x >> 5] = idx;
+  }
+  __syncthreads();
+  key = red_key[0];
+  idx = red_idx[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+    const long long k2 = red_key[w];
+    const int i2 = red_idx[w];
+    if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+  }
+  __syncthreads();
   bv = __longlong_as_double(key);
   bi = idx;
 }
 
 __device__ __forceinline__ void wzero(double *p, int n) {
-  for (int i = lane_id(); i < n; i += 32) p[i] = 0.0;
-  __syncwarp();
+  for (int i = team_rank(); i < n; i += TEAM) p[i] = 0.0;
+  tsync();
 }
 
 __device__ __forceinline__ void wcopy(double *dst, int ldd, const double *src, int lds, int rows,
                                       int cols) {
-  for (int idx = lane_id(); idx < rows * cols; idx += 32) {
+  for (int idx = team_rank(); idx < rows * cols; idx += TEAM) {
     int i = idx / cols, j = idx - i * cols;
     dst[i * ldd + j] = src[i * lds + j];
   }
-  __syncwarp();
+  tsync();
 }
 
 // C (m x n) = alpha * op(A) op(B) + beta * C; op(A) is m x k, op(B) is k x n.
@@ -62,7 +111,7 @@ __device__ __forceinline__ void wcopy(double *dst, int ldd, const double *src, i
 template <bool TA, bool TB>
 static __device__ void wgemm(int m, int n, int k, double alpha, const double *A, int lda, const double *B,
                       int ldb, double beta, double *C, int ldc) {
-  for (int idx = lane_id(); idx < m * n; idx += 32) {
+  for (int idx = team_rank(); idx < m * n; idx += TEAM) {
     int i = idx / n, j = idx - i * n;
     double s0 = 0.0, s1 = 0.0;
     int l = 0;
@@ -82,7 +131,7 @@ static __device__ void wgemm(int m, int n, int k, double alpha, const double *A,
     double s = alpha * (s0 + s1);
     C[i * ldc + j] = (beta == 0.0) ? s : fma(beta, C[i * ldc + j], s);
   }
-  __syncwarp();
+  tsync();
 }
 
 // ---------------------------------------------------------------------------
@@ -98,7 +147,7 @@ static __device__ void wgemm(int m, int n, int k, double alpha, const double *A,
 // On return rows [k0, k0 + krank) hold the kept relation in the kept columns
 // (upper-trapezoidal in pivot order); they are also written, each renormalised
 // to unit coefficient norm, to out (krank x (nkeep + 1), ldo) when out != 0.
-// scr: >= 2 * nc + r + nc/2 + 1 doubles of scratch private to the warp.
+// scr: >= 2 * nc + r + nc/2 + 1 doubles of scratch private to the task.
 // ---------------------------------------------------------------------------
 struct ProjResult {
   int grank[3];
@@ -110,7 +159,7 @@ struct ProjResult {
 static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const int *gsz, int nkeep,
                                double tau_rank, double tau_inc, double *out, int ldo,
                                double *scr) {
-  const int lane = lane_id();
+  const int tid = team_rank();
   int ncoef = nkeep;
   for (int g = 0; g < ng; g++) ncoef += gsz[g];
   const int nc = ncoef + 1, off = ncoef;
@@ -124,7 +173,7 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
   res.inconsistent = 0;
 
   // row scaling
-  for (int i = lane; i < r; i += 32) {
+  for (int i = tid; i < r; i += TEAM) {
     double s0 = 0.0, s1 = 0.0;
     int j = 0;
     for (; j + 1 < ncoef; j += 2) {
@@ -139,11 +188,11 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
       for (j = 0; j < nc; j++) M[i * ld + j] *= inv;
     }
   }
-  for (int j = lane; j < nc; j += 32) done[j] = 0;
-  __syncwarp();
+  for (int j = tid; j < nc; j += TEAM) done[j] = 0;
+  tsync();
   // nu and omega
   double nu = 0.0, om = 0.0;
-  for (int j = lane; j < ncoef; j += 32) {
+  for (int j = tid; j < ncoef; j += TEAM) {
     double s0 = 0.0, s1 = 0.0;
     int i = 0;
     for (; i + 1 < r; i += 2) {
@@ -153,9 +202,9 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
     if (i < r) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
     nu = fmax(nu, s0 + s1);
   }
-  for (int i = lane; i < r; i += 32) om = fmax(om, fabs(M[i * ld + off]));
-  nu = sqrt(warp_max(nu));
-  om = fmax(1.0, warp_max(om));
+  for (int i = tid; i < r; i += TEAM) om = fmax(om, fabs(M[i * ld + off]));
+  nu = sqrt(team_max(nu));
+  om = fmax(1.0, team_max(om));
   const double thr = tau_rank * nu;
 
   int k = 0, c0 = 0;
@@ -165,7 +214,7 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
     while (k < r) {
       double mybest = -1.0;
       int mypiv = 0x7fffffff;
-      for (int j = c0 + lane; j < c1; j += 32) {
+      for (int j = c0 + tid; j < c1; j += TEAM) {
         if (done[j]) continue;
         double s0 = 0.0, s1 = 0.0;
         int i = k;
@@ -179,16 +228,16 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
       }
       double best2;
       int piv;
-      warp_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, best2, piv);
+      team_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, best2, piv);
       if (piv == 0x7fffffff) break;
       const double best = sqrt(best2);
       if (!(best > thr)) break;
       const double xk = M[k * ld + piv];
       const double sg = xk >= 0.0 ? 1.0 : -1.0;
-      for (int i = k + lane; i < r; i += 32) v[i] = (i == k) ? xk + sg * best : M[i * ld + piv];
+      for (int i = k + tid; i < r; i += TEAM) v[i] = (i == k) ? xk + sg * best : M[i * ld + piv];
       const double beta = 1.0 / (best * (best + fabs(xk)));
-      __syncwarp();
-      for (int j = lane; j < nc; j += 32) {
+      tsync();
+      for (int j = tid; j < nc; j += TEAM) {
         if (done[j] || j == piv) continue;
         double s0 = 0.0, s1 = 0.0;
         int i = k;
@@ -199,17 +248,17 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
         if (i < r) s0 = fma(v[i], M[i * ld + j], s0);
         w[j] = beta * (s0 + s1);
       }
-      __syncwarp();
+      tsync();
       const int rows = r - k;
-      for (int idx = lane; idx < rows * nc; idx += 32) {
+      for (int idx = tid; idx < rows * nc; idx += TEAM) {
         int i = k + idx / nc, j = idx % nc;
         if (done[j] || j == piv) continue;
         M[i * ld + j] = fma(-w[j], v[i], M[i * ld + j]);
       }
-      __syncwarp();
-      for (int i = k + lane; i < r; i += 32) M[i * ld + piv] = (i == k) ? -sg * best : 0.0;
-      if (lane == 0) done[piv] = 1;
-      __syncwarp();
+      tsync();
+      for (int i = k + tid; i < r; i += TEAM) M[i * ld + piv] = (i == k) ? -sg * best : 0.0;
+      if (tid == 0) done[piv] = 1;
+      tsync();
       k++;
       rk++;
     }
@@ -218,12 +267,12 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
   }
   res.k0 = k - res.krank;
   int bad = 0;
-  for (int i = k + lane; i < r; i += 32)
+  for (int i = k + tid; i < r; i += TEAM)
     if (fabs(M[i * ld + off]) > tau_inc * om) bad = 1;
-  res.inconsistent = __any_sync(kFull, bad);
+  res.inconsistent = __syncthreads_or(bad);
   if (out) {
     const int kc0 = ncoef - nkeep;
-    for (int a = lane; a < res.krank; a += 32) {
+    for (int a = tid; a < res.krank; a += TEAM) {
       const double *row = M + (res.k0 + a) * ld;
       double s = 0.0;
       for (int j = 0; j < nkeep; j++) s = fma(row[kc0 + j], row[kc0 + j], s);
@@ -232,7 +281,7 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
       out[a * ldo + nkeep] = row[off] * inv;
     }
   }
-  __syncwarp();
+  tsync();
   return res;
 }
 
@@ -246,83 +295,83 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
 // ---------------------------------------------------------------------------
 static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_rank, double *W, int ldw,
                     double *Q, int ldq, int *perm, double *scr /* >= nk + max(nk, rk) */) {
-  const int lane = lane_id();
+  const int tid = team_rank();
   double *v = scr, *w = scr + nk;
-  for (int idx = lane; idx < nk * rk; idx += 32) {
+  for (int idx = tid; idx < nk * rk; idx += TEAM) {
     int i = idx / rk, j = idx - i * rk;
     W[i * ldw + j] = K[j * ldk + i];
   }
-  for (int idx = lane; idx < nk * nk; idx += 32) {
+  for (int idx = tid; idx < nk * nk; idx += TEAM) {
     int i = idx / nk, j = idx - i * nk;
     Q[i * ldq + j] = (i == j) ? 1.0 : 0.0;
   }
-  for (int j = lane; j < rk; j += 32) perm[j] = j;
-  __syncwarp();
+  for (int j = tid; j < rk; j += TEAM) perm[j] = j;
+  tsync();
   double nu = 0.0;
-  for (int j = lane; j < rk; j += 32) {
+  for (int j = tid; j < rk; j += TEAM) {
     double s = 0.0;
     for (int i = 0; i < nk; i++) s = fma(W[i * ldw + j], W[i * ldw + j], s);
     nu = fmax(nu, s);
   }
-  nu = sqrt(warp_max(nu));
+  nu = sqrt(team_max(nu));
   const double thr = tau_rank * nu;
   int rank = 0;
   for (int s = 0; s < rk && s < nk; s++) {
     double mybest = -1.0;
     int mypiv = 0x7fffffff;
-    for (int j = s + lane; j < rk; j += 32) {
+    for (int j = s + tid; j < rk; j += TEAM) {
       double t = 0.0;
       for (int i = s; i < nk; i++) t = fma(W[i * ldw + j], W[i * ldw + j], t);
       if (t > mybest) { mybest = t; mypiv = j; }
     }
     double b2;
     int piv;
-    warp_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
+    team_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
     if (piv == 0x7fffffff) break;
     const double best = sqrt(b2);
     if (!(best > thr)) break;
     if (piv != s) {
-      for (int i = lane; i < nk; i += 32) {
+      for (int i = tid; i < nk; i += TEAM) {
         double t = W[i * ldw + s];
         W[i * ldw + s] = W[i * ldw + piv];
         W[i * ldw + piv] = t;
       }
-      if (lane == 0) {
+      if (tid == 0) {
         int t = perm[s]; perm[s] = perm[piv]; perm[piv] = t;
       }
-      __syncwarp();
+      tsync();
     }
     const double xk = W[s * ldw + s];
     const double sg = xk >= 0.0 ? 1.0 : -1.0;
-    for (int i = s + lane; i < nk; i += 32) v[i] = (i == s) ? xk + sg * best : W[i * ldw + s];
+    for (int i = s + tid; i < nk; i += TEAM) v[i] = (i == s) ? xk + sg * best : W[i * ldw + s];
     const double beta = 1.0 / (best * (best + fabs(xk)));
-    __syncwarp();
+    tsync();
     // W columns > s
-    for (int j = s + 1 + lane; j < rk; j += 32) {
+    for (int j = s + 1 + tid; j < rk; j += TEAM) {
       double t = 0.0;
       for (int i = s; i < nk; i++) t = fma(v[i], W[i * ldw + j], t);
       w[j] = beta * t;
     }
-    __syncwarp();
+    tsync();
     const int cols = rk - s - 1, rows = nk - s;
-    for (int idx = lane; idx < rows * cols; idx += 32) {
+    for (int idx = tid; idx < rows * cols; idx += TEAM) {
       int i = s + idx / cols, j = s + 1 + idx % cols;
       W[i * ldw + j] = fma(-w[j], v[i], W[i * ldw + j]);
     }
-    __syncwarp();
-    for (int i = s + lane; i < nk; i += 32) W[i * ldw + s] = (i == s) ? -sg * best : 0.0;
+    tsync();
+    for (int i = s + tid; i < nk; i += TEAM) W[i * ldw + s] = (i == s) ? -sg * best : 0.0;
     // Q <- Q H on columns [s, nk)
-    for (int i = lane; i < nk; i += 32) {
+    for (int i = tid; i < nk; i += TEAM) {
       double t = 0.0;
       for (int l = s; l < nk; l++) t = fma(Q[i * ldq + l], v[l], t);
       w[i] = beta * t;
     }
-    __syncwarp();
-    for (int idx = lane; idx < nk * rows; idx += 32) {
+    tsync();
+    for (int idx = tid; idx < nk * rows; idx += TEAM) {
       int i = idx / rows, l = s + idx % rows;
       Q[i * ldq + l] = fma(-w[i], v[l], Q[i * ldq + l]);
     }
-    __syncwarp();
+    tsync();
     rank++;
   }
   return rank;
@@ -335,15 +384,15 @@ static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_
 static __device__ double wtqr_solve(const double *W, int ldw, const double *Q, int ldq, const int *perm,
                              int rk, int nk, int rank, const double *B, int ldb, int nb, double *X,
                              int ldx, double *Y, int ldy) {
-  const int lane = lane_id();
+  const int tid = team_rank();
   double bmax = 0.0;
-  for (int idx = lane; idx < rk * nb; idx += 32) {
+  for (int idx = tid; idx < rk * nb; idx += TEAM) {
     int i = idx / nb, j = idx - i * nb;
     bmax = fmax(bmax, fabs(B[i * ldb + j]));
   }
-  bmax = fmax(1.0, warp_max(bmax));
+  bmax = fmax(1.0, team_max(bmax));
   double rmax = 0.0;
-  for (int c = lane; c < nb; c += 32) {
+  for (int c = tid; c < nb; c += TEAM) {
     for (int i = 0; i < rank; i++) {
       double s = B[perm[i] * ldb + c];
       for (int l = 0; l < i; l++) s = fma(-W[l * ldw + i], Y[l * ldy + c], s);
@@ -355,21 +404,21 @@ static __device__ double wtqr_solve(const double *W, int ldw, const double *Q, i
       rmax = fmax(rmax, fabs(s));
     }
   }
-  __syncwarp();
-  for (int idx = lane; idx < nk * nb; idx += 32) {
+  tsync();
+  for (int idx = tid; idx < nk * nb; idx += TEAM) {
     int i = idx / nb, c = idx - i * nb;
     double s = 0.0;
     for (int l = 0; l < rank; l++) s = fma(Q[i * ldq + l], Y[l * ldy + c], s);
     X[i * ldx + c] = -s;
   }
-  __syncwarp();
-  return warp_max(rmax) / bmax;
+  tsync();
+  return team_max(rmax) / bmax;
 }
 
 // In-place Cholesky L L^T of an SPD n x n matrix (lower triangle, upper set
 // to zero).  Returns 0 on success, 1 if a pivot is not positive.
 static __device__ int wcholesky(double *Hm, int ld, int n) {
-  const int lane = lane_id();
+  const int tid = team_rank();
   int fail = 0;
   for (int j = 0; j < n; j++) {
     // diagonal
@@ -378,24 +427,24 @@ static __device__ int wcholesky(double *Hm, int ld, int n) {
     if (!(s > 0.0)) fail = 1;
     const double d = sqrt(fmax(s, 1e-300));
     const double inv = 1.0 / d;
-    for (int i = j + 1 + lane; i < n; i += 32) {
+    for (int i = j + 1 + tid; i < n; i += TEAM) {
       double t = Hm[i * ld + j];
       for (int l = 0; l < j; l++) t = fma(-Hm[i * ld + l], Hm[j * ld + l], t);
       Hm[i * ld + j] = t * inv;
     }
-    __syncwarp();
-    if (lane == 0) {
+    tsync();
+    if (tid == 0) {
       Hm[j * ld + j] = d;
       for (int i = 0; i < j; i++) Hm[i * ld + j] = 0.0;
     }
-    __syncwarp();
+    tsync();
   }
   return fail;
 }
 
 // Solve (L L^T) X = B in place, B n x nb (ld ldb); lanes over right-hand sides.
 static __device__ void wchol_solve(const double *L, int ldl, int n, double *B, int ldb, int nb) {
-  for (int c = lane_id(); c < nb; c += 32) {
+  for (int c = team_rank(); c < nb; c += TEAM) {
     for (int i = 0; i < n; i++) {
       double s = B[i * ldb + c];
       for (int l = 0; l < i; l++) s = fma(-L[i * ldl + l], B[l * ldb + c], s);
@@ -407,39 +456,39 @@ static __device__ void wchol_solve(const double *L, int ldl, int n, double *B, i
       B[i * ldb + c] = s / L[i * ldl + i];
     }
   }
-  __syncwarp();
+  tsync();
 }
 
 // In-place LU with partial pivoting of an n x n matrix; piv: n ints.
 static __device__ void wlu(double *A, int ld, int n, int *piv) {
-  const int lane = lane_id();
+  const int tid = team_rank();
   for (int j = 0; j < n; j++) {
     double mybest = -1.0;
     int myi = 0x7fffffff;
-    for (int i = j + lane; i < n; i += 32) {
+    for (int i = j + tid; i < n; i += TEAM) {
       double a = fabs(A[i * ld + j]);
       if (a > mybest) { mybest = a; myi = i; }
     }
     double b;
     int p;
-    warp_argmax(mybest < 0.0 ? 0.0 : mybest, myi, b, p);
+    team_argmax(mybest < 0.0 ? 0.0 : mybest, myi, b, p);
     if (p == 0x7fffffff) p = j;
     if (p != j) {
-      for (int c = lane; c < n; c += 32) {
+      for (int c = tid; c < n; c += TEAM) {
         double t = A[j * ld + c]; A[j * ld + c] = A[p * ld + c]; A[p * ld + c] = t;
       }
     }
-    if (lane == 0) piv[j] = p;
-    __syncwarp();
+    if (tid == 0) piv[j] = p;
+    tsync();
     const double inv = 1.0 / A[j * ld + j];
-    for (int i = j + 1 + lane; i < n; i += 32) A[i * ld + j] *= inv;
-    __syncwarp();
+    for (int i = j + 1 + tid; i < n; i += TEAM) A[i * ld + j] *= inv;
+    tsync();
     const int rows = n - j - 1, cols = n - j - 1;
-    for (int idx = lane; idx < rows * cols; idx += 32) {
+    for (int idx = tid; idx < rows * cols; idx += TEAM) {
       int i = j + 1 + idx / cols, c = j + 1 + idx % cols;
       A[i * ld + c] = fma(-A[i * ld + j], A[j * ld + c], A[i * ld + c]);
     }
-    __syncwarp();
+    tsync();
   }
 }
 
@@ -447,7 +496,7 @@ static __device__ void wlu(double *A, int ld, int n, int *piv) {
 // n x nb, overwritten with X; lanes over right-hand sides.
 static __device__ void wlu_solve(const double *LU, int ld, int n, const int *piv, double *B, int ldb, int nb,
                           int trans) {
-  for (int c = lane_id(); c < nb; c += 32) {
+  for (int c = team_rank(); c < nb; c += TEAM) {
     if (!trans) {
       for (int i = 0; i < n; i++)
         if (piv[i] != i) { double t = B[i * ldb + c]; B[i * ldb + c] = B[piv[i] * ldb + c]; B[piv[i] * ldb + c] = t; }
@@ -477,7 +526,7 @@ static __device__ void wlu_solve(const double *LU, int ld, int n, const int *piv
         if (piv[i] != i) { double t = B[i * ldb + c]; B[i * ldb + c] = B[piv[i] * ldb + c]; B[piv[i] * ldb + c] = t; }
     }
   }
-  __syncwarp();
+  tsync();
 }
 
 }  // namespace eclqr
@@ -512,13 +561,13 @@ struct LseResult {
 static __device__ void whouse_apply(double *M, int ld, int r0, int r1, int piv, int c0, int c1, const int *done,
                                     double *v, double *w, double nrm) {
   // reflector from column piv on rows [r0, r1) applied to columns [c0, c1) not done (piv excluded)
-  const int lane = lane_id();
+  const int tid = team_rank();
   const double xk = M[r0 * ld + piv];
   const double sg = xk >= 0.0 ? 1.0 : -1.0;
-  for (int i = r0 + lane; i < r1; i += 32) v[i] = (i == r0) ? xk + sg * nrm : M[i * ld + piv];
+  for (int i = r0 + tid; i < r1; i += TEAM) v[i] = (i == r0) ? xk + sg * nrm : M[i * ld + piv];
   const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
-  __syncwarp();
-  for (int j = c0 + lane; j < c1; j += 32) {
+  tsync();
+  for (int j = c0 + tid; j < c1; j += TEAM) {
     if ((done && done[j]) || j == piv) continue;
     double s0 = 0.0, s1 = 0.0;
     int i = r0;
@@ -529,16 +578,16 @@ static __device__ void whouse_apply(double *M, int ld, int r0, int r1, int piv, 
     if (i < r1) s0 = fma(v[i], M[i * ld + j], s0);
     w[j] = beta * (s0 + s1);
   }
-  __syncwarp();
+  tsync();
   const int rows = r1 - r0, cols = c1 - c0;
-  for (int idx = lane; idx < rows * cols; idx += 32) {
+  for (int idx = tid; idx < rows * cols; idx += TEAM) {
     int i = r0 + idx / cols, j = c0 + idx % cols;
     if ((done && done[j]) || j == piv) continue;
     M[i * ld + j] = fma(-w[j], v[i], M[i * ld + j]);
   }
-  __syncwarp();
-  for (int i = r0 + lane; i < r1; i += 32) M[i * ld + piv] = (i == r0) ? -sg * nrm : 0.0;
-  __syncwarp();
+  tsync();
+  for (int i = r0 + tid; i < r1; i += TEAM) M[i * ld + piv] = (i == r0) ? -sg * nrm : 0.0;
+  tsync();
 }
 
 // pivot search: largest column norm (squared) among columns [c0, c1) not done over rows [r0, r1)
@@ -546,7 +595,7 @@ static __device__ void wpivot(const double *M, int ld, int r0, int r1, int c0, i
                               double &best, int &piv) {
   double mybest = -1.0;
   int mypiv = 0x7fffffff;
-  for (int j = c0 + lane_id(); j < c1; j += 32) {
+  for (int j = c0 + team_rank(); j < c1; j += TEAM) {
     if (done && done[j]) continue;
     double s0 = 0.0, s1 = 0.0;
     int i = r0;
@@ -559,13 +608,13 @@ static __device__ void wpivot(const double *M, int ld, int r0, int r1, int c0, i
     if (s > mybest) { mybest = s; mypiv = j; }
   }
   double b2;
-  warp_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
+  team_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
   best = sqrt(b2);
 }
 
 static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne, int nk, double tau_rank,
                                       double tau_inc, double *outC, double *outQ, int ldo, double *scr) {
-  const int lane = lane_id();
+  const int tid = team_rank();
   const int nc = ne + nk + 1, off = ne + nk, r = rc + rq;
   double *v = scr;
   double *w = v + r;
@@ -574,7 +623,7 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
   LseResult res;
   res.k1 = res.k2 = res.kc = res.kq = res.inconsistent = 0;
   // scale constraint rows to unit coefficient norm
-  for (int i = lane; i < rc; i += 32) {
+  for (int i = tid; i < rc; i += TEAM) {
     double s = 0.0;
     for (int j = 0; j < off; j++) s = fma(M[i * ld + j], M[i * ld + j], s);
     if (s > 0.0) {
@@ -582,17 +631,17 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
       for (int j = 0; j < nc; j++) M[i * ld + j] *= inv;
     }
   }
-  for (int j = lane; j < nc; j += 32) done[j] = 0;
-  __syncwarp();
+  for (int j = tid; j < nc; j += TEAM) done[j] = 0;
+  tsync();
   double nu = 0.0, om = 0.0;
-  for (int j = lane; j < off; j += 32) {
+  for (int j = tid; j < off; j += TEAM) {
     double s = 0.0;
     for (int i = 0; i < rc; i++) s = fma(M[i * ld + j], M[i * ld + j], s);
     nu = fmax(nu, s);
   }
-  for (int i = lane; i < rc; i += 32) om = fmax(om, fabs(M[i * ld + off]));
-  nu = sqrt(warp_max(nu));
-  om = fmax(1.0, warp_max(om));
+  for (int i = tid; i < rc; i += TEAM) om = fmax(om, fabs(M[i * ld + off]));
+  nu = sqrt(team_max(nu));
+  om = fmax(1.0, team_max(om));
   const double thr = tau_rank * nu;
   // A
   int k = 0;
@@ -602,8 +651,8 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
     wpivot(M, ld, k, rc, 0, ne, done, best, piv);
     if (piv == 0x7fffffff || !(best > thr)) break;
     whouse_apply(M, ld, k, rc, piv, 0, nc, done, v, w, best);
-    if (lane == 0) { done[piv] = 1; pc[k] = piv; }
-    __syncwarp();
+    if (tid == 0) { done[piv] = 1; pc[k] = piv; }
+    tsync();
     k++;
   }
   res.k1 = k;
@@ -611,24 +660,24 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
   for (int p = 0; p < res.k1; p++) {
     const int col = pc[p];
     const double inv = 1.0 / M[p * ld + col];
-    for (int q = lane; q < rq; q += 32) w[q] = M[(rc + q) * ld + col] * inv;
-    __syncwarp();
-    for (int idx = lane; idx < rq * nc; idx += 32) {
+    for (int q = tid; q < rq; q += TEAM) w[q] = M[(rc + q) * ld + col] * inv;
+    tsync();
+    for (int idx = tid; idx < rq * nc; idx += TEAM) {
       int q = idx / nc, j = idx - q * nc;
       double val = (j == col) ? 0.0 : fma(-w[q], M[p * ld + j], M[(rc + q) * ld + j]);
       M[(rc + q) * ld + j] = val;
     }
-    __syncwarp();
+    tsync();
   }
   // C
   double nuq = 0.0;
-  for (int j = lane; j < ne; j += 32) {
+  for (int j = tid; j < ne; j += TEAM) {
     if (done[j]) continue;
     double s = 0.0;
     for (int i = rc; i < r; i++) s = fma(M[i * ld + j], M[i * ld + j], s);
     nuq = fmax(nuq, s);
   }
-  nuq = sqrt(warp_max(nuq));
+  nuq = sqrt(team_max(nuq));
   int kk = rc;
   while (kk < r) {
     double best;
@@ -636,8 +685,8 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
     wpivot(M, ld, kk, r, 0, ne, done, best, piv);
     if (piv == 0x7fffffff || !(best > tau_rank * nuq) || best == 0.0) break;
     whouse_apply(M, ld, kk, r, piv, 0, nc, done, v, w, best);
-    if (lane == 0) done[piv] = 1;
-    __syncwarp();
+    if (tid == 0) done[piv] = 1;
+    tsync();
     kk++;
   }
   res.k2 = kk - rc;
@@ -649,16 +698,16 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
     wpivot(M, ld, kd, rc, ne, off, done, best, piv);
     if (piv == 0x7fffffff || !(best > thr)) break;
     whouse_apply(M, ld, kd, rc, piv, ne, nc, done, v, w, best);
-    if (lane == 0) done[piv] = 1;
-    __syncwarp();
+    if (tid == 0) done[piv] = 1;
+    tsync();
     kd++;
   }
   res.kc = kd - res.k1;
   int bad = 0;
-  for (int i = kd + lane; i < rc; i += 32)
+  for (int i = kd + tid; i < rc; i += TEAM)
     if (fabs(M[i * ld + off]) > tau_inc * om) bad = 1;
-  res.inconsistent = __any_sync(kFull, bad);
-  for (int a = lane; a < res.kc; a += 32) {
+  res.inconsistent = __syncthreads_or(bad);
+  for (int a = tid; a < res.kc; a += TEAM) {
     const double *row = M + (res.k1 + a) * ld;
     double s = 0.0;
     for (int j = 0; j < nk; j++) s = fma(row[ne + j], row[ne + j], s);
@@ -666,23 +715,23 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
     for (int j = 0; j < nk; j++) outC[a * ldo + j] = row[ne + j] * inv;
     outC[a * ldo + nk] = row[off] * inv;
   }
-  __syncwarp();
+  tsync();
   // E: compress the remaining cost rows over the kept columns (no pivoting)
   int ke = kk;
   for (int col = ne; col < off && ke < r; col++) {
     double s = 0.0;
-    for (int i = ke + lane; i < r; i += 32) s = fma(M[i * ld + col], M[i * ld + col], s);
-    s = sqrt(warp_sum(s));
+    for (int i = ke + tid; i < r; i += TEAM) s = fma(M[i * ld + col], M[i * ld + col], s);
+    s = sqrt(team_sum(s));
     if (s == 0.0) continue;
     whouse_apply(M, ld, ke, r, col, col + 1, nc, nullptr, v, w, s);
     ke++;
   }
   res.kq = ke - kk;
-  for (int idx = lane; idx < res.kq * (nk + 1); idx += 32) {
+  for (int idx = tid; idx < res.kq * (nk + 1); idx += TEAM) {
     int a = idx / (nk + 1), j = idx - a * (nk + 1);
     outQ[a * ldo + j] = M[(kk + a) * ld + ne + j];
   }
-  __syncwarp();
+  tsync();
   return res;
 }
 

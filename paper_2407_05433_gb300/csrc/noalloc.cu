@@ -127,8 +127,7 @@ extern "C" int eclqr_kkt_residual_noalloc(const eclqr_desc *d, const eclqr_data 
     g.st = (const StageInfo *)(dbase + kProbBytes) + launches[k].s0;
     g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
     g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
-    const int warps = 4, blocks = (g.nstage + warps - 1) / warps;
-    k_kkt_residual<<<blocks, 32 * warps, 0, st>>>(g, s0, x, u, lam, mu, eta, alpha, resid);
+    k_kkt_residual<<<g.nstage, 128, 0, st>>>(g, s0, x, u, lam, mu, eta, alpha, resid);
     if (cudaPeekAtLastError() != cudaSuccess) return ECLQR_ECUDA;
   }
   return ECLQR_OK;

@@ -132,11 +132,12 @@ __device__ __forceinline__ void set_status(const Group &g, int prob, int code) {
 __device__ __forceinline__ double *stage_ws(const Group &g, int s) { return g.W + (size_t)s * g.ws.stride; }
 __device__ __forceinline__ int *stage_wi(const Group &g, int s) { return g.WI + (size_t)s * SI_STRIDE; }
 
-// task index of the calling warp, and its shared-memory window
-__device__ __forceinline__ int warp_task() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+// One task per CTA: the task index, and the task's shared-memory window (the
+// whole dynamic allocation).
+__device__ __forceinline__ int team_task() { return blockIdx.x; }
 
 extern __shared__ double g_smem[];
-__device__ __forceinline__ double *warp_smem(int per_warp) { return g_smem + (size_t)(threadIdx.x >> 5) * per_warp; }
+__device__ __forceinline__ double *team_smem(int /*per_task*/) { return g_smem; }
 
 // status codes (mirror include/eclqr.h)
 enum {
