@@ -37,13 +37,13 @@ WORKLOAD_DESC = ("degenerate_n12: one instance, N=1024, n=12, m=6, mixed rows U{
 KKT_GATE = 1e-9
 KERNELS = ["k_terminal", "k_primal_up", "k_rel_level", "k_primal_down", "k_param", "k_elim", "k_lqr_up",
            "k_lqr_level", "k_riccati_down", "k_aff_up", "k_aff_level", "k_aff_down", "k_solve_init",
-           "k_post_roll", "k_resid", "k_scorr", "k_recover", "k_dual_stage", "k_dual_terminal", "k_dual_up",
+           "k_post_roll", "k_resid", "k_pcorr", "k_recover", "k_dual_stage", "k_dual_terminal", "k_dual_up",
            "k_dual_down", "k_dual_root", "k_dual_leaf", "k_kkt_residual"]
 # phase of Algorithm 1 each kernel implements (index into the oracle's per-phase flop counts)
 KERNEL_PHASE = {"k_terminal": 0, "k_primal_up": 0, "k_rel_level": 0, "k_primal_down": 0, "k_param": 1,
                 "k_elim": 2, "k_lqr_up": 3, "k_lqr_level": 3, "k_riccati_down": 3, "k_aff_up": 4,
                 "k_aff_level": 4, "k_aff_down": 4, "k_solve_init": 4, "k_post_roll": 4, "k_resid": 4,
-                "k_scorr": 4, "k_recover": 4, "k_dual_stage": 5, "k_dual_terminal": 5, "k_dual_up": 5,
+                "k_pcorr": 4, "k_recover": 4, "k_dual_stage": 5, "k_dual_terminal": 5, "k_dual_up": 5,
                 "k_dual_down": 5, "k_dual_root": 5, "k_dual_leaf": 5, "k_kkt_residual": 6}
 
 
@@ -330,7 +330,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--refine", type=int, default=4)
+    ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()

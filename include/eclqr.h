@@ -96,8 +96,9 @@ typedef struct {
 typedef struct {
   double tau_rank;   /* relative rank cut after row scaling (Sec. 8 items 1-2); default 1e-10 */
   double tau_inc;    /* inconsistency cut on a scaled offset (Sec. 8 item 4); default 1e-8    */
-  int32_t refine;    /* refinement passes on the reduced LQR KKT residual; default 4          */
+  int32_t refine;    /* refinement passes on the reduced LQR KKT residual; default 2          */
   int32_t chunk;     /* stages per scan chunk; 0 = chosen from N and the SM count             */
+  int32_t team_warps; /* warps of the CTA that runs one task: 1, 2, 4 or 8; 0 = 4            */
 } eclqr_options;
 
 /* element counts of every packed array (for allocation) */

@@ -20,9 +20,9 @@ using namespace eclqr;
 namespace {
 
 // dynamic shared memory per task: the 227 KB opt-in limit less room for the
-// team reductions' static arrays
-constexpr int kMaxSmemBytes = 226 * 1024;
-constexpr int kTeamWarps = 4;
+// static scratch of the team reductions and the Householder core (< 7 KB)
+constexpr int kMaxSmemBytes = 220 * 1024;
+constexpr int kTeamWarps = 4;  // default team: one warp per SM sub-partition
 
 struct GroupHost {
   Group g;
@@ -56,14 +56,16 @@ struct eclqr_handle {
 
 namespace {
 
-// one CTA (a team of kTeamWarps warps, one per SM sub-partition) per task,
+// one CTA (a team of opt.team_warps warps) per task,
 // with per_task doubles of dynamic shared memory
 template <typename... KArgs, typename... Args>
 int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cudaStream_t st, Args... args) {
   if (ntasks <= 0) return ECLQR_OK;
   const size_t smem = (size_t)per_task * sizeof(double);
   if (smem > (size_t)kMaxSmemBytes) return ECLQR_EINVAL;
-  if (smem > 48 * 1024) {
+  // without the opt-in, dynamic plus static shared memory is capped at 48 KB;
+  // the kernels' static scratch stays below 8 KB
+  if (smem > 40 * 1024) {
     if (cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return ECLQR_ECUDA;
@@ -71,7 +73,7 @@ int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cu
   const int grid = ntasks;
   const bool timed = h->timed == (const void *)kern && h->nev + 2 <= (int)h->ev.size();
   if (timed) cudaEventRecord(h->ev[h->nev], st);
-  kern<<<grid, 32 * kTeamWarps, smem, st>>>(args...);
+  kern<<<grid, 32 * h->opt.team_warps, smem, st>>>(args...);
   if (timed) {
     cudaEventRecord(h->ev[h->nev + 1], st);
     h->nev += 2;
@@ -153,8 +155,9 @@ void eclqr_default_options(eclqr_options *opt) {
   if (!opt) return;
   opt->tau_rank = 1e-10;
   opt->tau_inc = 1e-8;
-  opt->refine = 4;
+  opt->refine = 2;
   opt->chunk = 0;
+  opt->team_warps = 0;
 }
 
 int eclqr_layout(const eclqr_desc *d, eclqr_layout_info *out) {
@@ -189,7 +192,10 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   if (!h) return ECLQR_ENOMEM;
   eclqr_default_options(&h->opt);
   if (opt) h->opt = *opt;
-  if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0)) {
+  if (h->opt.team_warps == 0) h->opt.team_warps = kTeamWarps;
+  const int tw = h->opt.team_warps;
+  if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0) ||
+      !(tw == 1 || tw == 2 || tw == 4 || tw == 8)) {
     delete h;
     return ECLQR_EINVAL;
   }
@@ -376,7 +382,7 @@ namespace {
 int aff_scan(eclqr_handle *h, GroupHost &gh, int mode, cudaStream_t st) {
   Group &g = gh.g;
   const int sa = smem_aff(g.n, g.m);
-  const int fwd = (mode == AFF_SLIN_) ? 0 : 1;
+  const int fwd = (mode == AFF_PLIN_) ? 0 : 1;
   TRY(launch(h, k_aff_up, g.nslot, sa, st, g, mode, sa));
   int src = 0;
   for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_aff_level, g.nslot, sa, st, g, src, 1 << k, fwd, sa));
@@ -398,9 +404,9 @@ int eclqr_solve(eclqr_handle *h, const double *s0, double *x, double *u, int32_t
     for (int r = 0; r < h->opt.refine; r++) {
       const int sres = 3 * g.n + 2 * g.m;
       TRY(launch(h, k_resid, g.nstage, sres, st, g, sres));
-      TRY(aff_scan(h, gh, AFF_SLIN_, st));
-      const int sc = 3 * (g.n + g.m) + 8;
-      TRY(launch(h, k_scorr, g.nstage, sc, st, g, sc));
+      TRY(aff_scan(h, gh, AFF_PLIN_, st));
+      const int sc = g.n + g.m;
+      TRY(launch(h, k_pcorr, g.nstage, sc, st, g, sc));
       TRY(aff_scan(h, gh, AFF_CROLL_, st));
       TRY(launch(h, k_post_roll, g.nstage, 0, st, g, 1));
     }
@@ -487,7 +493,7 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
       {"k_riccati_down", (const void *)k_riccati_down}, {"k_aff_up", (const void *)k_aff_up},
       {"k_aff_level", (const void *)k_aff_level}, {"k_aff_down", (const void *)k_aff_down},
       {"k_solve_init", (const void *)k_solve_init}, {"k_post_roll", (const void *)k_post_roll},
-      {"k_resid", (const void *)k_resid}, {"k_scorr", (const void *)k_scorr},
+      {"k_resid", (const void *)k_resid}, {"k_pcorr", (const void *)k_pcorr},
       {"k_recover", (const void *)k_recover}, {"k_dual_stage", (const void *)k_dual_stage},
       {"k_dual_terminal", (const void *)k_dual_terminal}, {"k_dual_up", (const void *)k_dual_up},
       {"k_dual_down", (const void *)k_dual_down}, {"k_dual_root", (const void *)k_dual_root},

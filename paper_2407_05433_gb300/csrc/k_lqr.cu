@@ -31,7 +31,7 @@ __host__ int smem_lqr_level(int n) {
   return rows * ldm + 2 * rows + 2 * (ldm + rows) + n + 16;
 }
 __host__ int smem_riccati(int n, int m) {
-  const int rows = 2 * n + m, ld = n + m + 1 + rows;
+  const int rows = 2 * n + m, ld = n + m + 1;
   return n * (n + 1) + rows * ld + rows + ld + 2 * m * (n + 1) + 8;
 }
 __host__ int smem_aff(int n, int m) { return 2 * (n * n + n) + n * n + 5 * n + 2 * m + 8; }
@@ -205,13 +205,11 @@ __global__ void k_lqr_level(Group g, int src, int d, int per_task) {
 // ----------------------------------------------------------- chunk down-sweep: square-root Riccati
 // From V_b = 1/2 ||C z_b + c||^2 (the scan's value at the chunk end), each stage
 // stacks [L'_v | L'_z | l] and [C Bbar | C Abar | C cbar + c] over (v | z | 1) and
-// triangularises them by Householder QR, carrying an identity block so that
-// Q' is formed too: R_vv v + R_vz z + o_v = 0 at the minimiser (K, k) and
-// V_i = 1/2 ||R_i z + s_i||^2 with R_i upper triangular, rows signed so that
-// its diagonal is positive (the unique such square root of P_i, so chunks
-// meeting at a boundary use the same frame).  Stored per stage: P_i = R_i'R_i,
-// p_i = R_i's_i, K, k, H_uu (Cholesky factor), H_ux = R_vv'R_vz, Phi = Abar + Bbar K,
-// and for the refinement passes R_i, R_vv and the top rows of Q'.
+// triangularises them by Householder QR: R_vv v + R_vz z + o_v = 0 at the
+// minimiser (K, k) and V_i = 1/2 ||R_i z + s_i||^2 with R_i upper triangular,
+// rows signed so that its diagonal is positive.  Stored per stage: P_i = R_i'R_i,
+// p_i = R_i's_i, K, k, the Cholesky factor of H_uu = R_vv'R_vv and
+// Phi = Abar + Bbar K (the closed-loop map of the affine chains).
 __global__ void k_riccati_down(Group g, int fin, int per_task) {
   const int t = team_task();
   if (t >= g.nslot) return;
@@ -220,9 +218,9 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
-  const int ldr = 2 * n + 1, ldq = 2 * n + m;
+  const int ldr = 2 * n + 1;
   double *sm = team_smem(per_task);
-  const int rows_max = 2 * n + m, ldst = n + m + 1 + rows_max;
+  const int rows_max = 2 * n + m, ldst = n + m + 1;
   double *V = sm, *St = V + n * (n + 1), *v = St + rows_max * ldst, *w = v + rows_max;
   double *Kt = w + ldst;  // m x (n + 1)
   // V_b, rows signed to a positive diagonal
@@ -238,17 +236,13 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       V[r * (n + 1) + j] = sg * src[r * ldr + j];
     }
     tsync();
-    if (b == P.N) {  // P_N = C'C, p_N = C'c, value factor for the refinement
+    if (b == P.N) {  // P_N = C'C, p_N = C'c
       double *wsN = stage_ws(g, P.st0 + b);
       for (int idx = tid; idx < nbz * (nbz + 1); idx += TEAM) {
         int r = idx / (nbz + 1), j = idx - r * (nbz + 1);
         double s0 = 0.0;
         for (int l = 0; l < rv; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + j], s0);
         if (j < nbz) wsN[g.ws.P + r * n + j] = s0; else wsN[g.ws.p + r] = s0;
-      }
-      for (int idx = tid; idx < rv * nbz; idx += TEAM) {
-        int r = idx / nbz, j = idx - r * nbz;
-        wsN[g.ws.RV + r * n + j] = V[r * (n + 1) + j];
       }
     }
   }
@@ -257,14 +251,12 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
     double *ws = stage_ws(g, s);
     int *wi = stage_wi(g, s);
     const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
-    const int kh = nx + mu, rows = kh + rv, ld = kh + 1 + rows;
+    const int kh = nx + mu, rows = kh + rv, ld = kh + 1;
     const double *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb, *cb = ws + g.ws.cb, *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
     for (int idx = tid; idx < rows * ld; idx += TEAM) {
       int r = idx / ld, j = idx - r * ld;
       double val = 0.0;
-      if (j > kh) {
-        val = (j - kh - 1 == r) ? 1.0 : 0.0;  // identity block: becomes Q'
-      } else if (r < kh) {
+      if (r < kh) {
         if (j < mu) val = LT[r * (n + m) + nx + j];
         else if (j < kh) val = LT[r * (n + m) + (j - mu)];
         else val = lt[r];
@@ -289,7 +281,7 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       if (s0 == 0.0) continue;
       whouse_apply(St, ld, col, rows, col, col + 1, ld, nullptr, v, w, s0);
     }
-    // sign the z rows to a positive diagonal (rows mu .. kh - 1, all columns)
+    // sign the z rows to a positive diagonal (rows mu .. kh - 1)
     for (int idx = tid; idx < nx * ld; idx += TEAM) {
       int r = mu + idx / ld, j = idx % ld;
       if (St[r * ld + r] < 0.0 && j != r) St[r * ld + j] = -St[r * ld + j];
@@ -314,13 +306,6 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       int r = idx / mu, j = idx - r * mu;
       double sg = St[j * ld + j] >= 0.0 ? 1.0 : -1.0;
       ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * St[j * ld + r] : 0.0;
-      ws[g.ws.RVV + r * m + j] = (j >= r) ? St[r * ld + j] : 0.0;
-    }
-    for (int idx = tid; idx < mu * nx; idx += TEAM) {
-      int r = idx / nx, c = idx - r * nx;
-      double s0 = 0.0;
-      for (int l = 0; l <= r; l++) s0 = fma(St[l * ld + r], St[l * ld + mu + c], s0);
-      ws[g.ws.Hx + r * n + c] = s0;
     }
     for (int idx = tid; idx < n1 * nx; idx += TEAM) {
       int r = idx / nx, c = idx - r * nx;
@@ -328,12 +313,6 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
       ws[g.ws.Phi + r * n + c] = s0;
     }
-    // top kh rows of Q' (columns: kh stage-cost offsets, then rv value offsets)
-    for (int idx = tid; idx < kh * rows; idx += TEAM) {
-      int r = idx / rows, c = idx - r * rows;
-      ws[g.ws.Qs + r * ldq + c] = St[r * ld + kh + 1 + c];
-    }
-    if (tid == 0) wi[SI_RV] = rv;
     // new value rows [R_i | s_i]
     tsync();
     for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
@@ -347,50 +326,26 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       double s0 = 0.0;
       for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
       if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
-      if (c < nx) ws[g.ws.RV + r * n + c] = V[r * (n + 1) + c];
     }
     tsync();
   }
-}
-
-// Offsets of the refinement's square-root linear pass at stage s:
-// lq = L^{-1} [rq; rr] (stage cost rows) and u = R_{i+1} rc (value rows).
-__device__ void slin_offsets(const Group &g, int s, double *lq, double *u) {
-  const int n = g.n, m = g.m, tid = team_rank();
-  const double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);
-  const int *wi = stage_wi(g, s);
-  const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], kh = nx + mu, rv = wi[SI_RV];
-  const double *LT = ws + g.ws.LT;
-  if (tid == 0) {
-    for (int a = 0; a < kh; a++) {
-      double s0 = (a < nx) ? ws[g.ws.rq + a] : ws[g.ws.rr + (a - nx)];
-      for (int l = 0; l < a; l++) s0 = fma(-LT[l * (n + m) + a], lq[l], s0);
-      lq[a] = s0 / LT[a * (n + m) + a];
-    }
-  }
-  for (int r = tid; r < rv; r += TEAM) {
-    double s0 = 0.0;
-    for (int l = r; l < rv; l++) s0 = fma(wn[g.ws.RV + r * n + l], ws[g.ws.rc + l], s0);
-    u[r] = s0;
-  }
-  tsync();
 }
 
 // ----------------------------------------------------------- affine chain scans
 // Per-stage maps by mode (d_i = dimension of the chained vector at stage i):
 //   AFF_ROLL  forward  z_{i+1} = Phi_i z_i + Bbar k_i + cbar_i        -> z
 //   AFF_CROLL forward  dz_{i+1} = Phi_i dz_i + Bbar k'_i + rc_i       -> dz (k' held in dv)
-//   AFF_SLIN  backward s'_i = G_i s'_{i+1} + g_i, the refinement's linear pass in square-root form:
-//             G_i = rows of Q' (norm <= 1), g_i from L^{-1}[rq; rr] and R_{i+1} rc     -> sp
+//   AFF_PLIN  backward p'_i = Phi_i' p'_{i+1} + rq_i + K_i' rr_i + Phi_i' P_{i+1} rc_i, the
+//             refinement's linear pass for the offsets (rq, rr, rc)                  -> pp
 //   AFF_NU    forward  nu_{i+1} = Pnu_i nu_i + pnu_i                  -> nu
-enum { AFF_ROLL = 0, AFF_CROLL = 1, AFF_SLIN = 2, AFF_NU = 3 };
+enum { AFF_ROLL = 0, AFF_CROLL = 1, AFF_PLIN = 2, AFF_NU = 3 };
 
 __device__ __forceinline__ int aff_dim(const Group &g, int s, int mode) {
   return (mode == AFF_NU) ? stage_wi(g, s)[SI_UR] : stage_wi(g, s)[SI_NBAR];
 }
-__device__ __forceinline__ bool aff_forward(int mode) { return mode != AFF_SLIN; }
+__device__ __forceinline__ bool aff_forward(int mode) { return mode != AFF_PLIN; }
 __device__ __forceinline__ int aff_out(const Group &g, int mode) {
-  return mode == AFF_ROLL ? g.ws.z : mode == AFF_CROLL ? g.ws.dz : mode == AFF_SLIN ? g.ws.sp : g.ws.nu;
+  return mode == AFF_ROLL ? g.ws.z : mode == AFF_CROLL ? g.ws.dz : mode == AFF_PLIN ? g.ws.pp : g.ws.nu;
 }
 
 // map of stage i: y_out = G y_in + gv.  Forward: in = stage i, out = stage i+1;
@@ -426,23 +381,25 @@ __device__ void aff_stage_map(const Group &g, int s, int mode, double *G, double
     tsync();
     return;
   }
-  // AFF_SLIN: G = rows mu.. of Q' on the value offsets (nx x rv), gv = Q'[z rows] [L^{-1}[rq; rr]; R_{i+1} rc]
-  const int kh = nx + mu, rv = wi[SI_RV], ldq = 2 * n + m;
-  const double *Qs = ws + g.ws.Qs;
-  double *lq = tmp, *u = tmp + (n + m);
-  slin_offsets(g, s, lq, u);
-  for (int idx = tid; idx < nx * rv; idx += TEAM) {
-    int i = idx / rv, j = idx - i * rv;
-    G[i * n + j] = Qs[(mu + i) * ldq + kh + j];
-  }
-  for (int i = tid; i < nx; i += TEAM) {
+  // AFF_PLIN: G = Phi' (nx x ny), gv = rq + K' rr + Phi' (P_{i+1} rc)
+  const double *K = ws + g.ws.K, *Pn = wn + g.ws.P, *rc = ws + g.ws.rc;
+  for (int b = tid; b < ny; b += TEAM) {
     double s0 = 0.0;
-    for (int l = 0; l < kh; l++) s0 = fma(Qs[(mu + i) * ldq + l], lq[l], s0);
-    for (int l = 0; l < rv; l++) s0 = fma(Qs[(mu + i) * ldq + kh + l], u[l], s0);
+    for (int l = 0; l < ny; l++) s0 = fma(Pn[b * n + l], rc[l], s0);
+    tmp[b] = s0;
+  }
+  for (int idx = tid; idx < nx * ny; idx += TEAM) {
+    int i = idx / ny, j = idx - i * ny;
+    G[i * n + j] = Phi[j * n + i];
+  }
+  tsync();
+  for (int i = tid; i < nx; i += TEAM) {
+    double s0 = ws[g.ws.rq + i];
+    for (int l = 0; l < mu; l++) s0 = fma(K[l * n + i], ws[g.ws.rr + l], s0);
+    for (int b = 0; b < ny; b++) s0 = fma(Phi[b * n + i], tmp[b], s0);
     gv[i] = s0;
   }
   tsync();
-  (void)ny;
 }
 
 // chunk aggregates; also the boundary value slot (forward: slot 0 of the
@@ -466,17 +423,9 @@ __global__ void k_aff_up(Group g, int mode, int per_task) {
       double v;
       if (mode == AFF_ROLL) v = src[g.ws.z + i];
       else if (mode == AFF_CROLL) v = 0.0;
-      else if (mode == AFF_SLIN) v = 0.0;  // set below: s'_N = R_N^{-T} rq_N
+      else if (mode == AFF_PLIN) v = src[g.ws.rq + i];  // p'_N = rq_N
       else v = src[g.ws.nu + i];
       gv[i] = v;
-    }
-    tsync();
-    if (mode == AFF_SLIN && tid == 0) {
-      for (int a = 0; a < dim; a++) {
-        double s0 = src[g.ws.rq + a];
-        for (int l = 0; l < a; l++) s0 = fma(-src[g.ws.RV + l * n + a], gv[l], s0);
-        gv[a] = s0 / src[g.ws.RV + a * n + a];
-      }
     }
     if (tid == 0) {
       int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
@@ -792,43 +741,46 @@ __global__ void k_resid(Group g, int per_task) {
   }
 }
 
-// From the square-root linear pass s': k'_i = -R_vv^{-1} o_v with
-// o_v = Q'[v rows] [L^{-1}[rq; rr]; R_{i+1} rc + s'_{i+1}]  (-> dv), and p'_i = R_i's'_i (-> pp).
-__global__ void k_scorr(Group g, int per_task) {
+// Correction controls of a refinement pass: with w = P_{i+1} rc_i + p'_{i+1},
+// k'_i = -H_uu^{-1} (rr_i + Bbar' w) through the Cholesky factor of H_uu (-> dv).
+__global__ void k_pcorr(Group g, int per_task) {
   const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (S.i >= P.N) return;
   const int n = g.n, m = g.m, tid = team_rank();
   double *ws = stage_ws(g, s);
-  const int *wi = stage_wi(g, s);
-  const int nx = wi[SI_NBAR];
-  const double *sp = ws + g.ws.sp, *RV = ws + g.ws.RV;
-  for (int r = tid; r < nx; r += TEAM) {
-    double s0 = 0.0;
-    for (int l = 0; l <= r; l++) s0 = fma(RV[l * n + r], sp[l], s0);
-    ws[g.ws.pp + r] = s0;
-  }
-  if (S.i >= P.N) return;
-  const int mu = wi[SI_MBAR], kh = nx + mu, rv = wi[SI_RV], ldq = 2 * n + m;
+  const double *wn = stage_ws(g, s + 1);
+  const int mu = stage_wi(g, s)[SI_MBAR], ny = stage_wi(g, s + 1)[SI_NBAR];
   double *sm = team_smem(per_task);
-  double *lq = sm, *u = sm + (n + m), *ov = u + n;
-  slin_offsets(g, s, lq, u);
-  const double *Qs = ws + g.ws.Qs, *sn = stage_ws(g, s + 1) + g.ws.sp;
-  for (int r = tid; r < mu; r += TEAM) {
-    double s0 = 0.0;
-    for (int l = 0; l < kh; l++) s0 = fma(Qs[r * ldq + l], lq[l], s0);
-    for (int l = 0; l < rv; l++) s0 = fma(Qs[r * ldq + kh + l], u[l] + sn[l], s0);
-    ov[r] = s0;
+  double *w = sm, *hu = sm + n;
+  const double *Pn = wn + g.ws.P, *ppn = wn + g.ws.pp, *rc = ws + g.ws.rc, *Bb = ws + g.ws.Bb;
+  for (int b = tid; b < ny; b += TEAM) {
+    double s0 = ppn[b];
+    for (int l = 0; l < ny; l++) s0 = fma(Pn[b * n + l], rc[l], s0);
+    w[b] = s0;
+  }
+  tsync();
+  for (int a = tid; a < mu; a += TEAM) {
+    double s0 = ws[g.ws.rr + a];
+    for (int b = 0; b < ny; b++) s0 = fma(Bb[b * m + a], w[b], s0);
+    hu[a] = s0;
   }
   tsync();
   if (tid == 0) {
-    const double *Rvv = ws + g.ws.RVV;
-    for (int r = mu - 1; r >= 0; r--) {
-      double s0 = -ov[r];
-      for (int l = r + 1; l < mu; l++) s0 = fma(-Rvv[r * m + l], ws[g.ws.dv + l], s0);
-      ws[g.ws.dv + r] = s0 / Rvv[r * m + r];
+    const double *Lh = ws + g.ws.Lh;  // lower triangular, ld m
+    for (int a = 0; a < mu; a++) {
+      double s0 = hu[a];
+      for (int l = 0; l < a; l++) s0 = fma(-Lh[a * m + l], hu[l], s0);
+      hu[a] = s0 / Lh[a * m + a];
     }
+    for (int a = mu - 1; a >= 0; a--) {
+      double s0 = hu[a];
+      for (int l = a + 1; l < mu; l++) s0 = fma(-Lh[l * m + a], hu[l], s0);
+      hu[a] = s0 / Lh[a * m + a];
+    }
+    for (int a = 0; a < mu; a++) ws[g.ws.dv + a] = -hu[a];
   }
 }
 

@@ -27,7 +27,7 @@ __global__ void k_param(Group g, int per_task);
 __global__ void k_elim(Group g, int per_task);
 
 // reduced LQR, affine chains, recovery (k_lqr.cu)
-enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_SLIN_ = 2, AFF_NU_ = 3 };
+enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_PLIN_ = 2, AFF_NU_ = 3 };
 __global__ void k_lqr_up(Group g, int per_task);
 __global__ void k_lqr_level(Group g, int src, int d, int per_task);
 __global__ void k_riccati_down(Group g, int fin, int per_task);
@@ -37,7 +37,7 @@ __global__ void k_aff_down(Group g, int mode, int fin, int per_task);
 __global__ void k_solve_init(Group g, const double *s0);
 __global__ void k_post_roll(Group g, int corr);
 __global__ void k_resid(Group g, int per_task);
-__global__ void k_scorr(Group g, int per_task);
+__global__ void k_pcorr(Group g, int per_task);
 __global__ void k_recover(Group g, double *x, double *u);
 __global__ void k_dims(Group g, int *nbar, int *mbar);
 

@@ -135,6 +135,131 @@ static __device__ void wgemm(int m, int n, int k, double alpha, const double *A,
 }
 
 // ---------------------------------------------------------------------------
+// Householder core shared by the factorizations below.
+//
+// Per-CTA static scratch: one partial dot product per thread, and for column
+// pivoting the running squared norms of the candidate columns with their
+// values at the last exact evaluation.  Sized for teams of up to kMaxTeam
+// threads and matrices of up to kMaxCols columns (the header's dimension
+// limits keep every factored matrix below 3 * 32 + 64 + 1 columns).
+// ---------------------------------------------------------------------------
+constexpr int kMaxTeam = 256;
+constexpr int kMaxCols = 192;
+__device__ __forceinline__ double *hh_part() {
+  __shared__ double part[kMaxTeam];
+  return part;
+}
+__device__ __forceinline__ double *hh_norms() {
+  __shared__ double norms[2 * kMaxCols];
+  return norms;
+}
+
+// Reflector H = I - beta v v' from column piv on rows [r0, r1) (nrm = the
+// column's 2-norm there, > 0), applied to the columns of [c0, c1) that are not
+// done and are not piv; column piv becomes (-sign(x_k) nrm, 0, ..., 0).  v
+// (indexed by row) keeps the reflector, beta = 1 / (nrm |v[r0]|).  The dot
+// products v'M_j are split over the team by column and by row segment, so a
+// column of R rows costs about R * columns / TEAM FMAs per thread.
+static __device__ void whouse_apply(double *M, int ld, int r0, int r1, int piv, int c0, int c1, const int *done,
+                                    double *v, double *w, double nrm) {
+  const int tid = team_rank(), T = TEAM;
+  double *part = hh_part();
+  const double xk = M[r0 * ld + piv];
+  const double sg = xk >= 0.0 ? 1.0 : -1.0;
+  for (int i = r0 + tid; i < r1; i += T) v[i] = (i == r0) ? xk + sg * nrm : M[i * ld + piv];
+  const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
+  tsync();
+  const int nc = c1 - c0, nr = r1 - r0;
+  // thread -> (column c0 + jj, row segment sgm): rows r0 + sgm, r0 + sgm + S, ...
+  // S * nc <= T when S > 1; with S == 1 threads step over columns
+  const int S = max(1, min(nc > 0 ? T / nc : 1, nr));
+  const int jj0 = (S > 1) ? tid % nc : tid, sgm = (S > 1) ? tid / nc : 0;
+  const bool seg_ok = sgm < S;
+  for (int jj = jj0; seg_ok && jj < nc; jj += (S > 1 ? nc : T)) {
+    const int j = c0 + jj;
+    double acc = 0.0;
+    if (!((done && done[j]) || j == piv))
+      for (int i = r0 + sgm; i < r1; i += S) acc = fma(v[i], M[i * ld + j], acc);
+    if (S == 1) w[j] = beta * acc;
+    else part[sgm * nc + jj] = acc;
+  }
+  tsync();
+  if (S > 1) {
+    for (int j2 = tid; j2 < nc; j2 += T) {
+      double acc = part[j2];
+      for (int k2 = 1; k2 < S; k2++) acc += part[k2 * nc + j2];
+      w[c0 + j2] = beta * acc;
+    }
+    tsync();
+  }
+  for (int jj = jj0; seg_ok && jj < nc; jj += (S > 1 ? nc : T)) {
+    const int j = c0 + jj;
+    if ((done && done[j]) || j == piv) continue;
+    const double wj = w[j];
+    for (int i = r0 + sgm; i < r1; i += S) M[i * ld + j] = fma(-wj, v[i], M[i * ld + j]);
+  }
+  tsync();
+  for (int i = r0 + tid; i < r1; i += T) M[i * ld + piv] = (i == r0) ? -sg * nrm : 0.0;
+  tsync();
+}
+
+// Column-pivoted Householder steps on rows [k, r).  Each step takes the
+// candidate column (in [cand0, cand1), not done) of largest remaining norm;
+// while its exact norm exceeds thr, its reflector is applied to the not-done
+// columns of [app0, app1), it is marked done and recorded in pc (when given).
+// Remaining norms are downdated after every step and evaluated afresh once
+// cancellation has consumed half their digits (the safeguard of LAPACK's
+// xLAQP2, threshold sqrt(eps) = 2^-26).  Returns the number of steps taken.
+static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int cand1, int app0, int app1,
+                                 int *done, int *pc, double thr, double *v, double *w) {
+  const int tid = team_rank(), T = TEAM;
+  double *cn = hh_norms(), *cref = cn + kMaxCols;
+  for (int j = cand0 + tid; j < cand1; j += T) {
+    double acc = 0.0;
+    if (!done[j])
+      for (int i = k; i < r; i++) acc = fma(M[i * ld + j], M[i * ld + j], acc);
+    cn[j] = acc;
+    cref[j] = acc;
+  }
+  tsync();
+  int steps = 0;
+  while (k < r) {
+    double mybest = -1.0;
+    int mypiv = 0x7fffffff;
+    for (int j = cand0 + tid; j < cand1; j += T)
+      if (!done[j] && cn[j] > mybest) { mybest = cn[j]; mypiv = j; }
+    double b2;
+    int piv;
+    team_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
+    if (piv == 0x7fffffff) break;
+    double acc = 0.0;
+    for (int i = k + tid; i < r; i += T) acc = fma(M[i * ld + piv], M[i * ld + piv], acc);
+    const double nrm = sqrt(team_sum(acc));
+    if (!(nrm > thr)) break;
+    whouse_apply(M, ld, k, r, piv, app0, app1, done, v, w, nrm);
+    if (tid == 0) {
+      done[piv] = 1;
+      if (pc) pc[steps] = piv;
+    }
+    for (int j = cand0 + tid; j < cand1; j += T) {
+      if (j == piv || done[j]) continue;
+      const double a = M[k * ld + j];
+      double nw = cn[j] - a * a;
+      if (nw <= 0x1p-26 * cref[j]) {
+        nw = 0.0;
+        for (int i = k + 1; i < r; i++) nw = fma(M[i * ld + j], M[i * ld + j], nw);
+        cref[j] = nw;
+      }
+      cn[j] = nw;
+    }
+    tsync();
+    k++;
+    steps++;
+  }
+  return steps;
+}
+
+// ---------------------------------------------------------------------------
 // Lemma 1 by ordered column-pivoted Householder row reduction.
 //
 // M (r x nc, ld) holds, column-wise: ng groups of columns to eliminate (sizes
@@ -210,58 +335,8 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
   int k = 0, c0 = 0;
   for (int g = 0; g <= ng; g++) {
     const int c1 = c0 + (g < ng ? gsz[g] : nkeep);
-    int rk = 0;
-    while (k < r) {
-      double mybest = -1.0;
-      int mypiv = 0x7fffffff;
-      for (int j = c0 + tid; j < c1; j += TEAM) {
-        if (done[j]) continue;
-        double s0 = 0.0, s1 = 0.0;
-        int i = k;
-        for (; i + 1 < r; i += 2) {
-          s0 = fma(M[i * ld + j], M[i * ld + j], s0);
-          s1 = fma(M[(i + 1) * ld + j], M[(i + 1) * ld + j], s1);
-        }
-        if (i < r) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
-        double s = s0 + s1;
-        if (s > mybest) { mybest = s; mypiv = j; }
-      }
-      double best2;
-      int piv;
-      team_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, best2, piv);
-      if (piv == 0x7fffffff) break;
-      const double best = sqrt(best2);
-      if (!(best > thr)) break;
-      const double xk = M[k * ld + piv];
-      const double sg = xk >= 0.0 ? 1.0 : -1.0;
-      for (int i = k + tid; i < r; i += TEAM) v[i] = (i == k) ? xk + sg * best : M[i * ld + piv];
-      const double beta = 1.0 / (best * (best + fabs(xk)));
-      tsync();
-      for (int j = tid; j < nc; j += TEAM) {
-        if (done[j] || j == piv) continue;
-        double s0 = 0.0, s1 = 0.0;
-        int i = k;
-        for (; i + 1 < r; i += 2) {
-          s0 = fma(v[i], M[i * ld + j], s0);
-          s1 = fma(v[i + 1], M[(i + 1) * ld + j], s1);
-        }
-        if (i < r) s0 = fma(v[i], M[i * ld + j], s0);
-        w[j] = beta * (s0 + s1);
-      }
-      tsync();
-      const int rows = r - k;
-      for (int idx = tid; idx < rows * nc; idx += TEAM) {
-        int i = k + idx / nc, j = idx % nc;
-        if (done[j] || j == piv) continue;
-        M[i * ld + j] = fma(-w[j], v[i], M[i * ld + j]);
-      }
-      tsync();
-      for (int i = k + tid; i < r; i += TEAM) M[i * ld + piv] = (i == k) ? -sg * best : 0.0;
-      if (tid == 0) done[piv] = 1;
-      tsync();
-      k++;
-      rk++;
-    }
+    const int rk = hh_pivoted(M, ld, k, r, c0, c1, 0, nc, done, nullptr, thr, v, w);
+    k += rk;
     if (g < ng) res.grank[g] = rk; else res.krank = rk;
     c0 = c1;
   }
@@ -295,23 +370,24 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
 // ---------------------------------------------------------------------------
 static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_rank, double *W, int ldw,
                     double *Q, int ldq, int *perm, double *scr /* >= nk + max(nk, rk) */) {
-  const int tid = team_rank();
+  const int tid = team_rank(), T = TEAM;
   double *v = scr, *w = scr + nk;
-  for (int idx = tid; idx < nk * rk; idx += TEAM) {
+  double *part = hh_part();
+  for (int idx = tid; idx < nk * rk; idx += T) {
     int i = idx / rk, j = idx - i * rk;
     W[i * ldw + j] = K[j * ldk + i];
   }
-  for (int idx = tid; idx < nk * nk; idx += TEAM) {
+  for (int idx = tid; idx < nk * nk; idx += T) {
     int i = idx / nk, j = idx - i * nk;
     Q[i * ldq + j] = (i == j) ? 1.0 : 0.0;
   }
-  for (int j = tid; j < rk; j += TEAM) perm[j] = j;
+  for (int j = tid; j < rk; j += T) perm[j] = j;
   tsync();
   double nu = 0.0;
-  for (int j = tid; j < rk; j += TEAM) {
-    double s = 0.0;
-    for (int i = 0; i < nk; i++) s = fma(W[i * ldw + j], W[i * ldw + j], s);
-    nu = fmax(nu, s);
+  for (int j = tid; j < rk; j += T) {
+    double acc = 0.0;
+    for (int i = 0; i < nk; i++) acc = fma(W[i * ldw + j], W[i * ldw + j], acc);
+    nu = fmax(nu, acc);
   }
   nu = sqrt(team_max(nu));
   const double thr = tau_rank * nu;
@@ -319,7 +395,7 @@ static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_
   for (int s = 0; s < rk && s < nk; s++) {
     double mybest = -1.0;
     int mypiv = 0x7fffffff;
-    for (int j = s + tid; j < rk; j += TEAM) {
+    for (int j = s + tid; j < rk; j += T) {
       double t = 0.0;
       for (int i = s; i < nk; i++) t = fma(W[i * ldw + j], W[i * ldw + j], t);
       if (t > mybest) { mybest = t; mypiv = j; }
@@ -331,7 +407,7 @@ static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_
     const double best = sqrt(b2);
     if (!(best > thr)) break;
     if (piv != s) {
-      for (int i = tid; i < nk; i += TEAM) {
+      for (int i = tid; i < nk; i += T) {
         double t = W[i * ldw + s];
         W[i * ldw + s] = W[i * ldw + piv];
         W[i * ldw + piv] = t;
@@ -341,34 +417,30 @@ static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_
       }
       tsync();
     }
-    const double xk = W[s * ldw + s];
-    const double sg = xk >= 0.0 ? 1.0 : -1.0;
-    for (int i = s + tid; i < nk; i += TEAM) v[i] = (i == s) ? xk + sg * best : W[i * ldw + s];
-    const double beta = 1.0 / (best * (best + fabs(xk)));
-    tsync();
-    // W columns > s
-    for (int j = s + 1 + tid; j < rk; j += TEAM) {
-      double t = 0.0;
-      for (int i = s; i < nk; i++) t = fma(v[i], W[i * ldw + j], t);
-      w[j] = beta * t;
+    // W columns > s (the reflector stays in v)
+    whouse_apply(W, ldw, s, nk, s, s + 1, rk, nullptr, v, w, best);
+    const double beta = 1.0 / (best * fabs(v[s]));
+    // Q <- Q H on columns [s, nk): row dots split by row of Q and segment of l
+    const int nl = nk - s;
+    const int S = max(1, min(T / nk, nl));
+    for (int idx = tid; idx < S * nk; idx += T) {
+      const int i = idx % nk, sgm = idx / nk;
+      double acc = 0.0;
+      for (int l = s + sgm; l < nk; l += S) acc = fma(Q[i * ldq + l], v[l], acc);
+      if (S == 1) w[i] = beta * acc;
+      else part[sgm * nk + i] = acc;
     }
     tsync();
-    const int cols = rk - s - 1, rows = nk - s;
-    for (int idx = tid; idx < rows * cols; idx += TEAM) {
-      int i = s + idx / cols, j = s + 1 + idx % cols;
-      W[i * ldw + j] = fma(-w[j], v[i], W[i * ldw + j]);
+    if (S > 1) {
+      for (int i = tid; i < nk; i += T) {
+        double acc = part[i];
+        for (int sgm = 1; sgm < S; sgm++) acc += part[sgm * nk + i];
+        w[i] = beta * acc;
+      }
+      tsync();
     }
-    tsync();
-    for (int i = s + tid; i < nk; i += TEAM) W[i * ldw + s] = (i == s) ? -sg * best : 0.0;
-    // Q <- Q H on columns [s, nk)
-    for (int i = tid; i < nk; i += TEAM) {
-      double t = 0.0;
-      for (int l = s; l < nk; l++) t = fma(Q[i * ldq + l], v[l], t);
-      w[i] = beta * t;
-    }
-    tsync();
-    for (int idx = tid; idx < nk * rows; idx += TEAM) {
-      int i = idx / rows, l = s + idx % rows;
+    for (int idx = tid; idx < nk * nl; idx += T) {
+      int i = idx / nl, l = s + idx % nl;
       Q[i * ldq + l] = fma(-w[i], v[l], Q[i * ldq + l]);
     }
     tsync();
@@ -558,60 +630,6 @@ struct LseResult {
   int k1, k2, kc, kq, inconsistent;
 };
 
-static __device__ void whouse_apply(double *M, int ld, int r0, int r1, int piv, int c0, int c1, const int *done,
-                                    double *v, double *w, double nrm) {
-  // reflector from column piv on rows [r0, r1) applied to columns [c0, c1) not done (piv excluded)
-  const int tid = team_rank();
-  const double xk = M[r0 * ld + piv];
-  const double sg = xk >= 0.0 ? 1.0 : -1.0;
-  for (int i = r0 + tid; i < r1; i += TEAM) v[i] = (i == r0) ? xk + sg * nrm : M[i * ld + piv];
-  const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
-  tsync();
-  for (int j = c0 + tid; j < c1; j += TEAM) {
-    if ((done && done[j]) || j == piv) continue;
-    double s0 = 0.0, s1 = 0.0;
-    int i = r0;
-    for (; i + 1 < r1; i += 2) {
-      s0 = fma(v[i], M[i * ld + j], s0);
-      s1 = fma(v[i + 1], M[(i + 1) * ld + j], s1);
-    }
-    if (i < r1) s0 = fma(v[i], M[i * ld + j], s0);
-    w[j] = beta * (s0 + s1);
-  }
-  tsync();
-  const int rows = r1 - r0, cols = c1 - c0;
-  for (int idx = tid; idx < rows * cols; idx += TEAM) {
-    int i = r0 + idx / cols, j = c0 + idx % cols;
-    if ((done && done[j]) || j == piv) continue;
-    M[i * ld + j] = fma(-w[j], v[i], M[i * ld + j]);
-  }
-  tsync();
-  for (int i = r0 + tid; i < r1; i += TEAM) M[i * ld + piv] = (i == r0) ? -sg * nrm : 0.0;
-  tsync();
-}
-
-// pivot search: largest column norm (squared) among columns [c0, c1) not done over rows [r0, r1)
-static __device__ void wpivot(const double *M, int ld, int r0, int r1, int c0, int c1, const int *done,
-                              double &best, int &piv) {
-  double mybest = -1.0;
-  int mypiv = 0x7fffffff;
-  for (int j = c0 + team_rank(); j < c1; j += TEAM) {
-    if (done && done[j]) continue;
-    double s0 = 0.0, s1 = 0.0;
-    int i = r0;
-    for (; i + 1 < r1; i += 2) {
-      s0 = fma(M[i * ld + j], M[i * ld + j], s0);
-      s1 = fma(M[(i + 1) * ld + j], M[(i + 1) * ld + j], s1);
-    }
-    if (i < r1) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
-    double s = s0 + s1;
-    if (s > mybest) { mybest = s; mypiv = j; }
-  }
-  double b2;
-  team_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
-  best = sqrt(b2);
-}
-
 static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne, int nk, double tau_rank,
                                       double tau_inc, double *outC, double *outQ, int ldo, double *scr) {
   const int tid = team_rank();
@@ -644,18 +662,7 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
   om = fmax(1.0, team_max(om));
   const double thr = tau_rank * nu;
   // A
-  int k = 0;
-  while (k < rc) {
-    double best;
-    int piv;
-    wpivot(M, ld, k, rc, 0, ne, done, best, piv);
-    if (piv == 0x7fffffff || !(best > thr)) break;
-    whouse_apply(M, ld, k, rc, piv, 0, nc, done, v, w, best);
-    if (tid == 0) { done[piv] = 1; pc[k] = piv; }
-    tsync();
-    k++;
-  }
-  res.k1 = k;
+  res.k1 = hh_pivoted(M, ld, 0, rc, 0, ne, 0, nc, done, pc, thr, v, w);
   // B
   for (int p = 0; p < res.k1; p++) {
     const int col = pc[p];
@@ -678,31 +685,11 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
     nuq = fmax(nuq, s);
   }
   nuq = sqrt(team_max(nuq));
-  int kk = rc;
-  while (kk < r) {
-    double best;
-    int piv;
-    wpivot(M, ld, kk, r, 0, ne, done, best, piv);
-    if (piv == 0x7fffffff || !(best > tau_rank * nuq) || best == 0.0) break;
-    whouse_apply(M, ld, kk, r, piv, 0, nc, done, v, w, best);
-    if (tid == 0) done[piv] = 1;
-    tsync();
-    kk++;
-  }
-  res.k2 = kk - rc;
+  res.k2 = hh_pivoted(M, ld, rc, r, 0, ne, 0, nc, done, nullptr, tau_rank * nuq, v, w);
+  const int kk = rc + res.k2;
   // D
-  int kd = res.k1;
-  while (kd < rc) {
-    double best;
-    int piv;
-    wpivot(M, ld, kd, rc, ne, off, done, best, piv);
-    if (piv == 0x7fffffff || !(best > thr)) break;
-    whouse_apply(M, ld, kd, rc, piv, ne, nc, done, v, w, best);
-    if (tid == 0) done[piv] = 1;
-    tsync();
-    kd++;
-  }
-  res.kc = kd - res.k1;
+  res.kc = hh_pivoted(M, ld, res.k1, rc, ne, off, ne, nc, done, nullptr, thr, v, w);
+  const int kd = res.k1 + res.kc;
   int bad = 0;
   for (int i = kd + tid; i < rc; i += TEAM)
     if (fabs(M[i * ld + off]) > tau_inc * om) bad = 1;

@@ -37,11 +37,10 @@ struct ChunkInfo {
 // ---- per-stage workspace layout (offsets in doubles) ----
 struct WsLayout {
   int H, UT, t, Y, Z, y, Ab, Bb, cb, Qb, Mb, Rb, qb, rb;
-  int P, p, K, k, Lh, Hx, Phi;
+  int P, p, K, k, Lh, Phi;
   int z, v, pi, dz, dv, dpi, rq, rr, rc, pp;
   int nu, NH, Pnu, pnu, UA, BU, UC, Ux, ru;
   int LT, lt;   // Cholesky factor L' of the reduced stage Hessian (order z, v) and L^{-1}[qbar; rbar]
-  int Qs, RV, RVV, sp;  // square-root Riccati: top rows of Q', value factor R_i, R_vv, linear term s'
   int stride;
 };
 
@@ -68,7 +67,6 @@ __host__ __device__ inline WsLayout make_ws_layout(int n, int m, int pmax, int q
   L.K = take(m * n);
   L.k = take(m);
   L.Lh = take(m * m);
-  L.Hx = take(m * n);
   L.Phi = take(n * n);
   L.z = take(n);
   L.v = take(m);
@@ -91,16 +89,12 @@ __host__ __device__ inline WsLayout make_ws_layout(int n, int m, int pmax, int q
   L.ru = take(m);
   L.LT = take((n + m) * (n + m));
   L.lt = take(n + m);
-  L.Qs = take((n + m) * (2 * n + m));
-  L.RV = take(n * n);
-  L.RVV = take(m * m);
-  L.sp = take(n);
   L.stride = (o + 3) & ~3;
   return L;
 }
 
 // per-stage ints
-enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_RV = 5, SI_STRIDE = 8 };
+enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_STRIDE = 8 };
 // per-chunk-slot ints: rows, left dim, right dim (0 = unary/value)
 enum { CI_ROWS = 0, CI_NA = 1, CI_NB = 2, CI_ROWS2 = 3, CI_STRIDE = 4 };
 

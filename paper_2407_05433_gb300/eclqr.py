@@ -33,7 +33,8 @@ class eclqr_data(ct.Structure):
 
 
 class eclqr_options(ct.Structure):
-    _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int32), ("chunk", ct.c_int32)]
+    _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int32), ("chunk", ct.c_int32),
+                ("team_warps", ct.c_int32)]
 
 
 LAYOUT_FIELDS = ("A", "B", "c", "C", "D", "d", "E", "e", "Q", "M", "R", "qv", "rv", "s0",
@@ -197,7 +198,7 @@ def make_desc(h):
 class Batch:
     """A batch of problems resident on one CUDA device, solved through the C ABI."""
 
-    def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=4, chunk=0):
+    def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=2, chunk=0, team_warps=0):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -208,6 +209,7 @@ class Batch:
         _check(rc, "eclqr_layout")
         opt = eclqr_default_options()
         opt.tau_rank, opt.tau_inc, opt.refine, opt.chunk = tau_rank, tau_inc, refine, chunk
+        opt.team_warps = team_warps
         with torch.cuda.device(self.device):
             rc, self.h = eclqr_create(self.desc, opt)
         _check(rc, "eclqr_create")
