@@ -274,13 +274,7 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       St[idx] = val;
     }
     tsync();
-    for (int col = 0; col < kh && col < rows; col++) {
-      double s0 = 0.0;
-      for (int r = col + tid; r < rows; r += TEAM) s0 = fma(St[r * ld + col], St[r * ld + col], s0);
-      s0 = sqrt(team_sum(s0));
-      if (s0 == 0.0) continue;
-      whouse_apply(St, ld, col, rows, col, col + 1, ld, nullptr, v, w, s0);
-    }
+    for (int col = 0; col < kh && col < rows; col++) hh_step(St, ld, col, rows, col, col, ld, nullptr, v, w, 0.0);
     // sign the z rows to a positive diagonal (rows mu .. kh - 1)
     for (int idx = tid; idx < nx * ld; idx += TEAM) {
       int r = mu + idx / ld, j = idx % ld;

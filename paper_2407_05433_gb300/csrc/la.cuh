@@ -203,13 +203,107 @@ static __device__ void whouse_apply(double *M, int ld, int r0, int r1, int piv, 
   tsync();
 }
 
+__device__ __forceinline__ double *hh_rowk() {
+  __shared__ double rowk[kMaxCols];
+  return rowk;
+}
+
+// One fused Householder step on rows [k, r) with pivot column piv in [a0, a1):
+// one pass over the rows gives the raw products d_j = M_piv . M_j for the
+// not-done columns of [a0, a1) together with d_piv = ||M_piv||^2.  If
+// sqrt(d_piv) <= thr, M is left untouched and 0 is returned; otherwise the
+// reflector (v = M_piv + sign(x_k) ||M_piv|| e_k) is applied to those columns,
+// column piv becomes (-sign(x_k) ||M_piv||, 0, ..., 0), done[piv] is set when
+// done is given, and the norm is returned.  Scratch: v (rows), d (columns).
+static __device__ double hh_step(double *M, int ld, int k, int r, int piv, int a0, int a1, int *done, double *v,
+                                 double *d, double thr) {
+  const int tid = team_rank(), T = TEAM;
+  double *part = hh_part(), *mk = hh_rowk();
+  const int nc = a1 - a0, nr = r - k;
+  // thread -> (column a0 + jj, row segment sgm): rows k + sgm, k + sgm + S, ...
+  const int S = max(1, min(nc > 0 ? T / nc : 1, nr));
+  const int jj0 = (S > 1) ? tid % nc : tid, sgm = (S > 1) ? tid / nc : 0;
+  const bool seg_ok = sgm < S;
+  const int jstep = (S > 1) ? nc : T;
+  for (int i = k + tid; i < r; i += T) v[i] = M[i * ld + piv];
+  for (int jj = tid; jj < nc; jj += T) mk[jj] = M[k * ld + a0 + jj];
+  for (int jj = jj0; seg_ok && jj < nc; jj += jstep) {
+    const int j = a0 + jj;
+    double acc = 0.0;
+    if (j == piv || !(done && done[j]))
+      for (int i = k + sgm; i < r; i += S) acc = fma(M[i * ld + piv], M[i * ld + j], acc);
+    if (S == 1) d[j] = acc;
+    else part[sgm * nc + jj] = acc;
+  }
+  tsync();
+  if (S > 1) {
+    for (int j2 = tid; j2 < nc; j2 += T) {
+      double acc = part[j2];
+      for (int k2 = 1; k2 < S; k2++) acc += part[k2 * nc + j2];
+      d[a0 + j2] = acc;
+    }
+    tsync();
+  }
+  const double nrm = sqrt(d[piv]);
+  if (!(nrm > thr)) return 0.0;
+  const double xk = v[k];
+  const double sg = xk >= 0.0 ? 1.0 : -1.0;
+  const double shift = sg * nrm;                 // v_k - x_k
+  const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
+  for (int jj = jj0; seg_ok && jj < nc; jj += jstep) {
+    const int j = a0 + jj;
+    if (j == piv) {
+      for (int i = k + sgm; i < r; i += S) M[i * ld + piv] = (i == k) ? -shift : 0.0;
+      if (sgm == 0 && done) done[piv] = 1;
+      continue;
+    }
+    if (done && done[j]) continue;
+    const double wj = beta * fma(shift, mk[jj], d[j]);
+    for (int i = k + sgm; i < r; i += S) {
+      const double vi = (i == k) ? xk + shift : v[i];
+      M[i * ld + j] = fma(-wj, vi, M[i * ld + j]);
+    }
+  }
+  tsync();
+  return nrm;
+}
+
+// Team arg-max with one barrier: partials alternate between two buffers by
+// parity, so consecutive calls must be separated by at least one other
+// barrier (hh_step provides it).  Warp stage on the integer pipe: the key of a
+// non-negative double orders like (high word, low word).
+__device__ __forceinline__ void team_argmax1(double val, int idx, int parity, double &bv, int &bi) {
+  __shared__ unsigned long long rk[2][32];
+  __shared__ int ri[2][32];
+  const unsigned long long key = (unsigned long long)__double_as_longlong(val);
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  const unsigned mhi = __reduce_max_sync(kFull, hi);
+  const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
+  const int widx = __reduce_min_sync(kFull, (hi == mhi && lo == mlo) ? idx : 0x7fffffff);
+  if ((threadIdx.x & 31) == 0) {
+    rk[parity][threadIdx.x >> 5] = ((unsigned long long)mhi << 32) | mlo;
+    ri[parity][threadIdx.x >> 5] = widx;
+  }
+  __syncthreads();
+  unsigned long long best = rk[parity][0];
+  int besti = ri[parity][0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+    const unsigned long long k2 = rk[parity][w];
+    const int i2 = ri[parity][w];
+    if (k2 > best || (k2 == best && i2 < besti)) { best = k2; besti = i2; }
+  }
+  bv = __longlong_as_double((long long)best);
+  bi = besti;
+}
+
 // Column-pivoted Householder steps on rows [k, r).  Each step takes the
 // candidate column (in [cand0, cand1), not done) of largest remaining norm;
 // while its exact norm exceeds thr, its reflector is applied to the not-done
-// columns of [app0, app1), it is marked done and recorded in pc (when given).
-// Remaining norms are downdated after every step and evaluated afresh once
-// cancellation has consumed half their digits (the safeguard of LAPACK's
-// xLAQP2, threshold sqrt(eps) = 2^-26).  Returns the number of steps taken.
+// columns of [app0, app1) (which must contain the candidates), it is marked
+// done and recorded in pc (when given).  Remaining norms are downdated after
+// every step and evaluated afresh once cancellation has consumed half their
+// digits (the safeguard of LAPACK's xLAQP2, threshold sqrt(eps) = 2^-26).
+// Returns the number of steps taken.
 static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int cand1, int app0, int app1,
                                  int *done, int *pc, double thr, double *v, double *w) {
   const int tid = team_rank(), T = TEAM;
@@ -224,38 +318,35 @@ static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int
   tsync();
   int steps = 0;
   while (k < r) {
+    // downdate by the row the previous step finished, then pick the largest
     double mybest = -1.0;
     int mypiv = 0x7fffffff;
-    for (int j = cand0 + tid; j < cand1; j += T)
-      if (!done[j] && cn[j] > mybest) { mybest = cn[j]; mypiv = j; }
+    for (int j = cand0 + tid; j < cand1; j += T) {
+      if (done[j]) continue;
+      double nw = cn[j];
+      if (steps > 0) {
+        const double a = M[(k - 1) * ld + j];
+        nw -= a * a;
+        if (nw <= 0x1p-26 * cref[j]) {
+          nw = 0.0;
+          for (int i = k; i < r; i++) nw = fma(M[i * ld + j], M[i * ld + j], nw);
+          cref[j] = nw;
+        }
+        cn[j] = nw;
+      }
+      if (nw > mybest) { mybest = nw; mypiv = j; }
+    }
     double b2;
     int piv;
-    team_argmax(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, b2, piv);
+    team_argmax1(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, steps & 1, b2, piv);
     if (piv == 0x7fffffff) break;
-    double acc = 0.0;
-    for (int i = k + tid; i < r; i += T) acc = fma(M[i * ld + piv], M[i * ld + piv], acc);
-    const double nrm = sqrt(team_sum(acc));
-    if (!(nrm > thr)) break;
-    whouse_apply(M, ld, k, r, piv, app0, app1, done, v, w, nrm);
-    if (tid == 0) {
-      done[piv] = 1;
-      if (pc) pc[steps] = piv;
-    }
-    for (int j = cand0 + tid; j < cand1; j += T) {
-      if (j == piv || done[j]) continue;
-      const double a = M[k * ld + j];
-      double nw = cn[j] - a * a;
-      if (nw <= 0x1p-26 * cref[j]) {
-        nw = 0.0;
-        for (int i = k + 1; i < r; i++) nw = fma(M[i * ld + j], M[i * ld + j], nw);
-        cref[j] = nw;
-      }
-      cn[j] = nw;
-    }
-    tsync();
+    const double nrm = hh_step(M, ld, k, r, piv, app0, app1, done, v, w, thr);
+    if (nrm == 0.0) break;
+    if (tid == 0 && pc) pc[steps] = piv;
     k++;
     steps++;
   }
+  tsync();
   return steps;
 }
 
@@ -705,14 +796,8 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
   tsync();
   // E: compress the remaining cost rows over the kept columns (no pivoting)
   int ke = kk;
-  for (int col = ne; col < off && ke < r; col++) {
-    double s = 0.0;
-    for (int i = ke + tid; i < r; i += TEAM) s = fma(M[i * ld + col], M[i * ld + col], s);
-    s = sqrt(team_sum(s));
-    if (s == 0.0) continue;
-    whouse_apply(M, ld, ke, r, col, col + 1, nc, nullptr, v, w, s);
-    ke++;
-  }
+  for (int col = ne; col < off && ke < r; col++)
+    if (hh_step(M, ld, ke, r, col, col, nc, nullptr, v, w, 0.0) > 0.0) ke++;
   res.kq = ke - kk;
   for (int idx = tid; idx < res.kq * (nk + 1); idx += TEAM) {
     int a = idx / (nk + 1), j = idx - a * (nk + 1);
