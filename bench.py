@@ -9,7 +9,12 @@ Sec. 9 residual, the gate of the metric).  The workload is the degenerate
 n = 12 instance (N = 1024, m = 6, mixed rows U{0..8} per stage, 20% of stages
 with duplicated or D = 0 rows, full-rank terminal rows), seeded and synthetic.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--no-extra]
+
+At N = 1 the line also carries "plain" (the same instance as one chunk: a
+single CTA sweeps every stage, no scan) and "batched" (4096 uneven problems,
+a stand-in for the batched configuration, with the oracle on all host cores
+beside it).
 
 Under torchrun every rank solves its own copy (weak scaling, no collective on
 the data path); rank 0 prints one JSON line.  ``--impl reference`` times the
@@ -124,6 +129,95 @@ def oracle_rate(pb, seconds):
         if time.perf_counter() - t0 > seconds:
             break
     return pb.N / statistics.median(times), n, statistics.median(times)
+
+
+def _timed_runs(batch, steps, flush, stream):
+    """Device time per full pass (build, solve, multipliers, residual) with L2 flushed between passes."""
+    import torch
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def measure_plain(pb, dev, flush, stream, refine, steps=3):
+    """The plain GPU solve: one chunk spanning the horizon, so a single CTA per problem sweeps every stage
+    in order (no scan), beside the chunked scan form of the main line."""
+    from paper_2407_05433_gb300 import eclqr
+    b = eclqr.Batch([pb], device=dev, refine=refine, chunk=pb.N)
+    b.run()
+    ms = _timed_runs(b, steps, flush, stream)
+    (r,) = b.results()
+    b.close()
+    return {"value": pb.N / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "chunk": pb.N,
+            "kkt_resid": r["resid"], "status": r["status"], "gate_passed": r["status"] == 0 and r["resid"] <= KKT_GATE}
+
+
+BATCH_DISTINCT, BATCH_PROBLEMS = 256, 4096
+
+
+def batched_problems():
+    from paper_2407_05433_gb300 import synth
+    base = [synth.config("batched_uneven", index=j) for j in range(BATCH_DISTINCT)]
+    return base, [base[j % BATCH_DISTINCT] for j in range(BATCH_PROBLEMS)]
+
+
+def measure_batched(pbs, dev, flush, stream, refine, steps=3):
+    """Config 4 stand-in: 4096 uneven problems (256 seeded draws of the generator, each repeated 16 times)
+    solved as one batch through the same calls."""
+    import numpy as np
+    from paper_2407_05433_gb300 import eclqr
+    b = eclqr.Batch(pbs, device=dev, refine=refine)
+    b.run()
+    ms = _timed_runs(b, steps, flush, stream)
+    res = b.resid.cpu().numpy()
+    stat = b.status.cpu().numpy()
+    launches = b.launches()
+    b.close()
+    stages = int(sum(p.N for p in pbs))
+    passed = (stat == 0) & (res <= KKT_GATE)
+    return {"value": stages / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "problems": len(pbs),
+            "stages": stages, "distinct_draws": BATCH_DISTINCT, "refine": refine,
+            "status_failures": int((stat != 0).sum()), "resid_max": float(res.max()),
+            "gate_passed_frac": float(passed.mean()), "gate_passed": bool(passed.all())}
+
+
+def _oracle_worker(args):
+    idx, seconds = args
+    import oracle
+    from paper_2407_05433_gb300 import synth
+    pbs = [synth.config("batched_uneven", index=j) for j in idx]
+    for pb in pbs:
+        oracle.solve(pb)
+    stages, spent, t0 = 0, 0.0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for pb in pbs:
+            t = time.perf_counter()
+            oracle.solve(pb)
+            spent += time.perf_counter() - t
+            stages += pb.N
+    return stages, spent
+
+
+def oracle_batched_rate(seconds, cores):
+    """The oracle on the host's cores over a bounded sample of the batch: every process solves its own
+    share of the 256 draws repeatedly for ~seconds; the rate is the sum of the per-process rates."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build_oracle()
+    shares = [list(range(w, BATCH_DISTINCT, cores)) for w in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        out = pool.map(_oracle_worker, [(s, seconds) for s in shares])
+    rate = sum(st / sp for st, sp in out if sp > 0)
+    return {"value": rate, "unit": "stages/s", "cores": cores, "kind": "oracle",
+            "sample": f"the {BATCH_DISTINCT} distinct draws split over {cores} processes, each solving its share "
+                      f"repeatedly for ~{seconds:.0f} s"}
 
 
 def run_reference(args):
@@ -268,6 +362,11 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return 0
 
+    extras = {}
+    if world == 1 and not args.no_extra:
+        extras["plain"] = measure_plain(pb, dev, flush, stream, args.refine)
+        _, bpbs = batched_problems()
+        extras["batched"] = measure_batched(bpbs, dev, flush, stream, args.refine)
     import oracle
     oracle.build_oracle()
     sref = oracle.solve(pb)
@@ -317,6 +416,10 @@ def run_gpu(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    line.update(extras)
+    if "batched" in extras and args.cpu_seconds > 0:
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        line["batched"]["cpu_baseline"] = oracle_batched_rate(args.cpu_seconds, cores)
     print(json.dumps(line), flush=True)
     batch.close()
     if world > 1:
@@ -333,6 +436,7 @@ def main():
     ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the plain-solve and batched lines")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

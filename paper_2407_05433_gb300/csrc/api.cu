@@ -20,8 +20,8 @@ using namespace eclqr;
 namespace {
 
 // dynamic shared memory per task: the 227 KB opt-in limit less room for the
-// static scratch of the team reductions and the Householder core (< 7 KB)
-constexpr int kMaxSmemBytes = 220 * 1024;
+// static scratch of the team reductions and the Householder core (< 8 KB)
+constexpr int kMaxSmemBytes = 219 * 1024;
 constexpr int kTeamWarps = 4;  // default team: one warp per SM sub-partition
 
 struct GroupHost {
