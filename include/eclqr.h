@@ -168,6 +168,36 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name);
 int eclqr_kernel_time(eclqr_handle *h, int64_t *launches, double *total_ms);
 int eclqr_probe_fp64_peak(double *tflops);
 
+/* Gradient outputs (device memory): one array per input of eclqr_data plus s0
+ * (P x n), each with the packed layout of the corresponding input. */
+typedef struct {
+  double *A, *B, *c;
+  double *C, *D, *d;
+  double *E, *e;
+  double *Q, *M, *R, *qv, *rv;
+  double *s0;
+} eclqr_grads;
+
+/* Parameter gradients of a scalar loss l(x, u) by implicit differentiation of
+ * the KKT system (problem statement of Sec. 2 with the stationarity equations
+ * and multiplier sign convention of Sec. 7; the paper itself has no gradients).
+ * (x, u, lam, mu, eta, alpha) is the solution of the problem, (xb, ub, lamb,
+ * mub, etab, alphab) the adjoint: the solution of the same problem with the
+ * same matrices but offsets q' = -dl/dx, r' = -dl/du, c' = d' = e' = 0 and
+ * s0' = 0 (obtained with eclqr_build / eclqr_solve / eclqr_multipliers on
+ * that data).  Writes every element of every array of *out:
+ *   dA_i = -(lam_{i+1} xb_i' + lamb_{i+1} x_i'), dB_i, dC_i, dD_i, dE_i, dM_i alike;
+ *   dQ_i, dR_i symmetrised; dq = -xb, dr = -ub, dc_i = -lamb_{i+1},
+ *   dd = -mub, de = -etab, ds0 = alphab.
+ * The multipliers enter the result, so where they are not unique (the global
+ * constraint Jacobian rank-deficient) neither is the gradient.  Requires a
+ * built handle (any data of the same batch structure).  Asynchronous on
+ * stream; all pointers device, same layouts as eclqr_multipliers. */
+int eclqr_param_grads(eclqr_handle *h, const double *x, const double *u, const double *lam, const double *mu,
+                      const double *eta, const double *alpha, const double *xb, const double *ub,
+                      const double *lamb, const double *mub, const double *etab, const double *alphab,
+                      const eclqr_grads *out, void *stream);
+
 void eclqr_destroy(eclqr_handle *h);
 const char *eclqr_strerror(int code);
 

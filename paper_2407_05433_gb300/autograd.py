@@ -1,0 +1,91 @@
+"""Differentiable solve: x, u of a batch as functions of its packed data.
+
+Backward is implicit differentiation of the KKT system through the C ABI
+(eclqr_param_grads): the adjoint is the solution of the same problems with
+the same matrices, the incoming gradients as linear costs (q' = -dl/dx,
+r' = -dl/du) and zero c, d, e, s0, computed by the same
+eclqr_build / eclqr_solve / eclqr_multipliers calls; the gradients are then
+outer products of solution and adjoint, one CTA per stage.  Gradients of Q_i
+and R_i are symmetrised.  The forward solution (with its multipliers) is kept
+for the backward pass; the handle's factors are rebuilt for the adjoint data.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import eclqr
+
+PARAM_KEYS = eclqr.DATA_KEYS + ("s0",)
+_OFFSETS = ("c", "d", "e")
+
+
+def batch_params(batch, requires_grad=True):
+    """Copies of a Batch's packed device data, one tensor per key of PARAM_KEYS."""
+    return [batch.d[k].detach().clone().requires_grad_(requires_grad) for k in PARAM_KEYS]
+
+
+def _run(batch, data_tensors, s0):
+    """build + solve + multipliers on the given data; returns the six packed outputs and status."""
+    L = batch.layout
+    f64 = dict(dtype=torch.float64, device=batch.device)
+    out = [torch.zeros(max(1, int(getattr(L, k))), **f64) for k in ("x", "u", "lam", "mu", "eta", "alpha")]
+    status = torch.zeros(len(batch.problems), dtype=torch.int32, device=batch.device)
+    data = eclqr.eclqr_data(*[t.data_ptr() for t in data_tensors])
+    st = batch._stream()
+    eclqr._check(eclqr.eclqr_build(batch.h, data, status.data_ptr(), st), "eclqr_build")
+    eclqr._check(eclqr.eclqr_solve(batch.h, s0.data_ptr(), out[0].data_ptr(), out[1].data_ptr(), status.data_ptr(),
+                                   st), "eclqr_solve")
+    eclqr._check(eclqr.eclqr_multipliers(batch.h, *[t.data_ptr() for t in out], status.data_ptr(), st),
+                 "eclqr_multipliers")
+    return out, status
+
+
+class ECLQRSolve(torch.autograd.Function):
+    """forward(batch, *params) -> (x, u), params in PARAM_KEYS order (packed float64 on batch.device)."""
+
+    @staticmethod
+    def forward(ctx, batch, *params):
+        params = [p.detach().contiguous() for p in params]
+        out, status = _run(batch, params[:-1], params[-1])
+        ctx.batch = batch
+        ctx.save_for_backward(*params, *out, status)
+        L = batch.layout
+        x, u = out[0][:int(L.x)], out[1][:int(L.u)]
+        return x.clone(), u.clone()
+
+    @staticmethod
+    def backward(ctx, gx, gu):
+        batch = ctx.batch
+        saved = ctx.saved_tensors
+        nk = len(PARAM_KEYS)
+        params, sol, status = saved[:nk], saved[nk:nk + 6], saved[nk + 6]
+        if int(status.abs().max()) != 0:
+            raise RuntimeError("eclqr forward solve reported a nonzero status; no gradient")
+        L = batch.layout
+        f64 = dict(dtype=torch.float64, device=batch.device)
+        lx = torch.zeros(max(1, int(L.x)), **f64)
+        lu = torch.zeros(max(1, int(L.u)), **f64)
+        if gx is not None:
+            lx[:int(L.x)] = gx
+        if gu is not None:
+            lu[:int(L.u)] = gu
+        adj = {k: p for k, p in zip(PARAM_KEYS, params)}
+        for k in _OFFSETS:
+            adj[k] = torch.zeros_like(adj[k])
+        adj["qv"] = -lx[:adj["qv"].numel()]
+        adj["rv"] = -lu[:adj["rv"].numel()]
+        s0b = torch.zeros_like(adj["s0"])
+        adjd = [adj[k].contiguous() for k in eclqr.DATA_KEYS]
+        wb, st_b = _run(batch, adjd, s0b)
+        grads = [torch.zeros_like(p) for p in params]
+        g = eclqr.eclqr_grads(*[t.data_ptr() for t in grads])
+        eclqr._check(eclqr.eclqr_param_grads(batch.h, *[t.data_ptr() for t in sol], *[t.data_ptr() for t in wb], g,
+                                             batch._stream()), "eclqr_param_grads")
+        if int(st_b.abs().max()) != 0:
+            raise RuntimeError("eclqr adjoint solve reported a nonzero status")
+        return (None, *grads)
+
+
+def solve(batch, *params):
+    """Differentiable x, u (packed) of batch's problems with the given data (PARAM_KEYS order)."""
+    return ECLQRSolve.apply(batch, *params)

@@ -456,6 +456,24 @@ int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const
   return ECLQR_OK;
 }
 
+int eclqr_param_grads(eclqr_handle *h, const double *x, const double *u, const double *lam, const double *mu,
+                      const double *eta, const double *alpha, const double *xb, const double *ub,
+                      const double *lamb, const double *mub, const double *etab, const double *alphab,
+                      const eclqr_grads *out, void *stream) {
+  if (!h || !x || !u || !lam || !alpha || !xb || !ub || !lamb || !alphab || !out) return ECLQR_EINVAL;
+  if (h->lay.mu > 0 && (!mu || !mub || !out->C || !out->D || !out->d)) return ECLQR_EINVAL;
+  if (h->lay.eta > 0 && (!eta || !etab || !out->E || !out->e)) return ECLQR_EINVAL;
+  if (!out->A || !out->B || !out->c || !out->Q || !out->M || !out->R || !out->qv || !out->rv || !out->s0)
+    return ECLQR_EINVAL;
+  if (!h->built) return ECLQR_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Sol w{x, u, lam, mu, eta, alpha}, wb{xb, ub, lamb, mub, etab, alphab};
+  const GradOut o{out->A, out->B, out->c, out->C, out->D, out->d, out->E, out->e,
+                  out->Q, out->M, out->R, out->qv, out->rv, out->s0};
+  for (auto &gh : h->groups) TRY(launch(h, k_param_grads, gh.g.nstage, 0, st, gh.g, w, wb, o));
+  return ECLQR_OK;
+}
+
 int eclqr_reduced_dims(eclqr_handle *h, int32_t *nbar, int32_t *mbar, void *stream) {
   if (!h || !nbar || !mbar) return ECLQR_EINVAL;
   if (!h->built) return ECLQR_ESTATE;
@@ -497,7 +515,7 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
       {"k_recover", (const void *)k_recover}, {"k_dual_stage", (const void *)k_dual_stage},
       {"k_dual_terminal", (const void *)k_dual_terminal}, {"k_dual_up", (const void *)k_dual_up},
       {"k_dual_down", (const void *)k_dual_down}, {"k_dual_root", (const void *)k_dual_root},
-      {"k_dual_leaf", (const void *)k_dual_leaf}, {"k_kkt_residual", (const void *)k_kkt_residual}};
+      {"k_dual_leaf", (const void *)k_dual_leaf}, {"k_kkt_residual", (const void *)k_kkt_residual}, {"k_param_grads", (const void *)k_param_grads}};
   for (const auto &e : table)
     if (std::strcmp(e.name, name) == 0) {
       if (h->ev.empty()) {

@@ -1,0 +1,78 @@
+// k_grad.cu -- parameter gradients of a scalar loss l(x, u) by implicit
+// differentiation of the KKT system of the problem (Sec. 2 problem statement,
+// Sec. 7 stationarity with its Lagrangian sign convention).  The paper itself
+// has no gradients.
+//
+// The KKT map F(w, theta) = 0 over w = (x, u, lambda, mu, eta, alpha) has the
+// symmetric Jacobian K = dF/dw (the Hessian of the Lagrangian).  For the
+// adjoint wb solving K wb = dl/dw -- an instance of the same problem with the
+// same matrices and offsets q' = -dl/dx, r' = -dl/du, c' = d' = e' = 0,
+// s_0' = 0 -- the gradient is dl/dtheta = -wb' dF/dtheta.  F is bilinear in
+// (matrix, variable), so every stage contributes outer products:
+//   dA_i = -(lambda_{i+1} xb_i' + lambdab_{i+1} x_i')   dB_i = -(lambda_{i+1} ub_i' + lambdab_{i+1} u_i')
+//   dC_i = -(mu_i xb_i' + mub_i x_i')                   dD_i = -(mu_i ub_i' + mub_i u_i')
+//   dE_i = -(eta_i xb_i' + etab_i x_i')                  dM_i = -(xb_i u_i' + x_i ub_i')
+//   dQ_i = -sym(xb_i x_i'), dR_i = -sym(ub_i u_i')      (symmetric parameters: symmetrised gradient)
+//   dq_i = -xb_i, dr_i = -ub_i, dc_i = -lambdab_{i+1}, dd_i = -mub_i, de_i = -etab_i, ds_0 = alphab.
+// One task (CTA) per stage; every output element is written exactly once.
+#include "kernels.cuh"
+
+namespace eclqr {
+
+__global__ void k_param_grads(Group g, Sol w, Sol wb, GradOut o) {
+  const int s = team_task();
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+  const double *xi = w.x + P.ox + (size_t)i * n, *xbi = wb.x + P.ox + (size_t)i * n;
+  if (i < P.N) {
+    const double *ui = w.u + P.ou + (size_t)i * m, *ubi = wb.u + P.ou + (size_t)i * m;
+    const double *ln = w.lam + P.olam + (size_t)(i + 1) * n, *lbn = wb.lam + P.olam + (size_t)(i + 1) * n;
+    for (int idx = tid; idx < n * n; idx += TEAM) {
+      const int a = idx / n, b = idx - a * n;
+      o.A[P.oA + (size_t)i * n * n + idx] = -(ln[a] * xbi[b] + lbn[a] * xi[b]);
+      o.Q[P.oQ + (size_t)i * n * n + idx] = -0.5 * (xbi[a] * xi[b] + xi[a] * xbi[b]);
+    }
+    for (int idx = tid; idx < n * m; idx += TEAM) {
+      const int a = idx / m, b = idx - a * m;
+      o.B[P.oB + (size_t)i * n * m + idx] = -(ln[a] * ubi[b] + lbn[a] * ui[b]);
+      o.M[P.oM + (size_t)i * n * m + idx] = -(xbi[a] * ui[b] + xi[a] * ubi[b]);
+    }
+    for (int idx = tid; idx < m * m; idx += TEAM) {
+      const int a = idx / m, b = idx - a * m;
+      o.R[P.oR + (size_t)i * m * m + idx] = -0.5 * (ubi[a] * ui[b] + ui[a] * ubi[b]);
+    }
+    for (int a = tid; a < n; a += TEAM) {
+      o.c[P.oc + (size_t)i * n + a] = -lbn[a];
+      o.qv[P.oqv + (size_t)i * n + a] = -xbi[a];
+    }
+    for (int a = tid; a < m; a += TEAM) o.rv[P.orv + (size_t)i * m + a] = -ubi[a];
+    const double *mui = w.mu + P.omu + S.prow, *mubi = wb.mu + P.omu + S.prow;
+    for (int idx = tid; idx < S.p * n; idx += TEAM) {
+      const int k = idx / n, b = idx - k * n;
+      o.C[P.oC + (size_t)S.prow * n + idx] = -(mui[k] * xbi[b] + mubi[k] * xi[b]);
+    }
+    for (int idx = tid; idx < S.p * m; idx += TEAM) {
+      const int k = idx / m, b = idx - k * m;
+      o.D[P.oD + (size_t)S.prow * m + idx] = -(mui[k] * ubi[b] + mubi[k] * ui[b]);
+    }
+    for (int k = tid; k < S.p; k += TEAM) o.d[P.od + S.prow + k] = -mubi[k];
+  } else {
+    for (int idx = tid; idx < n * n; idx += TEAM) {
+      const int a = idx / n, b = idx - a * n;
+      o.Q[P.oQ + (size_t)i * n * n + idx] = -0.5 * (xbi[a] * xi[b] + xi[a] * xbi[b]);
+    }
+    for (int a = tid; a < n; a += TEAM) o.qv[P.oqv + (size_t)i * n + a] = -xbi[a];
+  }
+  const double *etai = w.eta + P.oeta + S.qrow, *etabi = wb.eta + P.oeta + S.qrow;
+  for (int idx = tid; idx < S.q * n; idx += TEAM) {
+    const int k = idx / n, b = idx - k * n;
+    o.E[P.oE + (size_t)S.qrow * n + idx] = -(etai[k] * xbi[b] + etabi[k] * xi[b]);
+  }
+  for (int k = tid; k < S.q; k += TEAM) o.e[P.oe + S.qrow + k] = -etabi[k];
+  if (i == 0)
+    for (int a = tid; a < n; a += TEAM) o.s0[P.os0 + a] = wb.alpha[P.oalpha + a];
+}
+
+}  // namespace eclqr

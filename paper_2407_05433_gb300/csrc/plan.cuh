@@ -119,6 +119,14 @@ struct Group {
   double tau_rank, tau_inc;
 };
 
+// a primal-dual solution (device pointers, batch-packed as in the ABI) and gradient outputs
+struct Sol {
+  const double *x, *u, *lam, *mu, *eta, *alpha;
+};
+struct GradOut {
+  double *A, *B, *c, *C, *D, *d, *E, *e, *Q, *M, *R, *qv, *rv, *s0;
+};
+
 __device__ __forceinline__ void set_status(const Group &g, int prob, int code) {
   atomicCAS(g.status + g.prob[prob].id, 0, code);
 }

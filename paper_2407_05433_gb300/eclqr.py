@@ -32,6 +32,10 @@ class eclqr_data(ct.Structure):
     _fields_ = [(k, ct.c_void_p) for k in ("A", "B", "c", "C", "D", "d", "E", "e", "Q", "M", "R", "qv", "rv")]
 
 
+class eclqr_grads(ct.Structure):
+    _fields_ = [(k, ct.c_void_p) for k in ("A", "B", "c", "C", "D", "d", "E", "e", "Q", "M", "R", "qv", "rv", "s0")]
+
+
 class eclqr_options(ct.Structure):
     _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int32), ("chunk", ct.c_int32),
                 ("team_warps", ct.c_int32)]
@@ -83,6 +87,8 @@ def load():
     lib.eclqr_probe_fp64_peak.restype = i32
     lib.eclqr_kkt_residual_noalloc.argtypes = [ct.POINTER(eclqr_desc), ct.POINTER(eclqr_data)] + [vp] * 9
     lib.eclqr_kkt_residual_noalloc.restype = i32
+    lib.eclqr_param_grads.argtypes = [vp] * 13 + [ct.POINTER(eclqr_grads), vp]
+    lib.eclqr_param_grads.restype = i32
     lib.eclqr_destroy.argtypes = [vp]
     lib.eclqr_destroy.restype = None
     lib.eclqr_strerror.argtypes = [i32]
@@ -134,6 +140,11 @@ def eclqr_kkt_residual(h, s0, x, u, lam, mu, eta, alpha, resid, stream):
 def eclqr_kkt_residual_noalloc(desc, data, s0, x, u, lam, mu, eta, alpha, resid, stream):
     return load().eclqr_kkt_residual_noalloc(ct.byref(desc), ct.byref(data), s0, x, u, lam, mu, eta, alpha,
                                              resid, stream)
+
+
+def eclqr_param_grads(h, x, u, lam, mu, eta, alpha, xb, ub, lamb, mub, etab, alphab, out, stream):
+    return load().eclqr_param_grads(h, x, u, lam, mu, eta, alpha, xb, ub, lamb, mub, etab, alphab,
+                                    ct.byref(out), stream)
 
 
 def eclqr_reduced_dims(h, nbar, mbar, stream):

@@ -1,0 +1,88 @@
+"""Gradients through the CUDA path (autograd over eclqr_param_grads) against the
+oracle's dense implicit gradient and against central finite differences of the
+CUDA solve itself (symmetric Q_i, R_i only in the dense comparison: a
+single-entry step leaves the symmetric parameter space).  Loss of the differentiable-batch configuration:
+l = sum ||x_i - x_ref,i||^2 + sum ||u_i||^2."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.adjoint import implicit_gradients
+from paper_2407_05433_gb300 import eclqr, synth
+
+pytestmark = pytest.mark.gpu
+FIELDS = ("A", "B", "c", "C", "D", "d", "E", "e", "Q", "M", "R", "qv", "rv", "s0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2407_05433_gb300 import build as b
+    b.build()
+    eclqr.load()
+
+
+def _problems():
+    q = np.zeros(8, np.int32); q[4] = 1; q[7] = 2
+    return [synth.config("diff_batch", index=0, N=8), synth.config("diff_batch", index=1, N=6),
+            synth.make_problem(45, 7, 5, 3, 2, q, cross=True)]
+
+
+def _setup():
+    import torch
+    from paper_2407_05433_gb300 import autograd as ag
+    pbs = _problems()
+    batch = eclqr.Batch(pbs)
+    rng = np.random.default_rng(3)
+    xrefs = [rng.standard_normal((pb.N + 1, pb.n)) for pb in pbs]
+    xref = torch.from_numpy(np.concatenate([x.ravel() for x in xrefs])).to(batch.device)
+    params = ag.batch_params(batch)
+    return torch, ag, pbs, batch, xrefs, xref, params
+
+
+def _loss(torch, ag, batch, xref, params):
+    x, u = ag.solve(batch, *params)
+    return ((x - xref) ** 2).sum() + (u ** 2).sum()
+
+
+def test_autograd_matches_dense_implicit_gradient():
+    torch, ag, pbs, batch, xrefs, xref, params = _setup()
+    try:
+        loss = _loss(torch, ag, batch, xref, params)
+        loss.backward()
+        got = {k: p.grad.cpu().numpy() for k, p in zip(ag.PARAM_KEYS, params)}
+        exp = {k: [] for k in FIELDS}
+        for pb, xr in zip(pbs, xrefs):
+            s = oracle.dense_kkt(pb)
+            G = implicit_gradients(pb, 2.0 * (s["x"] - xr), 2.0 * s["u"])
+            for k in FIELDS:
+                exp[k].append(np.asarray(G[k]).ravel())
+        for k in FIELDS:
+            e = np.concatenate(exp[k])
+            if e.size == 0:
+                continue
+            err = np.max(np.abs(got[k][:e.size] - e)) / max(1.0, np.max(np.abs(e)))
+            assert err <= 1e-8, (k, err)
+    finally:
+        batch.close()
+
+
+def test_autograd_matches_finite_differences_of_the_cuda_solve():
+    torch, ag, pbs, batch, xrefs, xref, params = _setup()
+    try:
+        loss = _loss(torch, ag, batch, xref, params)
+        loss.backward()
+        rng = np.random.default_rng(11)
+        h = 1e-6
+        for k in ("A", "B", "c", "C", "D", "M", "E", "e", "qv", "rv", "s0"):
+            p = params[ag.PARAM_KEYS.index(k)]
+            for flat in rng.choice(p.numel(), size=3, replace=False):
+                def f(delta):
+                    q = [t.detach().clone() for t in params]
+                    q[ag.PARAM_KEYS.index(k)][flat] += delta
+                    with torch.no_grad():
+                        return float(_loss(torch, ag, batch, xref, q))
+                fd = (f(h) - f(-h)) / (2 * h)
+                g = float(p.grad[flat])
+                assert abs(fd - g) <= 1e-5 * max(1.0, abs(g)), (k, int(flat), fd, g)
+    finally:
+        batch.close()
