@@ -58,6 +58,7 @@ extern "C" {
 #define ECLQR_ECUDA (-3)     /* a CUDA call or kernel launch failed                */
 #define ECLQR_ESTATE (-4)    /* call order violated (e.g. solve before build)      */
 #define ECLQR_ETOOBIG (-5)   /* batch larger than the fixed array of eclqr_kkt_residual_noalloc */
+#define ECLQR_ESMEM (-6)     /* (n, m, max p_i, max q_i) of a group need more shared memory per task than a CTA holds */
 
 /* per-problem status codes (device array) */
 #define ECLQR_STATUS_OK 0
@@ -115,7 +116,11 @@ void eclqr_default_options(eclqr_options *opt);
 int eclqr_layout(const eclqr_desc *desc, eclqr_layout_info *out);
 
 /* Plans the batch and allocates the device workspace (cudaMalloc) on the
- * current device.  opt may be NULL (defaults).  Host-synchronous. */
+ * current device.  opt may be NULL (defaults).  Host-synchronous.  Problems
+ * are grouped by (n, m); a group whose n, m, largest p_i and largest q_i need
+ * more than 219 KB of shared memory in some kernel is rejected with
+ * ECLQR_ESMEM before anything is allocated (n <= 28 fits for any row counts up
+ * to ECLQR_MAX_ROWS; n = 32, m = 16 needs max p_i + max q_i <= 47). */
 int eclqr_create(const eclqr_desc *desc, const eclqr_options *opt, eclqr_handle **out);
 
 /* Feasible-domain scan and stagewise elimination of Algorithm 1 (Sec. 3-5)

@@ -250,6 +250,19 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     }
     g.pmax = pmax;
     g.qmax = qmax;
+    // every kernel's shared memory must fit one task (one CTA)
+    {
+      const int n = g.n, m = g.m;
+      const int need = std::max({smem_primal_sweep(n, m, pmax, qmax), smem_rel_level(n, pmax, qmax), smem_param(n),
+                                 smem_elim(n, m, pmax), smem_lqr_up(n, m), smem_lqr_level(n), smem_riccati(n, m),
+                                 smem_aff(n, m), smem_dual_stage(n, m), smem_dual_sweep(n, m, pmax, qmax),
+                                 smem_dual_leaf(n, m, pmax, qmax)});
+      if ((size_t)need * sizeof(double) > (size_t)kMaxSmemBytes) {
+        for (auto &x : h->groups) cudaFree(x.dmem);
+        delete h;
+        return ECLQR_ESMEM;
+      }
+    }
     std::vector<ProbInfo> gp;
     std::vector<StageInfo> gs;
     std::vector<ChunkInfo> gc;
@@ -324,18 +337,6 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     g.CS[1] = (double *)(base + o_CS1);
     g.CI[0] = (int *)(base + o_CI0);
     g.CI[1] = (int *)(base + o_CI1);
-    // every kernel's shared memory must fit one task (one CTA)
-    const int n = g.n, m = g.m;
-    const int need = std::max({smem_primal_sweep(n, m, pmax, qmax), smem_rel_level(n, pmax, qmax), smem_param(n),
-                               smem_elim(n, m, pmax), smem_lqr_up(n, m), smem_lqr_level(n), smem_riccati(n, m),
-                               smem_aff(n, m), smem_dual_stage(n, m), smem_dual_sweep(n, m, pmax, qmax),
-                               smem_dual_leaf(n, m, pmax, qmax)});
-    if ((size_t)need * sizeof(double) > (size_t)kMaxSmemBytes) {
-      cudaFree(gh.dmem);
-      for (auto &x : h->groups) cudaFree(x.dmem);
-      delete h;
-      return ECLQR_EINVAL;
-    }
     h->groups.push_back(gh);
   }
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -551,6 +552,7 @@ const char *eclqr_strerror(int code) {
     case ECLQR_ECUDA: return "CUDA error";
     case ECLQR_ESTATE: return "call out of order";
     case ECLQR_ETOOBIG: return "batch exceeds the fixed array of eclqr_kkt_residual_noalloc";
+    case ECLQR_ESMEM: return "dimensions need more shared memory per task than a CTA can hold";
     default: return "unknown error";
   }
 }

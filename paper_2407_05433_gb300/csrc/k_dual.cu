@@ -24,10 +24,17 @@
 namespace eclqr {
 
 __host__ int smem_dual_stage(int n, int m) { return n * n + 4 * n + m + 8; }
+// Down-sweep scratch for the forward maps (Wt, Qf, X, Ys, tq, perm), in doubles.
+// It is live only between the two projections of a stage, when M is dead, so
+// it sits inside M whenever it fits there.
+__host__ __device__ inline int dual_solve_scratch(int n, int rows) {
+  return n * rows + n * n + n * (n + 1) + rows * (n + 1) + 4 * n + rows;
+}
 __host__ int smem_dual_sweep(int n, int m, int pmax, int qmax) {
-  int rows = 3 * n + m, ldm = pmax + qmax + 3 * n + 1;
-  return 2 * n * (2 * n + 1) + rows * ldm + rows * (2 * n + 1) + rows + 2 * ldm + n * n + n * rows +
-         rows * (n + 1) + n * (n + 1) + 6 * n + rows + 16;
+  const int rows = 3 * n + m, ldm = pmax + qmax + 3 * n + 1, ldr = 2 * n + 1;
+  const int base = 2 * n * ldr + rows * ldm + rows * ldr + rows + 2 * ldm;
+  const int solve = dual_solve_scratch(n, rows);
+  return base + (solve <= rows * ldm ? 0 : solve) + 16;
 }
 __host__ int smem_dual_leaf(int n, int m, int pmax, int qmax) {
   int w = pmax + qmax, rows = n + m;
@@ -275,7 +282,8 @@ __global__ void k_dual_down(Group g, int fin, int per_task) {
   double *M = Ns + 2 * n * ldr;             // rows_max x ldm_max
   double *K = M + rows_max * ldm_max;       // rows_max x (2n+1): rows after eliminating mu,eta
   double *scr = K + rows_max * ldr;         // projection scratch
-  double *Wt = scr + rows_max + 2 * ldm_max;  // n x rows
+  // forward-map scratch: inside M (dead between the two projections) when it fits
+  double *Wt = (dual_solve_scratch(n, rows_max) <= rows_max * ldm_max) ? M : scr + rows_max + 2 * ldm_max;  // n x rows
   double *Qf = Wt + n * rows_max;           // n x n
   double *X = Qf + n * n;                   // n x (n+1)
   double *Ys = X + n * (n + 1);             // rows x (n+1)
@@ -319,6 +327,7 @@ __global__ void k_dual_down(Group g, int fin, int per_task) {
           int r = idx / (r0 + 1), j = idx - r * (r0 + 1);
           if (j < r0) Pnu[r * n + j] = X[r * (n + 1) + j]; else pnu[r] = X[r * (n + 1) + j];
         }
+        tsync();  // X may live inside M, which is rewritten next
       }
       // N_i: project nu_{i+1} out of the same rows
       for (int idx = tid; idx < kr * (r1 + r0 + 1); idx += TEAM) {

@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libeclqr.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETOOBIG, ESMEM = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "ok", 1: "infeasible_suffix", 2: "infeasible_x0", 3: "rank_inconsistent",
                 4: "nonconvex", 5: "dual_inconsistent"}
 

@@ -88,3 +88,19 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.eclqr_solve(None, None, None, None, None, None) == eclqr.EINVAL
     assert eclqr.eclqr_launch_count(None) == 0
     lib.eclqr_destroy(None)
+
+
+def _desc_arrays(N, n, m, p, q):
+    h = {"N": np.array([N], np.int32), "n": np.array([n], np.int32), "m": np.array([m], np.int32),
+         "p": np.full(N, p, np.int32), "q": np.zeros(N + 1, np.int32)}
+    h["q"][N] = q
+    return h
+
+
+def test_dimensions_beyond_shared_memory_rejected_before_allocation(lib):
+    """n = 32, m = 16 with 32 mixed rows and 32 terminal rows needs more shared memory per task
+    than a CTA holds: eclqr_create says so (ECLQR_ESMEM) before any device allocation."""
+    h = _desc_arrays(4, 32, 16, 32, 32)
+    rc, handle = eclqr.eclqr_create(eclqr.make_desc(h))
+    assert rc == eclqr.ESMEM and not handle
+    assert "shared memory" in eclqr.eclqr_strerror(eclqr.ESMEM)

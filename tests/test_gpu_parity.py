@@ -171,3 +171,13 @@ def test_infeasible_initial_state_status():
     st = int(b.status.cpu()[0])
     b.close()
     assert eclqr.STATUS_NAMES[st] == "infeasible_x0"
+
+
+def test_maximum_dimensions():
+    """n = ECLQR_MAX_N = 32, m = 16 with 12 mixed rows per stage and a 16-row terminal
+    constraint: among the largest shapes whose kernels fit a CTA's shared memory."""
+    q = np.zeros(25, np.int32); q[24] = 16
+    pbs = [synth.make_problem(61, 24, 32, 16, 12, q), synth.make_problem(62, 9, 32, 16, 5, 0, cross=True)]
+    res, dims = gpu_run(pbs)
+    for pb, r, d in zip(pbs, res, dims):
+        check(pb, r, d)
