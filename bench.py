@@ -113,6 +113,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, world, device):
+    """The largest of every rank's value (the job's time is its slowest rank's); identity at N = 1."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def all_ranks(flag, world, device):
+    """True when every rank's flag is true (the gate holds for the whole job)."""
+    if world <= 1:
+        return bool(flag)
+    import torch
+    t = torch.tensor([1 if flag else 0], dtype=torch.int32, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
+    return bool(int(t.item()))
+
+
+def job_rate(world, stages_per_rank, ms):
+    """Whole-job throughput: every rank solves its own copy (weak scaling) within the slowest rank's time."""
+    return world * stages_per_rank / (ms * 1e-3)
+
+
 def oracle_rate(pb, seconds):
     """The CPU oracle as it stands, one thread, repeated over the workload for ~seconds."""
     import oracle
@@ -318,12 +343,9 @@ def run_gpu(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     (res,) = batch.results()
-    ok = res["status"] == 0 and res["resid"] <= KKT_GATE
+    ok = all_ranks(res["status"] == 0 and res["resid"] <= KKT_GATE, world, dev)
 
     # end to end through the C ABI with host buffers: pinned H2D of the inputs,
     # the four calls, D2H of every output, all inside the timed region
@@ -353,8 +375,8 @@ def run_gpu(args):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms += ev0.elapsed_time(ev1)
-    e2e_ms /= e2e_steps
-    e2e_ok = int(host_out["status"][0]) == 0 and float(host_out["resid"][0]) <= KKT_GATE
+    e2e_ms = max_over_ranks(e2e_ms / e2e_steps, world, dev)
+    e2e_ok = all_ranks(int(host_out["status"][0]) == 0 and float(host_out["resid"][0]) <= KKT_GATE, world, dev)
 
     if rank != 0:
         batch.close()
@@ -373,7 +395,7 @@ def run_gpu(args):
     phase = sref.phase_flops
     step_flops = float(np.sum(phase[:6]))
     ms = total_ms / args.steps
-    value = world * pb.N / (ms * 1e-3)
+    value = job_rate(world, pb.N, ms)
     peak = eclqr.eclqr_probe_fp64_peak()
     dom_ms = t_dom / max(1, nl_dom)
     launches_per_step_dom = nl_dom / args.steps
@@ -402,7 +424,7 @@ def run_gpu(args):
                    "chunk": args.chunk or "auto", "l2": "256 MB buffer written between timed steps",
                    "kkt_resid": res["resid"], "status": res["status"], "gate_passed": ok,
                    "step": "eclqr_build + eclqr_solve + eclqr_multipliers + eclqr_kkt_residual"},
-        "e2e": {"value": (world * pb.N / (e2e_ms * 1e-3)) if e2e_ok else 0.0, "unit": "stages/s",
+        "e2e": {"value": job_rate(world, pb.N, e2e_ms) if e2e_ok else 0.0, "unit": "stages/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
