@@ -11,9 +11,10 @@ with duplicated or D = 0 rows, full-rank terminal rows), seeded and synthetic.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--no-extra]
 
-At N = 1 the line also carries "plain" (the same instance as one chunk: a
-single CTA sweeps every stage, no scan) and "batched" (4096 uneven problems,
-a stand-in for the batched configuration, with the oracle on all host cores
+At N = 1 the line also carries "graph" (the same step captured once into a
+CUDA graph and replayed), "plain" (the same instance as one chunk: a single
+CTA sweeps every stage, no scan) and "batched" (4096 uneven problems, a
+stand-in for the batched configuration, with the oracle on all host cores
 beside it).
 
 Under torchrun every rank solves its own copy (weak scaling, no collective on
@@ -169,6 +170,27 @@ def _timed_runs(batch, steps, flush, stream):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     return statistics.median(times)
+
+
+def measure_graph(batch, pb, flush, stream, steps):
+    """The same step captured once into a CUDA graph and replayed (same kernels, same order)."""
+    import torch
+    nl = batch.capture()
+    for _ in range(3):
+        batch.replay()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    (r,) = batch.results()
+    return {"value": pb.N / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "launches_per_replay": nl,
+            "kkt_resid": r["resid"], "gate_passed": r["status"] == 0 and r["resid"] <= KKT_GATE}
 
 
 def measure_plain(pb, dev, flush, stream, refine, steps=3):
@@ -386,6 +408,7 @@ def run_gpu(args):
 
     extras = {}
     if world == 1 and not args.no_extra:
+        extras["graph"] = measure_graph(batch, pb, flush, stream, max(5, args.steps // 2))
         extras["plain"] = measure_plain(pb, dev, flush, stream, args.refine)
         _, bpbs = batched_problems()
         extras["batched"] = measure_batched(bpbs, dev, flush, stream, args.refine)

@@ -268,6 +268,31 @@ class Batch:
         if residual and multipliers:
             self.residual()
 
+    def capture(self):
+        """Capture one full pass (build, solve, multipliers, residual) into a CUDA graph.
+
+        The graph keeps the current device pointers: refresh the inputs in place (self.d)
+        and call replay().  A first eager pass on a side stream sets every kernel's
+        shared-memory attribute before capture.  Returns the number of kernel launches
+        one replay performs."""
+        torch = self.torch
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.run()
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        torch.cuda.synchronize(self.device)
+        before = self.launches()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+            self.run()
+        self.graph = graph
+        self.graph_launches = self.launches() - before
+        return self.graph_launches
+
+    def replay(self):
+        self.graph.replay()
+
     def reduced_dims(self):
         torch = self.torch
         nb = torch.zeros(int(self.layout.x // 1), dtype=torch.int32, device=self.device)
