@@ -26,6 +26,8 @@ constexpr int kTeamWarps = 4;  // default team: one warp per SM sub-partition
 
 struct GroupHost {
   Group g;
+  cudaStream_t s = nullptr;     // the group's own stream when the batch has several groups
+  cudaEvent_t done = nullptr;   // records the end of the group's work on s
   int maxnch = 0;
   int levels = 0;
   void *dmem = nullptr;
@@ -52,6 +54,7 @@ struct eclqr_handle {
   const void *timed = nullptr;
   std::vector<cudaEvent_t> ev;
   int nev = 0;
+  cudaEvent_t fork = nullptr;   // the caller's stream position the group streams start from
 };
 
 namespace {
@@ -87,6 +90,28 @@ int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cu
     int _rc = (x);             \
     if (_rc != ECLQR_OK) return _rc; \
   } while (0)
+
+// Groups of different (n, m) share no data: with more than one group, each
+// runs on its own stream, forked from the caller's stream and joined back
+// into it, so that small groups fill the SMs a large group leaves idle.
+int fork_groups(eclqr_handle *h, cudaStream_t st) {
+  if (h->groups.size() < 2) return ECLQR_OK;
+  if (cudaEventRecord(h->fork, st) != cudaSuccess) return ECLQR_ECUDA;
+  for (auto &gh : h->groups)
+    if (cudaStreamWaitEvent(gh.s, h->fork, 0) != cudaSuccess) return ECLQR_ECUDA;
+  return ECLQR_OK;
+}
+cudaStream_t group_stream(const eclqr_handle *h, const GroupHost &gh, cudaStream_t st) {
+  return h->groups.size() < 2 ? st : gh.s;
+}
+int join_groups(eclqr_handle *h, cudaStream_t st) {
+  if (h->groups.size() < 2) return ECLQR_OK;
+  for (auto &gh : h->groups) {
+    if (cudaEventRecord(gh.done, gh.s) != cudaSuccess) return ECLQR_ECUDA;
+    if (cudaStreamWaitEvent(st, gh.done, 0) != cudaSuccess) return ECLQR_ECUDA;
+  }
+  return ECLQR_OK;
+}
 
 int validate(const eclqr_desc *d) {
   if (!d || d->num_problems < 1 || !d->N || !d->n || !d->m || !d->p || !d->q) return ECLQR_EINVAL;
@@ -339,6 +364,17 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     g.CI[1] = (int *)(base + o_CI1);
     h->groups.push_back(gh);
   }
+  if (h->groups.size() > 1) {
+    bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (auto &gh : h->groups) {
+      ok = ok && cudaStreamCreateWithFlags(&gh.s, cudaStreamNonBlocking) == cudaSuccess;
+      ok = ok && cudaEventCreateWithFlags(&gh.done, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      eclqr_destroy(h);
+      return ECLQR_ECUDA;
+    }
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     for (auto &x : h->groups) cudaFree(x.dmem);
     delete h;
@@ -352,28 +388,31 @@ int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *
   if (!h || !data || !status) return ECLQR_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(status, 0, sizeof(int32_t) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
+  TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
+    const cudaStream_t gst = group_stream(h, gh, st);
     Group &g = gh.g;
     g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
     g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
     g.status = status;
     const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
     const int sw = smem_primal_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
-    TRY(launch(h, k_terminal, g.nprob, sw, st, g, sw));
-    TRY(launch(h, k_primal_up, g.nslot, sw, st, g, sw));
+    TRY(launch(h, k_terminal, g.nprob, sw, gst, g, sw));
+    TRY(launch(h, k_primal_up, g.nslot, sw, gst, g, sw));
     int src = 0;
     for (int k = 0; k < gh.levels; k++, src ^= 1)
-      TRY(launch(h, k_rel_level, g.nslot, sl, st, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
-    TRY(launch(h, k_primal_down, g.nslot, sw, st, g, src, sw));
+      TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
+    TRY(launch(h, k_primal_down, g.nslot, sw, gst, g, src, sw));
     const int sp = smem_param(n), se = smem_elim(n, m, pm);
-    TRY(launch(h, k_param, g.nstage, sp, st, g, sp));
-    TRY(launch(h, k_elim, g.nstage, se, st, g, se));
+    TRY(launch(h, k_param, g.nstage, sp, gst, g, sp));
+    TRY(launch(h, k_elim, g.nstage, se, gst, g, se));
     const int su = smem_lqr_up(n, m), slv = smem_lqr_level(n), sr = smem_riccati(n, m);
-    TRY(launch(h, k_lqr_up, g.nslot, su, st, g, su));
+    TRY(launch(h, k_lqr_up, g.nslot, su, gst, g, su));
     src = 0;
-    for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_lqr_level, g.nslot, slv, st, g, src, 1 << k, slv));
-    TRY(launch(h, k_riccati_down, g.nslot, sr, st, g, src, sr));
+    for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_lqr_level, g.nslot, slv, gst, g, src, 1 << k, slv));
+    TRY(launch(h, k_riccati_down, g.nslot, sr, gst, g, src, sr));
   }
+  TRY(join_groups(h, st));
   h->built = true;
   h->solved = false;
   return ECLQR_OK;
@@ -396,23 +435,26 @@ int eclqr_solve(eclqr_handle *h, const double *s0, double *x, double *u, int32_t
   if (!h || !s0 || !x || !u || !status) return ECLQR_EINVAL;
   if (!h->built) return ECLQR_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
+  TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
+    const cudaStream_t gst = group_stream(h, gh, st);
     Group &g = gh.g;
     g.status = status;
-    TRY(launch(h, k_solve_init, g.nprob, 0, st, g, s0));
-    TRY(aff_scan(h, gh, AFF_ROLL_, st));
-    TRY(launch(h, k_post_roll, g.nstage, 0, st, g, 0));
+    TRY(launch(h, k_solve_init, g.nprob, 0, gst, g, s0));
+    TRY(aff_scan(h, gh, AFF_ROLL_, gst));
+    TRY(launch(h, k_post_roll, g.nstage, 0, gst, g, 0));
     for (int r = 0; r < h->opt.refine; r++) {
       const int sres = 3 * g.n + 2 * g.m;
-      TRY(launch(h, k_resid, g.nstage, sres, st, g, sres));
-      TRY(aff_scan(h, gh, AFF_PLIN_, st));
+      TRY(launch(h, k_resid, g.nstage, sres, gst, g, sres));
+      TRY(aff_scan(h, gh, AFF_PLIN_, gst));
       const int sc = g.n + g.m;
-      TRY(launch(h, k_pcorr, g.nstage, sc, st, g, sc));
-      TRY(aff_scan(h, gh, AFF_CROLL_, st));
-      TRY(launch(h, k_post_roll, g.nstage, 0, st, g, 1));
+      TRY(launch(h, k_pcorr, g.nstage, sc, gst, g, sc));
+      TRY(aff_scan(h, gh, AFF_CROLL_, gst));
+      TRY(launch(h, k_post_roll, g.nstage, 0, gst, g, 1));
     }
-    TRY(launch(h, k_recover, g.nstage, 0, st, g, x, u));
+    TRY(launch(h, k_recover, g.nstage, 0, gst, g, x, u));
   }
+  TRY(join_groups(h, st));
   h->solved = true;
   return ECLQR_OK;
 }
@@ -424,23 +466,26 @@ int eclqr_multipliers(eclqr_handle *h, const double *x, const double *u, double 
   if (h->lay.eta > 0 && !eta) return ECLQR_EINVAL;
   if (!h->solved) return ECLQR_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
+  TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
+    const cudaStream_t gst = group_stream(h, gh, st);
     Group &g = gh.g;
     g.status = status;
     const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
     const int sd = smem_dual_stage(n, m), sw = smem_dual_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
     const int sf = smem_dual_leaf(n, m, pm, qm);
-    TRY(launch(h, k_dual_stage, g.nstage, sd, st, g, x, u, sd));
-    TRY(launch(h, k_dual_terminal, g.nprob, sw, st, g, sw));
-    TRY(launch(h, k_dual_up, g.nslot, sw, st, g, sw));
+    TRY(launch(h, k_dual_stage, g.nstage, sd, gst, g, x, u, sd));
+    TRY(launch(h, k_dual_terminal, g.nprob, sw, gst, g, sw));
+    TRY(launch(h, k_dual_up, g.nslot, sw, gst, g, sw));
     int src = 0;
     for (int k = 0; k < gh.levels; k++, src ^= 1)
-      TRY(launch(h, k_rel_level, g.nslot, sl, st, g, src, 1 << k, (int)ST_DUAL_INCONSISTENT, sl));
-    TRY(launch(h, k_dual_down, g.nslot, sw, st, g, src, sw));
-    TRY(launch(h, k_dual_root, g.nprob, sw, st, g, sw));
-    TRY(aff_scan(h, gh, AFF_NU_, st));
-    TRY(launch(h, k_dual_leaf, g.nstage, sf, st, g, lam, mu, eta, alpha, sf));
+      TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_DUAL_INCONSISTENT, sl));
+    TRY(launch(h, k_dual_down, g.nslot, sw, gst, g, src, sw));
+    TRY(launch(h, k_dual_root, g.nprob, sw, gst, g, sw));
+    TRY(aff_scan(h, gh, AFF_NU_, gst));
+    TRY(launch(h, k_dual_leaf, g.nstage, sf, gst, g, lam, mu, eta, alpha, sf));
   }
+  TRY(join_groups(h, st));
   return ECLQR_OK;
 }
 
@@ -450,10 +495,13 @@ int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const
   if (!h->built) return ECLQR_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(resid, 0, sizeof(double) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
+  TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
+    const cudaStream_t gst = group_stream(h, gh, st);
     Group &g = gh.g;
-    TRY(launch(h, k_kkt_residual, g.nstage, 0, st, g, s0, x, u, lam, mu, eta, alpha, resid));
+    TRY(launch(h, k_kkt_residual, g.nstage, 0, gst, g, s0, x, u, lam, mu, eta, alpha, resid));
   }
+  TRY(join_groups(h, st));
   return ECLQR_OK;
 }
 
@@ -471,7 +519,9 @@ int eclqr_param_grads(eclqr_handle *h, const double *x, const double *u, const d
   const Sol w{x, u, lam, mu, eta, alpha}, wb{xb, ub, lamb, mub, etab, alphab};
   const GradOut o{out->A, out->B, out->c, out->C, out->D, out->d, out->E, out->e,
                   out->Q, out->M, out->R, out->qv, out->rv, out->s0};
-  for (auto &gh : h->groups) TRY(launch(h, k_param_grads, gh.g.nstage, 0, st, gh.g, w, wb, o));
+  TRY(fork_groups(h, st));
+  for (auto &gh : h->groups) TRY(launch(h, k_param_grads, gh.g.nstage, 0, group_stream(h, gh, st), gh.g, w, wb, o));
+  TRY(join_groups(h, st));
   return ECLQR_OK;
 }
 
@@ -492,7 +542,12 @@ int64_t eclqr_launch_count(const eclqr_handle *h) { return h ? h->launches : 0; 
 
 void eclqr_destroy(eclqr_handle *h) {
   if (!h) return;
-  for (auto &gh : h->groups) cudaFree(gh.dmem);
+  for (auto &gh : h->groups) {
+    cudaFree(gh.dmem);
+    if (gh.s) cudaStreamDestroy(gh.s);
+    if (gh.done) cudaEventDestroy(gh.done);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
   for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
 }
