@@ -317,7 +317,11 @@ def run_gpu(args):
     eclqr.load()
 
     pb = synth.config(WORKLOAD)
-    batch = eclqr.Batch([pb], device=dev, refine=args.refine, chunk=args.chunk)
+    chunk, trials = args.chunk, None
+    if chunk == 0:
+        # untimed setup: the fastest chunk length whose pass meets the residual gate
+        chunk, trials = eclqr.autotune_chunk([pb], device=dev, refine=args.refine, gate=KKT_GATE)
+    batch = eclqr.Batch([pb], device=dev, refine=args.refine, chunk=chunk)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -444,7 +448,9 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "stages_per_gpu": pb.N, "refine": args.refine,
-                   "chunk": args.chunk or "auto", "l2": "256 MB buffer written between timed steps",
+                   "chunk": chunk, "chunk_autotune": [{"chunk": c, "ms": round(t, 3), "kkt_resid": r, "passed": ok}
+                                                      for c, t, r, ok in (trials or [])],
+                   "l2": "256 MB buffer written between timed steps",
                    "kkt_resid": res["resid"], "status": res["status"], "gate_passed": ok,
                    "step": "eclqr_build + eclqr_solve + eclqr_multipliers + eclqr_kkt_residual"},
         "e2e": {"value": job_rate(world, pb.N, e2e_ms) if e2e_ok else 0.0, "unit": "stages/s",
@@ -479,7 +485,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--refine", type=int, default=2)
-    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0, help="stages per scan chunk; 0 = autotuned (untimed setup)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the plain-solve and batched lines")
     args = ap.parse_args()

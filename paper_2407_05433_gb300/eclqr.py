@@ -339,3 +339,38 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def autotune_chunk(problems, device="cuda", candidates=(0, 6, 12, 16, 32, -1), gate=1e-9, refine=2, passes=3,
+                   **kw):
+    """Chunk length for these problems: the fastest full pass (build, solve, multipliers, residual) among
+    the candidates whose every problem ends with status 0 and a KKT residual <= gate.
+
+    0 is the automatic choice of eclqr_create, -1 one chunk per problem (a single team sweeps every
+    stage).  The chunk boundaries place the scan's composed relations next to the sweeps' own sets,
+    and where they meet the multipliers inherit the difference, so which lengths pass depends on the
+    instance.  Returns (chunk, trials) with trials = [(chunk, ms, max residual, passed)].  When no
+    candidate passes, the one with the smallest residual is returned."""
+    import torch
+    trials = []
+    for L in candidates:
+        chunk = max(pb.N for pb in problems) if L == -1 else L
+        b = Batch(problems, device=device, refine=refine, chunk=chunk, **kw)
+        try:
+            b.run()
+            torch.cuda.synchronize(b.device)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(passes):
+                b.run()
+            e1.record()
+            torch.cuda.synchronize(b.device)
+            ms = e0.elapsed_time(e1) / passes
+            res = float(b.resid.max())
+            ok = bool(int(b.status.abs().max()) == 0 and res <= gate)
+        finally:
+            b.close()
+        trials.append((chunk, ms, res, ok))
+    passing = [t for t in trials if t[3]]
+    best = min(passing, key=lambda t: t[1]) if passing else min(trials, key=lambda t: t[2])
+    return best[0], trials

@@ -202,3 +202,14 @@ def test_graph_replay_is_bit_identical_to_eager():
             assert torch.equal(v, getattr(b, k)), k
     finally:
         b.close()
+
+
+def test_chunk_autotuner_returns_a_passing_length():
+    pbs = [synth.config("degenerate_n12", N=96)]
+    chunk, trials = eclqr.autotune_chunk(pbs, candidates=(0, 4, 16, -1), passes=1)
+    assert len(trials) == 4 and {t[0] for t in trials} == {0, 4, 16, 96}
+    picked = [t for t in trials if t[0] == chunk][0]
+    assert picked[3], trials
+    assert picked[1] == min(t[1] for t in trials if t[3])
+    res, dims = gpu_run(pbs, chunk=chunk)
+    check(pbs[0], res[0], dims[0])
