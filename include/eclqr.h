@@ -173,6 +173,21 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name);
 int eclqr_kernel_time(eclqr_handle *h, int64_t *launches, double *total_ms);
 int eclqr_probe_fp64_peak(double *tflops);
 
+/* Swaps in new linear costs with zero affine offsets on the factors of the
+ * last eclqr_build -- the adjoint problem of eclqr_param_grads without a new
+ * build.  data: the built problem's matrices (A, B, C, D, E, Q, M, R, same
+ * arrays or equal values), new qv and rv, and c, d, e pointing at zeros; the
+ * call does not check these preconditions, and with nonzero c, d or e the
+ * subsequent solve is wrong.  Zeroes t_i, y_i and cbar_i, recomputes
+ * qbar_i = T_i'q_i + Y_i'r_i and rbar_i = Z_i'r_i (eq. reduced-cost-data with
+ * t = y = 0) and the square-root Riccati's stage offsets.  The Riccati's own
+ * offsets keep the build's values, so the following eclqr_solve starts from
+ * a wrong point and relies on its refinement passes (one pass to reach the
+ * new solution, the default second pass for accuracy).  Asynchronous; the
+ * handle then needs eclqr_solve before eclqr_multipliers.  The paper has no
+ * counterpart. */
+int eclqr_set_costs(eclqr_handle *h, const eclqr_data *data, void *stream);
+
 /* Gradient outputs (device memory): one array per input of eclqr_data plus s0
  * (P x n), each with the packed layout of the corresponding input. */
 typedef struct {

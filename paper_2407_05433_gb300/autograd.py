@@ -3,11 +3,11 @@
 Backward is implicit differentiation of the KKT system through the C ABI
 (eclqr_param_grads): the adjoint is the solution of the same problems with
 the same matrices, the incoming gradients as linear costs (q' = -dl/dx,
-r' = -dl/du) and zero c, d, e, s0, computed by the same
-eclqr_build / eclqr_solve / eclqr_multipliers calls; the gradients are then
-outer products of solution and adjoint, one CTA per stage.  Gradients of Q_i
-and R_i are symmetrised.  The forward solution (with its multipliers) is kept
-for the backward pass; the handle's factors are rebuilt for the adjoint data.
+r' = -dl/du) and zero c, d, e, s0.  When the handle still holds the factors
+of this forward pass, the adjoint reuses them (eclqr_set_costs, then
+eclqr_solve and eclqr_multipliers: no new build); otherwise the factors are
+rebuilt on the adjoint data.  The gradients are outer products of solution
+and adjoint, one CTA per stage.  Gradients of Q_i and R_i are symmetrised.
 """
 from __future__ import annotations
 
@@ -24,15 +24,20 @@ def batch_params(batch, requires_grad=True):
     return [batch.d[k].detach().clone().requires_grad_(requires_grad) for k in PARAM_KEYS]
 
 
-def _run(batch, data_tensors, s0):
-    """build + solve + multipliers on the given data; returns the six packed outputs and status."""
+def _run(batch, data_tensors, s0, reuse=False):
+    """build (or, with reuse, eclqr_set_costs on the last build's factors) + solve + multipliers on the
+    given data; returns the six packed outputs and status."""
     L = batch.layout
     f64 = dict(dtype=torch.float64, device=batch.device)
     out = [torch.zeros(max(1, int(getattr(L, k))), **f64) for k in ("x", "u", "lam", "mu", "eta", "alpha")]
     status = torch.zeros(len(batch.problems), dtype=torch.int32, device=batch.device)
     data = eclqr.eclqr_data(*[t.data_ptr() for t in data_tensors])
     st = batch._stream()
-    eclqr._check(eclqr.eclqr_build(batch.h, data, status.data_ptr(), st), "eclqr_build")
+    if reuse:
+        eclqr._check(eclqr.eclqr_set_costs(batch.h, data, st), "eclqr_set_costs")
+    else:
+        eclqr._check(eclqr.eclqr_build(batch.h, data, status.data_ptr(), st), "eclqr_build")
+        batch._factor_token = getattr(batch, "_factor_token", 0) + 1
     eclqr._check(eclqr.eclqr_solve(batch.h, s0.data_ptr(), out[0].data_ptr(), out[1].data_ptr(), status.data_ptr(),
                                    st), "eclqr_solve")
     eclqr._check(eclqr.eclqr_multipliers(batch.h, *[t.data_ptr() for t in out], status.data_ptr(), st),
@@ -43,11 +48,14 @@ def _run(batch, data_tensors, s0):
 class ECLQRSolve(torch.autograd.Function):
     """forward(batch, *params) -> (x, u), params in PARAM_KEYS order (packed float64 on batch.device)."""
 
+    reuse_factors = True  # backward reuses the forward build's factors when the handle still holds them
+
     @staticmethod
     def forward(ctx, batch, *params):
         params = [p.detach().contiguous() for p in params]
         out, status = _run(batch, params[:-1], params[-1])
         ctx.batch = batch
+        ctx.token = batch._factor_token
         ctx.save_for_backward(*params, *out, status)
         L = batch.layout
         x, u = out[0][:int(L.x)], out[1][:int(L.u)]
@@ -76,7 +84,8 @@ class ECLQRSolve(torch.autograd.Function):
         adj["rv"] = -lu[:adj["rv"].numel()]
         s0b = torch.zeros_like(adj["s0"])
         adjd = [adj[k].contiguous() for k in eclqr.DATA_KEYS]
-        wb, st_b = _run(batch, adjd, s0b)
+        reuse = getattr(batch, "_factor_token", None) == ctx.token and ECLQRSolve.reuse_factors
+        wb, st_b = _run(batch, adjd, s0b, reuse=reuse)
         grads = [torch.zeros_like(p) for p in params]
         g = eclqr.eclqr_grads(*[t.data_ptr() for t in grads])
         eclqr._check(eclqr.eclqr_param_grads(batch.h, *[t.data_ptr() for t in sol], *[t.data_ptr() for t in wb], g,

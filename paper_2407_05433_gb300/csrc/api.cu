@@ -505,6 +505,22 @@ int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const
   return ECLQR_OK;
 }
 
+int eclqr_set_costs(eclqr_handle *h, const eclqr_data *data, void *stream) {
+  if (!h || !data) return ECLQR_EINVAL;
+  if (!h->built) return ECLQR_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  TRY(fork_groups(h, st));
+  for (auto &gh : h->groups) {
+    Group &g = gh.g;
+    g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
+    g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
+    TRY(launch(h, k_set_costs, g.nstage, 0, group_stream(h, gh, st), g, 0));
+  }
+  TRY(join_groups(h, st));
+  h->solved = false;
+  return ECLQR_OK;
+}
+
 int eclqr_param_grads(eclqr_handle *h, const double *x, const double *u, const double *lam, const double *mu,
                       const double *eta, const double *alpha, const double *xb, const double *ub,
                       const double *lamb, const double *mub, const double *etab, const double *alphab,
@@ -571,7 +587,7 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
       {"k_recover", (const void *)k_recover}, {"k_dual_stage", (const void *)k_dual_stage},
       {"k_dual_terminal", (const void *)k_dual_terminal}, {"k_dual_up", (const void *)k_dual_up},
       {"k_dual_down", (const void *)k_dual_down}, {"k_dual_root", (const void *)k_dual_root},
-      {"k_dual_leaf", (const void *)k_dual_leaf}, {"k_kkt_residual", (const void *)k_kkt_residual}, {"k_param_grads", (const void *)k_param_grads}};
+      {"k_dual_leaf", (const void *)k_dual_leaf}, {"k_kkt_residual", (const void *)k_kkt_residual}, {"k_param_grads", (const void *)k_param_grads}, {"k_set_costs", (const void *)k_set_costs}};
   for (const auto &e : table)
     if (std::strcmp(e.name, name) == 0) {
       if (h->ev.empty()) {

@@ -49,6 +49,7 @@ __global__ void k_dual_down(Group g, int fin, int per_task);
 __global__ void k_dual_root(Group g, int per_task);
 __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task);
 __global__ void k_param_grads(Group g, Sol w, Sol wb, GradOut o);
+__global__ void k_set_costs(Group g, int per_task);
 __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const double *u, const double *lam,
                                const double *mu, const double *eta, const double *alpha, double *resid);
 

@@ -88,6 +88,8 @@ def load():
     lib.eclqr_kkt_residual_noalloc.argtypes = [ct.POINTER(eclqr_desc), ct.POINTER(eclqr_data)] + [vp] * 9
     lib.eclqr_kkt_residual_noalloc.restype = i32
     lib.eclqr_param_grads.argtypes = [vp] * 13 + [ct.POINTER(eclqr_grads), vp]
+    lib.eclqr_set_costs.argtypes = [vp, ct.POINTER(eclqr_data), vp]
+    lib.eclqr_set_costs.restype = i32
     lib.eclqr_param_grads.restype = i32
     lib.eclqr_destroy.argtypes = [vp]
     lib.eclqr_destroy.restype = None
@@ -145,6 +147,10 @@ def eclqr_kkt_residual_noalloc(desc, data, s0, x, u, lam, mu, eta, alpha, resid,
 def eclqr_param_grads(h, x, u, lam, mu, eta, alpha, xb, ub, lamb, mub, etab, alphab, out, stream):
     return load().eclqr_param_grads(h, x, u, lam, mu, eta, alpha, xb, ub, lamb, mub, etab, alphab,
                                     ct.byref(out), stream)
+
+
+def eclqr_set_costs(h, data, stream):
+    return load().eclqr_set_costs(h, ct.byref(data), stream)
 
 
 def eclqr_reduced_dims(h, nbar, mbar, stream):

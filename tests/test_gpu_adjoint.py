@@ -86,3 +86,23 @@ def test_autograd_matches_finite_differences_of_the_cuda_solve():
                 assert abs(fd - g) <= 1e-5 * max(1.0, abs(g)), (k, int(flat), fd, g)
     finally:
         batch.close()
+
+
+def test_adjoint_on_reused_factors_matches_rebuilt_adjoint():
+    """eclqr_set_costs + solve (no new build) gives the gradients of a full adjoint rebuild."""
+    torch, ag, pbs, batch, xrefs, xref, params = _setup()
+    try:
+        grads = {}
+        for reuse in (True, False):
+            ag.ECLQRSolve.reuse_factors = reuse
+            ps = [p.detach().clone().requires_grad_(True) for p in params]
+            _loss(torch, ag, batch, xref, ps).backward()
+            grads[reuse] = [p.grad.clone() for p in ps]
+        for k, a, b in zip(ag.PARAM_KEYS, grads[True], grads[False]):
+            if b.numel() == 0:
+                continue
+            err = float((a - b).abs().max()) / max(1.0, float(b.abs().max()))
+            assert err <= 1e-9, (k, err)
+    finally:
+        ag.ECLQRSolve.reuse_factors = True
+        batch.close()
