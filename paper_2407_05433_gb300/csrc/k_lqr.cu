@@ -218,6 +218,10 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
+  // every chunk but the last re-sweeps the next chunk's stages from the same scan value, so that the
+  // value function it starts from is, bit for bit, the one the next chunk computes at their boundary
+  const bool resweep = ci.c + 1 < P.nch;
+  const int start = resweep ? min(b + P.L, P.N) : b;
   const int ldr = 2 * n + 1;
   double *sm = team_smem(per_task);
   const int rows_max = 2 * n + m, ldst = n + m + 1;
@@ -226,8 +230,9 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
   // V_b, rows signed to a positive diagonal
   int rv;
   {
-    const double *src = crel_cost(g.CS[fin] + (size_t)(t + 1) * g.cs_stride, n);
-    const int *I = g.CI[fin] + (size_t)(t + 1) * CI_STRIDE;
+    const int slot = resweep ? t + 2 : t + 1;
+    const double *src = crel_cost(g.CS[fin] + (size_t)slot * g.cs_stride, n);
+    const int *I = g.CI[fin] + (size_t)slot * CI_STRIDE;
     const int nbz = I[CI_NA];
     rv = I[CI_ROWS2];
     for (int idx = tid; idx < rv * (nbz + 1); idx += TEAM) {
@@ -246,7 +251,8 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       }
     }
   }
-  for (int i = b - 1; i >= a; --i) {
+  for (int i = start - 1; i >= a; --i) {
+    const bool store = i < b;  // the next chunk's stages are stored by that chunk
     const int s = P.st0 + i;
     double *ws = stage_ws(g, s);
     int *wi = stage_wi(g, s);
@@ -292,20 +298,22 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       }
     }
     tsync();
-    for (int idx = tid; idx < mu * (nx + 1); idx += TEAM) {
-      int r = idx / (nx + 1), c = idx - r * (nx + 1);
-      if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
-    }
-    for (int idx = tid; idx < mu * mu; idx += TEAM) {
-      int r = idx / mu, j = idx - r * mu;
-      double sg = St[j * ld + j] >= 0.0 ? 1.0 : -1.0;
-      ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * St[j * ld + r] : 0.0;
-    }
-    for (int idx = tid; idx < n1 * nx; idx += TEAM) {
-      int r = idx / nx, c = idx - r * nx;
-      double s0 = Ab[r * n + c];
-      for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
-      ws[g.ws.Phi + r * n + c] = s0;
+    if (store) {
+      for (int idx = tid; idx < mu * (nx + 1); idx += TEAM) {
+        int r = idx / (nx + 1), c = idx - r * (nx + 1);
+        if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
+      }
+      for (int idx = tid; idx < mu * mu; idx += TEAM) {
+        int r = idx / mu, j = idx - r * mu;
+        double sg = St[j * ld + j] >= 0.0 ? 1.0 : -1.0;
+        ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * St[j * ld + r] : 0.0;
+      }
+      for (int idx = tid; idx < n1 * nx; idx += TEAM) {
+        int r = idx / nx, c = idx - r * nx;
+        double s0 = Ab[r * n + c];
+        for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
+        ws[g.ws.Phi + r * n + c] = s0;
+      }
     }
     // new value rows [R_i | s_i]
     tsync();
@@ -319,6 +327,7 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       int r = idx / (nx + 1), c = idx - r * (nx + 1);
       double s0 = 0.0;
       for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
+      if (!store) continue;
       if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
     }
     tsync();

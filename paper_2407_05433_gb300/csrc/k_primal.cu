@@ -192,6 +192,52 @@ __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task
 }
 
 // ----------------------------------------------------------- chunk down-sweep: every X_i
+// One stage of the down-sweep: from X_{i+1} = {H x + h = 0} (rows rr of Hs),
+// project u_i out of [H B | H A | H c + h] stacked with the stage's own rows;
+// Hs receives X_i.  Returns its row count.
+__device__ int primal_down_stage(const Group &g, const ProbInfo &P, int i, double *Hs, int rr, double *M,
+                                 double *scr, int *inconsistent) {
+  const int n = g.n, m = g.m, tid = team_rank();
+  const int ldh = n + 1, ldm = m + n + 1;
+  const StageInfo S = g.st[P.st0 + i];
+  const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
+  const double *c = g.c + P.oc + (size_t)i * n;
+  wgemm<false, false>(rr, m, n, 1.0, Hs, ldh, B, m, 0.0, M, ldm);
+  wgemm<false, false>(rr, n, n, 1.0, Hs, ldh, A, n, 0.0, M + m, ldm);
+  for (int r = tid; r < rr; r += TEAM) {
+    double s0 = Hs[r * ldh + n];
+    for (int l = 0; l < n; l++) s0 = fma(Hs[r * ldh + l], c[l], s0);
+    M[r * ldm + m + n] = s0;
+  }
+  for (int idx = tid; idx < (S.p + S.q) * ldm; idx += TEAM) {
+    int r = idx / ldm, j = idx - r * ldm;
+    double val = 0.0;
+    if (r < S.p) {
+      const size_t row = S.prow + r;
+      if (j < m) val = g.D[P.oD + row * m + j];
+      else if (j < m + n) val = g.C[P.oC + row * n + (j - m)];
+      else val = g.d[P.od + row];
+    } else {
+      const size_t row = S.qrow + (r - S.p);
+      if (j >= m && j < m + n) val = g.E[P.oE + row * n + (j - m)];
+      else if (j == m + n) val = g.e[P.oe + row];
+    }
+    M[(rr + r) * ldm + j] = val;
+  }
+  tsync();
+  const int gs[1] = {m};
+  const ProjResult pr = wproject(M, ldm, rr + S.p + S.q, 1, gs, n, g.tau_rank, g.tau_inc, Hs, ldh, scr);
+  *inconsistent = pr.inconsistent;
+  return pr.krank;
+}
+
+// Every chunk but the last first re-sweeps the next chunk's stages from the
+// same scan value that chunk starts from.  The set it reaches at its own end
+// is then the one the next chunk computes and stores for that stage, bit for
+// bit, instead of the scan's composition of the same set: the two agree only
+// up to rounding, and a stage whose domain was derived from one set while the
+// next stage's basis comes from the other leaves U_b'(A T + B Y) at that
+// rounding level, which the multipliers of Sec. 7 multiply by |nu_b|.
 __global__ void k_primal_down(Group g, int fin, int per_task) {
   const int t = team_task();
   if (t >= g.nslot) return;
@@ -200,54 +246,31 @@ __global__ void k_primal_down(Group g, int fin, int per_task) {
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
+  const bool resweep = ci.c + 1 < P.nch;
+  const int start = resweep ? min(b + P.L, P.N) : b;
   double *sm = team_smem(per_task);
   const int ldh = n + 1, ldr = 2 * n + 1, ldm = m + n + 1;
   const int rows_max = n + g.pmax + g.qmax;
   double *Hs = sm, *M = Hs + n * ldh, *scr = M + rows_max * ldm;
-  // X_b from the scan (unary relation held by slot t + 1)
-  const double *xb = g.CS[fin] + (size_t)(t + 1) * g.cs_stride;
-  int rr = g.CI[fin][(size_t)(t + 1) * CI_STRIDE + CI_ROWS];
+  // X at `start` from the scan (unary relation held by the slot after the chunk that ends there)
+  const int src = resweep ? t + 2 : t + 1;
+  const double *xb = g.CS[fin] + (size_t)src * g.cs_stride;
+  int rr = g.CI[fin][(size_t)src * CI_STRIDE + CI_ROWS];
   for (int idx = tid; idx < rr * ldh; idx += TEAM) {
     int i = idx / ldh, j = idx - i * ldh;
     Hs[idx] = xb[i * ldr + j];
   }
   tsync();
-  for (int i = b - 1; i >= a; --i) {
+  for (int i = start - 1; i >= a; --i) {
+    int inc = 0;
+    rr = primal_down_stage(g, P, i, Hs, rr, M, scr, &inc);
+    if (i >= b) continue;  // the next chunk's stage: stored by that chunk
     const int s = P.st0 + i;
-    const StageInfo S = g.st[s];
-    const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
-    const double *c = g.c + P.oc + (size_t)i * n;
-    wgemm<false, false>(rr, m, n, 1.0, Hs, ldh, B, m, 0.0, M, ldm);
-    wgemm<false, false>(rr, n, n, 1.0, Hs, ldh, A, n, 0.0, M + m, ldm);
-    for (int r = tid; r < rr; r += TEAM) {
-      double s0 = Hs[r * ldh + n];
-      for (int l = 0; l < n; l++) s0 = fma(Hs[r * ldh + l], c[l], s0);
-      M[r * ldm + m + n] = s0;
-    }
-    for (int idx = tid; idx < (S.p + S.q) * ldm; idx += TEAM) {
-      int r = idx / ldm, j = idx - r * ldm;
-      double val = 0.0;
-      if (r < S.p) {
-        const size_t row = S.prow + r;
-        if (j < m) val = g.D[P.oD + row * m + j];
-        else if (j < m + n) val = g.C[P.oC + row * n + (j - m)];
-        else val = g.d[P.od + row];
-      } else {
-        const size_t row = S.qrow + (r - S.p);
-        if (j >= m && j < m + n) val = g.E[P.oE + row * n + (j - m)];
-        else if (j == m + n) val = g.e[P.oe + row];
-      }
-      M[(rr + r) * ldm + j] = val;
-    }
-    tsync();
-    const int gs[1] = {m};
-    ProjResult pr = wproject(M, ldm, rr + S.p + S.q, 1, gs, n, g.tau_rank, g.tau_inc, Hs, ldh, scr);
-    rr = pr.krank;
     double *H = stage_ws(g, s) + g.ws.H;
     for (int idx = tid; idx < rr * ldh; idx += TEAM) H[idx] = Hs[idx];
     if (tid == 0) {
       stage_wi(g, s)[SI_HROWS] = rr;
-      if (pr.inconsistent) set_status(g, ci.prob, ST_INFEASIBLE_SUFFIX);
+      if (inc) set_status(g, ci.prob, ST_INFEASIBLE_SUFFIX);
     }
     tsync();
   }

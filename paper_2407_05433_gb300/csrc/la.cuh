@@ -215,42 +215,49 @@ __device__ __forceinline__ double *hh_rowk() {
 // reflector (v = M_piv + sign(x_k) ||M_piv|| e_k) is applied to those columns,
 // column piv becomes (-sign(x_k) ||M_piv||, 0, ..., 0), done[piv] is set when
 // done is given, and the norm is returned.  Scratch: v (rows), d (columns).
+// Each column's row segments sit on neighbouring lanes of one warp, so their
+// partial products combine by shuffles.  With cn given (column pivoting), the
+// lane holding row k of a candidate column in [cand0, cand1) also downdates
+// its remaining squared norm, or marks it (-1) for exact re-evaluation when
+// cancellation has consumed half its digits (LAPACK xLAQP2, sqrt(eps) = 2^-26).
 static __device__ double hh_step(double *M, int ld, int k, int r, int piv, int a0, int a1, int *done, double *v,
-                                 double *d, double thr) {
+                                 double *d, double thr, double *cn = nullptr, const double *cref = nullptr,
+                                 int cand0 = 0, int cand1 = 0) {
   const int tid = team_rank(), T = TEAM;
-  double *part = hh_part(), *mk = hh_rowk();
+  double *mk = hh_rowk();
   const int nc = a1 - a0, nr = r - k;
-  // thread -> (column a0 + jj, row segment sgm): rows k + sgm, k + sgm + S, ...
-  const int S = max(1, min(nc > 0 ? T / nc : 1, nr));
-  const int jj0 = (S > 1) ? tid % nc : tid, sgm = (S > 1) ? tid / nc : 0;
-  const bool seg_ok = sgm < S;
-  const int jstep = (S > 1) ? nc : T;
+  // S row segments per column, a power of two within a warp; thread -> (column a0 + jj, segment sgm)
+  int S = 1;
+  while (2 * S <= 32 && 2 * S * nc <= T && 2 * S <= nr) S *= 2;
+  const int jj0 = (S > 1) ? tid / S : tid, sgm = (S > 1) ? (tid & (S - 1)) : 0;
+  const int jstep = (S > 1) ? T : T;   // S > 1: one column per thread group (S * nc <= T)
   for (int i = k + tid; i < r; i += T) v[i] = M[i * ld + piv];
   for (int jj = tid; jj < nc; jj += T) mk[jj] = M[k * ld + a0 + jj];
-  for (int jj = jj0; seg_ok && jj < nc; jj += jstep) {
-    const int j = a0 + jj;
+  if (S > 1) {
     double acc = 0.0;
-    if (j == piv || !(done && done[j]))
+    const int j = a0 + jj0;
+    if (jj0 < nc && (j == piv || !(done && done[j])))
       for (int i = k + sgm; i < r; i += S) acc = fma(M[i * ld + piv], M[i * ld + j], acc);
-    if (S == 1) d[j] = acc;
-    else part[sgm * nc + jj] = acc;
+    for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o, S);
+    if (jj0 < nc && sgm == 0) d[j] = acc;
+  } else {
+    for (int jj = jj0; jj < nc; jj += jstep) {
+      const int j = a0 + jj;
+      double acc = 0.0;
+      if (j == piv || !(done && done[j]))
+        for (int i = k; i < r; i++) acc = fma(M[i * ld + piv], M[i * ld + j], acc);
+      d[j] = acc;
+    }
   }
   tsync();
-  if (S > 1) {
-    for (int j2 = tid; j2 < nc; j2 += T) {
-      double acc = part[j2];
-      for (int k2 = 1; k2 < S; k2++) acc += part[k2 * nc + j2];
-      d[a0 + j2] = acc;
-    }
-    tsync();
-  }
   const double nrm = sqrt(d[piv]);
   if (!(nrm > thr)) return 0.0;
   const double xk = v[k];
   const double sg = xk >= 0.0 ? 1.0 : -1.0;
   const double shift = sg * nrm;                 // v_k - x_k
   const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
-  for (int jj = jj0; seg_ok && jj < nc; jj += jstep) {
+  for (int jj = jj0; jj < nc; jj += (S > 1 ? T : jstep)) {
+    if (S > 1 && jj != jj0) break;
     const int j = a0 + jj;
     if (j == piv) {
       for (int i = k + sgm; i < r; i += S) M[i * ld + piv] = (i == k) ? -shift : 0.0;
@@ -262,6 +269,11 @@ static __device__ double hh_step(double *M, int ld, int k, int r, int piv, int a
     for (int i = k + sgm; i < r; i += S) {
       const double vi = (i == k) ? xk + shift : v[i];
       M[i * ld + j] = fma(-wj, vi, M[i * ld + j]);
+    }
+    if (cn && sgm == 0 && j >= cand0 && j < cand1) {
+      const double a = M[k * ld + j];
+      const double nw = cn[j] - a * a;
+      cn[j] = (nw <= 0x1p-26 * cref[j]) ? -1.0 : nw;
     }
   }
   tsync();
@@ -318,21 +330,17 @@ static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int
   tsync();
   int steps = 0;
   while (k < r) {
-    // downdate by the row the previous step finished, then pick the largest
+    // columns the last step marked are evaluated afresh over the remaining rows
     double mybest = -1.0;
     int mypiv = 0x7fffffff;
     for (int j = cand0 + tid; j < cand1; j += T) {
       if (done[j]) continue;
       double nw = cn[j];
-      if (steps > 0) {
-        const double a = M[(k - 1) * ld + j];
-        nw -= a * a;
-        if (nw <= 0x1p-26 * cref[j]) {
-          nw = 0.0;
-          for (int i = k; i < r; i++) nw = fma(M[i * ld + j], M[i * ld + j], nw);
-          cref[j] = nw;
-        }
+      if (nw < 0.0) {
+        nw = 0.0;
+        for (int i = k; i < r; i++) nw = fma(M[i * ld + j], M[i * ld + j], nw);
         cn[j] = nw;
+        cref[j] = nw;
       }
       if (nw > mybest) { mybest = nw; mypiv = j; }
     }
@@ -340,7 +348,7 @@ static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int
     int piv;
     team_argmax1(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, steps & 1, b2, piv);
     if (piv == 0x7fffffff) break;
-    const double nrm = hh_step(M, ld, k, r, piv, app0, app1, done, v, w, thr);
+    const double nrm = hh_step(M, ld, k, r, piv, app0, app1, done, v, w, thr, cn, cref, cand0, cand1);
     if (nrm == 0.0) break;
     if (tid == 0 && pc) pc[steps] = piv;
     k++;
