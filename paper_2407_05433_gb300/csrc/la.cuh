@@ -216,13 +216,9 @@ __device__ __forceinline__ double *hh_rowk() {
 // column piv becomes (-sign(x_k) ||M_piv||, 0, ..., 0), done[piv] is set when
 // done is given, and the norm is returned.  Scratch: v (rows), d (columns).
 // Each column's row segments sit on neighbouring lanes of one warp, so their
-// partial products combine by shuffles.  With cn given (column pivoting), the
-// lane holding row k of a candidate column in [cand0, cand1) also downdates
-// its remaining squared norm, or marks it (-1) for exact re-evaluation when
-// cancellation has consumed half its digits (LAPACK xLAQP2, sqrt(eps) = 2^-26).
+// partial products combine by shuffles.
 static __device__ double hh_step(double *M, int ld, int k, int r, int piv, int a0, int a1, int *done, double *v,
-                                 double *d, double thr, double *cn = nullptr, const double *cref = nullptr,
-                                 int cand0 = 0, int cand1 = 0) {
+                                 double *d, double thr) {
   const int tid = team_rank(), T = TEAM;
   double *mk = hh_rowk();
   const int nc = a1 - a0, nr = r - k;
@@ -270,42 +266,129 @@ static __device__ double hh_step(double *M, int ld, int k, int r, int piv, int a
       const double vi = (i == k) ? xk + shift : v[i];
       M[i * ld + j] = fma(-wj, vi, M[i * ld + j]);
     }
-    if (cn && sgm == 0 && j >= cand0 && j < cand1) {
-      const double a = M[k * ld + j];
-      const double nw = cn[j] - a * a;
-      cn[j] = (nw <= 0x1p-26 * cref[j]) ? -1.0 : nw;
-    }
   }
   tsync();
   return nrm;
 }
 
 // Team arg-max with one barrier: partials alternate between two buffers by
-// parity, so consecutive calls must be separated by at least one other
-// barrier (hh_step provides it).  Warp stage on the integer pipe: the key of a
-// non-negative double orders like (high word, low word).
-__device__ __forceinline__ void team_argmax1(double val, int idx, int parity, double &bv, int &bi) {
+// parity, so consecutive uses of one buffer must be separated by at least one
+// other barrier.  Ties go to the smaller index.
+__device__ __forceinline__ unsigned long long *argmax_keys() {
   __shared__ unsigned long long rk[2][32];
+  return &rk[0][0];
+}
+__device__ __forceinline__ int *argmax_idx() {
   __shared__ int ri[2][32];
+  return &ri[0][0];
+}
+
+// Warp stage of the arg-max: lane 0 leaves (key, index) of the warp's best in
+// the parity buffer.  The key of a non-negative double orders like (high
+// word, low word), so the reduction runs on the integer pipe.
+__device__ __forceinline__ void warp_argmax_partial(double val, int idx, int parity) {
   const unsigned long long key = (unsigned long long)__double_as_longlong(val);
   const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
   const unsigned mhi = __reduce_max_sync(kFull, hi);
   const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
   const int widx = __reduce_min_sync(kFull, (hi == mhi && lo == mlo) ? idx : 0x7fffffff);
   if ((threadIdx.x & 31) == 0) {
-    rk[parity][threadIdx.x >> 5] = ((unsigned long long)mhi << 32) | mlo;
-    ri[parity][threadIdx.x >> 5] = widx;
+    argmax_keys()[parity * 32 + (threadIdx.x >> 5)] = ((unsigned long long)mhi << 32) | mlo;
+    argmax_idx()[parity * 32 + (threadIdx.x >> 5)] = widx;
   }
-  __syncthreads();
-  unsigned long long best = rk[parity][0];
-  int besti = ri[parity][0];
+}
+
+// Team stage: every thread reduces the warps' partials (after a barrier).
+__device__ __forceinline__ void argmax_finish(int parity, double &bv, int &bi) {
+  unsigned long long best = argmax_keys()[parity * 32];
+  int besti = argmax_idx()[parity * 32];
   for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
-    const unsigned long long k2 = rk[parity][w];
-    const int i2 = ri[parity][w];
+    const unsigned long long k2 = argmax_keys()[parity * 32 + w];
+    const int i2 = argmax_idx()[parity * 32 + w];
     if (k2 > best || (k2 == best && i2 < besti)) { best = k2; besti = i2; }
   }
   bv = __longlong_as_double((long long)best);
   bi = besti;
+}
+
+__device__ __forceinline__ void team_argmax1(double val, int idx, int parity, double &bv, int &bi) {
+  warp_argmax_partial(val, idx, parity);
+  __syncthreads();
+  argmax_finish(parity, bv, bi);
+}
+
+// The pivoted form of hh_step: the update pass also downdates the remaining
+// norms of the candidate columns (re-evaluating a marked one from its rows,
+// which sit on the same warp) and leaves each warp's best candidate in the
+// arg-max buffer `parity`, so that the next pivot is known after the pass's
+// own barrier.  Returns the norm, or 0 (M untouched) when it does not exceed thr.
+static __device__ double hh_pivot_step(double *M, int ld, int k, int r, int piv, int a0, int a1, int *done,
+                                       double *v, double *d, double thr, double *cn, double *cref, int cand0,
+                                       int cand1, int parity) {
+  const int tid = team_rank(), T = TEAM;
+  double *mk = hh_rowk();
+  const int nc = a1 - a0, nr = r - k;
+  int S = 1;
+  while (2 * S <= 32 && 2 * S * nc <= T && 2 * S <= nr) S *= 2;
+  const int jj0 = (S > 1) ? tid / S : tid, sgm = (S > 1) ? (tid & (S - 1)) : 0;
+  for (int i = k + tid; i < r; i += T) v[i] = M[i * ld + piv];
+  for (int jj = tid; jj < nc; jj += T) mk[jj] = M[k * ld + a0 + jj];
+  if (S > 1) {
+    double acc = 0.0;
+    const int j = a0 + jj0;
+    if (jj0 < nc && (j == piv || !done[j]))
+      for (int i = k + sgm; i < r; i += S) acc = fma(M[i * ld + piv], M[i * ld + j], acc);
+    for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o, S);
+    if (jj0 < nc && sgm == 0) d[j] = acc;
+  } else {
+    for (int jj = jj0; jj < nc; jj += T) {
+      const int j = a0 + jj;
+      double acc = 0.0;
+      if (j == piv || !done[j])
+        for (int i = k; i < r; i++) acc = fma(M[i * ld + piv], M[i * ld + j], acc);
+      d[j] = acc;
+    }
+  }
+  tsync();
+  const double nrm = sqrt(d[piv]);
+  if (!(nrm > thr)) return 0.0;
+  const double xk = v[k];
+  const double sg = xk >= 0.0 ? 1.0 : -1.0;
+  const double shift = sg * nrm;
+  const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
+  for (int jj = jj0; jj < nc && (S == 1 || jj == jj0); jj += T) {
+    const int j = a0 + jj;
+    if (j == piv) {
+      for (int i = k + sgm; i < r; i += S) M[i * ld + piv] = (i == k) ? -shift : 0.0;
+      if (sgm == 0) done[piv] = 1;
+      continue;
+    }
+    if (done[j]) continue;
+    const double wj = beta * fma(shift, mk[jj], d[j]);
+    for (int i = k + sgm; i < r; i += S) {
+      const double vi = (i == k) ? xk + shift : v[i];
+      M[i * ld + j] = fma(-wj, vi, M[i * ld + j]);
+    }
+  }
+  __syncwarp();  // a column's row segments are lanes of one warp
+  double best = -1.0;
+  int bidx = 0x7fffffff;
+  for (int jj = jj0; jj < nc && (S == 1 || jj == jj0); jj += T) {
+    const int j = a0 + jj;
+    if (sgm != 0 || j == piv || j < cand0 || j >= cand1 || done[j]) continue;
+    const double a = M[k * ld + j];
+    double nw = cn[j] - a * a;
+    if (nw <= 0x1p-26 * cref[j]) {
+      nw = 0.0;
+      for (int i = k + 1; i < r; i++) nw = fma(M[i * ld + j], M[i * ld + j], nw);
+      cref[j] = nw;
+    }
+    cn[j] = nw;
+    if (nw > best) { best = nw; bidx = j; }
+  }
+  warp_argmax_partial(best < 0.0 ? 0.0 : best, best < 0.0 ? 0x7fffffff : bidx, parity);
+  tsync();
+  return nrm;
 }
 
 // Column-pivoted Householder steps on rows [k, r).  Each step takes the
@@ -320,39 +403,29 @@ static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int
                                  int *done, int *pc, double thr, double *v, double *w) {
   const int tid = team_rank(), T = TEAM;
   double *cn = hh_norms(), *cref = cn + kMaxCols;
+  double mybest = -1.0;
+  int mypiv = 0x7fffffff;
   for (int j = cand0 + tid; j < cand1; j += T) {
     double acc = 0.0;
     if (!done[j])
       for (int i = k; i < r; i++) acc = fma(M[i * ld + j], M[i * ld + j], acc);
     cn[j] = acc;
     cref[j] = acc;
+    if (!done[j] && acc > mybest) { mybest = acc; mypiv = j; }
   }
-  tsync();
+  double b2;
+  int piv;
+  team_argmax1(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, 0, b2, piv);
   int steps = 0;
-  while (k < r) {
-    // columns the last step marked are evaluated afresh over the remaining rows
-    double mybest = -1.0;
-    int mypiv = 0x7fffffff;
-    for (int j = cand0 + tid; j < cand1; j += T) {
-      if (done[j]) continue;
-      double nw = cn[j];
-      if (nw < 0.0) {
-        nw = 0.0;
-        for (int i = k; i < r; i++) nw = fma(M[i * ld + j], M[i * ld + j], nw);
-        cn[j] = nw;
-        cref[j] = nw;
-      }
-      if (nw > mybest) { mybest = nw; mypiv = j; }
-    }
-    double b2;
-    int piv;
-    team_argmax1(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, steps & 1, b2, piv);
-    if (piv == 0x7fffffff) break;
-    const double nrm = hh_step(M, ld, k, r, piv, app0, app1, done, v, w, thr, cn, cref, cand0, cand1);
+  while (k < r && piv != 0x7fffffff) {
+    const double nrm = hh_pivot_step(M, ld, k, r, piv, app0, app1, done, v, w, thr, cn, cref, cand0, cand1,
+                                     (steps + 1) & 1);
     if (nrm == 0.0) break;
     if (tid == 0 && pc) pc[steps] = piv;
     k++;
     steps++;
+    if (k >= r) break;
+    argmax_finish(steps & 1, b2, piv);
   }
   tsync();
   return steps;
