@@ -67,8 +67,8 @@ int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cu
   const size_t smem = (size_t)per_task * sizeof(double);
   if (smem > (size_t)kMaxSmemBytes) return ECLQR_EINVAL;
   // without the opt-in, dynamic plus static shared memory is capped at 48 KB;
-  // the kernels' static scratch stays below 8 KB
-  if (smem > 40 * 1024) {
+  // the kernels' static scratch stays below 16 KB
+  if (smem > 32 * 1024) {
     if (cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return ECLQR_ECUDA;

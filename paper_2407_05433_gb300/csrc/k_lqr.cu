@@ -280,7 +280,7 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
       St[idx] = val;
     }
     tsync();
-    for (int col = 0; col < kh && col < rows; col++) hh_step(St, ld, col, rows, col, col, ld, nullptr, v, w, 0.0);
+    hh_diag_steps(St, ld, 0, rows, 0, kh, ld, v, w, 0.0, true);
     // sign the z rows to a positive diagonal (rows mu .. kh - 1)
     for (int idx = tid; idx < nx * ld; idx += TEAM) {
       int r = mu + idx / ld, j = idx % ld;

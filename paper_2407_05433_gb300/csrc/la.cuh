@@ -139,12 +139,14 @@ static __device__ void wgemm(int m, int n, int k, double alpha, const double *A,
 //
 // Per-CTA static scratch: one partial dot product per thread, and for column
 // pivoting the running squared norms of the candidate columns with their
-// values at the last exact evaluation.  Sized for teams of up to kMaxTeam
-// threads and matrices of up to kMaxCols columns (the header's dimension
-// limits keep every factored matrix below 3 * 32 + 64 + 1 columns).
+// values at the last exact evaluation and two lists of active columns.  Sized
+// for teams of up to kMaxTeam threads and matrices of up to kMaxCols columns
+// (the header's dimension limits keep every factored matrix at or below
+// 3 * 32 + 64 + 1 = 161 columns).  The static total stays below 10 KB, which
+// the largest dynamic request (219 KB) leaves room for.
 // ---------------------------------------------------------------------------
 constexpr int kMaxTeam = 256;
-constexpr int kMaxCols = 192;
+constexpr int kMaxCols = 168;
 __device__ __forceinline__ double *hh_part() {
   __shared__ double part[kMaxTeam];
   return part;
@@ -207,73 +209,124 @@ __device__ __forceinline__ double *hh_rowk() {
   __shared__ double rowk[kMaxCols];
   return rowk;
 }
+// Active-column lists of the pivoted factorization (two, alternating by step).
+__device__ __forceinline__ short *hh_lists() {
+  __shared__ short lists[2 * kMaxCols];
+  return lists;
+}
 
-// One fused Householder step on rows [k, r) with pivot column piv in [a0, a1):
-// one pass over the rows gives the raw products d_j = M_piv . M_j for the
-// not-done columns of [a0, a1) together with d_piv = ||M_piv||^2.  If
-// sqrt(d_piv) <= thr, M is left untouched and 0 is returned; otherwise the
-// reflector (v = M_piv + sign(x_k) ||M_piv|| e_k) is applied to those columns,
-// column piv becomes (-sign(x_k) ||M_piv||, 0, ..., 0), done[piv] is set when
-// done is given, and the norm is returned.  Scratch: v (rows), d (columns).
-// Each column's row segments sit on neighbouring lanes of one warp, so their
-// partial products combine by shuffles.
-static __device__ double hh_step(double *M, int ld, int k, int r, int piv, int a0, int a1, int *done, double *v,
-                                 double *d, double thr) {
-  const int tid = team_rank(), T = TEAM;
-  double *mk = hh_rowk();
-  const int nc = a1 - a0, nr = r - k;
-  // S row segments per column, a power of two within a warp; thread -> (column a0 + jj, segment sgm)
-  int S = 1;
-  while (2 * S <= 32 && 2 * S * nc <= T && 2 * S <= nr) S *= 2;
-  const int jj0 = (S > 1) ? tid / S : tid, sgm = (S > 1) ? (tid & (S - 1)) : 0;
-  const int jstep = (S > 1) ? T : T;   // S > 1: one column per thread group (S * nc <= T)
-  for (int i = k + tid; i < r; i += T) v[i] = M[i * ld + piv];
-  for (int jj = tid; jj < nc; jj += T) mk[jj] = M[k * ld + a0 + jj];
-  if (S > 1) {
-    double acc = 0.0;
-    const int j = a0 + jj0;
-    if (jj0 < nc && (j == piv || !(done && done[j])))
-      for (int i = k + sgm; i < r; i += S) acc = fma(M[i * ld + piv], M[i * ld + j], acc);
-    for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o, S);
-    if (jj0 < nc && sgm == 0) d[j] = acc;
-  } else {
-    for (int jj = jj0; jj < nc; jj += jstep) {
-      const int j = a0 + jj;
-      double acc = 0.0;
-      if (j == piv || !(done && done[j]))
-        for (int i = k; i < r; i++) acc = fma(M[i * ld + piv], M[i * ld + j], acc);
-      d[j] = acc;
-    }
+// ---------------------------------------------------------------------------
+// Work layout of a Householder pass.  The pass touches cnt columns (list
+// positions 0 .. cnt-1) over nr rows.  Positions are dealt to the warps in
+// equal contiguous blocks of cw, and each warp splits its columns into S row
+// segments held by neighbouring lanes (rows k + sg, k + sg + S, ...), so the
+// lanes of one column are always lanes of one warp.  An FP64 instruction costs
+// its warp the same whatever its active mask, so the widest split that fits
+// the warp, S = min(floor(32 / cw), nr), gives the fewest FP64 instructions
+// per warp; S need not be a power of two.  With more than 16 columns per warp,
+// S = 1 and each lane walks whole columns.  The integer work is kept free of
+// hardware divisions, each of which costs about 80 cycles of latency.
+// ---------------------------------------------------------------------------
+struct HHLayout {
+  int cw;  // list positions per warp
+  int S;   // row segments per column
+  int lc;  // this lane's column within its warp's block
+  int sg;  // this lane's segment
+};
+// single-precision approximations (PTX rsqrt.approx / rcp.approx, relative
+// error about 2^-22), used only as seeds and for small integer quotients
+__device__ __forceinline__ float rsqrt_seed(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_seed(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// Branch-free, so that the compiler can schedule it inside the latency of
+// the FP64 chains around it.  Teams have 1, 2, 4 or 8 warps.
+__device__ __forceinline__ HHLayout hh_layout(int cnt, int nr) {
+  HHLayout L;
+  const int nw = (int)(blockDim.x >> 5), lane = (int)(threadIdx.x & 31);
+  const int cw = (cnt + nw - 1) >> (__ffs(nw) - 1);
+  // floor(32 / cw) for cw in [1, 16] (nibbles for cw >= 3), 1 beyond
+  const int tab = (int)((0x2222223344568aull >> (4 * min(max(cw - 3, 0), 13))) & 0xf);
+  const int s32 = cw <= 2 ? (32 >> min(max(cw - 1, 0), 1)) : (cw > 16 ? 1 : tab);
+  L.cw = cw;
+  L.S = min(s32, nr);
+  // lane / S: (lane + 1/2) / S stays at least 1/64 away from an integer, far
+  // beyond the error of the single-precision product
+  L.lc = (int)(((float)lane + 0.5f) * rcp_seed((float)L.S));
+  L.sg = lane - L.lc * L.S;
+  return L;
+}
+
+// Sum over the S consecutive lanes of a segment group (S >= 2); the group's
+// first lane (sg == 0) receives the total.  Called by the whole warp.
+__device__ __forceinline__ double seg_sum(double acc, int sg, int S) {
+  int o = 1;
+  while (2 * o < S) o *= 2;
+  for (; o > 0; o >>= 1) {
+    const double t = __shfl_down_sync(kFull, acc, o);
+    if (sg + o < S) acc += t;
   }
-  tsync();
-  const double nrm = sqrt(d[piv]);
-  if (!(nrm > thr)) return 0.0;
-  const double xk = v[k];
-  const double sg = xk >= 0.0 ? 1.0 : -1.0;
-  const double shift = sg * nrm;                 // v_k - x_k
-  const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
-  for (int jj = jj0; jj < nc; jj += (S > 1 ? T : jstep)) {
-    if (S > 1 && jj != jj0) break;
-    const int j = a0 + jj;
-    if (j == piv) {
-      for (int i = k + sgm; i < r; i += S) M[i * ld + piv] = (i == k) ? -shift : 0.0;
-      if (sgm == 0 && done) done[piv] = 1;
-      continue;
-    }
-    if (done && done[j]) continue;
-    const double wj = beta * fma(shift, mk[jj], d[j]);
-    for (int i = k + sgm; i < r; i += S) {
-      const double vi = (i == k) ? xk + shift : v[i];
-      M[i * ld + j] = fma(-wj, vi, M[i * ld + j]);
-    }
-  }
-  tsync();
-  return nrm;
+  return acc;
+}
+
+// Reflector of a column x with squared norm d = ||x||^2 and pivot entry x_k:
+// nrm = sqrt(d), shift = sign(x_k) nrm (sign(0) = +1, also for -0),
+// v_k = x_k + shift and beta = 2 / ||v||^2 with ||v||^2 = (d - x_k^2) + v_k^2
+// evaluated from the v actually formed, so H = I - beta v v' is orthogonal to
+// rounding whatever the last bits of nrm.  The FP64 square root and divide
+// are long dependent chains (about 690 and 440 cycles), so both come from
+// single-precision seeds (exponents handled on the integer pipe) refined by
+// one third-order step: for d^(-1/2) the Householder iteration
+// y = y0 (1 + e/2 + 3 e^2 / 8), e = 1 - d y0^2, and for 1/q the Newton-type
+// step r = r0 (1 + e + e^2), e = 1 - q r0.  From a 2^-21 seed each leaves a
+// truncation error below 2^-60 (5 e^3 / 16 and e^3).  The code is branch-
+// free; it returns false, with the outputs unset, when d is zero, subnormal,
+// above 2^1000 or not finite, where the seeds do not apply.
+__device__ __forceinline__ bool hh_reflector(double d, double xk, double &nrm, double &shift, double &vk,
+                                             double &beta) {
+  const long long db = __double_as_longlong(d);
+  const int dh = (int)(db >> 32);
+  const int ex = ((dh >> 20) & 0x7ff) - 1023;
+  // d = 2^(2 h) m, m in [1, 4): y0 = rsqrt(m) 2^-h
+  const int odd = ex & 1, h = (ex - odd) >> 1;
+  const unsigned m23 = ((unsigned)(dh & 0xfffff) << 3) | ((unsigned)db >> 29);
+  const int yf = __float_as_int(rsqrt_seed(__int_as_float(((127 + odd) << 23) | (int)m23)));
+  const double y0 =
+      __hiloint2double(((((yf >> 23) & 0xff) + (1023 - 127) - h) << 20) | ((yf & 0x7fffff) >> 3), (yf & 7) << 29);
+  const double dx = fma(-xk, xk, d);
+  const double t = d * y0;
+  const double e = fma(-t, y0, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  nrm = fma(t * e, p, t);
+  const bool neg = (__double_as_longlong(xk) < 0) && ((__double_as_longlong(xk) << 1) != 0);
+  shift = neg ? -nrm : nrm;
+  vk = xk + shift;
+  const double q = fma(vk, vk, dx);
+  // q = 2^g m, m in [1, 2): r0 = (1 / m) 2^-g ~ 1 / q, and beta = 2 / q from
+  // the doubled seed (exponent + 1)
+  const long long qb = __double_as_longlong(q);
+  const int qh = (int)(qb >> 32);
+  const int g = ((qh >> 20) & 0x7ff) - 1023;
+  const unsigned n23 = ((unsigned)(qh & 0xfffff) << 3) | ((unsigned)qb >> 29);
+  const int rf = __float_as_int(rcp_seed(__int_as_float((127 << 23) | (int)n23)));
+  const int rhi = ((((rf >> 23) & 0xff) + (1023 - 127) - g) << 20) | ((rf & 0x7fffff) >> 3), rlo = (rf & 7) << 29;
+  const double r0 = __hiloint2double(rhi, rlo), r2 = __hiloint2double(rhi + (1 << 20), rlo);
+  const double f = fma(-q, r0, 1.0);
+  beta = fma(r2, fma(f, f, f), r2);
+  return ex >= -1000 && ex <= 1000;
 }
 
 // Team arg-max with one barrier: partials alternate between two buffers by
 // parity, so consecutive uses of one buffer must be separated by at least one
-// other barrier.  Ties go to the smaller index.
+// other barrier.  Keys are the bit patterns of non-negative doubles, which
+// order like the values, so the reduction runs on the integer pipe; ties go to
+// the smaller index.
 __device__ __forceinline__ unsigned long long *argmax_keys() {
   __shared__ unsigned long long rk[2][32];
   return &rk[0][0];
@@ -283,11 +336,8 @@ __device__ __forceinline__ int *argmax_idx() {
   return &ri[0][0];
 }
 
-// Warp stage of the arg-max: lane 0 leaves (key, index) of the warp's best in
-// the parity buffer.  The key of a non-negative double orders like (high
-// word, low word), so the reduction runs on the integer pipe.
-__device__ __forceinline__ void warp_argmax_partial(double val, int idx, int parity) {
-  const unsigned long long key = (unsigned long long)__double_as_longlong(val);
+// Warp stage: lane 0 leaves (key, index) of the warp's best in buffer parity.
+__device__ __forceinline__ void warp_argmax_key(unsigned long long key, int idx, int parity) {
   const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
   const unsigned mhi = __reduce_max_sync(kFull, hi);
   const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
@@ -311,18 +361,257 @@ __device__ __forceinline__ void argmax_finish(int parity, double &bv, int &bi) {
   bi = besti;
 }
 
-__device__ __forceinline__ void team_argmax1(double val, int idx, int parity, double &bv, int &bi) {
-  warp_argmax_partial(val, idx, parity);
-  __syncthreads();
-  argmax_finish(parity, bv, bi);
+__device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// One Householder step on rows [k, r) with pivot column piv among the cnt
+// columns of the pass (column of position p: list ? list[p] : a0 + p; the
+// pivot is one of them), laid out by L = hh_layout(cnt, r - k).  Dot pass:
+// d_j = M_piv . M_j for every column j of the pass, d_piv = ||M_piv||^2, and
+// the old row k kept in hh_rowk.  If sqrt(d_piv) <= thr (or d_piv = 0), M is
+// left untouched and 0 is returned.  Otherwise the reflector
+// H = I - beta v v' (v = M_piv + sign(x_k) ||M_piv|| e_k, beta =
+// 1 / (||M_piv|| (||M_piv|| + |x_k|))) is applied to the other columns,
+// column piv becomes (-sign(x_k) ||M_piv||, 0, ..., 0), and the norm is
+// returned.  L is then replaced by the layout of the next step (cnt - 1
+// columns on rows [k + 1, r)), computed in the shadow of the FP64 latency.
+// Scratch: v (rows), d (columns).
+//
+// Column pivoting (cn given): the update pass also downdates the remaining
+// squared norms cn of the candidate columns in [cand0, cand1) (LAPACK
+// xLAQP2's safeguard: a norm is evaluated afresh from its rows when it falls
+// to 2^-26 = sqrt(eps) of its last exact value, crs holding that value times
+// 2^-26), leaves each warp's best candidate in arg-max buffer parity, marks
+// piv done and writes the list without piv to next (order kept).
+static __device__ double hh_core(double *M, int ld, int k, int r, int piv, const short *list, int a0, int cnt,
+                                 HHLayout &L, double *v, double *d, double thr, int *done = nullptr,
+                                 short *next = nullptr, double *cn = nullptr, double *crs = nullptr,
+                                 int cand0 = 0, int cand1 = 0, int parity = 0) {
+  const int tid = team_rank(), T = TEAM, wid = tid >> 5;
+  double *mk = hh_rowk();
+  const int S = L.S, sg = L.sg;
+  const int pw0 = wid * L.cw, pw1 = min(pw0 + L.cw, cnt);
+  for (int i = k + tid; i < r; i += T) v[i] = M[i * ld + piv];
+  for (int p = tid; p < cnt; p += T) {
+    const int j = list ? list[p] : a0 + p;
+    mk[j] = M[k * ld + j];
+    if (next && j != piv) next[p - (j > piv ? 1 : 0)] = (short)j;
+  }
+  // dot pass
+  const int p1 = pw0 + L.lc;
+  const bool on1 = S > 1 && L.lc < L.cw && p1 < pw1;
+  const int j1 = on1 ? (list ? list[p1] : a0 + p1) : piv;
+  if (S > 1) {
+    double acc = 0.0;
+    if (on1)
+      for (int i = k + sg; i < r; i += S) acc = fma(M[i * ld + piv], M[i * ld + j1], acc);
+    acc = seg_sum(acc, sg, S);
+    if (on1 && sg == 0) d[j1] = acc;
+  } else {
+    for (int p = pw0 + (tid & 31); p < pw1; p += 32) {
+      const int j = list ? list[p] : a0 + p;
+      double acc = 0.0;
+      for (int i = k; i < r; i++) acc = fma(M[i * ld + piv], M[i * ld + j], acc);
+      d[j] = acc;
+    }
+  }
+  tsync();
+  const double dp = d[piv];
+  const double xk = v[k];
+  double nrm, shift, vk, beta;
+  const bool fast = hh_reflector(dp, xk, nrm, shift, vk, beta);
+  const HHLayout Ln = hh_layout(cnt - 1, r - k - 1);
+  if (!fast) {
+    nrm = sqrt(dp);
+    shift = ((__double_as_longlong(xk) < 0) && ((__double_as_longlong(xk) << 1) != 0)) ? -nrm : nrm;
+    vk = xk + shift;
+    beta = 1.0 / (nrm * (nrm + fabs(xk)));
+  }
+  if (!(dp > 0.0) || !(nrm > thr)) return 0.0;
+  L = Ln;
+  // update pass (and, when pivoting, the norm downdate and the warp's arg-max)
+  unsigned long long bkey = 0ull;
+  int bidx = 0x7fffffff;
+  if (S > 1) {
+    if (on1) {
+      if (j1 == piv) {
+        for (int i = k + sg; i < r; i += S) M[i * ld + piv] = (i == k) ? -shift : 0.0;
+        if (sg == 0 && done) done[piv] = 1;
+      } else {
+        const double wj = beta * fma(shift, mk[j1], d[j1]);
+        for (int i = k + sg; i < r; i += S) M[i * ld + j1] = fma(-wj, (i == k) ? vk : v[i], M[i * ld + j1]);
+      }
+    }
+    if (cn) {
+      __syncwarp();  // a column's row segments are lanes of this warp
+      const bool cand = on1 && j1 != piv && j1 >= cand0 && j1 < cand1;
+      double nw = 0.0;
+      bool fresh = false;
+      if (cand) {
+        const double a = M[k * ld + j1];
+        nw = fma(-a, a, cn[j1]);
+        fresh = !((long long)dkey(nw) > (long long)dkey(crs[j1]));
+      }
+      if (__any_sync(kFull, fresh)) {
+        double acc = 0.0;
+        if (fresh)
+          for (int i = k + 1 + sg; i < r; i += S) acc = fma(M[i * ld + j1], M[i * ld + j1], acc);
+        acc = seg_sum(acc, sg, S);
+        if (fresh) nw = acc;
+      }
+      if (cand && sg == 0) {
+        cn[j1] = nw;
+        if (fresh) crs[j1] = 0x1p-26 * nw;
+        bkey = dkey(nw);
+        bidx = j1;
+      }
+    }
+  } else {
+    for (int p = pw0 + (tid & 31); p < pw1; p += 32) {
+      const int j = list ? list[p] : a0 + p;
+      if (j == piv) {
+        for (int i = k; i < r; i++) M[i * ld + piv] = (i == k) ? -shift : 0.0;
+        if (done) done[piv] = 1;
+        continue;
+      }
+      const double wj = beta * fma(shift, mk[j], d[j]);
+      M[k * ld + j] = fma(-wj, vk, M[k * ld + j]);
+      for (int i = k + 1; i < r; i++) M[i * ld + j] = fma(-wj, v[i], M[i * ld + j]);
+      if (cn && j >= cand0 && j < cand1) {
+        const double a = M[k * ld + j];
+        double nw = fma(-a, a, cn[j]);
+        if (!((long long)dkey(nw) > (long long)dkey(crs[j]))) {
+          nw = 0.0;
+          for (int i = k + 1; i < r; i++) nw = fma(M[i * ld + j], M[i * ld + j], nw);
+          crs[j] = 0x1p-26 * nw;
+        }
+        cn[j] = nw;
+        if (bidx == 0x7fffffff || dkey(nw) > bkey) { bkey = dkey(nw); bidx = j; }
+      }
+    }
+  }
+  if (cn) warp_argmax_key(bkey, bidx, parity);
+  tsync();
+  return nrm;
 }
 
-// The pivoted form of hh_step: the update pass also downdates the remaining
-// norms of the candidate columns (re-evaluating a marked one from its rows,
-// which sit on the same warp) and leaves each warp's best candidate in the
-// arg-max buffer `parity`, so that the next pivot is known after the pass's
-// own barrier.  Returns the norm, or 0 (M untouched) when it does not exceed thr.
-static __device__ double hh_pivot_step(double *M, int ld, int k, int r, int piv, int a0, int a1, int *done,
+// One Householder step applied to the columns [a0, a1) (piv among them).
+static __device__ __forceinline__ double hh_step(double *M, int ld, int k, int r, int piv, int a0, int a1,
+                                                 double *v, double *d, double thr) {
+  HHLayout L = hh_layout(a1 - a0, r - k);
+  return hh_core(M, ld, k, r, piv, nullptr, a0, a1 - a0, L, v, d, thr);
+}
+
+// Unpivoted steps down the diagonal: for col = c0, c0 + 1, ... < c1 while the
+// row k < r, the reflector of column col on rows [k, r) applied to the
+// columns [col, a1).  k advances when the column's norm exceeds thr, or after
+// every column when keep_diag is set (row k then stays paired with column
+// k).  Returns the final k.
+static __device__ int hh_diag_steps(double *M, int ld, int k, int r, int c0, int c1, int a1, double *v, double *d,
+                                    double thr, bool keep_diag) {
+  HHLayout L = hh_layout(a1 - c0, r - k);
+  for (int col = c0; col < c1 && k < r; col++) {
+    const bool ok = hh_core(M, ld, k, r, col, nullptr, col, a1 - col, L, v, d, thr) > 0.0;
+    if (ok || keep_diag) k++;
+    if (!ok) L = hh_layout(a1 - col - 1, r - k);
+  }
+  return k;
+}
+
+// Column-pivoted Householder steps on rows [k, r).  Each step takes the
+// candidate column (in [cand0, cand1), not done) of largest remaining norm;
+// while its exact norm exceeds thr, its reflector is applied to the not-done
+// columns of [app0, app1) (which must contain the candidates), it is marked
+// done and recorded in pc (when given).  Remaining norms are downdated after
+// every step and evaluated afresh once cancellation has consumed half their
+// digits (the safeguard of LAPACK's xLAQP2, threshold sqrt(eps) = 2^-26).
+// The passes run over a list of the not-done columns, shortened by one
+// column per step.  Returns the number of steps taken.
+static __device__ int hh_pivoted_list(double *M, int ld, int k, int r, int cand0, int cand1, int app0,
+                                      int app1, int *done, int *pc, double thr, double *v, double *w) {
+  const int tid = team_rank(), lane = tid & 31, wid = tid >> 5;
+  double *cn = hh_norms(), *crs = cn + kMaxCols;
+  short *lists = hh_lists();
+  // the list: not-done columns of [app0, app1) in increasing order.  Every
+  // warp builds it (identical values), so each warp can read its own writes
+  // after __syncwarp and no team barrier is needed.
+  int cnt = 0, pc0 = 0, pc1 = 0;
+  for (int j0 = app0; j0 < app1; j0 += 32) {
+    const int j = j0 + lane;
+    const bool on = j < app1 && !done[j];
+    const unsigned b = __ballot_sync(kFull, on);
+    if (on) lists[cnt + __popc(b & ((1u << lane) - 1u))] = (short)j;
+    pc0 += __popc(b & __ballot_sync(kFull, j < cand0));
+    pc1 += __popc(b & __ballot_sync(kFull, j < cand1));
+    cnt += __popc(b);
+  }
+  __syncwarp();
+  const int ncand = pc1 - pc0;
+  // exact squared norms of the candidates over rows [k, r)
+  unsigned long long bkey = 0ull;
+  int bidx = 0x7fffffff;
+  {
+    const HHLayout C = hh_layout(ncand, r - k);
+    const int pw0 = wid * C.cw, pw1 = min(pw0 + C.cw, ncand);
+    if (C.S > 1) {
+      const int p = pw0 + C.lc;
+      const bool on = C.lc < C.cw && p < pw1;
+      const int j = on ? lists[pc0 + p] : 0;
+      double acc = 0.0;
+      if (on)
+        for (int i = k + C.sg; i < r; i += C.S) acc = fma(M[i * ld + j], M[i * ld + j], acc);
+      acc = seg_sum(acc, C.sg, C.S);
+      if (on && C.sg == 0) {
+        cn[j] = acc;
+        crs[j] = 0x1p-26 * acc;
+        bkey = dkey(acc);
+        bidx = j;
+      }
+    } else {
+      for (int p = pw0 + lane; p < pw1; p += 32) {
+        const int j = lists[pc0 + p];
+        double acc = 0.0;
+        for (int i = k; i < r; i++) acc = fma(M[i * ld + j], M[i * ld + j], acc);
+        cn[j] = acc;
+        crs[j] = 0x1p-26 * acc;
+        if (bidx == 0x7fffffff || dkey(acc) > bkey) { bkey = dkey(acc); bidx = j; }
+      }
+    }
+  }
+  warp_argmax_key(bkey, bidx, 0);
+  HHLayout L = hh_layout(cnt, r - k);
+  tsync();
+  double b2;
+  int piv;
+  argmax_finish(0, b2, piv);
+  // Between exact evaluations the downdated norms carry a relative error
+  // below about 2^-22, so a largest estimate under thr^2 (1 - 2^-16) means
+  // every candidate fails the exact test: stop without the step.
+  const double stop2 = thr * thr * (1.0 - 0x1p-16);
+  int steps = 0;
+  while (k < r && piv != 0x7fffffff && !(b2 < stop2)) {
+    const double nrm = hh_core(M, ld, k, r, piv, lists + (steps & 1) * kMaxCols, 0, cnt, L, v, w, thr, done,
+                               lists + ((steps + 1) & 1) * kMaxCols, cn, crs, cand0, cand1, (steps + 1) & 1);
+    if (nrm == 0.0) break;
+    if (tid == 0 && pc) pc[steps] = piv;
+    k++;
+    steps++;
+    cnt--;
+    if (k >= r) break;
+    argmax_finish(steps & 1, b2, piv);
+  }
+  tsync();
+  return steps;
+}
+
+// Range form of a pivoted step: the passes cover every column of [a0, a1)
+// (done ones idle) with power-of-two row segments, S (a1 - a0) <= team size,
+// and the reflector scalars come from the library square root and divide.
+// The update pass also downdates the remaining norms of the candidate
+// columns (re-evaluating a marked one from its rows, which sit on the same
+// warp) and leaves each warp's best candidate in the arg-max buffer `parity`,
+// so that the next pivot is known after the pass's own barrier.  Returns the
+// norm, or 0 (M untouched) when it does not exceed thr.
+static __device__ double hh_range_step(double *M, int ld, int k, int r, int piv, int a0, int a1, int *done,
                                        double *v, double *d, double thr, double *cn, double *cref, int cand0,
                                        int cand1, int parity) {
   const int tid = team_rank(), T = TEAM;
@@ -386,21 +675,17 @@ static __device__ double hh_pivot_step(double *M, int ld, int k, int r, int piv,
     cn[j] = nw;
     if (nw > best) { best = nw; bidx = j; }
   }
-  warp_argmax_partial(best < 0.0 ? 0.0 : best, best < 0.0 ? 0x7fffffff : bidx, parity);
+  warp_argmax_key(best < 0.0 ? 0ull : dkey(best), best < 0.0 ? 0x7fffffff : bidx, parity);
   tsync();
   return nrm;
 }
 
-// Column-pivoted Householder steps on rows [k, r).  Each step takes the
-// candidate column (in [cand0, cand1), not done) of largest remaining norm;
-// while its exact norm exceeds thr, its reflector is applied to the not-done
-// columns of [app0, app1) (which must contain the candidates), it is marked
-// done and recorded in pc (when given).  Remaining norms are downdated after
-// every step and evaluated afresh once cancellation has consumed half their
-// digits (the safeguard of LAPACK's xLAQP2, threshold sqrt(eps) = 2^-26).
-// Returns the number of steps taken.
-static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int cand1, int app0, int app1,
-                                 int *done, int *pc, double thr, double *v, double *w) {
+// Range form of the column-pivoted steps (same contract as hh_pivoted_list):
+// the passes cover every column of [app0, app1), done ones idle, with
+// power-of-two row segments; the next pivot's candidates are downdated in
+// the update pass and the first norms are evaluated one column per thread.
+static __device__ int hh_pivoted_range(double *M, int ld, int k, int r, int cand0, int cand1, int app0,
+                                       int app1, int *done, int *pc, double thr, double *v, double *w) {
   const int tid = team_rank(), T = TEAM;
   double *cn = hh_norms(), *cref = cn + kMaxCols;
   double mybest = -1.0;
@@ -415,10 +700,12 @@ static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int
   }
   double b2;
   int piv;
-  team_argmax1(mybest < 0.0 ? 0.0 : mybest, mybest < 0.0 ? 0x7fffffff : mypiv, 0, b2, piv);
+  warp_argmax_key(mybest < 0.0 ? 0ull : dkey(mybest), mybest < 0.0 ? 0x7fffffff : mypiv, 0);
+  tsync();
+  argmax_finish(0, b2, piv);
   int steps = 0;
   while (k < r && piv != 0x7fffffff) {
-    const double nrm = hh_pivot_step(M, ld, k, r, piv, app0, app1, done, v, w, thr, cn, cref, cand0, cand1,
+    const double nrm = hh_range_step(M, ld, k, r, piv, app0, app1, done, v, w, thr, cn, cref, cand0, cand1,
                                      (steps + 1) & 1);
     if (nrm == 0.0) break;
     if (tid == 0 && pc) pc[steps] = piv;
@@ -429,6 +716,28 @@ static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int
   }
   tsync();
   return steps;
+}
+
+// Column-pivoted Householder steps on rows [k, r) (contract of
+// hh_pivoted_list).  Two forms: the list form packs the active columns
+// evenly over the warps with any segment count, the range form keeps the
+// fixed power-of-two layout over [app0, app1).  The list form has a larger
+// fixed cost per factorization and per step (the list, its layout), so it is
+// taken only where its first step saves at least kListGain row FMAs per lane
+// and pass: tall, wide eliminations rather than short projections.
+constexpr int kListGain = 8;
+__device__ __forceinline__ bool hh_list_pays(int nc, int nr) {
+  const int T = TEAM;
+  int s_range = 1;
+  while (2 * s_range <= 32 && 2 * s_range * nc <= T && 2 * s_range <= nr) s_range *= 2;
+  const HHLayout L = hh_layout(nc, nr);
+  return (nr + s_range - 1) / s_range - (nr + L.S - 1) / L.S >= kListGain;
+}
+static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int cand1, int app0, int app1,
+                                 int *done, int *pc, double thr, double *v, double *w) {
+  if (hh_list_pays(app1 - app0, r - k))
+    return hh_pivoted_list(M, ld, k, r, cand0, cand1, app0, app1, done, pc, thr, v, w);
+  return hh_pivoted_range(M, ld, k, r, cand0, cand1, app0, app1, done, pc, thr, v, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -877,8 +1186,7 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
   tsync();
   // E: compress the remaining cost rows over the kept columns (no pivoting)
   int ke = kk;
-  for (int col = ne; col < off && ke < r; col++)
-    if (hh_step(M, ld, ke, r, col, col, nc, nullptr, v, w, 0.0) > 0.0) ke++;
+  ke = hh_diag_steps(M, ld, ke, r, ne, off, nc, v, w, 0.0, false);
   res.kq = ke - kk;
   for (int idx = tid; idx < res.kq * (nk + 1); idx += TEAM) {
     int a = idx / (nk + 1), j = idx - a * (nk + 1);
