@@ -13,7 +13,9 @@ with duplicated or D = 0 rows, full-rank terminal rows), seeded and synthetic.
 
 At N = 1 the line also carries "graph" (the same step captured once into a
 CUDA graph and replayed), "plain" (the same instance as one chunk: a single
-CTA sweeps every stage, no scan) and "batched" (4096 uneven problems, a
+CTA sweeps every stage, no scan), "scan_skip" (the Sec. 6 shortcut on an
+instance without state-only or terminal rows, with and without the skip) and
+"batched" (4096 uneven problems, a
 stand-in for the batched configuration, with the oracle on all host cores
 beside it).
 
@@ -206,6 +208,32 @@ def measure_plain(pb, dev, flush, stream, refine, steps=3):
             "kkt_resid": r["resid"], "status": r["status"], "gate_passed": r["status"] == 0 and r["resid"] <= KKT_GATE}
 
 
+def measure_scan_skip(dev, flush, stream, refine, steps=5):
+    """The Sec. 6 shortcut on an instance it applies to: mixed_only_n12 (N=1024, n=12, m=6, mixed rows
+    U{0..4} per stage with wide full-row-rank D_i, no state-only or terminal rows), timed with the shortcut
+    (domain scan skipped) and without it (scan forced).  Both passes must give the same results."""
+    import numpy as np
+    from paper_2407_05433_gb300 import eclqr, synth
+    pb = synth.config("mixed_only_n12")
+    out, ref = {"workload": "mixed_only_n12: N=1024, n=12, m=6, mixed rows U{0..4}, no state-only or terminal rows"}, None
+    for name, flag in (("skip", 1), ("scan", 0)):
+        b = eclqr.Batch([pb], device=dev, refine=refine, scan_skip=flag)
+        b.run()
+        ms = _timed_runs(b, steps, flush, stream)
+        (r,) = b.results()
+        skipped = bool(b.scan_skipped()[0])
+        b.close()
+        out[name] = {"value": pb.N / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "scan_skipped": skipped,
+                     "kkt_resid": r["resid"], "gate_passed": r["status"] == 0 and r["resid"] <= KKT_GATE}
+        if ref is None:
+            ref = r
+        else:
+            out["bit_identical"] = all(np.array_equal(np.asarray(ref[k]), np.asarray(r[k]))
+                                       for k in ("x", "u", "lam", "mu", "eta", "alpha"))
+    out["speedup"] = out["scan"]["ms_per_step"] / out["skip"]["ms_per_step"]
+    return out
+
+
 BATCH_DISTINCT, BATCH_PROBLEMS = 256, 4096
 
 
@@ -226,13 +254,15 @@ def measure_batched(pbs, dev, flush, stream, refine, steps=3):
     res = b.resid.cpu().numpy()
     stat = b.status.cpu().numpy()
     launches = b.launches()
+    skipped = int(b.scan_skipped().sum())
     b.close()
     stages = int(sum(p.N for p in pbs))
     passed = (stat == 0) & (res <= KKT_GATE)
     return {"value": stages / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "problems": len(pbs),
             "stages": stages, "distinct_draws": BATCH_DISTINCT, "refine": refine,
             "status_failures": int((stat != 0).sum()), "resid_max": float(res.max()),
-            "gate_passed_frac": float(passed.mean()), "gate_passed": bool(passed.all())}
+            "gate_passed_frac": float(passed.mean()), "gate_passed": bool(passed.all()),
+            "scan_skipped_problems": skipped}
 
 
 def _oracle_worker(args):
@@ -414,6 +444,7 @@ def run_gpu(args):
     if world == 1 and not args.no_extra:
         extras["graph"] = measure_graph(batch, pb, flush, stream, max(5, args.steps // 2))
         extras["plain"] = measure_plain(pb, dev, flush, stream, args.refine)
+        extras["scan_skip"] = measure_scan_skip(dev, flush, stream, args.refine)
         _, bpbs = batched_problems()
         extras["batched"] = measure_batched(bpbs, dev, flush, stream, args.refine)
     import oracle

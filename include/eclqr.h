@@ -100,6 +100,12 @@ typedef struct {
   int32_t refine;    /* refinement passes on the reduced LQR KKT residual; default 2          */
   int32_t chunk;     /* stages per scan chunk; 0 = chosen from N and the SM count             */
   int32_t team_warps; /* warps of the CTA that runs one task: 1, 2, 4 or 8; 0 = 4            */
+  int32_t scan_skip;  /* 1 (default): take the shortcut of Sec. 6 (complete algorithm and
+                       * complexity) where it applies: a problem without state-only or
+                       * terminal rows whose every stage's mixed rows leave no row on x_i
+                       * once u_i is projected out (Lemma 1, same tolerances) has
+                       * X_i = R^n for all i, and its feasible-domain scan is skipped.
+                       * 0: always run the scan.  Results are the same either way.       */
 } eclqr_options;
 
 /* element counts of every packed array (for allocation) */
@@ -127,6 +133,11 @@ int eclqr_create(const eclqr_desc *desc, const eclqr_options *opt, eclqr_handle 
  * plus the coefficient part of the reduced Riccati solve (Sec. 6): everything
  * that does not depend on s_0.  status: device int32[P], overwritten. */
 int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *stream);
+
+/* After eclqr_build: flags (device int32[P]) receives 1 for every problem whose
+ * feasible-domain scan the Sec. 6 shortcut skipped (see eclqr_options.scan_skip),
+ * 0 otherwise.  Asynchronous on stream.  ECLQR_ESTATE before a build. */
+int eclqr_scan_skipped(eclqr_handle *h, int32_t *flags, void *stream);
 
 /* Checks s_0 (eq. initial-feasibility), forms z_0 (eq. reduced-initial), rolls
  * the reduced LQR out with refinement on its KKT residual, and recovers

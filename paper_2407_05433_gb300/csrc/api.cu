@@ -30,6 +30,7 @@ struct GroupHost {
   cudaEvent_t done = nullptr;   // records the end of the group's work on s
   int maxnch = 0;
   int levels = 0;
+  bool any_skip = false;  // some problem of the group may take the Sec. 6 shortcut
   void *dmem = nullptr;
   std::vector<int> ids;  // batch indices of the problems in this group
 };
@@ -183,6 +184,7 @@ void eclqr_default_options(eclqr_options *opt) {
   opt->refine = 2;
   opt->chunk = 0;
   opt->team_warps = 0;
+  opt->scan_skip = 1;
 }
 
 int eclqr_layout(const eclqr_desc *d, eclqr_layout_info *out) {
@@ -220,7 +222,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   if (h->opt.team_warps == 0) h->opt.team_warps = kTeamWarps;
   const int tw = h->opt.team_warps;
   if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0) ||
-      !(tw == 1 || tw == 2 || tw == 4 || tw == 8)) {
+      !(tw == 1 || tw == 2 || tw == 4 || tw == 8) || !(h->opt.scan_skip == 0 || h->opt.scan_skip == 1)) {
     delete h;
     return ECLQR_EINVAL;
   }
@@ -281,7 +283,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       const int need = std::max({smem_primal_sweep(n, m, pmax, qmax), smem_rel_level(n, pmax, qmax), smem_param(n),
                                  smem_elim(n, m, pmax), smem_lqr_up(n, m), smem_lqr_level(n), smem_riccati(n, m),
                                  smem_aff(n, m), smem_dual_stage(n, m), smem_dual_sweep(n, m, pmax, qmax),
-                                 smem_dual_leaf(n, m, pmax, qmax)});
+                                 smem_dual_leaf(n, m, pmax, qmax), smem_scan_check(n, m, pmax)});
       if ((size_t)need * sizeof(double) > (size_t)kMaxSmemBytes) {
         for (auto &x : h->groups) cudaFree(x.dmem);
         delete h;
@@ -291,6 +293,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     std::vector<ProbInfo> gp;
     std::vector<StageInfo> gs;
     std::vector<ChunkInfo> gc;
+    gh.any_skip = false;
     for (int j : gh.ids) {
       ProbInfo pi = pinfo[j];
       int L = h->opt.chunk;
@@ -308,6 +311,9 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       pi.st0 = (int)gs.size();
       const int local = (int)gp.size();
       int prow = 0, qrow = 0;
+      // Sec. 6 shortcut: eligible when no stage has state-only or terminal rows and
+      // every D_i could have full row rank (p_i <= m); k_scan_check decides the rest
+      pi.skip_ok = h->opt.scan_skip ? 1 : 0;
       for (int i = 0; i <= pi.N; i++) {
         StageInfo si;
         si.prob = local;
@@ -316,12 +322,14 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
         si.q = d->q[qstage[j] + i];
         si.prow = prow;
         si.qrow = qrow;
+        if (si.q > 0 || si.p > g.m) pi.skip_ok = 0;
         prow += si.p;
         qrow += si.q;
         gs.push_back(si);
       }
       for (int c = 0; c <= pi.nch; c++) gc.push_back(ChunkInfo{local, c});
       gh.maxnch = std::max(gh.maxnch, pi.nch);
+      gh.any_skip = gh.any_skip || pi.skip_ok;
       gp.push_back(pi);
     }
     g.nprob = (int)gp.size();
@@ -343,6 +351,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     size_t o_CS0 = take(sizeof(double) * (size_t)g.cs_stride * g.nslot);
     size_t o_CS1 = take(sizeof(double) * (size_t)g.cs_stride * g.nslot);
     size_t o_CI0 = take(sizeof(int) * CI_STRIDE * g.nslot), o_CI1 = take(sizeof(int) * CI_STRIDE * g.nslot);
+    size_t o_need = take(sizeof(int) * (size_t)g.nprob);
     if (cudaMalloc(&gh.dmem, off) != cudaSuccess) {
       for (auto &x : h->groups) cudaFree(x.dmem);
       delete h;
@@ -362,6 +371,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     g.CS[1] = (double *)(base + o_CS1);
     g.CI[0] = (int *)(base + o_CI0);
     g.CI[1] = (int *)(base + o_CI1);
+    g.need_scan = (int *)(base + o_need);
     h->groups.push_back(gh);
   }
   if (h->groups.size() > 1) {
@@ -397,6 +407,11 @@ int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *
     g.status = status;
     const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
     const int sw = smem_primal_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
+    if (gh.any_skip) {
+      if (cudaMemsetAsync(g.need_scan, 0, sizeof(int) * g.nprob, gst) != cudaSuccess) return ECLQR_ECUDA;
+      const int sk = smem_scan_check(n, m, pm);
+      TRY(launch(h, k_scan_check, g.nstage, sk, gst, g, sk));
+    }
     TRY(launch(h, k_terminal, g.nprob, sw, gst, g, sw));
     TRY(launch(h, k_primal_up, g.nslot, sw, gst, g, sw));
     int src = 0;
@@ -554,6 +569,16 @@ int eclqr_reduced_dims(eclqr_handle *h, int32_t *nbar, int32_t *mbar, void *stre
   return ECLQR_OK;
 }
 
+int eclqr_scan_skipped(eclqr_handle *h, int32_t *flags, void *stream) {
+  if (!h || !flags) return ECLQR_EINVAL;
+  if (!h->built) return ECLQR_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  TRY(fork_groups(h, st));
+  for (auto &gh : h->groups) TRY(launch(h, k_skip_flags, gh.g.nprob, 0, group_stream(h, gh, st), gh.g, flags));
+  TRY(join_groups(h, st));
+  return ECLQR_OK;
+}
+
 int64_t eclqr_launch_count(const eclqr_handle *h) { return h ? h->launches : 0; }
 
 void eclqr_destroy(eclqr_handle *h) {
@@ -576,7 +601,7 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
     return ECLQR_OK;
   }
   static const struct { const char *name; const void *fn; } table[] = {
-      {"k_terminal", (const void *)k_terminal}, {"k_primal_up", (const void *)k_primal_up},
+      {"k_scan_check", (const void *)k_scan_check}, {"k_terminal", (const void *)k_terminal}, {"k_primal_up", (const void *)k_primal_up},
       {"k_rel_level", (const void *)k_rel_level}, {"k_primal_down", (const void *)k_primal_down},
       {"k_param", (const void *)k_param}, {"k_elim", (const void *)k_elim},
       {"k_lqr_up", (const void *)k_lqr_up}, {"k_lqr_level", (const void *)k_lqr_level},

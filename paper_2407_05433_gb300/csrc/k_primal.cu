@@ -28,11 +28,47 @@ __host__ int smem_rel_level(int n, int pmax, int qmax) {
   (void)pmax; (void)qmax;
   return rows * ldm + rows + 2 * ldm + 8;
 }
+__host__ int smem_scan_check(int n, int m, int pmax) {
+  const int ld = m + n + 1;
+  return pmax * ld + 2 * ld + pmax + ld / 2 + 8;
+}
 __host__ int smem_param(int n) { return n * (n + 1) + n * n + n * n + n + n + 4 * n + 8 + n; }
 __host__ int smem_elim(int n, int m, int pmax) {
   int rows = pmax + n;
   return 3 * n * n + m * (n + 1) + n * (n + 1) + rows * m + rows * (n + 1) + m * rows + m * m +
          m * (n + 1) + 4 * n * m + m * m + 12 * n + 8 * m + 2 * rows + 16 + (n + m) * (n + m) + (n + m);
+}
+
+// ----------------------------------------------------------- shortcut test (Sec. 6)
+// For a problem the host found eligible (no state-only or terminal rows,
+// p_i <= m), stage i keeps X_i = R^n only if projecting u_i out of its mixed
+// rows [D_i | C_i | d_i] (Lemma 1, the scan's tolerance policy) leaves no row
+// on x_i.  A stage that leaves one marks the problem as needing the scan.
+__global__ void k_scan_check(Group g, int per_task) {
+  const int s = team_task();
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  if (!P.skip_ok || S.i >= P.N || S.p == 0) return;
+  const int n = g.n, m = g.m, tid = team_rank(), ld = m + n + 1;
+  double *sm = team_smem(per_task);
+  double *M = sm, *scr = M + g.pmax * ld;
+  for (int idx = tid; idx < S.p * ld; idx += TEAM) {
+    const int r = idx / ld, j = idx - r * ld;
+    const size_t row = S.prow + r;
+    M[idx] = (j < m) ? g.D[P.oD + row * m + j]
+                     : ((j < m + n) ? g.C[P.oC + row * n + (j - m)] : g.d[P.od + row]);
+  }
+  tsync();
+  const int gs[1] = {m};
+  const ProjResult pr = wproject(M, ld, S.p, 1, gs, n, g.tau_rank, g.tau_inc, nullptr, 0, scr);
+  if (tid == 0 && (pr.krank > 0 || pr.inconsistent)) g.need_scan[S.prob] = 1;
+}
+
+// flags[P.id] = 1 where the shortcut skipped the problem's scan
+__global__ void k_skip_flags(Group g, int32_t *flags) {
+  const int t = team_task();
+  if (t < g.nprob && team_rank() == 0) flags[g.prob[t].id] = scan_skipped(g, t) ? 1 : 0;
 }
 
 // ----------------------------------------------------------- terminal domain X_N
@@ -42,6 +78,10 @@ __global__ void k_terminal(Group g, int per_task) {
   const ProbInfo &P = g.prob[t];
   const int n = g.n, tid = team_rank();
   const int s = P.st0 + P.N;
+  if (scan_skipped(g, t)) {  // X_N = R^n: no terminal rows
+    if (tid == 0) stage_wi(g, s)[SI_HROWS] = 0;
+    return;
+  }
   const StageInfo S = g.st[s];
   double *sm = team_smem(per_task);
   const int ld = n + 1;
@@ -77,7 +117,7 @@ __global__ void k_primal_up(Group g, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
-  if (ci.c >= P.nch) return;
+  if (ci.c >= P.nch || scan_skipped(g, ci.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   double *sm = team_smem(per_task);
@@ -147,6 +187,7 @@ __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (fail_code == ST_INFEASIBLE_SUFFIX && scan_skipped(g, ci.prob)) return;  // primal scan skipped
   const int tid = team_rank();
   const int ldr = 2 * g.n + 1;
   const double *S1 = g.CS[src] + (size_t)t * g.cs_stride;
@@ -246,6 +287,10 @@ __global__ void k_primal_down(Group g, int fin, int per_task) {
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
+  if (scan_skipped(g, ci.prob)) {  // X_i = R^n: no rows
+    for (int i = a + tid; i < b; i += TEAM) stage_wi(g, P.st0 + i)[SI_HROWS] = 0;
+    return;
+  }
   const bool resweep = ci.c + 1 < P.nch;
   const int start = resweep ? min(b + P.L, P.N) : b;
   double *sm = team_smem(per_task);

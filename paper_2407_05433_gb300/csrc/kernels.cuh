@@ -17,8 +17,11 @@ __host__ int smem_aff(int n, int m);
 __host__ int smem_dual_stage(int n, int m);
 __host__ int smem_dual_sweep(int n, int m, int pmax, int qmax);
 __host__ int smem_dual_leaf(int n, int m, int pmax, int qmax);
+__host__ int smem_scan_check(int n, int m, int pmax);
 
 // primal scan and elimination (k_primal.cu)
+__global__ void k_scan_check(Group g, int per_task);
+__global__ void k_skip_flags(Group g, int32_t *flags);
 __global__ void k_terminal(Group g, int per_task);
 __global__ void k_primal_up(Group g, int per_task);
 __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task);

@@ -20,6 +20,7 @@ struct ProbInfo {
   long long oA, oB, oc, oC, oD, od, oE, oe, oQ, oM, oR, oqv, orv;  // element offsets of the problem's data
   long long os0, ox, ou, olam, omu, oeta, oalpha;                // element offsets of s0 and outputs
   long long ost;  // sum over earlier problems of (N + 1): batch stage offset
+  int skip_ok;    // no state-only or terminal rows, p_i <= m, shortcut enabled: the scan may be skipped
 };
 
 struct StageInfo {
@@ -116,6 +117,7 @@ struct Group {
   double *CR;     // nslot * cr_stride: per-slot scan results kept across kernels
   int cr_stride;
   int *status;    // batch-global, indexed by ProbInfo::id
+  int *need_scan; // per problem: 1 once a stage leaves rows on x_i (set by k_scan_check)
   double tau_rank, tau_inc;
 };
 
@@ -129,6 +131,12 @@ struct GradOut {
 
 __device__ __forceinline__ void set_status(const Group &g, int prob, int code) {
   atomicCAS(g.status + g.prob[prob].id, 0, code);
+}
+
+// Sec. 6 shortcut: X_i = R^n for every stage of the problem, so its
+// feasible-domain scan is skipped and every H_i has no rows.
+__device__ __forceinline__ bool scan_skipped(const Group &g, int prob) {
+  return g.prob[prob].skip_ok && !g.need_scan[prob];
 }
 
 __device__ __forceinline__ double *stage_ws(const Group &g, int s) { return g.W + (size_t)s * g.ws.stride; }

@@ -38,7 +38,7 @@ class eclqr_grads(ct.Structure):
 
 class eclqr_options(ct.Structure):
     _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int32), ("chunk", ct.c_int32),
-                ("team_warps", ct.c_int32)]
+                ("team_warps", ct.c_int32), ("scan_skip", ct.c_int32)]
 
 
 LAYOUT_FIELDS = ("A", "B", "c", "C", "D", "d", "E", "e", "Q", "M", "R", "qv", "rv", "s0",
@@ -77,6 +77,8 @@ def load():
     lib.eclqr_kkt_residual.restype = i32
     lib.eclqr_reduced_dims.argtypes = [vp, vp, vp, vp]
     lib.eclqr_reduced_dims.restype = i32
+    lib.eclqr_scan_skipped.argtypes = [vp, vp, vp]
+    lib.eclqr_scan_skipped.restype = i32
     lib.eclqr_launch_count.argtypes = [vp]
     lib.eclqr_launch_count.restype = ct.c_int64
     lib.eclqr_time_kernel.argtypes = [vp, ct.c_char_p]
@@ -157,6 +159,10 @@ def eclqr_reduced_dims(h, nbar, mbar, stream):
     return load().eclqr_reduced_dims(h, nbar, mbar, stream)
 
 
+def eclqr_scan_skipped(h, flags, stream):
+    return load().eclqr_scan_skipped(h, flags, stream)
+
+
 def eclqr_launch_count(h):
     return int(load().eclqr_launch_count(h))
 
@@ -215,7 +221,8 @@ def make_desc(h):
 class Batch:
     """A batch of problems resident on one CUDA device, solved through the C ABI."""
 
-    def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=2, chunk=0, team_warps=0):
+    def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=2, chunk=0, team_warps=0,
+                 scan_skip=1):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -227,6 +234,7 @@ class Batch:
         opt = eclqr_default_options()
         opt.tau_rank, opt.tau_inc, opt.refine, opt.chunk = tau_rank, tau_inc, refine, chunk
         opt.team_warps = team_warps
+        opt.scan_skip = scan_skip
         with torch.cuda.device(self.device):
             rc, self.h = eclqr_create(self.desc, opt)
         _check(rc, "eclqr_create")
@@ -298,6 +306,13 @@ class Batch:
 
     def replay(self):
         self.graph.replay()
+
+    def scan_skipped(self):
+        """Per problem: True where the build skipped the feasible-domain scan (Sec. 6 shortcut)."""
+        torch = self.torch
+        f = torch.zeros(len(self.problems), dtype=torch.int32, device=self.device)
+        _check(eclqr_scan_skipped(self.h, f.data_ptr(), self._stream()), "eclqr_scan_skipped")
+        return f.cpu().numpy().astype(bool)
 
     def reduced_dims(self):
         torch = self.torch

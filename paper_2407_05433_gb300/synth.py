@@ -160,7 +160,8 @@ def make_problem(seed, N, n, m, p, q, *, a_mode="perturbed", degenerate_frac=0.0
                         x_star=xs, u_star=us)
 
 
-CONFIG_NAMES = ("single_n4", "degenerate_n12", "long_n16", "batched_uneven", "diff_batch", "table1")
+CONFIG_NAMES = ("single_n4", "degenerate_n12", "long_n16", "batched_uneven", "diff_batch", "table1",
+                "mixed_only_n12")
 
 
 def config(name, seed=0, N=None, index=0):
@@ -178,6 +179,12 @@ def config(name, seed=0, N=None, index=0):
                     4 terminal rows; seed = seed + index.
     table1          the paper's Table 1 shape: n=8, m=4, two state-only rows
                     per nonterminal stage, no mixed or terminal rows.
+    mixed_only_n12  N=1024, n=12, m=6, mixed rows U{0..4} per stage, no
+                    state-only or terminal rows: every D_i (p_i x m, randn,
+                    p_i < m) is wide with full row rank, so X_i = R^n for all
+                    i (the shortcut case of Sec. 6).  Square D_i are left out:
+                    their occasional ill-conditioning puts even the oracle's
+                    residual above 1e-9 over 1024 unconstrained stages.
     `N` overrides the horizon (shrunk instances of the same generator).
     """
     if name == "single_n4":
@@ -207,6 +214,11 @@ def config(name, seed=0, N=None, index=0):
         N = 256 if N is None else N
         q = np.zeros(N + 1, dtype=np.int32); q[N] = 4
         return make_problem(seed + index, N, 16, 8, 4, q)
+    if name == "mixed_only_n12":
+        N = 1024 if N is None else N
+        rng = np.random.default_rng(30_000 + seed)
+        p = rng.integers(0, 5, size=N)
+        return make_problem(seed, N, 12, 6, p, np.zeros(N + 1, dtype=np.int32))
     if name == "table1":
         N = 1024 if N is None else N
         q = np.full(N + 1, 2, dtype=np.int32); q[N] = 0

@@ -48,6 +48,7 @@ def test_strerror_and_defaults(lib):
     assert "invalid" in eclqr.eclqr_strerror(-1)
     o = eclqr.eclqr_default_options()
     assert o.tau_rank == 1e-10 and o.tau_inc == 1e-8 and o.refine == 2 and o.chunk == 0 and o.team_warps == 0
+    assert o.scan_skip == 1
 
 
 def test_layout_sizes_match_packing(lib):
@@ -83,9 +84,19 @@ def test_invalid_descriptors_rejected_before_any_device_call(lib, bad):
     assert rc == eclqr.EINVAL and not hd.value
 
 
+def test_invalid_scan_skip_option_rejected_before_any_device_call(lib):
+    """eclqr_options.scan_skip is 0 or 1; anything else is rejected while the options are checked,
+    before the handle touches the device."""
+    o = eclqr.eclqr_default_options()
+    o.scan_skip = 2
+    rc, handle = eclqr.eclqr_create(eclqr.make_desc(_desc_arrays(8, 4, 2, 1, 0)), o)
+    assert rc == eclqr.EINVAL and not handle
+
+
 def test_null_handle_calls_are_rejected(lib):
     assert lib.eclqr_build(None, None, None, None) == eclqr.EINVAL
     assert lib.eclqr_solve(None, None, None, None, None, None) == eclqr.EINVAL
+    assert lib.eclqr_scan_skipped(None, None, None) == eclqr.EINVAL
     assert eclqr.eclqr_launch_count(None) == 0
     lib.eclqr_destroy(None)
 
