@@ -740,6 +740,140 @@ static __device__ int hh_pivoted(double *M, int ld, int k, int r, int cand0, int
   return hh_pivoted_range(M, ld, k, r, cand0, cand1, app0, app1, done, pc, thr, v, w);
 }
 
+
+// ---------------------------------------------------------------------------
+// Row and column reductions of the factorizations, on the layout of the
+// Householder passes (items dealt evenly over the warps, each split into
+// segments on neighbouring lanes), so that no single lane walks a whole row
+// or column while the other warps wait.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long *colmax_keys() {
+  __shared__ unsigned long long k[2][32];
+  return &k[0][0];
+}
+
+// Largest key (bit pattern of a non-negative double) over the warp, to lane 0.
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long key) {
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  const unsigned mhi = __reduce_max_sync(kFull, hi);
+  const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
+  return ((unsigned long long)mhi << 32) | mlo;
+}
+
+// Scales each of the rows [0, r) of M to unit 2-norm over its columns
+// [0, ncoef), applying the factor to the columns [0, nscale); rows of zero
+// norm are left as they are.  Ends with a team barrier.
+static __device__ void wscale_rows(double *M, int ld, int r, int ncoef, int nscale) {
+  const int lane = team_rank() & 31, wid = team_rank() >> 5;
+  const HHLayout L = hh_layout(r, max(ncoef, 1));
+  const int pw0 = wid * L.cw, pw1 = min(pw0 + L.cw, r);
+  if (L.S > 1) {
+    const int i = pw0 + L.lc;
+    const bool on = L.lc < L.cw && i < pw1;
+    double acc = 0.0;
+    if (on)
+      for (int j = L.sg; j < ncoef; j += L.S) acc = fma(M[i * ld + j], M[i * ld + j], acc);
+    acc = seg_sum(acc, L.sg, L.S);
+    const double ss = __shfl_sync(kFull, acc, lane - L.sg);
+    if (on && ss > 0.0) {
+      const double inv = rsqrt(ss);
+      for (int j = L.sg; j < nscale; j += L.S) M[i * ld + j] *= inv;
+    }
+  } else {
+    for (int i = pw0 + lane; i < pw1; i += 32) {
+      double ss = 0.0;
+      for (int j = 0; j < ncoef; j++) ss = fma(M[i * ld + j], M[i * ld + j], ss);
+      if (ss > 0.0) {
+        const double inv = rsqrt(ss);
+        for (int j = 0; j < nscale; j++) M[i * ld + j] *= inv;
+      }
+    }
+  }
+  tsync();
+}
+
+// Largest squared 2-norm over the rows [r0, r1) of the columns j in [0, nc)
+// with skip[j] == 0 (skip may be null), and, for offc >= 0, the largest
+// |M[i][offc]| over the same rows (0 otherwise).  One team barrier; the key
+// buffers are reused by the next call, so calls must be separated by at
+// least one other barrier.
+static __device__ void wcol_max(const double *M, int ld, int r0, int r1, int nc, const int *skip, int offc,
+                                double &nu2, double &om) {
+  const int tid = team_rank(), lane = tid & 31, wid = tid >> 5;
+  const HHLayout L = hh_layout(nc, max(r1 - r0, 1));
+  const int pw0 = wid * L.cw, pw1 = min(pw0 + L.cw, nc);
+  unsigned long long kn = 0ull, ko = 0ull;
+  if (L.S > 1) {
+    const int j = pw0 + L.lc;
+    const bool on = L.lc < L.cw && j < pw1 && !(skip && skip[j]);
+    double acc = 0.0;
+    if (on)
+      for (int i = r0 + L.sg; i < r1; i += L.S) acc = fma(M[i * ld + j], M[i * ld + j], acc);
+    acc = seg_sum(acc, L.sg, L.S);
+    if (on && L.sg == 0) kn = dkey(acc);
+  } else {
+    for (int j = pw0 + lane; j < pw1; j += 32) {
+      if (skip && skip[j]) continue;
+      double acc = 0.0;
+      for (int i = r0; i < r1; i++) acc = fma(M[i * ld + j], M[i * ld + j], acc);
+      if (dkey(acc) > kn) kn = dkey(acc);
+    }
+  }
+  if (offc >= 0)
+    for (int i = r0 + tid; i < r1; i += TEAM) {
+      const unsigned long long k = dkey(fabs(M[i * ld + offc]));
+      if (k > ko) ko = k;
+    }
+  kn = warp_max_key(kn);
+  ko = warp_max_key(ko);
+  unsigned long long *keys = colmax_keys();
+  if (lane == 0) { keys[wid] = kn; keys[32 + wid] = ko; }
+  tsync();
+  kn = keys[0];
+  ko = keys[32];
+  for (int q = 1; q < (int)(blockDim.x >> 5); q++) {
+    kn = max(kn, keys[q]);
+    ko = max(ko, keys[32 + q]);
+  }
+  nu2 = __longlong_as_double((long long)kn);
+  om = __longlong_as_double((long long)ko);
+}
+
+// out[a][0 : nk] = the row's columns [c0, c0 + nk) and out[a][nk] = its column
+// offc, both divided by the 2-norm of the first part (0 for a zero row), for
+// the rows r0 + a, a in [0, cnt).  Ends with a team barrier.
+static __device__ void wnorm_rows_out(const double *M, int ld, int r0, int cnt, int c0, int nk, int offc,
+                                      double *out, int ldo) {
+  const int lane = team_rank() & 31, wid = team_rank() >> 5;
+  const HHLayout L = hh_layout(cnt, max(nk, 1));
+  const int pw0 = wid * L.cw, pw1 = min(pw0 + L.cw, cnt);
+  if (L.S > 1) {
+    const int a = pw0 + L.lc;
+    const bool on = L.lc < L.cw && a < pw1;
+    const double *row = M + (size_t)(r0 + (on ? a : 0)) * ld;
+    double acc = 0.0;
+    if (on)
+      for (int j = L.sg; j < nk; j += L.S) acc = fma(row[c0 + j], row[c0 + j], acc);
+    acc = seg_sum(acc, L.sg, L.S);
+    const double ss = __shfl_sync(kFull, acc, lane - L.sg);
+    if (on) {
+      const double inv = (ss > 0.0) ? rsqrt(ss) : 0.0;
+      for (int j = L.sg; j < nk; j += L.S) out[a * ldo + j] = row[c0 + j] * inv;
+      if (L.sg == 0) out[a * ldo + nk] = row[offc] * inv;
+    }
+  } else {
+    for (int a = pw0 + lane; a < pw1; a += 32) {
+      const double *row = M + (size_t)(r0 + a) * ld;
+      double ss = 0.0;
+      for (int j = 0; j < nk; j++) ss = fma(row[c0 + j], row[c0 + j], ss);
+      const double inv = (ss > 0.0) ? rsqrt(ss) : 0.0;
+      for (int j = 0; j < nk; j++) out[a * ldo + j] = row[c0 + j] * inv;
+      out[a * ldo + nk] = row[offc] * inv;
+    }
+  }
+  tsync();
+}
+
 // ---------------------------------------------------------------------------
 // Lemma 1 by ordered column-pivoted Householder row reduction.
 //
@@ -778,39 +912,13 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
   res.k0 = 0;
   res.inconsistent = 0;
 
-  // row scaling
-  for (int i = tid; i < r; i += TEAM) {
-    double s0 = 0.0, s1 = 0.0;
-    int j = 0;
-    for (; j + 1 < ncoef; j += 2) {
-      double a = M[i * ld + j], b = M[i * ld + j + 1];
-      s0 = fma(a, a, s0);
-      s1 = fma(b, b, s1);
-    }
-    if (j < ncoef) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
-    double s = s0 + s1;
-    if (s > 0.0) {
-      double inv = 1.0 / sqrt(s);
-      for (j = 0; j < nc; j++) M[i * ld + j] *= inv;
-    }
-  }
+  // row scaling, then nu (largest column norm) and the offset scale omega
+  wscale_rows(M, ld, r, ncoef, nc);
   for (int j = tid; j < nc; j += TEAM) done[j] = 0;
-  tsync();
-  // nu and omega
-  double nu = 0.0, om = 0.0;
-  for (int j = tid; j < ncoef; j += TEAM) {
-    double s0 = 0.0, s1 = 0.0;
-    int i = 0;
-    for (; i + 1 < r; i += 2) {
-      s0 = fma(M[i * ld + j], M[i * ld + j], s0);
-      s1 = fma(M[(i + 1) * ld + j], M[(i + 1) * ld + j], s1);
-    }
-    if (i < r) s0 = fma(M[i * ld + j], M[i * ld + j], s0);
-    nu = fmax(nu, s0 + s1);
-  }
-  for (int i = tid; i < r; i += TEAM) om = fmax(om, fabs(M[i * ld + off]));
-  nu = sqrt(team_max(nu));
-  om = fmax(1.0, team_max(om));
+  double nu2, om;
+  wcol_max(M, ld, 0, r, ncoef, nullptr, off, nu2, om);
+  const double nu = sqrt(nu2);
+  om = fmax(1.0, om);
   const double thr = tau_rank * nu;
 
   int k = 0, c0 = 0;
@@ -826,17 +934,7 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
   for (int i = k + tid; i < r; i += TEAM)
     if (fabs(M[i * ld + off]) > tau_inc * om) bad = 1;
   res.inconsistent = __syncthreads_or(bad);
-  if (out) {
-    const int kc0 = ncoef - nkeep;
-    for (int a = tid; a < res.krank; a += TEAM) {
-      const double *row = M + (res.k0 + a) * ld;
-      double s = 0.0;
-      for (int j = 0; j < nkeep; j++) s = fma(row[kc0 + j], row[kc0 + j], s);
-      double inv = 1.0 / sqrt(s);
-      for (int j = 0; j < nkeep; j++) out[a * ldo + j] = row[kc0 + j] * inv;
-      out[a * ldo + nkeep] = row[off] * inv;
-    }
-  }
+  if (out) wnorm_rows_out(M, ld, res.k0, res.krank, ncoef - nkeep, nkeep, off, out, ldo);
   tsync();
   return res;
 }
@@ -1122,50 +1220,41 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
   LseResult res;
   res.k1 = res.k2 = res.kc = res.kq = res.inconsistent = 0;
   // scale constraint rows to unit coefficient norm
-  for (int i = tid; i < rc; i += TEAM) {
-    double s = 0.0;
-    for (int j = 0; j < off; j++) s = fma(M[i * ld + j], M[i * ld + j], s);
-    if (s > 0.0) {
-      double inv = 1.0 / sqrt(s);
-      for (int j = 0; j < nc; j++) M[i * ld + j] *= inv;
-    }
-  }
+  wscale_rows(M, ld, rc, off, nc);
   for (int j = tid; j < nc; j += TEAM) done[j] = 0;
-  tsync();
-  double nu = 0.0, om = 0.0;
-  for (int j = tid; j < off; j += TEAM) {
-    double s = 0.0;
-    for (int i = 0; i < rc; i++) s = fma(M[i * ld + j], M[i * ld + j], s);
-    nu = fmax(nu, s);
-  }
-  for (int i = tid; i < rc; i += TEAM) om = fmax(om, fabs(M[i * ld + off]));
-  nu = sqrt(team_max(nu));
-  om = fmax(1.0, team_max(om));
+  double nu2, om;
+  wcol_max(M, ld, 0, rc, off, nullptr, off, nu2, om);
+  const double nu = sqrt(nu2);
+  om = fmax(1.0, om);
   const double thr = tau_rank * nu;
   // A
   res.k1 = hh_pivoted(M, ld, 0, rc, 0, ne, 0, nc, done, pc, thr, v, w);
-  // B
-  for (int p = 0; p < res.k1; p++) {
-    const int col = pc[p];
-    const double inv = 1.0 / M[p * ld + col];
-    for (int q = tid; q < rq; q += TEAM) w[q] = M[(rc + q) * ld + col] * inv;
+  // B: the reciprocal pivots up front; the thread that updates a cost row's
+  // next pivot entry also forms that row's next multiplier (two buffers), so
+  // each pivot costs one barrier
+  if (res.k1 > 0) {
+    double *pinv = v, *wb[2] = {w, v + res.k1};  // k1 + rq <= r doubles of v
+    for (int p = tid; p < res.k1; p += TEAM) pinv[p] = 1.0 / M[p * ld + pc[p]];
     tsync();
-    for (int idx = tid; idx < rq * nc; idx += TEAM) {
-      int q = idx / nc, j = idx - q * nc;
-      double val = (j == col) ? 0.0 : fma(-w[q], M[p * ld + j], M[(rc + q) * ld + j]);
-      M[(rc + q) * ld + j] = val;
+    for (int q = tid; q < rq; q += TEAM) wb[0][q] = M[(rc + q) * ld + pc[0]] * pinv[0];
+    tsync();
+    for (int p = 0; p < res.k1; p++) {
+      const int col = pc[p], coln = (p + 1 < res.k1) ? pc[p + 1] : -1;
+      const double *wc = wb[p & 1];
+      double *wn = wb[(p + 1) & 1];
+      for (int idx = tid; idx < rq * nc; idx += TEAM) {
+        const int q = idx / nc, j = idx - q * nc;
+        const double val = (j == col) ? 0.0 : fma(-wc[q], M[p * ld + j], M[(rc + q) * ld + j]);
+        M[(rc + q) * ld + j] = val;
+        if (j == coln) wn[q] = val * pinv[p + 1];
+      }
+      tsync();
     }
-    tsync();
   }
   // C
-  double nuq = 0.0;
-  for (int j = tid; j < ne; j += TEAM) {
-    if (done[j]) continue;
-    double s = 0.0;
-    for (int i = rc; i < r; i++) s = fma(M[i * ld + j], M[i * ld + j], s);
-    nuq = fmax(nuq, s);
-  }
-  nuq = sqrt(team_max(nuq));
+  double nuq2, om_unused;
+  wcol_max(M, ld, rc, r, ne, done, -1, nuq2, om_unused);
+  const double nuq = sqrt(nuq2);
   res.k2 = hh_pivoted(M, ld, rc, r, 0, ne, 0, nc, done, nullptr, tau_rank * nuq, v, w);
   const int kk = rc + res.k2;
   // D
@@ -1175,15 +1264,7 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
   for (int i = kd + tid; i < rc; i += TEAM)
     if (fabs(M[i * ld + off]) > tau_inc * om) bad = 1;
   res.inconsistent = __syncthreads_or(bad);
-  for (int a = tid; a < res.kc; a += TEAM) {
-    const double *row = M + (res.k1 + a) * ld;
-    double s = 0.0;
-    for (int j = 0; j < nk; j++) s = fma(row[ne + j], row[ne + j], s);
-    double inv = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-    for (int j = 0; j < nk; j++) outC[a * ldo + j] = row[ne + j] * inv;
-    outC[a * ldo + nk] = row[off] * inv;
-  }
-  tsync();
+  wnorm_rows_out(M, ld, res.k1, res.kc, ne, nk, off, outC, ldo);
   // E: compress the remaining cost rows over the kept columns (no pivoting)
   int ke = kk;
   ke = hh_diag_steps(M, ld, ke, r, ne, off, nc, v, w, 0.0, false);
