@@ -639,12 +639,15 @@ static __device__ double hh_range_step(double *M, int ld, int k, int r, int piv,
     }
   }
   tsync();
-  const double nrm = sqrt(d[piv]);
-  if (!(nrm > thr)) return 0.0;
-  const double xk = v[k];
-  const double sg = xk >= 0.0 ? 1.0 : -1.0;
-  const double shift = sg * nrm;
-  const double beta = 1.0 / (nrm * (nrm + fabs(xk)));
+  const double dp = d[piv], xk = v[k];
+  double nrm, shift, vk, beta;
+  if (!hh_reflector(dp, xk, nrm, shift, vk, beta)) {
+    nrm = sqrt(dp);
+    shift = ((__double_as_longlong(xk) < 0) && ((__double_as_longlong(xk) << 1) != 0)) ? -nrm : nrm;
+    vk = xk + shift;
+    beta = 1.0 / (nrm * (nrm + fabs(xk)));
+  }
+  if (!(dp > 0.0) || !(nrm > thr)) return 0.0;
   for (int jj = jj0; jj < nc && (S == 1 || jj == jj0); jj += T) {
     const int j = a0 + jj;
     if (j == piv) {
@@ -655,7 +658,7 @@ static __device__ double hh_range_step(double *M, int ld, int k, int r, int piv,
     if (done[j]) continue;
     const double wj = beta * fma(shift, mk[jj], d[j]);
     for (int i = k + sgm; i < r; i += S) {
-      const double vi = (i == k) ? xk + shift : v[i];
+      const double vi = (i == k) ? vk : v[i];
       M[i * ld + j] = fma(-wj, vi, M[i * ld + j]);
     }
   }
@@ -703,8 +706,9 @@ static __device__ int hh_pivoted_range(double *M, int ld, int k, int r, int cand
   warp_argmax_key(mybest < 0.0 ? 0ull : dkey(mybest), mybest < 0.0 ? 0x7fffffff : mypiv, 0);
   tsync();
   argmax_finish(0, b2, piv);
+  const double stop2 = thr * thr * (1.0 - 0x1p-16);  // see hh_pivoted_list
   int steps = 0;
-  while (k < r && piv != 0x7fffffff) {
+  while (k < r && piv != 0x7fffffff && !(b2 < stop2)) {
     const double nrm = hh_range_step(M, ld, k, r, piv, app0, app1, done, v, w, thr, cn, cref, cand0, cand1,
                                      (steps + 1) & 1);
     if (nrm == 0.0) break;
