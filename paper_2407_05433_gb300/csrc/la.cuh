@@ -686,24 +686,46 @@ static __device__ double hh_range_step(double *M, int ld, int k, int r, int piv,
 // Range form of the column-pivoted steps (same contract as hh_pivoted_list):
 // the passes cover every column of [app0, app1), done ones idle, with
 // power-of-two row segments; the next pivot's candidates are downdated in
-// the update pass and the first norms are evaluated one column per thread.
+// the update pass.
 static __device__ int hh_pivoted_range(double *M, int ld, int k, int r, int cand0, int cand1, int app0,
                                        int app1, int *done, int *pc, double thr, double *v, double *w) {
-  const int tid = team_rank(), T = TEAM;
+  const int tid = team_rank(), lane = tid & 31, wid = tid >> 5;
   double *cn = hh_norms(), *cref = cn + kMaxCols;
-  double mybest = -1.0;
-  int mypiv = 0x7fffffff;
-  for (int j = cand0 + tid; j < cand1; j += T) {
-    double acc = 0.0;
-    if (!done[j])
-      for (int i = k; i < r; i++) acc = fma(M[i * ld + j], M[i * ld + j], acc);
-    cn[j] = acc;
-    cref[j] = acc;
-    if (!done[j] && acc > mybest) { mybest = acc; mypiv = j; }
+  // exact squared norms of the candidates over rows [k, r), on the balanced layout
+  unsigned long long bkey = 0ull;
+  int bidx = 0x7fffffff;
+  {
+    const int nc = cand1 - cand0;
+    const HHLayout C = hh_layout(nc, max(r - k, 1));
+    const int pw0 = wid * C.cw, pw1 = min(pw0 + C.cw, nc);
+    if (C.S > 1) {
+      const int j = cand0 + pw0 + C.lc;
+      const bool on = C.lc < C.cw && pw0 + C.lc < pw1 && !done[j];
+      double acc = 0.0;
+      if (on)
+        for (int i = k + C.sg; i < r; i += C.S) acc = fma(M[i * ld + j], M[i * ld + j], acc);
+      acc = seg_sum(acc, C.sg, C.S);
+      if (on && C.sg == 0) {
+        cn[j] = acc;
+        cref[j] = acc;
+        bkey = dkey(acc);
+        bidx = j;
+      }
+    } else {
+      for (int p = pw0 + lane; p < pw1; p += 32) {
+        const int j = cand0 + p;
+        if (done[j]) continue;
+        double acc = 0.0;
+        for (int i = k; i < r; i++) acc = fma(M[i * ld + j], M[i * ld + j], acc);
+        cn[j] = acc;
+        cref[j] = acc;
+        if (bidx == 0x7fffffff || dkey(acc) > bkey) { bkey = dkey(acc); bidx = j; }
+      }
+    }
   }
   double b2;
   int piv;
-  warp_argmax_key(mybest < 0.0 ? 0ull : dkey(mybest), mybest < 0.0 ? 0x7fffffff : mypiv, 0);
+  warp_argmax_key(bkey, bidx, 0);
   tsync();
   argmax_finish(0, b2, piv);
   const double stop2 = thr * thr * (1.0 - 0x1p-16);  // see hh_pivoted_list
