@@ -122,6 +122,17 @@ def test_degenerate_n12_full():
     check(pb, r, d)
 
 
+@pytest.mark.parametrize("chunk,refine", [(6, 4), (12, 6), (16, 4), (32, 2)])
+def test_degenerate_n12_full_other_chunk_lengths(chunk, refine):
+    """The full degenerate instance with chunk lengths other than the automatic 8.  Where a boundary
+    falls next to an ill-conditioned stage the refinement needs more than the default two passes
+    (the residual after two passes is not monotone in the chunk length); with the passes given here
+    every length meets the parity bar and the gate."""
+    pb = synth.config("degenerate_n12")
+    (r,), (d,) = gpu_run([pb], chunk=chunk, refine=refine)
+    check(pb, r, d)
+
+
 def test_table1_n1024():
     pb = synth.config("table1", N=1024)
     (r,), (d,) = gpu_run([pb])
