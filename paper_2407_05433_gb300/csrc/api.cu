@@ -440,7 +440,8 @@ int aff_scan(eclqr_handle *h, GroupHost &gh, int mode, cudaStream_t st) {
   const int fwd = (mode == AFF_PLIN_) ? 0 : 1;
   TRY(launch(h, k_aff_up, g.nslot, sa, st, g, mode, sa));
   int src = 0;
-  for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_aff_level, g.nslot, sa, st, g, src, 1 << k, fwd, sa));
+  // radix-4 levels: strides 1, 4, 16, ... until they cover every slot
+  for (int d = 1; d < gh.maxnch + 1; d *= 4, src ^= 1) TRY(launch(h, k_aff_level, g.nslot, sa, st, g, src, d, fwd, sa));
   TRY(launch(h, k_aff_down, g.nslot, sa, st, g, mode, src, sa));
   return ECLQR_OK;
 }

@@ -478,54 +478,72 @@ __global__ void k_aff_up(Group g, int mode, int per_task) {
   }
 }
 
-// slot t <- slot t o slot t' (t' = t - d forward, t + d backward) inside one problem.
+// One level of a radix-4 Kogge-Stone scan over the chunk slots of an affine
+// chain.  Before the level with stride d every slot holds the composition of
+// the d slots ending at it; it composes that with the slots at distances d,
+// 2d and 3d in the scan direction (each holding the d slots before the
+// previous one), so after the levels d = 1, 4, 16, ... every slot holds its
+// inclusive prefix.  A value (a boundary vector, CI_ROWS == 1) ends the
+// composition.  The four-way level halves the launches of a radix-2 scan;
+// the chain elements are small (n x n), so the level is launch-bound.
 __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task) {
   const int t = team_task();
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
-  const int n = g.n, tid = team_rank();
+  const int n = g.n, tid = team_rank(), sz = n * n + n;
   const int j = t - P.ch0;  // slot index 0..nch
-  const double *S1 = g.CS[src] + (size_t)t * g.cs_stride;
+  const double *S0 = g.CS[src] + (size_t)t * g.cs_stride;
   const int *I1 = g.CI[src] + (size_t)t * CI_STRIDE;
   double *Dst = g.CS[src ^ 1] + (size_t)t * g.cs_stride;
   int *J = g.CI[src ^ 1] + (size_t)t * CI_STRIDE;
-  const int na = I1[CI_NA], nb = I1[CI_NB];
-  const bool value1 = I1[CI_ROWS] == 1;
-  const int j2 = fwd ? j - d : j + d;
-  if (value1 || j2 < 0 || j2 > P.nch) {
-    for (int idx = tid; idx < n * n + n; idx += TEAM) Dst[idx] = S1[idx];
-    if (tid == 0) { J[CI_ROWS] = I1[CI_ROWS]; J[CI_NA] = na; J[CI_NB] = nb; }
-    return;
-  }
-  const int t2 = P.ch0 + j2;
-  const double *S2 = g.CS[src] + (size_t)t2 * g.cs_stride;
-  const int *I2 = g.CI[src] + (size_t)t2 * CI_STRIDE;
+  int rows = I1[CI_ROWS], na = I1[CI_NA], nb = I1[CI_NB];
   double *sm = team_smem(per_task);
-  double *Tm = sm, *tv = Tm + n * n;
-  if (I2[CI_ROWS] == 1) {
-    // value: y = G1 v + g1
-    const int dv = I2[CI_NA];
-    for (int r = tid; r < nb; r += TEAM) {
-      double s0 = S1[n * n + r];
-      for (int l = 0; l < dv; l++) s0 = fma(S1[r * n + l], S2[n * n + l], s0);
-      Dst[n * n + r] = s0;
-    }
-    if (tid == 0) { J[CI_ROWS] = 1; J[CI_NA] = nb; J[CI_NB] = 0; }
-    return;
-  }
-  const int na2 = I2[CI_NA];
-  // (G1 G2, G1 g2 + g1): input dim na2, output nb
-  wgemm<false, false>(nb, na2, na, 1.0, S1, n, S2, n, 0.0, Tm, n);
-  for (int r = tid; r < nb; r += TEAM) {
-    double s0 = S1[n * n + r];
-    for (int l = 0; l < na; l++) s0 = fma(S1[r * n + l], S2[n * n + l], s0);
-    tv[r] = s0;
-  }
+  double *acc = sm, *oth = acc + sz, *Tm = oth + sz, *tv = Tm + n * n;
+  for (int idx = tid; idx < sz; idx += TEAM) acc[idx] = S0[idx];
   tsync();
-  for (int idx = tid; idx < n * n; idx += TEAM) Dst[idx] = Tm[idx];
-  for (int r = tid; r < n; r += TEAM) Dst[n * n + r] = tv[r];
-  if (tid == 0) { J[CI_ROWS] = 0; J[CI_NA] = na2; J[CI_NB] = nb; }
+  for (int q = 1; q <= 3 && rows != 1; q++) {
+    const int j2 = fwd ? j - q * d : j + q * d;
+    if (j2 < 0 || j2 > P.nch) break;
+    const int t2 = P.ch0 + j2;
+    const double *S2 = g.CS[src] + (size_t)t2 * g.cs_stride;
+    const int *I2 = g.CI[src] + (size_t)t2 * CI_STRIDE;
+    const int rows2 = I2[CI_ROWS], na2 = I2[CI_NA];
+    for (int idx = tid; idx < sz; idx += TEAM) oth[idx] = S2[idx];
+    tsync();
+    if (rows2 == 1) {
+      // value: y = G v + g, dimension nb
+      for (int r = tid; r < nb; r += TEAM) {
+        double s0 = acc[n * n + r];
+        for (int l = 0; l < na2; l++) s0 = fma(acc[r * n + l], oth[n * n + l], s0);
+        tv[r] = s0;
+      }
+      tsync();
+      for (int r = tid; r < nb; r += TEAM) acc[n * n + r] = tv[r];
+      rows = 1;
+      na = nb;
+      nb = 0;
+    } else {
+      // (G G2, G g2 + g): input dimension na2, output nb
+      wgemm<false, false>(nb, na2, na, 1.0, acc, n, oth, n, 0.0, Tm, n);
+      for (int r = tid; r < nb; r += TEAM) {
+        double s0 = acc[n * n + r];
+        for (int l = 0; l < na; l++) s0 = fma(acc[r * n + l], oth[n * n + l], s0);
+        tv[r] = s0;
+      }
+      tsync();
+      for (int idx = tid; idx < nb * na2; idx += TEAM) {
+        const int r = idx / na2, c = idx - r * na2;
+        acc[r * n + c] = Tm[r * n + c];
+      }
+      for (int r = tid; r < nb; r += TEAM) acc[n * n + r] = tv[r];
+      rows = 0;
+      na = na2;
+    }
+    tsync();
+  }
+  for (int idx = tid; idx < sz; idx += TEAM) Dst[idx] = acc[idx];
+  if (tid == 0) { J[CI_ROWS] = rows; J[CI_NA] = na; J[CI_NB] = nb; }
 }
 
 __global__ void k_aff_down(Group g, int mode, int fin, int per_task) {
