@@ -449,7 +449,9 @@ __global__ void k_elim(Group g, int per_task) {
   }
   tsync();
   // Lemma 4: Z = null(Gamma), [Y | y] = -Gamma^- [Phi | gamma] (min norm)
-  const int rank = wtqr(Gm, m, rows, m, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qm, m, perm, scr);
+  // the small form only: this kernel runs many CTAs to an SM, and the large form's
+  // registers and static scratch would cost it occupancy
+  const int rank = wtqr_small(Gm, m, rows, m, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qm, m, perm, scr);
   const double rs = wtqr_solve(Wt, (rows > 0 ? rows : 1), Qm, m, perm, rows, m, rank, Rh, nb + 1, nb + 1,
                                Sol, nb + 1, X1, nb + 1);
   if (tid == 0 && rs > g.tau_inc) set_status(g, S.prob, ST_RANK_INCONSISTENT);

@@ -374,7 +374,8 @@ __device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned 
 // column piv becomes (-sign(x_k) ||M_piv||, 0, ..., 0), and the norm is
 // returned.  L is then replaced by the layout of the next step (cnt - 1
 // columns on rows [k + 1, r)), computed in the shadow of the FP64 latency.
-// Scratch: v (rows), d (columns).
+// Scratch: v (rows), d (columns).  With refl given, (v_k, beta) go to
+// refl[0..1], so that v (with v[k] replaced by v_k) and beta describe H.
 //
 // Column pivoting (cn given): the update pass also downdates the remaining
 // squared norms cn of the candidate columns in [cand0, cand1) (LAPACK
@@ -385,7 +386,7 @@ __device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned 
 static __device__ double hh_core(double *M, int ld, int k, int r, int piv, const short *list, int a0, int cnt,
                                  HHLayout &L, double *v, double *d, double thr, int *done = nullptr,
                                  short *next = nullptr, double *cn = nullptr, double *crs = nullptr,
-                                 int cand0 = 0, int cand1 = 0, int parity = 0) {
+                                 int cand0 = 0, int cand1 = 0, int parity = 0, double *refl = nullptr) {
   const int tid = team_rank(), T = TEAM, wid = tid >> 5;
   double *mk = hh_rowk();
   const int S = L.S, sg = L.sg;
@@ -428,6 +429,7 @@ static __device__ double hh_core(double *M, int ld, int k, int r, int piv, const
   }
   if (!(dp > 0.0) || !(nrm > thr)) return 0.0;
   L = Ln;
+  if (refl && tid == 0) { refl[0] = vk; refl[1] = beta; }  // visible after the closing barrier
   // update pass (and, when pivoting, the norm downdate and the warp's arg-max)
   unsigned long long bkey = 0ull;
   int bidx = 0x7fffffff;
@@ -496,9 +498,10 @@ static __device__ double hh_core(double *M, int ld, int k, int r, int piv, const
 
 // One Householder step applied to the columns [a0, a1) (piv among them).
 static __device__ __forceinline__ double hh_step(double *M, int ld, int k, int r, int piv, int a0, int a1,
-                                                 double *v, double *d, double thr) {
+                                                 double *v, double *d, double thr, double *refl = nullptr) {
   HHLayout L = hh_layout(a1 - a0, r - k);
-  return hh_core(M, ld, k, r, piv, nullptr, a0, a1 - a0, L, v, d, thr);
+  return hh_core(M, ld, k, r, piv, nullptr, a0, a1 - a0, L, v, d, thr, nullptr, nullptr, nullptr, nullptr, 0, 0,
+                 0, refl);
 }
 
 // Unpivoted steps down the diagonal: for col = c0, c0 + 1, ... < c1 while the
@@ -973,7 +976,7 @@ static __device__ ProjResult wproject(double *M, int ld, int r, int ng, const in
 // formed explicitly: its first `rank` columns span range(K^T), the last
 // nk - rank are an orthonormal basis of null(K).  perm: rk ints.
 // ---------------------------------------------------------------------------
-static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_rank, double *W, int ldw,
+static __device__ int wtqr_small(const double *K, int ldk, int rk, int nk, double tau_rank, double *W, int ldw,
                     double *Q, int ldq, int *perm, double *scr /* >= nk + max(nk, rk) */) {
   const int tid = team_rank(), T = TEAM;
   double *v = scr, *w = scr + nk;
@@ -1054,6 +1057,110 @@ static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_
   return rank;
 }
 
+static __device__ int wtqr_large(const double *K, int ldk, int rk, int nk, double tau_rank, double *W, int ldw,
+                    double *Q, int ldq, int *perm, double *scr /* >= nk + max(nk, rk) + 2 */) {
+  const int tid = team_rank(), T = TEAM, lane = tid & 31, wid = tid >> 5;
+  double *v = scr, *w = scr + nk, *refl = w + (nk > rk ? nk : rk);
+  for (int idx = tid; idx < nk * rk; idx += T) {
+    int i = idx / rk, j = idx - i * rk;
+    W[i * ldw + j] = K[j * ldk + i];
+  }
+  for (int idx = tid; idx < nk * nk; idx += T) {
+    int i = idx / nk, j = idx - i * nk;
+    Q[i * ldq + j] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int j = tid; j < rk; j += T) perm[j] = j;
+  tsync();
+  double nu2, unused;
+  wcol_max(W, ldw, 0, nk, rk, nullptr, -1, nu2, unused);
+  const double thr = tau_rank * sqrt(nu2);
+  int rank = 0;
+  for (int s = 0; s < rk && s < nk; s++) {
+    // exact remaining norms of the columns [s, rk) over rows [s, nk), balanced layout
+    unsigned long long bkey = 0ull;
+    int bidx = 0x7fffffff;
+    {
+      const HHLayout C = hh_layout(rk - s, nk - s);
+      const int pw0 = wid * C.cw, pw1 = min(pw0 + C.cw, rk - s);
+      if (C.S > 1) {
+        const int p = pw0 + C.lc, j = s + p;
+        const bool on = C.lc < C.cw && p < pw1;
+        double acc = 0.0;
+        if (on)
+          for (int i = s + C.sg; i < nk; i += C.S) acc = fma(W[i * ldw + j], W[i * ldw + j], acc);
+        acc = seg_sum(acc, C.sg, C.S);
+        if (on && C.sg == 0) { bkey = dkey(acc); bidx = j; }
+      } else {
+        for (int p = pw0 + lane; p < pw1; p += 32) {
+          const int j = s + p;
+          double acc = 0.0;
+          for (int i = s; i < nk; i++) acc = fma(W[i * ldw + j], W[i * ldw + j], acc);
+          if (bidx == 0x7fffffff || dkey(acc) > bkey) { bkey = dkey(acc); bidx = j; }
+        }
+      }
+    }
+    warp_argmax_key(bkey, bidx, s & 1);
+    tsync();
+    double b2;
+    int piv;
+    argmax_finish(s & 1, b2, piv);
+    if (piv == 0x7fffffff || !(sqrt(b2) > thr)) break;
+    if (piv != s) {
+      for (int i = tid; i < nk; i += T) {
+        const double t = W[i * ldw + s];
+        W[i * ldw + s] = W[i * ldw + piv];
+        W[i * ldw + piv] = t;
+      }
+      if (tid == 0) {
+        const int t = perm[s]; perm[s] = perm[piv]; perm[piv] = t;
+      }
+      tsync();
+    }
+    // W columns [s, rk): reflector of column s (v keeps it, refl = (v_s, beta))
+    if (!(hh_step(W, ldw, s, nk, s, s, rk, v, w, 0.0, refl) > 0.0)) break;
+    // Q <- Q H on columns [s, nk): each row of Q on one segment group of a warp
+    {
+      const double vs = refl[0], beta = refl[1];
+      const HHLayout R = hh_layout(nk, nk - s);
+      const int pw0 = wid * R.cw, pw1 = min(pw0 + R.cw, nk);
+      if (R.S > 1) {
+        const int i = pw0 + R.lc;
+        const bool on = R.lc < R.cw && i < pw1;
+        double acc = 0.0;
+        if (on)
+          for (int l = s + R.sg; l < nk; l += R.S) acc = fma(Q[i * ldq + l], (l == s) ? vs : v[l], acc);
+        acc = seg_sum(acc, R.sg, R.S);
+        const double ti = beta * __shfl_sync(kFull, acc, lane - R.sg);
+        if (on)
+          for (int l = s + R.sg; l < nk; l += R.S) Q[i * ldq + l] = fma(-ti, (l == s) ? vs : v[l], Q[i * ldq + l]);
+      } else {
+        for (int i = pw0 + lane; i < pw1; i += 32) {
+          double acc = 0.0;
+          for (int l = s; l < nk; l++) acc = fma(Q[i * ldq + l], (l == s) ? vs : v[l], acc);
+          const double ti = beta * acc;
+          for (int l = s; l < nk; l++) Q[i * ldq + l] = fma(-ti, (l == s) ? vs : v[l], Q[i * ldq + l]);
+        }
+      }
+    }
+    rank++;
+  }
+  tsync();
+  return rank;
+}
+
+// Two forms with the same result contract.  wtqr_small (below 8 rows of
+// W): one thread per column for the norms and the classic reflector
+// application, little fixed cost per step, for the many small per-stage
+// factorizations that run several CTAs to an SM.  wtqr_large: norms on the
+// balanced layout, the one-barrier arg-max, the fused Householder step with
+// seeded scalars, and a warp-local update of Q, for the factorizations on
+// the critical path of the sweeps.
+static __device__ int wtqr(const double *K, int ldk, int rk, int nk, double tau_rank, double *W, int ldw,
+                    double *Q, int ldq, int *perm, double *scr /* >= nk + max(nk, rk) + 2 */) {
+  if (nk < 8) return wtqr_small(K, ldk, rk, nk, tau_rank, W, ldw, Q, ldq, perm, scr);
+  return wtqr_large(K, ldk, rk, nk, tau_rank, W, ldw, Q, ldq, perm, scr);
+}
+
 // After wtqr: X (nk x nb, ldx) = -Q1 R11^{-T} (Pi^T B)_1 for B (rk x nb, ldb),
 // the min-norm solutions of K X = -B.  Returns the largest residual of the
 // dependent rows relative to max(1, |B|_max) (a consistency check).
@@ -1068,12 +1175,17 @@ static __device__ double wtqr_solve(const double *W, int ldw, const double *Q, i
     bmax = fmax(bmax, fabs(B[i * ldb + j]));
   }
   bmax = fmax(1.0, team_max(bmax));
+  // reciprocals of R's diagonal (into X's first column, rewritten below), so that the
+  // substitution chains carry multiplies instead of divides
+  double *rdiag = X;
+  for (int i = tid; i < rank; i += TEAM) rdiag[i * ldx] = 1.0 / W[i * ldw + i];
+  tsync();
   double rmax = 0.0;
   for (int c = tid; c < nb; c += TEAM) {
     for (int i = 0; i < rank; i++) {
       double s = B[perm[i] * ldb + c];
       for (int l = 0; l < i; l++) s = fma(-W[l * ldw + i], Y[l * ldy + c], s);
-      Y[i * ldy + c] = s / W[i * ldw + i];
+      Y[i * ldy + c] = s * rdiag[i * ldx];
     }
     for (int j = rank; j < rk; j++) {
       double s = B[perm[j] * ldb + c];
