@@ -124,9 +124,11 @@ int eclqr_layout(const eclqr_desc *desc, eclqr_layout_info *out);
 /* Plans the batch and allocates the device workspace (cudaMalloc) on the
  * current device.  opt may be NULL (defaults).  Host-synchronous.  Problems
  * are grouped by (n, m); a group whose n, m, largest p_i and largest q_i need
- * more than 219 KB of shared memory in some kernel is rejected with
- * ECLQR_ESMEM before anything is allocated (n <= 28 fits for any row counts up
- * to ECLQR_MAX_ROWS; n = 32, m = 16 needs max p_i + max q_i <= 47). */
+ * more shared memory in some kernel than a CTA holds is rejected with
+ * ECLQR_ESMEM before anything is allocated: first a bound of 219 KB on the
+ * dynamic part (no device call), then each kernel's dynamic plus static
+ * shared memory against the device's per-CTA limit (n <= 28 fits for any row
+ * counts up to ECLQR_MAX_ROWS; n = 32, m = 16 needs max p_i + max q_i <= 46). */
 int eclqr_create(const eclqr_desc *desc, const eclqr_options *opt, eclqr_handle **out);
 
 /* Feasible-domain scan and stagewise elimination of Algorithm 1 (Sec. 3-5)

@@ -289,6 +289,34 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
         delete h;
         return ECLQR_ESMEM;
       }
+      // exact test: each kernel's dynamic request plus its static scratch against the
+      // device's per-CTA limit (the bound above leaves the static part out)
+      const int sw = smem_primal_sweep(n, m, pmax, qmax), sl = smem_rel_level(n, pmax, qmax), sa = smem_aff(n, m);
+      const int sdw = smem_dual_sweep(n, m, pmax, qmax);
+      const struct { const void *fn; int dyn; } kk[] = {
+          {(const void *)k_scan_check, smem_scan_check(n, m, pmax)}, {(const void *)k_terminal, sw},
+          {(const void *)k_primal_up, sw}, {(const void *)k_primal_down, sw}, {(const void *)k_rel_level, sl},
+          {(const void *)k_param, smem_param(n)}, {(const void *)k_elim, smem_elim(n, m, pmax)},
+          {(const void *)k_lqr_up, smem_lqr_up(n, m)}, {(const void *)k_lqr_level, smem_lqr_level(n)},
+          {(const void *)k_riccati_down, smem_riccati(n, m)}, {(const void *)k_aff_up, sa},
+          {(const void *)k_aff_level, sa}, {(const void *)k_aff_down, sa}, {(const void *)k_resid, 3 * n + 2 * m},
+          {(const void *)k_pcorr, n + m}, {(const void *)k_dual_stage, smem_dual_stage(n, m)},
+          {(const void *)k_dual_terminal, sdw}, {(const void *)k_dual_up, sdw}, {(const void *)k_dual_down, sdw},
+          {(const void *)k_dual_root, sdw}, {(const void *)k_dual_leaf, smem_dual_leaf(n, m, pmax, qmax)}};
+      int optin = 0;
+      int rc = (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) == cudaSuccess)
+                   ? ECLQR_OK : ECLQR_ECUDA;
+      for (const auto &k : kk) {
+        if (rc != ECLQR_OK) break;
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k.fn) != cudaSuccess) rc = ECLQR_ECUDA;
+        else if ((size_t)k.dyn * sizeof(double) + fa.sharedSizeBytes > (size_t)optin) rc = ECLQR_ESMEM;
+      }
+      if (rc != ECLQR_OK) {
+        for (auto &x : h->groups) cudaFree(x.dmem);
+        delete h;
+        return rc;
+      }
     }
     std::vector<ProbInfo> gp;
     std::vector<StageInfo> gs;

@@ -194,6 +194,23 @@ def test_maximum_dimensions():
         check(pb, r, d)
 
 
+def test_shared_memory_limit_at_the_documented_boundary():
+    """n = 32, m = 16 with max p_i + max q_i = 46 (16 mixed rows per stage, 30 terminal rows) is the
+    largest row count the header promises: every kernel's dynamic plus static shared memory fits a
+    CTA, the batch solves to parity.  One terminal row more (47) is rejected by eclqr_create with
+    ECLQR_ESMEM before anything is allocated."""
+    q = np.zeros(7, np.int32); q[6] = 30
+    pb = synth.make_problem(63, 6, 32, 16, 16, q)
+    (r,), (d,) = gpu_run([pb])
+    check(pb, r, d)
+    q47 = q.copy(); q47[6] = 31
+    pb47 = synth.make_problem(63, 6, 32, 16, 16, q47)
+    b = None
+    with pytest.raises(RuntimeError, match="shared memory"):
+        b = eclqr.Batch([pb47])
+    assert b is None
+
+
 def test_graph_replay_is_bit_identical_to_eager():
     """One pass captured into a CUDA graph replays the same kernels in the same order."""
     import torch
