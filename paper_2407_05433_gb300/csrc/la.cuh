@@ -754,7 +754,7 @@ static __device__ int hh_pivoted_range(double *M, int ld, int k, int r, int cand
 // fixed cost per factorization and per step (the list, its layout), so it is
 // taken only where its first step saves at least kListGain row FMAs per lane
 // and pass: tall, wide eliminations rather than short projections.
-constexpr int kListGain = 8;
+constexpr int kListGain = 4;
 __device__ __forceinline__ bool hh_list_pays(int nc, int nr) {
   const int T = TEAM;
   int s_range = 1;
