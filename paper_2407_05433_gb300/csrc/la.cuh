@@ -59,17 +59,6 @@ __device__ __forceinline__ double team_max(double v) {
   return r;
 }
 
-__device__ __forceinline__ double team_sum(double v) {
-  __shared__ double red_sum[32];
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) red_sum[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double r = red_sum[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); w++) r += red_sum[w];
-  __syncthreads();
-  return r;
-}
-
 __device__ __forceinline__ void team_argmax(double v, int idx, double &bv, int &bi) {
   __shared__ long long red_key[32];
   __shared__ int red_idx[32];
@@ -90,20 +79,6 @@ __device__ __forceinline__ void team_argmax(double v, int idx, double &bv, int &
   __syncthreads();
   bv = __longlong_as_double(key);
   bi = idx;
-}
-
-__device__ __forceinline__ void wzero(double *p, int n) {
-  for (int i = team_rank(); i < n; i += TEAM) p[i] = 0.0;
-  tsync();
-}
-
-__device__ __forceinline__ void wcopy(double *dst, int ldd, const double *src, int lds, int rows,
-                                      int cols) {
-  for (int idx = team_rank(); idx < rows * cols; idx += TEAM) {
-    int i = idx / cols, j = idx - i * cols;
-    dst[i * ldd + j] = src[i * lds + j];
-  }
-  tsync();
 }
 
 // C (m x n) = alpha * op(A) op(B) + beta * C; op(A) is m x k, op(B) is k x n.
@@ -1229,93 +1204,6 @@ static __device__ int wcholesky(double *Hm, int ld, int n) {
     tsync();
   }
   return fail;
-}
-
-// Solve (L L^T) X = B in place, B n x nb (ld ldb); lanes over right-hand sides.
-static __device__ void wchol_solve(const double *L, int ldl, int n, double *B, int ldb, int nb) {
-  for (int c = team_rank(); c < nb; c += TEAM) {
-    for (int i = 0; i < n; i++) {
-      double s = B[i * ldb + c];
-      for (int l = 0; l < i; l++) s = fma(-L[i * ldl + l], B[l * ldb + c], s);
-      B[i * ldb + c] = s / L[i * ldl + i];
-    }
-    for (int i = n - 1; i >= 0; i--) {
-      double s = B[i * ldb + c];
-      for (int l = i + 1; l < n; l++) s = fma(-L[l * ldl + i], B[l * ldb + c], s);
-      B[i * ldb + c] = s / L[i * ldl + i];
-    }
-  }
-  tsync();
-}
-
-// In-place LU with partial pivoting of an n x n matrix; piv: n ints.
-static __device__ void wlu(double *A, int ld, int n, int *piv) {
-  const int tid = team_rank();
-  for (int j = 0; j < n; j++) {
-    double mybest = -1.0;
-    int myi = 0x7fffffff;
-    for (int i = j + tid; i < n; i += TEAM) {
-      double a = fabs(A[i * ld + j]);
-      if (a > mybest) { mybest = a; myi = i; }
-    }
-    double b;
-    int p;
-    team_argmax(mybest < 0.0 ? 0.0 : mybest, myi, b, p);
-    if (p == 0x7fffffff) p = j;
-    if (p != j) {
-      for (int c = tid; c < n; c += TEAM) {
-        double t = A[j * ld + c]; A[j * ld + c] = A[p * ld + c]; A[p * ld + c] = t;
-      }
-    }
-    if (tid == 0) piv[j] = p;
-    tsync();
-    const double inv = 1.0 / A[j * ld + j];
-    for (int i = j + 1 + tid; i < n; i += TEAM) A[i * ld + j] *= inv;
-    tsync();
-    const int rows = n - j - 1, cols = n - j - 1;
-    for (int idx = tid; idx < rows * cols; idx += TEAM) {
-      int i = j + 1 + idx / cols, c = j + 1 + idx % cols;
-      A[i * ld + c] = fma(-A[i * ld + j], A[j * ld + c], A[i * ld + c]);
-    }
-    tsync();
-  }
-}
-
-// Solve A X = B (trans = 0) or A^T X = B (trans = 1) with the LU of wlu; B is
-// n x nb, overwritten with X; lanes over right-hand sides.
-static __device__ void wlu_solve(const double *LU, int ld, int n, const int *piv, double *B, int ldb, int nb,
-                          int trans) {
-  for (int c = team_rank(); c < nb; c += TEAM) {
-    if (!trans) {
-      for (int i = 0; i < n; i++)
-        if (piv[i] != i) { double t = B[i * ldb + c]; B[i * ldb + c] = B[piv[i] * ldb + c]; B[piv[i] * ldb + c] = t; }
-      for (int i = 0; i < n; i++) {
-        double s = B[i * ldb + c];
-        for (int l = 0; l < i; l++) s = fma(-LU[i * ld + l], B[l * ldb + c], s);
-        B[i * ldb + c] = s;
-      }
-      for (int i = n - 1; i >= 0; i--) {
-        double s = B[i * ldb + c];
-        for (int l = i + 1; l < n; l++) s = fma(-LU[i * ld + l], B[l * ldb + c], s);
-        B[i * ldb + c] = s / LU[i * ld + i];
-      }
-    } else {
-      // A^T = U^T L^T P
-      for (int i = 0; i < n; i++) {
-        double s = B[i * ldb + c];
-        for (int l = 0; l < i; l++) s = fma(-LU[l * ld + i], B[l * ldb + c], s);
-        B[i * ldb + c] = s / LU[i * ld + i];
-      }
-      for (int i = n - 1; i >= 0; i--) {
-        double s = B[i * ldb + c];
-        for (int l = i + 1; l < n; l++) s = fma(-LU[l * ld + i], B[l * ldb + c], s);
-        B[i * ldb + c] = s;
-      }
-      for (int i = n - 1; i >= 0; i--)
-        if (piv[i] != i) { double t = B[i * ldb + c]; B[i * ldb + c] = B[piv[i] * ldb + c]; B[piv[i] * ldb + c] = t; }
-    }
-  }
-  tsync();
 }
 
 }  // namespace eclqr
