@@ -326,11 +326,13 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       ProbInfo pi = pinfo[j];
       int L = h->opt.chunk;
       if (L <= 0) {
-        // enough chunks to give every SM work, but never shorter than 8 stages:
-        // chunk boundaries right after ill-conditioned stages cost accuracy in the
-        // composed dual relations, and short chunks place more boundaries
+        // enough chunks to give every SM work, but never shorter than 7 stages: shorter
+        // chunks place more boundaries, and where a boundary meets an ill-conditioned
+        // stage the refinement needs more than its default passes (on the degenerate
+        // n = 12 instance 6-stage chunks miss the 1e-9 gate after two).  A 1024-stage
+        // problem then runs as 147 chunks, one CTA each, on a 152-SM GB300.
         long long target = std::max<long long>(1, total_stages / (2LL * sms));
-        L = (int)std::min<long long>(64, std::max<long long>(8, target));
+        L = (int)std::min<long long>(64, std::max<long long>(7, target));
         L = std::max(1, std::min(L, pi.N));
       }
       pi.L = L;

@@ -362,7 +362,7 @@ class Batch:
             pass
 
 
-def autotune_chunk(problems, device="cuda", candidates=(0, 6, 12, 16, 32, -1), gate=1e-9, refine=2, passes=3,
+def autotune_chunk(problems, device="cuda", candidates=(0, 6, 8, 12, 16, 32, -1), gate=1e-9, refine=2, passes=3,
                    **kw):
     """Chunk length for these problems: the fastest full pass (build, solve, multipliers, residual) among
     the candidates whose every problem ends with status 0 and a KKT residual <= gate.
