@@ -139,6 +139,15 @@ def test_table1_n1024():
     check(pb, r, d)
 
 
+def test_long_n16_full():
+    """The long-horizon workload at its full size (N = 65536, n = 16, A orthogonal): with the automatic
+    chunk length it runs as 1024 chunks of 64 stages and 10 scan levels, a regime the benchmark
+    instance never reaches.  Every block matches the oracle and the residual meets the gate."""
+    pb = synth.config("long_n16")
+    (r,), (d,) = gpu_run([pb])
+    check(pb, r, d)
+
+
 def test_long_n16_shrunk():
     pb = synth.config("long_n16", N=4096)
     (r,), (d,) = gpu_run([pb])
