@@ -345,7 +345,8 @@ __device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned 
 // the old row k kept in hh_rowk.  If sqrt(d_piv) <= thr (or d_piv = 0), M is
 // left untouched and 0 is returned.  Otherwise the reflector
 // H = I - beta v v' (v = M_piv + sign(x_k) ||M_piv|| e_k, beta =
-// 1 / (||M_piv|| (||M_piv|| + |x_k|))) is applied to the other columns,
+// 1 / (||M_piv|| (||M_piv|| + |x_k|)), formed as 2 / ||v||^2 by hh_reflector)
+// is applied to the other columns,
 // column piv becomes (-sign(x_k) ||M_piv||, 0, ..., 0), and the norm is
 // returned.  L is then replaced by the layout of the next step (cnt - 1
 // columns on rows [k + 1, r)), computed in the shadow of the FP64 latency.
@@ -583,7 +584,8 @@ static __device__ int hh_pivoted_list(double *M, int ld, int k, int r, int cand0
 
 // Range form of a pivoted step: the passes cover every column of [a0, a1)
 // (done ones idle) with power-of-two row segments, S (a1 - a0) <= team size,
-// and the reflector scalars come from the library square root and divide.
+// and the reflector scalars from hh_reflector (library functions only at
+// extreme exponents).
 // The update pass also downdates the remaining norms of the candidate
 // columns (re-evaluating a marked one from its rows, which sit on the same
 // warp) and leaves each warp's best candidate in the arg-max buffer `parity`,
