@@ -98,7 +98,10 @@ typedef struct {
   double tau_rank;   /* relative rank cut after row scaling (Sec. 8 items 1-2); default 1e-10 */
   double tau_inc;    /* inconsistency cut on a scaled offset (Sec. 8 item 4); default 1e-8    */
   int32_t refine;    /* refinement passes on the reduced LQR KKT residual; default 2          */
-  int32_t chunk;     /* stages per scan chunk; 0 = chosen from N and the SM count             */
+  int32_t chunk;     /* stages per scan chunk; 0 = chosen from N and the SM count: one chunk
+                      * per problem when the batch holds at least two problems per SM, else
+                      * 7 to 64 stages.  A problem that fits one chunk is swept once per
+                      * scan, from its terminal element, with no chunk aggregate           */
   int32_t team_warps; /* warps of the CTA that runs one task: 1, 2, 4 or 8; 0 = 4            */
   int32_t scan_skip;  /* 1 (default): take the shortcut of Sec. 6 (complete algorithm and
                        * complexity) where it applies: a problem without state-only or

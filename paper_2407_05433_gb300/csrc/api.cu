@@ -325,7 +325,11 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     for (int j : gh.ids) {
       ProbInfo pi = pinfo[j];
       int L = h->opt.chunk;
-      if (L <= 0) {
+      if (L <= 0 && h->P >= 2 * sms) {
+        // at least two problems per SM: one chunk per problem.  Its sweeps then run
+        // without chunk aggregates, scan levels or next-chunk re-sweeps, the least work.
+        L = std::max(1, pi.N);
+      } else if (L <= 0) {
         // enough chunks to give every SM work, but never shorter than 7 stages: shorter
         // chunks place more boundaries, and where a boundary meets an ill-conditioned
         // stage the refinement needs more than its default passes (on the degenerate

@@ -221,6 +221,13 @@ __global__ void k_dual_up(Group g, int per_task) {
   const ProbInfo &P = g.prob[ci.prob];
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
+  if (P.nch == 1) {  // one chunk: k_dual_down starts from the terminal set alone
+    if (tid == 0) {
+      int *cm = g.CI[0] + (size_t)t * CI_STRIDE;
+      cm[CI_ROWS] = 0; cm[CI_NA] = 0; cm[CI_NB] = 0;
+    }
+    return;
+  }
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int rb = stage_wi(g, P.st0 + b)[SI_UR];
   const int ldr = 2 * n + 1;

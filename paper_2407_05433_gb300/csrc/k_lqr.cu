@@ -87,6 +87,10 @@ __global__ void k_lqr_up(Group g, int per_task) {
     }
     return;
   }
+  if (P.nch == 1) {  // one chunk: k_riccati_down starts from the terminal value alone
+    if (tid == 0) { cm[CI_ROWS] = 0; cm[CI_NA] = 0; cm[CI_NB] = 0; cm[CI_ROWS2] = 0; }
+    return;
+  }
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int nbz = stage_wi(g, P.st0 + b)[SI_NBAR];
   const int rows_max = 5 * n + m, ldm_max = m + 2 * n + 1;

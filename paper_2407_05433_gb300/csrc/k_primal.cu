@@ -119,6 +119,15 @@ __global__ void k_primal_up(Group g, int per_task) {
   const ProbInfo &P = g.prob[ci.prob];
   if (ci.c >= P.nch || scan_skipped(g, ci.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank();
+  if (P.nch == 1) {
+    // one chunk: its down-sweep starts from the terminal slot and reads no
+    // aggregate, so the slot gets an empty relation that the levels copy
+    if (tid == 0) {
+      int *cm = g.CI[0] + (size_t)t * CI_STRIDE;
+      cm[CI_ROWS] = 0; cm[CI_NA] = n; cm[CI_NB] = 0;
+    }
+    return;
+  }
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   double *sm = team_smem(per_task);
   const int ldr = 2 * n + 1, ldm = m + 2 * n + 1;

@@ -182,6 +182,44 @@ def test_infeasible_suffix_status():
     assert eclqr.STATUS_NAMES[st] == "infeasible_suffix"
 
 
+def test_single_chunk_problems_beside_chunked_ones():
+    """With 16-stage chunks the 5-, 12- and 16-stage problems fit one chunk: their sweeps start from
+    the terminal element with no chunk aggregate, in the same launches as the chunked problems."""
+    pbs = [synth.config("degenerate_n12", N=N) for N in (5, 12, 16, 17, 40, 61)]
+    res, dims = gpu_run(pbs, chunk=16)
+    for pb, r, d in zip(pbs, res, dims):
+        check(pb, r, d)
+
+
+def test_default_one_chunk_per_problem_for_large_batches():
+    """320 problems (over two per SM) take one chunk each by default; sampled against the oracle."""
+    pbs = [synth.config("batched_uneven", index=j, N=8 + (j % 29)) for j in range(320)]
+    res, dims = gpu_run(pbs)
+    for j in range(0, 320, 16):
+        pb = pbs[j]
+        s = oracle.solve(pb, debug=True)
+        check(pb, res[j], dims[j], orc=s, resid_gate=max(1e-9, rounding_floor(pb, s)))
+
+
+@pytest.mark.parametrize("chunk", [0, 32])
+def test_infeasible_interior_stage_status(chunk):
+    """Two contradictory state-only rows at stage 8: the suffix from stage 8 is empty.  With
+    32-stage chunks the 16-stage problem is one chunk and only its down-sweep sees the rows."""
+    pb = synth.config("single_n4", N=16)
+    bad = np.array([[1.0, 0, 0, 0], [1.0, 0, 0, 0]])
+    pb.q = pb.q.copy()
+    pb.q[8] = 2
+    pb.E = np.vstack([bad, pb.E])
+    pb.e = np.concatenate([[0.0, 1.0], pb.e])
+    assert oracle.STATUS_NAMES[oracle.solve(pb).status] == "infeasible_suffix"
+    b = eclqr.Batch([pb], chunk=chunk)
+    b.build()
+    b.solve()
+    st = int(b.status.cpu()[0])
+    b.close()
+    assert eclqr.STATUS_NAMES[st] == "infeasible_suffix"
+
+
 def test_infeasible_initial_state_status():
     pb = synth.config("table1", N=8)
     pb.s0 = pb.s0 + 0.1
