@@ -270,6 +270,9 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     g.n = kv.first.first;
     g.m = kv.first.second;
     gh.ids = kv.second;
+    // longest horizons first: the tasks of a launch are issued in this order, so the
+    // longest sweeps start in the first wave instead of finishing alone in the last
+    std::stable_sort(gh.ids.begin(), gh.ids.end(), [&](int a, int b) { return d->N[a] > d->N[b]; });
     int pmax = 0, qmax = 0;
     for (int j : gh.ids) {
       for (long long i = 0; i < d->N[j]; i++) pmax = std::max(pmax, d->p[pstage[j] + i]);
