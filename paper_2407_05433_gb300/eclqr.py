@@ -362,6 +362,33 @@ class Batch:
             pass
 
 
+def _timed_pass(problems, device, refine, passes, gate, **kw):
+    """(ms per full pass, max KKT residual, passed) of one schedule; the first pass is untimed."""
+    import torch
+    b = Batch(problems, device=device, refine=refine, **kw)
+    try:
+        b.run()
+        torch.cuda.synchronize(b.device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(passes):
+            b.run()
+        e1.record()
+        torch.cuda.synchronize(b.device)
+        ms = e0.elapsed_time(e1) / passes
+        res = float(b.resid.max())
+        ok = bool(int(b.status.abs().max()) == 0 and res <= gate)
+    finally:
+        b.close()
+    return ms, res, ok
+
+
+def _pick(trials):
+    """The fastest passing trial, else the one with the smallest residual."""
+    passing = [t for t in trials if t[-1]]
+    return min(passing, key=lambda t: t[-3]) if passing else min(trials, key=lambda t: t[-2])
+
+
 def autotune_chunk(problems, device="cuda", candidates=(0, 6, 8, 12, 16, 32, -1), gate=1e-9, refine=2, passes=3,
                    **kw):
     """Chunk length for these problems: the fastest full pass (build, solve, multipliers, residual) among
@@ -372,26 +399,25 @@ def autotune_chunk(problems, device="cuda", candidates=(0, 6, 8, 12, 16, 32, -1)
     and where they meet the multipliers inherit the difference, so which lengths pass depends on the
     instance.  Returns (chunk, trials) with trials = [(chunk, ms, max residual, passed)].  When no
     candidate passes, the one with the smallest residual is returned."""
-    import torch
     trials = []
     for L in candidates:
         chunk = max(pb.N for pb in problems) if L == -1 else L
-        b = Batch(problems, device=device, refine=refine, chunk=chunk, **kw)
-        try:
-            b.run()
-            torch.cuda.synchronize(b.device)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(passes):
-                b.run()
-            e1.record()
-            torch.cuda.synchronize(b.device)
-            ms = e0.elapsed_time(e1) / passes
-            res = float(b.resid.max())
-            ok = bool(int(b.status.abs().max()) == 0 and res <= gate)
-        finally:
-            b.close()
-        trials.append((chunk, ms, res, ok))
-    passing = [t for t in trials if t[3]]
-    best = min(passing, key=lambda t: t[1]) if passing else min(trials, key=lambda t: t[2])
-    return best[0], trials
+        trials.append((chunk,) + _timed_pass(problems, device, refine, passes, gate, chunk=chunk, **kw))
+    return _pick(trials)[0], trials
+
+
+def autotune_schedule(problems, device="cuda", chunks=(0, 8, 16, -1), teams=(1, 2, 4), gate=1e-9, refine=2,
+                      passes=3, **kw):
+    """Schedule for these problems: chunk length (as in autotune_chunk) and team size, the warps of the
+    CTA that composes one relation (1 = a warp per relation, 4 = the default CTA).  Small relations
+    (n of a few states) leave most of a four-warp team idle; large ones need it.  Every pair is timed
+    over full passes and gated like autotune_chunk.  Returns ((chunk, team_warps), trials) with
+    trials = [(chunk, team_warps, ms, max residual, passed)]."""
+    trials = []
+    for L in chunks:
+        chunk = max(pb.N for pb in problems) if L == -1 else L
+        for w in teams:
+            trials.append((chunk, w) + _timed_pass(problems, device, refine, passes, gate, chunk=chunk,
+                                                   team_warps=w, **kw))
+    best = _pick(trials)
+    return (best[0], best[1]), trials

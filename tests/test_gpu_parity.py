@@ -124,7 +124,7 @@ def test_degenerate_n12_full():
 
 @pytest.mark.parametrize("chunk,refine", [(6, 4), (12, 6), (16, 4), (32, 2)])
 def test_degenerate_n12_full_other_chunk_lengths(chunk, refine):
-    """The full degenerate instance with chunk lengths other than the automatic 8.  Where a boundary
+    """The full degenerate instance with chunk lengths other than the automatic 7.  Where a boundary
     falls next to an ill-conditioned stage the refinement needs more than the default two passes
     (the residual after two passes is not monotone in the chunk length); with the passes given here
     every length meets the parity bar and the gate."""
@@ -258,6 +258,16 @@ def test_shared_memory_limit_at_the_documented_boundary():
     assert b is None
 
 
+@pytest.mark.parametrize("team_warps", [1, 2, 8])
+def test_team_sizes(team_warps):
+    """One relation per warp, per two warps or per eight warps: the same results as the default four."""
+    pbs = [synth.config("single_n4", N=48), synth.config("degenerate_n12", N=61),
+           synth.config("batched_uneven", N=24, index=3), synth.config("table1", N=24)]
+    res, dims = gpu_run(pbs, team_warps=team_warps)
+    for pb, r, d in zip(pbs, res, dims):
+        check(pb, r, d)
+
+
 def test_graph_replay_is_bit_identical_to_eager():
     """One pass captured into a CUDA graph replays the same kernels in the same order."""
     import torch
@@ -287,4 +297,15 @@ def test_chunk_autotuner_returns_a_passing_length():
     assert picked[3], trials
     assert picked[1] == min(t[1] for t in trials if t[3])
     res, dims = gpu_run(pbs, chunk=chunk)
+    check(pbs[0], res[0], dims[0])
+
+
+def test_schedule_autotuner_returns_a_passing_pair():
+    pbs = [synth.config("single_n4")]
+    (chunk, team), trials = eclqr.autotune_schedule(pbs, chunks=(0, -1), teams=(1, 4), passes=1)
+    assert len(trials) == 4 and {(t[0], t[1]) for t in trials} == {(0, 1), (0, 4), (64, 1), (64, 4)}
+    picked = [t for t in trials if (t[0], t[1]) == (chunk, team)][0]
+    assert picked[4], trials
+    assert picked[2] == min(t[2] for t in trials if t[4])
+    res, dims = gpu_run(pbs, chunk=chunk, team_warps=team)
     check(pbs[0], res[0], dims[0])
