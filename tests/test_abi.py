@@ -115,3 +115,13 @@ def test_dimensions_beyond_shared_memory_rejected_before_allocation(lib):
     rc, handle = eclqr.eclqr_create(eclqr.make_desc(h))
     assert rc == eclqr.ESMEM and not handle
     assert "shared memory" in eclqr.eclqr_strerror(eclqr.ESMEM)
+
+
+def test_autotuner_keeps_the_fastest_passing_trial():
+    """The autotuners' selection rule: fastest among the trials that met the gate, else the smallest residual."""
+    chunk_trials = [(0, 5.6, 7e-11, True), (6, 5.4, 8e-5, False), (8, 5.9, 1e-10, True)]
+    assert eclqr._pick(chunk_trials)[0] == 0
+    pair_trials = [(0, 1, 8.2, 1e-10, True), (0, 2, 6.3, 2e-11, True), (0, 4, 5.6, 2e-9, False)]
+    assert eclqr._pick(pair_trials)[:2] == (0, 2)
+    failing = [(0, 4, 5.6, 3e-9, False), (8, 4, 5.9, 2e-9, False)]
+    assert eclqr._pick(failing)[:2] == (8, 4)
