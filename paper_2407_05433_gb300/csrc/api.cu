@@ -395,10 +395,14 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       return ECLQR_ENOMEM;
     }
     char *base = (char *)gh.dmem;
-    cudaMemset(gh.dmem, 0, off);
-    cudaMemcpy(base + o_prob, gp.data(), sizeof(ProbInfo) * gp.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_st, gs.data(), sizeof(StageInfo) * gs.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_ch, gc.data(), sizeof(ChunkInfo) * gc.size(), cudaMemcpyHostToDevice);
+    if (cudaMemset(base, 0, off) != cudaSuccess ||
+        cudaMemcpy(base + o_prob, gp.data(), sizeof(ProbInfo) * gp.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(base + o_st, gs.data(), sizeof(StageInfo) * gs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(base + o_ch, gc.data(), sizeof(ChunkInfo) * gc.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(gh.dmem);
+      eclqr_destroy(h);  // the groups planned so far
+      return ECLQR_ECUDA;
+    }
     g.prob = (const ProbInfo *)(base + o_prob);
     g.st = (const StageInfo *)(base + o_st);
     g.chunk = (const ChunkInfo *)(base + o_ch);
@@ -423,8 +427,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     }
   }
   if (cudaDeviceSynchronize() != cudaSuccess) {
-    for (auto &x : h->groups) cudaFree(x.dmem);
-    delete h;
+    eclqr_destroy(h);
     return ECLQR_ECUDA;
   }
   *out = h;
