@@ -440,8 +440,17 @@ __global__ void k_aff_up(Group g, int mode, int per_task) {
     }
     return;
   }
-  const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int slot = fwd ? P.ch0 + ci.c + 1 : P.ch0 + ci.c;
+  if (P.nch == 1) {
+    // one chunk: k_aff_down starts from the boundary value, so the chunk's map is not
+    // composed; an empty map (no rows, no dimensions) ends the level at once
+    if (tid == 0) {
+      int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
+      cm[CI_ROWS] = 0; cm[CI_NA] = 0; cm[CI_NB] = 0;
+    }
+    return;
+  }
+  const int a = ci.c * P.L, b = min(a + P.L, P.N);
   double *sm = team_smem(per_task);
   double *Gm = sm, *gm = Gm + n * n, *Gs = gm + n, *gs = Gs + n * n, *Tm = gs + n, *tmp = Tm + n * n;
   const int d0 = fwd ? aff_dim(g, P.st0 + a, mode) : aff_dim(g, P.st0 + b, mode);
