@@ -83,8 +83,15 @@ typedef struct {
 #define ECLQR_MAX_N 32
 #define ECLQR_MAX_M 16
 #define ECLQR_MAX_ROWS 32
-/* Combinations whose largest kernel needs more than 227 KB of shared memory
- * per warp are rejected by eclqr_create with ECLQR_EINVAL. */
+/* Combinations whose largest kernel needs more shared memory than one CTA
+ * holds are rejected by eclqr_create with ECLQR_ESMEM.
+ * Stage-varying dimensions n_i, m_i (Sec. 2) enter by zero padding to the
+ * problem's largest n_i and m_i: zero rows and columns of A_i, B_i, c_i, C_i,
+ * D_i, E_i, M_i, q_i, r_i and s_0 at the padded coordinates and identity
+ * blocks of Q_i and R_i there.  The padded states stay 0 through the
+ * dynamics, the padded controls at their unconstrained minimum 0, and the
+ * multipliers of the padded rows are 0; the rest of the solution is that of
+ * the unpadded problem. */
 
 /* Problem data (device memory), layout in the header comment. */
 typedef struct {

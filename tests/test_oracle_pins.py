@@ -484,3 +484,46 @@ def test_planted_mistakes_are_caught(plant, tmp_path):
 def test_unplanted_build_passes_pin_subset(tmp_path):
     lib = oracle.load_mutant(0, str(tmp_path))
     assert _pins_pass(lib)
+
+
+def _zero_padded(pb, n2, m2):
+    """The same problem with n2 - n state and m2 - m control coordinates added: zero rows and columns in
+    A, B, c, C, D, E, M, q, r and s_0, identity blocks in Q, Q_N and R."""
+    N, n, m = pb.N, pb.n, pb.m
+    P, Qr = pb.C.shape[0], pb.E.shape[0]
+
+    def pad(a, shape, fill_eye=False):
+        out = np.zeros(shape)
+        out[tuple(slice(0, s) for s in a.shape)] = a
+        if fill_eye:
+            k0, k1 = a.shape[-1], shape[-1]
+            out[..., np.arange(k0, k1), np.arange(k0, k1)] = 1.0
+        return out
+
+    return synth.ECLQRProblem(
+        N=N, n=n2, m=m2, p=pb.p.copy(), q=pb.q.copy(),
+        A=pad(pb.A, (N, n2, n2)), B=pad(pb.B, (N, n2, m2)), c=pad(pb.c, (N, n2)),
+        C=pad(pb.C, (P, n2)), D=pad(pb.D, (P, m2)), d=pb.d.copy(),
+        E=pad(pb.E, (Qr, n2)), e=pb.e.copy(),
+        Q=pad(pb.Q, (N + 1, n2, n2), True), M=pad(pb.M, (N, n2, m2)), R=pad(pb.R, (N, m2, m2), True),
+        qv=pad(pb.qv, (N + 1, n2)), rv=pad(pb.rv, (N, m2)), s0=pad(pb.s0, (n2,)))
+
+
+def test_zero_padding_embeds_stage_varying_dimensions():
+    """Stage-varying n_i, m_i (Sec. 2) enter the per-problem (n, m) layout by zero padding: padded states
+    are zero rows of the dynamics (so x_pad = 0 from x_0 on), padded controls have no coupling and an
+    identity cost (so u_pad = 0), and stationarity then gives zero multipliers on the padded rows.  The
+    padded solution restricted to the original coordinates is the original one."""
+    pb = synth.config("degenerate_n12", N=24)
+    s = oracle.solve(pb)
+    assert s.ok
+    pp = _zero_padded(pb, pb.n + 3, pb.m + 2)
+    t = oracle.solve(pp)
+    assert t.ok
+    n, m = pb.n, pb.m
+    for got, ref in ((t.x[:, :n], s.x), (t.u[:, :m], s.u), (t.lam[:, :n], s.lam), (t.mu, s.mu), (t.eta, s.eta),
+                     (t.alpha[:n], s.alpha)):
+        assert rel(got, ref) <= 1e-9
+    for pad_part in (t.x[:, n:], t.u[:, m:], t.lam[:, n:], t.alpha[n:]):
+        assert amax(pad_part) <= 1e-12
+    assert oracle.kkt_residual(pp, t.x, t.u, t.lam, t.mu, t.eta, t.alpha) <= 1e-9
