@@ -17,9 +17,9 @@ FP64 and solves for the correction with the same factors.
 The finding these tests pin: refinement converges from FP32 factors on the
 well-conditioned differentiable-batch draw (n = 16, four mixed rows), but on
 the degenerate n = 12 instance and on uneven-batch draws the reduced problem
-is too ill-conditioned for FP32 factors (FP64 factors themselves contract
-only by about 1e-8 per pass there), so the iteration does not reach the 1e-9
-tolerance.  The CUDA path therefore computes every factor in FP64.
+is too ill-conditioned for FP32 factors (the first pass with FP64 factors
+contracts the error there by only 1.6e-9, an effective condition near 1e7),
+so the iteration does not reach the 1e-9 tolerance.  The CUDA path therefore computes every factor in FP64.
 """
 import numpy as np
 import pytest
