@@ -19,7 +19,8 @@ well-conditioned differentiable-batch draw (n = 16, four mixed rows), but on
 the degenerate n = 12 instance and on uneven-batch draws the reduced problem
 is too ill-conditioned for FP32 factors (the first pass with FP64 factors
 contracts the error there by only 1.6e-9, an effective condition near 1e7),
-so the iteration does not reach the 1e-9 tolerance.  The CUDA path therefore computes every factor in FP64.
+so the iteration does not reach the 1e-9 tolerance.  The CUDA path therefore
+computes every factor in FP64.
 """
 import numpy as np
 import pytest
