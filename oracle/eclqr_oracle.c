@@ -926,7 +926,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
           vi[a] = s;
         }
         for (int a = 0; a < nn; a++) {
-          double s = co_[(size_t)i * n + a];
+          double s = (ORC_PLANT == 14) ? 0.0 : co_[(size_t)i * n + a];
           for (int j = 0; j < ni; j++) s += Ab[(size_t)i * n * n + a * n + j] * zi[j];
           for (int j = 0; j < mi; j++) s += Bb[(size_t)i * n * m + a * m + j] * vi[j];
           zn[a] = s;
@@ -940,8 +940,9 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
           PI_[(size_t)i * n + a] = s;
         }
       if (pass) {
-        for (size_t k = 0; k < (size_t)(N + 1) * n; k++) { zz[k] += dz[k]; pis[k] += dpi[k]; }
-        for (size_t k = 0; k < (size_t)N * m; k++) vv[k] += dv[k];
+        const double sgn = (ORC_PLANT == 11) ? -1.0 : 1.0;
+        for (size_t k = 0; k < (size_t)(N + 1) * n; k++) { zz[k] += sgn * dz[k]; pis[k] += sgn * dpi[k]; }
+        for (size_t k = 0; k < (size_t)N * m; k++) vv[k] += sgn * dv[k];
       }
       if (pass == opt->refine) break;
       /* residual of the reduced KKT system, evaluated through the original data.
@@ -1279,7 +1280,8 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
             for (int j = 0; j < pi; j++) Fl[(r0 + a) * nw + j] = P->D[(size_t)(po[i] + j) * m + a];
             for (int j = 0; j < qi; j++) Fl[(r0 + a) * nw + pi + j] = 0.0;
             double s = ru[(size_t)i * m + a];
-            for (int b = 0; b < r1; b++) s += BU[a * n + b] * nu1[b];
+            if (ORC_PLANT != 12)
+              for (int b = 0; b < r1; b++) s += BU[a * n + b] * nu1[b];
             rhs[r0 + a] = s;
           }
           ADDF(2.0 * (r0 + m) * r1);
@@ -1299,7 +1301,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
             Fl[a * qN + j] = w;
           }
           for (int l = 0; l < n; l++) s += UX(N, l, a) * gx[(size_t)N * n + l];
-          rhs[a] = s - nus[(size_t)N * n + a];
+          rhs[a] = (ORC_PLANT == 13) ? s + nus[(size_t)N * n + a] : s - nus[(size_t)N * n + a];
         }
         for (int j = 0; j < qN; j++) wsol[j] = 0.0;
         if (rN > 0) tqr_solve(Fl, rN, qN, tr, rhs, 1, wsol, NULL, &rs);

@@ -475,7 +475,7 @@ def _pins_pass(lib):
     return True
 
 
-@pytest.mark.parametrize("plant", range(1, 11))
+@pytest.mark.parametrize("plant", range(1, 15))
 def test_planted_mistakes_are_caught(plant, tmp_path):
     lib = oracle.load_mutant(plant, str(tmp_path))
     assert not _pins_pass(lib), f"planted mistake {plant} slipped through the pins"
