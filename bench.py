@@ -255,6 +255,20 @@ def measure_batched(pbs, dev, flush, stream, refine, steps=3):
     stat = b.status.cpu().numpy()
     launches = b.launches()
     skipped = int(b.scan_skipped().sum())
+    # per-kernel device time over one untimed pass each; the (n, m) groups run concurrently on their
+    # own streams, so a kernel's time is summed over its groups' overlapping launches
+    kernel_ms = {}
+    try:
+        for name in KERNELS + ["k_scan_check"]:
+            eclqr.eclqr_time_kernel(b.h, name)
+            b.run()
+            nl, tms = eclqr.eclqr_kernel_time(b.h)
+            if nl:
+                kernel_ms[name] = round(tms, 3)
+    except Exception as exc:  # informative only: never lose the line for it
+        kernel_ms = {"error": str(exc)}
+    finally:
+        eclqr.eclqr_time_kernel(b.h, None)
     b.close()
     stages = int(sum(p.N for p in pbs))
     passed = (stat == 0) & (res <= KKT_GATE)
@@ -262,7 +276,7 @@ def measure_batched(pbs, dev, flush, stream, refine, steps=3):
             "stages": stages, "distinct_draws": BATCH_DISTINCT, "refine": refine,
             "status_failures": int((stat != 0).sum()), "resid_max": float(res.max()),
             "gate_passed_frac": float(passed.mean()), "gate_passed": bool(passed.all()),
-            "scan_skipped_problems": skipped}
+            "scan_skipped_problems": skipped, "kernel_ms_per_pass_summed_over_groups": kernel_ms}
 
 
 def _oracle_worker(args):
