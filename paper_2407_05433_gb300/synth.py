@@ -15,6 +15,8 @@ Problem statement (Sec. 2, eq. problem):
 with l_i(x, u) = 1/2 x^T Q_i x + x^T M_i u + 1/2 u^T R_i u + q_i^T x + r_i^T u
 (eq. stage-cost).  State and control dimensions are uniform within one
 problem; constraint row counts p_i (mixed) and q_i (state-only) vary per stage.
+Stage-varying n_i, m_i enter through pack_varying (zero padding to the largest
+ones, which leaves the solution on the original coordinates unchanged).
 
 Packed layout (row-major, stage after stage), shared by every consumer:
     A (N,n,n)  B (N,n,m)  c (N,n)
@@ -32,7 +34,8 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 import numpy as np
 
-__all__ = ["ECLQRProblem", "make_problem", "config", "CONFIG_NAMES", "random_spd"]
+__all__ = ["ECLQRProblem", "make_problem", "config", "CONFIG_NAMES", "random_spd", "pack_varying",
+           "unpack_varying"]
 
 
 @dataclass
@@ -158,6 +161,63 @@ def make_problem(seed, N, n, m, p, q, *, a_mode="perturbed", degenerate_frac=0.0
     return ECLQRProblem(N=N, n=n, m=m, p=p, q=q, A=A, B=B, c=c, C=Cm, D=Dm, d=d,
                         E=Em, e=e, Q=Q, M=M, R=R, qv=qv, rv=rv, s0=xs[0].copy(),
                         x_star=xs, u_star=us)
+
+
+def pack_varying(A, B, c, C, D, d, E, e, Q, M, R, qv, rv, s0):
+    """One problem with stage-varying dimensions (Sec. 2: x_i in R^{n_i}, u_i in R^{m_i}) in the packed
+    per-problem layout, by zero padding to n = max n_i and m = max m_i.
+
+    Per-stage lists: A[i] (n_{i+1}, n_i), B[i] (n_{i+1}, m_i), c[i] (n_{i+1},), C[i] (p_i, n_i),
+    D[i] (p_i, m_i), d[i] (p_i,), M[i] (n_i, m_i), R[i] (m_i, m_i), rv[i] (m_i,) for i < N;
+    E[i] (q_i, n_i), e[i] (q_i,), Q[i] (n_i, n_i), qv[i] (n_i,) for i <= N; s0 (n_0,).
+    Padded coordinates get zero rows and columns everywhere and identity blocks in Q and R: the padded
+    states stay 0 through the dynamics, the padded controls sit at their minimum 0, and the multipliers
+    of the padded rows are 0, so the solution on the original coordinates is unchanged.
+    Returns (problem, (n_i, m_i)); unpack_varying cuts a solution back to the original shapes."""
+    N = len(A)
+    ni = [Q[i].shape[0] for i in range(N + 1)]
+    mi = [R[i].shape[0] for i in range(N)]
+    n, m = max(ni), max(mi)
+
+    def put(block, shape):
+        out = np.zeros(shape)
+        block = np.asarray(block, dtype=np.float64)
+        out[tuple(slice(0, k) for k in block.shape)] = block
+        return out
+
+    def eye_pad(block, k):
+        out = put(block, (k, k))
+        for j in range(np.asarray(block).shape[0], k):
+            out[j, j] = 1.0
+        return out
+
+    p = np.array([np.asarray(d[i]).size for i in range(N)], dtype=np.int32)
+    q = np.array([np.asarray(e[i]).size for i in range(N + 1)], dtype=np.int32)
+    pb = ECLQRProblem(
+        N=N, n=n, m=m, p=p, q=q,
+        A=np.stack([put(A[i], (n, n)) for i in range(N)]),
+        B=np.stack([put(B[i], (n, m)) for i in range(N)]),
+        c=np.stack([put(c[i], (n,)) for i in range(N)]),
+        C=np.concatenate([put(C[i], (p[i], n)) for i in range(N)]),
+        D=np.concatenate([put(D[i], (p[i], m)) for i in range(N)]),
+        d=np.concatenate([np.asarray(d[i], dtype=np.float64).reshape(-1) for i in range(N)]),
+        E=np.concatenate([put(E[i], (q[i], n)) for i in range(N + 1)]),
+        e=np.concatenate([np.asarray(e[i], dtype=np.float64).reshape(-1) for i in range(N + 1)]),
+        Q=np.stack([eye_pad(Q[i], n) for i in range(N + 1)]),
+        M=np.stack([put(M[i], (n, m)) for i in range(N)]),
+        R=np.stack([eye_pad(R[i], m) for i in range(N)]),
+        qv=np.stack([put(qv[i], (n,)) for i in range(N + 1)]),
+        rv=np.stack([put(rv[i], (m,)) for i in range(N)]),
+        s0=put(s0, (n,)))
+    return pb, (ni, mi)
+
+
+def unpack_varying(dims, x, u, lam, alpha):
+    """Per-stage x_i (n_i), u_i (m_i), lambda_i (n_i) and alpha (n_0) of a pack_varying problem's solution;
+    mu and eta keep their packed order (the row counts were not padded)."""
+    ni, mi = dims
+    return ([np.asarray(x[i])[:ni[i]] for i in range(len(ni))], [np.asarray(u[i])[:mi[i]] for i in range(len(mi))],
+            [np.asarray(lam[i])[:ni[i]] for i in range(len(ni))], np.asarray(alpha)[:ni[0]])
 
 
 CONFIG_NAMES = ("single_n4", "degenerate_n12", "long_n16", "batched_uneven", "diff_batch", "table1",

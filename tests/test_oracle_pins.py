@@ -527,3 +527,98 @@ def test_zero_padding_embeds_stage_varying_dimensions():
     for pad_part in (t.x[:, n:], t.u[:, m:], t.lam[:, n:], t.alpha[n:]):
         assert amax(pad_part) <= 1e-12
     assert oracle.kkt_residual(pp, t.x, t.u, t.lam, t.mu, t.eta, t.alpha) <= 1e-9
+
+
+def _varying_instance(seed):
+    """A feasible instance whose state and control dimensions change from stage to stage."""
+    rng = np.random.default_rng(seed)
+    ni, mi = [3, 4, 2, 4, 3, 3, 2], [2, 1, 2, 2, 1, 2]
+    pi, qi = [1, 0, 1, 2, 0, 1], [0, 1, 0, 0, 1, 0, 1]
+    N = len(mi)
+    xs = [rng.standard_normal(k) for k in ni]
+    us = [rng.standard_normal(k) for k in mi]
+    A = [np.eye(ni[i + 1], ni[i]) + 0.3 * rng.standard_normal((ni[i + 1], ni[i])) for i in range(N)]
+    B = [rng.standard_normal((ni[i + 1], mi[i])) for i in range(N)]
+    c = [xs[i + 1] - A[i] @ xs[i] - B[i] @ us[i] for i in range(N)]
+    C = [rng.standard_normal((pi[i], ni[i])) for i in range(N)]
+    D = [rng.standard_normal((pi[i], mi[i])) for i in range(N)]
+    d = [-(C[i] @ xs[i] + D[i] @ us[i]) for i in range(N)]
+    E = [rng.standard_normal((qi[i], ni[i])) for i in range(N + 1)]
+    e = [-(E[i] @ xs[i]) for i in range(N + 1)]
+    Q = [synth.random_spd(rng, k) for k in ni]
+    M = [0.1 * rng.standard_normal((ni[i], mi[i])) for i in range(N)]
+    R = [synth.random_spd(rng, k) + 2.0 * np.eye(k) for k in mi]
+    qv = [rng.standard_normal(k) for k in ni]
+    rv = [rng.standard_normal(k) for k in mi]
+    return dict(A=A, B=B, c=c, C=C, D=D, d=d, E=E, e=e, Q=Q, M=M, R=R, qv=qv, rv=rv, s0=xs[0].copy())
+
+
+def _dense_varying(v):
+    """The KKT system of the varying-dimension QP written out directly (Sec. 2 problem, Sec. 7 signs):
+    unknowns (x_0..x_N, u_0..u_{N-1}), rows x_0 = s_0, dynamics, mixed rows, state-only rows."""
+    N = len(v["A"])
+    ni = [q.shape[0] for q in v["Q"]]
+    mi = [r.shape[0] for r in v["R"]]
+    xo = np.concatenate([[0], np.cumsum(ni)])
+    uo = xo[-1] + np.concatenate([[0], np.cumsum(mi)])
+    nv = int(uo[-1])
+    H, g = np.zeros((nv, nv)), np.zeros(nv)
+    for i in range(N + 1):
+        H[xo[i]:xo[i + 1], xo[i]:xo[i + 1]] = v["Q"][i]
+        g[xo[i]:xo[i + 1]] = v["qv"][i]
+    for i in range(N):
+        H[uo[i]:uo[i + 1], uo[i]:uo[i + 1]] = v["R"][i]
+        H[xo[i]:xo[i + 1], uo[i]:uo[i + 1]] = v["M"][i]
+        H[uo[i]:uo[i + 1], xo[i]:xo[i + 1]] = v["M"][i].T
+        g[uo[i]:uo[i + 1]] = v["rv"][i]
+    rows, rhs = [], []
+
+    def row_block(parts, off):
+        r = np.zeros((parts[0][1].shape[0], nv))
+        for o, blk in parts:
+            r[:, o:o + blk.shape[1]] += blk
+        rows.append(r)
+        rhs.append(-off)
+
+    row_block([(xo[0], np.eye(ni[0]))], -v["s0"])
+    for i in range(N):
+        row_block([(xo[i], v["A"][i]), (uo[i], v["B"][i]), (xo[i + 1], -np.eye(ni[i + 1]))], v["c"][i])
+    for i in range(N):
+        if v["d"][i].size:
+            row_block([(xo[i], v["C"][i]), (uo[i], v["D"][i])], v["d"][i])
+    for i in range(N + 1):
+        if v["e"][i].size:
+            row_block([(xo[i], v["E"][i])], v["e"][i])
+    J, b = np.vstack(rows), np.concatenate(rhs)
+    K = np.block([[H, J.T], [J, np.zeros((J.shape[0], J.shape[0]))]])
+    sol = np.linalg.solve(K, np.concatenate([-g, b]))
+    w, y = sol[:nv], sol[nv:]
+    x = [w[xo[i]:xo[i + 1]] for i in range(N + 1)]
+    u = [w[uo[i]:uo[i + 1]] for i in range(N)]
+    alpha = y[:ni[0]]
+    k = ni[0]
+    lam = [-alpha]
+    for i in range(N):
+        lam.append(y[k:k + ni[i + 1]])
+        k += ni[i + 1]
+    P = sum(di.size for di in v["d"])
+    mu, eta = y[k:k + P], y[k + P:]
+    return x, u, lam, mu, eta, alpha
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_stage_varying_dimensions_against_their_own_dense_kkt(seed):
+    """pack_varying's zero padding, solved by the oracle and cut back, matches the KKT solution of the
+    varying-dimension problem assembled directly, primal and multipliers."""
+    v = _varying_instance(seed)
+    pb, dims = synth.pack_varying(**v)
+    s = oracle.solve(pb)
+    assert s.ok
+    x, u, lam, alpha = synth.unpack_varying(dims, s.x, s.u, s.lam, s.alpha)
+    xd, ud, lamd, mud, etad, alphad = _dense_varying(v)
+    for got, ref in zip(x + u + lam, xd + ud + lamd):
+        assert rel(got, ref) <= 1e-9
+    assert rel(alpha, alphad) <= 1e-9
+    assert rel(s.mu, mud) <= 1e-9 and rel(s.eta, etad) <= 1e-9
+    for i in range(len(dims[0])):
+        assert amax(s.x[i][dims[0][i]:]) <= 1e-12 and amax(s.lam[i][dims[0][i]:]) <= 1e-12
