@@ -622,3 +622,19 @@ def test_stage_varying_dimensions_against_their_own_dense_kkt(seed):
     assert rel(s.mu, mud) <= 1e-9 and rel(s.eta, etad) <= 1e-9
     for i in range(len(dims[0])):
         assert amax(s.x[i][dims[0][i]:]) <= 1e-12 and amax(s.lam[i][dims[0][i]:]) <= 1e-12
+
+
+def test_work_is_linear_in_the_horizon_and_cubic_in_the_local_sizes():
+    """Sec. 6's complexity: O(N) work over the horizon, cubic in the bounded local dimensions.  The oracle's
+    flop count (the roofline's algorithmic work) doubles with N and tends to 8x when n, m, p and the
+    terminal rows all double."""
+    for name in ("single_n4", "long_n16", "table1"):
+        f = [oracle.solve(synth.config(name, N=N)).flops for N in (64, 128, 256)]
+        assert abs(f[1] / f[0] - 2.0) < 0.01 and abs(f[2] / f[1] - 2.0) < 0.01, (name, f)
+    f = []
+    for n in (8, 16, 32):
+        q = np.zeros(65, np.int32)
+        q[64] = n // 2
+        f.append(oracle.solve(synth.make_problem(5, 64, n, n // 2, n // 4, q)).flops)
+    r1, r2 = f[1] / f[0], f[2] / f[1]
+    assert 6.0 < r1 < r2 < 8.0, f
