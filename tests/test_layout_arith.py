@@ -55,3 +55,57 @@ def test_shift_form_of_columns_per_warp_for_power_of_two_teams():
         sh = nw.bit_length() - 1
         for cnt in range(0, 400):
             assert (cnt + nw - 1) >> sh == -(-cnt // nw)
+
+
+def layout(cnt, nr, nw):
+    """la.cuh hh_layout for every lane of a team: (cw, S, lc[lane], sg[lane])."""
+    cw = (cnt + nw - 1) >> (nw.bit_length() - 1)
+    S = min(floor32_over(cw), nr)
+    lanes = np.arange(32)
+    return cw, S, lanes // S, lanes - (lanes // S) * S
+
+
+def test_balanced_layout_visits_every_column_row_pair_once():
+    # the segmented form (S > 1): warp w owns columns [w cw, w cw + cw), lane (lc, sg) takes column
+    # w cw + lc and rows sg, sg + S, ...; the per-lane form (S == 1): lane takes columns w cw + lane + 32 j
+    for nw in (1, 2, 4, 8):
+        for cnt in range(0, 170):
+            for nr in (1, 2, 3, 4, 5, 7, 8, 12, 16, 17, 24, 31, 32, 33, 48):
+                cw, S, lc, sg = layout(cnt, nr, nw)
+                seen = np.zeros((cnt, nr), dtype=np.int64)
+                for w in range(nw):
+                    pw0, pw1 = w * cw, min(w * cw + cw, cnt)
+                    if S > 1:
+                        for lane in range(32):
+                            p = pw0 + lc[lane]
+                            if lc[lane] < cw and p < pw1:
+                                seen[p, sg[lane]::S] += 1
+                    else:
+                        for lane in range(32):
+                            for p in range(pw0 + lane, pw1, 32):
+                                seen[p, :] += 1
+                assert (seen == 1).all(), (nw, cnt, nr)
+
+
+def seg_sum(acc, sg, S):
+    """la.cuh seg_sum over a warp: shuffle-down tree, the segment's first lane receives the total."""
+    acc = list(acc)
+    o = 1
+    while 2 * o < S:
+        o *= 2
+    while o > 0:
+        t = [acc[l + o] if l + o < 32 else acc[l] for l in range(32)]  # __shfl_down_sync
+        acc = [acc[l] + t[l] if sg[l] + o < S else acc[l] for l in range(32)]
+        o >>= 1
+    return acc
+
+
+def test_segment_sums_reach_each_segment_first_lane():
+    rng = np.random.default_rng(0)
+    for S in range(2, 33):
+        lanes = np.arange(32)
+        sg = lanes % S
+        vals = [int(v) for v in rng.integers(-1000, 1000, 32)]
+        out = seg_sum(vals, sg, S)
+        for g in range(32 // S):
+            assert out[g * S] == sum(vals[g * S:(g + 1) * S]), (S, g)
