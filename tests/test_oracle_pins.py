@@ -327,6 +327,9 @@ CLASSES = [
     ("redundant", lambda: synth.make_problem(13, 16, 4, 3, 3, np.r_[np.ones(16, np.int32), 3],
                                              dup_rows=[(0, 1), (6, 7)], zero_D_rows=[12])),
     ("one_stage", lambda: synth.make_problem(14, 1, 3, 2, 1, np.array([0, 1], np.int32))),
+    # four state-only rows pin x_5 (nbar_5 = 0); the domains before it shrink to 3, 2, 1 and some mbar_i = 0
+    ("pinned_interior", lambda: synth.make_problem(21, 12, 4, 2, 1, np.r_[np.zeros(5, np.int32), 4,
+                                                                          np.zeros(6, np.int32), 2])),
 ]
 
 
