@@ -66,7 +66,11 @@ extern "C" {
 #define ECLQR_STATUS_INFEASIBLE_X0 2     /* s_0 violates H_0 s_0 + h_0 = 0 (eq. initial-feasibility) */
 #define ECLQR_STATUS_RANK_INCONSISTENT 3 /* nonzero residual row in Gamma u = -(Phi z + gamma) (Lemma 4 remark) */
 #define ECLQR_STATUS_NONCONVEX 4         /* Cholesky of Rbar + Bbar'P Bbar failed (Prop. 6 violated) */
-#define ECLQR_STATUS_DUAL_INCONSISTENT 5 /* a dual relation reads 0 = gamma != 0 (Sec. 7)         */
+/* 5 is not written: a dual relation (Sec. 7) that reads 0 = gamma != 0 cannot arise
+ * in exact arithmetic, since the KKT conditions of a feasible problem with linear
+ * equality constraints have a solution.  Where rounding produces one, the row is
+ * dropped like a redundant one; the KKT residual and eclqr_refine judge the result. */
+#define ECLQR_STATUS_NONFINITE 6         /* a NaN or an infinity in the data, s_0 or an output */
 
 typedef struct eclqr_handle eclqr_handle;
 
@@ -116,6 +120,10 @@ typedef struct {
                        * once u_i is projected out (Lemma 1, same tolerances) has
                        * X_i = R^n for all i, and its feasible-domain scan is skipped.
                        * 0: always run the scan.  Results are the same either way.       */
+  int32_t kkt_refine; /* passes of eclqr_refine, 0..16; default 8.  0 allocates no
+                       * refinement workspace and eclqr_refine only computes the residual */
+  double refine_tol;  /* eclqr_refine corrects a problem only while its residual exceeds
+                       * this; default 5e-10                                              */
 } eclqr_options;
 
 /* element counts of every packed array (for allocation) */
@@ -167,11 +175,46 @@ int eclqr_multipliers(eclqr_handle *h, const double *x, const double *u, double 
 
 /* Infinity-norm KKT residual of the original problem (Sec. 9 residual
  * definition): x_0 - s_0, dynamics, equality rows divided by max(1, largest
- * |coefficient|, |offset|) of the row, and stationarity.  resid: device
- * double[P]. */
+ * |coefficient|, |offset|) of the row, and stationarity (Sec. 7 sign
+ * convention, lambda_0 = -alpha).  resid: device double[P], overwritten.  A NaN
+ * anywhere in a row makes that problem's residual NaN (it never passes a
+ * comparison with a gate).  Needs a build of the same batch structure; reads
+ * the data of the last eclqr_build. */
 int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const double *u,
                        const double *lam, const double *mu, const double *eta,
                        const double *alpha, double *resid, void *stream);
+
+/* The same residual with its four parts (Sec. 9 residual definition):
+ * parts[4 j + 0] initial condition, + 1 dynamics, + 2 normalised equality
+ * rows, + 3 stationarity; resid[j] is their maximum.  parts: device
+ * double[4 P], overwritten; NULL is ECLQR_EINVAL. */
+int eclqr_kkt_residual_parts(eclqr_handle *h, const double *s0, const double *x, const double *u,
+                             const double *lam, const double *mu, const double *eta,
+                             const double *alpha, double *resid, double *parts, void *stream);
+
+/* Refinement on the original KKT residual (Sec. 8 advises verifying the
+ * original residuals; Sec. 5: the reduction is linear in the offsets).  The
+ * KKT map F(w) of the problem is affine, so for the point w = (x, u, lam, mu,
+ * eta, alpha) with residual rows r = F(w) the correction dw with F(w + dw) = 0
+ * solves the same problem with the same matrices and the offsets replaced by
+ * r: c' = dynamics rows, d' = mixed rows, e' = state-only rows, q' = state
+ * stationarity, r' = control stationarity, s0' = -(x_0 - s_0).  Each pass
+ * computes those rows, runs build, solve and multipliers on them (the
+ * handle's own workspace: no allocation) and keeps w + dw where its residual
+ * is smaller.  A problem takes part in pass k while its status is OK, the
+ * previous pass kept its correction, and its residual exceeds
+ * opt.refine_tol; the others are left as they are (their kernels return at
+ * once).  Up to opt.kkt_refine passes.
+ *   In: s0 and the point (the output of eclqr_solve and eclqr_multipliers,
+ *   device), status (device int32[P], read only).  Out: the point, improved
+ *   in place, and resid (device double[P]): the Sec. 9 residual of the
+ *   returned point (the call computes it first, so no eclqr_kkt_residual is
+ *   needed before it).
+ *   The offset-dependent parts of the workspace then belong to the last
+ *   correction: eclqr_solve and eclqr_multipliers return ECLQR_ESTATE until
+ *   the next eclqr_build or eclqr_set_costs.  Asynchronous on stream. */
+int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double *lam, double *mu,
+                 double *eta, double *alpha, double *resid, int32_t *status, void *stream);
 
 /* Reduced dimensions nbar_i (sum_j (N_j+1)) and mbar_i (sum_j N_j) of the last
  * build, into device int32 arrays. */
@@ -248,8 +291,8 @@ const char *eclqr_strerror(int code);
  * exists for callers that cannot allocate device memory at the moment they need
  * the check -- real-time control loops that forbid allocation after start-up,
  * or processes whose device memory is fully reserved by another allocator so
- * that cudaMalloc fails.  It computes exactly what eclqr_kkt_residual computes
- * (Sec. 9 residual definition), for the batch described by desc and data, with
+ * that cudaMalloc fails.  It computes the same residual as eclqr_kkt_residual,
+ * for the batch described by desc and data, with
  * no handle: the per-problem and per-stage descriptors that the handle keeps in
  * its workspace are written instead into one fixed device array of
  * ECLQR_NOALLOC_MAX_PROBLEMS problem and ECLQR_NOALLOC_MAX_STAGES stage records
@@ -262,8 +305,11 @@ const char *eclqr_strerror(int code);
  *     ECLQR_NOALLOC_MAX_STAGES stage records (sum_j (N_j + 1)) are rejected
  *     with ECLQR_ETOOBIG before anything is enqueued.
  *   - The first call on a device looks up the device address of the array
- *     (cudaGetSymbolAddress) with that device current; make this first call
- *     before any stream capture on that device.
+ *     (cudaGetSymbolAddress) with that device current.
+ *   - The descriptors reach the device by a copy from a host staging array
+ *     that the next call rewrites, so the call cannot be recorded into a CUDA
+ *     graph: on a stream that is capturing it returns ECLQR_ESTATE and
+ *     enqueues nothing.
  *   - Every call rewrites the array (and a host staging array of the same
  *     size) in full for its batch; calls that overlap -- on the GPU, or from
  *     several host threads -- race and must be serialised by the caller. */

@@ -20,7 +20,7 @@ _lock = threading.Lock()
 _lib = None
 
 STATUS_NAMES = {0: "ok", 1: "infeasible_suffix", 2: "infeasible_x0", 3: "rank_inconsistent",
-                4: "nonconvex", 5: "dual_inconsistent", 6: "bad_input"}
+                4: "nonconvex", 6: "nonfinite", 7: "bad_input"}
 
 
 def build_oracle(force=False, plant=0, out=None):
@@ -49,7 +49,8 @@ class _Debug(ct.Structure):
 
 
 class _Options(ct.Structure):
-    _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int)]
+    _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int),
+                ("kkt_refine", ct.c_int), ("refine_tol", ct.c_double)]
 
 
 def _bind(path):
@@ -132,8 +133,14 @@ class OracleSolution:
         return self.status == 0
 
 
-def solve(pb, tau_rank=1e-10, tau_inc=1e-8, multipliers=True, debug=False, refine=2, lib=None):
-    """Run O2 on one problem; returns an OracleSolution (numpy arrays)."""
+def solve(pb, tau_rank=1e-10, tau_inc=1e-8, multipliers=True, debug=False, refine=2, kkt_refine=8,
+          refine_tol=5e-10, lib=None):
+    """Run O2 on one problem; returns an OracleSolution (numpy arrays).
+
+    ``refine`` passes of refinement on the reduced LQR's residual run inside every solve;
+    ``kkt_refine`` passes on the original KKT residual (Sec. 8 advice to check the original
+    residuals, Sec. 5 linearity in the offsets) follow, each only while the Sec. 9 residual
+    exceeds ``refine_tol``.  ``debug`` arrays describe the first (unrefined) solve."""
     lib = lib or _load()
     N, n, m = pb.N, pb.n, pb.m
     P, Qn = int(np.sum(pb.p)), int(np.sum(pb.q))
@@ -154,7 +161,7 @@ def solve(pb, tau_rank=1e-10, tau_inc=1e-8, multipliers=True, debug=False, refin
             z=np.zeros((N + 1, n)), v=np.zeros((N, m)), lrows=np.zeros(N + 1, np.int32),
             L=np.zeros((N + 1, n, n + 1)), pi=np.zeros((N + 1, n)), UT=np.zeros((N + 1, n, n)))
         dbgp = ct.byref(_Debug(*[dbg_arrays[k].ctypes.data for k, _ in _Debug._fields_]))
-    opt = _Options(tau_rank, tau_inc, refine)
+    opt = _Options(tau_rank, tau_inc, refine, kkt_refine if multipliers else 0, refine_tol)
     st = lib.orc_solve(ct.byref(s), ct.byref(opt), x.ctypes.data, u.ctypes.data,
                        lam.ctypes.data if multipliers else None, _ptr(mu) or mu.ctypes.data,
                        _ptr(eta) or eta.ctypes.data, alpha.ctypes.data, ct.byref(fail), ct.byref(fl), dbgp)

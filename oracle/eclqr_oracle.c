@@ -24,7 +24,26 @@
  *      sets propagated right to left, min-norm lambda_0, then forward
  *      substitution choosing the min-norm lambda_{i+1}; min-norm leaf
  *      solves for (mu_i, eta_i), eta_N; alpha = -lambda_0.              (Sec. 7)
- *  10. KKT residual of the original problem (Sec. 9, residual definition)
+ *      A dual relation that reads 0 = gamma != 0 cannot arise in exact
+ *      arithmetic (the KKT conditions of a feasible problem with linear
+ *      equality constraints always have a solution), so such a row is a
+ *      rounding effect: it is dropped like a redundant one and the pass goes
+ *      on; the KKT residual and its refinement (step 11) judge the result.
+ *  10. KKT residual of the original problem (Sec. 9, residual definition);
+ *      a non-finite row makes the residual NaN.
+ *  11. Refinement on the original KKT residual (Sec. 8 asks to check the
+ *      original residuals; Sec. 5: the reduction is linear in the offsets).
+ *      For a point w with residual rows r, the correction dw solves the
+ *      same problem with the same matrices and the offsets replaced by r
+ *      (c' = dynamics rows, d' = mixed rows, e' = state-only rows,
+ *      q' = state stationarity, r' = control stationarity, s0' = -(x_0 - s_0)),
+ *      because F(w + dw) = r + K dw for the affine KKT map F.  Pass k runs
+ *      when the status is OK and the Sec. 9 residual exceeds refine_tol;
+ *      the corrected point replaces w only when its own solve ended with
+ *      status OK and its residual is smaller than w's (otherwise the passes
+ *      stop): where the reduction itself loses its accuracy, the correction
+ *      solves lose it as well, and the iteration would diverge.
+ *  Inputs with a NaN or an infinity give status ORC_NONFINITE at once.
  *
  * Numerical policy (Sec. 8 asks for one; the paper fixes no constants):
  *   - every projected system is row-scaled to unit 2-norm over its
@@ -58,16 +77,20 @@
 #define ORC_INFEASIBLE_X0 2
 #define ORC_RANK_INCONSISTENT 3
 #define ORC_NONCONVEX 4
-#define ORC_DUAL_INCONSISTENT 5
-#define ORC_BAD_INPUT 6
+/* 5 is retired: a dual relation that reads 0 = gamma != 0 no longer stops
+   the multiplier pass (see step 9 below) */
+#define ORC_NONFINITE 6
+#define ORC_BAD_INPUT 7
 
 static double g_flops = 0.0;
 /* flops per phase of Algorithm 1: 0 suffix domains, 1 parameterisation,
    2 stage elimination, 3 Riccati factors, 4 linear passes/rollout/refinement/
-   recovery, 5 multipliers, 6 KKT residual */
+   recovery, 5 multipliers, 6 KKT residual, 7 corrections of the refinement on
+   the original KKT residual (step 11) */
 static double g_phase[8];
 static int g_cur = 0;
-#define ADDF(x) do { double _f = (x); g_flops += _f; g_phase[g_cur] += _f; } while (0)
+static int g_in_correction = 0;
+#define ADDF(x) do { double _f = (x); g_flops += _f; g_phase[g_in_correction ? 7 : g_cur] += _f; } while (0)
 
 /* ------------------------------------------------------------------ */
 /* small dense helpers, row-major, explicit leading dimensions          */
@@ -394,20 +417,20 @@ typedef struct {
 
 typedef struct {
   double tau_rank, tau_inc;
-  int refine;   /* refinement passes on the reduced LQR KKT residual */
+  int refine;        /* refinement passes on the reduced LQR KKT residual */
+  int kkt_refine;    /* passes of step 11 (refinement on the original KKT residual) */
+  double refine_tol; /* step 11 runs a pass only while the residual exceeds this */
 } orc_options;
 
 /* ------------------------------------------------------------------ */
 /* the solver                                                           */
 /* ------------------------------------------------------------------ */
-int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
-              double *u, double *lam, double *mu, double *eta,
-              double *alpha, int *fail_stage, double *flops, orc_debug *dbg) {
+/* one pass of steps 1-9 (Algorithm 1 and Sec. 7) */
+static int solve_once(const orc_problem *P, const orc_options *opt, double *x,
+                      double *u, double *lam, double *mu, double *eta,
+                      double *alpha, int *fail_stage, orc_debug *dbg) {
   const int N = P->N, n = P->n, m = P->m;
   const double tr = opt->tau_rank, ti = opt->tau_inc;
-  if (N < 1 || n < 1 || m < 1) return ORC_BAD_INPUT;
-  g_flops = 0.0;
-  for (int k = 0; k < 8; k++) g_phase[k] = 0.0;
   g_cur = 0;
   *fail_stage = -1;
   int status = ORC_OK;
@@ -1180,7 +1203,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
       for (int a = 0; a < krank; a++)
         for (int b = 0; b <= rN; b++) Ls[(size_t)N * n * lld + a * lld + b] = outp[a * (rN + 1) + b];
       free(outp);
-      if (inc) { status = ORC_DUAL_INCONSISTENT; *fail_stage = N; goto dual_done; }
+      /* an inconsistent leftover row was dropped (step 9) */
     }
     /* right to left: N_i = D'_i o N_{i+1} */
     for (int i = N - 1; i >= 0; i--) {
@@ -1213,7 +1236,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
       for (int a = 0; a < krank; a++)
         for (int b = 0; b <= r0; b++) Ls[(size_t)i * n * lld + a * lld + b] = outp[a * (r0 + 1) + b];
       free(outp);
-      if (inc) { status = ORC_DUAL_INCONSISTENT; *fail_stage = i; goto dual_done; }
+      /* an inconsistent leftover row was dropped (step 9) */
     }
     /* root: min-norm nu_0 in N_0 */
     {
@@ -1258,7 +1281,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
         int gs[1] = {nw};
         double *rel = dalloc((size_t)(rows ? rows : 1) * (r1 + 1));
         project(Wd, rows, nc, 1, gs, r1, tr, ti, grank, &krank, &inc, rel);
-        if (inc) { status = ORC_DUAL_INCONSISTENT; *fail_stage = i; free(rel); break; }
+        /* an inconsistent leftover row was dropped (step 9) */
         for (int l = 0; l < n; l++) nu1[l] = 0.0;
         if (krank > 0 && r1 > 0) {
           for (int a = 0; a < krank; a++) {
@@ -1323,7 +1346,6 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
     }
 #undef STAGE_BLOCKS
 #undef UX
-  dual_done:
     if (dbg && dbg->lrows) memcpy(dbg->lrows, lr, sizeof(int) * (N + 1));
     if (dbg && dbg->L) memcpy(dbg->L, Ls, sizeof(double) * (N + 1) * n * lld);
     free(Ls); free(lr); free(gx); free(gu); free(Wd); free(nus); free(rx); free(ru);
@@ -1355,7 +1377,6 @@ done:
     if (dbg->UT) memcpy(dbg->UT, Ux, sizeof(double) * (N + 1) * n * n);
     if (dbg->v) memcpy(dbg->v, vv, sizeof(double) * N * m);
   }
-  if (flops) *flops = g_flops;
   free(po); free(qo); free(H); free(hr); free(T); free(t); free(nb); free(mb);
   free(Y); free(Z); free(yv); free(Ab); free(Bb); free(cb); free(Qb); free(Mb); free(Rb);
   free(qb); free(rb); free(kap); free(Kg); free(kg); free(zz); free(vv); free(work);
@@ -1366,20 +1387,26 @@ done:
 /* ------------------------------------------------------------------ */
 /* KKT residual of the original problem (Sec. 9 residual definition)    */
 /* ------------------------------------------------------------------ */
+/* The larger of a and b; NaN when either is NaN (fmax would drop it). */
+static double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
+
 /*
- * Infinity norm over: x_0 - s_0; dynamics residuals; mixed and state-only
- * equality rows, each divided by max(1, largest |coefficient|, |offset|) of
- * its row; state, control and terminal stationarity with alpha = -lambda_0
- * (eqs. stage-stationarity, terminal-stationarity).  parts[0..3] receive the
- * four group maxima (init, dynamics, equalities, stationarity).
+ * Residual rows of the KKT system at (x, u, lam, mu, eta, alpha), in the
+ * layout of the problem's offsets (Sec. 7 sign convention, lambda_0 = -alpha):
+ *   rs0 (n)          x_0 - s_0
+ *   rc  (N x n)      A_i x_i + B_i u_i + c_i - x_{i+1}
+ *   rd  (sum p)      C_i x_i + D_i u_i + d_i
+ *   re  (sum q)      E_i x_i + e_i
+ *   rq  ((N+1) x n)  Q_i x_i + M_i u_i + q_i + A_i' lam_{i+1} - lam_i + C_i' mu_i + E_i' eta_i
+ *                    (stage 0: + alpha for - lam_0; stage N: Q_N x_N + q_N - lam_N + E_N' eta_N)
+ *   rr  (N x m)      M_i' x_i + R_i u_i + r_i + B_i' lam_{i+1} + D_i' mu_i
  */
-double orc_kkt_residual(const orc_problem *P, const double *x, const double *u,
-                        const double *lam, const double *mu, const double *eta,
-                        const double *alpha, double *parts) {
+static void kkt_rows(const orc_problem *P, const double *x, const double *u, const double *lam,
+                     const double *mu, const double *eta, const double *alpha, double *rs0, double *rc,
+                     double *rd, double *re, double *rq, double *rr) {
   const int N = P->N, n = P->n, m = P->m;
-  double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
   int po = 0, qo = 0;
-  for (int a = 0; a < n; a++) r0 = fmax(r0, fabs(x[a] - P->s0[a]));
+  for (int a = 0; a < n; a++) rs0[a] = x[a] - P->s0[a];
   for (int i = 0; i <= N; i++) {
     const double *xi = x + (size_t)i * n, *li = lam + (size_t)i * n;
     int pi = i < N ? P->p[i] : 0, qi = P->q[i];
@@ -1390,25 +1417,23 @@ double orc_kkt_residual(const orc_problem *P, const double *x, const double *u,
         double s = P->c[(size_t)i * n + a] - xn[a];
         for (int j = 0; j < n; j++) s += Ai[a * n + j] * xi[j];
         for (int j = 0; j < m; j++) s += Bi[a * m + j] * ui[j];
-        r1 = fmax(r1, fabs(s));
+        rc[(size_t)i * n + a] = s;
       }
       for (int k = 0; k < pi; k++) {
         const double *Ck = P->C + (size_t)(po + k) * n, *Dk = P->D + (size_t)(po + k) * m;
-        double s = P->d[po + k], sc = fmax(1.0, fabs(P->d[po + k]));
-        for (int j = 0; j < n; j++) { s += Ck[j] * xi[j]; sc = fmax(sc, fabs(Ck[j])); }
-        for (int j = 0; j < m; j++) { s += Dk[j] * ui[j]; sc = fmax(sc, fabs(Dk[j])); }
-        r2 = fmax(r2, fabs(s) / ((ORC_PLANT == 10) ? 1.0 : sc));
+        double s = P->d[po + k];
+        for (int j = 0; j < n; j++) s += Ck[j] * xi[j];
+        for (int j = 0; j < m; j++) s += Dk[j] * ui[j];
+        rd[po + k] = s;
       }
-      /* control stationarity */
       for (int a = 0; a < m; a++) {
         double s = P->rv[(size_t)i * m + a];
         for (int j = 0; j < n; j++) s += P->M[(size_t)i * n * m + j * m + a] * xi[j];
         for (int j = 0; j < m; j++) s += P->R[(size_t)i * m * m + a * m + j] * ui[j];
         for (int j = 0; j < n; j++) s += Bi[j * m + a] * ln[j];
         for (int k = 0; k < pi; k++) s += P->D[(size_t)(po + k) * m + a] * mu[po + k];
-        r3 = fmax(r3, fabs(s));
+        rr[(size_t)i * m + a] = s;
       }
-      /* state stationarity */
       for (int a = 0; a < n; a++) {
         double s = P->qv[(size_t)i * n + a];
         for (int j = 0; j < n; j++) s += P->Q[(size_t)i * n * n + a * n + j] * xi[j];
@@ -1417,27 +1442,151 @@ double orc_kkt_residual(const orc_problem *P, const double *x, const double *u,
         for (int j = 0; j < n; j++) s += Ai[j * n + a] * ln[j];
         for (int k = 0; k < pi; k++) s += P->C[(size_t)(po + k) * n + a] * mu[po + k];
         for (int k = 0; k < qi; k++) s += P->E[(size_t)(qo + k) * n + a] * eta[qo + k];
-        r3 = fmax(r3, fabs(s));
+        rq[(size_t)i * n + a] = s;
       }
     } else {
       for (int a = 0; a < n; a++) {
         double s = P->qv[(size_t)N * n + a] - li[a];
         for (int j = 0; j < n; j++) s += P->Q[(size_t)N * n * n + a * n + j] * xi[j];
         for (int k = 0; k < qi; k++) s += P->E[(size_t)(qo + k) * n + a] * eta[qo + k];
-        r3 = fmax(r3, fabs(s));
+        rq[(size_t)N * n + a] = s;
       }
     }
     for (int k = 0; k < qi; k++) {
       const double *Ek = P->E + (size_t)(qo + k) * n;
-      double s = P->e[qo + k], sc = fmax(1.0, fabs(P->e[qo + k]));
-      for (int j = 0; j < n; j++) { s += Ek[j] * xi[j]; sc = fmax(sc, fabs(Ek[j])); }
-      r2 = fmax(r2, fabs(s) / sc);
+      double s = P->e[qo + k];
+      for (int j = 0; j < n; j++) s += Ek[j] * xi[j];
+      re[qo + k] = s;
     }
     po += pi;
     qo += qi;
   }
+}
+
+static void row_counts(const orc_problem *P, int *ptot, int *qtot) {
+  int a = 0, b = 0;
+  for (int i = 0; i < P->N; i++) a += P->p[i];
+  for (int i = 0; i <= P->N; i++) b += P->q[i];
+  *ptot = a;
+  *qtot = b;
+}
+
+/*
+ * Infinity norm over: x_0 - s_0; dynamics; mixed and state-only rows, each
+ * divided by max(1, largest |coefficient|, |offset|) of its row; stationarity
+ * (unnormalised).  parts = {initial, dynamics, equalities, stationarity}.
+ * Any non-finite row makes the result (and its part) NaN.
+ */
+double orc_kkt_residual(const orc_problem *P, const double *x, const double *u,
+                        const double *lam, const double *mu, const double *eta,
+                        const double *alpha, double *parts) {
+  const int N = P->N, n = P->n, m = P->m;
+  int pt, qt;
+  row_counts(P, &pt, &qt);
+  double *rs0 = dalloc(n), *rc = dalloc((size_t)N * n), *rd = dalloc(pt + 1), *re = dalloc(qt + 1);
+  double *rq = dalloc((size_t)(N + 1) * n), *rr = dalloc((size_t)N * m);
+  kkt_rows(P, x, u, lam, mu, eta, alpha, rs0, rc, rd, re, rq, rr);
+  double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+  for (int a = 0; a < n; a++) r0 = nanmax(r0, fabs(rs0[a]));
+  for (size_t k = 0; k < (size_t)N * n; k++) r1 = nanmax(r1, fabs(rc[k]));
+  for (int k = 0; k < pt; k++) {
+    const double *Ck = P->C + (size_t)k * n, *Dk = P->D + (size_t)k * m;
+    double sc = nanmax(1.0, fabs(P->d[k]));
+    for (int j = 0; j < n; j++) sc = nanmax(sc, fabs(Ck[j]));
+    for (int j = 0; j < m; j++) sc = nanmax(sc, fabs(Dk[j]));
+    r2 = nanmax(r2, fabs(rd[k]) / ((ORC_PLANT == 10) ? 1.0 : sc));
+  }
+  for (int k = 0; k < qt; k++) {
+    const double *Ek = P->E + (size_t)k * n;
+    double sc = nanmax(1.0, fabs(P->e[k]));
+    for (int j = 0; j < n; j++) sc = nanmax(sc, fabs(Ek[j]));
+    r2 = nanmax(r2, fabs(re[k]) / sc);
+  }
+  for (size_t k = 0; k < (size_t)(N + 1) * n; k++) r3 = nanmax(r3, fabs(rq[k]));
+  for (size_t k = 0; k < (size_t)N * m; k++) r3 = nanmax(r3, fabs(rr[k]));
+  free(rs0); free(rc); free(rd); free(re); free(rq); free(rr);
   if (parts) { parts[0] = r0; parts[1] = r1; parts[2] = r2; parts[3] = r3; }
-  return fmax(fmax(r0, r1), fmax(r2, r3));
+  return nanmax(nanmax(r0, r1), nanmax(r2, r3));
+}
+
+/* ------------------------------------------------------------------ */
+/* Entry point: steps 1-9, then the refinement of step 11               */
+/* ------------------------------------------------------------------ */
+static int finite_all(const double *a, size_t k) {
+  for (size_t i = 0; i < k; i++)
+    if (!isfinite(a[i])) return 0;
+  return 1;
+}
+
+static int inputs_finite(const orc_problem *P) {
+  const size_t N = P->N, n = P->n, m = P->m;
+  int pt, qt;
+  row_counts(P, &pt, &qt);
+  return finite_all(P->A, N * n * n) && finite_all(P->B, N * n * m) && finite_all(P->c, N * n) &&
+         finite_all(P->C, (size_t)pt * n) && finite_all(P->D, (size_t)pt * m) && finite_all(P->d, pt) &&
+         finite_all(P->E, (size_t)qt * n) && finite_all(P->e, qt) && finite_all(P->Q, (N + 1) * n * n) &&
+         finite_all(P->M, N * n * m) && finite_all(P->R, N * m * m) && finite_all(P->qv, (N + 1) * n) &&
+         finite_all(P->rv, N * m) && finite_all(P->s0, n);
+}
+
+int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
+              double *u, double *lam, double *mu, double *eta,
+              double *alpha, int *fail_stage, double *flops, orc_debug *dbg) {
+  const int N = P->N, n = P->n, m = P->m;
+  if (N < 1 || n < 1 || m < 1) return ORC_BAD_INPUT;
+  g_flops = 0.0;
+  for (int k = 0; k < 8; k++) g_phase[k] = 0.0;
+  g_in_correction = 0;
+  *fail_stage = -1;
+  if (flops) *flops = 0.0;
+  if (!inputs_finite(P)) return ORC_NONFINITE;
+  int status = solve_once(P, opt, x, u, lam, mu, eta, alpha, fail_stage, dbg);
+  int pt, qt;
+  row_counts(P, &pt, &qt);
+  if (status == ORC_OK &&
+      !(finite_all(x, (size_t)(N + 1) * n) && finite_all(u, (size_t)N * m) &&
+        (!lam || (finite_all(lam, (size_t)(N + 1) * n) && finite_all(mu, pt) && finite_all(eta, qt) &&
+                  finite_all(alpha, n)))))
+    status = ORC_NONFINITE;
+  if (lam && status == ORC_OK && opt->kkt_refine > 0) {
+    g_in_correction = 1;
+    orc_problem C = *P;
+    double *rs0 = dalloc(n), *rc = dalloc((size_t)N * n), *rd = dalloc(pt + 1), *re = dalloc(qt + 1);
+    double *rq = dalloc((size_t)(N + 1) * n), *rr = dalloc((size_t)N * m), *s0c = dalloc(n);
+    double *dx = dalloc((size_t)(N + 1) * n), *du = dalloc((size_t)N * m), *dl = dalloc((size_t)(N + 1) * n);
+    double *dmu = dalloc(pt + 1), *deta = dalloc(qt + 1), *dal = dalloc(n);
+    C.c = rc; C.d = rd; C.e = re; C.qv = rq; C.rv = rr; C.s0 = s0c;
+    for (int k = 0; k < opt->kkt_refine; k++) {
+      const double res = orc_kkt_residual(P, x, u, lam, mu, eta, alpha, NULL);
+      if (!(res > opt->refine_tol)) break;
+      kkt_rows(P, x, u, lam, mu, eta, alpha, rs0, rc, rd, re, rq, rr);
+      for (int a = 0; a < n; a++) s0c[a] = -rs0[a];
+      int fs;
+      const int st = solve_once(&C, opt, dx, du, dl, dmu, deta, dal, &fs, NULL);
+      if (st != ORC_OK) break;
+      /* trial point w + dw, kept only when its residual is smaller (a
+         correction from a solve that lost its accuracy is refused) */
+      const double sg = (ORC_PLANT == 16) ? -1.0 : 1.0;
+      for (size_t j = 0; j < (size_t)(N + 1) * n; j++) { dx[j] = x[j] + sg * dx[j]; dl[j] += lam[j]; }
+      for (size_t j = 0; j < (size_t)N * m; j++) du[j] += u[j];
+      for (int j = 0; j < pt; j++) dmu[j] = ((ORC_PLANT == 15) ? 0.0 : dmu[j]) + mu[j];
+      for (int j = 0; j < qt; j++) deta[j] += eta[j];
+      for (int j = 0; j < n; j++) dal[j] += alpha[j];
+      const double trial = orc_kkt_residual(P, dx, du, dl, dmu, deta, dal, NULL);
+      if (!(trial < res)) break;
+      memcpy(x, dx, sizeof(double) * (N + 1) * n);
+      memcpy(lam, dl, sizeof(double) * (N + 1) * n);
+      memcpy(u, du, sizeof(double) * N * m);
+      memcpy(mu, dmu, sizeof(double) * pt);
+      memcpy(eta, deta, sizeof(double) * qt);
+      memcpy(alpha, dal, sizeof(double) * n);
+    }
+    free(rs0); free(rc); free(rd); free(re); free(rq); free(rr); free(s0c);
+    free(dx); free(du); free(dl); free(dmu); free(deta); free(dal);
+    g_in_correction = 0;
+  }
+  if (flops) *flops = g_flops;
+  return status;
 }
 
 /* exported helpers so tests can exercise Lemma 1 and the null-space solve

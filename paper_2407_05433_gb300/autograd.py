@@ -25,14 +25,18 @@ def batch_params(batch, requires_grad=True):
 
 
 def _run(batch, data_tensors, s0, reuse=False):
-    """build (or, with reuse, eclqr_set_costs on the last build's factors) + solve + multipliers on the
-    given data; returns the six packed outputs and status."""
+    """build (or, with reuse, eclqr_set_costs on the last build's factors) + solve + multipliers +
+    refinement on the original KKT residual, on the given data; returns the six packed outputs and
+    status.  The handle then points at data_tensors, not at batch.data: the Batch is marked so that
+    its own solve, multipliers and residual calls refuse to run until its next build()."""
     L = batch.layout
     f64 = dict(dtype=torch.float64, device=batch.device)
     out = [torch.zeros(max(1, int(getattr(L, k))), **f64) for k in ("x", "u", "lam", "mu", "eta", "alpha")]
     status = torch.zeros(len(batch.problems), dtype=torch.int32, device=batch.device)
+    resid = torch.zeros(len(batch.problems), **f64)
     data = eclqr.eclqr_data(*[t.data_ptr() for t in data_tensors])
     st = batch._stream()
+    batch.invalidate()
     if reuse:
         eclqr._check(eclqr.eclqr_set_costs(batch.h, data, st), "eclqr_set_costs")
     else:
@@ -42,6 +46,8 @@ def _run(batch, data_tensors, s0, reuse=False):
                                    st), "eclqr_solve")
     eclqr._check(eclqr.eclqr_multipliers(batch.h, *[t.data_ptr() for t in out], status.data_ptr(), st),
                  "eclqr_multipliers")
+    eclqr._check(eclqr.eclqr_refine(batch.h, s0.data_ptr(), *[t.data_ptr() for t in out], resid.data_ptr(),
+                                    status.data_ptr(), st), "eclqr_refine")
     return out, status
 
 

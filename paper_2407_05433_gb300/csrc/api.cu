@@ -56,6 +56,15 @@ struct eclqr_handle {
   std::vector<cudaEvent_t> ev;
   int nev = 0;
   cudaEvent_t fork = nullptr;   // the caller's stream position the group streams start from
+  // refinement on the original KKT residual (eclqr_refine): correction offsets, trial
+  // point, per-problem pass status, trial residual and mask, in one allocation
+  void *rmem = nullptr;
+  KktRows rows{};
+  SolMut trial{};
+  int32_t *cstatus = nullptr;
+  double *tresid = nullptr;
+  int *active = nullptr;
+  bool stale = false;  // the offset-dependent factors are a correction's (after eclqr_refine)
 };
 
 namespace {
@@ -185,6 +194,8 @@ void eclqr_default_options(eclqr_options *opt) {
   opt->chunk = 0;
   opt->team_warps = 0;
   opt->scan_skip = 1;
+  opt->kkt_refine = 8;
+  opt->refine_tol = 5e-10;
 }
 
 int eclqr_layout(const eclqr_desc *d, eclqr_layout_info *out) {
@@ -222,7 +233,8 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   if (h->opt.team_warps == 0) h->opt.team_warps = kTeamWarps;
   const int tw = h->opt.team_warps;
   if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0) ||
-      !(tw == 1 || tw == 2 || tw == 4 || tw == 8) || !(h->opt.scan_skip == 0 || h->opt.scan_skip == 1)) {
+      !(tw == 1 || tw == 2 || tw == 4 || tw == 8) || !(h->opt.scan_skip == 0 || h->opt.scan_skip == 1) ||
+      h->opt.kkt_refine < 0 || h->opt.kkt_refine > 16 || !(h->opt.refine_tol >= 0)) {
     delete h;
     return ECLQR_EINVAL;
   }
@@ -415,6 +427,27 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     g.need_scan = (int *)(base + o_need);
     h->groups.push_back(gh);
   }
+  if (h->opt.kkt_refine > 0) {
+    const eclqr_layout_info &L = h->lay;
+    size_t off = 0;
+    auto take = [&](size_t elems, size_t esz) { size_t r = off; off += (std::max<size_t>(elems, 1) * esz + 255) & ~size_t(255); return r; };
+    const size_t o_c = take(L.c, 8), o_d = take(L.d, 8), o_e = take(L.e, 8), o_qv = take(L.qv, 8),
+                 o_rv = take(L.rv, 8), o_s0 = take(L.s0, 8), o_x = take(L.x, 8), o_u = take(L.u, 8),
+                 o_lam = take(L.lam, 8), o_mu = take(L.mu, 8), o_eta = take(L.eta, 8), o_al = take(L.alpha, 8),
+                 o_cs = take(P, 4), o_tr = take(P, 8), o_ac = take(P, 4);
+    if (cudaMalloc(&h->rmem, off) != cudaSuccess || cudaMemset(h->rmem, 0, off) != cudaSuccess) {
+      eclqr_destroy(h);
+      return ECLQR_ENOMEM;
+    }
+    char *b = (char *)h->rmem;
+    h->rows = KktRows{(double *)(b + o_c), (double *)(b + o_d), (double *)(b + o_e), (double *)(b + o_qv),
+                      (double *)(b + o_rv), (double *)(b + o_s0)};
+    h->trial = SolMut{(double *)(b + o_x), (double *)(b + o_u), (double *)(b + o_lam), (double *)(b + o_mu),
+                      (double *)(b + o_eta), (double *)(b + o_al)};
+    h->cstatus = (int32_t *)(b + o_cs);
+    h->tresid = (double *)(b + o_tr);
+    h->active = (int *)(b + o_ac);
+  }
   if (h->groups.size() > 1) {
     bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess;
     for (auto &gh : h->groups) {
@@ -434,48 +467,43 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   return ECLQR_OK;
 }
 
-int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *stream) {
-  if (!h || !data || !status) return ECLQR_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemsetAsync(status, 0, sizeof(int32_t) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
-  TRY(fork_groups(h, st));
-  for (auto &gh : h->groups) {
-    const cudaStream_t gst = group_stream(h, gh, st);
-    Group &g = gh.g;
-    g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
-    g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
-    g.status = status;
-    const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
-    const int sw = smem_primal_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
+}  // extern "C"
+
+namespace {
+
+// Algorithm 1 up to the Riccati factors (Sec. 3-6) for one group, with the data,
+// status and mask that g carries.  scan_check: run the Sec. 6 shortcut's test
+// and the check of the data for NaN (the first build of a data set; correction
+// problems have the same matrices and reuse its flags).
+int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, bool first) {
+  const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
+  const int sw = smem_primal_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
+  if (first) {
+    TRY(launch(h, k_check_inputs, g.nstage, 0, gst, g));
     if (gh.any_skip) {
       if (cudaMemsetAsync(g.need_scan, 0, sizeof(int) * g.nprob, gst) != cudaSuccess) return ECLQR_ECUDA;
       const int sk = smem_scan_check(n, m, pm);
       TRY(launch(h, k_scan_check, g.nstage, sk, gst, g, sk));
     }
-    TRY(launch(h, k_terminal, g.nprob, sw, gst, g, sw));
-    TRY(launch(h, k_primal_up, g.nslot, sw, gst, g, sw));
-    int src = 0;
-    for (int k = 0; k < gh.levels; k++, src ^= 1)
-      TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
-    TRY(launch(h, k_primal_down, g.nslot, sw, gst, g, src, sw));
-    const int sp = smem_param(n), se = smem_elim(n, m, pm);
-    TRY(launch(h, k_param, g.nstage, sp, gst, g, sp));
-    TRY(launch(h, k_elim, g.nstage, se, gst, g, se));
-    const int su = smem_lqr_up(n, m), slv = smem_lqr_level(n), sr = smem_riccati(n, m);
-    TRY(launch(h, k_lqr_up, g.nslot, su, gst, g, su));
-    src = 0;
-    for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_lqr_level, g.nslot, slv, gst, g, src, 1 << k, slv));
-    TRY(launch(h, k_riccati_down, g.nslot, sr, gst, g, src, sr));
   }
-  TRY(join_groups(h, st));
-  h->built = true;
-  h->solved = false;
+  TRY(launch(h, k_terminal, g.nprob, sw, gst, g, sw));
+  TRY(launch(h, k_primal_up, g.nslot, sw, gst, g, sw));
+  int src = 0;
+  for (int k = 0; k < gh.levels; k++, src ^= 1)
+    TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
+  TRY(launch(h, k_primal_down, g.nslot, sw, gst, g, src, sw));
+  const int sp = smem_param(n), se = smem_elim(n, m, pm);
+  TRY(launch(h, k_param, g.nstage, sp, gst, g, sp));
+  TRY(launch(h, k_elim, g.nstage, se, gst, g, se));
+  const int su = smem_lqr_up(n, m), slv = smem_lqr_level(n), sr = smem_riccati(n, m);
+  TRY(launch(h, k_lqr_up, g.nslot, su, gst, g, su));
+  src = 0;
+  for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_lqr_level, g.nslot, slv, gst, g, src, 1 << k, slv));
+  TRY(launch(h, k_riccati_down, g.nslot, sr, gst, g, src, sr));
   return ECLQR_OK;
 }
 
-namespace {
-int aff_scan(eclqr_handle *h, GroupHost &gh, int mode, cudaStream_t st) {
-  Group &g = gh.g;
+int aff_scan(eclqr_handle *h, const GroupHost &gh, const Group &g, int mode, cudaStream_t st) {
   const int sa = smem_aff(g.n, g.m);
   const int fwd = (mode == AFF_PLIN_) ? 0 : 1;
   TRY(launch(h, k_aff_up, g.nslot, sa, st, g, mode, sa));
@@ -485,30 +513,80 @@ int aff_scan(eclqr_handle *h, GroupHost &gh, int mode, cudaStream_t st) {
   TRY(launch(h, k_aff_down, g.nslot, sa, st, g, mode, src, sa));
   return ECLQR_OK;
 }
+
+// rollout with refinement on the reduced residual, and recovery (Sec. 6, eq. recovery-maps)
+int run_solve(eclqr_handle *h, const GroupHost &gh, const Group &g, cudaStream_t gst, const double *s0, double *x,
+              double *u) {
+  TRY(launch(h, k_solve_init, g.nprob, 0, gst, g, s0));
+  TRY(aff_scan(h, gh, g, AFF_ROLL_, gst));
+  TRY(launch(h, k_post_roll, g.nstage, 0, gst, g, 0));
+  for (int r = 0; r < h->opt.refine; r++) {
+    const int sres = 3 * g.n + 2 * g.m;
+    TRY(launch(h, k_resid, g.nstage, sres, gst, g, sres));
+    TRY(aff_scan(h, gh, g, AFF_PLIN_, gst));
+    const int sc = g.n + g.m;
+    TRY(launch(h, k_pcorr, g.nstage, sc, gst, g, sc));
+    TRY(aff_scan(h, gh, g, AFF_CROLL_, gst));
+    TRY(launch(h, k_post_roll, g.nstage, 0, gst, g, 1));
+  }
+  TRY(launch(h, k_recover, g.nstage, 0, gst, g, x, u));
+  return ECLQR_OK;
+}
+
+// multipliers (Sec. 7)
+int run_mult(eclqr_handle *h, const GroupHost &gh, const Group &g, cudaStream_t gst, const double *x, const double *u,
+             double *lam, double *mu, double *eta, double *alpha) {
+  const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
+  const int sd = smem_dual_stage(n, m), sw = smem_dual_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
+  const int sf = smem_dual_leaf(n, m, pm, qm);
+  TRY(launch(h, k_dual_stage, g.nstage, sd, gst, g, x, u, sd));
+  TRY(launch(h, k_dual_terminal, g.nprob, sw, gst, g, sw));
+  TRY(launch(h, k_dual_up, g.nslot, sw, gst, g, sw));
+  int src = 0;
+  for (int k = 0; k < gh.levels; k++, src ^= 1)
+    TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_OK, sl));
+  TRY(launch(h, k_dual_down, g.nslot, sw, gst, g, src, sw));
+  TRY(launch(h, k_dual_root, g.nprob, sw, gst, g, sw));
+  TRY(aff_scan(h, gh, g, AFF_NU_, gst));
+  TRY(launch(h, k_dual_leaf, g.nstage, sf, gst, g, lam, mu, eta, alpha, sf));
+  return ECLQR_OK;
+}
+
+void set_data(Group &g, const eclqr_data *data) {
+  g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
+  g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
+}
+
 }  // namespace
+
+extern "C" {
+
+int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *stream) {
+  if (!h || !data || !status) return ECLQR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
+  TRY(fork_groups(h, st));
+  for (auto &gh : h->groups) {
+    set_data(gh.g, data);
+    gh.g.status = status;
+    gh.g.active = nullptr;
+    TRY(run_build(h, gh, gh.g, group_stream(h, gh, st), true));
+  }
+  TRY(join_groups(h, st));
+  h->built = true;
+  h->solved = false;
+  h->stale = false;
+  return ECLQR_OK;
+}
 
 int eclqr_solve(eclqr_handle *h, const double *s0, double *x, double *u, int32_t *status, void *stream) {
   if (!h || !s0 || !x || !u || !status) return ECLQR_EINVAL;
-  if (!h->built) return ECLQR_ESTATE;
+  if (!h->built || h->stale) return ECLQR_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
   TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
-    const cudaStream_t gst = group_stream(h, gh, st);
-    Group &g = gh.g;
-    g.status = status;
-    TRY(launch(h, k_solve_init, g.nprob, 0, gst, g, s0));
-    TRY(aff_scan(h, gh, AFF_ROLL_, gst));
-    TRY(launch(h, k_post_roll, g.nstage, 0, gst, g, 0));
-    for (int r = 0; r < h->opt.refine; r++) {
-      const int sres = 3 * g.n + 2 * g.m;
-      TRY(launch(h, k_resid, g.nstage, sres, gst, g, sres));
-      TRY(aff_scan(h, gh, AFF_PLIN_, gst));
-      const int sc = g.n + g.m;
-      TRY(launch(h, k_pcorr, g.nstage, sc, gst, g, sc));
-      TRY(aff_scan(h, gh, AFF_CROLL_, gst));
-      TRY(launch(h, k_post_roll, g.nstage, 0, gst, g, 1));
-    }
-    TRY(launch(h, k_recover, g.nstage, 0, gst, g, x, u));
+    gh.g.status = status;
+    TRY(run_solve(h, gh, gh.g, group_stream(h, gh, st), s0, x, u));
   }
   TRY(join_groups(h, st));
   h->solved = true;
@@ -524,40 +602,90 @@ int eclqr_multipliers(eclqr_handle *h, const double *x, const double *u, double 
   cudaStream_t st = (cudaStream_t)stream;
   TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
-    const cudaStream_t gst = group_stream(h, gh, st);
-    Group &g = gh.g;
-    g.status = status;
-    const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
-    const int sd = smem_dual_stage(n, m), sw = smem_dual_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
-    const int sf = smem_dual_leaf(n, m, pm, qm);
-    TRY(launch(h, k_dual_stage, g.nstage, sd, gst, g, x, u, sd));
-    TRY(launch(h, k_dual_terminal, g.nprob, sw, gst, g, sw));
-    TRY(launch(h, k_dual_up, g.nslot, sw, gst, g, sw));
-    int src = 0;
-    for (int k = 0; k < gh.levels; k++, src ^= 1)
-      TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_DUAL_INCONSISTENT, sl));
-    TRY(launch(h, k_dual_down, g.nslot, sw, gst, g, src, sw));
-    TRY(launch(h, k_dual_root, g.nprob, sw, gst, g, sw));
-    TRY(aff_scan(h, gh, AFF_NU_, gst));
-    TRY(launch(h, k_dual_leaf, g.nstage, sf, gst, g, lam, mu, eta, alpha, sf));
+    gh.g.status = status;
+    TRY(run_mult(h, gh, gh.g, group_stream(h, gh, st), x, u, lam, mu, eta, alpha));
   }
   TRY(join_groups(h, st));
   return ECLQR_OK;
 }
 
-int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const double *u, const double *lam,
-                       const double *mu, const double *eta, const double *alpha, double *resid, void *stream) {
+namespace {
+int residual(eclqr_handle *h, const double *s0, const double *x, const double *u, const double *lam,
+             const double *mu, const double *eta, const double *alpha, double *resid, double *parts, void *stream) {
   if (!h || !s0 || !x || !u || !lam || !alpha || !resid) return ECLQR_EINVAL;
+  if (h->lay.mu > 0 && !mu) return ECLQR_EINVAL;
+  if (h->lay.eta > 0 && !eta) return ECLQR_EINVAL;
   if (!h->built) return ECLQR_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(resid, 0, sizeof(double) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
+  if (parts && cudaMemsetAsync(parts, 0, sizeof(double) * 4 * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
+  TRY(fork_groups(h, st));
+  for (auto &gh : h->groups) {
+    Group g = gh.g;
+    g.active = nullptr;
+    TRY(launch(h, k_kkt, g.nstage, 0, group_stream(h, gh, st), g, s0, x, u, lam, mu, eta, alpha, KktRows{},
+               resid, parts));
+  }
+  TRY(join_groups(h, st));
+  return ECLQR_OK;
+}
+}  // namespace
+
+int eclqr_kkt_residual(eclqr_handle *h, const double *s0, const double *x, const double *u, const double *lam,
+                       const double *mu, const double *eta, const double *alpha, double *resid, void *stream) {
+  return residual(h, s0, x, u, lam, mu, eta, alpha, resid, nullptr, stream);
+}
+
+int eclqr_kkt_residual_parts(eclqr_handle *h, const double *s0, const double *x, const double *u, const double *lam,
+                             const double *mu, const double *eta, const double *alpha, double *resid, double *parts,
+                             void *stream) {
+  if (!parts) return ECLQR_EINVAL;
+  return residual(h, s0, x, u, lam, mu, eta, alpha, resid, parts, stream);
+}
+
+int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double *lam, double *mu, double *eta,
+                 double *alpha, double *resid, int32_t *status, void *stream) {
+  if (!h || !s0 || !x || !u || !lam || !alpha || !resid || !status) return ECLQR_EINVAL;
+  if (h->lay.mu > 0 && !mu) return ECLQR_EINVAL;
+  if (h->lay.eta > 0 && !eta) return ECLQR_EINVAL;
+  if (!h->built || h->stale) return ECLQR_ESTATE;
+  TRY(residual(h, s0, x, u, lam, mu, eta, alpha, resid, nullptr, stream));
+  if (h->opt.kkt_refine == 0) return ECLQR_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Sol w{x, u, lam, mu, eta, alpha};
+  const SolMut &t = h->trial;
+  const Sol tc{t.x, t.u, t.lam, t.mu, t.eta, t.alpha};
   TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
     const cudaStream_t gst = group_stream(h, gh, st);
-    Group &g = gh.g;
-    TRY(launch(h, k_kkt_residual, g.nstage, 0, gst, g, s0, x, u, lam, mu, eta, alpha, resid));
+    Group g = gh.g;          // the problem's data, masked to the active problems
+    g.active = h->active;
+    g.status = h->cstatus;
+    Group gc = g;            // the correction problem: same matrices, residual rows as offsets
+    gc.c = h->rows.c; gc.d = h->rows.d; gc.e = h->rows.e; gc.qv = h->rows.qv; gc.rv = h->rows.rv;
+    Group gu = gh.g;         // unmasked, for the per-problem bookkeeping
+    gu.active = nullptr;
+    for (int k = 0; k < h->opt.kkt_refine; k++) {
+      TRY(launch(h, k_refine_prep, gu.nprob, 0, gst, gu, (const int32_t *)status, (const double *)resid, h->active,
+                 h->cstatus, h->tresid, h->opt.refine_tol, k == 0 ? 1 : 0));
+      TRY(launch(h, k_kkt, g.nstage, 0, gst, g, s0, (const double *)x, (const double *)u, (const double *)lam,
+                 (const double *)mu, (const double *)eta, (const double *)alpha, h->rows, (double *)nullptr,
+                 (double *)nullptr));
+      TRY(run_build(h, gh, gc, gst, false));
+      TRY(run_solve(h, gh, gc, gst, h->rows.s0, t.x, t.u));
+      TRY(run_mult(h, gh, gc, gst, t.x, t.u, t.lam, t.mu, t.eta, t.alpha));
+      TRY(launch(h, k_refine_gate, gu.nprob, 0, gst, gu, (const int32_t *)h->cstatus, h->active));
+      TRY(launch(h, k_refine_trial, g.nstage, 0, gst, g, w, t));
+      TRY(launch(h, k_kkt, g.nstage, 0, gst, g, s0, tc.x, tc.u, tc.lam, tc.mu, tc.eta, tc.alpha, KktRows{},
+                 h->tresid, (double *)nullptr));
+      TRY(launch(h, k_refine_accept, g.nstage, 0, gst, g, tc, x, u, lam, mu, eta, alpha, (const double *)resid,
+                 (const double *)h->tresid));
+      TRY(launch(h, k_refine_post, gu.nprob, 0, gst, gu, resid, (const double *)h->tresid, h->active));
+    }
   }
   TRY(join_groups(h, st));
+  h->stale = true;
+  h->solved = false;
   return ECLQR_OK;
 }
 
@@ -570,10 +698,12 @@ int eclqr_set_costs(eclqr_handle *h, const eclqr_data *data, void *stream) {
     Group &g = gh.g;
     g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
     g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
+    g.active = nullptr;
     TRY(launch(h, k_set_costs, g.nstage, 0, group_stream(h, gh, st), g, 0));
   }
   TRY(join_groups(h, st));
   h->solved = false;
+  h->stale = false;
   return ECLQR_OK;
 }
 
@@ -630,6 +760,7 @@ void eclqr_destroy(eclqr_handle *h) {
     if (gh.done) cudaEventDestroy(gh.done);
   }
   if (h->fork) cudaEventDestroy(h->fork);
+  if (h->rmem) cudaFree(h->rmem);
   for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
 }
@@ -653,7 +784,11 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
       {"k_recover", (const void *)k_recover}, {"k_dual_stage", (const void *)k_dual_stage},
       {"k_dual_terminal", (const void *)k_dual_terminal}, {"k_dual_up", (const void *)k_dual_up},
       {"k_dual_down", (const void *)k_dual_down}, {"k_dual_root", (const void *)k_dual_root},
-      {"k_dual_leaf", (const void *)k_dual_leaf}, {"k_kkt_residual", (const void *)k_kkt_residual}, {"k_param_grads", (const void *)k_param_grads}, {"k_set_costs", (const void *)k_set_costs}};
+      {"k_dual_leaf", (const void *)k_dual_leaf}, {"k_kkt", (const void *)k_kkt},
+      {"k_param_grads", (const void *)k_param_grads}, {"k_set_costs", (const void *)k_set_costs},
+      {"k_check_inputs", (const void *)k_check_inputs}, {"k_refine_prep", (const void *)k_refine_prep},
+      {"k_refine_gate", (const void *)k_refine_gate}, {"k_refine_trial", (const void *)k_refine_trial},
+      {"k_refine_accept", (const void *)k_refine_accept}, {"k_refine_post", (const void *)k_refine_post}};
   for (const auto &e : table)
     if (std::strcmp(e.name, name) == 0) {
       if (h->ev.empty()) {

@@ -19,6 +19,11 @@
 // leaf solves for (mu_i, eta_i).  Since ||lambda_i||^2 = ||pi_i||^2 + ||nu_i||^2
 // this is the min-norm representative of the sequential variant of Sec. 7,
 // without propagating the tangential part of lambda through the horizon.
+// A dual relation that reads 0 = gamma != 0 cannot arise in exact arithmetic
+// (the KKT conditions of a feasible problem with linear equality constraints
+// have a solution); where rounding produces one, the projection drops the row
+// like a redundant one and the pass goes on, leaving the judgement to the KKT
+// residual and the refinement on it (eclqr_refine).
 #include "kernels.cuh"
 
 namespace eclqr {
@@ -47,6 +52,7 @@ __global__ void k_dual_stage(Group g, const double *x, const double *u, int per_
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
@@ -177,6 +183,7 @@ __global__ void k_dual_terminal(Group g, int per_task) {
   const int t = team_task();
   if (t >= g.nprob) return;
   const ProbInfo &P = g.prob[t];
+  if (skipped_by_mask(g, t)) return;
   const int n = g.n, tid = team_rank();
   const int s = P.st0 + P.N;
   const StageInfo S = g.st[s];
@@ -209,7 +216,6 @@ __global__ void k_dual_terminal(Group g, int per_task) {
     wi[SI_NUROWS] = pr.krank;
     int *cm = g.CI[0] + (size_t)slot * CI_STRIDE;
     cm[CI_ROWS] = pr.krank; cm[CI_NA] = rN; cm[CI_NB] = 0;
-    if (pr.inconsistent) set_status(g, t, ST_DUAL_INCONSISTENT);
   }
 }
 
@@ -219,6 +225,7 @@ __global__ void k_dual_up(Group g, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   if (P.nch == 1) {  // one chunk: k_dual_down starts from the terminal set alone
@@ -262,7 +269,6 @@ __global__ void k_dual_up(Group g, int per_task) {
     const int gs[2] = {w, r1};
     ProjResult pr = wproject(M, ldm, rows + rr, 2, gs, r0 + rb, g.tau_rank, g.tau_inc, Rel, ldr, scr);
     rr = pr.krank;
-    if (pr.inconsistent && tid == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
     tsync();
   }
   double *cs = g.CS[0] + (size_t)t * g.cs_stride;
@@ -279,6 +285,7 @@ __global__ void k_dual_down(Group g, int fin, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
@@ -324,7 +331,6 @@ __global__ void k_dual_down(Group g, int fin, int per_task) {
       const int gs1[1] = {w};
       ProjResult p1 = wproject(M, ldm, rows2 + rr, 1, gs1, r1 + r0, g.tau_rank, g.tau_inc, K, ldr, scr);
       const int kr = p1.krank;
-      if (p1.inconsistent && tid == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
       // forward map: nu_{i+1} = -Kn^+ (L nu_i + l)
       double *Pnu = ws + g.ws.Pnu, *pnu = ws + g.ws.pnu;
       {
@@ -345,7 +351,6 @@ __global__ void k_dual_down(Group g, int fin, int per_task) {
       const int gs2[1] = {r1};
       ProjResult p2 = wproject(M, r1 + r0 + 1, kr, 1, gs2, r0, g.tau_rank, g.tau_inc, Ns, ldr, scr);
       rr = p2.krank;
-      if (p2.inconsistent && tid == 0) set_status(g, ci.prob, ST_DUAL_INCONSISTENT);
       double *NH = ws + g.ws.NH;
       for (int idx = tid; idx < rr * (r0 + 1); idx += TEAM) {
         int r = idx / (r0 + 1), j = idx - r * (r0 + 1);
@@ -362,6 +367,7 @@ __global__ void k_dual_root(Group g, int per_task) {
   const int t = team_task();
   if (t >= g.nprob) return;
   const ProbInfo &P = g.prob[t];
+  if (skipped_by_mask(g, t)) return;
   const int n = g.n, tid = team_rank();
   const int s = P.st0;
   double *ws = stage_ws(g, s);
@@ -385,6 +391,7 @@ __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, doubl
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   const double *ws = stage_ws(g, s);
   const int r0 = stage_wi(g, s)[SI_UR], nb = n - r0;
@@ -392,13 +399,16 @@ __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, doubl
   const double *nu0 = ws + g.ws.nu;
   // lambda_i = T_i pi_i + U_i nu_i
   const double *UT = ws + g.ws.UT, *pi = ws + g.ws.pi;
+  bool bad = false;
   for (int a = tid; a < n; a += TEAM) {
     double v = 0.0;
     for (int j = 0; j < r0; j++) v = fma(UT[a * n + j], nu0[j], v);
     for (int j = 0; j < nb; j++) v = fma(UT[a * n + r0 + j], pi[j], v);
     lam[P.olam + (size_t)i * n + a] = v;
     if (i == 0) alpha[P.oalpha + a] = -v;
+    bad = bad || !isfinite(v);
   }
+  if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
   const int w = (i < P.N) ? S.p + S.q : S.q;
   if (w == 0) return;
   double *sm = team_smem(per_task);
@@ -441,37 +451,75 @@ __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, doubl
   tsync();
   const int rank = wtqr(F, w, rows, w, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qf, wmax, perm, tq);
   wtqr_solve(Wt, (rows > 0 ? rows : 1), Qf, wmax, perm, rows, w, rank, rhs, 1, 1, X, 1, Ys, 1);
+  bad = false;
   if (i < P.N) {
     for (int j = tid; j < S.p; j += TEAM) mu[P.omu + S.prow + j] = X[j];
     for (int j = tid; j < S.q; j += TEAM) eta[P.oeta + S.qrow + j] = X[S.p + j];
   } else {
     for (int j = tid; j < S.q; j += TEAM) eta[P.oeta + S.qrow + j] = X[j];
   }
+  for (int j = tid; j < w; j += TEAM) bad = bad || !isfinite(X[j]);
+  if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
 }
 
 // ---------------------------------------------------------------- KKT residual (Sec. 9 definition)
+// Values reduced here are magnitudes or NaN.  The bit pattern of a non-negative
+// double orders like its value, and a positive NaN's pattern is above +inf's, so
+// an integer maximum over the patterns is a maximum that keeps NaN (fmax drops it).
+__device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
+
+__device__ __forceinline__ double team_max_keep_nan(double v) {
+  __shared__ long long red_bits[32];
+  long long k = __double_as_longlong(fabs(v));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) k = max(k, __shfl_xor_sync(kFull, k, o));
+  if ((threadIdx.x & 31) == 0) red_bits[threadIdx.x >> 5] = k;
+  __syncthreads();
+  long long r = red_bits[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) r = max(r, red_bits[w]);
+  __syncthreads();
+  return __longlong_as_double(r);
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void k_kkt_residual(Group g, const double *s0, const double *x, const double *u, const double *lam,
-                               const double *mu, const double *eta, const double *alpha, double *resid) {
+// One stage of the residual rows (Sec. 7 sign convention, lambda_0 = -alpha):
+//   x_0 - s_0;  A x + B u + c - x';  C x + D u + d;  E x + e;
+//   Q x + M u + q + A' lam' - lam + C' mu + E' eta;  M' x + R u + r + B' lam' + D' mu
+// (stage N: Q_N x_N + q_N - lam_N + E_N' eta_N).  With rows set, the rows are
+// written in the layout of the offsets they replace in a correction problem
+// (c, d, e, qv, rv, and s0 = -(x_0 - s_0)); with resid set, the Sec. 9 norm
+// (equality rows divided by max(1, largest |coefficient|, |offset|)) is reduced
+// into resid[id] and, with parts set, into parts[4 id + k] for k = initial,
+// dynamics, equalities, stationarity.  Any NaN in a row reaches the norm.
+__global__ void k_kkt(Group g, const double *s0, const double *x, const double *u, const double *lam,
+                      const double *mu, const double *eta, const double *alpha, KktRows rows, double *resid,
+                      double *parts) {
   const int s = team_task();
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+  const bool wr = rows.c != nullptr;
   const double *xi = x + P.ox + (size_t)i * n, *li = lam + P.olam + (size_t)i * n;
   const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
-  double r = 0.0;
+  double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
   if (i == 0)
-    for (int a = tid; a < n; a += TEAM) r = fmax(r, fabs(xi[a] - s0[P.os0 + a]));
+    for (int a = tid; a < n; a += TEAM) {
+      const double v = xi[a] - s0[P.os0 + a];
+      r0 = nanmax(r0, fabs(v));
+      if (wr) rows.s0[P.os0 + a] = -v;
+    }
   // state-only rows, normalised
   for (int k = tid; k < S.q; k += TEAM) {
     const double *Ek = g.E + P.oE + (size_t)(S.qrow + k) * n;
-    double e = g.e[P.oe + S.qrow + k], v = e, sc = fmax(1.0, fabs(e));
-    for (int j = 0; j < n; j++) { v = fma(Ek[j], xi[j], v); sc = fmax(sc, fabs(Ek[j])); }
-    r = fmax(r, fabs(v) / sc);
+    double e = g.e[P.oe + S.qrow + k], v = e, sc = nanmax(1.0, fabs(e));
+    for (int j = 0; j < n; j++) { v = fma(Ek[j], xi[j], v); sc = nanmax(sc, fabs(Ek[j])); }
+    r2 = nanmax(r2, fabs(v) / sc);
+    if (wr) rows.e[P.oe + S.qrow + k] = v;
   }
   const double *etai = eta + P.oeta + S.qrow;
   if (i < P.N) {
@@ -485,14 +533,16 @@ __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const
       double v = c[a] - xn[a];
       for (int j = 0; j < n; j++) v = fma(A[a * n + j], xi[j], v);
       for (int j = 0; j < m; j++) v = fma(B[a * m + j], ui[j], v);
-      r = fmax(r, fabs(v));
+      r1 = nanmax(r1, fabs(v));
+      if (wr) rows.c[P.oc + (size_t)i * n + a] = v;
     }
     for (int k = tid; k < S.p; k += TEAM) {
       const double *Ck = g.C + P.oC + (size_t)(S.prow + k) * n, *Dk = g.D + P.oD + (size_t)(S.prow + k) * m;
-      double dd = g.d[P.od + S.prow + k], v = dd, sc = fmax(1.0, fabs(dd));
-      for (int j = 0; j < n; j++) { v = fma(Ck[j], xi[j], v); sc = fmax(sc, fabs(Ck[j])); }
-      for (int j = 0; j < m; j++) { v = fma(Dk[j], ui[j], v); sc = fmax(sc, fabs(Dk[j])); }
-      r = fmax(r, fabs(v) / sc);
+      double dd = g.d[P.od + S.prow + k], v = dd, sc = nanmax(1.0, fabs(dd));
+      for (int j = 0; j < n; j++) { v = fma(Ck[j], xi[j], v); sc = nanmax(sc, fabs(Ck[j])); }
+      for (int j = 0; j < m; j++) { v = fma(Dk[j], ui[j], v); sc = nanmax(sc, fabs(Dk[j])); }
+      r2 = nanmax(r2, fabs(v) / sc);
+      if (wr) rows.d[P.od + S.prow + k] = v;
     }
     for (int a = tid; a < m; a += TEAM) {
       double v = rv[a];
@@ -500,7 +550,8 @@ __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const
       for (int j = 0; j < m; j++) v = fma(R[a * m + j], ui[j], v);
       for (int j = 0; j < n; j++) v = fma(B[j * m + a], ln[j], v);
       for (int k = 0; k < S.p; k++) v = fma(g.D[P.oD + (size_t)(S.prow + k) * m + a], mui[k], v);
-      r = fmax(r, fabs(v));
+      r3 = nanmax(r3, fabs(v));
+      if (wr) rows.rv[P.orv + (size_t)i * m + a] = v;
     }
     for (int a = tid; a < n; a += TEAM) {
       double v = q[a] + ((i == 0) ? alpha[P.oalpha + a] : -li[a]);
@@ -509,18 +560,36 @@ __global__ void k_kkt_residual(Group g, const double *s0, const double *x, const
       for (int j = 0; j < n; j++) v = fma(A[j * n + a], ln[j], v);
       for (int k = 0; k < S.p; k++) v = fma(g.C[P.oC + (size_t)(S.prow + k) * n + a], mui[k], v);
       for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
-      r = fmax(r, fabs(v));
+      r3 = nanmax(r3, fabs(v));
+      if (wr) rows.qv[P.oqv + (size_t)i * n + a] = v;
     }
   } else {
     for (int a = tid; a < n; a += TEAM) {
       double v = q[a] - li[a];
       for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
       for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
-      r = fmax(r, fabs(v));
+      r3 = nanmax(r3, fabs(v));
+      if (wr) rows.qv[P.oqv + (size_t)i * n + a] = v;
     }
   }
-  r = team_max(r);
-  if (tid == 0) atomic_max_nonneg(resid + P.id, r);
+  if (resid == nullptr) return;
+  if (parts != nullptr) {
+    r0 = team_max_keep_nan(r0);
+    r1 = team_max_keep_nan(r1);
+    r2 = team_max_keep_nan(r2);
+    r3 = team_max_keep_nan(r3);
+    if (tid == 0) {
+      double *pp = parts + 4 * (size_t)P.id;
+      atomic_max_nonneg(pp + 0, r0);
+      atomic_max_nonneg(pp + 1, r1);
+      atomic_max_nonneg(pp + 2, r2);
+      atomic_max_nonneg(pp + 3, r3);
+      atomic_max_nonneg(resid + P.id, nanmax(nanmax(r0, r1), nanmax(r2, r3)));
+    }
+  } else {
+    const double r = team_max_keep_nan(nanmax(nanmax(r0, r1), nanmax(r2, r3)));
+    if (tid == 0) atomic_max_nonneg(resid + P.id, r);
+  }
 }
 
 }  // namespace eclqr

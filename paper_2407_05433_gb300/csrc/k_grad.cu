@@ -24,6 +24,7 @@ __global__ void k_param_grads(Group g, Sol w, Sol wb, GradOut o) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   const double *xi = w.x + P.ox + (size_t)i * n, *xbi = wb.x + P.ox + (size_t)i * n;
   if (i < P.N) {
@@ -93,6 +94,7 @@ __global__ void k_set_costs(Group g, int per_task) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);

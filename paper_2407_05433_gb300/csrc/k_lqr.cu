@@ -51,6 +51,7 @@ __global__ void k_lqr_up(Group g, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int ldr = 2 * n + 1;
   double *slot = g.CS[0] + (size_t)t * g.cs_stride;
@@ -158,6 +159,7 @@ __global__ void k_lqr_level(Group g, int src, int d, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   const int n = g.n, tid = team_rank(), ldr = 2 * n + 1;
   double *S1 = g.CS[src] + (size_t)t * g.cs_stride;
   const int *I1 = g.CI[src] + (size_t)t * CI_STRIDE;
@@ -219,6 +221,7 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
@@ -416,6 +419,7 @@ __global__ void k_aff_up(Group g, int mode, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   const int n = g.n, tid = team_rank();
   const bool fwd = aff_forward(mode);
   double *cs0 = g.CS[0];
@@ -504,6 +508,7 @@ __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   const int n = g.n, tid = team_rank(), sz = n * n + n;
   const int j = t - P.ch0;  // slot index 0..nch
   const double *S0 = g.CS[src] + (size_t)t * g.cs_stride;
@@ -564,6 +569,7 @@ __global__ void k_aff_down(Group g, int mode, int fin, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   if (ci.c >= P.nch) return;
   const int n = g.n, tid = team_rank();
   const bool fwd = aff_forward(mode);
@@ -628,6 +634,7 @@ __global__ void k_solve_init(Group g, const double *s0) {
   const int t = team_task();
   if (t >= g.nprob) return;
   const ProbInfo &P = g.prob[t];
+  if (skipped_by_mask(g, t)) return;
   const int n = g.n, tid = team_rank();
   const int s = P.st0;
   double *ws = stage_ws(g, s);
@@ -642,7 +649,14 @@ __global__ void k_solve_init(Group g, const double *s0) {
     for (int l = 0; l < n; l++) v = fma(H[a * (n + 1) + l], x0[l], v);
     worst = fmax(worst, fabs(v));
   }
-  for (int l = tid; l < n; l += TEAM) om = fmax(om, fabs(x0[l]));
+  bool bad = false;
+  for (int l = tid; l < n; l += TEAM) {
+    om = fmax(om, fabs(x0[l]));
+    bad = bad || !isfinite(x0[l]);
+  }
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) set_status(g, t, ST_NONFINITE);
+  }
   worst = team_max(worst);
   om = fmax(1.0, team_max(om));
   if (tid == 0 && worst > g.tau_inc * om) set_status(g, t, ST_INFEASIBLE_X0);
@@ -661,6 +675,7 @@ __global__ void k_post_roll(Group g, int corr) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank();
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
@@ -702,6 +717,7 @@ __global__ void k_resid(Group g, int per_task) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
@@ -782,6 +798,7 @@ __global__ void k_pcorr(Group g, int per_task) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   if (S.i >= P.N) return;
   const int n = g.n, m = g.m, tid = team_rank();
   double *ws = stage_ws(g, s);
@@ -824,15 +841,18 @@ __global__ void k_recover(Group g, double *x, double *u) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const double *ws = stage_ws(g, s);
   const int *wi = stage_wi(g, s);
   const int ur = wi[SI_UR], nb = n - ur;
   const double *T = ws + g.ws.UT + ur, *z = ws + g.ws.z;
+  bool bad = false;
   for (int a = tid; a < n; a += TEAM) {
     double v = ws[g.ws.t + a];
     for (int j = 0; j < nb; j++) v = fma(T[a * n + j], z[j], v);
     x[P.ox + (size_t)S.i * n + a] = v;
+    bad = bad || !isfinite(v);
   }
   if (S.i < P.N) {
     const int mb = wi[SI_MBAR];
@@ -842,8 +862,10 @@ __global__ void k_recover(Group g, double *x, double *u) {
       for (int j = 0; j < nb; j++) v = fma(Y[a * n + j], z[j], v);
       for (int j = 0; j < mb; j++) v = fma(Z[a * m + j], vv[j], v);
       u[P.ou + (size_t)S.i * m + a] = v;
+      bad = bad || !isfinite(v);
     }
   }
+  if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
 }
 
 }  // namespace eclqr
@@ -856,6 +878,7 @@ __global__ void k_dims(Group g, int *nbar, int *mbar) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int *wi = stage_wi(g, s);
   nbar[P.ost + S.i] = wi[SI_NBAR];
   if (S.i < P.N) mbar[P.ost - P.id + S.i] = wi[SI_MBAR];

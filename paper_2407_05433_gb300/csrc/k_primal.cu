@@ -49,6 +49,7 @@ __global__ void k_scan_check(Group g, int per_task) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   if (!P.skip_ok || S.i >= P.N || S.p == 0) return;
   const int n = g.n, m = g.m, tid = team_rank(), ld = m + n + 1;
   double *sm = team_smem(per_task);
@@ -76,6 +77,7 @@ __global__ void k_terminal(Group g, int per_task) {
   const int t = team_task();
   if (t >= g.nprob) return;
   const ProbInfo &P = g.prob[t];
+  if (skipped_by_mask(g, t)) return;
   const int n = g.n, tid = team_rank();
   const int s = P.st0 + P.N;
   if (scan_skipped(g, t)) {  // X_N = R^n: no terminal rows
@@ -117,6 +119,7 @@ __global__ void k_primal_up(Group g, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   if (ci.c >= P.nch || scan_skipped(g, ci.prob)) return;
   const int n = g.n, m = g.m, tid = team_rank();
   if (P.nch == 1) {
@@ -196,6 +199,7 @@ __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   if (fail_code == ST_INFEASIBLE_SUFFIX && scan_skipped(g, ci.prob)) return;  // primal scan skipped
   const int tid = team_rank();
   const int ldr = 2 * g.n + 1;
@@ -237,7 +241,7 @@ __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task
   ProjResult pr = wproject(M, ldm, r1 + r2, 1, gs, na + nd, g.tau_rank, g.tau_inc, Dst, ldr, scr);
   if (tid == 0) {
     J[CI_ROWS] = pr.krank; J[CI_NA] = na; J[CI_NB] = nd;
-    if (pr.inconsistent) set_status(g, ci.prob, fail_code);
+    if (pr.inconsistent && fail_code != ST_OK) set_status(g, ci.prob, fail_code);
   }
 }
 
@@ -293,6 +297,7 @@ __global__ void k_primal_down(Group g, int fin, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
+  if (skipped_by_mask(g, ci.prob)) return;
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
@@ -338,6 +343,7 @@ __global__ void k_param(Group g, int per_task) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   const int n = g.n, tid = team_rank();
   double *ws = stage_ws(g, s);
   int *wi = stage_wi(g, s);
@@ -382,6 +388,7 @@ __global__ void k_elim(Group g, int per_task) {
   if (s >= g.nstage) return;
   const StageInfo S = g.st[s];
   const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
   if (S.i >= P.N) return;
   const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
   double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);

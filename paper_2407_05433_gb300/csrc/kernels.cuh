@@ -53,7 +53,18 @@ __global__ void k_dual_root(Group g, int per_task);
 __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task);
 __global__ void k_param_grads(Group g, Sol w, Sol wb, GradOut o);
 __global__ void k_set_costs(Group g, int per_task);
-__global__ void k_kkt_residual(Group g, const double *s0, const double *x, const double *u, const double *lam,
-                               const double *mu, const double *eta, const double *alpha, double *resid);
+__global__ void k_kkt(Group g, const double *s0, const double *x, const double *u, const double *lam,
+                      const double *mu, const double *eta, const double *alpha, KktRows rows, double *resid,
+                      double *parts);
+
+// refinement on the original KKT residual and non-finite checks (k_refine.cu)
+__global__ void k_check_inputs(Group g);
+__global__ void k_refine_prep(Group g, const int32_t *status, const double *resid, int *active, int32_t *cstatus,
+                              double *tresid, double tol, int first);
+__global__ void k_refine_gate(Group g, const int32_t *cstatus, int *active);
+__global__ void k_refine_trial(Group g, Sol w, SolMut t);
+__global__ void k_refine_accept(Group g, Sol t, double *x, double *u, double *lam, double *mu, double *eta,
+                                double *alpha, const double *resid, const double *tresid);
+__global__ void k_refine_post(Group g, double *resid, const double *tresid, int *active);
 
 }  // namespace eclqr

@@ -43,6 +43,12 @@ extern "C" int eclqr_kkt_residual_noalloc(const eclqr_desc *d, const eclqr_data 
   if (lay.eta > 0 && !eta) return ECLQR_EINVAL;
   const int P = d->num_problems;
   if (P > ECLQR_NOALLOC_MAX_PROBLEMS || lay.stages + P > ECLQR_NOALLOC_MAX_STAGES) return ECLQR_ETOOBIG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the descriptors reach the device by a copy from the host staging array, which
+  // the next call rewrites: a captured copy would replay whatever it then holds
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return ECLQR_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return ECLQR_ESTATE;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ECLQR_ECUDA;
   if (!d_noalloc_scratch[dev]) {
@@ -51,7 +57,6 @@ extern "C" int eclqr_kkt_residual_noalloc(const eclqr_desc *d, const eclqr_data 
     d_noalloc_scratch[dev] = p;
   }
   unsigned char *dbase = (unsigned char *)d_noalloc_scratch[dev];
-  cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(resid, 0, sizeof(double) * P, st) != cudaSuccess) return ECLQR_ECUDA;
 
   // descriptors: all problems, then their stages grouped by (n, m) as the kernel expects
@@ -127,7 +132,7 @@ extern "C" int eclqr_kkt_residual_noalloc(const eclqr_desc *d, const eclqr_data 
     g.st = (const StageInfo *)(dbase + kProbBytes) + launches[k].s0;
     g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
     g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
-    k_kkt_residual<<<g.nstage, 128, 0, st>>>(g, s0, x, u, lam, mu, eta, alpha, resid);
+    k_kkt<<<g.nstage, 128, 0, st>>>(g, s0, x, u, lam, mu, eta, alpha, KktRows{}, resid, nullptr);
     if (cudaPeekAtLastError() != cudaSuccess) return ECLQR_ECUDA;
   }
   return ECLQR_OK;

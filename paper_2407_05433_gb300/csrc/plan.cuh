@@ -118,6 +118,8 @@ struct Group {
   int cr_stride;
   int *status;    // batch-global, indexed by ProbInfo::id
   int *need_scan; // per problem: 1 once a stage leaves rows on x_i (set by k_scan_check)
+  const int *active;  // batch-global, indexed by ProbInfo::id; when set, every kernel skips
+                      // the tasks of problems whose entry is 0 (refinement passes)
   double tau_rank, tau_inc;
 };
 
@@ -125,12 +127,31 @@ struct Group {
 struct Sol {
   const double *x, *u, *lam, *mu, *eta, *alpha;
 };
+struct SolMut {
+  double *x, *u, *lam, *mu, *eta, *alpha;
+};
+// residual rows of the KKT system, written where a correction problem keeps the
+// offsets they replace (any pointer null: rows not written)
+struct KktRows {
+  double *c, *d, *e, *qv, *rv, *s0;
+};
 struct GradOut {
   double *A, *B, *c, *C, *D, *d, *E, *e, *Q, *M, *R, *qv, *rv, *s0;
 };
 
 __device__ __forceinline__ void set_status(const Group &g, int prob, int code) {
   atomicCAS(g.status + g.prob[prob].id, 0, code);
+}
+
+// true when a refinement pass leaves this problem (group-local index) alone
+__device__ __forceinline__ bool skipped_by_mask(const Group &g, int prob) {
+  return g.active != nullptr && g.active[g.prob[prob].id] == 0;
+}
+
+__device__ __forceinline__ bool all_finite(const double *a, int k) {
+  bool ok = true;
+  for (int j = 0; j < k; j++) ok = ok && isfinite(a[j]);
+  return ok;
 }
 
 // Sec. 6 shortcut: X_i = R^n for every stage of the problem, so its
@@ -152,7 +173,7 @@ __device__ __forceinline__ double *team_smem(int /*per_task*/) { return g_smem; 
 // status codes (mirror include/eclqr.h)
 enum {
   ST_OK = 0, ST_INFEASIBLE_SUFFIX = 1, ST_INFEASIBLE_X0 = 2, ST_RANK_INCONSISTENT = 3,
-  ST_NONCONVEX = 4, ST_DUAL_INCONSISTENT = 5
+  ST_NONCONVEX = 4, ST_NONFINITE = 6
 };
 
 }  // namespace eclqr

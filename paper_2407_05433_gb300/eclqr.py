@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libeclqr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETOOBIG, ESMEM = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "ok", 1: "infeasible_suffix", 2: "infeasible_x0", 3: "rank_inconsistent",
-                4: "nonconvex", 5: "dual_inconsistent"}
+                4: "nonconvex", 6: "nonfinite"}
 
 
 class eclqr_desc(ct.Structure):
@@ -38,7 +38,8 @@ class eclqr_grads(ct.Structure):
 
 class eclqr_options(ct.Structure):
     _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int32), ("chunk", ct.c_int32),
-                ("team_warps", ct.c_int32), ("scan_skip", ct.c_int32)]
+                ("team_warps", ct.c_int32), ("scan_skip", ct.c_int32), ("kkt_refine", ct.c_int32),
+                ("refine_tol", ct.c_double)]
 
 
 LAYOUT_FIELDS = ("A", "B", "c", "C", "D", "d", "E", "e", "Q", "M", "R", "qv", "rv", "s0",
@@ -75,6 +76,10 @@ def load():
     lib.eclqr_multipliers.restype = i32
     lib.eclqr_kkt_residual.argtypes = [vp] * 10
     lib.eclqr_kkt_residual.restype = i32
+    lib.eclqr_kkt_residual_parts.argtypes = [vp] * 11
+    lib.eclqr_kkt_residual_parts.restype = i32
+    lib.eclqr_refine.argtypes = [vp] * 11
+    lib.eclqr_refine.restype = i32
     lib.eclqr_reduced_dims.argtypes = [vp, vp, vp, vp]
     lib.eclqr_reduced_dims.restype = i32
     lib.eclqr_scan_skipped.argtypes = [vp, vp, vp]
@@ -139,6 +144,14 @@ def eclqr_multipliers(h, x, u, lam, mu, eta, alpha, status, stream):
 
 def eclqr_kkt_residual(h, s0, x, u, lam, mu, eta, alpha, resid, stream):
     return load().eclqr_kkt_residual(h, s0, x, u, lam, mu, eta, alpha, resid, stream)
+
+
+def eclqr_kkt_residual_parts(h, s0, x, u, lam, mu, eta, alpha, resid, parts, stream):
+    return load().eclqr_kkt_residual_parts(h, s0, x, u, lam, mu, eta, alpha, resid, parts, stream)
+
+
+def eclqr_refine(h, s0, x, u, lam, mu, eta, alpha, resid, status, stream):
+    return load().eclqr_refine(h, s0, x, u, lam, mu, eta, alpha, resid, status, stream)
 
 
 def eclqr_kkt_residual_noalloc(desc, data, s0, x, u, lam, mu, eta, alpha, resid, stream):
@@ -222,7 +235,7 @@ class Batch:
     """A batch of problems resident on one CUDA device, solved through the C ABI."""
 
     def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=2, chunk=0, team_warps=0,
-                 scan_skip=1):
+                 scan_skip=1, kkt_refine=8, refine_tol=5e-10):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -235,6 +248,7 @@ class Batch:
         opt.tau_rank, opt.tau_inc, opt.refine, opt.chunk = tau_rank, tau_inc, refine, chunk
         opt.team_warps = team_warps
         opt.scan_skip = scan_skip
+        opt.kkt_refine, opt.refine_tol = kkt_refine, refine_tol
         with torch.cuda.device(self.device):
             rc, self.h = eclqr_create(self.desc, opt)
         _check(rc, "eclqr_create")
@@ -254,33 +268,68 @@ class Batch:
     def _stream(self):
         return ct.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream)
 
+    def invalidate(self):
+        """Marks the handle as holding another build than this Batch's own data (autograd builds on
+        copies of the data): solve, multipliers, refine and residual then raise until build()."""
+        self._own_build = False
+
+    def _require_own_build(self, what):
+        if not getattr(self, "_own_build", False):
+            raise RuntimeError(f"{what}: the handle does not hold a build of this Batch's data; call build() first")
+
     def build(self):
         _check(eclqr_build(self.h, self.data, self.status.data_ptr(), self._stream()), "eclqr_build")
+        self._own_build = True
 
     def solve(self, s0=None):
+        self._require_own_build("solve")
         s0 = self.d["s0"] if s0 is None else s0
         _check(eclqr_solve(self.h, s0.data_ptr(), self.x.data_ptr(), self.u.data_ptr(), self.status.data_ptr(),
                            self._stream()), "eclqr_solve")
 
     def multipliers(self):
+        self._require_own_build("multipliers")
         _check(eclqr_multipliers(self.h, self.x.data_ptr(), self.u.data_ptr(), self.lam.data_ptr(),
                                  self.mu.data_ptr(), self.eta.data_ptr(), self.alpha.data_ptr(),
                                  self.status.data_ptr(), self._stream()), "eclqr_multipliers")
 
     def residual(self, s0=None):
+        self._require_own_build("residual")
         s0 = self.d["s0"] if s0 is None else s0
         _check(eclqr_kkt_residual(self.h, s0.data_ptr(), self.x.data_ptr(), self.u.data_ptr(),
                                   self.lam.data_ptr(), self.mu.data_ptr(), self.eta.data_ptr(),
                                   self.alpha.data_ptr(), self.resid.data_ptr(), self._stream()),
                "eclqr_kkt_residual")
 
+    def residual_parts(self, s0=None):
+        """Per problem the four parts of the Sec. 9 residual (initial condition, dynamics, normalised
+        equality rows, stationarity) as a numpy (P, 4) array; also refreshes self.resid."""
+        self._require_own_build("residual_parts")
+        s0 = self.d["s0"] if s0 is None else s0
+        parts = self.torch.zeros(4 * len(self.problems), dtype=self.torch.float64, device=self.device)
+        _check(eclqr_kkt_residual_parts(self.h, s0.data_ptr(), self.x.data_ptr(), self.u.data_ptr(),
+                                        self.lam.data_ptr(), self.mu.data_ptr(), self.eta.data_ptr(),
+                                        self.alpha.data_ptr(), self.resid.data_ptr(), parts.data_ptr(),
+                                        self._stream()), "eclqr_kkt_residual_parts")
+        return parts.cpu().numpy().reshape(-1, 4)
+
+    def refine(self, s0=None):
+        """Refinement on the original KKT residual (eclqr_refine); leaves the residual in self.resid."""
+        self._require_own_build("refine")
+        s0 = self.d["s0"] if s0 is None else s0
+        _check(eclqr_refine(self.h, s0.data_ptr(), self.x.data_ptr(), self.u.data_ptr(), self.lam.data_ptr(),
+                            self.mu.data_ptr(), self.eta.data_ptr(), self.alpha.data_ptr(), self.resid.data_ptr(),
+                            self.status.data_ptr(), self._stream()), "eclqr_refine")
+
     def run(self, multipliers=True, residual=True):
+        """One pass of the path: build, solve and, with multipliers, the multipliers and the refinement
+        on the original KKT residual, which leaves the Sec. 9 residual in self.resid."""
         self.build()
         self.solve()
         if multipliers:
             self.multipliers()
         if residual and multipliers:
-            self.residual()
+            self.refine()
 
     def capture(self):
         """Capture one full pass (build, solve, multipliers, residual) into a CUDA graph.

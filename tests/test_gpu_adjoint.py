@@ -106,3 +106,29 @@ def test_adjoint_on_reused_factors_matches_rebuilt_adjoint():
     finally:
         ag.ECLQRSolve.reuse_factors = True
         batch.close()
+
+
+def test_batch_refuses_its_own_calls_after_autograd_until_rebuilt():
+    """autograd builds the handle on copies of the data (and backward points it at the adjoint's
+    arrays), which are freed with the graph: the Batch's own solve and residual refuse to run on
+    those pointers, and after build() they give the oracle's solution again."""
+    import gc
+    torch, ag, pbs, batch, xrefs, xref, params = _setup()
+    try:
+        _loss(torch, ag, batch, xref, params).backward()
+        del params
+        gc.collect()
+        torch.cuda.empty_cache()
+        for call in (batch.solve, batch.multipliers, batch.residual, batch.refine):
+            with pytest.raises(RuntimeError, match="build"):
+                call()
+        batch.run()
+        for pb, r in zip(pbs, batch.results()):
+            s = oracle.solve(pb)
+            assert r["status"] == 0 and r["resid"] <= 1e-9
+            for k in ("x", "u", "lam", "mu", "eta", "alpha"):
+                ref = getattr(s, k)
+                if ref.size:
+                    assert np.max(np.abs(r[k] - ref)) / max(1.0, np.max(np.abs(ref))) <= 1e-9, k
+    finally:
+        batch.close()

@@ -93,6 +93,9 @@ CLASSES = [
                                              dup_rows=[(0, 1), (6, 7)], zero_D_rows=[12])),
     ("one_stage", lambda: synth.make_problem(14, 1, 3, 2, 1, np.array([0, 1], np.int32))),
     ("two_stage", lambda: synth.make_problem(15, 2, 3, 2, 1, np.array([1, 0, 2], np.int32))),
+    # four state-only rows pin x_5 (nbar_5 = 0); the domains before it shrink to 3, 2, 1 and some mbar_i = 0
+    ("pinned_interior", lambda: synth.make_problem(21, 12, 4, 2, 1, np.r_[np.zeros(5, np.int32), 4,
+                                                                          np.zeros(6, np.int32), 2])),
 ]
 
 
@@ -309,3 +312,21 @@ def test_schedule_autotuner_returns_a_passing_pair():
     assert picked[2] == min(t[2] for t in trials if t[4])
     res, dims = gpu_run(pbs, chunk=chunk, team_warps=team)
     check(pbs[0], res[0], dims[0])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_stage_varying_dimensions(seed):
+    """Stage-varying n_i, m_i (Sec. 2) zero-padded into one (n, m) per problem (synth.pack_varying):
+    the padded problem against the oracle at 1e-9, and the padded coordinates of x, u, lambda and
+    alpha at zero."""
+    from test_oracle_pins import _varying_instance
+    v = _varying_instance(seed)
+    pb, dims = synth.pack_varying(**v)
+    (r,), (d,) = gpu_run([pb])
+    check(pb, r, d)
+    ni, mi = dims
+    for i in range(pb.N + 1):
+        assert np.all(r["x"][i, ni[i]:] == 0.0) or np.max(np.abs(r["x"][i, ni[i]:])) <= 1e-12
+        assert np.max(np.abs(r["lam"][i, ni[i]:]), initial=0.0) <= 1e-12
+    for i in range(pb.N):
+        assert np.max(np.abs(r["u"][i, mi[i]:]), initial=0.0) <= 1e-12

@@ -101,3 +101,45 @@ def test_noalloc_rejects_batches_beyond_its_array():
     h3, d3 = _desc([4])
     d3.num_problems = 0                                # invalid descriptors still read as EINVAL
     assert eclqr.eclqr_kkt_residual_noalloc(d3, data, *args, None) == eclqr.EINVAL
+
+
+@pytest.mark.gpu
+def test_noalloc_on_a_larger_then_a_smaller_different_batch():
+    """Each call rewrites the shared array for its own batch: a call on a larger batch, then on a
+    smaller batch of other shapes, each against the handle path on the same inputs."""
+    big = [synth.config("batched_uneven", index=j, N=30 + j) for j in range(6)] + [synth.config("table1", N=25)]
+    small = [synth.config("single_n4", N=9), synth.config("degenerate_n12", N=11)]
+    out = []
+    for pbs in (big, small):
+        batch = eclqr.Batch(pbs)
+        try:
+            batch.run()
+            ref = _handle(batch)
+            got = _noalloc(batch)
+            assert _close(got, ref), (got, ref)
+            out.append(got)
+        finally:
+            batch.close()
+    assert len(out[0]) == 7 and len(out[1]) == 2
+
+
+@pytest.mark.gpu
+def test_noalloc_refuses_a_capturing_stream():
+    """The descriptors are copied from a host array that the next call rewrites, so a graph would
+    replay stale descriptors: on a capturing stream the call returns ECLQR_ESTATE and enqueues nothing."""
+    import torch
+    batch = eclqr.Batch([synth.config("single_n4", N=9)])
+    try:
+        batch.run()
+        _noalloc(batch)
+        out = torch.zeros(1, dtype=torch.float64, device=batch.device)
+        g = torch.cuda.CUDAGraph()
+        rcs = []
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            rcs.append(eclqr.eclqr_kkt_residual_noalloc(
+                batch.desc, batch.data, batch.d["s0"].data_ptr(), batch.x.data_ptr(), batch.u.data_ptr(),
+                batch.lam.data_ptr(), batch.mu.data_ptr(), batch.eta.data_ptr(), batch.alpha.data_ptr(),
+                out.data_ptr(), batch._stream()))
+        assert rcs == [eclqr.ESTATE]
+    finally:
+        batch.close()
