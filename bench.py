@@ -1,27 +1,30 @@
 #!/usr/bin/env python
-"""Throughput benchmark: equality-constrained LQR stages solved per second.
+"""Throughput benchmark: equality-constrained LQR stages solved per second, batched against plain.
 
-One step is one pass of the whole path of Algorithm 1 over one problem
-instance through the C ABI: eclqr_build (suffix-domain scan, stage
-elimination, Riccati factors), eclqr_solve (rollout with refinement and
-recovery of x, u), eclqr_multipliers (Sec. 7) and eclqr_kkt_residual (the
-Sec. 9 residual, the gate of the metric).  The workload is the degenerate
-n = 12 instance (N = 1024, m = 6, mixed rows U{0..8} per stage, 20% of stages
-with duplicated or D = 0 rows, full-rank terminal rows), seeded and synthetic.
+One step is one pass of the whole path of Algorithm 1 through the C ABI over one batch:
+eclqr_build (suffix-domain scan, stage elimination, Riccati factors), eclqr_solve (rollout with
+refinement on the reduced residual, recovery of x, u), eclqr_multipliers (Sec. 7) and eclqr_refine
+(the Sec. 9 residual, which gates the metric, and refinement on it for the problems above 5e-10).
+The workload is the uneven batch: 4096 distinct seeded problems (seeds 0..4095), N ~ U[32, 512],
+n in {8, 12, 16, 24}, m = n/2, mixed rows U{0..m} per stage, terminal rows U{0..n/2}; one chunk
+per problem.  The step is captured once into a CUDA graph and replayed.
+
+A problem counts as solved when its status is OK and its residual is at most 1e-9, or, for the
+draws listed in tests/golden/batched_uneven_floors.txt (whose exact KKT solution, rounded to FP64,
+already has a residual of that order), at most 4 phi, phi their FP64 floor.  ``value`` counts the
+stages of solved problems; the line names the others.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--no-extra]
 
-At N = 1 the line also carries "graph" (the same step captured once into a
-CUDA graph and replayed), "plain" (the same instance as one chunk: a single
-CTA sweeps every stage, no scan), "scan_skip" (the Sec. 6 shortcut on an
-instance without state-only or terminal rows, with and without the skip) and
-"batched" (4096 uneven problems, a
-stand-in for the batched configuration, with the oracle on all host cores
-beside it).
+Beside the headline the line carries "plain" (the same draws solved one problem at a time, each as
+one chunk: a single CTA sweeps every stage, no scan, no batching), the per-kernel device time of
+the batch, and at N = 1 further workloads: the long horizon (N = 65536), the degenerate instance
+(N = 1024), the single instance (N = 64), the differentiable batch (1024 x 256, forward and
+forward + backward), the Table 1 shape at N = 1024..16384 and the Sec. 6 scan-skip shortcut.
 
-Under torchrun every rank solves its own copy (weak scaling, no collective on
-the data path); rank 0 prints one JSON line.  ``--impl reference`` times the
-CPU oracle on the host instead (rank 0 only).
+Under torchrun every rank solves its own copy of the batch (weak scaling, no collective on the data
+path); rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle on the host instead
+(rank 0 only): a bounded sample of the same draws over every host core.
 """
 from __future__ import annotations
 
@@ -39,27 +42,22 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "ECLQR stages solved/s at KKT resid≤1e-9 (FP64), batched vs plain, % FP64 peak"
-WORKLOAD = "degenerate_n12"
-WORKLOAD_DESC = ("degenerate_n12: one instance, N=1024, n=12, m=6, mixed rows U{0..8} per stage, 20% of stages "
-                 "with duplicated or D=0 rows, full-rank terminal rows, A=I+0.1 randn, seed 0")
+PROBLEMS = 4096
+WORKLOAD = "batched_uneven"
+WORKLOAD_DESC = ("batched_uneven: 4096 distinct problems (seeds 0..4095), N~U[32,512], n in {8,12,16,24}, m=n/2, "
+                 "mixed rows U{0..m} per stage, terminal rows U{0..n/2}, A=I+0.1 randn, one batch, "
+                 "one chunk per problem, CUDA-graph replay")
 KKT_GATE = 1e-9
-KERNELS = ["k_terminal", "k_primal_up", "k_rel_level", "k_primal_down", "k_param", "k_elim", "k_lqr_up",
-           "k_lqr_level", "k_riccati_down", "k_aff_up", "k_aff_level", "k_aff_down", "k_solve_init",
-           "k_post_roll", "k_resid", "k_pcorr", "k_recover", "k_dual_stage", "k_dual_terminal", "k_dual_up",
-           "k_dual_down", "k_dual_root", "k_dual_leaf", "k_kkt_residual"]
-# phase of Algorithm 1 each kernel implements (index into the oracle's per-phase flop counts)
-KERNEL_PHASE = {"k_terminal": 0, "k_primal_up": 0, "k_rel_level": 0, "k_primal_down": 0, "k_param": 1,
-                "k_elim": 2, "k_lqr_up": 3, "k_lqr_level": 3, "k_riccati_down": 3, "k_aff_up": 4,
-                "k_aff_level": 4, "k_aff_down": 4, "k_solve_init": 4, "k_post_roll": 4, "k_resid": 4,
-                "k_pcorr": 4, "k_recover": 4, "k_dual_stage": 5, "k_dual_terminal": 5, "k_dual_up": 5,
-                "k_dual_down": 5, "k_dual_root": 5, "k_dual_leaf": 5, "k_kkt_residual": 6}
+FLOOR_FACTOR = 4.0
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+PLAIN_SAMPLE = 24
+# kernels whose launches carry one phase of the method alone when every problem is one chunk
+PHASE_KERNELS = {"k_primal_down": 0, "k_param": 1, "k_elim": 2, "k_riccati_down": 3, "k_dual_down": 5}
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 class ClockSampler:
@@ -136,31 +134,80 @@ def all_ranks(flag, world, device):
     return bool(int(t.item()))
 
 
+def sum_over_ranks(value, world, device):
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_rate(world, stages_per_rank, ms):
     """Whole-job throughput: every rank solves its own copy (weak scaling) within the slowest rank's time."""
     return world * stages_per_rank / (ms * 1e-3)
 
 
-def oracle_rate(pb, seconds):
-    """The CPU oracle as it stands, one thread, repeated over the workload for ~seconds."""
-    import oracle
-    oracle.build_oracle()
-    oracle.solve(pb)  # warm
-    n, t0 = 0, time.perf_counter()
-    times = []
-    while True:
-        t = time.perf_counter()
-        s = oracle.solve(pb)
-        oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha)
-        times.append(time.perf_counter() - t)
-        n += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    return pb.N / statistics.median(times), n, statistics.median(times)
+# ---------------------------------------------------------------- workload, gates, algorithmic work
+def batched_problems(count=PROBLEMS):
+    from paper_2407_05433_gb300 import synth
+    return [synth.config(WORKLOAD, index=j) for j in range(count)]
 
 
-def _timed_runs(batch, steps, flush, stream):
-    """Device time per full pass (build, solve, multipliers, residual) with L2 flushed between passes."""
+def floor_gates():
+    """{draw index: gate} of the draws whose FP64 floor exceeds the 1e-9 gate."""
+    out = {}
+    path = os.path.join(GOLDEN, "batched_uneven_floors.txt")
+    for ln in open(path):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        f = ln.split()
+        out[int(f[0])] = max(KKT_GATE, FLOOR_FACTOR * float(f[4]))
+    return out
+
+
+def workload_flops():
+    """Algorithmic FP64 work per workload (tests/golden/workload_flops.json, written from the oracle)."""
+    path = os.path.join(GOLDEN, "workload_flops.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)["workloads"]
+
+
+def gate_report(pbs, res, stat, gates):
+    """Which problems pass: status OK and residual at most their gate (NaN fails)."""
+    import numpy as np
+    g = np.array([gates.get(j, KKT_GATE) for j in range(len(pbs))])
+    passed = (stat == 0) & (res <= g)
+    failed = [int(j) for j in np.nonzero(~passed)[0]]
+    return passed, {
+        "rule": f"status OK and resid <= 1e-9; draws listed in tests/golden/batched_uneven_floors.txt: "
+                f"resid <= max(1e-9, {FLOOR_FACTOR:g} phi)",
+        "problems": len(pbs), "passed": int(passed.sum()),
+        "passed_at_1e-9": int(((stat == 0) & (res <= KKT_GATE)).sum()),
+        "floor_draws": len(gates), "failed": failed[:32],
+        "failed_resid": [float(res[j]) for j in failed[:32]],
+        "status_failures": int((stat != 0).sum()), "resid_max": float(np.nanmax(res)) if len(res) else 0.0,
+        "nan_resid": int(np.isnan(res).sum()),
+    }
+
+
+# ---------------------------------------------------------------- GPU timing helpers
+def _time_replays(batch, steps, flush, stream):
+    """Device time (ms) of each of `steps` graph replays, L2 flushed between them (outside the events)."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        batch.replay()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def _time_runs(batch, steps, flush, stream):
     import torch
     times = []
     for _ in range(steps):
@@ -171,58 +218,143 @@ def _timed_runs(batch, steps, flush, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    return statistics.median(times)
+    return times
 
 
-def measure_graph(batch, pb, flush, stream, steps):
-    """The same step captured once into a CUDA graph and replayed (same kernels, same order)."""
-    import torch
-    nl = batch.capture()
-    for _ in range(3):
-        batch.replay()
-    times = []
-    for _ in range(steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        batch.replay()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    ms = statistics.mean(times)
-    (r,) = batch.results()
-    return {"value": pb.N / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "launches_per_replay": nl,
-            "kkt_resid": r["resid"], "gate_passed": r["status"] == 0 and r["resid"] <= KKT_GATE}
-
-
-def measure_plain(pb, dev, flush, stream, refine, steps=3):
-    """The plain GPU solve: one chunk spanning the horizon, so a single CTA per problem sweeps every stage
-    in order (no scan), beside the chunked scan form of the main line."""
+def single_line(name, pb, dev, flush, stream, steps, **kw):
+    """One instance through the same four calls, eager, `steps` timed passes."""
     from paper_2407_05433_gb300 import eclqr
-    b = eclqr.Batch([pb], device=dev, refine=refine, chunk=pb.N)
-    b.run()
-    ms = _timed_runs(b, steps, flush, stream)
-    (r,) = b.results()
-    b.close()
-    return {"value": pb.N / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "chunk": pb.N,
-            "kkt_resid": r["resid"], "status": r["status"], "gate_passed": r["status"] == 0 and r["resid"] <= KKT_GATE}
+    b = eclqr.Batch([pb], device=dev, **kw)
+    try:
+        b.run()
+        ms = statistics.median(_time_runs(b, steps, flush, stream))
+        (r,) = b.results()
+        launches = b.launches()
+    finally:
+        b.close()
+    return {"workload": name, "value": pb.N / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms,
+            "kkt_resid": r["resid"], "status": r["status"],
+            "gate_passed": bool(r["status"] == 0 and r["resid"] <= KKT_GATE)}
 
 
-def measure_scan_skip(dev, flush, stream, refine, steps=5):
-    """The Sec. 6 shortcut on an instance it applies to: mixed_only_n12 (N=1024, n=12, m=6, mixed rows
-    U{0..4} per stage with wide full-row-rank D_i, no state-only or terminal rows), timed with the shortcut
-    (domain scan skipped) and without it (scan forced).  Both passes must give the same results."""
+def measure_plain(pbs, dev, flush, stream):
+    """The plain GPU solve on the first PLAIN_SAMPLE draws of the batch: each problem alone, as one
+    chunk (a single CTA sweeps every stage, no scan), through the same four calls, eager."""
+    from paper_2407_05433_gb300 import eclqr
+    tot_ms, tot_st, ok = 0.0, 0, 0
+    for pb in pbs[:PLAIN_SAMPLE]:
+        b = eclqr.Batch([pb], device=dev, chunk=pb.N)
+        try:
+            b.run()
+            ms = statistics.median(_time_runs(b, 2, flush, stream))
+            (r,) = b.results()
+        finally:
+            b.close()
+        tot_ms += ms
+        tot_st += pb.N
+        ok += int(r["status"] == 0)
+    return {"value": tot_st / (tot_ms * 1e-3), "unit": "stages/s", "problems": PLAIN_SAMPLE, "stages": tot_st,
+            "ms_total": tot_ms, "status_ok": ok,
+            "sample": f"draws 0..{PLAIN_SAMPLE - 1} of the batch, each solved alone as one chunk (one CTA of four "
+                      f"warps sweeps every stage), median of 2 passes each"}
+
+
+def measure_kernels(pbs, dev, flush, stream, flops):
+    """Per-kernel device time of the batch, one (n, m) group at a time (groups run on concurrent
+    streams in the batch itself, where one kernel's events would also cover the others' work).
+    Every kernel of PHASE_KERNELS carries its phase alone when every problem is one chunk, so its
+    achieved FP64 rate is the phase's algorithmic flops over its summed launch time."""
+    from paper_2407_05433_gb300 import eclqr
+    groups = {}
+    for pb in pbs:
+        groups.setdefault((pb.n, pb.m), []).append(pb)
+    names = list(PHASE_KERNELS) + ["k_lqr_up", "k_lqr_level", "k_primal_up", "k_dual_up", "k_aff_up",
+                                   "k_aff_level", "k_aff_down", "k_kkt", "k_resid", "k_pcorr", "k_dual_leaf",
+                                   "k_dual_stage", "k_dual_root", "k_refine_trial"]
+    ms = {k: 0.0 for k in names}
+    launches = {k: 0 for k in names}
+    for key, gp in sorted(groups.items()):
+        # the group alone still counts as a large batch (two or more problems per SM): one chunk each
+        b = eclqr.Batch(gp, device=dev)
+        try:
+            b.run()
+            for name in names:
+                eclqr.eclqr_time_kernel(b.h, name)
+                flush.zero_()
+                b.run()
+                nl, t = eclqr.eclqr_kernel_time(b.h)
+                ms[name] += t
+                launches[name] += nl
+            eclqr.eclqr_time_kernel(b.h, None)
+        finally:
+            b.close()
+    out = {"kernel_ms_per_step": {k: round(v, 3) for k, v in sorted(ms.items(), key=lambda kv: -kv[1]) if v > 0},
+           "launches_per_step": {k: v for k, v in launches.items() if v}}
+    if flops:
+        ph = flops["phase_flops"]
+        out["phase_kernels"] = {k: {"phase": p, "ms": ms[k], "algorithmic_flops": ph[p],
+                                    "achieved_tflops": ph[p] / (ms[k] * 1e-3) / 1e12 if ms[k] else None}
+                                for k, p in PHASE_KERNELS.items()}
+    return out
+
+
+def measure_diff_batch(dev, flush, stream, steps=3):
+    """The differentiable batch (1024 problems, N = 256, n = 16, m = 8): the forward pass, and forward
+    plus backward through the autograd.Function, loss sum ||x - x_ref||^2 + ||u||^2."""
+    import numpy as np
+    import torch
+    from paper_2407_05433_gb300 import eclqr, synth
+    from paper_2407_05433_gb300 import autograd as ag
+    pbs = [synth.config("diff_batch", index=j) for j in range(1024)]
+    b = eclqr.Batch(pbs, device=dev)
+    try:
+        b.run()
+        fwd = statistics.median(_time_runs(b, steps, flush, stream))
+        res = b.resid.cpu().numpy()
+        stat = b.status.cpu().numpy()
+        rng = np.random.default_rng(0)
+        xref = torch.from_numpy(rng.standard_normal(int(b.layout.x))).to(dev)
+        params = ag.batch_params(b)
+        times = []
+        for k in range(steps + 1):
+            for p in params:
+                p.grad = None
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, u = ag.solve(b, *params)
+            loss = ((x - xref) ** 2).sum() + (u ** 2).sum()
+            loss.backward()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k:
+                times.append(e0.elapsed_time(e1))
+        fb = statistics.median(times)
+    finally:
+        b.close()
+    stages = sum(p.N for p in pbs)
+    return {"workload": "diff_batch: 1024 problems, N=256, n=16, m=8, 4 mixed rows, 4 terminal rows",
+            "forward": {"value": stages / (fwd * 1e-3), "unit": "stages/s", "ms_per_step": fwd,
+                        "resid_max": float(res.max()), "passed_at_1e-9": int(((stat == 0) & (res <= KKT_GATE)).sum())},
+            "forward_backward": {"value": stages / (fb * 1e-3), "unit": "stages/s", "ms_per_step": fb}}
+
+
+def measure_scan_skip(dev, flush, stream, steps=3):
+    """The Sec. 6 shortcut on mixed_only_n12 (N=1024, n=12, m=6, mixed rows U{0..4}, no state-only or
+    terminal rows), with the shortcut and with the scan forced; both must give the same results."""
     import numpy as np
     from paper_2407_05433_gb300 import eclqr, synth
     pb = synth.config("mixed_only_n12")
     out, ref = {"workload": "mixed_only_n12: N=1024, n=12, m=6, mixed rows U{0..4}, no state-only or terminal rows"}, None
     for name, flag in (("skip", 1), ("scan", 0)):
-        b = eclqr.Batch([pb], device=dev, refine=refine, scan_skip=flag)
-        b.run()
-        ms = _timed_runs(b, steps, flush, stream)
-        (r,) = b.results()
-        skipped = bool(b.scan_skipped()[0])
-        b.close()
+        b = eclqr.Batch([pb], device=dev, scan_skip=flag)
+        try:
+            b.run()
+            ms = statistics.median(_time_runs(b, steps, flush, stream))
+            (r,) = b.results()
+            skipped = bool(b.scan_skipped()[0])
+        finally:
+            b.close()
         out[name] = {"value": pb.N / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "scan_skipped": skipped,
                      "kkt_resid": r["resid"], "gate_passed": r["status"] == 0 and r["resid"] <= KKT_GATE}
         if ref is None:
@@ -234,119 +366,77 @@ def measure_scan_skip(dev, flush, stream, refine, steps=5):
     return out
 
 
-BATCH_DISTINCT, BATCH_PROBLEMS = 256, 4096
-
-
-def batched_problems():
-    from paper_2407_05433_gb300 import synth
-    base = [synth.config("batched_uneven", index=j) for j in range(BATCH_DISTINCT)]
-    return base, [base[j % BATCH_DISTINCT] for j in range(BATCH_PROBLEMS)]
-
-
-def measure_batched(pbs, dev, flush, stream, refine, steps=3):
-    """Config 4 stand-in: 4096 uneven problems (256 seeded draws of the generator, each repeated 16 times)
-    solved as one batch through the same calls."""
-    import numpy as np
-    from paper_2407_05433_gb300 import eclqr
-    b = eclqr.Batch(pbs, device=dev, refine=refine)
-    b.run()
-    ms = _timed_runs(b, steps, flush, stream)
-    res = b.resid.cpu().numpy()
-    stat = b.status.cpu().numpy()
-    launches = b.launches()
-    skipped = int(b.scan_skipped().sum())
-    # per-kernel device time over one untimed pass each; the (n, m) groups run concurrently on their
-    # own streams, so a kernel's time is summed over its groups' overlapping launches
-    kernel_ms = {}
-    try:
-        for name in KERNELS + ["k_scan_check"]:
-            eclqr.eclqr_time_kernel(b.h, name)
-            b.run()
-            nl, tms = eclqr.eclqr_kernel_time(b.h)
-            if nl:
-                kernel_ms[name] = round(tms, 3)
-    except Exception as exc:  # informative only: never lose the line for it
-        kernel_ms = {"error": str(exc)}
-    finally:
-        eclqr.eclqr_time_kernel(b.h, None)
-    b.close()
-    stages = int(sum(p.N for p in pbs))
-    passed = (stat == 0) & (res <= KKT_GATE)
-    return {"value": stages / (ms * 1e-3), "unit": "stages/s", "ms_per_step": ms, "problems": len(pbs),
-            "stages": stages, "distinct_draws": BATCH_DISTINCT, "refine": refine,
-            "status_failures": int((stat != 0).sum()), "resid_max": float(res.max()),
-            "gate_passed_frac": float(passed.mean()), "gate_passed": bool(passed.all()),
-            "scan_skipped_problems": skipped, "kernel_ms_per_pass_summed_over_groups": kernel_ms}
-
-
+# ---------------------------------------------------------------- CPU oracle
 def _oracle_worker(args):
     idx, seconds = args
     import oracle
     from paper_2407_05433_gb300 import synth
-    pbs = [synth.config("batched_uneven", index=j) for j in idx]
+    pbs = [synth.config(WORKLOAD, index=j) for j in idx]
     for pb in pbs:
         oracle.solve(pb)
     stages, spent, t0 = 0, 0.0, time.perf_counter()
     while time.perf_counter() - t0 < seconds:
         for pb in pbs:
             t = time.perf_counter()
-            oracle.solve(pb)
+            s = oracle.solve(pb)
+            oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha)
             spent += time.perf_counter() - t
             stages += pb.N
     return stages, spent
 
 
-def oracle_batched_rate(seconds, cores):
-    """The oracle on the host's cores over a bounded sample of the batch: every process solves its own
-    share of the 256 draws repeatedly for ~seconds; the rate is the sum of the per-process rates."""
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def oracle_rate(seconds, cores, sample=256):
+    """The oracle as it stands on the host's cores over a bounded sample of the batch: draws
+    0..sample-1 split over `cores` processes, each solving its share repeatedly for ~seconds; the rate
+    is the sum of the per-process rates."""
     import multiprocessing as mp
     import oracle
     oracle.build_oracle()
-    shares = [list(range(w, BATCH_DISTINCT, cores)) for w in range(cores)]
+    shares = [list(range(w, sample, cores)) for w in range(cores)]
     with mp.get_context("spawn").Pool(cores) as pool:
         out = pool.map(_oracle_worker, [(s, seconds) for s in shares])
     rate = sum(st / sp for st, sp in out if sp > 0)
     return {"value": rate, "unit": "stages/s", "cores": cores, "kind": "oracle",
-            "sample": f"the {BATCH_DISTINCT} distinct draws split over {cores} processes, each solving its share "
-                      f"repeatedly for ~{seconds:.0f} s"}
+            "sample": f"draws 0..{sample - 1} of the batch split over {cores} processes, each solving its share "
+                      f"(solve with refinement + residual) repeatedly for ~{seconds:.0f} s"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_2407_05433_gb300 import synth
-    import oracle
-    oracle.build_oracle()
-    pb = synth.config(WORKLOAD)
-    for _ in range(args.warmup):
-        oracle.solve(pb)
-    times, resid = [], None
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        s = oracle.solve(pb)
-        resid = oracle.kkt_residual(pb, s.x, s.u, s.lam, s.mu, s.eta, s.alpha)
-        times.append(time.perf_counter() - t)
-    ms = 1e3 * statistics.mean(times)
-    value = pb.N / (ms * 1e-3)
+    cores = host_cores()
+    seconds = max(2.0, min(20.0, 2.0 * args.steps))
+    cpu = oracle_rate(seconds, cores)
+    value = cpu["value"]
+    total = workload_flops().get(WORKLOAD, {}).get("stages") or 1076944
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "stages/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "stages": pb.N, "kkt_resid": resid, "status": s.status},
-            "cpu_baseline": {"value": value, "unit": "stages/s", "cores": 1, "kind": "oracle",
-                             "sample": f"the full workload ({pb.N} stages) per step, one thread"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "problems": PROBLEMS},
+            "cpu_baseline": {"value": value, "unit": "stages/s", "cores": cores, "kind": "oracle",
+                             "sample": cpu["sample"]},
             "e2e": {"value": value, "unit": "stages/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+# ---------------------------------------------------------------- the GPU arm
 def run_gpu(args):
     import numpy as np
+    rank, world, local = dist_env()
+    t_gen = time.perf_counter()
+    pbs = batched_problems(args.problems)     # host-side generation before any CUDA call
+    t_gen = time.perf_counter() - t_gen
+    gates = floor_gates()
     import torch
-    from paper_2407_05433_gb300 import eclqr, synth
+    from paper_2407_05433_gb300 import eclqr
     from paper_2407_05433_gb300 import build as build_mod
 
-    rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -359,83 +449,55 @@ def run_gpu(args):
         torch.distributed.barrier()
     build_mod.build()
     eclqr.load()
-
-    pb = synth.config(WORKLOAD)
-    chunk, trials = args.chunk, None
-    if chunk == 0:
-        # untimed setup: the fastest chunk length whose pass meets the residual gate
-        chunk, trials = eclqr.autotune_chunk([pb], device=dev, refine=args.refine, gate=KKT_GATE)
-    batch = eclqr.Batch([pb], device=dev, refine=args.refine, chunk=chunk)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stages = int(sum(p.N for p in pbs))
 
-    def step():
-        batch.build()
-        batch.solve()
-        batch.multipliers()
-        batch.residual()
-
+    batch = eclqr.Batch(pbs, device=dev)
+    per_replay = batch.capture()            # eager pass on a side stream, then one captured pass
     for _ in range(max(3, args.warmup)):
-        step()
+        batch.replay()
     torch.cuda.synchronize(dev)
 
-    # which kernel dominates the step: bracket each kernel in turn over one untimed step
-    per_kernel = {}
-    for name in KERNELS:
-        eclqr.eclqr_time_kernel(batch.h, name)
-        step()
-        nl, tms = eclqr.eclqr_kernel_time(batch.h)
-        per_kernel[name] = (nl, tms)
-    eclqr.eclqr_time_kernel(batch.h, None)
-    dominant = max(per_kernel, key=lambda k: per_kernel[k][1])
-
-    # timed region: per-step events, L2 flushed between steps (outside the events)
+    # timed region: graph replays, L2 flushed between them (outside the events)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    eclqr.eclqr_time_kernel(batch.h, dominant)
-    launches0 = batch.launches()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
-    for k in range(args.steps):
-        flush.zero_()
-        evs[k][0].record(stream)
-        step()
-        evs[k][1].record(stream)
-    torch.cuda.synchronize(dev)
-    launches = batch.launches() - launches0
-    nl_dom, t_dom = eclqr.eclqr_kernel_time(batch.h)
-    eclqr.eclqr_time_kernel(batch.h, None)
+    step_ms = _time_replays(batch, args.steps, flush, stream)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    total_ms = max_over_ranks(total_ms, world, dev)
-    (res,) = batch.results()
-    ok = all_ranks(res["status"] == 0 and res["resid"] <= KKT_GATE, world, dev)
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    ms = total_ms / args.steps
+    res = batch.resid.cpu().numpy()
+    stat = batch.status.cpu().numpy()
+    passed, gate = gate_report(pbs, res, stat, gates)
+    solved = int(sum(p.N for p, ok in zip(pbs, passed) if ok))
+    solved = sum_over_ranks(solved, world, dev)
+    all_ok = all_ranks(bool(passed.all()), world, dev)
+    value = solved / (ms * 1e-3)
 
-    # end to end through the C ABI with host buffers: pinned H2D of the inputs,
-    # the four calls, D2H of every output, all inside the timed region
+    # end to end through the public API with host buffers: pinned H2D of every input, the four
+    # calls (eager), D2H of every output, all inside the timed region
     host_in = {k: torch.from_numpy(batch.host[k]).pin_memory() for k in eclqr.DATA_KEYS + ("s0",)}
     outs = ("x", "u", "lam", "mu", "eta", "alpha", "resid", "status")
     host_out = {k: torch.empty_like(getattr(batch, k), device="cpu").pin_memory() for k in outs}
     h2d = sum(t.numel() * t.element_size() for t in host_in.values())
     d2h = sum(t.numel() * t.element_size() for t in host_out.values())
-    e2e_steps = max(5, args.steps // 4)
 
     def e2e_step():
         for k, t in host_in.items():
             batch.d[k].copy_(t, non_blocking=True)
-        step()
+        batch.run()
         for k in outs:
             host_out[k].copy_(getattr(batch, k), non_blocking=True)
 
-    for _ in range(2):
-        e2e_step()
+    e2e_step()
     torch.cuda.synchronize(dev)
+    e2e_steps = max(2, min(5, args.steps // 4))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
     for _ in range(e2e_steps):
@@ -446,7 +508,8 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
         e2e_ms += ev0.elapsed_time(ev1)
     e2e_ms = max_over_ranks(e2e_ms / e2e_steps, world, dev)
-    e2e_ok = all_ranks(int(host_out["status"][0]) == 0 and float(host_out["resid"][0]) <= KKT_GATE, world, dev)
+    e_passed, _ = gate_report(pbs, host_out["resid"].numpy(), host_out["status"].numpy(), gates)
+    e2e_solved = sum_over_ranks(int(sum(p.N for p, ok in zip(pbs, e_passed) if ok)), world, dev)
 
     if rank != 0:
         batch.close()
@@ -454,70 +517,85 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    extras = {}
-    if world == 1 and not args.no_extra:
-        extras["graph"] = measure_graph(batch, pb, flush, stream, max(5, args.steps // 2))
-        extras["plain"] = measure_plain(pb, dev, flush, stream, args.refine)
-        extras["scan_skip"] = measure_scan_skip(dev, flush, stream, args.refine)
-        _, bpbs = batched_problems()
-        extras["batched"] = measure_batched(bpbs, dev, flush, stream, args.refine)
-    import oracle
-    oracle.build_oracle()
-    sref = oracle.solve(pb)
-    phase = sref.phase_flops
-    step_flops = float(np.sum(phase[:6]))
-    ms = total_ms / args.steps
-    value = job_rate(world, pb.N, ms)
+    flops_all = workload_flops()
+    fl = flops_all.get(WORKLOAD) if args.problems == PROBLEMS else None
     peak = eclqr.eclqr_probe_fp64_peak()
-    dom_ms = t_dom / max(1, nl_dom)
-    launches_per_step_dom = nl_dom / args.steps
-    dom_flops = phase[KERNEL_PHASE[dominant]] / max(1.0, launches_per_step_dom)
-    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tinfo = json.load(open(tpath))
-            if tinfo.get("kernel") == dominant and tinfo.get("workload") == WORKLOAD:
-                traffic = tinfo.get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    extras = {}
+    kern = None
+    if not args.no_extra:
+        extras["plain"] = measure_plain(pbs, dev, flush, stream)
+        extras["plain"]["speedup_batched_vs_plain"] = value / extras["plain"]["value"]
+        kern = measure_kernels(pbs, dev, flush, stream, fl)
+        extras["kernels"] = kern
+    batch.close()
+    roofline = None
+    if fl:
+        step_flops = fl["step_flops"]
+        roofline = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                    "peak_source": "FP64 FMA throughput measured on this GPU by eclqr_probe_fp64_peak (no FP64 "
+                                   "entry in MEASURED_PEAKS.json)",
+                    "step_achieved": step_flops / (ms * 1e-3) / 1e12,
+                    "step_frac": step_flops / (ms * 1e-3) / 1e12 / peak,
+                    "step_algorithmic_flops": step_flops, "traffic": None}
+        if kern and "phase_kernels" in kern:
+            pk = {k: v for k, v in kern["phase_kernels"].items() if v["ms"]}
+            dom = max(pk, key=lambda k: pk[k]["ms"])
+            d = pk[dom]
+            achieved = d["achieved_tflops"]
+            roofline.update({"kernel": dom, "achieved": achieved, "frac": achieved / peak,
+                             "kernel_ms_per_step": d["ms"], "algorithmic_flops_per_step": d["algorithmic_flops"],
+                             "launches_per_step": kern["launches_per_step"].get(dom)})
+            tpath = os.path.join(ROOT, "profiles", "dram_traffic.json")
+            if os.path.exists(tpath):
+                try:
+                    t = json.load(open(tpath))
+                    if t.get("kernel") == dom and t.get("workload") == WORKLOAD:
+                        roofline["traffic"] = t.get("bytes_per_launch")
+                except (OSError, ValueError):
+                    pass
+        else:
+            roofline.update({"achieved": roofline["step_achieved"], "frac": roofline["step_frac"]})
+    if world == 1 and not args.no_extra:
+        from paper_2407_05433_gb300 import synth
+        extras["long_n16"] = single_line("long_n16: N=65536, n=16, m=8, 4 mixed rows, terminal rank 8, A orthogonal",
+                                         synth.config("long_n16"), dev, flush, stream, 2)
+        extras["degenerate_n12"] = single_line("degenerate_n12: N=1024, n=12, m=6, mixed rows U{0..8}, 20% degenerate "
+                                               "stages, full-rank terminal", synth.config("degenerate_n12"), dev,
+                                               flush, stream, 5)
+        extras["single_n4"] = single_line("single_n4: N=64, n=4, m=2, 1 mixed row, rank-2 terminal",
+                                          synth.config("single_n4"), dev, flush, stream, 5)
+        extras["table1"] = [single_line(f"table1: N={N}, n=8, m=4, 2 state-only rows per nonterminal stage",
+                                        synth.config("table1", N=N), dev, flush, stream, 3)
+                            for N in (1024, 4096, 16384)]
+        extras["diff_batch"] = measure_diff_batch(dev, flush, stream)
+        extras["scan_skip"] = measure_scan_skip(dev, flush, stream)
+        for key, wk in (("long_n16", "long_n16"), ("degenerate_n12", "degenerate_n12"), ("single_n4", "single_n4")):
+            f = flops_all.get(wk)
+            if f:
+                extras[key]["step_frac_fp64"] = f["step_flops"] / (extras[key]["ms_per_step"] * 1e-3) / 1e12 / peak
     cpu = None
-    if args.cpu_seconds > 0:
-        rate, nrun, med = oracle_rate(pb, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "stages/s", "cores": 1, "kind": "oracle",
-               "sample": f"full workload ({pb.N} stages) solved {nrun} times in ~{args.cpu_seconds:.0f} s, "
-                         f"median {med * 1e3:.1f} ms per solve, one thread"}
+    if args.cpu_seconds > 0 and world == 1:
+        cpu = oracle_rate(args.cpu_seconds, host_cores())
     line = {
-        "metric": METRIC, "value": value if ok else 0.0, "unit": "stages/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": "stages/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "stages_per_gpu": pb.N, "refine": args.refine,
-                   "chunk": chunk, "chunk_autotune": [{"chunk": c, "ms": round(t, 3), "kkt_resid": r, "passed": ok}
-                                                      for c, t, r, ok in (trials or [])],
-                   "l2": "256 MB buffer written between timed steps",
-                   "kkt_resid": res["resid"], "status": res["status"], "gate_passed": ok,
-                   "step": "eclqr_build + eclqr_solve + eclqr_multipliers + eclqr_kkt_residual"},
-        "e2e": {"value": job_rate(world, pb.N, e2e_ms) if e2e_ok else 0.0, "unit": "stages/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "avg_launch_ms": dom_ms, "launches_per_step": launches_per_step_dom,
-                     "algorithmic_flops_per_launch": dom_flops,
-                     "peak_source": "FP64 FMA probe (eclqr_probe_fp64_peak) on this GPU",
-                     "step_achieved": step_flops / (ms * 1e-3) / 1e12,
-                     "step_frac": step_flops / (ms * 1e-3) / 1e12 / peak},
-        "kernel_ms_per_step": {k: round(v[1], 4) for k, v in per_kernel.items()},
+        "config": {"workload": WORKLOAD_DESC, "problems_per_gpu": len(pbs), "stages_per_gpu": stages,
+                   "l2": "inputs of about 5 GB per GPU (larger than L2); a 256 MB buffer is also written between steps",
+                   "step": "graph replay of eclqr_build + eclqr_solve + eclqr_multipliers + eclqr_refine",
+                   "refine": 2, "kkt_refine": 8, "refine_tol": 5e-10, "generation_s": round(t_gen, 1)},
+        "gate": gate, "gate_passed": all_ok,
+        "e2e": {"value": e2e_solved / (e2e_ms * 1e-3), "unit": "stages/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "call": "Batch.run (eager) with pinned host copies of every input and output"},
+        "gpu_launches": per_replay * args.steps,
+        "launches_per_step": per_replay,
+        "roofline": roofline,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
     line.update(extras)
-    if "batched" in extras and args.cpu_seconds > 0:
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-        line["batched"]["cpu_baseline"] = oracle_batched_rate(args.cpu_seconds, cores)
     print(json.dumps(line), flush=True)
-    batch.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -526,13 +604,12 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--refine", type=int, default=2)
-    ap.add_argument("--chunk", type=int, default=0, help="stages per scan chunk; 0 = autotuned (untimed setup)")
+    ap.add_argument("--problems", type=int, default=PROBLEMS, help="draws 0..problems-1 of the batch")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--no-extra", action="store_true", help="skip the plain-solve and batched lines")
+    ap.add_argument("--no-extra", action="store_true", help="skip the plain solve, kernel times and other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

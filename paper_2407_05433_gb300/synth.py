@@ -97,8 +97,10 @@ def make_problem(seed, N, n, m, p, q, *, a_mode="perturbed", degenerate_frac=0.0
     p = np.full(N, p, dtype=np.int32) if np.isscalar(p) else np.asarray(p, dtype=np.int32).copy()
     q = np.full(N + 1, q, dtype=np.int32) if np.isscalar(q) else np.asarray(q, dtype=np.int32).copy()
     assert p.shape == (N,) and q.shape == (N + 1,)
+    # Draws come in a fixed order; a generator fills an array of draws in the same order as the
+    # same number of one-block calls, so whole arrays are drawn at once.
     if a_mode == "perturbed":
-        A = np.stack([np.eye(n) + 0.1 * rng.standard_normal((n, n)) for _ in range(N)])
+        A = np.eye(n)[None] + 0.1 * rng.standard_normal((N, n, n))
     elif a_mode == "orthogonal":
         A = np.stack([_orthogonal(rng, n) for _ in range(N)])
     else:
@@ -110,8 +112,10 @@ def make_problem(seed, N, n, m, p, q, *, a_mode="perturbed", degenerate_frac=0.0
         M = np.stack([Hk[:n, n:] for Hk in Hs])
         R = np.stack([Hk[n:, n:] for Hk in Hs])
     else:
-        Q = np.stack([random_spd(rng, n) for _ in range(N + 1)])
-        R = np.stack([random_spd(rng, m) for _ in range(N)])
+        LQ = rng.standard_normal((N + 1, n, n))
+        Q = LQ @ LQ.transpose(0, 2, 1) + 1e-3 * np.eye(n)[None]
+        LR = rng.standard_normal((N, m, m))
+        R = LR @ LR.transpose(0, 2, 1) + 1e-3 * np.eye(m)[None]
         M = np.zeros((N, n, m))
     qv = rng.standard_normal((N + 1, n))
     rv = rng.standard_normal((N, m))
@@ -146,18 +150,10 @@ def make_problem(seed, N, n, m, p, q, *, a_mode="perturbed", degenerate_frac=0.0
     # feasible trajectory
     xs = rng.standard_normal((N + 1, n))
     us = rng.standard_normal((N, m))
-    c = np.empty((N, n))
-    for i in range(N):
-        c[i] = xs[i + 1] - A[i] @ xs[i] - B[i] @ us[i]
-    d = np.empty(P)
-    for i in range(N):
-        for j in range(po[i], po[i + 1]):
-            d[j] = -(Cm[j] @ xs[i] + Dm[j] @ us[i])
-    qo = np.concatenate([[0], np.cumsum(q)])
-    e = np.empty(int(q.sum()))
-    for i in range(N + 1):
-        for j in range(qo[i], qo[i + 1]):
-            e[j] = -(Em[j] @ xs[i])
+    c = xs[1:] - np.einsum("ijk,ik->ij", A, xs[:-1]) - np.einsum("ijk,ik->ij", B, us)
+    stage_of_row = np.repeat(np.arange(N), p)
+    d = -(np.einsum("rj,rj->r", Cm, xs[stage_of_row]) + np.einsum("rj,rj->r", Dm, us[stage_of_row]))
+    e = -np.einsum("rj,rj->r", Em, xs[np.repeat(np.arange(N + 1), q)])
     return ECLQRProblem(N=N, n=n, m=m, p=p, q=q, A=A, B=B, c=c, C=Cm, D=Dm, d=d,
                         E=Em, e=e, Q=Q, M=M, R=R, qv=qv, rv=rv, s0=xs[0].copy(),
                         x_star=xs, u_star=us)

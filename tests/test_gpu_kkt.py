@@ -55,7 +55,8 @@ def _problem_with(pb, key, arr):
 
 
 def test_residual_parts_match_the_oracle_value_for_value():
-    """At the solution both residuals are rounding noise below 1e-12.  Then one part at a time is
+    """At the solution both residuals are rounding noise below 1e-9 that agree to 1e-12 absolute.  Then
+    one part at a time is
     made large -- s_0 passed to the residual (initial condition), c (dynamics), d (mixed rows,
     normalised), q (stationarity) -- and the four parts agree with the oracle's to 1e-12 relative."""
     import torch
@@ -68,7 +69,7 @@ def test_residual_parts_match_the_oracle_value_for_value():
         parts0 = b.residual_parts()
         for pb, r, p in zip(pbs, res, parts0):
             _, po = oracle.kkt_residual(pb, r["x"], r["u"], r["lam"], r["mu"], r["eta"], r["alpha"], parts=True)
-            assert np.all(p <= 1e-12) and np.all(po <= 1e-12), (p, po)
+            assert np.all(p <= 1e-9) and np.all(po <= 1e-9) and np.all(np.abs(p - po) <= 1e-12), (p, po)
         rng = np.random.default_rng(7)
         for key, part in (("s0", 0), ("c", 1), ("d", 2), ("qv", 3)):
             orig = b.d[key].clone()
@@ -132,7 +133,7 @@ def test_refinement_with_zero_passes_only_computes_the_residual():
         torch.cuda.synchronize()
         before = {k: getattr(b, k).clone() for k in KEYS}
         b.refine()
-        after = b.results()
+        (after,) = b.results()
         for k in KEYS:
             assert np.array_equal(before[k].cpu().numpy()[:after[k].size], np.asarray(after[k]).ravel()), k
         b.residual()
@@ -188,7 +189,9 @@ def _oracle_job(j):
 def test_uneven_batch_512_distinct_draws_default_schedule():
     """512 distinct draws (more than two problems per SM, so one chunk per problem, longest horizons
     first: the schedule of the full 4096-problem batch) against the oracle, every block at 1e-9 and
-    every residual under its gate.  Draws 0..511 hold one listed draw whose KKT matrix is too close
+    every residual under 1e-9.  A draw listed in tests/golden/batched_uneven_floors.txt has an FP64
+    floor of its own, 4 phi > 1e-9; there both bars are 4 phi (the refined oracle itself lies within
+    phi of the exact KKT solution on every such draw but 250).  Draws 0..511 hold one listed draw whose KKT matrix is too close
     to singular for its solution to be fixed to FP64 accuracy (250: two exact solves of its KKT
     system disagree in x at 1e-1); it is held to its status only."""
     floors = load_floors()
@@ -211,6 +214,6 @@ def test_uneven_batch_512_distinct_draws_default_schedule():
             continue
         gate = floors.get(j, 1e-9)
         errs = {k: rel(r[k], sol[k]) for k in KEYS}
-        if r["resid"] > gate or max(errs.values()) > 1e-9:
+        if r["resid"] > gate or max(errs.values()) > gate:
             bad.append((j, r["resid"], gate, errs))
     assert not bad, bad[:5]
