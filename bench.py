@@ -260,8 +260,9 @@ def measure_plain(pbs, dev, flush, stream):
 
 
 def measure_kernels(pbs, dev, flush, stream, flops):
-    """Per-kernel device time of the batch, one (n, m) group at a time (groups run on concurrent
-    streams in the batch itself, where one kernel's events would also cover the others' work).
+    """Per-kernel device time of one pass over the batch (without the refinement on the KKT
+    residual), one (n, m) group at a time (groups run on concurrent streams in the batch itself,
+    where one kernel's events would also cover the others' work).
     Every kernel of PHASE_KERNELS carries its phase alone when every problem is one chunk, so its
     achieved FP64 rate is the phase's algorithmic flops over its summed launch time."""
     from paper_2407_05433_gb300 import eclqr
@@ -274,8 +275,10 @@ def measure_kernels(pbs, dev, flush, stream, flops):
     ms = {k: 0.0 for k in names}
     launches = {k: 0 for k in names}
     for key, gp in sorted(groups.items()):
-        # the group alone still counts as a large batch (two or more problems per SM): one chunk each
-        b = eclqr.Batch(gp, device=dev)
+        # the group alone still counts as a large batch (two or more problems per SM): one chunk each.
+        # Without the refinement on the KKT residual every kernel launches once per phase, so the
+        # phase's flops and the kernel's time describe the same work.
+        b = eclqr.Batch(gp, device=dev, kkt_refine=0)
         try:
             b.run()
             for name in names:
@@ -296,6 +299,24 @@ def measure_kernels(pbs, dev, flush, stream, flops):
                                     "achieved_tflops": ph[p] / (ms[k] * 1e-3) / 1e12 if ms[k] else None}
                                 for k, p in PHASE_KERNELS.items()}
     return out
+
+
+def measure_without_kkt_refine(pbs, dev, flush, stream, gates, steps=2):
+    """The same batch and step without the refinement on the KKT residual (kkt_refine = 0), eager:
+    what the refinement costs and what it buys."""
+    from paper_2407_05433_gb300 import eclqr
+    b = eclqr.Batch(pbs, device=dev, kkt_refine=0)
+    try:
+        b.run()
+        ms = statistics.median(_time_runs(b, steps, flush, stream))
+        res = b.resid.cpu().numpy()
+        stat = b.status.cpu().numpy()
+    finally:
+        b.close()
+    passed, rep = gate_report(pbs, res, stat, gates)
+    return {"ms_per_step": ms, "passed": rep["passed"], "passed_at_1e-9": rep["passed_at_1e-9"],
+            "resid_max": rep["resid_max"], "step": "eager eclqr_build + eclqr_solve + eclqr_multipliers + "
+                                                   "eclqr_kkt_residual (no refinement passes)"}
 
 
 def measure_diff_batch(dev, flush, stream, steps=3):
@@ -527,6 +548,7 @@ def run_gpu(args):
         extras["plain"]["speedup_batched_vs_plain"] = value / extras["plain"]["value"]
         kern = measure_kernels(pbs, dev, flush, stream, fl)
         extras["kernels"] = kern
+        extras["without_kkt_refine"] = measure_without_kkt_refine(pbs, dev, flush, stream, gates)
     batch.close()
     roofline = None
     if fl:

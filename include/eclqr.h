@@ -210,9 +210,14 @@ int eclqr_kkt_residual_parts(eclqr_handle *h, const double *s0, const double *x,
  *   in place, and resid (device double[P]): the Sec. 9 residual of the
  *   returned point (the call computes it first, so no eclqr_kkt_residual is
  *   needed before it).
- *   The offset-dependent parts of the workspace then belong to the last
- *   correction: eclqr_solve and eclqr_multipliers return ECLQR_ESTATE until
- *   the next eclqr_build or eclqr_set_costs.  Asynchronous on stream. */
+ *   When a pass ran, the offset-dependent parts of the workspace belong to
+ *   the last correction: eclqr_solve and eclqr_multipliers return
+ *   ECLQR_ESTATE until the next eclqr_build or eclqr_set_costs.
+ *   Outside a stream capture the call waits, once per pass, for a 4-byte
+ *   flag telling whether any problem takes part, and returns when none does
+ *   (so it is host-synchronous); on a capturing stream it records all
+ *   opt.kkt_refine passes, whose kernels return at once for the problems
+ *   that take no part. */
 int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double *lam, double *mu,
                  double *eta, double *alpha, double *resid, int32_t *status, void *stream);
 

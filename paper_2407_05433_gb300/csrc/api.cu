@@ -2,8 +2,9 @@
 //
 // eclqr_create plans the batch (groups of equal (n, m), stage and chunk
 // descriptors, workspace layout) and allocates one device block per group.
-// The other calls only enqueue kernels on the caller's stream: no host
-// synchronisation, no allocation.
+// The other calls only enqueue kernels on the caller's stream, with no
+// allocation; the only host synchronisation is eclqr_refine's check, outside
+// a stream capture, whether another refinement pass has work.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,6 +65,8 @@ struct eclqr_handle {
   int32_t *cstatus = nullptr;
   double *tresid = nullptr;
   int *active = nullptr;
+  int *any = nullptr;       // device: some problem takes part in the pass
+  int *any_host = nullptr;  // pinned host copy of it
   bool stale = false;  // the offset-dependent factors are a correction's (after eclqr_refine)
 };
 
@@ -434,7 +437,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     const size_t o_c = take(L.c, 8), o_d = take(L.d, 8), o_e = take(L.e, 8), o_qv = take(L.qv, 8),
                  o_rv = take(L.rv, 8), o_s0 = take(L.s0, 8), o_x = take(L.x, 8), o_u = take(L.u, 8),
                  o_lam = take(L.lam, 8), o_mu = take(L.mu, 8), o_eta = take(L.eta, 8), o_al = take(L.alpha, 8),
-                 o_cs = take(P, 4), o_tr = take(P, 8), o_ac = take(P, 4);
+                 o_cs = take(P, 4), o_tr = take(P, 8), o_ac = take(P, 4), o_any = take(1, 4);
     if (cudaMalloc(&h->rmem, off) != cudaSuccess || cudaMemset(h->rmem, 0, off) != cudaSuccess) {
       eclqr_destroy(h);
       return ECLQR_ENOMEM;
@@ -447,6 +450,12 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     h->cstatus = (int32_t *)(b + o_cs);
     h->tresid = (double *)(b + o_tr);
     h->active = (int *)(b + o_ac);
+    h->any = (int *)(b + o_any);
+    if (cudaMallocHost(&h->any_host, sizeof(int)) != cudaSuccess) {
+      h->any_host = nullptr;
+      eclqr_destroy(h);
+      return ECLQR_ENOMEM;
+    }
   }
   if (h->groups.size() > 1) {
     bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess;
@@ -655,19 +664,41 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
   const Sol w{x, u, lam, mu, eta, alpha};
   const SolMut &t = h->trial;
   const Sol tc{t.x, t.u, t.lam, t.mu, t.eta, t.alpha};
-  TRY(fork_groups(h, st));
-  for (auto &gh : h->groups) {
-    const cudaStream_t gst = group_stream(h, gh, st);
-    Group g = gh.g;          // the problem's data, masked to the active problems
-    g.active = h->active;
-    g.status = h->cstatus;
-    Group gc = g;            // the correction problem: same matrices, residual rows as offsets
-    gc.c = h->rows.c; gc.d = h->rows.d; gc.e = h->rows.e; gc.qv = h->rows.qv; gc.rv = h->rows.rv;
-    Group gu = gh.g;         // unmasked, for the per-problem bookkeeping
-    gu.active = nullptr;
-    for (int k = 0; k < h->opt.kkt_refine; k++) {
-      TRY(launch(h, k_refine_prep, gu.nprob, 0, gst, gu, (const int32_t *)status, (const double *)resid, h->active,
-                 h->cstatus, h->tresid, h->opt.refine_tol, k == 0 ? 1 : 0));
+  // outside a stream capture the passes stop as soon as no problem takes part (one 4-byte read
+  // back per pass); a captured sequence holds every pass, whose kernels return at once for
+  // problems that take no part
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return ECLQR_ECUDA;
+  const bool eager = cap == cudaStreamCaptureStatusNone;
+  bool corrected = false;
+  for (int k = 0; k < h->opt.kkt_refine; k++) {
+    if (cudaMemsetAsync(h->any, 0, sizeof(int), st) != cudaSuccess) return ECLQR_ECUDA;
+    TRY(fork_groups(h, st));
+    for (auto &gh : h->groups) {
+      Group gu = gh.g;  // unmasked, for the per-problem bookkeeping
+      gu.active = nullptr;
+      TRY(launch(h, k_refine_prep, gu.nprob, 0, group_stream(h, gh, st), gu, (const int32_t *)status,
+                 (const double *)resid, h->active, h->cstatus, h->tresid, h->opt.refine_tol, k == 0 ? 1 : 0,
+                 h->any));
+    }
+    if (eager) {
+      TRY(join_groups(h, st));
+      if (cudaMemcpyAsync(h->any_host, h->any, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return ECLQR_ECUDA;
+      if (*h->any_host == 0) break;
+      TRY(fork_groups(h, st));
+    }
+    corrected = true;
+    for (auto &gh : h->groups) {
+      const cudaStream_t gst = group_stream(h, gh, st);
+      Group g = gh.g;  // the problem's data, masked to the active problems
+      g.active = h->active;
+      g.status = h->cstatus;
+      Group gc = g;    // the correction problem: same matrices, residual rows as offsets
+      gc.c = h->rows.c; gc.d = h->rows.d; gc.e = h->rows.e; gc.qv = h->rows.qv; gc.rv = h->rows.rv;
+      Group gu = gh.g;
+      gu.active = nullptr;
       TRY(launch(h, k_kkt, g.nstage, 0, gst, g, s0, (const double *)x, (const double *)u, (const double *)lam,
                  (const double *)mu, (const double *)eta, (const double *)alpha, h->rows, (double *)nullptr,
                  (double *)nullptr));
@@ -682,10 +713,12 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
                  (const double *)h->tresid));
       TRY(launch(h, k_refine_post, gu.nprob, 0, gst, gu, resid, (const double *)h->tresid, h->active));
     }
+    TRY(join_groups(h, st));
   }
-  TRY(join_groups(h, st));
-  h->stale = true;
-  h->solved = false;
+  if (corrected) {
+    h->stale = true;
+    h->solved = false;
+  }
   return ECLQR_OK;
 }
 
@@ -761,6 +794,7 @@ void eclqr_destroy(eclqr_handle *h) {
   }
   if (h->fork) cudaEventDestroy(h->fork);
   if (h->rmem) cudaFree(h->rmem);
+  if (h->any_host) cudaFreeHost(h->any_host);
   for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
 }

@@ -48,15 +48,18 @@ __global__ void k_check_inputs(Group g) {
 // Per problem, before a pass: it runs when the previous pass kept its correction
 // (or this is the first pass), the status is OK and the residual exceeds tol
 // (a NaN residual does not); the pass's status and trial residual start at 0.
+// *any is set when some problem takes part.
 __global__ void k_refine_prep(Group g, const int32_t *status, const double *resid, int *active, int32_t *cstatus,
-                              double *tresid, double tol, int first) {
+                              double *tresid, double tol, int first, int *any) {
   const int t = team_task();
   if (t >= g.nprob || team_rank() != 0) return;
   const int id = g.prob[t].id;
   const bool prev = first ? true : active[id] != 0;
-  active[id] = (prev && status[id] == ST_OK && resid[id] > tol) ? 1 : 0;
+  const bool on = prev && status[id] == ST_OK && resid[id] > tol;
+  active[id] = on ? 1 : 0;
   cstatus[id] = ST_OK;
   tresid[id] = 0.0;
+  if (on) *any = 1;
 }
 
 // After the correction solve: a problem whose correction ended with a status

@@ -144,13 +144,21 @@ def test_refinement_with_zero_passes_only_computes_the_residual():
 
 
 def test_solve_after_refine_needs_a_new_build():
-    pb = synth.config("single_n4", N=20)
-    b = eclqr.Batch([pb])
+    """After a pass ran, the offset-dependent workspace is the last correction's: solve refuses until
+    the next build.  Where no problem needed a pass, the workspace is untouched and solve runs."""
+    b = eclqr.Batch([synth.config("batched_uneven", index=252)])
     try:
         b.run()
         with pytest.raises(RuntimeError, match="call out of order"):
             b.solve()
         b.build()
+        b.solve()
+    finally:
+        b.close()
+    b = eclqr.Batch([synth.config("single_n4", N=20)])
+    try:
+        b.run()
+        assert float(b.resid[0]) <= 5e-10
         b.solve()
     finally:
         b.close()
