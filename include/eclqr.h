@@ -199,12 +199,16 @@ int eclqr_kkt_residual_parts(eclqr_handle *h, const double *s0, const double *x,
  * solves the same problem with the same matrices and the offsets replaced by
  * r: c' = dynamics rows, d' = mixed rows, e' = state-only rows, q' = state
  * stationarity, r' = control stationarity, s0' = -(x_0 - s_0).  Each pass
- * computes those rows, runs build, solve and multipliers on them (the
- * handle's own workspace: no allocation) and keeps w + dw where its residual
- * is smaller.  A problem takes part in pass k while its status is OK, the
- * previous pass kept its correction, and its residual exceeds
- * opt.refine_tol; the others are left as they are (their kernels return at
- * once).  Up to opt.kkt_refine passes.
+ * computes those rows and solves the correction problem in the handle's own
+ * workspace (no allocation): through a new build when a primal part of the
+ * residual (initial condition, dynamics, equality rows) exceeds
+ * opt.refine_tol, otherwise with c' = d' = e' = s0' = 0, homogeneous
+ * constraints for which the build's factors serve unchanged (eclqr_set_costs,
+ * then solve and multipliers).  It keeps w + dw where the residual is
+ * smaller.  A problem takes part in pass k while its status is OK, its
+ * residual exceeds opt.refine_tol and every earlier pass at least halved it;
+ * the others are left as they are (their kernels return at once).  Up to
+ * opt.kkt_refine passes.
  *   In: s0 and the point (the output of eclqr_solve and eclqr_multipliers,
  *   device), status (device int32[P], read only).  Out: the point, improved
  *   in place, and resid (device double[P]): the Sec. 9 residual of the
@@ -251,10 +255,11 @@ int eclqr_probe_fp64_peak(double *tflops);
  * call does not check these preconditions, and with nonzero c, d or e the
  * subsequent solve is wrong.  Zeroes t_i, y_i and cbar_i, recomputes
  * qbar_i = T_i'q_i + Y_i'r_i and rbar_i = Z_i'r_i (eq. reduced-cost-data with
- * t = y = 0) and the square-root Riccati's stage offsets.  The Riccati's own
- * offsets keep the build's values, so the following eclqr_solve starts from
- * a wrong point and relies on its refinement passes (one pass to reach the
- * new solution, the default second pass for accuracy).  Asynchronous; the
+ * t = y = 0) and the square-root Riccati's stage offsets, and sets the
+ * Riccati's own offsets to zero, so that the following eclqr_solve starts
+ * from z = v = 0 and its first refinement pass (the P-form offset recursion
+ * on the stored factors) reaches the new solution, the default second pass
+ * adding accuracy.  Asynchronous; the
  * handle then needs eclqr_solve before eclqr_multipliers.  The paper has no
  * counterpart. */
 int eclqr_set_costs(eclqr_handle *h, const eclqr_data *data, void *stream);

@@ -40,9 +40,14 @@
  *      because F(w + dw) = r + K dw for the affine KKT map F.  Pass k runs
  *      when the status is OK and the Sec. 9 residual exceeds refine_tol;
  *      the corrected point replaces w only when its own solve ended with
- *      status OK and its residual is smaller than w's (otherwise the passes
- *      stop): where the reduction itself loses its accuracy, the correction
- *      solves lose it as well, and the iteration would diverge.
+ *      status OK and its residual is smaller than w's, and the passes go on
+ *      only while each one at least halves the residual: where the reduction
+ *      itself loses its accuracy, the correction solves lose it as well and
+ *      the iteration would diverge, and at the problem's own rounding floor
+ *      a pass only trades rounding errors.  When the primal rows of r (x_0,
+ *      dynamics, mixed and state-only rows) are all within refine_tol, the
+ *      correction takes c' = d' = e' = s0' = 0: the same problem with
+ *      homogeneous constraints, whose reduction needs no new offsets.
  *  Inputs with a NaN or an infinity give status ORC_NONFINITE at once.
  *
  * Numerical policy (Sec. 8 asks for one; the paper fixes no constants):
@@ -1559,8 +1564,17 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
     for (int k = 0; k < opt->kkt_refine; k++) {
       const double res = orc_kkt_residual(P, x, u, lam, mu, eta, alpha, NULL);
       if (!(res > opt->refine_tol)) break;
+      double parts[4];
+      orc_kkt_residual(P, x, u, lam, mu, eta, alpha, parts);
       kkt_rows(P, x, u, lam, mu, eta, alpha, rs0, rc, rd, re, rq, rr);
       for (int a = 0; a < n; a++) s0c[a] = -rs0[a];
+      if (nanmax(parts[0], nanmax(parts[1], parts[2])) <= opt->refine_tol) {
+        /* primal rows within the tolerance: homogeneous constraints */
+        for (int a = 0; a < n; a++) s0c[a] = 0.0;
+        for (size_t j = 0; j < (size_t)N * n; j++) rc[j] = 0.0;
+        for (int j = 0; j < pt; j++) rd[j] = 0.0;
+        for (int j = 0; j < qt; j++) re[j] = 0.0;
+      }
       int fs;
       const int st = solve_once(&C, opt, dx, du, dl, dmu, deta, dal, &fs, NULL);
       if (st != ORC_OK) break;
@@ -1580,6 +1594,7 @@ int orc_solve(const orc_problem *P, const orc_options *opt, double *x,
       memcpy(mu, dmu, sizeof(double) * pt);
       memcpy(eta, deta, sizeof(double) * qt);
       memcpy(alpha, dal, sizeof(double) * n);
+      if (!(trial < 0.5 * res)) break;
     }
     free(rs0); free(rc); free(rd); free(re); free(rq); free(rr); free(s0c);
     free(dx); free(du); free(dl); free(dmu); free(deta); free(dal);

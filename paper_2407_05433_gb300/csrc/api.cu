@@ -64,7 +64,9 @@ struct eclqr_handle {
   SolMut trial{};
   int32_t *cstatus = nullptr;
   double *tresid = nullptr;
-  int *active = nullptr;
+  RefineMasks mk{};
+  double *parts = nullptr, *tparts = nullptr;  // residual parts of the point and of the trial point
+  double *zeros = nullptr;  // offsets of the corrections with homogeneous constraints
   int *any = nullptr;       // device: some problem takes part in the pass
   int *any_host = nullptr;  // pinned host copy of it
   bool stale = false;  // the offset-dependent factors are a correction's (after eclqr_refine)
@@ -437,7 +439,9 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     const size_t o_c = take(L.c, 8), o_d = take(L.d, 8), o_e = take(L.e, 8), o_qv = take(L.qv, 8),
                  o_rv = take(L.rv, 8), o_s0 = take(L.s0, 8), o_x = take(L.x, 8), o_u = take(L.u, 8),
                  o_lam = take(L.lam, 8), o_mu = take(L.mu, 8), o_eta = take(L.eta, 8), o_al = take(L.alpha, 8),
-                 o_cs = take(P, 4), o_tr = take(P, 8), o_ac = take(P, 4), o_any = take(1, 4);
+                 o_cs = take(P, 4), o_tr = take(P, 8), o_ac = take(P, 4), o_any = take(1, 4),
+                 o_fu = take(P, 4), o_ch = take(P, 4), o_pa = take(4 * (size_t)P, 8), o_tp = take(4 * (size_t)P, 8),
+                 o_z = take(std::max({L.c, L.d, L.e, L.s0}), 8);
     if (cudaMalloc(&h->rmem, off) != cudaSuccess || cudaMemset(h->rmem, 0, off) != cudaSuccess) {
       eclqr_destroy(h);
       return ECLQR_ENOMEM;
@@ -449,7 +453,10 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
                       (double *)(b + o_eta), (double *)(b + o_al)};
     h->cstatus = (int32_t *)(b + o_cs);
     h->tresid = (double *)(b + o_tr);
-    h->active = (int *)(b + o_ac);
+    h->mk = RefineMasks{(int *)(b + o_ac), (int *)(b + o_fu), (int *)(b + o_ch)};
+    h->parts = (double *)(b + o_pa);
+    h->tparts = (double *)(b + o_tp);
+    h->zeros = (double *)(b + o_z);
     h->any = (int *)(b + o_any);
     if (cudaMallocHost(&h->any_host, sizeof(int)) != cudaSuccess) {
       h->any_host = nullptr;
@@ -658,12 +665,13 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
   if (h->lay.mu > 0 && !mu) return ECLQR_EINVAL;
   if (h->lay.eta > 0 && !eta) return ECLQR_EINVAL;
   if (!h->built || h->stale) return ECLQR_ESTATE;
-  TRY(residual(h, s0, x, u, lam, mu, eta, alpha, resid, nullptr, stream));
+  TRY(residual(h, s0, x, u, lam, mu, eta, alpha, resid, h->opt.kkt_refine > 0 ? h->parts : nullptr, stream));
   if (h->opt.kkt_refine == 0) return ECLQR_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const Sol w{x, u, lam, mu, eta, alpha};
   const SolMut &t = h->trial;
   const Sol tc{t.x, t.u, t.lam, t.mu, t.eta, t.alpha};
+  const RefineMasks mk = h->mk;
   // outside a stream capture the passes stop as soon as no problem takes part (one 4-byte read
   // back per pass); a captured sequence holds every pass, whose kernels return at once for
   // problems that take no part
@@ -678,8 +686,8 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
       Group gu = gh.g;  // unmasked, for the per-problem bookkeeping
       gu.active = nullptr;
       TRY(launch(h, k_refine_prep, gu.nprob, 0, group_stream(h, gh, st), gu, (const int32_t *)status,
-                 (const double *)resid, h->active, h->cstatus, h->tresid, h->opt.refine_tol, k == 0 ? 1 : 0,
-                 h->any));
+                 (const double *)resid, (const double *)h->parts, mk, h->cstatus, h->tresid, h->tparts, h->opt.refine_tol,
+                 k == 0 ? 1 : 0, h->any));
     }
     if (eager) {
       TRY(join_groups(h, st));
@@ -692,26 +700,41 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
     corrected = true;
     for (auto &gh : h->groups) {
       const cudaStream_t gst = group_stream(h, gh, st);
-      Group g = gh.g;  // the problem's data, masked to the active problems
-      g.active = h->active;
+      Group g = gh.g;  // the problem's data, masked to the problems that take part
+      g.active = mk.active;
       g.status = h->cstatus;
-      Group gc = g;    // the correction problem: same matrices, residual rows as offsets
-      gc.c = h->rows.c; gc.d = h->rows.d; gc.e = h->rows.e; gc.qv = h->rows.qv; gc.rv = h->rows.rv;
       Group gu = gh.g;
       gu.active = nullptr;
+      // residual rows of the point, in the layout of the offsets they replace
       TRY(launch(h, k_kkt, g.nstage, 0, gst, g, s0, (const double *)x, (const double *)u, (const double *)lam,
                  (const double *)mu, (const double *)eta, (const double *)alpha, h->rows, (double *)nullptr,
                  (double *)nullptr));
-      TRY(run_build(h, gh, gc, gst, false));
-      TRY(run_solve(h, gh, gc, gst, h->rows.s0, t.x, t.u));
-      TRY(run_mult(h, gh, gc, gst, t.x, t.u, t.lam, t.mu, t.eta, t.alpha));
-      TRY(launch(h, k_refine_gate, gu.nprob, 0, gst, gu, (const int32_t *)h->cstatus, h->active));
+      // primal rows above the tolerance: the same matrices with the residual rows as offsets,
+      // through a new build
+      Group gf = g;
+      gf.active = mk.full;
+      gf.c = h->rows.c; gf.d = h->rows.d; gf.e = h->rows.e; gf.qv = h->rows.qv; gf.rv = h->rows.rv;
+      TRY(run_build(h, gh, gf, gst, false));
+      TRY(run_solve(h, gh, gf, gst, h->rows.s0, t.x, t.u));
+      TRY(run_mult(h, gh, gf, gst, t.x, t.u, t.lam, t.mu, t.eta, t.alpha));
+      // primal rows within it: homogeneous constraints, so the build's factors serve as they
+      // are and only the linear costs change (as for the adjoint, eclqr_set_costs)
+      Group gz = g;
+      gz.active = mk.cheap;
+      gz.c = h->zeros; gz.d = h->zeros; gz.e = h->zeros; gz.qv = h->rows.qv; gz.rv = h->rows.rv;
+      TRY(launch(h, k_set_costs, gz.nstage, 0, gst, gz, 0));
+      TRY(run_solve(h, gh, gz, gst, h->zeros, t.x, t.u));
+      TRY(run_mult(h, gh, gz, gst, t.x, t.u, t.lam, t.mu, t.eta, t.alpha));
+      // trial point w + dw, its residual, and the choice
+      TRY(launch(h, k_refine_gate, gu.nprob, 0, gst, gu, (const int32_t *)h->cstatus, mk.active));
       TRY(launch(h, k_refine_trial, g.nstage, 0, gst, g, w, t));
       TRY(launch(h, k_kkt, g.nstage, 0, gst, g, s0, tc.x, tc.u, tc.lam, tc.mu, tc.eta, tc.alpha, KktRows{},
-                 h->tresid, (double *)nullptr));
+                 h->tresid, h->tparts));
       TRY(launch(h, k_refine_accept, g.nstage, 0, gst, g, tc, x, u, lam, mu, eta, alpha, (const double *)resid,
                  (const double *)h->tresid));
-      TRY(launch(h, k_refine_post, gu.nprob, 0, gst, gu, resid, (const double *)h->tresid, h->active));
+      TRY(launch(h, k_refine_parts, gu.nprob, 0, gst, gu, (const int *)mk.active, h->parts,
+                 (const double *)h->tparts, (const double *)resid, (const double *)h->tresid));
+      TRY(launch(h, k_refine_post, gu.nprob, 0, gst, gu, resid, (const double *)h->tresid, mk.active));
     }
     TRY(join_groups(h, st));
   }
@@ -822,7 +845,8 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
       {"k_param_grads", (const void *)k_param_grads}, {"k_set_costs", (const void *)k_set_costs},
       {"k_check_inputs", (const void *)k_check_inputs}, {"k_refine_prep", (const void *)k_refine_prep},
       {"k_refine_gate", (const void *)k_refine_gate}, {"k_refine_trial", (const void *)k_refine_trial},
-      {"k_refine_accept", (const void *)k_refine_accept}, {"k_refine_post", (const void *)k_refine_post}};
+      {"k_refine_accept", (const void *)k_refine_accept}, {"k_refine_post", (const void *)k_refine_post},
+      {"k_refine_parts", (const void *)k_refine_parts}};
   for (const auto &e : table)
     if (std::strcmp(e.name, name) == 0) {
       if (h->ev.empty()) {

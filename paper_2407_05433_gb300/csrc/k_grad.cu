@@ -85,10 +85,11 @@ namespace eclqr {
 // every suffix domain is a subspace, so t = y = 0 and cbar = 0; the reduced
 // linear costs are qbar = T'q + Y'r and rbar = Z'r (eqs. reduced-cost-data and
 // terminal-cost-data with t = y = 0), and the square-root Riccati's stage
-// offset is l = L^{-1}[qbar; rbar] with the stored stage factor L.  The
-// Riccati's own offsets (k, p) stay those of the build: the solve's first
-// pass starts from them and its refinement, whose residual reads the new data,
-// converges to the new solution.
+// offset is l = L^{-1}[rbar; qbar] with the stored stage factor L.  The
+// Riccati's own offsets (k, p) are set to zero, so the solve's first rollout
+// is z = v = 0, and its first refinement pass -- whose residual reads the new
+// data, and whose linear pass is the P-form offset recursion on the stored
+// factors -- solves the problem; the next pass adds accuracy.
 __global__ void k_set_costs(Group g, int per_task) {
   const int s = team_task();
   if (s >= g.nstage) return;
@@ -105,8 +106,13 @@ __global__ void k_set_costs(Group g, int per_task) {
   const double *q = g.qv + P.oqv + (size_t)i * n, *r = last ? nullptr : g.rv + P.orv + (size_t)i * m;
   for (int a = tid; a < n; a += TEAM) {
     ws[g.ws.t + a] = 0.0;
+    ws[g.ws.p + a] = 0.0;
     if (!last) ws[g.ws.cb + a] = 0.0;
   }
+  if (!last)
+    for (int a = tid; a < m; a += TEAM) ws[g.ws.k + a] = 0.0;
+  // homogeneous constraints: every domain is a subspace, h_i = 0 (the s_0 check reads h_0)
+  for (int a = tid; a < wi[SI_HROWS]; a += TEAM) ws[g.ws.H + a * (n + 1) + n] = 0.0;
   if (!last)
     for (int a = tid; a < m; a += TEAM) ws[g.ws.y + a] = 0.0;
   for (int a = tid; a < nb; a += TEAM) {
@@ -127,7 +133,7 @@ __global__ void k_set_costs(Group g, int per_task) {
     const double *LT = ws + g.ws.LT;
     double *lt = ws + g.ws.lt;
     for (int a = 0; a < kh; a++) {
-      double s0 = (a < nb) ? ws[g.ws.qb + a] : ws[g.ws.rb + (a - nb)];
+      double s0 = (a < mb) ? ws[g.ws.rb + a] : ws[g.ws.qb + (a - mb)];  // order (v, z)
       for (int l = 0; l < a; l++) s0 = fma(-LT[l * ldh + a], lt[l], s0);
       lt[a] = s0 / LT[a * ldh + a];
     }

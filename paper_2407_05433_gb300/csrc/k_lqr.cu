@@ -130,9 +130,8 @@ __global__ void k_lqr_up(Group g, int per_task) {
           for (int l = 0; l < n1; l++) val = fma(row[l], cb[l], val);
         }
       } else {
-        const int q = r - rc;  // stage cost row q of L' (columns z then v)
-        if (j < mu) val = LT[q * (n + m) + nx + j];
-        else if (j < mu + nx) val = LT[q * (n + m) + (j - mu)];
+        const int q = r - rc;  // stage cost row q of L' (columns v then z, as here)
+        if (j < mu + nx) val = LT[q * (n + m) + j];
         else if (j == ldm - 1) val = lt[q];
       }
       M[idx] = val;
@@ -264,30 +263,37 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
     double *ws = stage_ws(g, s);
     int *wi = stage_wi(g, s);
     const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
-    const int kh = nx + mu, rows = kh + rv, ld = kh + 1;
+    const int kh = nx + mu, ld = kh + 1;
     const double *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb, *cb = ws + g.ws.cb, *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
-    for (int idx = tid; idx < rows * ld; idx += TEAM) {
+    // value rows [V Bbar | V Abar | V cbar + s] at St rows kh .. kh + rv - 1
+    for (int idx = tid; idx < rv * ld; idx += TEAM) {
       int r = idx / ld, j = idx - r * ld;
+      const double *row = V + r * (n + 1);
       double val = 0.0;
-      if (r < kh) {
-        if (j < mu) val = LT[r * (n + m) + nx + j];
-        else if (j < kh) val = LT[r * (n + m) + (j - mu)];
-        else val = lt[r];
+      if (j < mu) {
+        for (int l = 0; l < n1; l++) val = fma(row[l], Bb[l * m + j], val);
+      } else if (j < kh) {
+        for (int l = 0; l < n1; l++) val = fma(row[l], Ab[l * n + (j - mu)], val);
       } else {
-        const double *row = V + (r - kh) * (n + 1);
-        if (j < mu) {
-          for (int l = 0; l < n1; l++) val = fma(row[l], Bb[l * m + j], val);
-        } else if (j < kh) {
-          for (int l = 0; l < n1; l++) val = fma(row[l], Ab[l * n + (j - mu)], val);
-        } else {
-          val = row[n1];
-          for (int l = 0; l < n1; l++) val = fma(row[l], cb[l], val);
-        }
+        val = row[n1];
+        for (int l = 0; l < n1; l++) val = fma(row[l], cb[l], val);
       }
-      St[idx] = val;
+      St[(kh + r) * ld + j] = val;
     }
-    tsync();
-    hh_diag_steps(St, ld, 0, rows, 0, kh, ld, v, w, 0.0, true);
+    // QR of [L' l; value rows] with L' (columns v, z) upper triangular: the reflector of
+    // column k has entries only in row k of L' and in the value rows, so step k works on
+    // those rv + 1 rows alone.  Row k of L' is loaded into the slot right above the value
+    // rows (St row kh - 1), and the finished row moves to St row k before the next load.
+    for (int k = 0; k < kh; k++) {
+      double *W = St + (kh - 1) * ld;
+      for (int j = max(k - 1, 0) + tid; j <= kh; j += TEAM) {
+        if (k > 0 && j >= k - 1) St[(k - 1) * ld + j] = W[j];
+        if (j >= k) W[j] = (j < kh) ? LT[k * (n + m) + j] : lt[k];
+      }
+      tsync();
+      HHLayout L = hh_layout(kh + 1 - k, rv + 1);
+      hh_core(W, ld, 0, rv + 1, k, nullptr, k, kh + 1 - k, L, v, w, 0.0);
+    }
     // sign the z rows to a positive diagonal (rows mu .. kh - 1)
     for (int idx = tid; idx < nx * ld; idx += TEAM) {
       int r = mu + idx / ld, j = idx % ld;

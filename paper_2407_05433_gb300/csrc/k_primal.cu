@@ -36,7 +36,7 @@ __host__ int smem_param(int n) { return n * (n + 1) + n * n + n * n + n + n + 4 
 __host__ int smem_elim(int n, int m, int pmax) {
   int rows = pmax + n;
   return 3 * n * n + m * (n + 1) + n * (n + 1) + rows * m + rows * (n + 1) + m * rows + m * m +
-         m * (n + 1) + 4 * n * m + m * m + 12 * n + 8 * m + 2 * rows + 16 + (n + m) * (n + m) + (n + m);
+         m * (n + 1) + 4 * n * m + m * m + 12 * n + 8 * m + 2 * rows + 16 + (n + m + 1) * (n + m + 1) + 8;
 }
 
 // ----------------------------------------------------------- shortcut test (Sec. 6)
@@ -553,34 +553,32 @@ __global__ void k_elim(Group g, int per_task) {
   // square root of the reduced stage Hessian [[Qbar, Mbar], [Mbar', Rbar]] (order z, v):
   // L L' = H, stored as L' (upper) with l = L^{-1} [qbar; rbar], for the square-root LQR
   {
-    const int kh = nb + mb, ldh = n + m;
+    // stage Hessian in the order (v, z) -- the column order of the Riccati's QR, so that L'
+    // is upper triangular there -- bordered by g = [rbar; qbar]
+    const int kh = nb + mb, ldh = n + m, ldH = kh + 1;
     double *Hh = (double *)(perm + rmax + 2);  // past the permutation scratch
     Hh = (double *)(((uintptr_t)Hh + 7) & ~(uintptr_t)7);
-    for (int idx = tid; idx < kh * kh; idx += TEAM) {
+    for (int idx = tid; idx < (kh + 1) * kh; idx += TEAM) {
       int a = idx / kh, j = idx - a * kh;
       double h;
-      if (a < nb && j < nb) h = Qb[a * n + j];
-      else if (a < nb) h = Mb[a * m + (j - nb)];
-      else if (j < nb) h = Mb[j * m + (a - nb)];
-      else h = Rb[(a - nb) * m + (j - nb)];
-      Hh[idx] = h;
+      if (a == kh) h = (j < mb) ? rb[j] : qb[j - mb];
+      else if (a < mb && j < mb) h = Rb[a * m + j];
+      else if (a < mb) h = Mb[(j - mb) * m + a];
+      else if (j < mb) h = Mb[(a - mb) * m + j];
+      else h = Qb[(a - mb) * n + (j - mb)];
+      Hh[a * ldH + j] = h;
     }
     tsync();
-    const int fail = wcholesky(Hh, kh, kh);
+    int fail = 0;
+    if (tid < 32) fail = wchol_bordered(Hh, ldH, kh);
+    fail = __syncthreads_or(fail);
     if (fail && tid == 0) set_status(g, S.prob, ST_NONCONVEX);
     double *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
     for (int idx = tid; idx < kh * kh; idx += TEAM) {
       int a = idx / kh, j = idx - a * kh;
-      LT[a * ldh + j] = Hh[j * kh + a];
+      LT[a * ldh + j] = (j >= a) ? Hh[j * ldH + a] : 0.0;
     }
-    // l = L^{-1} [qbar; rbar] (one tid, small)
-    if (tid == 0) {
-      for (int a = 0; a < kh; a++) {
-        double s0 = (a < nb) ? qb[a] : rb[a - nb];
-        for (int l = 0; l < a; l++) s0 = fma(-Hh[a * kh + l], lt[l], s0);
-        lt[a] = s0 / Hh[a * kh + a];
-      }
-    }
+    for (int a = tid; a < kh; a += TEAM) lt[a] = Hh[kh * ldH + a];  // L^{-1} [rbar; qbar]
   }
 }
 

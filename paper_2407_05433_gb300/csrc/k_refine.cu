@@ -46,19 +46,29 @@ __global__ void k_check_inputs(Group g) {
 }
 
 // Per problem, before a pass: it runs when the previous pass kept its correction
-// (or this is the first pass), the status is OK and the residual exceeds tol
-// (a NaN residual does not); the pass's status and trial residual start at 0.
-// *any is set when some problem takes part.
-__global__ void k_refine_prep(Group g, const int32_t *status, const double *resid, int *active, int32_t *cstatus,
-                              double *tresid, double tol, int first, int *any) {
+// and halved the residual (or this is the first pass), the status is OK and the
+// residual exceeds tol (a NaN residual does not); the pass's status and trial
+// residual start at 0.  A problem whose primal parts (initial condition,
+// dynamics, equality rows) are within tol takes the correction with homogeneous
+// constraints (full[id] = 0), which reuses the build's offset-free factors;
+// the others rebuild on the residual rows (full[id] = 1).  *any is set when some
+// problem takes part.
+__global__ void k_refine_prep(Group g, const int32_t *status, const double *resid, const double *parts,
+                              RefineMasks mk, int32_t *cstatus, double *tresid, double *tparts, double tol, int first,
+                              int *any) {
   const int t = team_task();
   if (t >= g.nprob || team_rank() != 0) return;
   const int id = g.prob[t].id;
-  const bool prev = first ? true : active[id] != 0;
+  const bool prev = first ? true : mk.active[id] != 0;
   const bool on = prev && status[id] == ST_OK && resid[id] > tol;
-  active[id] = on ? 1 : 0;
+  const double *pp = parts + 4 * (size_t)id;
+  const bool full = on && !(pp[0] <= tol && pp[1] <= tol && pp[2] <= tol);
+  mk.active[id] = on ? 1 : 0;
+  mk.full[id] = full ? 1 : 0;
+  mk.cheap[id] = (on && !full) ? 1 : 0;
   cstatus[id] = ST_OK;
   tresid[id] = 0.0;
+  for (int k = 0; k < 4; k++) tparts[4 * (size_t)id + k] = 0.0;
   if (on) *any = 1;
 }
 
@@ -69,6 +79,17 @@ __global__ void k_refine_gate(Group g, const int32_t *cstatus, int *active) {
   if (t >= g.nprob || team_rank() != 0) return;
   const int id = g.prob[t].id;
   if (active[id] && cstatus[id] != ST_OK) active[id] = 0;
+}
+
+// The parts of the residual at the trial point replace the point's where the
+// trial point is kept (k_refine_post decides with the same comparison).
+__global__ void k_refine_parts(Group g, const int *active, double *parts, const double *tparts,
+                               const double *resid, const double *tresid) {
+  const int t = team_task();
+  if (t >= g.nprob || team_rank() != 0) return;
+  const int id = g.prob[t].id;
+  if (active[id] && tresid[id] < resid[id])
+    for (int k = 0; k < 4; k++) parts[4 * (size_t)id + k] = tparts[4 * (size_t)id + k];
 }
 
 // t = w + t for one stage's blocks (t holds the correction on entry).
@@ -117,15 +138,17 @@ __global__ void k_refine_accept(Group g, Sol t, double *x, double *u, double *la
     for (int a = tid; a < n; a += TEAM) alpha[P.oalpha + a] = t.alpha[P.oalpha + a];
 }
 
-// Per problem, after the accept: the residual of the kept point, or the end of
-// this problem's passes.
+// Per problem, after the accept: the residual of the kept point; the passes go
+// on while each one at least halves it (at the problem's rounding floor a pass
+// only trades rounding errors).
 __global__ void k_refine_post(Group g, double *resid, const double *tresid, int *active) {
   const int t = team_task();
   if (t >= g.nprob || team_rank() != 0) return;
   const int id = g.prob[t].id;
   if (!active[id]) return;
-  if (tresid[id] < resid[id]) resid[id] = tresid[id];
-  else active[id] = 0;
+  const double old = resid[id], now = tresid[id];
+  if (now < old) resid[id] = now;
+  if (!(now < 0.5 * old)) active[id] = 0;
 }
 
 }  // namespace eclqr

@@ -59,8 +59,11 @@ __global__ void k_kkt(Group g, const double *s0, const double *x, const double *
 
 // refinement on the original KKT residual and non-finite checks (k_refine.cu)
 __global__ void k_check_inputs(Group g);
-__global__ void k_refine_prep(Group g, const int32_t *status, const double *resid, int *active, int32_t *cstatus,
-                              double *tresid, double tol, int first, int *any);
+__global__ void k_refine_prep(Group g, const int32_t *status, const double *resid, const double *parts,
+                              RefineMasks mk, int32_t *cstatus, double *tresid, double *tparts, double tol,
+                              int first, int *any);
+__global__ void k_refine_parts(Group g, const int *active, double *parts, const double *tparts,
+                               const double *resid, const double *tresid);
 __global__ void k_refine_gate(Group g, const int32_t *cstatus, int *active);
 __global__ void k_refine_trial(Group g, Sol w, SolMut t);
 __global__ void k_refine_accept(Group g, Sol t, double *x, double *u, double *lam, double *mu, double *eta,

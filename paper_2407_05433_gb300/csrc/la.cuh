@@ -297,6 +297,25 @@ __device__ __forceinline__ bool hh_reflector(double d, double xk, double &nrm, d
   return ex >= -1000 && ex <= 1000;
 }
 
+// d^(-1/2) by the method of hh_reflector: a single-precision seed (exponent
+// on the integer pipe) and one third-order step y = y0 (1 + e/2 + 3 e^2 / 8),
+// e = 1 - d y0^2, truncation error below 2^-60.  ok is false, with the result
+// unusable, unless d is positive, normal and within [2^-1000, 2^1001).
+__device__ __forceinline__ double seeded_rsqrt(double d, bool &ok) {
+  const long long db = __double_as_longlong(d);
+  const int dh = (int)(db >> 32);
+  const int ex = ((dh >> 20) & 0x7ff) - 1023;
+  const int odd = ex & 1, h = (ex - odd) >> 1;
+  const unsigned m23 = ((unsigned)(dh & 0xfffff) << 3) | ((unsigned)db >> 29);
+  const int yf = __float_as_int(rsqrt_seed(__int_as_float(((127 + odd) << 23) | (int)m23)));
+  const double y0 =
+      __hiloint2double(((((yf >> 23) & 0xff) + (1023 - 127) - h) << 20) | ((yf & 0x7fffff) >> 3), (yf & 7) << 29);
+  const double e = fma(-(d * y0), y0, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  ok = (d > 0.0) && ex >= -1000 && ex <= 1000;
+  return fma(y0 * e, p, y0);
+}
+
 // Team arg-max with one barrier: partials alternate between two buffers by
 // parity, so consecutive uses of one buffer must be separated by at least one
 // other barrier.  Keys are the bit patterns of non-negative doubles, which
@@ -1183,6 +1202,46 @@ static __device__ double wtqr_solve(const double *W, int ldw, const double *Q, i
 
 // In-place Cholesky L L^T of an SPD n x n matrix (lower triangle, upper set
 // to zero).  Returns 0 on success, 1 if a pivot is not positive.
+// Cholesky factor of a bordered matrix, by ONE warp: on entry the lower
+// triangle of the leading kh x kh block of Hm (row-major, ld) holds the
+// symmetric H and row kh holds g (columns 0..kh-1); on exit the lower triangle
+// holds L with L L' = H and row kh holds L^{-1} g (the factor of [H g; g' *]
+// without its last diagonal).  Left-looking by columns: lane i owns rows i and
+// i + 32 (kh + 1 <= 64), and column j is one dot product of length j per row,
+// so each FP64 instruction carries every row still below the diagonal; the
+// pivot's reciprocal square root comes from seeded_rsqrt.  The upper triangle
+// is left as it was.  Returns nonzero when a pivot is not positive.
+static __device__ int wchol_bordered(double *Hm, int ld, int kh) {
+  const int lane = threadIdx.x & 31;
+  const int i0 = lane, i1 = lane + 32;
+  int fail = 0;
+  for (int j = 0; j < kh; j++) {
+    const bool on0 = i0 >= j && i0 <= kh, on1 = i1 >= j && i1 <= kh;
+    const double *rj = Hm + j * ld;
+    double s0 = 0.0, s1 = 0.0;
+    if (on0) {
+      const double *ri = Hm + i0 * ld;
+      s0 = ri[j];
+      for (int l = 0; l < j; l++) s0 = fma(-ri[l], rj[l], s0);
+    }
+    if (on1) {
+      const double *ri = Hm + i1 * ld;
+      s1 = ri[j];
+      for (int l = 0; l < j; l++) s1 = fma(-ri[l], rj[l], s1);
+    }
+    const double sd = __shfl_sync(kFull, j < 32 ? s0 : s1, j & 31);
+    bool ok;
+    double inv = seeded_rsqrt(sd, ok);
+    if (!(sd > 0.0)) fail = 1;
+    if (!ok) inv = 1.0 / sqrt(fmax(sd, 1e-300));
+    const double dj = sd * inv;
+    if (on0) Hm[i0 * ld + j] = (i0 == j) ? dj : s0 * inv;
+    if (on1) Hm[i1 * ld + j] = (i1 == j) ? dj : s1 * inv;
+    __syncwarp();
+  }
+  return fail;
+}
+
 static __device__ int wcholesky(double *Hm, int ld, int n) {
   const int tid = team_rank();
   int fail = 0;

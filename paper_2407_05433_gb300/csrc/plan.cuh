@@ -41,7 +41,8 @@ struct WsLayout {
   int P, p, K, k, Lh, Phi;
   int z, v, pi, dz, dv, dpi, rq, rr, rc, pp;
   int nu, NH, Pnu, pnu, UA, BU, UC, Ux, ru;
-  int LT, lt;   // Cholesky factor L' of the reduced stage Hessian (order z, v) and L^{-1}[qbar; rbar]
+  int LT, lt;   // Cholesky factor L' of the reduced stage Hessian in the order (v, z), upper
+                // triangular (L L' = [Rbar Mbar'; Mbar Qbar]), and L^{-1} [rbar; qbar]
   int stride;
 };
 
@@ -129,6 +130,11 @@ struct Sol {
 };
 struct SolMut {
   double *x, *u, *lam, *mu, *eta, *alpha;
+};
+// the per-problem masks of a refinement pass (batch-global, indexed by ProbInfo::id):
+// taking part, with a rebuild on the residual rows, with homogeneous constraints
+struct RefineMasks {
+  int *active, *full, *cheap;
 };
 // residual rows of the KKT system, written where a correction problem keeps the
 // offsets they replace (any pointer null: rows not written)
