@@ -319,6 +319,53 @@ def measure_without_kkt_refine(pbs, dev, flush, stream, gates, steps=2):
                                                    "eclqr_kkt_residual (no refinement passes)"}
 
 
+def measure_mixed(name, pbs, dev, flush, stream, gates=None, steps=2, graph=False):
+    """The same workload in mixed precision (riccati_fp32 = 1: the Riccati sweep in FP32, refinement in
+    FP64, FP64 redo where it does not converge) beside FP64: time, problems under the gate, problems
+    redone in FP64, and per problem the largest relative difference from the FP64 result (x, u and the
+    multipliers, ||delta||_inf / max(1, ||fp64||_inf); the FP64 path is held to the oracle at 1e-9 by
+    the tests)."""
+    import numpy as np
+    from paper_2407_05433_gb300 import eclqr
+    out, ref = {"workload": name, "problems": len(pbs)}, None
+    for tag, fp32 in (("fp64", 0), ("mixed", 1)):
+        b = eclqr.Batch(pbs, device=dev, riccati_fp32=fp32)
+        try:
+            if graph:
+                b.capture()
+                b.replay()
+                ms = statistics.median(_time_replays(b, steps, flush, stream))
+            else:
+                b.run()
+                ms = statistics.median(_time_runs(b, steps, flush, stream))
+            res = b.results()
+            redo = int(b.riccati_fp64().sum()) if fp32 else len(pbs)
+        finally:
+            b.close()
+        rr = np.array([r["resid"] for r in res])
+        st = np.array([r["status"] for r in res])
+        g = np.array([(gates or {}).get(j, KKT_GATE) for j in range(len(pbs))])
+        out[tag] = {"ms_per_step": ms, "stages_per_s": sum(p.N for p in pbs) / (ms * 1e-3),
+                    "passed": int(((st == 0) & (rr <= g)).sum()), "resid_max": float(np.nanmax(rr))}
+        if fp32:
+            out[tag]["redone_in_fp64"] = redo
+            diffs = []
+            for a, r in zip(ref, res):
+                d = 0.0
+                for k in ("x", "u", "lam", "mu", "eta", "alpha"):
+                    x, y = np.asarray(r[k], float), np.asarray(a[k], float)
+                    if y.size:
+                        d = max(d, float(np.max(np.abs(x - y)) / max(1.0, np.max(np.abs(y)))))
+                diffs.append(d)
+            diffs = np.array(diffs)
+            out[tag]["rel_diff_vs_fp64"] = {"max": float(diffs.max()), "median": float(np.median(diffs)),
+                                            "over_1e-9": int((diffs > 1e-9).sum())}
+        else:
+            ref = res
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
 def measure_diff_batch(dev, flush, stream, steps=3):
     """The differentiable batch (1024 problems, N = 256, n = 16, m = 8): the forward pass, and forward
     plus backward through the autograd.Function, loss sum ||x - x_ref||^2 + ||u||^2."""
@@ -591,6 +638,16 @@ def run_gpu(args):
                             for N in (1024, 4096, 16384)]
         extras["diff_batch"] = measure_diff_batch(dev, flush, stream)
         extras["scan_skip"] = measure_scan_skip(dev, flush, stream)
+        extras["mixed"] = {
+            "long_n16": measure_mixed("long_n16: N=65536, n=16, m=8", [synth.config("long_n16")], dev, flush, stream),
+            "diff_batch": measure_mixed("diff_batch: 1024 problems, N=256, n=16, m=8",
+                                        [synth.config("diff_batch", index=j) for j in range(1024)], dev, flush,
+                                        stream),
+            "single_n4": measure_mixed("single_n4: N=64, n=4, m=2", [synth.config("single_n4")], dev, flush,
+                                       stream, steps=5),
+            "batched_uneven": measure_mixed("batched_uneven: the headline batch, graph replay", pbs, dev, flush,
+                                            stream, gates=gates, graph=True),
+        }
         for key, wk in (("long_n16", "long_n16"), ("degenerate_n12", "degenerate_n12"), ("single_n4", "single_n4")):
             f = flops_all.get(wk)
             if f:

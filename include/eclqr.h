@@ -124,6 +124,12 @@ typedef struct {
                        * refinement workspace and eclqr_refine only computes the residual */
   double refine_tol;  /* eclqr_refine corrects a problem only while its residual exceeds
                        * this; default 5e-10                                              */
+  int32_t riccati_fp32; /* 1: mixed precision -- the square-root Riccati sweep of every
+                       * problem runs in FP32, everything else in FP64 (the domain scan,
+                       * null-space bases and rank decisions, the elimination, rollout,
+                       * refinement and multipliers); eclqr_refine then refines in FP64
+                       * and redoes in FP64 the problems it leaves above refine_tol.
+                       * 0 (default): FP64 throughout                                   */
 } eclqr_options;
 
 /* element counts of every packed array (for allocation) */
@@ -224,6 +230,12 @@ int eclqr_kkt_residual_parts(eclqr_handle *h, const double *s0, const double *x,
  *   that take no part. */
 int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double *lam, double *mu,
                  double *eta, double *alpha, double *resid, int32_t *status, void *stream);
+
+/* Mixed precision (opt.riccati_fp32 = 1): flags (device int32[P]) receives 1 for
+ * every problem whose Riccati sweep eclqr_refine redid in FP64 since the last
+ * eclqr_build, 0 for those that kept the FP32 sweep; all 1 when the handle
+ * runs in FP64.  Asynchronous on stream.  The paper has no counterpart. */
+int eclqr_riccati_fp64_flags(eclqr_handle *h, int32_t *flags, void *stream);
 
 /* Reduced dimensions nbar_i (sum_j (N_j+1)) and mbar_i (sum_j N_j) of the last
  * build, into device int32 arrays. */

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeclqr.so")
-SOURCES = ["k_primal.cu", "k_lqr.cu", "k_dual.cu", "k_grad.cu", "k_refine.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["k_primal.cu", "k_lqr.cu", "k_dual.cu", "k_grad.cu", "k_refine.cu", "k_mixed.cu", "api.cu", "noalloc.cu"]
 HEADERS = ["la.cuh", "plan.cuh", "kernels.cuh", os.path.join("..", "..", "include", "eclqr.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

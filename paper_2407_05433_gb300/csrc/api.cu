@@ -68,6 +68,7 @@ struct eclqr_handle {
   double *parts = nullptr, *tparts = nullptr;  // residual parts of the point and of the trial point
   double *zeros = nullptr;  // offsets of the corrections with homogeneous constraints
   int *any = nullptr;       // device: some problem takes part in the pass
+  int *fp64 = nullptr;      // mixed precision: per-problem flags of the Riccati sweep's precision
   int *any_host = nullptr;  // pinned host copy of it
   bool stale = false;  // the offset-dependent factors are a correction's (after eclqr_refine)
 };
@@ -201,6 +202,7 @@ void eclqr_default_options(eclqr_options *opt) {
   opt->scan_skip = 1;
   opt->kkt_refine = 8;
   opt->refine_tol = 5e-10;
+  opt->riccati_fp32 = 0;
 }
 
 int eclqr_layout(const eclqr_desc *d, eclqr_layout_info *out) {
@@ -239,7 +241,8 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   const int tw = h->opt.team_warps;
   if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0) ||
       !(tw == 1 || tw == 2 || tw == 4 || tw == 8) || !(h->opt.scan_skip == 0 || h->opt.scan_skip == 1) ||
-      h->opt.kkt_refine < 0 || h->opt.kkt_refine > 16 || !(h->opt.refine_tol >= 0)) {
+      h->opt.kkt_refine < 0 || h->opt.kkt_refine > 16 || !(h->opt.refine_tol >= 0) ||
+      !(h->opt.riccati_fp32 == 0 || h->opt.riccati_fp32 == 1)) {
     delete h;
     return ECLQR_EINVAL;
   }
@@ -464,6 +467,11 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       return ECLQR_ENOMEM;
     }
   }
+  if (h->opt.riccati_fp32 && cudaMalloc(&h->fp64, sizeof(int) * (size_t)P) != cudaSuccess) {
+    h->fp64 = nullptr;
+    eclqr_destroy(h);
+    return ECLQR_ENOMEM;
+  }
   if (h->groups.size() > 1) {
     bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess;
     for (auto &gh : h->groups) {
@@ -516,6 +524,7 @@ int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, 
   src = 0;
   for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_lqr_level, g.nslot, slv, gst, g, src, 1 << k, slv));
   TRY(launch(h, k_riccati_down, g.nslot, sr, gst, g, src, sr));
+  if (g.fp64) TRY(launch(h, k_riccati_down_f32, g.nslot, sr, gst, g, src, sr));
   return ECLQR_OK;
 }
 
@@ -581,11 +590,14 @@ int eclqr_build(eclqr_handle *h, const eclqr_data *data, int32_t *status, void *
   if (!h || !data || !status) return ECLQR_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(status, 0, sizeof(int32_t) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
+  // mixed precision: every problem starts with its Riccati sweep in FP32
+  if (h->fp64 && cudaMemsetAsync(h->fp64, 0, sizeof(int) * h->P, st) != cudaSuccess) return ECLQR_ECUDA;
   TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
     set_data(gh.g, data);
     gh.g.status = status;
     gh.g.active = nullptr;
+    gh.g.fp64 = h->fp64;
     TRY(run_build(h, gh, gh.g, group_stream(h, gh, st), true));
   }
   TRY(join_groups(h, st));
@@ -679,6 +691,9 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return ECLQR_ECUDA;
   const bool eager = cap == cudaStreamCaptureStatusNone;
   bool corrected = false;
+  // up to opt.kkt_refine passes; first = 1 starts every problem afresh, 0 continues the problems
+  // that mk.active marks
+  auto passes = [&](int first) -> int {
   for (int k = 0; k < h->opt.kkt_refine; k++) {
     if (cudaMemsetAsync(h->any, 0, sizeof(int), st) != cudaSuccess) return ECLQR_ECUDA;
     TRY(fork_groups(h, st));
@@ -687,7 +702,7 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
       gu.active = nullptr;
       TRY(launch(h, k_refine_prep, gu.nprob, 0, group_stream(h, gh, st), gu, (const int32_t *)status,
                  (const double *)resid, (const double *)h->parts, mk, h->cstatus, h->tresid, h->tparts, h->opt.refine_tol,
-                 k == 0 ? 1 : 0, h->any));
+                 k == 0 ? first : 0, h->any));
     }
     if (eager) {
       TRY(join_groups(h, st));
@@ -737,6 +752,46 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
       TRY(launch(h, k_refine_post, gu.nprob, 0, gst, gu, resid, (const double *)h->tresid, mk.active));
     }
     TRY(join_groups(h, st));
+  }
+  return ECLQR_OK;
+  };
+  TRY(passes(1));
+  if (h->fp64) {
+    // mixed precision: the problems still above the tolerance are redone with their Riccati
+    // sweep in FP64 (build, solve, multipliers, residual), then refined again
+    if (cudaMemsetAsync(h->any, 0, sizeof(int), st) != cudaSuccess) return ECLQR_ECUDA;
+    TRY(fork_groups(h, st));
+    for (auto &gh : h->groups) {
+      Group gu = gh.g;
+      gu.active = nullptr;
+      TRY(launch(h, k_rescue_prep, gu.nprob, 0, group_stream(h, gh, st), gu, (const int32_t *)status, resid, h->parts,
+                 h->fp64, mk.active, h->opt.refine_tol, h->any));
+    }
+    bool work = true;
+    if (eager) {
+      TRY(join_groups(h, st));
+      if (cudaMemcpyAsync(h->any_host, h->any, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return ECLQR_ECUDA;
+      work = *h->any_host != 0;
+      if (work) TRY(fork_groups(h, st));
+    }
+    if (work) {
+      corrected = true;
+      for (auto &gh : h->groups) {
+        const cudaStream_t gst = group_stream(h, gh, st);
+        Group g = gh.g;  // the problem's own data, masked to the rescued problems
+        g.active = mk.active;
+        g.status = status;
+        TRY(run_build(h, gh, g, gst, false));
+        TRY(run_solve(h, gh, g, gst, s0, x, u));
+        TRY(run_mult(h, gh, g, gst, x, u, lam, mu, eta, alpha));
+        TRY(launch(h, k_kkt, g.nstage, 0, gst, g, s0, (const double *)x, (const double *)u, (const double *)lam,
+                   (const double *)mu, (const double *)eta, (const double *)alpha, KktRows{}, resid, h->parts));
+      }
+      TRY(join_groups(h, st));
+      TRY(passes(0));
+    }
   }
   if (corrected) {
     h->stale = true;
@@ -808,6 +863,22 @@ int eclqr_scan_skipped(eclqr_handle *h, int32_t *flags, void *stream) {
 
 int64_t eclqr_launch_count(const eclqr_handle *h) { return h ? h->launches : 0; }
 
+int eclqr_riccati_fp64_flags(eclqr_handle *h, int32_t *flags, void *stream) {
+  if (!h || !flags) return ECLQR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!h->fp64) {
+    // FP64 throughout: every sweep in FP64
+    std::vector<int32_t> ones(h->P, 1);
+    return cudaMemcpyAsync(flags, ones.data(), sizeof(int32_t) * h->P, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                   cudaStreamSynchronize(st) == cudaSuccess
+               ? ECLQR_OK
+               : ECLQR_ECUDA;
+  }
+  return cudaMemcpyAsync(flags, h->fp64, sizeof(int32_t) * h->P, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+             ? ECLQR_OK
+             : ECLQR_ECUDA;
+}
+
 void eclqr_destroy(eclqr_handle *h) {
   if (!h) return;
   for (auto &gh : h->groups) {
@@ -818,6 +889,7 @@ void eclqr_destroy(eclqr_handle *h) {
   if (h->fork) cudaEventDestroy(h->fork);
   if (h->rmem) cudaFree(h->rmem);
   if (h->any_host) cudaFreeHost(h->any_host);
+  if (h->fp64) cudaFree(h->fp64);
   for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
 }
@@ -846,7 +918,8 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
       {"k_check_inputs", (const void *)k_check_inputs}, {"k_refine_prep", (const void *)k_refine_prep},
       {"k_refine_gate", (const void *)k_refine_gate}, {"k_refine_trial", (const void *)k_refine_trial},
       {"k_refine_accept", (const void *)k_refine_accept}, {"k_refine_post", (const void *)k_refine_post},
-      {"k_refine_parts", (const void *)k_refine_parts}};
+      {"k_refine_parts", (const void *)k_refine_parts}, {"k_rescue_prep", (const void *)k_rescue_prep},
+      {"k_riccati_down_f32", (const void *)k_riccati_down_f32}};
   for (const auto &e : table)
     if (std::strcmp(e.name, name) == 0) {
       if (h->ev.empty()) {

@@ -221,6 +221,7 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
   if (skipped_by_mask(g, ci.prob)) return;
+  if (g.fp64 != nullptr && g.fp64[P.id] == 0) return;  // mixed precision: k_riccati_down_f32 sweeps it
   if (ci.c >= P.nch) return;
   const int n = g.n, m = g.m, tid = team_rank();
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
@@ -284,13 +285,28 @@ __global__ void k_riccati_down(Group g, int fin, int per_task) {
     // column k has entries only in row k of L' and in the value rows, so step k works on
     // those rv + 1 rows alone.  Row k of L' is loaded into the slot right above the value
     // rows (St row kh - 1), and the finished row moves to St row k before the next load.
+    // The next row of L' is read from global memory into registers before the current step
+    // runs (thread tid holds columns tid and tid + TEAM, kh + 1 <= 2 TEAM), so its latency
+    // hides behind the step.
+    double nxt[2];
+    for (int q = 0; q < 2; q++) {
+      const int j = tid + q * TEAM;
+      nxt[q] = (j <= kh && kh > 0) ? ((j < kh) ? LT[j] : lt[0]) : 0.0;
+    }
     for (int k = 0; k < kh; k++) {
       double *W = St + (kh - 1) * ld;
-      for (int j = max(k - 1, 0) + tid; j <= kh; j += TEAM) {
+      for (int q = 0; q < 2; q++) {
+        const int j = tid + q * TEAM;
+        if (j > kh) continue;
         if (k > 0 && j >= k - 1) St[(k - 1) * ld + j] = W[j];
-        if (j >= k) W[j] = (j < kh) ? LT[k * (n + m) + j] : lt[k];
+        if (j >= k) W[j] = nxt[q];
       }
       tsync();
+      if (k + 1 < kh)
+        for (int q = 0; q < 2; q++) {
+          const int j = tid + q * TEAM;
+          if (j >= k + 1 && j <= kh) nxt[q] = (j < kh) ? LT[(k + 1) * (n + m) + j] : lt[k + 1];
+        }
       HHLayout L = hh_layout(kh + 1 - k, rv + 1);
       hh_core(W, ld, 0, rv + 1, k, nullptr, k, kh + 1 - k, L, v, w, 0.0);
     }

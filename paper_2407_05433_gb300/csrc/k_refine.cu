@@ -151,4 +151,21 @@ __global__ void k_refine_post(Group g, double *resid, const double *tresid, int 
   if (!(now < 0.5 * old)) active[id] = 0;
 }
 
+// Mixed precision, after the passes: a problem whose status is OK but whose
+// residual is still above tol (or NaN) is redone with its Riccati sweep in FP64
+// (fp64 flag 1); its residual and parts restart from zero for the new point.
+__global__ void k_rescue_prep(Group g, const int32_t *status, double *resid, double *parts, int *fp64, int *active,
+                              double tol, int *any) {
+  const int t = team_task();
+  if (t >= g.nprob || team_rank() != 0) return;
+  const int id = g.prob[t].id;
+  const bool on = status[id] == ST_OK && fp64[id] == 0 && !(resid[id] <= tol);
+  active[id] = on ? 1 : 0;
+  if (!on) return;
+  fp64[id] = 1;
+  resid[id] = 0.0;
+  for (int k = 0; k < 4; k++) parts[4 * (size_t)id + k] = 0.0;
+  *any = 1;
+}
+
 }  // namespace eclqr

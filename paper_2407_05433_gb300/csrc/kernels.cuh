@@ -34,6 +34,7 @@ enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_PLIN_ = 2, AFF_NU_ = 3 };
 __global__ void k_lqr_up(Group g, int per_task);
 __global__ void k_lqr_level(Group g, int src, int d, int per_task);
 __global__ void k_riccati_down(Group g, int fin, int per_task);
+__global__ void k_riccati_down_f32(Group g, int fin, int per_task);  // k_mixed.cu
 __global__ void k_aff_up(Group g, int mode, int per_task);
 __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task);
 __global__ void k_aff_down(Group g, int mode, int fin, int per_task);
@@ -69,5 +70,7 @@ __global__ void k_refine_trial(Group g, Sol w, SolMut t);
 __global__ void k_refine_accept(Group g, Sol t, double *x, double *u, double *lam, double *mu, double *eta,
                                 double *alpha, const double *resid, const double *tresid);
 __global__ void k_refine_post(Group g, double *resid, const double *tresid, int *active);
+__global__ void k_rescue_prep(Group g, const int32_t *status, double *resid, double *parts, int *fp64, int *active,
+                              double tol, int *any);
 
 }  // namespace eclqr

@@ -121,6 +121,8 @@ struct Group {
   int *need_scan; // per problem: 1 once a stage leaves rows on x_i (set by k_scan_check)
   const int *active;  // batch-global, indexed by ProbInfo::id; when set, every kernel skips
                       // the tasks of problems whose entry is 0 (refinement passes)
+  const int *fp64;    // mixed precision: batch-global flags, 1 = this problem's Riccati sweep in
+                      // FP64, 0 = in FP32; null = every sweep in FP64
   double tau_rank, tau_inc;
 };
 

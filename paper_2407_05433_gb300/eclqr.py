@@ -39,7 +39,7 @@ class eclqr_grads(ct.Structure):
 class eclqr_options(ct.Structure):
     _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int32), ("chunk", ct.c_int32),
                 ("team_warps", ct.c_int32), ("scan_skip", ct.c_int32), ("kkt_refine", ct.c_int32),
-                ("refine_tol", ct.c_double)]
+                ("refine_tol", ct.c_double), ("riccati_fp32", ct.c_int32)]
 
 
 LAYOUT_FIELDS = ("A", "B", "c", "C", "D", "d", "E", "e", "Q", "M", "R", "qv", "rv", "s0",
@@ -80,6 +80,8 @@ def load():
     lib.eclqr_kkt_residual_parts.restype = i32
     lib.eclqr_refine.argtypes = [vp] * 11
     lib.eclqr_refine.restype = i32
+    lib.eclqr_riccati_fp64_flags.argtypes = [vp, vp, vp]
+    lib.eclqr_riccati_fp64_flags.restype = i32
     lib.eclqr_reduced_dims.argtypes = [vp, vp, vp, vp]
     lib.eclqr_reduced_dims.restype = i32
     lib.eclqr_scan_skipped.argtypes = [vp, vp, vp]
@@ -235,7 +237,7 @@ class Batch:
     """A batch of problems resident on one CUDA device, solved through the C ABI."""
 
     def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=2, chunk=0, team_warps=0,
-                 scan_skip=1, kkt_refine=8, refine_tol=5e-10):
+                 scan_skip=1, kkt_refine=8, refine_tol=5e-10, riccati_fp32=0):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -249,6 +251,7 @@ class Batch:
         opt.team_warps = team_warps
         opt.scan_skip = scan_skip
         opt.kkt_refine, opt.refine_tol = kkt_refine, refine_tol
+        opt.riccati_fp32 = riccati_fp32
         with torch.cuda.device(self.device):
             rc, self.h = eclqr_create(self.desc, opt)
         _check(rc, "eclqr_create")
@@ -355,6 +358,14 @@ class Batch:
 
     def replay(self):
         self.graph.replay()
+
+    def riccati_fp64(self):
+        """Per problem: True where the Riccati sweep ran in FP64 (always in FP64 mode; in mixed precision,
+        the problems eclqr_refine redid in FP64)."""
+        torch = self.torch
+        f = torch.zeros(len(self.problems), dtype=torch.int32, device=self.device)
+        _check(load().eclqr_riccati_fp64_flags(self.h, f.data_ptr(), self._stream()), "eclqr_riccati_fp64_flags")
+        return f.cpu().numpy().astype(bool)
 
     def scan_skipped(self):
         """Per problem: True where the build skipped the feasible-domain scan (Sec. 6 shortcut)."""
