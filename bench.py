@@ -400,11 +400,36 @@ def measure_diff_batch(dev, flush, stream, steps=3):
         fb = statistics.median(times)
     finally:
         b.close()
+    # checkpointed: four segments of 256 problems on one segment-sized handle, factors recomputed
+    seg = eclqr.Batch(pbs[:256], device=dev)
+    try:
+        full = eclqr.Batch(pbs, device=dev)
+        params = ag.batch_params(full)
+        full.close()
+        times = []
+        for k in range(steps + 1):
+            for p in params:
+                p.grad = None
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, u = ag.solve_checkpointed(seg, 4, *params)
+            (((x - xref) ** 2).sum() + (u ** 2).sum()).backward()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k:
+                times.append(e0.elapsed_time(e1))
+        fbc = statistics.median(times)
+    finally:
+        seg.close()
     stages = sum(p.N for p in pbs)
     return {"workload": "diff_batch: 1024 problems, N=256, n=16, m=8, 4 mixed rows, 4 terminal rows",
             "forward": {"value": stages / (fwd * 1e-3), "unit": "stages/s", "ms_per_step": fwd,
                         "resid_max": float(res.max()), "passed_at_1e-9": int(((stat == 0) & (res <= KKT_GATE)).sum())},
-            "forward_backward": {"value": stages / (fb * 1e-3), "unit": "stages/s", "ms_per_step": fb}}
+            "forward_backward": {"value": stages / (fb * 1e-3), "unit": "stages/s", "ms_per_step": fb},
+            "forward_backward_checkpointed": {"value": stages / (fbc * 1e-3), "unit": "stages/s", "ms_per_step": fbc,
+                                              "segments": 4, "note": "one 256-problem handle; factors recomputed "
+                                                                     "in the backward pass"}}
 
 
 def measure_scan_skip(dev, flush, stream, steps=3):

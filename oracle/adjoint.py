@@ -30,26 +30,35 @@ def _solve_kkt(K, rhs, refine=3):
     return sol
 
 
-def implicit_gradients(pb, lx, lu):
+def implicit_gradients(pb, lx, lu, sparse=False):
     """Gradients of l w.r.t. every problem array, given dl/dx ((N+1) x n) and dl/du (N x m).
 
+    sparse: solve the KKT system and its transpose with the sparse LU of oracle.exact (refined in
+    extended precision) instead of the dense least-squares solve -- for full-size problems, whose
+    constraint Jacobian must then have full row rank.  The same index maps serve both.
     Returns a dict keyed like the problem fields (A, B, c, C, D, d, E, e, Q, M, R, qv, rv, s0),
     each with the shape of that field."""
     N, n, m = pb.N, pb.n, pb.m
-    J, b = dense.constraint_matrix(pb)
-    H, g = dense.hessian_gradient(pb)
-    nv, nr = H.shape[0], J.shape[0]
-    K = np.zeros((nv + nr, nv + nr))
-    K[:nv, :nv] = H
-    K[:nv, nv:] = J.T
-    K[nv:, :nv] = J
-    sol = _solve_kkt(K, np.concatenate([-g, b]))
+    if sparse:
+        from .exact import kkt_matrix, solve_refined
+        K, rhs, nv = kkt_matrix(pb)
+        nr = K.shape[0] - nv
+        sol, _, lu_f = solve_refined(K, rhs)
+    else:
+        J, b = dense.constraint_matrix(pb)
+        H, g = dense.hessian_gradient(pb)
+        nv, nr = H.shape[0], J.shape[0]
+        K = np.zeros((nv + nr, nv + nr))
+        K[:nv, :nv] = H
+        K[:nv, nv:] = J.T
+        K[nv:, :nv] = J
+        sol = _solve_kkt(K, np.concatenate([-g, b]))
     lw = np.zeros(nv + nr)
     for i in range(N + 1):
         lw[dense._xidx(pb, i)] = lx[i]
     for i in range(N):
         lw[dense._uidx(pb, i)] = lu[i]
-    adj = _solve_kkt(K.T, lw)
+    adj = solve_refined(K.T.tocsr(), lw, lu=lu_f)[0] if sparse else _solve_kkt(K.T, lw)
     w, y = sol[:nv], sol[nv:]
     wb, yb = adj[:nv], adj[nv:]
     po, qo = dense._offsets(pb)

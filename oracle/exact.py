@@ -114,21 +114,27 @@ def _unpack(pb, sol, nv):
     return dict(x=x, u=u, lam=lam, mu=mu, eta=eta, alpha=alpha)
 
 
+def solve_refined(K, rhs, passes=6, lu=None):
+    """K w = rhs by one FP64 sparse LU and `passes` steps of refinement whose residuals are
+    accumulated in extended precision; returns (w in FP64, extended-precision residual norm, lu)."""
+    lu = lu or spl.splu(K.tocsc())
+    Kl = K.astype(np.longdouble)
+    rl = np.asarray(rhs, dtype=np.float64).astype(np.longdouble)
+    sl = lu.solve(np.asarray(rhs, dtype=np.float64)).astype(np.longdouble)
+    for _ in range(passes):
+        r = rl - Kl @ sl
+        sl = sl + lu.solve(np.asarray(r, dtype=np.float64)).astype(np.longdouble)
+    return np.asarray(sl, dtype=np.float64), float(np.max(np.abs(rl - Kl @ sl))), lu
+
+
 def exact_kkt(pb, passes=6):
     """The KKT solution, refined with extended-precision residuals and rounded to FP64.
     Also returns 'ext_resid', the infinity norm of the extended-precision residual of the
     unrounded iterate (a measure of how far the refinement got)."""
     K, rhs, nv = kkt_matrix(pb)
-    lu = spl.splu(K.tocsc())
-    sol = lu.solve(rhs)
-    Kl = K.astype(np.longdouble)
-    rl = rhs.astype(np.longdouble)
-    sl = sol.astype(np.longdouble)
-    for _ in range(passes):
-        r = rl - Kl @ sl
-        sl = sl + lu.solve(np.asarray(r, dtype=np.float64)).astype(np.longdouble)
-    out = _unpack(pb, np.asarray(sl, dtype=np.float64), nv)
-    out["ext_resid"] = float(np.max(np.abs(rl - Kl @ sl)))
+    sol, ext, _ = solve_refined(K, rhs, passes)
+    out = _unpack(pb, sol, nv)
+    out["ext_resid"] = ext
     return out
 
 

@@ -104,3 +104,78 @@ class ECLQRSolve(torch.autograd.Function):
 def solve(batch, *params):
     """Differentiable x, u (packed) of batch's problems with the given data (PARAM_KEYS order)."""
     return ECLQRSolve.apply(batch, *params)
+
+
+class ECLQRSolveCheckpointed(torch.autograd.Function):
+    """Checkpointed form for a batch of S segments of identical structure: seg is a Batch of one
+    segment (its problems' structure repeats S times in the packed params).  The forward pass solves
+    the segments one after another on seg's handle and keeps only their solutions; the backward pass
+    rebuilds each segment's factors from its data (the scan factors recomputed instead of stored)
+    and runs the adjoint on them.  Device workspace: one segment's instead of the batch's, at the
+    price of one more build per segment in the backward pass.
+
+    forward(seg, S, *params) -> (x, u), params in PARAM_KEYS order for all S segments."""
+
+    @staticmethod
+    def forward(ctx, seg, S, *params):
+        L = seg.layout
+        sizes = {k: int(getattr(L, k)) for k in PARAM_KEYS}
+        outs = {k: [] for k in ("x", "u", "lam", "mu", "eta", "alpha")}
+        for j in range(S):
+            sl = [p.detach()[j * sizes[k]:(j + 1) * sizes[k]].contiguous() for k, p in zip(PARAM_KEYS, params)]
+            out, status = _run(seg, sl[:-1], sl[-1])
+            if int(status.abs().max()) != 0:
+                raise RuntimeError("eclqr forward solve reported a nonzero status")
+            for k, t in zip(outs, out):
+                outs[k].append(t[:int(getattr(L, k))].clone())
+        sol = [torch.cat(outs[k]) for k in outs]
+        ctx.seg, ctx.S = seg, S
+        ctx.save_for_backward(*[p.detach() for p in params], *sol)
+        return sol[0].clone(), sol[1].clone()
+
+    @staticmethod
+    def backward(ctx, gx, gu):
+        seg, S = ctx.seg, ctx.S
+        nk = len(PARAM_KEYS)
+        saved = ctx.saved_tensors
+        params, sol = saved[:nk], saved[nk:]
+        L = seg.layout
+        f64 = dict(dtype=torch.float64, device=seg.device)
+        sizes = {k: int(getattr(L, k)) for k in PARAM_KEYS}
+        osz = {k: int(getattr(L, k)) for k in ("x", "u", "lam", "mu", "eta", "alpha")}
+        grads = [torch.zeros_like(p) for p in params]
+        for j in range(S):
+            sl = {k: p[j * sizes[k]:(j + 1) * sizes[k]].contiguous() for k, p in zip(PARAM_KEYS, params)}
+            w = [torch.zeros(max(1, v), **f64) for v in osz.values()]
+            for t, (k, v) in zip(w, osz.items()):
+                t[:v] = sol[list(osz).index(k)][j * v:(j + 1) * v]
+            # the forward factors of this segment, recomputed
+            _run(seg, [sl[k] for k in eclqr.DATA_KEYS], sl["s0"])
+            lx = torch.zeros(max(1, osz["x"]), **f64)
+            lu = torch.zeros(max(1, osz["u"]), **f64)
+            if gx is not None:
+                lx[:osz["x"]] = gx[j * osz["x"]:(j + 1) * osz["x"]]
+            if gu is not None:
+                lu[:osz["u"]] = gu[j * osz["u"]:(j + 1) * osz["u"]]
+            adj = dict(sl)
+            for k in _OFFSETS:
+                adj[k] = torch.zeros_like(adj[k])
+            adj["qv"] = -lx[:sizes["qv"]]
+            adj["rv"] = -lu[:sizes["rv"]]
+            wb, st_b = _run(seg, [adj[k].contiguous() for k in eclqr.DATA_KEYS], torch.zeros_like(sl["s0"]),
+                            reuse=True)
+            if int(st_b.abs().max()) != 0:
+                raise RuntimeError("eclqr adjoint solve reported a nonzero status")
+            gj = [torch.zeros(max(1, sizes[k]), **f64) for k in PARAM_KEYS]
+            g = eclqr.eclqr_grads(*[t.data_ptr() for t in gj])
+            eclqr._check(eclqr.eclqr_param_grads(seg.h, *[t.data_ptr() for t in w], *[t.data_ptr() for t in wb], g,
+                                                 seg._stream()), "eclqr_param_grads")
+            for gr, t, k in zip(grads, gj, PARAM_KEYS):
+                gr[j * sizes[k]:(j + 1) * sizes[k]] = t[:sizes[k]]
+        return (None, None, *grads)
+
+
+def solve_checkpointed(seg, segments, *params):
+    """Differentiable x, u (packed) of `segments` copies of seg's structure with the given data
+    (PARAM_KEYS order, all segments back to back); factors are recomputed in the backward pass."""
+    return ECLQRSolveCheckpointed.apply(seg, segments, *params)

@@ -73,3 +73,17 @@ def test_gradient_of_linear_cost_is_the_solution():
         q = pb.copy(); q.s0 = q.s0.copy(); q.s0[k] += 1.0
         # without state constraints x depends affinely on s0, so a unit step is exact
         assert abs((oracle.solve(q, refine=3).x[pb.N, 0] - base) - G["s0"][k]) < 1e-9
+
+
+@pytest.mark.parametrize("index", [0, 1])
+def test_sparse_implicit_gradient_matches_dense(index):
+    """The sparse form of the implicit gradient (oracle.exact's LU, for full-size problems) against the
+    dense least-squares form, on shrunk differentiable-batch draws."""
+    pb = synth.config("diff_batch", index=index, N=12)
+    rng = np.random.default_rng(index)
+    lx, lu = rng.standard_normal((pb.N + 1, pb.n)), rng.standard_normal((pb.N, pb.m))
+    a, b = implicit_gradients(pb, lx, lu), implicit_gradients(pb, lx, lu, sparse=True)
+    for k in FIELDS:
+        ref = np.asarray(a[k])
+        if ref.size:
+            assert np.max(np.abs(np.asarray(b[k]) - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref))), k
