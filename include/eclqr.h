@@ -113,7 +113,11 @@ typedef struct {
                       * per problem when the batch holds at least two problems per SM, else
                       * 7 to 64 stages.  A problem that fits one chunk is swept once per
                       * scan, from its terminal element, with no chunk aggregate           */
-  int32_t team_warps; /* warps of the CTA that runs one task: 1, 2, 4 or 8; 0 = 4            */
+  int32_t team_warps; /* warps of the CTA that runs one task: 1, 2, 4 or 8 for every kernel;
+                       * 0 (default) = per kernel: 4 when a launch has fewer than 4 tasks
+                       * per SM, else the kernel's measured best (1 for the per-problem
+                       * sweeps and the small per-stage kernels, 4 for the stage
+                       * elimination, 8 for the affine-chain sweep)                      */
   int32_t scan_skip;  /* 1 (default): take the shortcut of Sec. 6 (complete algorithm and
                        * complexity) where it applies: a problem without state-only or
                        * terminal rows whose every stage's mixed rows leave no row on x_i

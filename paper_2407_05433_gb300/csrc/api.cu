@@ -24,6 +24,7 @@ namespace {
 // static scratch of the team reductions and the Householder core (< 8 KB)
 constexpr int kMaxSmemBytes = 219 * 1024;
 constexpr int kTeamWarps = 4;  // default team: one warp per SM sub-partition
+constexpr int kManyTasksPerSm = 4;  // a launch with at least this many tasks per SM takes the table's team
 
 struct GroupHost {
   Group g;
@@ -71,11 +72,48 @@ struct eclqr_handle {
   int *fp64 = nullptr;      // mixed precision: per-problem flags of the Riccati sweep's precision
   int *any_host = nullptr;  // pinned host copy of it
   bool stale = false;  // the offset-dependent factors are a correction's (after eclqr_refine)
+  int sms = 152;       // SMs of the handle's device
 };
 
 namespace {
 
-// one CTA (a team of opt.team_warps warps) per task,
+// Team size of one launch.  opt.team_warps != 0 fixes it for every kernel.
+// Otherwise a launch with fewer than kManyTasksPerSm tasks per SM takes four
+// warps, one per SM sub-partition, so that one task spreads over the SM; a
+// launch with more takes the kernel's entry below.  There the SM is filled by
+// many tasks at once, and an FP64 warp instruction costs its sub-partition the
+// same time whatever its active lanes, so the sequential per-problem sweeps and
+// the small per-stage kernels run fastest as one warp per task: one warp forms
+// each reflector's scalars, each reduction and each triangular solve once,
+// where four warps would each repeat them, and needs no CTA barrier.  The
+// entries are the fastest team measured per kernel on the 4096-problem uneven
+// batch (each (n, m) group alone, about seven problems per SM): for example
+// the Riccati sweep takes 247 ms with one warp against 320 ms with four, and
+// the stage elimination, whose stage matrices fill four warps, 284 ms with four
+// against 374 ms with one.
+int team_for(const eclqr_handle *h, const void *kern, int ntasks) {
+  if (h->opt.team_warps != 0) return h->opt.team_warps;
+  if (ntasks < kManyTasksPerSm * h->sms) return kTeamWarps;
+  static const struct { const void *fn; int warps; } table[] = {
+      {(const void *)k_riccati_down, 1}, {(const void *)k_riccati_down_f32, 1},
+      {(const void *)k_primal_down, 1},  {(const void *)k_dual_down, 1},
+      {(const void *)k_aff_down, 8},     {(const void *)k_dual_leaf, 1},
+      {(const void *)k_dual_stage, 2},   {(const void *)k_param, 1},
+      {(const void *)k_resid, 1},        {(const void *)k_pcorr, 1},
+      {(const void *)k_kkt, 1},          {(const void *)k_post_roll, 1},
+      {(const void *)k_recover, 1},      {(const void *)k_check_inputs, 1},
+      {(const void *)k_refine_trial, 1}, {(const void *)k_refine_accept, 1},
+      {(const void *)k_refine_prep, 1},  {(const void *)k_refine_gate, 1},
+      {(const void *)k_refine_parts, 1}, {(const void *)k_refine_post, 1},
+      {(const void *)k_rescue_prep, 1},  {(const void *)k_scan_check, 1},
+      {(const void *)k_terminal, 1},     {(const void *)k_dual_terminal, 1},
+      {(const void *)k_lqr_up, 1}};
+  for (const auto &e : table)
+    if (e.fn == kern) return e.warps;
+  return kTeamWarps;
+}
+
+// one CTA (a team of team_for warps) per task,
 // with per_task doubles of dynamic shared memory
 template <typename... KArgs, typename... Args>
 int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cudaStream_t st, Args... args) {
@@ -92,7 +130,7 @@ int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cu
   const int grid = ntasks;
   const bool timed = h->timed == (const void *)kern && h->nev + 2 <= (int)h->ev.size();
   if (timed) cudaEventRecord(h->ev[h->nev], st);
-  kern<<<grid, 32 * h->opt.team_warps, smem, st>>>(args...);
+  kern<<<grid, 32 * team_for(h, (const void *)kern, ntasks), smem, st>>>(args...);
   if (timed) {
     cudaEventRecord(h->ev[h->nev + 1], st);
     h->nev += 2;
@@ -237,10 +275,9 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   if (!h) return ECLQR_ENOMEM;
   eclqr_default_options(&h->opt);
   if (opt) h->opt = *opt;
-  if (h->opt.team_warps == 0) h->opt.team_warps = kTeamWarps;
   const int tw = h->opt.team_warps;
   if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0) ||
-      !(tw == 1 || tw == 2 || tw == 4 || tw == 8) || !(h->opt.scan_skip == 0 || h->opt.scan_skip == 1) ||
+      !(tw == 0 || tw == 1 || tw == 2 || tw == 4 || tw == 8) || !(h->opt.scan_skip == 0 || h->opt.scan_skip == 1) ||
       h->opt.kkt_refine < 0 || h->opt.kkt_refine > 16 || !(h->opt.refine_tol >= 0) ||
       !(h->opt.riccati_fp32 == 0 || h->opt.riccati_fp32 == 1)) {
     delete h;
@@ -251,6 +288,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   cudaGetDevice(&h->device);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->sms = sms;
 
   // batch offsets of every problem
   const int P = d->num_problems;
