@@ -149,9 +149,13 @@ def job_rate(world, stages_per_rank, ms):
 
 
 # ---------------------------------------------------------------- workload, gates, algorithmic work
-def batched_problems(count=PROBLEMS):
+def batched_problems(count=PROBLEMS, state_dim=None):
+    """Draws 0..count-1 of the batch; with state_dim, only those whose state dimension is state_dim.
+    Returns (draw indices, problems)."""
     from paper_2407_05433_gb300 import synth
-    return [synth.config(WORKLOAD, index=j) for j in range(count)]
+    pbs = [synth.config(WORKLOAD, index=j) for j in range(count)]
+    keep = [j for j, pb in enumerate(pbs) if state_dim is None or pb.n == state_dim]
+    return keep, [pbs[j] for j in keep]
 
 
 def floor_gates():
@@ -237,13 +241,13 @@ def single_line(name, pb, dev, flush, stream, steps, **kw):
             "gate_passed": bool(r["status"] == 0 and r["resid"] <= KKT_GATE)}
 
 
-def autotune_kkt_refine(pbs, dev, gates, flush, stream, candidates=(2, 3, 4, 8)):
+def autotune_kkt_refine(pbs, dev, gates, flush, stream, candidates=(2, 3, 4, 8), team_warps=0):
     """(passes, trials): the smallest candidate whose eager pass leaves as many problems under their
     gate as the largest candidate; trials = [(passes, ms, passed)]."""
     from paper_2407_05433_gb300 import eclqr
     trials = []
     for kr in candidates:
-        b = eclqr.Batch(pbs, device=dev, kkt_refine=kr)
+        b = eclqr.Batch(pbs, device=dev, kkt_refine=kr, team_warps=team_warps)
         try:
             b.run()
             ms = statistics.median(_time_runs(b, 1, flush, stream))
@@ -541,9 +545,10 @@ def run_gpu(args):
     import numpy as np
     rank, world, local = dist_env()
     t_gen = time.perf_counter()
-    pbs = batched_problems(args.problems)     # host-side generation before any CUDA call
+    draws, pbs = batched_problems(args.problems, args.state_dim)  # host-side generation before any CUDA call
     t_gen = time.perf_counter() - t_gen
-    gates = floor_gates()
+    fg = floor_gates()
+    gates = {pos: fg[j] for pos, j in enumerate(draws) if j in fg}
     import torch
     from paper_2407_05433_gb300 import eclqr
     from paper_2407_05433_gb300 import build as build_mod
@@ -567,8 +572,8 @@ def run_gpu(args):
     # untimed setup: the fewest refinement passes on the KKT residual that leave as many problems
     # under their gate as the library default (8); a captured step records every pass, so passes
     # that no problem needs still cost their launches and the sweeps of slow-converging problems
-    kkt_refine, kr_trials = autotune_kkt_refine(pbs, dev, gates, flush, stream)
-    batch = eclqr.Batch(pbs, device=dev, kkt_refine=kkt_refine)
+    kkt_refine, kr_trials = autotune_kkt_refine(pbs, dev, gates, flush, stream, team_warps=args.team_warps)
+    batch = eclqr.Batch(pbs, device=dev, kkt_refine=kkt_refine, team_warps=args.team_warps)
     per_replay = batch.capture()            # eager pass on a side stream, then one captured pass
     for _ in range(max(3, args.warmup)):
         batch.replay()
@@ -633,7 +638,7 @@ def run_gpu(args):
         return 0
 
     flops_all = workload_flops()
-    fl = flops_all.get(WORKLOAD) if args.problems == PROBLEMS else None
+    fl = flops_all.get(WORKLOAD) if args.problems == PROBLEMS and args.state_dim is None else None
     peak = eclqr.eclqr_probe_fp64_peak()
     extras = {}
     kern = None
@@ -710,7 +715,9 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "problems_per_gpu": len(pbs), "stages_per_gpu": stages,
-                   "l2": "inputs of about 5 GB per GPU (larger than L2); a 256 MB buffer is also written between steps",
+                   "l2": f"inputs of {h2d / 1e9:.1f} GB per GPU (larger than L2); a 256 MB buffer is also written "
+                         "between steps",
+                   "team_warps": args.team_warps or "per kernel", "state_dim": args.state_dim,
                    "step": "graph replay of eclqr_build + eclqr_solve + eclqr_multipliers + eclqr_refine",
                    "refine": 2, "kkt_refine": kkt_refine, "kkt_refine_autotune": kr_trials,
                    "refine_tol": 5e-10, "generation_s": round(t_gen, 1)},
@@ -738,6 +745,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--problems", type=int, default=PROBLEMS, help="draws 0..problems-1 of the batch")
+    ap.add_argument("--state-dim", type=int, default=None,
+                    help="keep only the draws with this state dimension (one (n, m) group, for profiling)")
+    ap.add_argument("--team-warps", type=int, default=0,
+                    help="warps per task for every kernel (0: the library's per-kernel choice)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the plain solve, kernel times and other workloads")
     args = ap.parse_args()

@@ -95,7 +95,16 @@ static double g_flops = 0.0;
 static double g_phase[8];
 static int g_cur = 0;
 static int g_in_correction = 0;
-#define ADDF(x) do { double _f = (x); g_flops += _f; g_phase[g_in_correction ? 7 : g_cur] += _f; } while (0)
+/* set around a product that is not counted as work (a product with T_i = I, see step 5) */
+static int g_uncounted = 0;
+#define ADDF(x)                                                               \
+  do {                                                                        \
+    if (!g_uncounted) {                                                       \
+      double _f = (x);                                                        \
+      g_flops += _f;                                                          \
+      g_phase[g_in_correction ? 7 : g_cur] += _f;                             \
+    }                                                                         \
+  } while (0)
 
 /* ------------------------------------------------------------------ */
 /* small dense helpers, row-major, explicit leading dimensions          */
@@ -587,6 +596,10 @@ static int solve_once(const orc_problem *P, const orc_options *opt, double *x,
       const double *Hn = H + (size_t)(i + 1) * n * hld;
       int rn = hr[i + 1], pi = P->p[i], ni = nb[i], nn = nb[i + 1];
       int rows = pi + rn;
+      /* where the domain has no rows of rank (ur = 0), T = I and t = 0 (eq. state-param): a
+         product with T_i or T_{i+1} there is its other factor, which a solver copies, so its
+         flops are computed here but not counted as the method's work */
+      const int te = ur[i] == 0, tne = ur[i + 1] == 0;
       /* Gamma = [D; H B], [Phi | gamma] = [C T, C t + d; H A T, H (A t + c) + h] */
       for (int a = 0; a < pi; a++) {
         int src = po[i] + a;
@@ -600,15 +613,17 @@ static int solve_once(const orc_problem *P, const orc_options *opt, double *x,
         for (int l = 0; l < n; l++) s += P->C[(size_t)src * n + l] * ti_[l];
         Rhs[a * (n + 1) + ni] = s;
       }
-      ADDF(2.0 * pi * n * (ni + 1));
+      if (!te) ADDF(2.0 * pi * n * (ni + 1));
       /* A T and A t + c */
+      g_uncounted = te;
       gemm(0, 0, n, ni, n, 1.0, Ai, n, Ti, n, 0.0, AT, n);
+      g_uncounted = 0;
       for (int l = 0; l < n; l++) {
         double s = ci[l];
         for (int j = 0; j < n; j++) s += Ai[l * n + j] * ti_[j];
         tmp[l] = s;
       }
-      ADDF(2.0 * n * n);
+      if (!te) ADDF(2.0 * n * n);
       for (int a = 0; a < rn; a++) {
         const double *hrow = Hn + a * hld;
         for (int j = 0; j < m; j++) {
@@ -645,36 +660,46 @@ static int solve_once(const orc_problem *P, const orc_options *opt, double *x,
       /* reduced dynamics (eq. reduced-dynamics-data), S_{i+1} = T_{i+1}^T */
       double *Abi = Ab + (size_t)i * n * n, *Bbi = Bb + (size_t)i * n * m, *cbi = cb + (size_t)i * n;
       gemm(0, 0, n, ni, m, 1.0, Bi, m, Yi, n, 1.0, AT, n);  /* AT <- A T + B Y */
+      g_uncounted = tne;
       gemm(1, 0, nn, ni, n, 1.0, Tn, n, AT, n, 0.0, Abi, n);
+      g_uncounted = 0;
       gemm(0, 0, n, mi, m, 1.0, Bi, m, Zi, m, 0.0, BZ, m);       /* B Z */
+      g_uncounted = tne;
       gemm(1, 0, nn, mi, n, 1.0, Tn, n, BZ, m, 0.0, Bbi, m);
+      g_uncounted = 0;
       for (int l = 0; l < n; l++) {
         double s = tmp[l] - tn[l];       /* A t + c - t_{i+1} */
         for (int j = 0; j < m; j++) s += Bi[l * m + j] * yi[j];
         tmp2[l] = s;
       }
       ADDF(2.0 * n * m);
+      g_uncounted = tne;
       gemm(1, 0, nn, 1, n, 1.0, Tn, n, tmp2, 1, 0.0, cbi, 1);
+      g_uncounted = 0;
       /* state substitution (eq. state-cost-data) */
       const double *Qi = P->Q + (size_t)i * n * n, *Mi = P->M + (size_t)i * n * m;
       const double *Ri = P->R + (size_t)i * m * m, *qi = P->qv + (size_t)i * n, *ri = P->rv + (size_t)i * m;
-      gemm(0, 0, n, ni, n, 1.0, Qi, n, Ti, n, 0.0, tmp, n);           /* Q T */
       double *Qbi = Qb + (size_t)i * n * n;
+      g_uncounted = te;
+      gemm(0, 0, n, ni, n, 1.0, Qi, n, Ti, n, 0.0, tmp, n);           /* Q T */
       gemm(1, 0, ni, ni, n, 1.0, Ti, n, tmp, n, 0.0, Qbi, n);          /* Q^z = T^T Q T */
       gemm(1, 0, ni, m, n, 1.0, Ti, n, Mi, m, 0.0, Mz, m);             /* M^z = T^T M */
+      g_uncounted = 0;
       for (int l = 0; l < n; l++) {
         double s = qi[l];
         for (int j = 0; j < n; j++) s += Qi[l * n + j] * ti_[j];
         tmp2[l] = s;                                                    /* Q t + q */
       }
-      ADDF(2.0 * n * n);
+      if (!te) ADDF(2.0 * n * n);
+      g_uncounted = te;
       gemm(1, 0, ni, 1, n, 1.0, Ti, n, tmp2, 1, 0.0, qz, 1);            /* q^z */
+      g_uncounted = 0;
       for (int j = 0; j < m; j++) {
         double s = ri[j];
         for (int l = 0; l < n; l++) s += Mi[l * m + j] * ti_[l];
         rz[j] = s;                                                      /* r^z = M^T t + r */
       }
-      ADDF(2.0 * n * m);
+      if (!te) ADDF(2.0 * n * m);
       /* reduced cost (eq. reduced-cost-data) */
       gemm(0, 0, m, ni, m, 1.0, Ri, m, Yi, n, 0.0, RY, n);             /* R Y */
       gemm(0, 0, m, mi, m, 1.0, Ri, m, Zi, m, 0.0, RZ, m);             /* R Z */

@@ -360,9 +360,21 @@ __global__ void k_param(Group g, int per_task) {
   double *Ys = scr + 2 * n;  // rank x 1
   wtqr_solve(Wt, (r > 0 ? r : 1), Qf, n, perm, r, n, rank, hb, 1, 1, X, 1, Ys, 1);
   double *UT = ws + g.ws.UT, *tt = ws + g.ws.t;
-  for (int idx = tid; idx < n * n; idx += TEAM) UT[idx] = Qf[idx];
-  for (int i = tid; i < n; i += TEAM) tt[i] = X[i];
-  if (tid == 0) { wi[SI_UR] = rank; wi[SI_NBAR] = n - rank; }
+  // T = I and t = 0 exactly (compared as bit patterns, on the integer pipe; a zero of
+  // either sign counts as zero): the stage elimination then skips its products with T_i,
+  // whose results are the factors themselves
+  bool eye = true;
+  for (int idx = tid; idx < n * n; idx += TEAM) {
+    UT[idx] = Qf[idx];
+    const long long b = __double_as_longlong(Qf[idx]);
+    eye = eye && ((idx / n) * (n + 1) == idx ? b == __double_as_longlong(1.0) : (b << 1) == 0);
+  }
+  for (int i = tid; i < n; i += TEAM) {
+    tt[i] = X[i];
+    eye = eye && (__double_as_longlong(X[i]) << 1) == 0;
+  }
+  eye = __syncthreads_and(eye) != 0;
+  if (tid == 0) { wi[SI_UR] = rank; wi[SI_NBAR] = n - rank; wi[SI_TEYE] = (rank == 0 && eye) ? 1 : 0; }
   tsync();
   if (S.i == P.N) {
     // terminal cost (eq. terminal-cost-data): Qbar_N = T' Q_N T, qbar_N = T'(Q_N t + q_N)
@@ -395,6 +407,9 @@ __global__ void k_elim(Group g, int per_task) {
   int *wi = stage_wi(g, s), *win = stage_wi(g, s + 1);
   const int ur = wi[SI_UR], nb = n - ur, ur1 = win[SI_UR], nn = n - ur1, r1 = win[SI_HROWS];
   const int rows = S.p + r1;
+  // T_i = I, t_i = 0 (te) and T_{i+1} = I, t_{i+1} = 0 (tne): a product with T is then its other
+  // factor, bit for bit up to the sign of zeros, and is copied instead of computed
+  const bool te = wi[SI_TEYE] != 0, tne = win[SI_TEYE] != 0;
   const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
   const double *c = g.c + P.oc + (size_t)i * n;
   const double *Q = g.Q + P.oQ + (size_t)i * n * n, *Mm = g.M + P.oM + (size_t)i * n * m;
@@ -425,11 +440,16 @@ __global__ void k_elim(Group g, int per_task) {
   double *ys = Ry + m, *scr = ys + m;    // scratch >= 2n + 2 rows
   int *perm = (int *)(scr + 4 * n + 2 * m + 2 * rmax);
   // A T, A t + c
-  wgemm<false, false>(n, nb, n, 1.0, A, n, T, n, 0.0, AT, n);
-  for (int l = tid; l < n; l += TEAM) {
-    double s0 = c[l];
-    for (int j = 0; j < n; j++) s0 = fma(A[l * n + j], t[j], s0);
-    Atc[l] = s0;
+  if (te) {
+    for (int idx = tid; idx < n * n; idx += TEAM) AT[idx] = A[idx];
+    for (int l = tid; l < n; l += TEAM) Atc[l] = c[l];
+  } else {
+    wgemm<false, false>(n, nb, n, 1.0, A, n, T, n, 0.0, AT, n);
+    for (int l = tid; l < n; l += TEAM) {
+      double s0 = c[l];
+      for (int j = 0; j < n; j++) s0 = fma(A[l * n + j], t[j], s0);
+      Atc[l] = s0;
+    }
   }
   for (int idx = tid; idx < r1 * (n + 1); idx += TEAM) Hs[idx] = Hn[idx];
   tsync();
@@ -443,7 +463,9 @@ __global__ void k_elim(Group g, int per_task) {
     int a = idx / (nb + 1), j = idx - a * (nb + 1);
     const double *Cr = g.C + P.oC + (size_t)(S.prow + a) * n;
     double s0 = 0.0;
-    if (j < nb) {
+    if (te) {
+      s0 = (j < nb) ? Cr[j] : g.d[P.od + S.prow + a];
+    } else if (j < nb) {
       for (int l = 0; l < n; l++) s0 = fma(Cr[l], T[l * n + j], s0);
     } else {
       s0 = g.d[P.od + S.prow + a];
@@ -482,33 +504,53 @@ __global__ void k_elim(Group g, int per_task) {
   tsync();
   // reduced dynamics (eq. reduced-dynamics-data), S_{i+1} = T_{i+1}^T
   wgemm<false, false>(n, nb, m, 1.0, B, m, Yw, n, 1.0, AT, n);            // A T + B Y
-  wgemm<true, false>(nn, nb, n, 1.0, Tn, n, AT, n, 0.0, ws + g.ws.Ab, n);
+  if (!tne) wgemm<true, false>(nn, nb, n, 1.0, Tn, n, AT, n, 0.0, ws + g.ws.Ab, n);
   wgemm<false, false>(n, mb, m, 1.0, B, m, Z, m, 0.0, BZ, m);             // B Z
-  wgemm<true, false>(nn, mb, n, 1.0, Tn, n, BZ, m, 0.0, ws + g.ws.Bb, m);
+  if (!tne) wgemm<true, false>(nn, mb, n, 1.0, Tn, n, BZ, m, 0.0, ws + g.ws.Bb, m);
   for (int l = tid; l < n; l += TEAM) {
     double s0 = Atc[l] - tn[l];
     for (int j = 0; j < m; j++) s0 = fma(B[l * m + j], ys[j], s0);
     cv[l] = s0;
   }
   tsync();
-  wgemm<true, false>(nn, 1, n, 1.0, Tn, n, cv, 1, 0.0, ws + g.ws.cb, 1);
+  if (tne) {  // Abar = A T + B Y, Bbar = B Z, cbar = c_v
+    for (int idx = tid; idx < n * nb; idx += TEAM) {
+      const int a = idx / nb, j = idx - a * nb;
+      ws[g.ws.Ab + a * n + j] = AT[a * n + j];
+    }
+    for (int idx = tid; idx < n * mb; idx += TEAM) {
+      const int a = idx / mb, j = idx - a * mb;
+      ws[g.ws.Bb + a * m + j] = BZ[a * m + j];
+    }
+    for (int l = tid; l < n; l += TEAM) ws[g.ws.cb + l] = cv[l];
+  } else {
+    wgemm<true, false>(nn, 1, n, 1.0, Tn, n, cv, 1, 0.0, ws + g.ws.cb, 1);
+  }
   // state substitution (eq. state-cost-data)
-  wgemm<false, false>(n, nb, n, 1.0, Q, n, T, n, 0.0, QT, n);             // Q T
   double *Qb = ws + g.ws.Qb, *Mb = ws + g.ws.Mb, *Rb = ws + g.ws.Rb;
-  wgemm<true, false>(nb, nb, n, 1.0, T, n, QT, n, 0.0, Qb, n);            // Q^z
-  wgemm<true, false>(nb, m, n, 1.0, T, n, Mm, m, 0.0, Mz, m);             // M^z
-  for (int l = tid; l < n; l += TEAM) {
-    double s0 = q[l];
-    for (int j = 0; j < n; j++) s0 = fma(Q[l * n + j], t[j], s0);
-    Qtq[l] = s0;
+  if (te) {  // Q^z = Q, M^z = M, q^z = q, r^z = r
+    for (int idx = tid; idx < n * n; idx += TEAM) Qb[idx] = Q[idx];
+    for (int idx = tid; idx < n * m; idx += TEAM) Mz[idx] = Mm[idx];
+    for (int l = tid; l < n; l += TEAM) qz[l] = q[l];
+    for (int a = tid; a < m; a += TEAM) rz[a] = r[a];
+    tsync();
+  } else {
+    wgemm<false, false>(n, nb, n, 1.0, Q, n, T, n, 0.0, QT, n);             // Q T
+    wgemm<true, false>(nb, nb, n, 1.0, T, n, QT, n, 0.0, Qb, n);            // Q^z
+    wgemm<true, false>(nb, m, n, 1.0, T, n, Mm, m, 0.0, Mz, m);             // M^z
+    for (int l = tid; l < n; l += TEAM) {
+      double s0 = q[l];
+      for (int j = 0; j < n; j++) s0 = fma(Q[l * n + j], t[j], s0);
+      Qtq[l] = s0;
+    }
+    for (int a = tid; a < m; a += TEAM) {
+      double s0 = r[a];
+      for (int l = 0; l < n; l++) s0 = fma(Mm[l * m + a], t[l], s0);
+      rz[a] = s0;                                                           // r^z
+    }
+    tsync();
+    wgemm<true, false>(nb, 1, n, 1.0, T, n, Qtq, 1, 0.0, qz, 1);            // q^z
   }
-  for (int a = tid; a < m; a += TEAM) {
-    double s0 = r[a];
-    for (int l = 0; l < n; l++) s0 = fma(Mm[l * m + a], t[l], s0);
-    rz[a] = s0;                                                           // r^z
-  }
-  tsync();
-  wgemm<true, false>(nb, 1, n, 1.0, T, n, Qtq, 1, 0.0, qz, 1);            // q^z
   // reduced cost (eq. reduced-cost-data)
   wgemm<false, false>(m, nb, m, 1.0, R, m, Yw, n, 0.0, RY, n);            // R Y
   wgemm<false, false>(m, mb, m, 1.0, R, m, Z, m, 0.0, RZ, m);             // R Z

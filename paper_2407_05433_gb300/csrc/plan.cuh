@@ -96,7 +96,8 @@ __host__ __device__ inline WsLayout make_ws_layout(int n, int m, int pmax, int q
 }
 
 // per-stage ints
-enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_STRIDE = 8 };
+// SI_TEYE: 1 when T_i is the identity and t_i = 0, bit for bit (X_i = R^n)
+enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_TEYE = 5, SI_STRIDE = 8 };
 // per-chunk-slot ints: rows, left dim, right dim (0 = unary/value)
 enum { CI_ROWS = 0, CI_NA = 1, CI_NB = 2, CI_ROWS2 = 3, CI_STRIDE = 4 };
 

@@ -725,11 +725,14 @@ def test_stage_varying_dimensions_against_their_own_dense_kkt(seed):
 
 def test_work_is_linear_in_the_horizon_and_cubic_in_the_local_sizes():
     """Sec. 6's complexity: O(N) work over the horizon, cubic in the bounded local dimensions.  The oracle's
-    flop count (the roofline's algorithmic work) doubles with N and tends to 8x when n, m, p and the
-    terminal rows all double."""
+    flop count (the roofline's algorithmic work) is affine in N -- each added stage costs the same, and
+    the few stages whose domain the terminal rows restrict add a constant -- and tends to 8x when n, m,
+    p and the terminal rows all double."""
     for name in ("single_n4", "long_n16", "table1"):
         f = [oracle.solve(synth.config(name, N=N)).flops for N in (64, 128, 256)]
-        assert abs(f[1] / f[0] - 2.0) < 0.01 and abs(f[2] / f[1] - 2.0) < 0.01, (name, f)
+        d1, d2 = f[1] - f[0], f[2] - f[1]
+        assert d1 > 0 and abs(d2 / d1 - 2.0) < 0.01, (name, f)
+        assert abs(f[1] / f[0] - 2.0) < 0.05, (name, f)
     f = []
     for n in (8, 16, 32):
         q = np.zeros(65, np.int32)
