@@ -134,6 +134,13 @@ typedef struct {
                        * refinement and multipliers); eclqr_refine then refines in FP64
                        * and redoes in FP64 the problems it leaves above refine_tol.
                        * 0 (default): FP64 throughout                                   */
+  int32_t persist;    /* persistent launches of the per-problem sweeps: a fixed number of
+                       * CTAs per SM, each taking the next task from a device counter,
+                       * longest horizon first (Sec. 6, complexity and depth: the sweeps'
+                       * depth is the longest horizon, so it starts first).  0 (default):
+                       * 8 CTAs per SM for launches with at least 4 tasks per SM; k in
+                       * 1..32: k CTAs per SM for every launch with more than k tasks per
+                       * SM; -1: one CTA per task.  Results are the same either way.      */
 } eclqr_options;
 
 /* element counts of every packed array (for allocation) */

@@ -25,6 +25,7 @@ namespace {
 constexpr int kMaxSmemBytes = 219 * 1024;
 constexpr int kTeamWarps = 4;  // default team: one warp per SM sub-partition
 constexpr int kManyTasksPerSm = 4;  // a launch with at least this many tasks per SM takes the table's team
+constexpr int kPersistCtasPerSm = 8;  // default CTAs per SM of a persistent launch
 
 struct GroupHost {
   Group g;
@@ -34,6 +35,7 @@ struct GroupHost {
   int levels = 0;
   bool any_skip = false;  // some problem of the group may take the Sec. 6 shortcut
   void *dmem = nullptr;
+  int *queue = nullptr;  // device counter of the group's persistent launches (in dmem)
   std::vector<int> ids;  // batch indices of the problems in this group
 };
 
@@ -113,10 +115,11 @@ int team_for(const eclqr_handle *h, const void *kern, int ntasks) {
   return kTeamWarps;
 }
 
-// one CTA (a team of team_for warps) per task,
-// with per_task doubles of dynamic shared memory
+// grid CTAs (teams of team_for warps, chosen for ntasks tasks), with per_task
+// doubles of dynamic shared memory
 template <typename... KArgs, typename... Args>
-int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cudaStream_t st, Args... args) {
+int launch_grid(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int grid, int per_task, cudaStream_t st,
+                Args... args) {
   if (ntasks <= 0) return ECLQR_OK;
   const size_t smem = (size_t)per_task * sizeof(double);
   if (smem > (size_t)kMaxSmemBytes) return ECLQR_EINVAL;
@@ -127,7 +130,6 @@ int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cu
         cudaSuccess)
       return ECLQR_ECUDA;
   }
-  const int grid = ntasks;
   const bool timed = h->timed == (const void *)kern && h->nev + 2 <= (int)h->ev.size();
   if (timed) cudaEventRecord(h->ev[h->nev], st);
   kern<<<grid, 32 * team_for(h, (const void *)kern, ntasks), smem, st>>>(args...);
@@ -137,6 +139,31 @@ int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cu
   }
   h->launches++;
   return cudaPeekAtLastError() == cudaSuccess ? ECLQR_OK : ECLQR_ECUDA;
+}
+
+// one CTA per task
+template <typename... KArgs, typename... Args>
+int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cudaStream_t st, Args... args) {
+  return launch_grid(h, kern, ntasks, ntasks, per_task, st, args...);
+}
+
+// A per-problem sweep as a persistent launch: per_sm CTAs per SM take the tasks
+// from the group's counter in index order (longest horizon first), so an SM that
+// finishes its problems early takes more instead of idling while the longest
+// sweeps end.  opt.persist = 0 does this for launches with at least
+// kManyTasksPerSm tasks per SM, with kPersistCtasPerSm CTAs per SM; k > 0 for
+// every launch with more than k tasks per SM; -1 never.  Otherwise one CTA per
+// task.  The kernel's last argument is the counter, or null.
+template <typename... KArgs, typename... Args>
+int launch_sweep(eclqr_handle *h, int *queue, void (*kern)(KArgs...), int ntasks, int per_task, cudaStream_t st,
+                 Args... args) {
+  if (ntasks <= 0) return ECLQR_OK;
+  const int per_sm = h->opt.persist == 0 ? kPersistCtasPerSm : h->opt.persist;
+  const bool many = h->opt.persist != 0 || ntasks >= kManyTasksPerSm * h->sms;
+  if (h->opt.persist == -1 || !many || ntasks <= per_sm * h->sms)
+    return launch(h, kern, ntasks, per_task, st, args..., (int *)nullptr);
+  if (cudaMemsetAsync(queue, 0, sizeof(int), st) != cudaSuccess) return ECLQR_ECUDA;
+  return launch_grid(h, kern, ntasks, per_sm * h->sms, per_task, st, args..., queue);
 }
 
 #define TRY(x)                 \
@@ -241,6 +268,7 @@ void eclqr_default_options(eclqr_options *opt) {
   opt->kkt_refine = 8;
   opt->refine_tol = 5e-10;
   opt->riccati_fp32 = 0;
+  opt->persist = 0;
 }
 
 int eclqr_layout(const eclqr_desc *d, eclqr_layout_info *out) {
@@ -279,7 +307,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0) ||
       !(tw == 0 || tw == 1 || tw == 2 || tw == 4 || tw == 8) || !(h->opt.scan_skip == 0 || h->opt.scan_skip == 1) ||
       h->opt.kkt_refine < 0 || h->opt.kkt_refine > 16 || !(h->opt.refine_tol >= 0) ||
-      !(h->opt.riccati_fp32 == 0 || h->opt.riccati_fp32 == 1)) {
+      !(h->opt.riccati_fp32 == 0 || h->opt.riccati_fp32 == 1) || h->opt.persist < -1 || h->opt.persist > 32) {
     delete h;
     return ECLQR_EINVAL;
   }
@@ -446,7 +474,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     size_t o_CS0 = take(sizeof(double) * (size_t)g.cs_stride * g.nslot);
     size_t o_CS1 = take(sizeof(double) * (size_t)g.cs_stride * g.nslot);
     size_t o_CI0 = take(sizeof(int) * CI_STRIDE * g.nslot), o_CI1 = take(sizeof(int) * CI_STRIDE * g.nslot);
-    size_t o_need = take(sizeof(int) * (size_t)g.nprob);
+    size_t o_need = take(sizeof(int) * (size_t)g.nprob), o_queue = take(sizeof(int));
     if (cudaMalloc(&gh.dmem, off) != cudaSuccess) {
       for (auto &x : h->groups) cudaFree(x.dmem);
       delete h;
@@ -471,6 +499,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     g.CI[0] = (int *)(base + o_CI0);
     g.CI[1] = (int *)(base + o_CI1);
     g.need_scan = (int *)(base + o_need);
+    gh.queue = (int *)(base + o_queue);
     h->groups.push_back(gh);
   }
   if (h->opt.kkt_refine > 0) {
@@ -561,7 +590,7 @@ int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, 
   TRY(launch(h, k_lqr_up, g.nslot, su, gst, g, su));
   src = 0;
   for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_lqr_level, g.nslot, slv, gst, g, src, 1 << k, slv));
-  TRY(launch(h, k_riccati_down, g.nslot, sr, gst, g, src, sr));
+  TRY(launch_sweep(h, gh.queue, k_riccati_down, g.nslot, sr, gst, g, src, sr));
   if (g.fp64) TRY(launch(h, k_riccati_down_f32, g.nslot, sr, gst, g, src, sr));
   return ECLQR_OK;
 }

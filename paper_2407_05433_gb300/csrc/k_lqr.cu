@@ -215,8 +215,12 @@ __global__ void k_lqr_level(Group g, int src, int d, int per_task) {
 // rows signed so that its diagonal is positive.  Stored per stage: P_i = R_i'R_i,
 // p_i = R_i's_i, K, k, the Cholesky factor of H_uu = R_vv'R_vv and
 // Phi = Abar + Bbar K (the closed-loop map of the affine chains).
-__global__ void k_riccati_down(Group g, int fin, int per_task) {
-  const int t = team_task();
+static __device__ void riccati_task(const Group &g, int fin, int t, int per_task);
+__global__ void k_riccati_down(Group g, int fin, int per_task, int *queue) {
+  for_tasks(g.nslot, queue, [&](int t) { riccati_task(g, fin, t, per_task); });
+}
+
+static __device__ void riccati_task(const Group &g, int fin, int t, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];

@@ -33,7 +33,7 @@ __global__ void k_elim(Group g, int per_task);
 enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_PLIN_ = 2, AFF_NU_ = 3 };
 __global__ void k_lqr_up(Group g, int per_task);
 __global__ void k_lqr_level(Group g, int src, int d, int per_task);
-__global__ void k_riccati_down(Group g, int fin, int per_task);
+__global__ void k_riccati_down(Group g, int fin, int per_task, int *queue);
 __global__ void k_riccati_down_f32(Group g, int fin, int per_task);  // k_mixed.cu
 __global__ void k_aff_up(Group g, int mode, int per_task);
 __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task);

@@ -179,6 +179,28 @@ __device__ __forceinline__ int team_task() { return blockIdx.x; }
 extern __shared__ double g_smem[];
 __device__ __forceinline__ double *team_smem(int /*per_task*/) { return g_smem; }
 
+// Runs body(t) for the tasks [0, ntasks) of a launch.  queue null: the CTA's own
+// task.  Otherwise the launch is persistent: each CTA takes the next task index
+// from the counter *queue (zero before the launch) until none is left, so the
+// tasks start in index order -- longest horizon first, as the plan orders the
+// problems -- and an SM that finishes early takes more work.
+template <typename F>
+__device__ __forceinline__ void for_tasks(int ntasks, int *queue, F body) {
+  if (queue == nullptr) {
+    body(team_task());
+    return;
+  }
+  __shared__ int next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+    __syncthreads();
+    const int t = next;
+    __syncthreads();  // every thread has read next before thread 0 takes the following task
+    if (t >= ntasks) return;
+    body(t);
+  }
+}
+
 // status codes (mirror include/eclqr.h)
 enum {
   ST_OK = 0, ST_INFEASIBLE_SUFFIX = 1, ST_INFEASIBLE_X0 = 2, ST_RANK_INCONSISTENT = 3,
