@@ -53,6 +53,8 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 PLAIN_SAMPLE = 24
 # kernels whose launches carry one phase of the method alone when every problem is one chunk
 PHASE_KERNELS = {"k_primal_down": 0, "k_param": 1, "k_elim": 2, "k_riccati_down": 3, "k_dual_down": 5}
+# kernels that carry the rest of the same phase (their time counts with the phase's kernel)
+PHASE_PARTNERS = {"k_riccati_down": ("k_riccati_finish",)}
 
 
 def dist_env():
@@ -285,13 +287,15 @@ def measure_kernels(pbs, dev, flush, stream, flops):
     """Per-kernel device time of one pass over the batch (without the refinement on the KKT
     residual), one (n, m) group at a time (groups run on concurrent streams in the batch itself,
     where one kernel's events would also cover the others' work).
-    Every kernel of PHASE_KERNELS carries its phase alone when every problem is one chunk, so its
-    achieved FP64 rate is the phase's algorithmic flops over its summed launch time."""
+    Every kernel of PHASE_KERNELS carries its phase alone when every problem is one chunk (together
+    with its PHASE_PARTNERS), so its achieved FP64 rate is the phase's algorithmic flops over the
+    summed launch time of those kernels."""
     from paper_2407_05433_gb300 import eclqr
     groups = {}
     for pb in pbs:
         groups.setdefault((pb.n, pb.m), []).append(pb)
-    names = list(PHASE_KERNELS) + ["k_lqr_up", "k_lqr_level", "k_primal_up", "k_dual_up", "k_aff_up",
+    names = list(PHASE_KERNELS) + [p for ps in PHASE_PARTNERS.values() for p in ps] + [
+                                   "k_lqr_up", "k_lqr_level", "k_primal_up", "k_dual_up", "k_aff_up",
                                    "k_aff_level", "k_aff_down", "k_kkt", "k_resid", "k_pcorr", "k_dual_leaf",
                                    "k_dual_stage", "k_dual_root", "k_refine_trial"]
     ms = {k: 0.0 for k in names}
@@ -317,9 +321,12 @@ def measure_kernels(pbs, dev, flush, stream, flops):
            "launches_per_step": {k: v for k, v in launches.items() if v}}
     if flops:
         ph = flops["phase_flops"]
-        out["phase_kernels"] = {k: {"phase": p, "ms": ms[k], "algorithmic_flops": ph[p],
-                                    "achieved_tflops": ph[p] / (ms[k] * 1e-3) / 1e12 if ms[k] else None}
-                                for k, p in PHASE_KERNELS.items()}
+        out["phase_kernels"] = {}
+        for k, p in PHASE_KERNELS.items():
+            t = ms[k] + sum(ms[q] for q in PHASE_PARTNERS.get(k, ()))
+            out["phase_kernels"][k] = {"phase": p, "ms": t, "with": list(PHASE_PARTNERS.get(k, ())),
+                                       "algorithmic_flops": ph[p],
+                                       "achieved_tflops": ph[p] / (t * 1e-3) / 1e12 if t else None}
     return out
 
 

@@ -79,40 +79,51 @@ struct eclqr_handle {
 
 namespace {
 
-// Team size of one launch.  opt.team_warps != 0 fixes it for every kernel.
-// Otherwise a launch with fewer than kManyTasksPerSm tasks per SM takes four
-// warps, one per SM sub-partition, so that one task spreads over the SM; a
-// launch with more takes the kernel's entry below.  There the SM is filled by
-// many tasks at once, and an FP64 warp instruction costs its sub-partition the
-// same time whatever its active lanes, so the sequential per-problem sweeps and
-// the small per-stage kernels run fastest as one warp per task: one warp forms
-// each reflector's scalars, each reduction and each triangular solve once,
-// where four warps would each repeat them, and needs no CTA barrier.  The
-// entries are the fastest team measured per kernel on the 4096-problem uneven
-// batch (each (n, m) group alone, about seven problems per SM): for example
-// the Riccati sweep takes 247 ms with one warp against 320 ms with four, and
-// the stage elimination, whose stage matrices fill four warps, 284 ms with four
-// against 374 ms with one.
-int team_for(const eclqr_handle *h, const void *kern, int ntasks) {
+// Team size of one launch of a kernel on a group with state dimension n.
+// opt.team_warps != 0 fixes it for every kernel.  Otherwise a launch with fewer
+// than kManyTasksPerSm tasks per SM takes four warps, one per SM sub-partition,
+// so that one task spreads over the SM.  A launch with more takes the kernel's
+// entry below.  There the SM is filled by many tasks at once, and an FP64 warp
+// instruction costs its sub-partition the same time whatever its active lanes,
+// so the sequential per-problem sweeps and the small per-stage kernels run
+// fastest as one warp per task: one warp forms each reflector's scalars, each
+// reduction and each triangular solve once, where four warps would each repeat
+// them, and needs no CTA barrier.  The entries are the fastest team measured per
+// kernel and state dimension on the 4096-problem uneven batch (each (n, m) group
+// alone, about seven problems per SM).  For example the Riccati sweep takes 247
+// ms over the four groups with one warp per problem against 320 ms with four;
+// the stage elimination takes 14 ms with one warp at n = 8 against 29 ms with
+// four, but 86 ms with four at n = 24 against 120 ms with one, where its stage
+// matrices fill four warps.
+int team_for(const eclqr_handle *h, const void *kern, int ntasks, int n) {
   if (h->opt.team_warps != 0) return h->opt.team_warps;
   if (ntasks < kManyTasksPerSm * h->sms) return kTeamWarps;
-  static const struct { const void *fn; int warps; } table[] = {
-      {(const void *)k_riccati_down, 1}, {(const void *)k_riccati_down_f32, 1},
-      {(const void *)k_primal_down, 1},  {(const void *)k_dual_down, 1},
-      {(const void *)k_aff_down, 8},     {(const void *)k_dual_leaf, 1},
-      {(const void *)k_dual_stage, 2},   {(const void *)k_param, 1},
-      {(const void *)k_resid, 1},        {(const void *)k_pcorr, 1},
-      {(const void *)k_kkt, 1},          {(const void *)k_post_roll, 1},
-      {(const void *)k_recover, 1},      {(const void *)k_check_inputs, 1},
-      {(const void *)k_refine_trial, 1}, {(const void *)k_refine_accept, 1},
-      {(const void *)k_refine_prep, 1},  {(const void *)k_refine_gate, 1},
-      {(const void *)k_refine_parts, 1}, {(const void *)k_refine_post, 1},
-      {(const void *)k_rescue_prep, 1},  {(const void *)k_scan_check, 1},
-      {(const void *)k_terminal, 1},     {(const void *)k_dual_terminal, 1},
-      {(const void *)k_lqr_up, 1}};
+  // warps below n_from, and from n_from up
+  static const struct { const void *fn; int warps, n_from, warps_from; } table[] = {
+      {(const void *)k_riccati_down, 1, 0, 1},   {(const void *)k_riccati_down_f32, 1, 0, 1},
+      {(const void *)k_riccati_finish, 1, 0, 1}, {(const void *)k_elim, 1, 16, 4},
+      {(const void *)k_primal_down, 1, 24, 2},   {(const void *)k_dual_down, 1, 0, 1},
+      {(const void *)k_aff_down, 8, 0, 8},       {(const void *)k_dual_leaf, 1, 0, 1},
+      {(const void *)k_dual_stage, 2, 0, 2},     {(const void *)k_param, 1, 0, 1},
+      {(const void *)k_resid, 1, 0, 1},          {(const void *)k_pcorr, 1, 0, 1},
+      {(const void *)k_kkt, 1, 0, 1},            {(const void *)k_post_roll, 1, 0, 1},
+      {(const void *)k_recover, 1, 0, 1},        {(const void *)k_check_inputs, 1, 0, 1},
+      {(const void *)k_refine_trial, 1, 0, 1},   {(const void *)k_refine_accept, 1, 0, 1},
+      {(const void *)k_refine_prep, 1, 0, 1},    {(const void *)k_refine_gate, 1, 0, 1},
+      {(const void *)k_refine_parts, 1, 0, 1},   {(const void *)k_refine_post, 1, 0, 1},
+      {(const void *)k_rescue_prep, 1, 0, 1},    {(const void *)k_scan_check, 1, 0, 1},
+      {(const void *)k_terminal, 1, 0, 1},       {(const void *)k_dual_terminal, 1, 0, 1},
+      {(const void *)k_lqr_up, 1, 0, 1}};
   for (const auto &e : table)
-    if (e.fn == kern) return e.warps;
+    if (e.fn == kern) return n >= e.n_from ? e.warps_from : e.warps;
   return kTeamWarps;
+}
+
+// the state dimension of the group a launch works on (every kernel's first argument)
+inline int group_n(const Group &g) { return g.n; }
+template <typename A0, typename... Rest>
+int group_n(const A0 &a0, const Rest &...) {
+  return group_n(a0);
 }
 
 // grid CTAs (teams of team_for warps, chosen for ntasks tasks), with per_task
@@ -132,7 +143,7 @@ int launch_grid(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int grid, i
   }
   const bool timed = h->timed == (const void *)kern && h->nev + 2 <= (int)h->ev.size();
   if (timed) cudaEventRecord(h->ev[h->nev], st);
-  kern<<<grid, 32 * team_for(h, (const void *)kern, ntasks), smem, st>>>(args...);
+  kern<<<grid, 32 * team_for(h, (const void *)kern, ntasks, group_n(args...)), smem, st>>>(args...);
   if (timed) {
     cudaEventRecord(h->ev[h->nev + 1], st);
     h->nev += 2;
@@ -371,6 +382,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       const int n = g.n, m = g.m;
       const int need = std::max({smem_primal_sweep(n, m, pmax, qmax), smem_rel_level(n, pmax, qmax), smem_param(n),
                                  smem_elim(n, m, pmax), smem_lqr_up(n, m), smem_lqr_level(n), smem_riccati(n, m),
+                                 smem_riccati_finish(n, m),
                                  smem_aff(n, m), smem_dual_stage(n, m), smem_dual_sweep(n, m, pmax, qmax),
                                  smem_dual_leaf(n, m, pmax, qmax), smem_scan_check(n, m, pmax)});
       if ((size_t)need * sizeof(double) > (size_t)kMaxSmemBytes) {
@@ -387,7 +399,8 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
           {(const void *)k_primal_up, sw}, {(const void *)k_primal_down, sw}, {(const void *)k_rel_level, sl},
           {(const void *)k_param, smem_param(n)}, {(const void *)k_elim, smem_elim(n, m, pmax)},
           {(const void *)k_lqr_up, smem_lqr_up(n, m)}, {(const void *)k_lqr_level, smem_lqr_level(n)},
-          {(const void *)k_riccati_down, smem_riccati(n, m)}, {(const void *)k_aff_up, sa},
+          {(const void *)k_riccati_down, smem_riccati(n, m)},
+          {(const void *)k_riccati_finish, smem_riccati_finish(n, m)}, {(const void *)k_aff_up, sa},
           {(const void *)k_aff_level, sa}, {(const void *)k_aff_down, sa}, {(const void *)k_resid, 3 * n + 2 * m},
           {(const void *)k_pcorr, n + m}, {(const void *)k_dual_stage, smem_dual_stage(n, m)},
           {(const void *)k_dual_terminal, sdw}, {(const void *)k_dual_up, sdw}, {(const void *)k_dual_down, sdw},
@@ -592,6 +605,8 @@ int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, 
   for (int k = 0; k < gh.levels; k++, src ^= 1) TRY(launch(h, k_lqr_level, g.nslot, slv, gst, g, src, 1 << k, slv));
   TRY(launch_sweep(h, gh.queue, k_riccati_down, g.nslot, sr, gst, g, src, sr));
   if (g.fp64) TRY(launch(h, k_riccati_down_f32, g.nslot, sr, gst, g, src, sr));
+  const int sf = smem_riccati_finish(n, m);
+  TRY(launch(h, k_riccati_finish, g.nstage, sf, gst, g, sf));
   return ECLQR_OK;
 }
 
@@ -973,7 +988,8 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
       {"k_rel_level", (const void *)k_rel_level}, {"k_primal_down", (const void *)k_primal_down},
       {"k_param", (const void *)k_param}, {"k_elim", (const void *)k_elim},
       {"k_lqr_up", (const void *)k_lqr_up}, {"k_lqr_level", (const void *)k_lqr_level},
-      {"k_riccati_down", (const void *)k_riccati_down}, {"k_aff_up", (const void *)k_aff_up},
+      {"k_riccati_down", (const void *)k_riccati_down}, {"k_riccati_finish", (const void *)k_riccati_finish},
+      {"k_aff_up", (const void *)k_aff_up},
       {"k_aff_level", (const void *)k_aff_level}, {"k_aff_down", (const void *)k_aff_down},
       {"k_solve_init", (const void *)k_solve_init}, {"k_post_roll", (const void *)k_post_roll},
       {"k_resid", (const void *)k_resid}, {"k_pcorr", (const void *)k_pcorr},

@@ -34,6 +34,7 @@ __host__ int smem_riccati(int n, int m) {
   const int rows = 2 * n + m, ld = n + m + 1;
   return n * (n + 1) + rows * ld + rows + ld + 2 * m * (n + 1) + 8;
 }
+__host__ int smem_riccati_finish(int n, int m) { return m * (n + m + 1) + n * (n + 1) + m * (n + 1) + 8; }
 __host__ int smem_aff(int n, int m) { return 2 * (n * n + n) + n * n + 5 * n + 2 * m + 8; }
 
 // Cost-relation slot layout (ld 2n + 1): constraint rows at 0 (CI_ROWS of them),
@@ -212,9 +213,10 @@ __global__ void k_lqr_level(Group g, int src, int d, int per_task) {
 // stacks [L'_v | L'_z | l] and [C Bbar | C Abar | C cbar + c] over (v | z | 1) and
 // triangularises them by Householder QR: R_vv v + R_vz z + o_v = 0 at the
 // minimiser (K, k) and V_i = 1/2 ||R_i z + s_i||^2 with R_i upper triangular,
-// rows signed so that its diagonal is positive.  Stored per stage: P_i = R_i'R_i,
-// p_i = R_i's_i, K, k, the Cholesky factor of H_uu = R_vv'R_vv and
-// Phi = Abar + Bbar K (the closed-loop map of the affine chains).
+// rows signed so that its diagonal is positive.  The sweep carries only V from
+// stage to stage; it stores the minimiser's rows (R_vv | R_vz | o_v) and
+// [R_i | s_i] (in the slots of P_i, p_i), and k_riccati_finish forms the
+// factors from them for every stage at once, off the sequential chain.
 static __device__ void riccati_task(const Group &g, int fin, int t, int per_task);
 __global__ void k_riccati_down(Group g, int fin, int per_task, int *queue) {
   for_tasks(g.nslot, queue, [&](int t) { riccati_task(g, fin, t, per_task); });
@@ -237,7 +239,6 @@ static __device__ void riccati_task(const Group &g, int fin, int t, int per_task
   double *sm = team_smem(per_task);
   const int rows_max = 2 * n + m, ldst = n + m + 1;
   double *V = sm, *St = V + n * (n + 1), *v = St + rows_max * ldst, *w = v + rows_max;
-  double *Kt = w + ldst;  // m x (n + 1)
   // V_b, rows signed to a positive diagonal
   int rv;
   {
@@ -322,48 +323,89 @@ static __device__ void riccati_task(const Group &g, int fin, int t, int per_task
     tsync();
     for (int r = mu + tid; r < kh; r += TEAM) St[r * ld + r] = fabs(St[r * ld + r]);
     tsync();
-    // K, k:  R_vv [K | k] = -[R_vz | o_v]
-    for (int c = tid; c <= nx; c += TEAM) {
-      for (int r = mu - 1; r >= 0; r--) {
-        double s0 = -St[r * ld + mu + c];
-        for (int l = r + 1; l < mu; l++) s0 = fma(-St[r * ld + l], Kt[l * (n + 1) + c], s0);
-        Kt[r * (n + 1) + c] = s0 / St[r * ld + r];
-      }
-    }
-    tsync();
+    // the minimiser's rows (R_vv | R_vz | o_v) for k_riccati_finish, and the new value rows
+    // [R_i | s_i], kept here and stored in the slots of P_i, p_i (ld n + 1)
     if (store) {
-      for (int idx = tid; idx < mu * (nx + 1); idx += TEAM) {
-        int r = idx / (nx + 1), c = idx - r * (nx + 1);
-        if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
-      }
-      for (int idx = tid; idx < mu * mu; idx += TEAM) {
-        int r = idx / mu, j = idx - r * mu;
-        double sg = St[j * ld + j] >= 0.0 ? 1.0 : -1.0;
-        ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * St[j * ld + r] : 0.0;
-      }
-      for (int idx = tid; idx < n1 * nx; idx += TEAM) {
-        int r = idx / nx, c = idx - r * nx;
-        double s0 = Ab[r * n + c];
-        for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
-        ws[g.ws.Phi + r * n + c] = s0;
+      double *Rv = ws + g.ws.Rv;
+      for (int idx = tid; idx < mu * ld; idx += TEAM) {
+        int r = idx / ld, j = idx - r * ld;
+        Rv[r * (n + m + 1) + j] = St[r * ld + j];
       }
     }
-    // new value rows [R_i | s_i]
-    tsync();
     for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
       int r = idx / (nx + 1), c = idx - r * (nx + 1);
       V[r * (n + 1) + c] = (c < nx) ? ((c >= r) ? St[(mu + r) * ld + mu + c] : 0.0) : St[(mu + r) * ld + kh];
     }
     tsync();
     rv = nx;
-    for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
-      int r = idx / (nx + 1), c = idx - r * (nx + 1);
-      double s0 = 0.0;
-      for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
-      if (!store) continue;
-      if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
+    if (store)
+      for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
+        int r = idx / (nx + 1), c = idx - r * (nx + 1);
+        ws[g.ws.P + r * (n + 1) + c] = V[r * (n + 1) + c];
+      }
+  }
+}
+
+// ----------------------------------------------------------- Riccati factors, every stage at once
+// For each stage i < N that the sweep stored (FP64 sweeps only): from the
+// minimiser's rows, R_vv [K | k] = -[R_vz | o_v] by back substitution, the
+// Cholesky factor of H_uu = R_vv'R_vv (R_vv' with rows signed to a positive
+// diagonal), Phi = Abar + Bbar K (the closed-loop map of the affine chains), and
+// from [R_i | s_i], P_i = R_i'R_i and p_i = R_i's_i, which replace it.
+__global__ void k_riccati_finish(Group g, int per_task) {
+  const int s = team_task();
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
+  if (S.i >= P.N) return;
+  if (g.fp64 != nullptr && g.fp64[P.id] == 0) return;  // k_riccati_down_f32 stored this problem's factors
+  const int n = g.n, m = g.m, tid = team_rank();
+  double *ws = stage_ws(g, s);
+  const int *wi = stage_wi(g, s);
+  const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
+  const int ldr = n + m + 1;
+  double *sm = team_smem(per_task);
+  double *R = sm, *V = R + m * ldr, *Kt = V + n * (n + 1);
+  const double *Rv = ws + g.ws.Rv, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
+  for (int idx = tid; idx < mu * (nx + mu + 1); idx += TEAM) {
+    int r = idx / (nx + mu + 1), j = idx - r * (nx + mu + 1);
+    R[r * ldr + j] = Rv[r * ldr + j];
+  }
+  for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
+    int r = idx / (nx + 1), c = idx - r * (nx + 1);
+    V[r * (n + 1) + c] = ws[g.ws.P + r * (n + 1) + c];
+  }
+  tsync();
+  // K, k:  R_vv [K | k] = -[R_vz | o_v]
+  for (int c = tid; c <= nx; c += TEAM) {
+    for (int r = mu - 1; r >= 0; r--) {
+      double s0 = -R[r * ldr + mu + c];
+      for (int l = r + 1; l < mu; l++) s0 = fma(-R[r * ldr + l], Kt[l * (n + 1) + c], s0);
+      Kt[r * (n + 1) + c] = s0 / R[r * ldr + r];
     }
-    tsync();
+  }
+  for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
+    int r = idx / (nx + 1), c = idx - r * (nx + 1);
+    double s0 = 0.0;
+    for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
+    if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
+  }
+  for (int idx = tid; idx < mu * mu; idx += TEAM) {
+    int r = idx / mu, j = idx - r * mu;
+    double sg = R[j * ldr + j] >= 0.0 ? 1.0 : -1.0;
+    ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * R[j * ldr + r] : 0.0;
+  }
+  tsync();
+  for (int idx = tid; idx < mu * (nx + 1); idx += TEAM) {
+    int r = idx / (nx + 1), c = idx - r * (nx + 1);
+    if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
+  }
+  for (int idx = tid; idx < n1 * nx; idx += TEAM) {
+    int r = idx / nx, c = idx - r * nx;
+    double s0 = Ab[r * n + c];
+    for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
+    ws[g.ws.Phi + r * n + c] = s0;
   }
 }
 

@@ -13,6 +13,7 @@ __host__ int smem_elim(int n, int m, int pmax);
 __host__ int smem_lqr_up(int n, int m);
 __host__ int smem_lqr_level(int n);
 __host__ int smem_riccati(int n, int m);
+__host__ int smem_riccati_finish(int n, int m);
 __host__ int smem_aff(int n, int m);
 __host__ int smem_dual_stage(int n, int m);
 __host__ int smem_dual_sweep(int n, int m, int pmax, int qmax);
@@ -34,6 +35,7 @@ enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_PLIN_ = 2, AFF_NU_ = 3 };
 __global__ void k_lqr_up(Group g, int per_task);
 __global__ void k_lqr_level(Group g, int src, int d, int per_task);
 __global__ void k_riccati_down(Group g, int fin, int per_task, int *queue);
+__global__ void k_riccati_finish(Group g, int per_task);
 __global__ void k_riccati_down_f32(Group g, int fin, int per_task);  // k_mixed.cu
 __global__ void k_aff_up(Group g, int mode, int per_task);
 __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task);

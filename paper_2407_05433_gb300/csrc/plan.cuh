@@ -43,6 +43,7 @@ struct WsLayout {
   int nu, NH, Pnu, pnu, UA, BU, UC, Ux, ru;
   int LT, lt;   // Cholesky factor L' of the reduced stage Hessian in the order (v, z), upper
                 // triangular (L L' = [Rbar Mbar'; Mbar Qbar]), and L^{-1} [rbar; qbar]
+  int Rv;       // the Riccati QR's rows of the minimiser, (R_vv | R_vz | o_v), ld n + m + 1
   int stride;
 };
 
@@ -91,6 +92,7 @@ __host__ __device__ inline WsLayout make_ws_layout(int n, int m, int pmax, int q
   L.ru = take(m);
   L.LT = take((n + m) * (n + m));
   L.lt = take(n + m);
+  L.Rv = take(m * (n + m + 1));
   L.stride = (o + 3) & ~3;
   return L;
 }
