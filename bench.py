@@ -54,7 +54,10 @@ PLAIN_SAMPLE = 24
 # kernels whose launches carry one phase of the method alone when every problem is one chunk
 PHASE_KERNELS = {"k_primal_down": 0, "k_param": 1, "k_elim": 2, "k_riccati_down": 3, "k_dual_down": 5}
 # kernels that carry the rest of the same phase (their time counts with the phase's kernel)
-PHASE_PARTNERS = {"k_riccati_down": ("k_riccati_finish",)}
+# (phase 5's forward substitution of nu also runs in k_aff_down, whose launches serve the rollout too and
+# are left out, so the multipliers' rate is an upper bound)
+PHASE_PARTNERS = {"k_riccati_down": ("k_riccati_finish",),
+                  "k_dual_down": ("k_dual_stage", "k_dual_leaf", "k_dual_root", "k_dual_terminal", "k_dual_up")}
 
 
 def dist_env():
@@ -298,6 +301,7 @@ def measure_kernels(pbs, dev, flush, stream, flops):
                                    "k_lqr_up", "k_lqr_level", "k_primal_up", "k_dual_up", "k_aff_up",
                                    "k_aff_level", "k_aff_down", "k_kkt", "k_resid", "k_pcorr", "k_dual_leaf",
                                    "k_dual_stage", "k_dual_root", "k_refine_trial"]
+    names = list(dict.fromkeys(names))  # each kernel timed once
     ms = {k: 0.0 for k in names}
     launches = {k: 0 for k in names}
     for key, gp in sorted(groups.items()):

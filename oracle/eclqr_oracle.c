@@ -1261,7 +1261,11 @@ static int solve_once(const orc_problem *P, const orc_options *opt, double *x,
       }
       int gs[2] = {nw, r1};
       double *outp = dalloc((size_t)(rows ? rows : 1) * (r0 + 1));
+      /* with r0 = r1 = 0 nothing is kept (N_i has no coordinates) and the projection only
+         finds rows 0 = const, which step 9 drops: a solver skips it, so it is not counted */
+      g_uncounted = r0 == 0 && r1 == 0;
       project(Wd, rows, nc, 2, gs, r0, tr, ti, grank, &krank, &inc, outp);
+      g_uncounted = 0;
       lr[i] = krank;
       for (int a = 0; a < krank; a++)
         for (int b = 0; b <= r0; b++) Ls[(size_t)i * n * lld + a * lld + b] = outp[a * (r0 + 1) + b];

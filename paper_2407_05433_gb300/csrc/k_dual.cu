@@ -316,6 +316,14 @@ __global__ void k_dual_down(Group g, int fin, int per_task) {
       const StageInfo S = g.st[s];
       double *ws = stage_ws(g, s);
       const int r0 = stage_wi(g, s)[SI_UR], r1 = stage_wi(g, s + 1)[SI_UR], w = S.p + S.q;
+      if (r0 == 0 && r1 == 0) {
+        // nu_i and nu_{i+1} have no coordinates (X_i = X_{i+1} = R^n): no forward map, and
+        // eliminating (mu, eta) leaves only rows 0 = const, which the relation drops as
+        // redundant or (from rounding) inconsistent, so N_i has no rows
+        rr = 0;
+        if (tid == 0) stage_wi(g, s)[SI_NUROWS] = 0;
+        continue;
+      }
       const int ldm = w + r1 + r0 + 1;
       int rows2 = dual_stage_rows(g, s, M, ldm, 0);
       for (int idx = tid; idx < rr * ldm; idx += TEAM) {

@@ -315,13 +315,17 @@ static __device__ void riccati_task(const Group &g, int fin, int t, int per_task
       HHLayout L = hh_layout(kh + 1 - k, rv + 1);
       hh_core(W, ld, 0, rv + 1, k, nullptr, k, kh + 1 - k, L, v, w, 0.0);
     }
-    // sign the z rows to a positive diagonal (rows mu .. kh - 1)
+    // sign the z rows to a positive diagonal (rows mu .. kh - 1), on the integer pipe: a row
+    // whose diagonal is below zero (sign bit set, not -0, not NaN) has every sign bit flipped
     for (int idx = tid; idx < nx * ld; idx += TEAM) {
-      int r = mu + idx / ld, j = idx % ld;
-      if (St[r * ld + r] < 0.0 && j != r) St[r * ld + j] = -St[r * ld + j];
+      int r = mu + idx / ld, j = idx - (idx / ld) * ld;
+      const long long db = __double_as_longlong(St[r * ld + r]);
+      const bool neg = db < 0 && (db & 0x7fffffffffffffffll) != 0 && (db & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll;
+      if (neg && j != r) St[r * ld + j] = __longlong_as_double(__double_as_longlong(St[r * ld + j]) ^ (1ll << 63));
     }
     tsync();
-    for (int r = mu + tid; r < kh; r += TEAM) St[r * ld + r] = fabs(St[r * ld + r]);
+    for (int r = mu + tid; r < kh; r += TEAM)
+      St[r * ld + r] = __longlong_as_double(__double_as_longlong(St[r * ld + r]) & 0x7fffffffffffffffll);
     tsync();
     // the minimiser's rows (R_vv | R_vz | o_v) for k_riccati_finish, and the new value rows
     // [R_i | s_i], kept here and stored in the slots of P_i, p_i (ld n + 1)

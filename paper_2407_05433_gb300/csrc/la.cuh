@@ -357,6 +357,15 @@ __device__ __forceinline__ void argmax_finish(int parity, double &bv, int &bi) {
 
 __device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// Whether a Householder step runs: d = ||x||^2 > 0 (a NaN d gives false) and
+// nrm = sqrt(d) > thr, compared as bit patterns on the integer pipe: non-negative
+// doubles order like their patterns, and a negative thr (sign bit set) is below
+// every nrm of a positive d.
+__device__ __forceinline__ bool hh_step_runs(double d, double nrm, double thr) {
+  const long long db = __double_as_longlong(d), nb = __double_as_longlong(nrm), tb = __double_as_longlong(thr);
+  return db > 0 && db <= 0x7ff0000000000000ll && (tb < 0 || nb > tb);
+}
+
 // One Householder step on rows [k, r) with pivot column piv among the cnt
 // columns of the pass (column of position p: list ? list[p] : a0 + p; the
 // pivot is one of them), laid out by L = hh_layout(cnt, r - k).  Dot pass:
@@ -422,7 +431,7 @@ static __device__ double hh_core(double *M, int ld, int k, int r, int piv, const
     vk = xk + shift;
     beta = 1.0 / (nrm * (nrm + fabs(xk)));
   }
-  if (!(dp > 0.0) || !(nrm > thr)) return 0.0;
+  if (!hh_step_runs(dp, nrm, thr)) return 0.0;
   L = Ln;
   if (refl && tid == 0) { refl[0] = vk; refl[1] = beta; }  // visible after the closing barrier
   // update pass (and, when pivoting, the norm downdate and the warp's arg-max)
@@ -646,7 +655,7 @@ static __device__ double hh_range_step(double *M, int ld, int k, int r, int piv,
     vk = xk + shift;
     beta = 1.0 / (nrm * (nrm + fabs(xk)));
   }
-  if (!(dp > 0.0) || !(nrm > thr)) return 0.0;
+  if (!hh_step_runs(dp, nrm, thr)) return 0.0;
   for (int jj = jj0; jj < nc && (S == 1 || jj == jj0); jj += T) {
     const int j = a0 + jj;
     if (j == piv) {
@@ -1211,32 +1220,42 @@ static __device__ double wtqr_solve(const double *W, int ldw, const double *Q, i
 // so each FP64 instruction carries every row still below the diagonal; the
 // pivot's reciprocal square root comes from seeded_rsqrt.  The upper triangle
 // is left as it was.  Returns nonzero when a pivot is not positive.
+// Rows 32 .. kh (kh + 1 > 32) go to the lanes whose own row is already done:
+// at column j lane l < j has finished row l, so it takes row l + 32, and one
+// chain of length j per lane covers every open row; only for j < kh + 1 - 32
+// does a lane hold two open rows and run a second chain.
 static __device__ int wchol_bordered(double *Hm, int ld, int kh) {
   const int lane = threadIdx.x & 31;
-  const int i0 = lane, i1 = lane + 32;
+  const int extra = kh + 1 - 32;  // rows beyond the warp's first 32 (<= 0: none)
   int fail = 0;
   for (int j = 0; j < kh; j++) {
-    const bool on0 = i0 >= j && i0 <= kh, on1 = i1 >= j && i1 <= kh;
+    // this lane's open rows: ia (its chain), ib (a second chain, only while j < extra)
+    int ia = (lane >= j && lane <= kh) ? lane : -1, ib = -1;
+    if (lane + 32 <= kh && lane + 32 >= j) {
+      if (ia < 0) ia = lane + 32;
+      else ib = lane + 32;
+    }
     const double *rj = Hm + j * ld;
     double s0 = 0.0, s1 = 0.0;
-    if (on0) {
-      const double *ri = Hm + i0 * ld;
+    if (ia >= 0) {
+      const double *ri = Hm + ia * ld;
       s0 = ri[j];
       for (int l = 0; l < j; l++) s0 = fma(-ri[l], rj[l], s0);
     }
-    if (on1) {
-      const double *ri = Hm + i1 * ld;
+    if (j < extra && ib >= 0) {
+      const double *ri = Hm + ib * ld;
       s1 = ri[j];
       for (int l = 0; l < j; l++) s1 = fma(-ri[l], rj[l], s1);
     }
-    const double sd = __shfl_sync(kFull, j < 32 ? s0 : s1, j & 31);
+    // row j is lane j's first row (j < 32) or lane j - 32's (then its only open row)
+    const double sd = __shfl_sync(kFull, s0, j & 31);
     bool ok;
     double inv = seeded_rsqrt(sd, ok);
     if (!(sd > 0.0)) fail = 1;
     if (!ok) inv = 1.0 / sqrt(fmax(sd, 1e-300));
     const double dj = sd * inv;
-    if (on0) Hm[i0 * ld + j] = (i0 == j) ? dj : s0 * inv;
-    if (on1) Hm[i1 * ld + j] = (i1 == j) ? dj : s1 * inv;
+    if (ia >= 0) Hm[ia * ld + j] = (ia == j) ? dj : s0 * inv;
+    if (ib >= 0) Hm[ib * ld + j] = s1 * inv;
     __syncwarp();
   }
   return fail;
