@@ -33,10 +33,20 @@ __host__ int smem_scan_check(int n, int m, int pmax) {
   return pmax * ld + 2 * ld + pmax + ld / 2 + 8;
 }
 __host__ int smem_param(int n) { return n * (n + 1) + n * n + n * n + n + n + 4 * n + 8 + n; }
+// k_elim's shared memory: the blocks live through the whole stage (A T, Q_m, Y, the
+// vectors, the QR scratch and permutation) and one region that three phases use in
+// turn: Lemma 4's solve (H_{i+1}, Gamma, [Phi | gamma], the factor and the solution),
+// the substitution products, and the bordered stage Hessian.
+__host__ __device__ inline int elim_union(int n, int m, int pmax) {
+  const int rows = pmax + n;
+  const int ab = n * (n + 1) + rows * m + rows * (n + 1) + m * rows + 2 * m * (n + 1);
+  const int c = 2 * n * n + 3 * n * m + m * m;
+  const int d = (n + m + 1) * (n + m + 1);
+  return ab > c ? (ab > d ? ab : d) : (c > d ? c : d);
+}
 __host__ int smem_elim(int n, int m, int pmax) {
-  int rows = pmax + n;
-  return 3 * n * n + m * (n + 1) + n * (n + 1) + rows * m + rows * (n + 1) + m * rows + m * m +
-         m * (n + 1) + 4 * n * m + m * m + 12 * n + 8 * m + 2 * rows + 16 + (n + m + 1) * (n + m + 1) + 8;
+  const int rows = pmax + n;
+  return n * n + m * m + n * m + 12 * n + 8 * m + 2 * rows + 16 + elim_union(n, m, pmax) + 8;
 }
 
 // ----------------------------------------------------------- shortcut test (Sec. 6)
@@ -420,24 +430,28 @@ __global__ void k_elim(Group g, int per_task) {
   const double *Hn = wn + g.ws.H;                                 // ld n + 1
   double *sm = team_smem(per_task);
   const int rmax = g.pmax + n;
+  // live through the stage
   double *AT = sm;                       // n x n (ld n)
-  double *QT = AT + n * n;               // n x n
-  double *X2 = QT + n * n;               // n x n  scratch
-  double *X1 = X2 + n * n;               // m x (n+1) scratch for the min-norm solve
-  double *Hs = X1 + m * (n + 1);         // n x (n+1)
-  double *Gm = Hs + n * (n + 1);         // rmax x m
-  double *Rh = Gm + rmax * m;            // rmax x (n+1)
-  double *Wt = Rh + rmax * (n + 1);      // m x rmax
-  double *Qm = Wt + m * rmax;            // m x m
-  double *Sol = Qm + m * m;              // m x (n+1)
-  double *Mz = Sol + m * (n + 1);        // n x m
-  double *RY = Mz + n * m;               // m x n
-  double *BZ = RY + n * m;               // n x m
-  double *RZ = BZ + n * m;               // m x m
-  double *Yw = RZ + m * m;               // m x n  (ld n): Y ; reused
+  double *Qm = AT + n * n;               // m x m: Q of Gamma' (Z = its last columns)
+  double *Yw = Qm + m * m;               // m x n  (ld n): Y
   double *vec = Yw + n * m;              // 12 n + 8 m
   double *Atc = vec, *cv = Atc + n, *Qtq = cv + n, *qz = Qtq + n, *rz = qz + n, *Ry = rz + m;
   double *ys = Ry + m, *scr = ys + m;    // scratch >= 2n + 2 rows
+  double *U = vec + 12 * n + 8 * m + 2 * rmax + 16;  // the phases' region
+  // Lemma 4's solve
+  double *Hs = U;                        // n x (n+1)
+  double *Gm = Hs + n * (n + 1);         // rmax x m
+  double *Rh = Gm + rmax * m;            // rmax x (n+1)
+  double *Wt = Rh + rmax * (n + 1);      // m x rmax
+  double *Sol = Wt + m * rmax;           // m x (n+1)
+  double *X1 = Sol + m * (n + 1);        // m x (n+1) scratch for the min-norm solve
+  // the substitution products
+  double *QT = U;                        // n x n
+  double *X2 = QT + n * n;               // n x n  scratch
+  double *Mz = X2 + n * n;               // n x m
+  double *RY = Mz + n * m;               // m x n
+  double *BZ = RY + n * m;               // n x m
+  double *RZ = BZ + n * m;               // m x m
   int *perm = (int *)(scr + 4 * n + 2 * m + 2 * rmax);
   // A T, A t + c
   if (te) {
@@ -598,8 +612,7 @@ __global__ void k_elim(Group g, int per_task) {
     // stage Hessian in the order (v, z) -- the column order of the Riccati's QR, so that L'
     // is upper triangular there -- bordered by g = [rbar; qbar]
     const int kh = nb + mb, ldh = n + m, ldH = kh + 1;
-    double *Hh = (double *)(perm + rmax + 2);  // past the permutation scratch
-    Hh = (double *)(((uintptr_t)Hh + 7) & ~(uintptr_t)7);
+    double *Hh = U;  // the phases' region: everything else there is dead
     for (int idx = tid; idx < (kh + 1) * kh; idx += TEAM) {
       int a = idx / kh, j = idx - a * kh;
       double h;
