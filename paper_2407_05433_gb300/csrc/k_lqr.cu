@@ -271,18 +271,21 @@ static __device__ void riccati_task(const Group &g, int fin, int t, int per_task
     const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
     const int kh = nx + mu, ld = kh + 1;
     const double *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb, *cb = ws + g.ws.cb, *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
-    // value rows [V Bbar | V Abar | V cbar + s] at St rows kh .. kh + rv - 1
+    // value rows [V Bbar | V Abar | V cbar + s] at St rows kh .. kh + rv - 1; after the first
+    // stage V = [R_{i+1} | s_{i+1}] with R_{i+1} upper triangular (exact zeros below its
+    // diagonal), so row r's products start at column r
     for (int idx = tid; idx < rv * ld; idx += TEAM) {
       int r = idx / ld, j = idx - r * ld;
       const double *row = V + r * (n + 1);
+      const int l0 = (i < start - 1) ? r : 0;
       double val = 0.0;
       if (j < mu) {
-        for (int l = 0; l < n1; l++) val = fma(row[l], Bb[l * m + j], val);
+        for (int l = l0; l < n1; l++) val = fma(row[l], Bb[l * m + j], val);
       } else if (j < kh) {
-        for (int l = 0; l < n1; l++) val = fma(row[l], Ab[l * n + (j - mu)], val);
+        for (int l = l0; l < n1; l++) val = fma(row[l], Ab[l * n + (j - mu)], val);
       } else {
         val = row[n1];
-        for (int l = 0; l < n1; l++) val = fma(row[l], cb[l], val);
+        for (int l = l0; l < n1; l++) val = fma(row[l], cb[l], val);
       }
       St[(kh + r) * ld + j] = val;
     }
