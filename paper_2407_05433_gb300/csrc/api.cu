@@ -104,6 +104,7 @@ int team_for(const eclqr_handle *h, const void *kern, int ntasks, int n) {
       {(const void *)k_riccati_finish, 1, 0, 1}, {(const void *)k_elim, 1, 16, 4},
       {(const void *)k_primal_down, 1, 24, 2},   {(const void *)k_dual_down, 1, 0, 1},
       {(const void *)k_aff_down, 8, 0, 8},       {(const void *)k_dual_leaf, 1, 0, 1},
+      {(const void *)k_aff_prep, 1, 0, 1},
       {(const void *)k_dual_stage, 2, 0, 2},     {(const void *)k_param, 1, 0, 1},
       {(const void *)k_resid, 1, 0, 1},          {(const void *)k_pcorr, 1, 0, 1},
       {(const void *)k_kkt, 1, 0, 1},            {(const void *)k_post_roll, 1, 0, 1},
@@ -613,6 +614,7 @@ int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, 
 int aff_scan(eclqr_handle *h, const GroupHost &gh, const Group &g, int mode, cudaStream_t st) {
   const int sa = smem_aff(g.n, g.m);
   const int fwd = (mode == AFF_PLIN_) ? 0 : 1;
+  TRY(launch(h, k_aff_prep, g.nstage, g.n + 8, st, g, mode, g.n + 8));
   TRY(launch(h, k_aff_up, g.nslot, sa, st, g, mode, sa));
   int src = 0;
   // radix-4 levels: strides 1, 4, 16, ... until they cover every slot
@@ -991,6 +993,7 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
       {"k_riccati_down", (const void *)k_riccati_down}, {"k_riccati_finish", (const void *)k_riccati_finish},
       {"k_aff_up", (const void *)k_aff_up},
       {"k_aff_level", (const void *)k_aff_level}, {"k_aff_down", (const void *)k_aff_down},
+      {"k_aff_prep", (const void *)k_aff_prep},
       {"k_solve_init", (const void *)k_solve_init}, {"k_post_roll", (const void *)k_post_roll},
       {"k_resid", (const void *)k_resid}, {"k_pcorr", (const void *)k_pcorr},
       {"k_recover", (const void *)k_recover}, {"k_dual_stage", (const void *)k_dual_stage},

@@ -487,6 +487,49 @@ __device__ void aff_stage_map(const Group &g, int s, int mode, double *G, double
   tsync();
 }
 
+// The offsets of every stage's map, stage-parallel, before a chain sweeps
+// them (ws.gv; the same arithmetic as aff_stage_map): ROLL cbar + Bbar k,
+// CROLL rc + Bbar k', PLIN rq + K' rr + Phi' P_{i+1} rc.  NU reads pnu.
+__global__ void k_aff_prep(Group g, int mode, int per_task) {
+  const int s = team_task();
+  if (s >= g.nstage) return;
+  const StageInfo S = g.st[s];
+  const ProbInfo &P = g.prob[S.prob];
+  if (skipped_by_mask(g, S.prob)) return;
+  if (S.i >= P.N || mode == AFF_NU) return;
+  const int n = g.n, m = g.m, tid = team_rank();
+  double *ws = stage_ws(g, s);
+  const double *wn = stage_ws(g, s + 1);
+  const int *wi = stage_wi(g, s);
+  const int nx = wi[SI_NBAR], ny = stage_wi(g, s + 1)[SI_NBAR], mu = wi[SI_MBAR];
+  const double *Phi = ws + g.ws.Phi, *Bb = ws + g.ws.Bb;
+  double *gv = ws + g.ws.gv;
+  if (mode == AFF_ROLL || mode == AFF_CROLL) {
+    const double *kk = ws + (mode == AFF_ROLL ? g.ws.k : g.ws.dv);
+    const double *cc = ws + (mode == AFF_ROLL ? g.ws.cb : g.ws.rc);
+    for (int i = tid; i < ny; i += TEAM) {
+      double s0 = cc[i];
+      for (int l = 0; l < mu; l++) s0 = fma(Bb[i * m + l], kk[l], s0);
+      gv[i] = s0;
+    }
+    return;
+  }
+  double *tmp = team_smem(per_task);  // P_{i+1} rc (ny)
+  const double *K = ws + g.ws.K, *Pn = wn + g.ws.P, *rc = ws + g.ws.rc;
+  for (int b = tid; b < ny; b += TEAM) {
+    double s0 = 0.0;
+    for (int l = 0; l < ny; l++) s0 = fma(Pn[b * n + l], rc[l], s0);
+    tmp[b] = s0;
+  }
+  tsync();
+  for (int i = tid; i < nx; i += TEAM) {
+    double s0 = ws[g.ws.rq + i];
+    for (int l = 0; l < mu; l++) s0 = fma(K[l * n + i], ws[g.ws.rr + l], s0);
+    for (int b = 0; b < ny; b++) s0 = fma(Phi[b * n + i], tmp[b], s0);
+    gv[i] = s0;
+  }
+}
+
 // chunk aggregates; also the boundary value slot (forward: slot 0 of the
 // problem holds y_0, backward: slot nch holds y_N).
 __global__ void k_aff_up(Group g, int mode, int per_task) {
@@ -639,6 +682,13 @@ __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task) {
   if (tid == 0) { J[CI_ROWS] = rows; J[CI_NA] = na; J[CI_NB] = nb; }
 }
 
+// The chain of one chunk: y_out = G_i y_in + gv_i stage after stage, G_i = Phi_i
+// (ROLL, CROLL), Phi_i' (PLIN, backward) or Pnu_i (NU), gv_i from k_aff_prep (pnu
+// for NU).  Each output row is a dot product split over seg lanes (seg a power of
+// two with seg * n <= the team), so its dependent chain is about n / seg FMAs and
+// log2(seg) shuffle additions; the lanes load the next stage's G and gv into
+// registers while the current stage runs, and y alternates between two buffers,
+// one barrier per stage.
 __global__ void k_aff_down(Group g, int mode, int fin, int per_task) {
   const int t = team_task();
   if (t >= g.nslot) return;
@@ -647,59 +697,85 @@ __global__ void k_aff_down(Group g, int mode, int fin, int per_task) {
   if (skipped_by_mask(g, ci.prob)) return;
   if (ci.c >= P.nch) return;
   const int n = g.n, tid = team_rank();
-  const bool fwd = aff_forward(mode);
+  const bool fwd = aff_forward(mode), tr = mode == AFF_PLIN;
   const int a = ci.c * P.L, b = min(a + P.L, P.N);
   const int off = aff_out(g, mode);
+  const int goff = mode == AFF_NU ? g.ws.Pnu : g.ws.Phi, voff = mode == AFF_NU ? g.ws.pnu : g.ws.gv;
   double *sm = team_smem(per_task);
-  double *Gs = sm, *gs = Gs + n * n, *y = gs + n, *y2 = y + n, *tmp = y2 + n;
+  double *ya = sm, *yb = ya + n;
+  int seg = 8;
+  while (seg > 1 && seg * n > TEAM) seg >>= 1;
+  const int q = tid & (seg - 1), row = tid / seg;  // this lane's row and column offset
   // boundary value after the scan: forward slot (ch0 + c) = y_a; backward slot (ch0 + c + 1) = y_b
   const int slot = fwd ? P.ch0 + ci.c : P.ch0 + ci.c + 1;
   const double *sv = g.CS[fin] + (size_t)slot * g.cs_stride + n * n;
   int dcur = fwd ? aff_dim(g, P.st0 + a, mode) : aff_dim(g, P.st0 + b, mode);
-  for (int i = tid; i < n; i += TEAM) y[i] = (i < dcur) ? sv[i] : 0.0;
+  for (int i = tid; i < n; i += TEAM) ya[i] = (i < dcur) ? sv[i] : 0.0;
+  // stage k of the sweep (k = 0 .. b - a - 1): its stage, and its output dimension
+  auto stage_of = [&](int k) { return P.st0 + (fwd ? a + k : b - 1 - k); };
+  auto dout_of = [&](int s) { return fwd ? aff_dim(g, s + 1, mode) : aff_dim(g, s, mode); };
+  // registers: this lane's entries of G (columns q, q + seg, q + 2 seg, q + 3 seg) and gv
+  constexpr int KP = 4;
+  double gr[KP], gvr = 0.0;
+  auto load = [&](int s, int din, int dout, double *gx, double &gvx) {
+    const double *G = stage_ws(g, s) + goff;
+#pragma unroll
+    for (int k = 0; k < KP; k++) {
+      const int l = q + k * seg;
+      gx[k] = (row < dout && l < din) ? (tr ? G[l * n + row] : G[row * n + l]) : 0.0;
+    }
+    gvx = (row < dout && q == 0) ? stage_ws(g, s)[voff + row] : 0.0;
+  };
+  const int steps = b - a;
+  if (!fwd && b == P.N) {
+    double *o = stage_ws(g, P.st0 + b) + off;
+    for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? ya[r] : 0.0;
+  }
+  int s = steps > 0 ? stage_of(0) : 0;
+  int dout = steps > 0 ? dout_of(s) : 0;
+  if (steps > 0) load(s, dcur, dout, gr, gvr);
   tsync();
-  if (fwd) {
-    for (int i = a; i < b; i++) {
-      const int s = P.st0 + i;
+  for (int k = 0; k < steps; k++) {
+    if (fwd) {  // the value of stage s is the chain's input
       double *o = stage_ws(g, s) + off;
-      for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? y[r] : 0.0;
-      aff_stage_map(g, s, mode, Gs, gs, tmp);
-      const int dout = aff_dim(g, s + 1, mode);
-      for (int r = tid; r < dout; r += TEAM) {
-        double s0 = gs[r];
-        for (int l = 0; l < dcur; l++) s0 = fma(Gs[r * n + l], y[l], s0);
-        y2[r] = s0;
-      }
-      tsync();
-      for (int r = tid; r < n; r += TEAM) y[r] = (r < dout) ? y2[r] : 0.0;
-      tsync();
-      dcur = dout;
+      for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? ya[r] : 0.0;
     }
-    if (b == P.N) {
-      double *o = stage_ws(g, P.st0 + b) + off;
-      for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? y[r] : 0.0;
+    // next stage's entries, in flight while this stage runs
+    double gn[KP], gvn = 0.0;
+    int sn = s, dn = 0;
+    if (k + 1 < steps) {
+      sn = stage_of(k + 1);
+      dn = dout_of(sn);
+      load(sn, dout, dn, gn, gvn);
     }
-  } else {
-    if (b == P.N) {
-      double *o = stage_ws(g, P.st0 + b) + off;
-      for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? y[r] : 0.0;
+    double acc = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < KP; kk++) {
+      const int l = q + kk * seg;
+      if (l < dcur) acc = fma(gr[kk], ya[l], acc);
     }
-    for (int i = b - 1; i >= a; i--) {
-      const int s = P.st0 + i;
-      aff_stage_map(g, s, mode, Gs, gs, tmp);
-      const int dout = aff_dim(g, s, mode);
-      for (int r = tid; r < dout; r += TEAM) {
-        double s0 = gs[r];
-        for (int l = 0; l < dcur; l++) s0 = fma(Gs[r * n + l], y[l], s0);
-        y2[r] = s0;
-      }
-      tsync();
-      for (int r = tid; r < n; r += TEAM) y[r] = (r < dout) ? y2[r] : 0.0;
-      tsync();
-      dcur = dout;
+    if (row < dout) {  // columns beyond the registers (teams too small for seg = 8)
+      const double *G = stage_ws(g, s) + goff;
+      for (int l = q + KP * seg; l < dcur; l += seg) acc = fma(tr ? G[l * n + row] : G[row * n + l], ya[l], acc);
+    }
+    for (int o = seg >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (q == 0 && row < dout) yb[row] = gvr + acc;
+    tsync();
+    double *tmp = ya; ya = yb; yb = tmp;
+    if (!fwd) {  // the chain's output is the value of stage s
       double *o = stage_ws(g, s) + off;
-      for (int r = tid; r < n; r += TEAM) o[r] = y[r];
+      for (int r = tid; r < n; r += TEAM) o[r] = (r < dout) ? ya[r] : 0.0;
     }
+    dcur = dout;
+    s = sn;
+    dout = dn;
+#pragma unroll
+    for (int kk = 0; kk < KP; kk++) gr[kk] = gn[kk];
+    gvr = gvn;
+  }
+  if (fwd && b == P.N) {
+    double *o = stage_ws(g, P.st0 + b) + off;
+    for (int r = tid; r < n; r += TEAM) o[r] = (r < dcur) ? ya[r] : 0.0;
   }
 }
 

@@ -40,6 +40,7 @@ __global__ void k_riccati_down_f32(Group g, int fin, int per_task);  // k_mixed.
 __global__ void k_aff_up(Group g, int mode, int per_task);
 __global__ void k_aff_level(Group g, int src, int d, int fwd, int per_task);
 __global__ void k_aff_down(Group g, int mode, int fin, int per_task);
+__global__ void k_aff_prep(Group g, int mode, int per_task);
 __global__ void k_solve_init(Group g, const double *s0);
 __global__ void k_post_roll(Group g, int corr);
 __global__ void k_resid(Group g, int per_task);

@@ -44,6 +44,7 @@ struct WsLayout {
   int LT, lt;   // Cholesky factor L' of the reduced stage Hessian in the order (v, z), upper
                 // triangular (L L' = [Rbar Mbar'; Mbar Qbar]), and L^{-1} [rbar; qbar]
   int Rv;       // the Riccati QR's rows of the minimiser, (R_vv | R_vz | o_v), ld n + m + 1
+  int gv;       // offset of the affine chain's stage map (k_aff_prep), n
   int stride;
 };
 
@@ -93,6 +94,7 @@ __host__ __device__ inline WsLayout make_ws_layout(int n, int m, int pmax, int q
   L.LT = take((n + m) * (n + m));
   L.lt = take(n + m);
   L.Rv = take(m * (n + m + 1));
+  L.gv = take(n);
   L.stride = (o + 3) & ~3;
   return L;
 }
