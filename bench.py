@@ -154,11 +154,15 @@ def job_rate(world, stages_per_rank, ms):
 
 
 # ---------------------------------------------------------------- workload, gates, algorithmic work
-def batched_problems(count=PROBLEMS, state_dim=None):
-    """Draws 0..count-1 of the batch; with state_dim, only those whose state dimension is state_dim.
-    Returns (draw indices, problems)."""
+def batched_problems(count=PROBLEMS, state_dim=None, max_horizon=None):
+    """Draws 0..count-1 of the batch; with state_dim, only those whose state dimension is state_dim;
+    with max_horizon, a draw whose horizon exceeds it is drawn again from the same seed at that
+    horizon (a smaller case of the same shape, for profiling).  Returns (draw indices, problems)."""
     from paper_2407_05433_gb300 import synth
     pbs = [synth.config(WORKLOAD, index=j) for j in range(count)]
+    if max_horizon is not None:
+        pbs = [pb if pb.N <= max_horizon else synth.config(WORKLOAD, index=j, N=max_horizon)
+               for j, pb in enumerate(pbs)]
     keep = [j for j, pb in enumerate(pbs) if state_dim is None or pb.n == state_dim]
     return keep, [pbs[j] for j in keep]
 
@@ -556,7 +560,7 @@ def run_gpu(args):
     import numpy as np
     rank, world, local = dist_env()
     t_gen = time.perf_counter()
-    draws, pbs = batched_problems(args.problems, args.state_dim)  # host-side generation before any CUDA call
+    draws, pbs = batched_problems(args.problems, args.state_dim, args.max_horizon)  # host-side, before any CUDA call
     t_gen = time.perf_counter() - t_gen
     fg = floor_gates()
     gates = {pos: fg[j] for pos, j in enumerate(draws) if j in fg}
@@ -649,7 +653,8 @@ def run_gpu(args):
         return 0
 
     flops_all = workload_flops()
-    fl = flops_all.get(WORKLOAD) if args.problems == PROBLEMS and args.state_dim is None else None
+    fl = flops_all.get(WORKLOAD) if (args.problems == PROBLEMS and args.state_dim is None
+                                     and args.max_horizon is None) else None
     peak = eclqr.eclqr_probe_fp64_peak()
     extras = {}
     kern = None
@@ -729,6 +734,7 @@ def run_gpu(args):
                    "l2": f"inputs of {h2d / 1e9:.1f} GB per GPU (larger than L2); a 256 MB buffer is also written "
                          "between steps",
                    "team_warps": args.team_warps or "per kernel", "state_dim": args.state_dim,
+                   "max_horizon": args.max_horizon,
                    "step": "graph replay of eclqr_build + eclqr_solve + eclqr_multipliers + eclqr_refine",
                    "refine": 2, "kkt_refine": kkt_refine, "kkt_refine_autotune": kr_trials,
                    "refine_tol": 5e-10, "generation_s": round(t_gen, 1)},
@@ -758,6 +764,8 @@ def main():
     ap.add_argument("--problems", type=int, default=PROBLEMS, help="draws 0..problems-1 of the batch")
     ap.add_argument("--state-dim", type=int, default=None,
                     help="keep only the draws with this state dimension (one (n, m) group, for profiling)")
+    ap.add_argument("--max-horizon", type=int, default=None,
+                    help="cap the horizons (a smaller case of the same shape, for profiling)")
     ap.add_argument("--team-warps", type=int, default=0,
                     help="warps per task for every kernel (0: the library's per-kernel choice)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
