@@ -110,14 +110,15 @@ typedef struct {
   double tau_inc;    /* inconsistency cut on a scaled offset (Sec. 8 item 4); default 1e-8    */
   int32_t refine;    /* refinement passes on the reduced LQR KKT residual; default 2          */
   int32_t chunk;     /* stages per scan chunk; 0 = chosen from N and the SM count: one chunk
-                      * per problem when the batch holds at least two problems per SM, else
-                      * 7 to 64 stages.  A problem that fits one chunk is swept once per
+                      * per problem when the longest horizon is at most the batch's stages
+                      * per SM, else 7 to 64 stages.  A problem that fits one chunk is swept once per
                       * scan, from its terminal element, with no chunk aggregate           */
   int32_t team_warps; /* warps of the CTA that runs one task: 1, 2, 4 or 8 for every kernel;
-                       * 0 (default) = per kernel: 4 when a launch has fewer than 4 tasks
-                       * per SM, else the kernel's measured best (1 for the per-problem
-                       * sweeps and the small per-stage kernels, 4 for the stage
-                       * elimination, 8 for the affine-chain sweep)                      */
+                       * 0 (default) = per kernel: 4 when a launch has fewer tasks than
+                       * SMs; with at least 4 tasks per SM the kernel's measured best for
+                       * the group's n (1 for the per-problem sweeps and the small
+                       * per-stage kernels, 1 or 4 for the stage elimination, 8 for the
+                       * affine-chain sweep); in between that but at least 2            */
   int32_t scan_skip;  /* 1 (default): take the shortcut of Sec. 6 (complete algorithm and
                        * complexity) where it applies: a problem without state-only or
                        * terminal rows whose every stage's mixed rows leave no row on x_i
@@ -141,6 +142,9 @@ typedef struct {
                        * 8 CTAs per SM for launches with at least 4 tasks per SM; k in
                        * 1..32: k CTAs per SM for every launch with more than k tasks per
                        * SM; -1: one CTA per task.  Results are the same either way.      */
+  int32_t corr_refine; /* refinement passes on the reduced residual inside the corrections
+                       * of eclqr_refine, 0..8; -1 (default) = refine.  A correction only
+                       * has to shrink the residual that the next pass measures again     */
 } eclqr_options;
 
 /* element counts of every packed array (for allocation) */

@@ -81,9 +81,9 @@ namespace {
 
 // Team size of one launch of a kernel on a group with state dimension n.
 // opt.team_warps != 0 fixes it for every kernel.  Otherwise a launch with fewer
-// than kManyTasksPerSm tasks per SM takes four warps, one per SM sub-partition,
-// so that one task spreads over the SM.  A launch with more takes the kernel's
-// entry below.  There the SM is filled by many tasks at once, and an FP64 warp
+// tasks than SMs takes four warps, one per SM sub-partition, so that one task
+// spreads over the SM; one with at least kManyTasksPerSm tasks per SM takes the
+// kernel's entry below, and one in between the entry but at least two warps.  There the SM is filled by many tasks at once, and an FP64 warp
 // instruction costs its sub-partition the same time whatever its active lanes,
 // so the sequential per-problem sweeps and the small per-stage kernels run
 // fastest as one warp per task: one warp forms each reflector's scalars, each
@@ -97,7 +97,7 @@ namespace {
 // matrices fill four warps.
 int team_for(const eclqr_handle *h, const void *kern, int ntasks, int n) {
   if (h->opt.team_warps != 0) return h->opt.team_warps;
-  if (ntasks < kManyTasksPerSm * h->sms) return kTeamWarps;
+  if (ntasks < h->sms) return kTeamWarps;
   // warps below n_from, and from n_from up
   static const struct { const void *fn; int warps, n_from, warps_from; } table[] = {
       {(const void *)k_riccati_down, 1, 0, 1},   {(const void *)k_riccati_down_f32, 1, 0, 1},
@@ -115,8 +115,14 @@ int team_for(const eclqr_handle *h, const void *kern, int ntasks, int n) {
       {(const void *)k_rescue_prep, 1, 0, 1},    {(const void *)k_scan_check, 1, 0, 1},
       {(const void *)k_terminal, 1, 0, 1},       {(const void *)k_dual_terminal, 1, 0, 1},
       {(const void *)k_lqr_up, 1, 0, 1}};
+  const bool many = ntasks >= kManyTasksPerSm * h->sms;
   for (const auto &e : table)
-    if (e.fn == kern) return n >= e.n_from ? e.warps_from : e.warps;
+    if (e.fn == kern) {
+      const int w = n >= e.n_from ? e.warps_from : e.warps;
+      // one to four tasks per SM: a one-warp entry takes two warps (256 problems of 256
+      // stages, n = 16: 37 ms with two, 42 with one, 49 with four)
+      return many ? w : std::max(w, 2);
+    }
   return kTeamWarps;
 }
 
@@ -281,6 +287,7 @@ void eclqr_default_options(eclqr_options *opt) {
   opt->refine_tol = 5e-10;
   opt->riccati_fp32 = 0;
   opt->persist = 0;
+  opt->corr_refine = -1;
 }
 
 int eclqr_layout(const eclqr_desc *d, eclqr_layout_info *out) {
@@ -319,7 +326,8 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   if (h->opt.refine < 0 || h->opt.refine > 8 || h->opt.chunk < 0 || !(h->opt.tau_rank > 0) || !(h->opt.tau_inc > 0) ||
       !(tw == 0 || tw == 1 || tw == 2 || tw == 4 || tw == 8) || !(h->opt.scan_skip == 0 || h->opt.scan_skip == 1) ||
       h->opt.kkt_refine < 0 || h->opt.kkt_refine > 16 || !(h->opt.refine_tol >= 0) ||
-      !(h->opt.riccati_fp32 == 0 || h->opt.riccati_fp32 == 1) || h->opt.persist < -1 || h->opt.persist > 32) {
+      !(h->opt.riccati_fp32 == 0 || h->opt.riccati_fp32 == 1) || h->opt.persist < -1 || h->opt.persist > 32 ||
+      h->opt.corr_refine < -1 || h->opt.corr_refine > 8) {
     delete h;
     return ECLQR_EINVAL;
   }
@@ -361,6 +369,8 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
   std::map<std::pair<int, int>, std::vector<int>> by_dims;
   for (int j = 0; j < P; j++) by_dims[{d->n[j], d->m[j]}].push_back(j);
   long long total_stages = h->lay.stages;
+  int nmax = 1;  // the longest horizon of the batch
+  for (int j = 0; j < P; j++) nmax = std::max(nmax, d->N[j]);
   for (auto &kv : by_dims) {
     GroupHost gh;
     Group &g = gh.g;
@@ -428,9 +438,11 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     for (int j : gh.ids) {
       ProbInfo pi = pinfo[j];
       int L = h->opt.chunk;
-      if (L <= 0 && h->P >= 2 * sms) {
-        // at least two problems per SM: one chunk per problem.  Its sweeps then run
-        // without chunk aggregates, scan levels or next-chunk re-sweeps, the least work.
+      if (L <= 0 && (long long)nmax * sms <= total_stages) {
+        // the longest horizon is at most the stages per SM: one chunk per problem.  Its
+        // sweeps then run without chunk aggregates, scan levels or next-chunk re-sweeps,
+        // the least work, and no problem's sequential sweep outlasts an SM's share of the
+        // batch (256 problems of 256 stages: 37 ms against 83 ms chunked).
         L = std::max(1, pi.N);
       } else if (L <= 0) {
         // enough chunks to give every SM work, but never shorter than 7 stages: shorter
@@ -625,11 +637,11 @@ int aff_scan(eclqr_handle *h, const GroupHost &gh, const Group &g, int mode, cud
 
 // rollout with refinement on the reduced residual, and recovery (Sec. 6, eq. recovery-maps)
 int run_solve(eclqr_handle *h, const GroupHost &gh, const Group &g, cudaStream_t gst, const double *s0, double *x,
-              double *u) {
+              double *u, int refine_passes) {
   TRY(launch(h, k_solve_init, g.nprob, 0, gst, g, s0));
   TRY(aff_scan(h, gh, g, AFF_ROLL_, gst));
   TRY(launch(h, k_post_roll, g.nstage, 0, gst, g, 0));
-  for (int r = 0; r < h->opt.refine; r++) {
+  for (int r = 0; r < refine_passes; r++) {
     const int sres = 3 * g.n + 2 * g.m;
     TRY(launch(h, k_resid, g.nstage, sres, gst, g, sres));
     TRY(aff_scan(h, gh, g, AFF_PLIN_, gst));
@@ -698,7 +710,7 @@ int eclqr_solve(eclqr_handle *h, const double *s0, double *x, double *u, int32_t
   TRY(fork_groups(h, st));
   for (auto &gh : h->groups) {
     gh.g.status = status;
-    TRY(run_solve(h, gh, gh.g, group_stream(h, gh, st), s0, x, u));
+    TRY(run_solve(h, gh, gh.g, group_stream(h, gh, st), s0, x, u, h->opt.refine));
   }
   TRY(join_groups(h, st));
   h->solved = true;
@@ -768,6 +780,7 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
   const SolMut &t = h->trial;
   const Sol tc{t.x, t.u, t.lam, t.mu, t.eta, t.alpha};
   const RefineMasks mk = h->mk;
+  const int corr = h->opt.corr_refine < 0 ? h->opt.refine : h->opt.corr_refine;
   // outside a stream capture the passes stop as soon as no problem takes part (one 4-byte read
   // back per pass); a captured sequence holds every pass, whose kernels return at once for
   // problems that take no part
@@ -814,7 +827,7 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
       gf.active = mk.full;
       gf.c = h->rows.c; gf.d = h->rows.d; gf.e = h->rows.e; gf.qv = h->rows.qv; gf.rv = h->rows.rv;
       TRY(run_build(h, gh, gf, gst, false));
-      TRY(run_solve(h, gh, gf, gst, h->rows.s0, t.x, t.u));
+      TRY(run_solve(h, gh, gf, gst, h->rows.s0, t.x, t.u, corr));
       TRY(run_mult(h, gh, gf, gst, t.x, t.u, t.lam, t.mu, t.eta, t.alpha));
       // primal rows within it: homogeneous constraints, so the build's factors serve as they
       // are and only the linear costs change (as for the adjoint, eclqr_set_costs)
@@ -822,7 +835,7 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
       gz.active = mk.cheap;
       gz.c = h->zeros; gz.d = h->zeros; gz.e = h->zeros; gz.qv = h->rows.qv; gz.rv = h->rows.rv;
       TRY(launch(h, k_set_costs, gz.nstage, 0, gst, gz, 0));
-      TRY(run_solve(h, gh, gz, gst, h->zeros, t.x, t.u));
+      TRY(run_solve(h, gh, gz, gst, h->zeros, t.x, t.u, corr));
       TRY(run_mult(h, gh, gz, gst, t.x, t.u, t.lam, t.mu, t.eta, t.alpha));
       // trial point w + dw, its residual, and the choice
       TRY(launch(h, k_refine_gate, gu.nprob, 0, gst, gu, (const int32_t *)h->cstatus, mk.active));
@@ -868,7 +881,7 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
         g.active = mk.active;
         g.status = status;
         TRY(run_build(h, gh, g, gst, false));
-        TRY(run_solve(h, gh, g, gst, s0, x, u));
+        TRY(run_solve(h, gh, g, gst, s0, x, u, h->opt.refine));
         TRY(run_mult(h, gh, g, gst, x, u, lam, mu, eta, alpha));
         TRY(launch(h, k_kkt, g.nstage, 0, gst, g, s0, (const double *)x, (const double *)u, (const double *)lam,
                    (const double *)mu, (const double *)eta, (const double *)alpha, KktRows{}, resid, h->parts));

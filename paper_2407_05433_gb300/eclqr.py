@@ -39,7 +39,8 @@ class eclqr_grads(ct.Structure):
 class eclqr_options(ct.Structure):
     _fields_ = [("tau_rank", ct.c_double), ("tau_inc", ct.c_double), ("refine", ct.c_int32), ("chunk", ct.c_int32),
                 ("team_warps", ct.c_int32), ("scan_skip", ct.c_int32), ("kkt_refine", ct.c_int32),
-                ("refine_tol", ct.c_double), ("riccati_fp32", ct.c_int32), ("persist", ct.c_int32)]
+                ("refine_tol", ct.c_double), ("riccati_fp32", ct.c_int32), ("persist", ct.c_int32),
+                ("corr_refine", ct.c_int32)]
 
 
 LAYOUT_FIELDS = ("A", "B", "c", "C", "D", "d", "E", "e", "Q", "M", "R", "qv", "rv", "s0",
@@ -237,7 +238,7 @@ class Batch:
     """A batch of problems resident on one CUDA device, solved through the C ABI."""
 
     def __init__(self, problems, device="cuda", tau_rank=1e-10, tau_inc=1e-8, refine=2, chunk=0, team_warps=0,
-                 scan_skip=1, kkt_refine=8, refine_tol=5e-10, riccati_fp32=0, persist=0):
+                 scan_skip=1, kkt_refine=8, refine_tol=5e-10, riccati_fp32=0, persist=0, corr_refine=-1):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -253,6 +254,7 @@ class Batch:
         opt.kkt_refine, opt.refine_tol = kkt_refine, refine_tol
         opt.riccati_fp32 = riccati_fp32
         opt.persist = persist
+        opt.corr_refine = corr_refine
         with torch.cuda.device(self.device):
             rc, self.h = eclqr_create(self.desc, opt)
         _check(rc, "eclqr_create")

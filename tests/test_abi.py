@@ -49,7 +49,7 @@ def test_strerror_and_defaults(lib):
     o = eclqr.eclqr_default_options()
     assert o.tau_rank == 1e-10 and o.tau_inc == 1e-8 and o.refine == 2 and o.chunk == 0 and o.team_warps == 0
     assert o.scan_skip == 1 and o.kkt_refine == 8 and o.refine_tol == 5e-10 and o.riccati_fp32 == 0
-    assert o.persist == 0
+    assert o.persist == 0 and o.corr_refine == -1
 
 
 def test_layout_sizes_match_packing(lib):
