@@ -309,7 +309,7 @@ def measure_kernels(pbs, dev, flush, stream, flops):
     ms = {k: 0.0 for k in names}
     launches = {k: 0 for k in names}
     for key, gp in sorted(groups.items()):
-        # the group alone still counts as a large batch (two or more problems per SM): one chunk each.
+        # the group alone still takes one chunk per problem (its longest horizon fits an SM's share).
         # Without the refinement on the KKT residual every kernel launches once per phase, so the
         # phase's flops and the kernel's time describe the same work.
         b = eclqr.Batch(gp, device=dev, kkt_refine=0)
