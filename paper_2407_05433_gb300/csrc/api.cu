@@ -91,7 +91,11 @@ namespace {
 // them, and needs no CTA barrier.  The entries are the fastest team measured per
 // kernel and state dimension on the 4096-problem uneven batch (each (n, m) group
 // alone, about seven problems per SM).  For example the Riccati sweep takes 247
-// ms over the four groups with one warp per problem against 320 ms with four;
+// ms over the four groups with one warp per problem against 320 ms with four
+// (at n = 24, 86 ms with two warps against 93 with one); the affine chains take
+// 4 ms with two warps at n = 8 against 7 with eight, but 7 ms with eight at
+// n = 24 against 11 with two; the chunk up-sweeps of the long horizon (65536
+// stages in 1024 chunks) take 27 ms with two warps per chunk against 37 with one;
 // the stage elimination takes 14 ms with one warp at n = 8 against 29 ms with
 // four, but 86 ms with four at n = 24 against 120 ms with one, where its stage
 // matrices fill four warps.
@@ -100,10 +104,10 @@ int team_for(const eclqr_handle *h, const void *kern, int ntasks, int n) {
   if (ntasks < h->sms) return kTeamWarps;
   // warps below n_from, and from n_from up
   static const struct { const void *fn; int warps, n_from, warps_from; } table[] = {
-      {(const void *)k_riccati_down, 1, 0, 1},   {(const void *)k_riccati_down_f32, 1, 0, 1},
+      {(const void *)k_riccati_down, 1, 24, 2},  {(const void *)k_riccati_down_f32, 1, 0, 1},
       {(const void *)k_riccati_finish, 1, 0, 1}, {(const void *)k_elim, 1, 16, 4},
       {(const void *)k_primal_down, 1, 24, 2},   {(const void *)k_dual_down, 1, 0, 1},
-      {(const void *)k_aff_down, 8, 0, 8},       {(const void *)k_dual_leaf, 1, 0, 1},
+      {(const void *)k_aff_down, 2, 24, 8},      {(const void *)k_dual_leaf, 1, 0, 1},
       {(const void *)k_aff_prep, 1, 0, 1},
       {(const void *)k_dual_stage, 2, 0, 2},     {(const void *)k_param, 1, 0, 1},
       {(const void *)k_resid, 1, 0, 1},          {(const void *)k_pcorr, 1, 0, 1},
@@ -114,7 +118,8 @@ int team_for(const eclqr_handle *h, const void *kern, int ntasks, int n) {
       {(const void *)k_refine_parts, 1, 0, 1},   {(const void *)k_refine_post, 1, 0, 1},
       {(const void *)k_rescue_prep, 1, 0, 1},    {(const void *)k_scan_check, 1, 0, 1},
       {(const void *)k_terminal, 1, 0, 1},       {(const void *)k_dual_terminal, 1, 0, 1},
-      {(const void *)k_lqr_up, 1, 0, 1}};
+      {(const void *)k_lqr_up, 2, 0, 2},         {(const void *)k_primal_up, 1, 0, 1},
+      {(const void *)k_dual_up, 2, 0, 2}};
   const bool many = ntasks >= kManyTasksPerSm * h->sms;
   for (const auto &e : table)
     if (e.fn == kern) {
