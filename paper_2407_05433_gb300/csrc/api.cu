@@ -26,6 +26,7 @@ constexpr int kMaxSmemBytes = 219 * 1024;
 constexpr int kTeamWarps = 4;  // default team: one warp per SM sub-partition
 constexpr int kManyTasksPerSm = 4;  // a launch with at least this many tasks per SM takes the table's team
 constexpr int kPersistCtasPerSm = 8;  // default CTAs per SM of a persistent launch
+constexpr int kListCtasPerSm = 8;     // CTAs per SM of a per-stage launch over a stage list
 
 struct GroupHost {
   Group g;
@@ -36,6 +37,8 @@ struct GroupHost {
   bool any_skip = false;  // some problem of the group may take the Sec. 6 shortcut
   void *dmem = nullptr;
   int *queue = nullptr;  // device counter of the group's persistent launches (in dmem)
+  int *slists = nullptr; // a refinement pass's stage lists (active, full, cheap), 3 x nstage (in dmem)
+  int *scounts = nullptr;  // their lengths (3)
   std::vector<int> ids;  // batch indices of the problems in this group
 };
 
@@ -108,7 +111,7 @@ int team_for(const eclqr_handle *h, const void *kern, int ntasks, int n) {
       {(const void *)k_riccati_finish, 1, 0, 1}, {(const void *)k_elim, 1, 16, 4},
       {(const void *)k_primal_down, 1, 24, 2},   {(const void *)k_dual_down, 1, 0, 1},
       {(const void *)k_aff_down, 2, 24, 8},      {(const void *)k_dual_leaf, 1, 0, 1},
-      {(const void *)k_aff_prep, 1, 0, 1},
+      {(const void *)k_aff_prep, 1, 0, 1},       {(const void *)k_stage_lists, 1, 0, 1},
       {(const void *)k_dual_stage, 2, 0, 2},     {(const void *)k_param, 1, 0, 1},
       {(const void *)k_resid, 1, 0, 1},          {(const void *)k_pcorr, 1, 0, 1},
       {(const void *)k_kkt, 1, 0, 1},            {(const void *)k_post_roll, 1, 0, 1},
@@ -164,10 +167,32 @@ int launch_grid(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int grid, i
   return cudaPeekAtLastError() == cudaSuccess ? ECLQR_OK : ECLQR_ECUDA;
 }
 
-// one CTA per task
+// the per-stage kernels written with for_stages, which can run over a stage list
+bool stage_list_kernel(const void *kern) {
+  static const void *const table[] = {
+      (const void *)k_kkt,        (const void *)k_param,         (const void *)k_elim,
+      (const void *)k_riccati_finish, (const void *)k_aff_prep,  (const void *)k_post_roll,
+      (const void *)k_resid,      (const void *)k_pcorr,         (const void *)k_recover,
+      (const void *)k_dual_stage, (const void *)k_dual_leaf,     (const void *)k_set_costs,
+      (const void *)k_refine_trial, (const void *)k_refine_accept};
+  for (const void *k : table)
+    if (k == kern) return true;
+  return false;
+}
+inline const int *group_slist(const Group &g) { return g.slist; }
+template <typename A0, typename... Rest>
+const int *group_slist(const A0 &a0, const Rest &...) {
+  return group_slist(a0);
+}
+
+// one CTA per task; a per-stage kernel on a group with a stage list takes
+// kListCtasPerSm CTAs per SM (at most one per stage) that loop over the list
 template <typename... KArgs, typename... Args>
 int launch(eclqr_handle *h, void (*kern)(KArgs...), int ntasks, int per_task, cudaStream_t st, Args... args) {
-  return launch_grid(h, kern, ntasks, ntasks, per_task, st, args...);
+  int grid = ntasks;
+  if (group_slist(args...) != nullptr && stage_list_kernel((const void *)kern))
+    grid = std::min(ntasks, kListCtasPerSm * h->sms);
+  return launch_grid(h, kern, ntasks, grid, per_task, st, args...);
 }
 
 // A per-problem sweep as a persistent launch: per_sm CTAs per SM take the tasks
@@ -506,6 +531,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     size_t o_CS1 = take(sizeof(double) * (size_t)g.cs_stride * g.nslot);
     size_t o_CI0 = take(sizeof(int) * CI_STRIDE * g.nslot), o_CI1 = take(sizeof(int) * CI_STRIDE * g.nslot);
     size_t o_need = take(sizeof(int) * (size_t)g.nprob), o_queue = take(sizeof(int));
+    size_t o_sl = take(sizeof(int) * 3 * (size_t)g.nstage), o_sc = take(sizeof(int) * 3);
     if (cudaMalloc(&gh.dmem, off) != cudaSuccess) {
       for (auto &x : h->groups) cudaFree(x.dmem);
       delete h;
@@ -531,6 +557,8 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     g.CI[1] = (int *)(base + o_CI1);
     g.need_scan = (int *)(base + o_need);
     gh.queue = (int *)(base + o_queue);
+    gh.slists = (int *)(base + o_sl);
+    gh.scounts = (int *)(base + o_sc);
     h->groups.push_back(gh);
   }
   if (h->opt.kkt_refine > 0) {
@@ -817,11 +845,17 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
     corrected = true;
     for (auto &gh : h->groups) {
       const cudaStream_t gst = group_stream(h, gh, st);
+      Group gu = gh.g;
+      gu.active = nullptr;
+      // the stages of the problems that take part, of those that rebuild and of those that
+      // take the cheap correction: the pass's per-stage kernels visit only those
+      if (cudaMemsetAsync(gh.scounts, 0, 3 * sizeof(int), gst) != cudaSuccess) return ECLQR_ECUDA;
+      TRY(launch(h, k_stage_lists, gu.nprob, 0, gst, gu, mk, gh.slists, gh.scounts));
       Group g = gh.g;  // the problem's data, masked to the problems that take part
       g.active = mk.active;
       g.status = h->cstatus;
-      Group gu = gh.g;
-      gu.active = nullptr;
+      g.slist = gh.slists;
+      g.scount = gh.scounts;
       // residual rows of the point, in the layout of the offsets they replace
       TRY(launch(h, k_kkt, g.nstage, 0, gst, g, s0, (const double *)x, (const double *)u, (const double *)lam,
                  (const double *)mu, (const double *)eta, (const double *)alpha, h->rows, (double *)nullptr,
@@ -830,6 +864,8 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
       // through a new build
       Group gf = g;
       gf.active = mk.full;
+      gf.slist = gh.slists + gu.nstage;
+      gf.scount = gh.scounts + 1;
       gf.c = h->rows.c; gf.d = h->rows.d; gf.e = h->rows.e; gf.qv = h->rows.qv; gf.rv = h->rows.rv;
       TRY(run_build(h, gh, gf, gst, false));
       TRY(run_solve(h, gh, gf, gst, h->rows.s0, t.x, t.u, corr));
@@ -838,6 +874,8 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
       // are and only the linear costs change (as for the adjoint, eclqr_set_costs)
       Group gz = g;
       gz.active = mk.cheap;
+      gz.slist = gh.slists + 2 * (size_t)gu.nstage;
+      gz.scount = gh.scounts + 2;
       gz.c = h->zeros; gz.d = h->zeros; gz.e = h->zeros; gz.qv = h->rows.qv; gz.rv = h->rows.rv;
       TRY(launch(h, k_set_costs, gz.nstage, 0, gst, gz, 0));
       TRY(run_solve(h, gh, gz, gst, h->zeros, t.x, t.u, corr));

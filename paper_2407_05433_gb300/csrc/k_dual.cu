@@ -48,102 +48,102 @@ __host__ int smem_dual_leaf(int n, int m, int pmax, int qmax) {
 
 // ---------------------------------------------------------------- per-stage blocks
 __global__ void k_dual_stage(Group g, const double *x, const double *u, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
-  double *ws = stage_ws(g, s);
-  const int *wi = stage_wi(g, s);
-  const int r0 = wi[SI_UR];
-  const double *U = ws + g.ws.UT;  // first r0 columns, ld n
-  const double *xi = x + P.ox + (size_t)i * n;
-  const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
-  const int ldc = g.pmax + g.qmax + 1;
-  double *sm = team_smem(per_task);
-  double *X = sm, *gx = X + n * n, *tp = gx + n, *rx = tp + n, *gu = rx + n;
-  if (i == P.N) {
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+    double *ws = stage_ws(g, s);
+    const int *wi = stage_wi(g, s);
+    const int r0 = wi[SI_UR];
+    const double *U = ws + g.ws.UT;  // first r0 columns, ld n
+    const double *xi = x + P.ox + (size_t)i * n;
+    const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
+    const int ldc = g.pmax + g.qmax + 1;
+    double *sm = team_smem(per_task);
+    double *X = sm, *gx = X + n * n, *tp = gx + n, *rx = tp + n, *gu = rx + n;
+    if (i == P.N) {
+      for (int a = tid; a < n; a += TEAM) {
+        double v = q[a];
+        for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
+        gx[a] = v;
+      }
+      tsync();
+      for (int a = tid; a < r0; a += TEAM) {
+        double v = 0.0;
+        for (int l = 0; l < n; l++) v = fma(U[l * n + a], gx[l], v);
+        ws[g.ws.Ux + a] = v;
+      }
+      for (int idx = tid; idx < r0 * S.q; idx += TEAM) {
+        int a = idx / S.q, j = idx - a * S.q;
+        double v = 0.0;
+        for (int l = 0; l < n; l++) v = fma(U[l * n + a], g.E[P.oE + (size_t)(S.qrow + j) * n + l], v);
+        ws[g.ws.UC + a * ldc + j] = v;
+      }
+      return;
+    }
+    const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
+    const double *Mm = g.M + P.oM + (size_t)i * n * m, *R = g.R + P.oR + (size_t)i * m * m;
+    const double *r = g.rv + P.orv + (size_t)i * m, *ui = u + P.ou + (size_t)i * m;
+    const double *wn = stage_ws(g, s + 1);
+    const int *win = stage_wi(g, s + 1);
+    const int r1 = win[SI_UR], nb1 = n - r1;
+    const double *U1 = wn + g.ws.UT, *T1 = wn + g.ws.UT + r1, *pi1 = wn + g.ws.pi;
+    // objective gradients (eq. objective-gradients) and T_{i+1} pi_{i+1}
     for (int a = tid; a < n; a += TEAM) {
       double v = q[a];
       for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
+      for (int j = 0; j < m; j++) v = fma(Mm[a * m + j], ui[j], v);
       gx[a] = v;
+      double t = 0.0;
+      for (int j = 0; j < nb1; j++) t = fma(T1[a * n + j], pi1[j], t);
+      tp[a] = t;
+    }
+    for (int a = tid; a < m; a += TEAM) {
+      double v = r[a];
+      for (int j = 0; j < n; j++) v = fma(Mm[j * m + a], xi[j], v);
+      for (int j = 0; j < m; j++) v = fma(R[a * m + j], ui[j], v);
+      gu[a] = v;
     }
     tsync();
+    for (int a = tid; a < n; a += TEAM) {
+      double v = gx[a];
+      for (int l = 0; l < n; l++) v = fma(A[l * n + a], tp[l], v);
+      rx[a] = v;
+    }
+    for (int a = tid; a < m; a += TEAM) {
+      double v = gu[a];
+      for (int l = 0; l < n; l++) v = fma(B[l * m + a], tp[l], v);
+      ws[g.ws.ru + a] = v;
+    }
+    // X = A' U_{i+1} (n x r1)
+    for (int idx = tid; idx < n * r1; idx += TEAM) {
+      int l = idx / r1, b = idx - l * r1;
+      double v = 0.0;
+      for (int k = 0; k < n; k++) v = fma(A[k * n + l], U1[k * n + b], v);
+      X[l * n + b] = v;
+    }
+    tsync();
+    wgemm<true, false>(r0, r1, n, 1.0, U, n, X, n, 0.0, ws + g.ws.UA, n);   // U' A' U1
+    for (int idx = tid; idx < m * r1; idx += TEAM) {
+      int a = idx / r1, b = idx - a * r1;
+      double v = 0.0;
+      for (int k = 0; k < n; k++) v = fma(B[k * m + a], U1[k * n + b], v);
+      ws[g.ws.BU + a * n + b] = v;                                         // B' U1
+    }
+    for (int idx = tid; idx < r0 * (S.p + S.q); idx += TEAM) {
+      int a = idx / (S.p + S.q), j = idx - a * (S.p + S.q);
+      const double *row = (j < S.p) ? g.C + P.oC + (size_t)(S.prow + j) * n : g.E + P.oE + (size_t)(S.qrow + j - S.p) * n;
+      double v = 0.0;
+      for (int l = 0; l < n; l++) v = fma(U[l * n + a], row[l], v);
+      ws[g.ws.UC + a * ldc + j] = v;                                       // U' [C' E']
+    }
     for (int a = tid; a < r0; a += TEAM) {
       double v = 0.0;
-      for (int l = 0; l < n; l++) v = fma(U[l * n + a], gx[l], v);
-      ws[g.ws.Ux + a] = v;
+      for (int l = 0; l < n; l++) v = fma(U[l * n + a], rx[l], v);
+      ws[g.ws.Ux + a] = v;                                                 // U' rho^x
     }
-    for (int idx = tid; idx < r0 * S.q; idx += TEAM) {
-      int a = idx / S.q, j = idx - a * S.q;
-      double v = 0.0;
-      for (int l = 0; l < n; l++) v = fma(U[l * n + a], g.E[P.oE + (size_t)(S.qrow + j) * n + l], v);
-      ws[g.ws.UC + a * ldc + j] = v;
-    }
-    return;
-  }
-  const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
-  const double *Mm = g.M + P.oM + (size_t)i * n * m, *R = g.R + P.oR + (size_t)i * m * m;
-  const double *r = g.rv + P.orv + (size_t)i * m, *ui = u + P.ou + (size_t)i * m;
-  const double *wn = stage_ws(g, s + 1);
-  const int *win = stage_wi(g, s + 1);
-  const int r1 = win[SI_UR], nb1 = n - r1;
-  const double *U1 = wn + g.ws.UT, *T1 = wn + g.ws.UT + r1, *pi1 = wn + g.ws.pi;
-  // objective gradients (eq. objective-gradients) and T_{i+1} pi_{i+1}
-  for (int a = tid; a < n; a += TEAM) {
-    double v = q[a];
-    for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
-    for (int j = 0; j < m; j++) v = fma(Mm[a * m + j], ui[j], v);
-    gx[a] = v;
-    double t = 0.0;
-    for (int j = 0; j < nb1; j++) t = fma(T1[a * n + j], pi1[j], t);
-    tp[a] = t;
-  }
-  for (int a = tid; a < m; a += TEAM) {
-    double v = r[a];
-    for (int j = 0; j < n; j++) v = fma(Mm[j * m + a], xi[j], v);
-    for (int j = 0; j < m; j++) v = fma(R[a * m + j], ui[j], v);
-    gu[a] = v;
-  }
-  tsync();
-  for (int a = tid; a < n; a += TEAM) {
-    double v = gx[a];
-    for (int l = 0; l < n; l++) v = fma(A[l * n + a], tp[l], v);
-    rx[a] = v;
-  }
-  for (int a = tid; a < m; a += TEAM) {
-    double v = gu[a];
-    for (int l = 0; l < n; l++) v = fma(B[l * m + a], tp[l], v);
-    ws[g.ws.ru + a] = v;
-  }
-  // X = A' U_{i+1} (n x r1)
-  for (int idx = tid; idx < n * r1; idx += TEAM) {
-    int l = idx / r1, b = idx - l * r1;
-    double v = 0.0;
-    for (int k = 0; k < n; k++) v = fma(A[k * n + l], U1[k * n + b], v);
-    X[l * n + b] = v;
-  }
-  tsync();
-  wgemm<true, false>(r0, r1, n, 1.0, U, n, X, n, 0.0, ws + g.ws.UA, n);   // U' A' U1
-  for (int idx = tid; idx < m * r1; idx += TEAM) {
-    int a = idx / r1, b = idx - a * r1;
-    double v = 0.0;
-    for (int k = 0; k < n; k++) v = fma(B[k * m + a], U1[k * n + b], v);
-    ws[g.ws.BU + a * n + b] = v;                                         // B' U1
-  }
-  for (int idx = tid; idx < r0 * (S.p + S.q); idx += TEAM) {
-    int a = idx / (S.p + S.q), j = idx - a * (S.p + S.q);
-    const double *row = (j < S.p) ? g.C + P.oC + (size_t)(S.prow + j) * n : g.E + P.oE + (size_t)(S.qrow + j - S.p) * n;
-    double v = 0.0;
-    for (int l = 0; l < n; l++) v = fma(U[l * n + a], row[l], v);
-    ws[g.ws.UC + a * ldc + j] = v;                                       // U' [C' E']
-  }
-  for (int a = tid; a < r0; a += TEAM) {
-    double v = 0.0;
-    for (int l = 0; l < n; l++) v = fma(U[l * n + a], rx[l], v);
-    ws[g.ws.Ux + a] = v;                                                 // U' rho^x
-  }
+  });
 }
 
 // rows (a) and (b) of stage s into M (ld ldm) at row 0, with the column
@@ -395,79 +395,79 @@ __global__ void k_dual_root(Group g, int per_task) {
 
 // ---------------------------------------------------------------- leaves: mu_i, eta_i, lambda_i, alpha, eta_N
 __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
-  const double *ws = stage_ws(g, s);
-  const int r0 = stage_wi(g, s)[SI_UR], nb = n - r0;
-  const int ldc = g.pmax + g.qmax + 1;
-  const double *nu0 = ws + g.ws.nu;
-  // lambda_i = T_i pi_i + U_i nu_i
-  const double *UT = ws + g.ws.UT, *pi = ws + g.ws.pi;
-  bool bad = false;
-  for (int a = tid; a < n; a += TEAM) {
-    double v = 0.0;
-    for (int j = 0; j < r0; j++) v = fma(UT[a * n + j], nu0[j], v);
-    for (int j = 0; j < nb; j++) v = fma(UT[a * n + r0 + j], pi[j], v);
-    lam[P.olam + (size_t)i * n + a] = v;
-    if (i == 0) alpha[P.oalpha + a] = -v;
-    bad = bad || !isfinite(v);
-  }
-  if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
-  const int w = (i < P.N) ? S.p + S.q : S.q;
-  if (w == 0) return;
-  double *sm = team_smem(per_task);
-  const int wmax = g.pmax + g.qmax, rmax = n + m;
-  double *F = sm, *rhs = F + rmax * wmax, *Wt = rhs + rmax, *Qf = Wt + wmax * rmax, *X = Qf + wmax * wmax;
-  double *Ys = X + wmax, *tq = Ys + rmax;
-  int *perm = (int *)(tq + 2 * (rmax + wmax));
-  int rows;
-  if (i < P.N) {
-    const double *wn = stage_ws(g, s + 1);
-    const int r1 = stage_wi(g, s + 1)[SI_UR];
-    const double *nu1 = wn + g.ws.nu;
-    rows = r0 + m;
-    for (int idx = tid; idx < rows * w; idx += TEAM) {
-      int r = idx / w, j = idx - r * w;
-      double val;
-      if (r < r0) val = ws[g.ws.UC + r * ldc + j];
-      else val = (j < S.p) ? g.D[P.oD + (size_t)(S.prow + j) * m + (r - r0)] : 0.0;
-      F[idx] = val;
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+    const double *ws = stage_ws(g, s);
+    const int r0 = stage_wi(g, s)[SI_UR], nb = n - r0;
+    const int ldc = g.pmax + g.qmax + 1;
+    const double *nu0 = ws + g.ws.nu;
+    // lambda_i = T_i pi_i + U_i nu_i
+    const double *UT = ws + g.ws.UT, *pi = ws + g.ws.pi;
+    bool bad = false;
+    for (int a = tid; a < n; a += TEAM) {
+      double v = 0.0;
+      for (int j = 0; j < r0; j++) v = fma(UT[a * n + j], nu0[j], v);
+      for (int j = 0; j < nb; j++) v = fma(UT[a * n + r0 + j], pi[j], v);
+      lam[P.olam + (size_t)i * n + a] = v;
+      if (i == 0) alpha[P.oalpha + a] = -v;
+      bad = bad || !isfinite(v);
     }
-    for (int r = tid; r < rows; r += TEAM) {
-      double v;
-      if (r < r0) {
-        v = ws[g.ws.Ux + r] - nu0[r];
-        for (int b = 0; b < r1; b++) v = fma(ws[g.ws.UA + r * n + b], nu1[b], v);
-      } else {
-        v = ws[g.ws.ru + (r - r0)];
-        for (int b = 0; b < r1; b++) v = fma(ws[g.ws.BU + (r - r0) * n + b], nu1[b], v);
+    if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
+    const int w = (i < P.N) ? S.p + S.q : S.q;
+    if (w == 0) return;
+    double *sm = team_smem(per_task);
+    const int wmax = g.pmax + g.qmax, rmax = n + m;
+    double *F = sm, *rhs = F + rmax * wmax, *Wt = rhs + rmax, *Qf = Wt + wmax * rmax, *X = Qf + wmax * wmax;
+    double *Ys = X + wmax, *tq = Ys + rmax;
+    int *perm = (int *)(tq + 2 * (rmax + wmax));
+    int rows;
+    if (i < P.N) {
+      const double *wn = stage_ws(g, s + 1);
+      const int r1 = stage_wi(g, s + 1)[SI_UR];
+      const double *nu1 = wn + g.ws.nu;
+      rows = r0 + m;
+      for (int idx = tid; idx < rows * w; idx += TEAM) {
+        int r = idx / w, j = idx - r * w;
+        double val;
+        if (r < r0) val = ws[g.ws.UC + r * ldc + j];
+        else val = (j < S.p) ? g.D[P.oD + (size_t)(S.prow + j) * m + (r - r0)] : 0.0;
+        F[idx] = val;
       }
-      rhs[r] = v;
+      for (int r = tid; r < rows; r += TEAM) {
+        double v;
+        if (r < r0) {
+          v = ws[g.ws.Ux + r] - nu0[r];
+          for (int b = 0; b < r1; b++) v = fma(ws[g.ws.UA + r * n + b], nu1[b], v);
+        } else {
+          v = ws[g.ws.ru + (r - r0)];
+          for (int b = 0; b < r1; b++) v = fma(ws[g.ws.BU + (r - r0) * n + b], nu1[b], v);
+        }
+        rhs[r] = v;
+      }
+    } else {
+      rows = r0;
+      for (int idx = tid; idx < rows * w; idx += TEAM) {
+        int r = idx / w, j = idx - r * w;
+        F[idx] = ws[g.ws.UC + r * ldc + j];
+      }
+      for (int r = tid; r < rows; r += TEAM) rhs[r] = ws[g.ws.Ux + r] - nu0[r];
     }
-  } else {
-    rows = r0;
-    for (int idx = tid; idx < rows * w; idx += TEAM) {
-      int r = idx / w, j = idx - r * w;
-      F[idx] = ws[g.ws.UC + r * ldc + j];
+    tsync();
+    const int rank = wtqr(F, w, rows, w, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qf, wmax, perm, tq);
+    wtqr_solve(Wt, (rows > 0 ? rows : 1), Qf, wmax, perm, rows, w, rank, rhs, 1, 1, X, 1, Ys, 1);
+    bad = false;
+    if (i < P.N) {
+      for (int j = tid; j < S.p; j += TEAM) mu[P.omu + S.prow + j] = X[j];
+      for (int j = tid; j < S.q; j += TEAM) eta[P.oeta + S.qrow + j] = X[S.p + j];
+    } else {
+      for (int j = tid; j < S.q; j += TEAM) eta[P.oeta + S.qrow + j] = X[j];
     }
-    for (int r = tid; r < rows; r += TEAM) rhs[r] = ws[g.ws.Ux + r] - nu0[r];
-  }
-  tsync();
-  const int rank = wtqr(F, w, rows, w, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qf, wmax, perm, tq);
-  wtqr_solve(Wt, (rows > 0 ? rows : 1), Qf, wmax, perm, rows, w, rank, rhs, 1, 1, X, 1, Ys, 1);
-  bad = false;
-  if (i < P.N) {
-    for (int j = tid; j < S.p; j += TEAM) mu[P.omu + S.prow + j] = X[j];
-    for (int j = tid; j < S.q; j += TEAM) eta[P.oeta + S.qrow + j] = X[S.p + j];
-  } else {
-    for (int j = tid; j < S.q; j += TEAM) eta[P.oeta + S.qrow + j] = X[j];
-  }
-  for (int j = tid; j < w; j += TEAM) bad = bad || !isfinite(X[j]);
-  if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
+    for (int j = tid; j < w; j += TEAM) bad = bad || !isfinite(X[j]);
+    if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
+  });
 }
 
 // ---------------------------------------------------------------- KKT residual (Sec. 9 definition)
@@ -505,99 +505,99 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
 __global__ void k_kkt(Group g, const double *s0, const double *x, const double *u, const double *lam,
                       const double *mu, const double *eta, const double *alpha, KktRows rows, double *resid,
                       double *parts) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
-  const bool wr = rows.c != nullptr;
-  const double *xi = x + P.ox + (size_t)i * n, *li = lam + P.olam + (size_t)i * n;
-  const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
-  double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
-  if (i == 0)
-    for (int a = tid; a < n; a += TEAM) {
-      const double v = xi[a] - s0[P.os0 + a];
-      r0 = nanmax(r0, fabs(v));
-      if (wr) rows.s0[P.os0 + a] = -v;
-    }
-  // state-only rows, normalised
-  for (int k = tid; k < S.q; k += TEAM) {
-    const double *Ek = g.E + P.oE + (size_t)(S.qrow + k) * n;
-    double e = g.e[P.oe + S.qrow + k], v = e, sc = nanmax(1.0, fabs(e));
-    for (int j = 0; j < n; j++) { v = fma(Ek[j], xi[j], v); sc = nanmax(sc, fabs(Ek[j])); }
-    r2 = nanmax(r2, fabs(v) / sc);
-    if (wr) rows.e[P.oe + S.qrow + k] = v;
-  }
-  const double *etai = eta + P.oeta + S.qrow;
-  if (i < P.N) {
-    const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
-    const double *c = g.c + P.oc + (size_t)i * n;
-    const double *Mm = g.M + P.oM + (size_t)i * n * m, *R = g.R + P.oR + (size_t)i * m * m;
-    const double *rv = g.rv + P.orv + (size_t)i * m;
-    const double *ui = u + P.ou + (size_t)i * m, *xn = x + P.ox + (size_t)(i + 1) * n;
-    const double *ln = lam + P.olam + (size_t)(i + 1) * n, *mui = mu + P.omu + S.prow;
-    for (int a = tid; a < n; a += TEAM) {
-      double v = c[a] - xn[a];
-      for (int j = 0; j < n; j++) v = fma(A[a * n + j], xi[j], v);
-      for (int j = 0; j < m; j++) v = fma(B[a * m + j], ui[j], v);
-      r1 = nanmax(r1, fabs(v));
-      if (wr) rows.c[P.oc + (size_t)i * n + a] = v;
-    }
-    for (int k = tid; k < S.p; k += TEAM) {
-      const double *Ck = g.C + P.oC + (size_t)(S.prow + k) * n, *Dk = g.D + P.oD + (size_t)(S.prow + k) * m;
-      double dd = g.d[P.od + S.prow + k], v = dd, sc = nanmax(1.0, fabs(dd));
-      for (int j = 0; j < n; j++) { v = fma(Ck[j], xi[j], v); sc = nanmax(sc, fabs(Ck[j])); }
-      for (int j = 0; j < m; j++) { v = fma(Dk[j], ui[j], v); sc = nanmax(sc, fabs(Dk[j])); }
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+    const bool wr = rows.c != nullptr;
+    const double *xi = x + P.ox + (size_t)i * n, *li = lam + P.olam + (size_t)i * n;
+    const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+    if (i == 0)
+      for (int a = tid; a < n; a += TEAM) {
+        const double v = xi[a] - s0[P.os0 + a];
+        r0 = nanmax(r0, fabs(v));
+        if (wr) rows.s0[P.os0 + a] = -v;
+      }
+    // state-only rows, normalised
+    for (int k = tid; k < S.q; k += TEAM) {
+      const double *Ek = g.E + P.oE + (size_t)(S.qrow + k) * n;
+      double e = g.e[P.oe + S.qrow + k], v = e, sc = nanmax(1.0, fabs(e));
+      for (int j = 0; j < n; j++) { v = fma(Ek[j], xi[j], v); sc = nanmax(sc, fabs(Ek[j])); }
       r2 = nanmax(r2, fabs(v) / sc);
-      if (wr) rows.d[P.od + S.prow + k] = v;
+      if (wr) rows.e[P.oe + S.qrow + k] = v;
     }
-    for (int a = tid; a < m; a += TEAM) {
-      double v = rv[a];
-      for (int j = 0; j < n; j++) v = fma(Mm[j * m + a], xi[j], v);
-      for (int j = 0; j < m; j++) v = fma(R[a * m + j], ui[j], v);
-      for (int j = 0; j < n; j++) v = fma(B[j * m + a], ln[j], v);
-      for (int k = 0; k < S.p; k++) v = fma(g.D[P.oD + (size_t)(S.prow + k) * m + a], mui[k], v);
-      r3 = nanmax(r3, fabs(v));
-      if (wr) rows.rv[P.orv + (size_t)i * m + a] = v;
+    const double *etai = eta + P.oeta + S.qrow;
+    if (i < P.N) {
+      const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
+      const double *c = g.c + P.oc + (size_t)i * n;
+      const double *Mm = g.M + P.oM + (size_t)i * n * m, *R = g.R + P.oR + (size_t)i * m * m;
+      const double *rv = g.rv + P.orv + (size_t)i * m;
+      const double *ui = u + P.ou + (size_t)i * m, *xn = x + P.ox + (size_t)(i + 1) * n;
+      const double *ln = lam + P.olam + (size_t)(i + 1) * n, *mui = mu + P.omu + S.prow;
+      for (int a = tid; a < n; a += TEAM) {
+        double v = c[a] - xn[a];
+        for (int j = 0; j < n; j++) v = fma(A[a * n + j], xi[j], v);
+        for (int j = 0; j < m; j++) v = fma(B[a * m + j], ui[j], v);
+        r1 = nanmax(r1, fabs(v));
+        if (wr) rows.c[P.oc + (size_t)i * n + a] = v;
+      }
+      for (int k = tid; k < S.p; k += TEAM) {
+        const double *Ck = g.C + P.oC + (size_t)(S.prow + k) * n, *Dk = g.D + P.oD + (size_t)(S.prow + k) * m;
+        double dd = g.d[P.od + S.prow + k], v = dd, sc = nanmax(1.0, fabs(dd));
+        for (int j = 0; j < n; j++) { v = fma(Ck[j], xi[j], v); sc = nanmax(sc, fabs(Ck[j])); }
+        for (int j = 0; j < m; j++) { v = fma(Dk[j], ui[j], v); sc = nanmax(sc, fabs(Dk[j])); }
+        r2 = nanmax(r2, fabs(v) / sc);
+        if (wr) rows.d[P.od + S.prow + k] = v;
+      }
+      for (int a = tid; a < m; a += TEAM) {
+        double v = rv[a];
+        for (int j = 0; j < n; j++) v = fma(Mm[j * m + a], xi[j], v);
+        for (int j = 0; j < m; j++) v = fma(R[a * m + j], ui[j], v);
+        for (int j = 0; j < n; j++) v = fma(B[j * m + a], ln[j], v);
+        for (int k = 0; k < S.p; k++) v = fma(g.D[P.oD + (size_t)(S.prow + k) * m + a], mui[k], v);
+        r3 = nanmax(r3, fabs(v));
+        if (wr) rows.rv[P.orv + (size_t)i * m + a] = v;
+      }
+      for (int a = tid; a < n; a += TEAM) {
+        double v = q[a] + ((i == 0) ? alpha[P.oalpha + a] : -li[a]);
+        for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
+        for (int j = 0; j < m; j++) v = fma(Mm[a * m + j], ui[j], v);
+        for (int j = 0; j < n; j++) v = fma(A[j * n + a], ln[j], v);
+        for (int k = 0; k < S.p; k++) v = fma(g.C[P.oC + (size_t)(S.prow + k) * n + a], mui[k], v);
+        for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
+        r3 = nanmax(r3, fabs(v));
+        if (wr) rows.qv[P.oqv + (size_t)i * n + a] = v;
+      }
+    } else {
+      for (int a = tid; a < n; a += TEAM) {
+        double v = q[a] - li[a];
+        for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
+        for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
+        r3 = nanmax(r3, fabs(v));
+        if (wr) rows.qv[P.oqv + (size_t)i * n + a] = v;
+      }
     }
-    for (int a = tid; a < n; a += TEAM) {
-      double v = q[a] + ((i == 0) ? alpha[P.oalpha + a] : -li[a]);
-      for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
-      for (int j = 0; j < m; j++) v = fma(Mm[a * m + j], ui[j], v);
-      for (int j = 0; j < n; j++) v = fma(A[j * n + a], ln[j], v);
-      for (int k = 0; k < S.p; k++) v = fma(g.C[P.oC + (size_t)(S.prow + k) * n + a], mui[k], v);
-      for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
-      r3 = nanmax(r3, fabs(v));
-      if (wr) rows.qv[P.oqv + (size_t)i * n + a] = v;
+    if (resid == nullptr) return;
+    if (parts != nullptr) {
+      r0 = team_max_keep_nan(r0);
+      r1 = team_max_keep_nan(r1);
+      r2 = team_max_keep_nan(r2);
+      r3 = team_max_keep_nan(r3);
+      if (tid == 0) {
+        double *pp = parts + 4 * (size_t)P.id;
+        atomic_max_nonneg(pp + 0, r0);
+        atomic_max_nonneg(pp + 1, r1);
+        atomic_max_nonneg(pp + 2, r2);
+        atomic_max_nonneg(pp + 3, r3);
+        atomic_max_nonneg(resid + P.id, nanmax(nanmax(r0, r1), nanmax(r2, r3)));
+      }
+    } else {
+      const double r = team_max_keep_nan(nanmax(nanmax(r0, r1), nanmax(r2, r3)));
+      if (tid == 0) atomic_max_nonneg(resid + P.id, r);
     }
-  } else {
-    for (int a = tid; a < n; a += TEAM) {
-      double v = q[a] - li[a];
-      for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
-      for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
-      r3 = nanmax(r3, fabs(v));
-      if (wr) rows.qv[P.oqv + (size_t)i * n + a] = v;
-    }
-  }
-  if (resid == nullptr) return;
-  if (parts != nullptr) {
-    r0 = team_max_keep_nan(r0);
-    r1 = team_max_keep_nan(r1);
-    r2 = team_max_keep_nan(r2);
-    r3 = team_max_keep_nan(r3);
-    if (tid == 0) {
-      double *pp = parts + 4 * (size_t)P.id;
-      atomic_max_nonneg(pp + 0, r0);
-      atomic_max_nonneg(pp + 1, r1);
-      atomic_max_nonneg(pp + 2, r2);
-      atomic_max_nonneg(pp + 3, r3);
-      atomic_max_nonneg(resid + P.id, nanmax(nanmax(r0, r1), nanmax(r2, r3)));
-    }
-  } else {
-    const double r = team_max_keep_nan(nanmax(nanmax(r0, r1), nanmax(r2, r3)));
-    if (tid == 0) atomic_max_nonneg(resid + P.id, r);
-  }
+  });
 }
 
 }  // namespace eclqr

@@ -91,54 +91,54 @@ namespace eclqr {
 // data, and whose linear pass is the P-form offset recursion on the stored
 // factors -- solves the problem; the next pass adds accuracy.
 __global__ void k_set_costs(Group g, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
-  double *ws = stage_ws(g, s);
-  const int *wi = stage_wi(g, s);
-  const int ur = wi[SI_UR], nb = n - ur;
-  const bool last = i == P.N;
-  const int mb = last ? 0 : wi[SI_MBAR];
-  const double *T = ws + g.ws.UT + ur, *Y = ws + g.ws.Y, *Z = ws + g.ws.Z;
-  const double *q = g.qv + P.oqv + (size_t)i * n, *r = last ? nullptr : g.rv + P.orv + (size_t)i * m;
-  for (int a = tid; a < n; a += TEAM) {
-    ws[g.ws.t + a] = 0.0;
-    ws[g.ws.p + a] = 0.0;
-    if (!last) ws[g.ws.cb + a] = 0.0;
-  }
-  if (!last)
-    for (int a = tid; a < m; a += TEAM) ws[g.ws.k + a] = 0.0;
-  // homogeneous constraints: every domain is a subspace, h_i = 0 (the s_0 check reads h_0)
-  for (int a = tid; a < wi[SI_HROWS]; a += TEAM) ws[g.ws.H + a * (n + 1) + n] = 0.0;
-  if (!last)
-    for (int a = tid; a < m; a += TEAM) ws[g.ws.y + a] = 0.0;
-  for (int a = tid; a < nb; a += TEAM) {
-    double s0 = 0.0;
-    for (int l = 0; l < n; l++) s0 = fma(T[l * n + a], q[l], s0);
-    if (!last)
-      for (int l = 0; l < m; l++) s0 = fma(Y[l * n + a], r[l], s0);
-    ws[g.ws.qb + a] = s0;
-  }
-  for (int a = tid; a < mb; a += TEAM) {
-    double s0 = 0.0;
-    for (int l = 0; l < m; l++) s0 = fma(Z[l * m + a], r[l], s0);
-    ws[g.ws.rb + a] = s0;
-  }
-  tsync();
-  if (!last && tid == 0) {
-    const int kh = nb + mb, ldh = n + m;
-    const double *LT = ws + g.ws.LT;
-    double *lt = ws + g.ws.lt;
-    for (int a = 0; a < kh; a++) {
-      double s0 = (a < mb) ? ws[g.ws.rb + a] : ws[g.ws.qb + (a - mb)];  // order (v, z)
-      for (int l = 0; l < a; l++) s0 = fma(-LT[l * ldh + a], lt[l], s0);
-      lt[a] = s0 / LT[a * ldh + a];
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+    double *ws = stage_ws(g, s);
+    const int *wi = stage_wi(g, s);
+    const int ur = wi[SI_UR], nb = n - ur;
+    const bool last = i == P.N;
+    const int mb = last ? 0 : wi[SI_MBAR];
+    const double *T = ws + g.ws.UT + ur, *Y = ws + g.ws.Y, *Z = ws + g.ws.Z;
+    const double *q = g.qv + P.oqv + (size_t)i * n, *r = last ? nullptr : g.rv + P.orv + (size_t)i * m;
+    for (int a = tid; a < n; a += TEAM) {
+      ws[g.ws.t + a] = 0.0;
+      ws[g.ws.p + a] = 0.0;
+      if (!last) ws[g.ws.cb + a] = 0.0;
     }
-  }
-  (void)per_task;
+    if (!last)
+      for (int a = tid; a < m; a += TEAM) ws[g.ws.k + a] = 0.0;
+    // homogeneous constraints: every domain is a subspace, h_i = 0 (the s_0 check reads h_0)
+    for (int a = tid; a < wi[SI_HROWS]; a += TEAM) ws[g.ws.H + a * (n + 1) + n] = 0.0;
+    if (!last)
+      for (int a = tid; a < m; a += TEAM) ws[g.ws.y + a] = 0.0;
+    for (int a = tid; a < nb; a += TEAM) {
+      double s0 = 0.0;
+      for (int l = 0; l < n; l++) s0 = fma(T[l * n + a], q[l], s0);
+      if (!last)
+        for (int l = 0; l < m; l++) s0 = fma(Y[l * n + a], r[l], s0);
+      ws[g.ws.qb + a] = s0;
+    }
+    for (int a = tid; a < mb; a += TEAM) {
+      double s0 = 0.0;
+      for (int l = 0; l < m; l++) s0 = fma(Z[l * m + a], r[l], s0);
+      ws[g.ws.rb + a] = s0;
+    }
+    tsync();
+    if (!last && tid == 0) {
+      const int kh = nb + mb, ldh = n + m;
+      const double *LT = ws + g.ws.LT;
+      double *lt = ws + g.ws.lt;
+      for (int a = 0; a < kh; a++) {
+        double s0 = (a < mb) ? ws[g.ws.rb + a] : ws[g.ws.qb + (a - mb)];  // order (v, z)
+        for (int l = 0; l < a; l++) s0 = fma(-LT[l * ldh + a], lt[l], s0);
+        lt[a] = s0 / LT[a * ldh + a];
+      }
+    }
+    (void)per_task;
+  });
 }
 
 }  // namespace eclqr

@@ -360,60 +360,60 @@ static __device__ void riccati_task(const Group &g, int fin, int t, int per_task
 // diagonal), Phi = Abar + Bbar K (the closed-loop map of the affine chains), and
 // from [R_i | s_i], P_i = R_i'R_i and p_i = R_i's_i, which replace it.
 __global__ void k_riccati_finish(Group g, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  if (S.i >= P.N) return;
-  if (g.fp64 != nullptr && g.fp64[P.id] == 0) return;  // k_riccati_down_f32 stored this problem's factors
-  const int n = g.n, m = g.m, tid = team_rank();
-  double *ws = stage_ws(g, s);
-  const int *wi = stage_wi(g, s);
-  const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
-  const int ldr = n + m + 1;
-  double *sm = team_smem(per_task);
-  double *R = sm, *V = R + m * ldr, *Kt = V + n * (n + 1);
-  const double *Rv = ws + g.ws.Rv, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
-  for (int idx = tid; idx < mu * (nx + mu + 1); idx += TEAM) {
-    int r = idx / (nx + mu + 1), j = idx - r * (nx + mu + 1);
-    R[r * ldr + j] = Rv[r * ldr + j];
-  }
-  for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
-    int r = idx / (nx + 1), c = idx - r * (nx + 1);
-    V[r * (n + 1) + c] = ws[g.ws.P + r * (n + 1) + c];
-  }
-  tsync();
-  // K, k:  R_vv [K | k] = -[R_vz | o_v]
-  for (int c = tid; c <= nx; c += TEAM) {
-    for (int r = mu - 1; r >= 0; r--) {
-      double s0 = -R[r * ldr + mu + c];
-      for (int l = r + 1; l < mu; l++) s0 = fma(-R[r * ldr + l], Kt[l * (n + 1) + c], s0);
-      Kt[r * (n + 1) + c] = s0 / R[r * ldr + r];
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    if (S.i >= P.N) return;
+    if (g.fp64 != nullptr && g.fp64[P.id] == 0) return;  // k_riccati_down_f32 stored this problem's factors
+    const int n = g.n, m = g.m, tid = team_rank();
+    double *ws = stage_ws(g, s);
+    const int *wi = stage_wi(g, s);
+    const int nx = wi[SI_NBAR], mu = wi[SI_MBAR], n1 = stage_wi(g, s + 1)[SI_NBAR];
+    const int ldr = n + m + 1;
+    double *sm = team_smem(per_task);
+    double *R = sm, *V = R + m * ldr, *Kt = V + n * (n + 1);
+    const double *Rv = ws + g.ws.Rv, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
+    for (int idx = tid; idx < mu * (nx + mu + 1); idx += TEAM) {
+      int r = idx / (nx + mu + 1), j = idx - r * (nx + mu + 1);
+      R[r * ldr + j] = Rv[r * ldr + j];
     }
-  }
-  for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
-    int r = idx / (nx + 1), c = idx - r * (nx + 1);
-    double s0 = 0.0;
-    for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
-    if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
-  }
-  for (int idx = tid; idx < mu * mu; idx += TEAM) {
-    int r = idx / mu, j = idx - r * mu;
-    double sg = R[j * ldr + j] >= 0.0 ? 1.0 : -1.0;
-    ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * R[j * ldr + r] : 0.0;
-  }
-  tsync();
-  for (int idx = tid; idx < mu * (nx + 1); idx += TEAM) {
-    int r = idx / (nx + 1), c = idx - r * (nx + 1);
-    if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
-  }
-  for (int idx = tid; idx < n1 * nx; idx += TEAM) {
-    int r = idx / nx, c = idx - r * nx;
-    double s0 = Ab[r * n + c];
-    for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
-    ws[g.ws.Phi + r * n + c] = s0;
-  }
+    for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
+      int r = idx / (nx + 1), c = idx - r * (nx + 1);
+      V[r * (n + 1) + c] = ws[g.ws.P + r * (n + 1) + c];
+    }
+    tsync();
+    // K, k:  R_vv [K | k] = -[R_vz | o_v]
+    for (int c = tid; c <= nx; c += TEAM) {
+      for (int r = mu - 1; r >= 0; r--) {
+        double s0 = -R[r * ldr + mu + c];
+        for (int l = r + 1; l < mu; l++) s0 = fma(-R[r * ldr + l], Kt[l * (n + 1) + c], s0);
+        Kt[r * (n + 1) + c] = s0 / R[r * ldr + r];
+      }
+    }
+    for (int idx = tid; idx < nx * (nx + 1); idx += TEAM) {
+      int r = idx / (nx + 1), c = idx - r * (nx + 1);
+      double s0 = 0.0;
+      for (int l = 0; l <= r && l < nx; l++) s0 = fma(V[l * (n + 1) + r], V[l * (n + 1) + c], s0);
+      if (c < nx) ws[g.ws.P + r * n + c] = s0; else ws[g.ws.p + r] = s0;
+    }
+    for (int idx = tid; idx < mu * mu; idx += TEAM) {
+      int r = idx / mu, j = idx - r * mu;
+      double sg = R[j * ldr + j] >= 0.0 ? 1.0 : -1.0;
+      ws[g.ws.Lh + r * m + j] = (j <= r) ? sg * R[j * ldr + r] : 0.0;
+    }
+    tsync();
+    for (int idx = tid; idx < mu * (nx + 1); idx += TEAM) {
+      int r = idx / (nx + 1), c = idx - r * (nx + 1);
+      if (c < nx) ws[g.ws.K + r * n + c] = Kt[r * (n + 1) + c]; else ws[g.ws.k + r] = Kt[r * (n + 1) + c];
+    }
+    for (int idx = tid; idx < n1 * nx; idx += TEAM) {
+      int r = idx / nx, c = idx - r * nx;
+      double s0 = Ab[r * n + c];
+      for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], Kt[l * (n + 1) + c], s0);
+      ws[g.ws.Phi + r * n + c] = s0;
+    }
+  });
 }
 
 // ----------------------------------------------------------- affine chain scans
@@ -491,43 +491,43 @@ __device__ void aff_stage_map(const Group &g, int s, int mode, double *G, double
 // them (ws.gv; the same arithmetic as aff_stage_map): ROLL cbar + Bbar k,
 // CROLL rc + Bbar k', PLIN rq + K' rr + Phi' P_{i+1} rc.  NU reads pnu.
 __global__ void k_aff_prep(Group g, int mode, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  if (S.i >= P.N || mode == AFF_NU) return;
-  const int n = g.n, m = g.m, tid = team_rank();
-  double *ws = stage_ws(g, s);
-  const double *wn = stage_ws(g, s + 1);
-  const int *wi = stage_wi(g, s);
-  const int nx = wi[SI_NBAR], ny = stage_wi(g, s + 1)[SI_NBAR], mu = wi[SI_MBAR];
-  const double *Phi = ws + g.ws.Phi, *Bb = ws + g.ws.Bb;
-  double *gv = ws + g.ws.gv;
-  if (mode == AFF_ROLL || mode == AFF_CROLL) {
-    const double *kk = ws + (mode == AFF_ROLL ? g.ws.k : g.ws.dv);
-    const double *cc = ws + (mode == AFF_ROLL ? g.ws.cb : g.ws.rc);
-    for (int i = tid; i < ny; i += TEAM) {
-      double s0 = cc[i];
-      for (int l = 0; l < mu; l++) s0 = fma(Bb[i * m + l], kk[l], s0);
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    if (S.i >= P.N || mode == AFF_NU) return;
+    const int n = g.n, m = g.m, tid = team_rank();
+    double *ws = stage_ws(g, s);
+    const double *wn = stage_ws(g, s + 1);
+    const int *wi = stage_wi(g, s);
+    const int nx = wi[SI_NBAR], ny = stage_wi(g, s + 1)[SI_NBAR], mu = wi[SI_MBAR];
+    const double *Phi = ws + g.ws.Phi, *Bb = ws + g.ws.Bb;
+    double *gv = ws + g.ws.gv;
+    if (mode == AFF_ROLL || mode == AFF_CROLL) {
+      const double *kk = ws + (mode == AFF_ROLL ? g.ws.k : g.ws.dv);
+      const double *cc = ws + (mode == AFF_ROLL ? g.ws.cb : g.ws.rc);
+      for (int i = tid; i < ny; i += TEAM) {
+        double s0 = cc[i];
+        for (int l = 0; l < mu; l++) s0 = fma(Bb[i * m + l], kk[l], s0);
+        gv[i] = s0;
+      }
+      return;
+    }
+    double *tmp = team_smem(per_task);  // P_{i+1} rc (ny)
+    const double *K = ws + g.ws.K, *Pn = wn + g.ws.P, *rc = ws + g.ws.rc;
+    for (int b = tid; b < ny; b += TEAM) {
+      double s0 = 0.0;
+      for (int l = 0; l < ny; l++) s0 = fma(Pn[b * n + l], rc[l], s0);
+      tmp[b] = s0;
+    }
+    tsync();
+    for (int i = tid; i < nx; i += TEAM) {
+      double s0 = ws[g.ws.rq + i];
+      for (int l = 0; l < mu; l++) s0 = fma(K[l * n + i], ws[g.ws.rr + l], s0);
+      for (int b = 0; b < ny; b++) s0 = fma(Phi[b * n + i], tmp[b], s0);
       gv[i] = s0;
     }
-    return;
-  }
-  double *tmp = team_smem(per_task);  // P_{i+1} rc (ny)
-  const double *K = ws + g.ws.K, *Pn = wn + g.ws.P, *rc = ws + g.ws.rc;
-  for (int b = tid; b < ny; b += TEAM) {
-    double s0 = 0.0;
-    for (int l = 0; l < ny; l++) s0 = fma(Pn[b * n + l], rc[l], s0);
-    tmp[b] = s0;
-  }
-  tsync();
-  for (int i = tid; i < nx; i += TEAM) {
-    double s0 = ws[g.ws.rq + i];
-    for (int l = 0; l < mu; l++) s0 = fma(K[l * n + i], ws[g.ws.rr + l], s0);
-    for (int b = 0; b < ny; b++) s0 = fma(Phi[b * n + i], tmp[b], s0);
-    gv[i] = s0;
-  }
+  });
 }
 
 // chunk aggregates; also the boundary value slot (forward: slot 0 of the
@@ -822,37 +822,37 @@ __global__ void k_solve_init(Group g, const double *s0) {
 // pass 0: v_i = K z + k, pi_i = P z + p.  correction passes: dv = K dz + k', dpi = P dz + p',
 // then z += dz, v += dv, pi += dpi.
 __global__ void k_post_roll(Group g, int corr) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, m = g.m, tid = team_rank();
-  double *ws = stage_ws(g, s);
-  const int *wi = stage_wi(g, s);
-  const int nx = wi[SI_NBAR], mu = (S.i < P.N) ? wi[SI_MBAR] : 0;
-  const double *zz = ws + (corr ? g.ws.dz : g.ws.z);
-  const double *kk = ws + (corr ? g.ws.dv : g.ws.k);
-  const double *pp = ws + (corr ? g.ws.pp : g.ws.p);
-  // v (or dv) -- computed into registers of the lanes then written
-  double myv = 0.0, mypi = 0.0;
-  const int r = tid;
-  if (r < mu) {
-    myv = kk[r];
-    for (int l = 0; l < nx; l++) myv = fma(ws[g.ws.K + r * n + l], zz[l], myv);
-  }
-  if (r < nx) {
-    mypi = pp[r];
-    for (int l = 0; l < nx; l++) mypi = fma(ws[g.ws.P + r * n + l], zz[l], mypi);
-  }
-  tsync();
-  if (!corr) {
-    if (r < m) ws[g.ws.v + r] = (r < mu) ? myv : 0.0;
-    if (r < n) ws[g.ws.pi + r] = (r < nx) ? mypi : 0.0;
-  } else {
-    if (r < mu) ws[g.ws.v + r] += myv;
-    if (r < nx) { ws[g.ws.pi + r] += mypi; ws[g.ws.z + r] += zz[r]; }
-  }
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank();
+    double *ws = stage_ws(g, s);
+    const int *wi = stage_wi(g, s);
+    const int nx = wi[SI_NBAR], mu = (S.i < P.N) ? wi[SI_MBAR] : 0;
+    const double *zz = ws + (corr ? g.ws.dz : g.ws.z);
+    const double *kk = ws + (corr ? g.ws.dv : g.ws.k);
+    const double *pp = ws + (corr ? g.ws.pp : g.ws.p);
+    // v (or dv) -- computed into registers of the lanes then written
+    double myv = 0.0, mypi = 0.0;
+    const int r = tid;
+    if (r < mu) {
+      myv = kk[r];
+      for (int l = 0; l < nx; l++) myv = fma(ws[g.ws.K + r * n + l], zz[l], myv);
+    }
+    if (r < nx) {
+      mypi = pp[r];
+      for (int l = 0; l < nx; l++) mypi = fma(ws[g.ws.P + r * n + l], zz[l], mypi);
+    }
+    tsync();
+    if (!corr) {
+      if (r < m) ws[g.ws.v + r] = (r < mu) ? myv : 0.0;
+      if (r < n) ws[g.ws.pi + r] = (r < nx) ? mypi : 0.0;
+    } else {
+      if (r < mu) ws[g.ws.v + r] += myv;
+      if (r < nx) { ws[g.ws.pi + r] += mypi; ws[g.ws.z + r] += zz[r]; }
+    }
+  });
 }
 
 // Residual of the reduced KKT system, evaluated through the original data.
@@ -864,159 +864,159 @@ __global__ void k_post_roll(Group g, int corr) {
 // ill-conditioned |Y| is large, and that cancellation would set the accuracy
 // of the costates and so of the multipliers.  Per task: 3n + 2m doubles.
 __global__ void k_resid(Group g, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
-  double *ws = stage_ws(g, s);
-  const int *wi = stage_wi(g, s);
-  const bool last = i == P.N;
-  const double *wn = last ? ws : stage_ws(g, s + 1);
-  const int nx = wi[SI_NBAR], mu = last ? 0 : wi[SI_MBAR], ny = last ? 0 : stage_wi(g, s + 1)[SI_NBAR];
-  const int ur = wi[SI_UR], ur1 = last ? 0 : stage_wi(g, s + 1)[SI_UR];
-  const double *z = ws + g.ws.z, *v = ws + g.ws.v, *pi = ws + g.ws.pi, *pin = wn + g.ws.pi, *zn = wn + g.ws.z;
-  const double *T = ws + g.ws.UT + ur, *Tn = wn + g.ws.UT + ur1;
-  const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
-  double *sm = team_smem(per_task);
-  double *xs = sm, *us = xs + n, *lh = us + m, *ga = lh + n, *gb = ga + n;
-  for (int a = tid; a < n; a += TEAM) {
-    double s0 = ws[g.ws.t + a];
-    for (int j = 0; j < nx; j++) s0 = fma(T[a * n + j], z[j], s0);
-    xs[a] = s0;
-  }
-  if (!last) {
-    for (int a = tid; a < m; a += TEAM) {
-      double s0 = ws[g.ws.y + a];
-      for (int j = 0; j < nx; j++) s0 = fma(Y[a * n + j], z[j], s0);
-      for (int j = 0; j < mu; j++) s0 = fma(Z[a * m + j], v[j], s0);
-      us[a] = s0;
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+    double *ws = stage_ws(g, s);
+    const int *wi = stage_wi(g, s);
+    const bool last = i == P.N;
+    const double *wn = last ? ws : stage_ws(g, s + 1);
+    const int nx = wi[SI_NBAR], mu = last ? 0 : wi[SI_MBAR], ny = last ? 0 : stage_wi(g, s + 1)[SI_NBAR];
+    const int ur = wi[SI_UR], ur1 = last ? 0 : stage_wi(g, s + 1)[SI_UR];
+    const double *z = ws + g.ws.z, *v = ws + g.ws.v, *pi = ws + g.ws.pi, *pin = wn + g.ws.pi, *zn = wn + g.ws.z;
+    const double *T = ws + g.ws.UT + ur, *Tn = wn + g.ws.UT + ur1;
+    const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
+    double *sm = team_smem(per_task);
+    double *xs = sm, *us = xs + n, *lh = us + m, *ga = lh + n, *gb = ga + n;
+    for (int a = tid; a < n; a += TEAM) {
+      double s0 = ws[g.ws.t + a];
+      for (int j = 0; j < nx; j++) s0 = fma(T[a * n + j], z[j], s0);
+      xs[a] = s0;
     }
-    for (int l = tid; l < n; l += TEAM) {
-      double s0 = 0.0;
-      for (int j = 0; j < ny; j++) s0 = fma(Tn[l * n + j], pin[j], s0);
-      lh[l] = s0;                                               // T_{i+1} pi_{i+1}
-    }
-  }
-  tsync();
-  const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
-  const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
-  const double *Mm = g.M + P.oM + (size_t)i * n * m, *R = g.R + P.oR + (size_t)i * m * m;
-  const double *rv = g.rv + P.orv + (size_t)i * m;
-  for (int a = tid; a < n; a += TEAM) {
-    double s0 = q[a];
-    for (int j = 0; j < n; j++) s0 = fma(Q[a * n + j], xs[j], s0);
     if (!last) {
-      for (int j = 0; j < m; j++) s0 = fma(Mm[a * m + j], us[j], s0);
-      for (int l = 0; l < n; l++) s0 = fma(A[l * n + a], lh[l], s0);
+      for (int a = tid; a < m; a += TEAM) {
+        double s0 = ws[g.ws.y + a];
+        for (int j = 0; j < nx; j++) s0 = fma(Y[a * n + j], z[j], s0);
+        for (int j = 0; j < mu; j++) s0 = fma(Z[a * m + j], v[j], s0);
+        us[a] = s0;
+      }
+      for (int l = tid; l < n; l += TEAM) {
+        double s0 = 0.0;
+        for (int j = 0; j < ny; j++) s0 = fma(Tn[l * n + j], pin[j], s0);
+        lh[l] = s0;                                               // T_{i+1} pi_{i+1}
+      }
     }
-    ga[a] = s0;
-  }
-  if (!last)
-    for (int a = tid; a < m; a += TEAM) {
-      double s0 = rv[a];
-      for (int j = 0; j < n; j++) s0 = fma(Mm[j * m + a], xs[j], s0);
-      for (int j = 0; j < m; j++) s0 = fma(R[a * m + j], us[j], s0);
-      for (int l = 0; l < n; l++) s0 = fma(B[l * m + a], lh[l], s0);
-      gb[a] = s0;
+    tsync();
+    const double *Q = g.Q + P.oQ + (size_t)i * n * n, *q = g.qv + P.oqv + (size_t)i * n;
+    const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
+    const double *Mm = g.M + P.oM + (size_t)i * n * m, *R = g.R + P.oR + (size_t)i * m * m;
+    const double *rv = g.rv + P.orv + (size_t)i * m;
+    for (int a = tid; a < n; a += TEAM) {
+      double s0 = q[a];
+      for (int j = 0; j < n; j++) s0 = fma(Q[a * n + j], xs[j], s0);
+      if (!last) {
+        for (int j = 0; j < m; j++) s0 = fma(Mm[a * m + j], us[j], s0);
+        for (int l = 0; l < n; l++) s0 = fma(A[l * n + a], lh[l], s0);
+      }
+      ga[a] = s0;
     }
-  tsync();
-  for (int r = tid; r < nx; r += TEAM) {
-    double s0 = -pi[r];
-    for (int l = 0; l < n; l++) s0 = fma(T[l * n + r], ga[l], s0);
     if (!last)
-      for (int l = 0; l < m; l++) s0 = fma(Y[l * n + r], gb[l], s0);
-    ws[g.ws.rq + r] = s0;
-  }
-  for (int r = tid; r < mu; r += TEAM) {
-    double s0 = 0.0;
-    for (int l = 0; l < m; l++) s0 = fma(Z[l * m + r], gb[l], s0);
-    ws[g.ws.rr + r] = s0;
-  }
-  for (int r = tid; r < ny; r += TEAM) {
-    double s0 = ws[g.ws.cb + r] - zn[r];
-    for (int l = 0; l < nx; l++) s0 = fma(Ab[r * n + l], z[l], s0);
-    for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], v[l], s0);
-    ws[g.ws.rc + r] = s0;
-  }
+      for (int a = tid; a < m; a += TEAM) {
+        double s0 = rv[a];
+        for (int j = 0; j < n; j++) s0 = fma(Mm[j * m + a], xs[j], s0);
+        for (int j = 0; j < m; j++) s0 = fma(R[a * m + j], us[j], s0);
+        for (int l = 0; l < n; l++) s0 = fma(B[l * m + a], lh[l], s0);
+        gb[a] = s0;
+      }
+    tsync();
+    for (int r = tid; r < nx; r += TEAM) {
+      double s0 = -pi[r];
+      for (int l = 0; l < n; l++) s0 = fma(T[l * n + r], ga[l], s0);
+      if (!last)
+        for (int l = 0; l < m; l++) s0 = fma(Y[l * n + r], gb[l], s0);
+      ws[g.ws.rq + r] = s0;
+    }
+    for (int r = tid; r < mu; r += TEAM) {
+      double s0 = 0.0;
+      for (int l = 0; l < m; l++) s0 = fma(Z[l * m + r], gb[l], s0);
+      ws[g.ws.rr + r] = s0;
+    }
+    for (int r = tid; r < ny; r += TEAM) {
+      double s0 = ws[g.ws.cb + r] - zn[r];
+      for (int l = 0; l < nx; l++) s0 = fma(Ab[r * n + l], z[l], s0);
+      for (int l = 0; l < mu; l++) s0 = fma(Bb[r * m + l], v[l], s0);
+      ws[g.ws.rc + r] = s0;
+    }
+  });
 }
 
 // Correction controls of a refinement pass: with w = P_{i+1} rc_i + p'_{i+1},
 // k'_i = -H_uu^{-1} (rr_i + Bbar' w) through the Cholesky factor of H_uu (-> dv).
 __global__ void k_pcorr(Group g, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  if (S.i >= P.N) return;
-  const int n = g.n, m = g.m, tid = team_rank();
-  double *ws = stage_ws(g, s);
-  const double *wn = stage_ws(g, s + 1);
-  const int mu = stage_wi(g, s)[SI_MBAR], ny = stage_wi(g, s + 1)[SI_NBAR];
-  double *sm = team_smem(per_task);
-  double *w = sm, *hu = sm + n;
-  const double *Pn = wn + g.ws.P, *ppn = wn + g.ws.pp, *rc = ws + g.ws.rc, *Bb = ws + g.ws.Bb;
-  for (int b = tid; b < ny; b += TEAM) {
-    double s0 = ppn[b];
-    for (int l = 0; l < ny; l++) s0 = fma(Pn[b * n + l], rc[l], s0);
-    w[b] = s0;
-  }
-  tsync();
-  for (int a = tid; a < mu; a += TEAM) {
-    double s0 = ws[g.ws.rr + a];
-    for (int b = 0; b < ny; b++) s0 = fma(Bb[b * m + a], w[b], s0);
-    hu[a] = s0;
-  }
-  tsync();
-  if (tid == 0) {
-    const double *Lh = ws + g.ws.Lh;  // lower triangular, ld m
-    for (int a = 0; a < mu; a++) {
-      double s0 = hu[a];
-      for (int l = 0; l < a; l++) s0 = fma(-Lh[a * m + l], hu[l], s0);
-      hu[a] = s0 / Lh[a * m + a];
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    if (S.i >= P.N) return;
+    const int n = g.n, m = g.m, tid = team_rank();
+    double *ws = stage_ws(g, s);
+    const double *wn = stage_ws(g, s + 1);
+    const int mu = stage_wi(g, s)[SI_MBAR], ny = stage_wi(g, s + 1)[SI_NBAR];
+    double *sm = team_smem(per_task);
+    double *w = sm, *hu = sm + n;
+    const double *Pn = wn + g.ws.P, *ppn = wn + g.ws.pp, *rc = ws + g.ws.rc, *Bb = ws + g.ws.Bb;
+    for (int b = tid; b < ny; b += TEAM) {
+      double s0 = ppn[b];
+      for (int l = 0; l < ny; l++) s0 = fma(Pn[b * n + l], rc[l], s0);
+      w[b] = s0;
     }
-    for (int a = mu - 1; a >= 0; a--) {
-      double s0 = hu[a];
-      for (int l = a + 1; l < mu; l++) s0 = fma(-Lh[l * m + a], hu[l], s0);
-      hu[a] = s0 / Lh[a * m + a];
+    tsync();
+    for (int a = tid; a < mu; a += TEAM) {
+      double s0 = ws[g.ws.rr + a];
+      for (int b = 0; b < ny; b++) s0 = fma(Bb[b * m + a], w[b], s0);
+      hu[a] = s0;
     }
-    for (int a = 0; a < mu; a++) ws[g.ws.dv + a] = -hu[a];
-  }
+    tsync();
+    if (tid == 0) {
+      const double *Lh = ws + g.ws.Lh;  // lower triangular, ld m
+      for (int a = 0; a < mu; a++) {
+        double s0 = hu[a];
+        for (int l = 0; l < a; l++) s0 = fma(-Lh[a * m + l], hu[l], s0);
+        hu[a] = s0 / Lh[a * m + a];
+      }
+      for (int a = mu - 1; a >= 0; a--) {
+        double s0 = hu[a];
+        for (int l = a + 1; l < mu; l++) s0 = fma(-Lh[l * m + a], hu[l], s0);
+        hu[a] = s0 / Lh[a * m + a];
+      }
+      for (int a = 0; a < mu; a++) ws[g.ws.dv + a] = -hu[a];
+    }
+  });
 }
 
 // x_i = T z + t, u_i = Y z + Z v + y (eq. recovery-maps)
 __global__ void k_recover(Group g, double *x, double *u) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, m = g.m, tid = team_rank();
-  const double *ws = stage_ws(g, s);
-  const int *wi = stage_wi(g, s);
-  const int ur = wi[SI_UR], nb = n - ur;
-  const double *T = ws + g.ws.UT + ur, *z = ws + g.ws.z;
-  bool bad = false;
-  for (int a = tid; a < n; a += TEAM) {
-    double v = ws[g.ws.t + a];
-    for (int j = 0; j < nb; j++) v = fma(T[a * n + j], z[j], v);
-    x[P.ox + (size_t)S.i * n + a] = v;
-    bad = bad || !isfinite(v);
-  }
-  if (S.i < P.N) {
-    const int mb = wi[SI_MBAR];
-    const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *vv = ws + g.ws.v;
-    for (int a = tid; a < m; a += TEAM) {
-      double v = ws[g.ws.y + a];
-      for (int j = 0; j < nb; j++) v = fma(Y[a * n + j], z[j], v);
-      for (int j = 0; j < mb; j++) v = fma(Z[a * m + j], vv[j], v);
-      u[P.ou + (size_t)S.i * m + a] = v;
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank();
+    const double *ws = stage_ws(g, s);
+    const int *wi = stage_wi(g, s);
+    const int ur = wi[SI_UR], nb = n - ur;
+    const double *T = ws + g.ws.UT + ur, *z = ws + g.ws.z;
+    bool bad = false;
+    for (int a = tid; a < n; a += TEAM) {
+      double v = ws[g.ws.t + a];
+      for (int j = 0; j < nb; j++) v = fma(T[a * n + j], z[j], v);
+      x[P.ox + (size_t)S.i * n + a] = v;
       bad = bad || !isfinite(v);
     }
-  }
-  if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
+    if (S.i < P.N) {
+      const int mb = wi[SI_MBAR];
+      const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *vv = ws + g.ws.v;
+      for (int a = tid; a < m; a += TEAM) {
+        double v = ws[g.ws.y + a];
+        for (int j = 0; j < nb; j++) v = fma(Y[a * n + j], z[j], v);
+        for (int j = 0; j < mb; j++) v = fma(Z[a * m + j], vv[j], v);
+        u[P.ou + (size_t)S.i * m + a] = v;
+        bad = bad || !isfinite(v);
+      }
+    }
+    if (__syncthreads_or(bad) && tid == 0) set_status(g, S.prob, ST_NONFINITE);
+  });
 }
 
 }  // namespace eclqr

@@ -349,292 +349,292 @@ __global__ void k_primal_down(Group g, int fin, int per_task) {
 // QR of H_i^T: Q = [U_i | T_i], U_i spans range(H_i^T), T_i = orthonormal basis
 // of null(H_i); t_i = min-norm solution of H_i t = -h_i; S_i = T_i^T.
 __global__ void k_param(Group g, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, tid = team_rank();
-  double *ws = stage_ws(g, s);
-  int *wi = stage_wi(g, s);
-  const int r = wi[SI_HROWS];
-  double *sm = team_smem(per_task);
-  double *Hs = sm, *Wt = Hs + n * (n + 1), *Qf = Wt + n * n, *hb = Qf + n * n, *X = hb + n;
-  double *scr = X + n;
-  int *perm = (int *)(scr + 4 * n);
-  const double *H = ws + g.ws.H;
-  for (int idx = tid; idx < r * (n + 1); idx += TEAM) Hs[idx] = H[idx];
-  for (int i = tid; i < r; i += TEAM) hb[i] = H[i * (n + 1) + n];
-  tsync();
-  const int rank = wtqr(Hs, n + 1, r, n, g.tau_rank, Wt, (r > 0 ? r : 1), Qf, n, perm, scr);
-  double *Ys = scr + 2 * n;  // rank x 1
-  wtqr_solve(Wt, (r > 0 ? r : 1), Qf, n, perm, r, n, rank, hb, 1, 1, X, 1, Ys, 1);
-  double *UT = ws + g.ws.UT, *tt = ws + g.ws.t;
-  // T = I and t = 0 exactly (compared as bit patterns, on the integer pipe; a zero of
-  // either sign counts as zero): the stage elimination then skips its products with T_i,
-  // whose results are the factors themselves
-  bool eye = true;
-  for (int idx = tid; idx < n * n; idx += TEAM) {
-    UT[idx] = Qf[idx];
-    const long long b = __double_as_longlong(Qf[idx]);
-    eye = eye && ((idx / n) * (n + 1) == idx ? b == __double_as_longlong(1.0) : (b << 1) == 0);
-  }
-  for (int i = tid; i < n; i += TEAM) {
-    tt[i] = X[i];
-    eye = eye && (__double_as_longlong(X[i]) << 1) == 0;
-  }
-  eye = __syncthreads_and(eye) != 0;
-  if (tid == 0) { wi[SI_UR] = rank; wi[SI_NBAR] = n - rank; wi[SI_TEYE] = (rank == 0 && eye) ? 1 : 0; }
-  tsync();
-  if (S.i == P.N) {
-    // terminal cost (eq. terminal-cost-data): Qbar_N = T' Q_N T, qbar_N = T'(Q_N t + q_N)
-    const int nb = n - rank;
-    const double *QN = g.Q + P.oQ + (size_t)P.N * n * n, *qN = g.qv + P.oqv + (size_t)P.N * n;
-    double *QT = Wt;  // n x nb (reuse)
-    double *T = Qf + rank;  // columns rank.. of Qf, ld n
-    wgemm<false, false>(n, nb, n, 1.0, QN, n, T, n, 0.0, QT, n);
-    wgemm<true, false>(nb, nb, n, 1.0, T, n, QT, n, 0.0, ws + g.ws.Qb, n);
-    for (int l = tid; l < n; l += TEAM) {
-      double s0 = qN[l];
-      for (int j = 0; j < n; j++) s0 = fma(QN[l * n + j], X[j], s0);
-      Hs[l] = s0;
-    }
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, tid = team_rank();
+    double *ws = stage_ws(g, s);
+    int *wi = stage_wi(g, s);
+    const int r = wi[SI_HROWS];
+    double *sm = team_smem(per_task);
+    double *Hs = sm, *Wt = Hs + n * (n + 1), *Qf = Wt + n * n, *hb = Qf + n * n, *X = hb + n;
+    double *scr = X + n;
+    int *perm = (int *)(scr + 4 * n);
+    const double *H = ws + g.ws.H;
+    for (int idx = tid; idx < r * (n + 1); idx += TEAM) Hs[idx] = H[idx];
+    for (int i = tid; i < r; i += TEAM) hb[i] = H[i * (n + 1) + n];
     tsync();
-    wgemm<true, false>(nb, 1, n, 1.0, T, n, Hs, 1, 0.0, ws + g.ws.qb, 1);
-  }
+    const int rank = wtqr(Hs, n + 1, r, n, g.tau_rank, Wt, (r > 0 ? r : 1), Qf, n, perm, scr);
+    double *Ys = scr + 2 * n;  // rank x 1
+    wtqr_solve(Wt, (r > 0 ? r : 1), Qf, n, perm, r, n, rank, hb, 1, 1, X, 1, Ys, 1);
+    double *UT = ws + g.ws.UT, *tt = ws + g.ws.t;
+    // T = I and t = 0 exactly (compared as bit patterns, on the integer pipe; a zero of
+    // either sign counts as zero): the stage elimination then skips its products with T_i,
+    // whose results are the factors themselves
+    bool eye = true;
+    for (int idx = tid; idx < n * n; idx += TEAM) {
+      UT[idx] = Qf[idx];
+      const long long b = __double_as_longlong(Qf[idx]);
+      eye = eye && ((idx / n) * (n + 1) == idx ? b == __double_as_longlong(1.0) : (b << 1) == 0);
+    }
+    for (int i = tid; i < n; i += TEAM) {
+      tt[i] = X[i];
+      eye = eye && (__double_as_longlong(X[i]) << 1) == 0;
+    }
+    eye = __syncthreads_and(eye) != 0;
+    if (tid == 0) { wi[SI_UR] = rank; wi[SI_NBAR] = n - rank; wi[SI_TEYE] = (rank == 0 && eye) ? 1 : 0; }
+    tsync();
+    if (S.i == P.N) {
+      // terminal cost (eq. terminal-cost-data): Qbar_N = T' Q_N T, qbar_N = T'(Q_N t + q_N)
+      const int nb = n - rank;
+      const double *QN = g.Q + P.oQ + (size_t)P.N * n * n, *qN = g.qv + P.oqv + (size_t)P.N * n;
+      double *QT = Wt;  // n x nb (reuse)
+      double *T = Qf + rank;  // columns rank.. of Qf, ld n
+      wgemm<false, false>(n, nb, n, 1.0, QN, n, T, n, 0.0, QT, n);
+      wgemm<true, false>(nb, nb, n, 1.0, T, n, QT, n, 0.0, ws + g.ws.Qb, n);
+      for (int l = tid; l < n; l += TEAM) {
+        double s0 = qN[l];
+        for (int j = 0; j < n; j++) s0 = fma(QN[l * n + j], X[j], s0);
+        Hs[l] = s0;
+      }
+      tsync();
+      wgemm<true, false>(nb, 1, n, 1.0, T, n, Hs, 1, 0.0, ws + g.ws.qb, 1);
+    }
+  });
 }
 
 // ----------------------------------------------------------- stage elimination (Sec. 5)
 __global__ void k_elim(Group g, int per_task) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  if (S.i >= P.N) return;
-  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
-  double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);
-  int *wi = stage_wi(g, s), *win = stage_wi(g, s + 1);
-  const int ur = wi[SI_UR], nb = n - ur, ur1 = win[SI_UR], nn = n - ur1, r1 = win[SI_HROWS];
-  const int rows = S.p + r1;
-  // T_i = I, t_i = 0 (te) and T_{i+1} = I, t_{i+1} = 0 (tne): a product with T is then its other
-  // factor, bit for bit up to the sign of zeros, and is copied instead of computed
-  const bool te = wi[SI_TEYE] != 0, tne = win[SI_TEYE] != 0;
-  const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
-  const double *c = g.c + P.oc + (size_t)i * n;
-  const double *Q = g.Q + P.oQ + (size_t)i * n * n, *Mm = g.M + P.oM + (size_t)i * n * m;
-  const double *R = g.R + P.oR + (size_t)i * m * m;
-  const double *q = g.qv + P.oqv + (size_t)i * n, *r = g.rv + P.orv + (size_t)i * m;
-  const double *T = ws + g.ws.UT + ur, *t = ws + g.ws.t;        // ld n
-  const double *Tn = wn + g.ws.UT + ur1, *tn = wn + g.ws.t;     // ld n
-  const double *Hn = wn + g.ws.H;                                 // ld n + 1
-  double *sm = team_smem(per_task);
-  const int rmax = g.pmax + n;
-  // live through the stage
-  double *AT = sm;                       // n x n (ld n)
-  double *Qm = AT + n * n;               // m x m: Q of Gamma' (Z = its last columns)
-  double *Yw = Qm + m * m;               // m x n  (ld n): Y
-  double *vec = Yw + n * m;              // 12 n + 8 m
-  double *Atc = vec, *cv = Atc + n, *Qtq = cv + n, *qz = Qtq + n, *rz = qz + n, *Ry = rz + m;
-  double *ys = Ry + m, *scr = ys + m;    // scratch >= 2n + 2 rows
-  double *U = vec + 12 * n + 8 * m + 2 * rmax + 16;  // the phases' region
-  // Lemma 4's solve
-  double *Hs = U;                        // n x (n+1)
-  double *Gm = Hs + n * (n + 1);         // rmax x m
-  double *Rh = Gm + rmax * m;            // rmax x (n+1)
-  double *Wt = Rh + rmax * (n + 1);      // m x rmax
-  double *Sol = Wt + m * rmax;           // m x (n+1)
-  double *X1 = Sol + m * (n + 1);        // m x (n+1) scratch for the min-norm solve
-  // the substitution products
-  double *QT = U;                        // n x n
-  double *X2 = QT + n * n;               // n x n  scratch
-  double *Mz = X2 + n * n;               // n x m
-  double *RY = Mz + n * m;               // m x n
-  double *BZ = RY + n * m;               // n x m
-  double *RZ = BZ + n * m;               // m x m
-  int *perm = (int *)(scr + 4 * n + 2 * m + 2 * rmax);
-  // A T, A t + c
-  if (te) {
-    for (int idx = tid; idx < n * n; idx += TEAM) AT[idx] = A[idx];
-    for (int l = tid; l < n; l += TEAM) Atc[l] = c[l];
-  } else {
-    wgemm<false, false>(n, nb, n, 1.0, A, n, T, n, 0.0, AT, n);
-    for (int l = tid; l < n; l += TEAM) {
-      double s0 = c[l];
-      for (int j = 0; j < n; j++) s0 = fma(A[l * n + j], t[j], s0);
-      Atc[l] = s0;
-    }
-  }
-  for (int idx = tid; idx < r1 * (n + 1); idx += TEAM) Hs[idx] = Hn[idx];
-  tsync();
-  // Gamma = [D; Hn B],  [Phi | gamma] = [C T | C t + d; Hn A T | Hn (A t + c) + hn]
-  for (int idx = tid; idx < S.p * m; idx += TEAM) {
-    int a = idx / m, j = idx - a * m;
-    Gm[a * m + j] = g.D[P.oD + (size_t)(S.prow + a) * m + j];
-  }
-  wgemm<false, false>(r1, m, n, 1.0, Hs, n + 1, B, m, 0.0, Gm + S.p * m, m);
-  for (int idx = tid; idx < S.p * (nb + 1); idx += TEAM) {
-    int a = idx / (nb + 1), j = idx - a * (nb + 1);
-    const double *Cr = g.C + P.oC + (size_t)(S.prow + a) * n;
-    double s0 = 0.0;
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    if (S.i >= P.N) return;
+    const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+    double *ws = stage_ws(g, s), *wn = stage_ws(g, s + 1);
+    int *wi = stage_wi(g, s), *win = stage_wi(g, s + 1);
+    const int ur = wi[SI_UR], nb = n - ur, ur1 = win[SI_UR], nn = n - ur1, r1 = win[SI_HROWS];
+    const int rows = S.p + r1;
+    // T_i = I, t_i = 0 (te) and T_{i+1} = I, t_{i+1} = 0 (tne): a product with T is then its other
+    // factor, bit for bit up to the sign of zeros, and is copied instead of computed
+    const bool te = wi[SI_TEYE] != 0, tne = win[SI_TEYE] != 0;
+    const double *A = g.A + P.oA + (size_t)i * n * n, *B = g.B + P.oB + (size_t)i * n * m;
+    const double *c = g.c + P.oc + (size_t)i * n;
+    const double *Q = g.Q + P.oQ + (size_t)i * n * n, *Mm = g.M + P.oM + (size_t)i * n * m;
+    const double *R = g.R + P.oR + (size_t)i * m * m;
+    const double *q = g.qv + P.oqv + (size_t)i * n, *r = g.rv + P.orv + (size_t)i * m;
+    const double *T = ws + g.ws.UT + ur, *t = ws + g.ws.t;        // ld n
+    const double *Tn = wn + g.ws.UT + ur1, *tn = wn + g.ws.t;     // ld n
+    const double *Hn = wn + g.ws.H;                                 // ld n + 1
+    double *sm = team_smem(per_task);
+    const int rmax = g.pmax + n;
+    // live through the stage
+    double *AT = sm;                       // n x n (ld n)
+    double *Qm = AT + n * n;               // m x m: Q of Gamma' (Z = its last columns)
+    double *Yw = Qm + m * m;               // m x n  (ld n): Y
+    double *vec = Yw + n * m;              // 12 n + 8 m
+    double *Atc = vec, *cv = Atc + n, *Qtq = cv + n, *qz = Qtq + n, *rz = qz + n, *Ry = rz + m;
+    double *ys = Ry + m, *scr = ys + m;    // scratch >= 2n + 2 rows
+    double *U = vec + 12 * n + 8 * m + 2 * rmax + 16;  // the phases' region
+    // Lemma 4's solve
+    double *Hs = U;                        // n x (n+1)
+    double *Gm = Hs + n * (n + 1);         // rmax x m
+    double *Rh = Gm + rmax * m;            // rmax x (n+1)
+    double *Wt = Rh + rmax * (n + 1);      // m x rmax
+    double *Sol = Wt + m * rmax;           // m x (n+1)
+    double *X1 = Sol + m * (n + 1);        // m x (n+1) scratch for the min-norm solve
+    // the substitution products
+    double *QT = U;                        // n x n
+    double *X2 = QT + n * n;               // n x n  scratch
+    double *Mz = X2 + n * n;               // n x m
+    double *RY = Mz + n * m;               // m x n
+    double *BZ = RY + n * m;               // n x m
+    double *RZ = BZ + n * m;               // m x m
+    int *perm = (int *)(scr + 4 * n + 2 * m + 2 * rmax);
+    // A T, A t + c
     if (te) {
-      s0 = (j < nb) ? Cr[j] : g.d[P.od + S.prow + a];
-    } else if (j < nb) {
-      for (int l = 0; l < n; l++) s0 = fma(Cr[l], T[l * n + j], s0);
+      for (int idx = tid; idx < n * n; idx += TEAM) AT[idx] = A[idx];
+      for (int l = tid; l < n; l += TEAM) Atc[l] = c[l];
     } else {
-      s0 = g.d[P.od + S.prow + a];
-      for (int l = 0; l < n; l++) s0 = fma(Cr[l], t[l], s0);
+      wgemm<false, false>(n, nb, n, 1.0, A, n, T, n, 0.0, AT, n);
+      for (int l = tid; l < n; l += TEAM) {
+        double s0 = c[l];
+        for (int j = 0; j < n; j++) s0 = fma(A[l * n + j], t[j], s0);
+        Atc[l] = s0;
+      }
     }
-    Rh[a * (nb + 1) + j] = s0;
-  }
-  for (int idx = tid; idx < r1 * (nb + 1); idx += TEAM) {
-    int a = idx / (nb + 1), j = idx - a * (nb + 1);
-    const double *hr = Hs + a * (n + 1);
-    double s0 = 0.0;
-    if (j < nb) {
-      for (int l = 0; l < n; l++) s0 = fma(hr[l], AT[l * n + j], s0);
-    } else {
-      s0 = hr[n];
-      for (int l = 0; l < n; l++) s0 = fma(hr[l], Atc[l], s0);
-    }
-    Rh[(S.p + a) * (nb + 1) + j] = s0;
-  }
-  tsync();
-  // Lemma 4: Z = null(Gamma), [Y | y] = -Gamma^- [Phi | gamma] (min norm)
-  // the small form only: this kernel runs many CTAs to an SM, and the large form's
-  // registers and static scratch would cost it occupancy
-  const int rank = wtqr_small(Gm, m, rows, m, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qm, m, perm, scr);
-  const double rs = wtqr_solve(Wt, (rows > 0 ? rows : 1), Qm, m, perm, rows, m, rank, Rh, nb + 1, nb + 1,
-                               Sol, nb + 1, X1, nb + 1);
-  if (tid == 0 && rs > g.tau_inc) set_status(g, S.prob, ST_RANK_INCONSISTENT);
-  const int mb = m - rank;
-  const double *Z = Qm + rank;  // ld m
-  // Y (m x nb, ld n), y (m)
-  for (int idx = tid; idx < m * nb; idx += TEAM) {
-    int a = idx / nb, j = idx - a * nb;
-    Yw[a * n + j] = Sol[a * (nb + 1) + j];
-  }
-  for (int a = tid; a < m; a += TEAM) ys[a] = Sol[a * (nb + 1) + nb];
-  tsync();
-  // reduced dynamics (eq. reduced-dynamics-data), S_{i+1} = T_{i+1}^T
-  wgemm<false, false>(n, nb, m, 1.0, B, m, Yw, n, 1.0, AT, n);            // A T + B Y
-  if (!tne) wgemm<true, false>(nn, nb, n, 1.0, Tn, n, AT, n, 0.0, ws + g.ws.Ab, n);
-  wgemm<false, false>(n, mb, m, 1.0, B, m, Z, m, 0.0, BZ, m);             // B Z
-  if (!tne) wgemm<true, false>(nn, mb, n, 1.0, Tn, n, BZ, m, 0.0, ws + g.ws.Bb, m);
-  for (int l = tid; l < n; l += TEAM) {
-    double s0 = Atc[l] - tn[l];
-    for (int j = 0; j < m; j++) s0 = fma(B[l * m + j], ys[j], s0);
-    cv[l] = s0;
-  }
-  tsync();
-  if (tne) {  // Abar = A T + B Y, Bbar = B Z, cbar = c_v
-    for (int idx = tid; idx < n * nb; idx += TEAM) {
-      const int a = idx / nb, j = idx - a * nb;
-      ws[g.ws.Ab + a * n + j] = AT[a * n + j];
-    }
-    for (int idx = tid; idx < n * mb; idx += TEAM) {
-      const int a = idx / mb, j = idx - a * mb;
-      ws[g.ws.Bb + a * m + j] = BZ[a * m + j];
-    }
-    for (int l = tid; l < n; l += TEAM) ws[g.ws.cb + l] = cv[l];
-  } else {
-    wgemm<true, false>(nn, 1, n, 1.0, Tn, n, cv, 1, 0.0, ws + g.ws.cb, 1);
-  }
-  // state substitution (eq. state-cost-data)
-  double *Qb = ws + g.ws.Qb, *Mb = ws + g.ws.Mb, *Rb = ws + g.ws.Rb;
-  if (te) {  // Q^z = Q, M^z = M, q^z = q, r^z = r
-    for (int idx = tid; idx < n * n; idx += TEAM) Qb[idx] = Q[idx];
-    for (int idx = tid; idx < n * m; idx += TEAM) Mz[idx] = Mm[idx];
-    for (int l = tid; l < n; l += TEAM) qz[l] = q[l];
-    for (int a = tid; a < m; a += TEAM) rz[a] = r[a];
+    for (int idx = tid; idx < r1 * (n + 1); idx += TEAM) Hs[idx] = Hn[idx];
     tsync();
-  } else {
-    wgemm<false, false>(n, nb, n, 1.0, Q, n, T, n, 0.0, QT, n);             // Q T
-    wgemm<true, false>(nb, nb, n, 1.0, T, n, QT, n, 0.0, Qb, n);            // Q^z
-    wgemm<true, false>(nb, m, n, 1.0, T, n, Mm, m, 0.0, Mz, m);             // M^z
+    // Gamma = [D; Hn B],  [Phi | gamma] = [C T | C t + d; Hn A T | Hn (A t + c) + hn]
+    for (int idx = tid; idx < S.p * m; idx += TEAM) {
+      int a = idx / m, j = idx - a * m;
+      Gm[a * m + j] = g.D[P.oD + (size_t)(S.prow + a) * m + j];
+    }
+    wgemm<false, false>(r1, m, n, 1.0, Hs, n + 1, B, m, 0.0, Gm + S.p * m, m);
+    for (int idx = tid; idx < S.p * (nb + 1); idx += TEAM) {
+      int a = idx / (nb + 1), j = idx - a * (nb + 1);
+      const double *Cr = g.C + P.oC + (size_t)(S.prow + a) * n;
+      double s0 = 0.0;
+      if (te) {
+        s0 = (j < nb) ? Cr[j] : g.d[P.od + S.prow + a];
+      } else if (j < nb) {
+        for (int l = 0; l < n; l++) s0 = fma(Cr[l], T[l * n + j], s0);
+      } else {
+        s0 = g.d[P.od + S.prow + a];
+        for (int l = 0; l < n; l++) s0 = fma(Cr[l], t[l], s0);
+      }
+      Rh[a * (nb + 1) + j] = s0;
+    }
+    for (int idx = tid; idx < r1 * (nb + 1); idx += TEAM) {
+      int a = idx / (nb + 1), j = idx - a * (nb + 1);
+      const double *hr = Hs + a * (n + 1);
+      double s0 = 0.0;
+      if (j < nb) {
+        for (int l = 0; l < n; l++) s0 = fma(hr[l], AT[l * n + j], s0);
+      } else {
+        s0 = hr[n];
+        for (int l = 0; l < n; l++) s0 = fma(hr[l], Atc[l], s0);
+      }
+      Rh[(S.p + a) * (nb + 1) + j] = s0;
+    }
+    tsync();
+    // Lemma 4: Z = null(Gamma), [Y | y] = -Gamma^- [Phi | gamma] (min norm)
+    // the small form only: this kernel runs many CTAs to an SM, and the large form's
+    // registers and static scratch would cost it occupancy
+    const int rank = wtqr_small(Gm, m, rows, m, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qm, m, perm, scr);
+    const double rs = wtqr_solve(Wt, (rows > 0 ? rows : 1), Qm, m, perm, rows, m, rank, Rh, nb + 1, nb + 1,
+                                 Sol, nb + 1, X1, nb + 1);
+    if (tid == 0 && rs > g.tau_inc) set_status(g, S.prob, ST_RANK_INCONSISTENT);
+    const int mb = m - rank;
+    const double *Z = Qm + rank;  // ld m
+    // Y (m x nb, ld n), y (m)
+    for (int idx = tid; idx < m * nb; idx += TEAM) {
+      int a = idx / nb, j = idx - a * nb;
+      Yw[a * n + j] = Sol[a * (nb + 1) + j];
+    }
+    for (int a = tid; a < m; a += TEAM) ys[a] = Sol[a * (nb + 1) + nb];
+    tsync();
+    // reduced dynamics (eq. reduced-dynamics-data), S_{i+1} = T_{i+1}^T
+    wgemm<false, false>(n, nb, m, 1.0, B, m, Yw, n, 1.0, AT, n);            // A T + B Y
+    if (!tne) wgemm<true, false>(nn, nb, n, 1.0, Tn, n, AT, n, 0.0, ws + g.ws.Ab, n);
+    wgemm<false, false>(n, mb, m, 1.0, B, m, Z, m, 0.0, BZ, m);             // B Z
+    if (!tne) wgemm<true, false>(nn, mb, n, 1.0, Tn, n, BZ, m, 0.0, ws + g.ws.Bb, m);
     for (int l = tid; l < n; l += TEAM) {
-      double s0 = q[l];
-      for (int j = 0; j < n; j++) s0 = fma(Q[l * n + j], t[j], s0);
-      Qtq[l] = s0;
+      double s0 = Atc[l] - tn[l];
+      for (int j = 0; j < m; j++) s0 = fma(B[l * m + j], ys[j], s0);
+      cv[l] = s0;
     }
+    tsync();
+    if (tne) {  // Abar = A T + B Y, Bbar = B Z, cbar = c_v
+      for (int idx = tid; idx < n * nb; idx += TEAM) {
+        const int a = idx / nb, j = idx - a * nb;
+        ws[g.ws.Ab + a * n + j] = AT[a * n + j];
+      }
+      for (int idx = tid; idx < n * mb; idx += TEAM) {
+        const int a = idx / mb, j = idx - a * mb;
+        ws[g.ws.Bb + a * m + j] = BZ[a * m + j];
+      }
+      for (int l = tid; l < n; l += TEAM) ws[g.ws.cb + l] = cv[l];
+    } else {
+      wgemm<true, false>(nn, 1, n, 1.0, Tn, n, cv, 1, 0.0, ws + g.ws.cb, 1);
+    }
+    // state substitution (eq. state-cost-data)
+    double *Qb = ws + g.ws.Qb, *Mb = ws + g.ws.Mb, *Rb = ws + g.ws.Rb;
+    if (te) {  // Q^z = Q, M^z = M, q^z = q, r^z = r
+      for (int idx = tid; idx < n * n; idx += TEAM) Qb[idx] = Q[idx];
+      for (int idx = tid; idx < n * m; idx += TEAM) Mz[idx] = Mm[idx];
+      for (int l = tid; l < n; l += TEAM) qz[l] = q[l];
+      for (int a = tid; a < m; a += TEAM) rz[a] = r[a];
+      tsync();
+    } else {
+      wgemm<false, false>(n, nb, n, 1.0, Q, n, T, n, 0.0, QT, n);             // Q T
+      wgemm<true, false>(nb, nb, n, 1.0, T, n, QT, n, 0.0, Qb, n);            // Q^z
+      wgemm<true, false>(nb, m, n, 1.0, T, n, Mm, m, 0.0, Mz, m);             // M^z
+      for (int l = tid; l < n; l += TEAM) {
+        double s0 = q[l];
+        for (int j = 0; j < n; j++) s0 = fma(Q[l * n + j], t[j], s0);
+        Qtq[l] = s0;
+      }
+      for (int a = tid; a < m; a += TEAM) {
+        double s0 = r[a];
+        for (int l = 0; l < n; l++) s0 = fma(Mm[l * m + a], t[l], s0);
+        rz[a] = s0;                                                           // r^z
+      }
+      tsync();
+      wgemm<true, false>(nb, 1, n, 1.0, T, n, Qtq, 1, 0.0, qz, 1);            // q^z
+    }
+    // reduced cost (eq. reduced-cost-data)
+    wgemm<false, false>(m, nb, m, 1.0, R, m, Yw, n, 0.0, RY, n);            // R Y
+    wgemm<false, false>(m, mb, m, 1.0, R, m, Z, m, 0.0, RZ, m);             // R Z
     for (int a = tid; a < m; a += TEAM) {
-      double s0 = r[a];
-      for (int l = 0; l < n; l++) s0 = fma(Mm[l * m + a], t[l], s0);
-      rz[a] = s0;                                                           // r^z
+      double s0 = rz[a];
+      for (int j = 0; j < m; j++) s0 = fma(R[a * m + j], ys[j], s0);
+      Ry[a] = s0;                                                           // R y + r^z
     }
     tsync();
-    wgemm<true, false>(nb, 1, n, 1.0, T, n, Qtq, 1, 0.0, qz, 1);            // q^z
-  }
-  // reduced cost (eq. reduced-cost-data)
-  wgemm<false, false>(m, nb, m, 1.0, R, m, Yw, n, 0.0, RY, n);            // R Y
-  wgemm<false, false>(m, mb, m, 1.0, R, m, Z, m, 0.0, RZ, m);             // R Z
-  for (int a = tid; a < m; a += TEAM) {
-    double s0 = rz[a];
-    for (int j = 0; j < m; j++) s0 = fma(R[a * m + j], ys[j], s0);
-    Ry[a] = s0;                                                           // R y + r^z
-  }
-  tsync();
-  wgemm<false, false>(nb, nb, m, 1.0, Mz, m, Yw, n, 0.0, X2, n);          // M^z Y
-  for (int idx = tid; idx < nb * nb; idx += TEAM) {
-    int a = idx / nb, j = idx - a * nb;
-    Qb[a * n + j] += X2[a * n + j] + X2[j * n + a];
-  }
-  tsync();
-  wgemm<true, false>(nb, nb, m, 1.0, Yw, n, RY, n, 1.0, Qb, n);           // + Y' R Y
-  wgemm<false, false>(nb, mb, m, 1.0, Mz, m, Z, m, 0.0, Mb, m);           // M^z Z
-  wgemm<true, false>(nb, mb, m, 1.0, Yw, n, RZ, m, 1.0, Mb, m);           // + Y' R Z
-  wgemm<true, false>(mb, mb, m, 1.0, Z, m, RZ, m, 0.0, Rb, m);            // Z' R Z
-  double *qb = ws + g.ws.qb, *rb = ws + g.ws.rb;
-  for (int a = tid; a < nb; a += TEAM) {
-    double s0 = qz[a];
-    for (int j = 0; j < m; j++) s0 = fma(Mz[a * m + j], ys[j], s0);
-    for (int j = 0; j < m; j++) s0 = fma(Yw[j * n + a], Ry[j], s0);
-    qb[a] = s0;
-  }
-  for (int a = tid; a < mb; a += TEAM) {
-    double s0 = 0.0;
-    for (int j = 0; j < m; j++) s0 = fma(Z[j * m + a], Ry[j], s0);
-    rb[a] = s0;
-  }
-  // Y, Z, y for recovery (eq. recovery-maps)
-  double *Yo = ws + g.ws.Y, *Zo = ws + g.ws.Z, *yo = ws + g.ws.y;
-  for (int idx = tid; idx < m * n; idx += TEAM) Yo[idx] = Yw[idx];
-  for (int idx = tid; idx < m * m; idx += TEAM) {
-    int a = idx / m, j = idx - a * m;
-    Zo[idx] = (j < mb) ? Z[a * m + j] : 0.0;
-  }
-  for (int a = tid; a < m; a += TEAM) yo[a] = ys[a];
-  if (tid == 0) wi[SI_MBAR] = mb;
-  tsync();
-  // square root of the reduced stage Hessian [[Qbar, Mbar], [Mbar', Rbar]] (order z, v):
-  // L L' = H, stored as L' (upper) with l = L^{-1} [qbar; rbar], for the square-root LQR
-  {
-    // stage Hessian in the order (v, z) -- the column order of the Riccati's QR, so that L'
-    // is upper triangular there -- bordered by g = [rbar; qbar]
-    const int kh = nb + mb, ldh = n + m, ldH = kh + 1;
-    double *Hh = U;  // the phases' region: everything else there is dead
-    for (int idx = tid; idx < (kh + 1) * kh; idx += TEAM) {
-      int a = idx / kh, j = idx - a * kh;
-      double h;
-      if (a == kh) h = (j < mb) ? rb[j] : qb[j - mb];
-      else if (a < mb && j < mb) h = Rb[a * m + j];
-      else if (a < mb) h = Mb[(j - mb) * m + a];
-      else if (j < mb) h = Mb[(a - mb) * m + j];
-      else h = Qb[(a - mb) * n + (j - mb)];
-      Hh[a * ldH + j] = h;
+    wgemm<false, false>(nb, nb, m, 1.0, Mz, m, Yw, n, 0.0, X2, n);          // M^z Y
+    for (int idx = tid; idx < nb * nb; idx += TEAM) {
+      int a = idx / nb, j = idx - a * nb;
+      Qb[a * n + j] += X2[a * n + j] + X2[j * n + a];
     }
     tsync();
-    int fail = 0;
-    if (tid < 32) fail = wchol_bordered(Hh, ldH, kh);
-    fail = __syncthreads_or(fail);
-    if (fail && tid == 0) set_status(g, S.prob, ST_NONCONVEX);
-    double *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
-    for (int idx = tid; idx < kh * kh; idx += TEAM) {
-      int a = idx / kh, j = idx - a * kh;
-      LT[a * ldh + j] = (j >= a) ? Hh[j * ldH + a] : 0.0;
+    wgemm<true, false>(nb, nb, m, 1.0, Yw, n, RY, n, 1.0, Qb, n);           // + Y' R Y
+    wgemm<false, false>(nb, mb, m, 1.0, Mz, m, Z, m, 0.0, Mb, m);           // M^z Z
+    wgemm<true, false>(nb, mb, m, 1.0, Yw, n, RZ, m, 1.0, Mb, m);           // + Y' R Z
+    wgemm<true, false>(mb, mb, m, 1.0, Z, m, RZ, m, 0.0, Rb, m);            // Z' R Z
+    double *qb = ws + g.ws.qb, *rb = ws + g.ws.rb;
+    for (int a = tid; a < nb; a += TEAM) {
+      double s0 = qz[a];
+      for (int j = 0; j < m; j++) s0 = fma(Mz[a * m + j], ys[j], s0);
+      for (int j = 0; j < m; j++) s0 = fma(Yw[j * n + a], Ry[j], s0);
+      qb[a] = s0;
     }
-    for (int a = tid; a < kh; a += TEAM) lt[a] = Hh[kh * ldH + a];  // L^{-1} [rbar; qbar]
-  }
+    for (int a = tid; a < mb; a += TEAM) {
+      double s0 = 0.0;
+      for (int j = 0; j < m; j++) s0 = fma(Z[j * m + a], Ry[j], s0);
+      rb[a] = s0;
+    }
+    // Y, Z, y for recovery (eq. recovery-maps)
+    double *Yo = ws + g.ws.Y, *Zo = ws + g.ws.Z, *yo = ws + g.ws.y;
+    for (int idx = tid; idx < m * n; idx += TEAM) Yo[idx] = Yw[idx];
+    for (int idx = tid; idx < m * m; idx += TEAM) {
+      int a = idx / m, j = idx - a * m;
+      Zo[idx] = (j < mb) ? Z[a * m + j] : 0.0;
+    }
+    for (int a = tid; a < m; a += TEAM) yo[a] = ys[a];
+    if (tid == 0) wi[SI_MBAR] = mb;
+    tsync();
+    // square root of the reduced stage Hessian [[Qbar, Mbar], [Mbar', Rbar]] (order z, v):
+    // L L' = H, stored as L' (upper) with l = L^{-1} [qbar; rbar], for the square-root LQR
+    {
+      // stage Hessian in the order (v, z) -- the column order of the Riccati's QR, so that L'
+      // is upper triangular there -- bordered by g = [rbar; qbar]
+      const int kh = nb + mb, ldh = n + m, ldH = kh + 1;
+      double *Hh = U;  // the phases' region: everything else there is dead
+      for (int idx = tid; idx < (kh + 1) * kh; idx += TEAM) {
+        int a = idx / kh, j = idx - a * kh;
+        double h;
+        if (a == kh) h = (j < mb) ? rb[j] : qb[j - mb];
+        else if (a < mb && j < mb) h = Rb[a * m + j];
+        else if (a < mb) h = Mb[(j - mb) * m + a];
+        else if (j < mb) h = Mb[(a - mb) * m + j];
+        else h = Qb[(a - mb) * n + (j - mb)];
+        Hh[a * ldH + j] = h;
+      }
+      tsync();
+      int fail = 0;
+      if (tid < 32) fail = wchol_bordered(Hh, ldH, kh);
+      fail = __syncthreads_or(fail);
+      if (fail && tid == 0) set_status(g, S.prob, ST_NONCONVEX);
+      double *LT = ws + g.ws.LT, *lt = ws + g.ws.lt;
+      for (int idx = tid; idx < kh * kh; idx += TEAM) {
+        int a = idx / kh, j = idx - a * kh;
+        LT[a * ldh + j] = (j >= a) ? Hh[j * ldH + a] : 0.0;
+      }
+      for (int a = tid; a < kh; a += TEAM) lt[a] = Hh[kh * ldH + a];  // L^{-1} [rbar; qbar]
+    }
+  });
 }
 
 }  // namespace eclqr

@@ -72,6 +72,26 @@ __global__ void k_refine_prep(Group g, const int32_t *status, const double *resi
   if (on) *any = 1;
 }
 
+// Per problem, after k_refine_prep: the stages of the problems in each of the
+// pass's masks (active, full, cheap) are appended to that mask's list (lists +
+// f * nstage, length counts[f], zero before the launch), so that the pass's
+// per-stage kernels visit those stages only.  The order of the stages in a list
+// does not matter: every stage's work is independent of the others'.
+__global__ void k_stage_lists(Group g, RefineMasks mk, int *lists, int *counts) {
+  const int t = team_task();
+  if (t >= g.nprob || threadIdx.x >= 32) return;  // one warp per problem
+  const ProbInfo &P = g.prob[t];
+  const int lane = threadIdx.x, ns = P.N + 1;
+  const int *flags[3] = {mk.active, mk.full, mk.cheap};
+  for (int f = 0; f < 3; f++) {
+    if (!flags[f][P.id]) continue;  // uniform
+    int base = 0;
+    if (lane == 0) base = atomicAdd(counts + f, ns);
+    base = __shfl_sync(kFull, base, 0);
+    for (int k = lane; k < ns; k += 32) lists[(size_t)f * g.nstage + base + k] = P.st0 + k;
+  }
+}
+
 // After the correction solve: a problem whose correction ended with a status
 // other than OK keeps its point and stops refining.
 __global__ void k_refine_gate(Group g, const int32_t *cstatus, int *active) {
@@ -94,48 +114,48 @@ __global__ void k_refine_parts(Group g, const int *active, double *parts, const 
 
 // t = w + t for one stage's blocks (t holds the correction on entry).
 __global__ void k_refine_trial(Group g, Sol w, SolMut t) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
-  for (int a = tid; a < n; a += TEAM) {
-    const size_t o = P.ox + (size_t)i * n + a;
-    t.x[o] += w.x[o];
-    t.lam[o] += w.lam[o];
-  }
-  if (i < P.N) {
-    for (int a = tid; a < m; a += TEAM) t.u[P.ou + (size_t)i * m + a] += w.u[P.ou + (size_t)i * m + a];
-    for (int k = tid; k < S.p; k += TEAM) t.mu[P.omu + S.prow + k] += w.mu[P.omu + S.prow + k];
-  }
-  for (int k = tid; k < S.q; k += TEAM) t.eta[P.oeta + S.qrow + k] += w.eta[P.oeta + S.qrow + k];
-  if (i == 0)
-    for (int a = tid; a < n; a += TEAM) t.alpha[P.oalpha + a] += w.alpha[P.oalpha + a];
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+    for (int a = tid; a < n; a += TEAM) {
+      const size_t o = P.ox + (size_t)i * n + a;
+      t.x[o] += w.x[o];
+      t.lam[o] += w.lam[o];
+    }
+    if (i < P.N) {
+      for (int a = tid; a < m; a += TEAM) t.u[P.ou + (size_t)i * m + a] += w.u[P.ou + (size_t)i * m + a];
+      for (int k = tid; k < S.p; k += TEAM) t.mu[P.omu + S.prow + k] += w.mu[P.omu + S.prow + k];
+    }
+    for (int k = tid; k < S.q; k += TEAM) t.eta[P.oeta + S.qrow + k] += w.eta[P.oeta + S.qrow + k];
+    if (i == 0)
+      for (int a = tid; a < n; a += TEAM) t.alpha[P.oalpha + a] += w.alpha[P.oalpha + a];
+  });
 }
 
 // Copies the trial point over the solution where its residual is smaller.
 __global__ void k_refine_accept(Group g, Sol t, double *x, double *u, double *lam, double *mu, double *eta,
                                 double *alpha, const double *resid, const double *tresid) {
-  const int s = team_task();
-  if (s >= g.nstage) return;
-  const StageInfo S = g.st[s];
-  const ProbInfo &P = g.prob[S.prob];
-  if (skipped_by_mask(g, S.prob)) return;
-  if (!(tresid[P.id] < resid[P.id])) return;
-  const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
-  for (int a = tid; a < n; a += TEAM) {
-    const size_t o = P.ox + (size_t)i * n + a;
-    x[o] = t.x[o];
-    lam[o] = t.lam[o];
-  }
-  if (i < P.N) {
-    for (int a = tid; a < m; a += TEAM) u[P.ou + (size_t)i * m + a] = t.u[P.ou + (size_t)i * m + a];
-    for (int k = tid; k < S.p; k += TEAM) mu[P.omu + S.prow + k] = t.mu[P.omu + S.prow + k];
-  }
-  for (int k = tid; k < S.q; k += TEAM) eta[P.oeta + S.qrow + k] = t.eta[P.oeta + S.qrow + k];
-  if (i == 0)
-    for (int a = tid; a < n; a += TEAM) alpha[P.oalpha + a] = t.alpha[P.oalpha + a];
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    if (!(tresid[P.id] < resid[P.id])) return;
+    const int n = g.n, m = g.m, tid = team_rank(), i = S.i;
+    for (int a = tid; a < n; a += TEAM) {
+      const size_t o = P.ox + (size_t)i * n + a;
+      x[o] = t.x[o];
+      lam[o] = t.lam[o];
+    }
+    if (i < P.N) {
+      for (int a = tid; a < m; a += TEAM) u[P.ou + (size_t)i * m + a] = t.u[P.ou + (size_t)i * m + a];
+      for (int k = tid; k < S.p; k += TEAM) mu[P.omu + S.prow + k] = t.mu[P.omu + S.prow + k];
+    }
+    for (int k = tid; k < S.q; k += TEAM) eta[P.oeta + S.qrow + k] = t.eta[P.oeta + S.qrow + k];
+    if (i == 0)
+      for (int a = tid; a < n; a += TEAM) alpha[P.oalpha + a] = t.alpha[P.oalpha + a];
+  });
 }
 
 // Per problem, after the accept: the residual of the kept point; the passes go

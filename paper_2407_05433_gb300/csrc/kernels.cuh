@@ -63,6 +63,7 @@ __global__ void k_kkt(Group g, const double *s0, const double *x, const double *
 
 // refinement on the original KKT residual and non-finite checks (k_refine.cu)
 __global__ void k_check_inputs(Group g);
+__global__ void k_stage_lists(Group g, RefineMasks mk, int *lists, int *counts);
 __global__ void k_refine_prep(Group g, const int32_t *status, const double *resid, const double *parts,
                               RefineMasks mk, int32_t *cstatus, double *tresid, double *tparts, double tol,
                               int first, int *any);

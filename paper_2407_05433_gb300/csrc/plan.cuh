@@ -128,6 +128,8 @@ struct Group {
                       // the tasks of problems whose entry is 0 (refinement passes)
   const int *fp64;    // mixed precision: batch-global flags, 1 = this problem's Riccati sweep in
                       // FP64, 0 = in FP32; null = every sweep in FP64
+  const int *slist;   // when set, the per-stage kernels run only the stages slist[0 .. *scount)
+  const int *scount;  // (a refinement pass's problems), each CTA looping over them
   double tau_rank, tau_inc;
 };
 
@@ -182,6 +184,24 @@ __device__ __forceinline__ int team_task() { return blockIdx.x; }
 
 extern __shared__ double g_smem[];
 __device__ __forceinline__ double *team_smem(int /*per_task*/) { return g_smem; }
+
+// Runs body(s) for the stages of a per-stage launch: the CTA's own stage (one CTA per
+// stage), or, when the group carries a stage list, the listed stages
+// blockIdx.x, blockIdx.x + gridDim.x, ... in turn, with a barrier between them so
+// that a stage's shared memory is free before the next one writes it.
+template <typename F>
+__device__ __forceinline__ void for_stages(const Group &g, F body) {
+  if (g.slist == nullptr) {
+    const int s = team_task();
+    if (s < g.nstage) body(s);
+    return;
+  }
+  const int cnt = *g.scount;
+  for (int t = blockIdx.x; t < cnt; t += gridDim.x) {
+    body(g.slist[t]);
+    __syncthreads();
+  }
+}
 
 // Runs body(t) for the tasks [0, ntasks) of a launch.  queue null: the CTA's own
 // task.  Otherwise the launch is persistent: each CTA takes the next task index
