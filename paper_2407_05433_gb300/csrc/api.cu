@@ -26,7 +26,7 @@ constexpr int kMaxSmemBytes = 219 * 1024;
 constexpr int kTeamWarps = 4;  // default team: one warp per SM sub-partition
 constexpr int kManyTasksPerSm = 4;  // a launch with at least this many tasks per SM takes the table's team
 constexpr int kPersistCtasPerSm = 8;  // default CTAs per SM of a persistent launch
-constexpr int kListCtasPerSm = 8;     // CTAs per SM of a per-stage launch over a stage list
+constexpr int kListCtasPerSm = 32;    // CTAs per SM of a per-stage launch over a stage list
 
 struct GroupHost {
   Group g;
