@@ -877,7 +877,7 @@ int eclqr_refine(eclqr_handle *h, const double *s0, double *x, double *u, double
       gz.slist = gh.slists + 2 * (size_t)gu.nstage;
       gz.scount = gh.scounts + 2;
       gz.c = h->zeros; gz.d = h->zeros; gz.e = h->zeros; gz.qv = h->rows.qv; gz.rv = h->rows.rv;
-      TRY(launch(h, k_set_costs, gz.nstage, 0, gst, gz, 0));
+      TRY(launch(h, k_set_costs, gz.nstage, smem_set_costs(gz.n, gz.m), gst, gz, smem_set_costs(gz.n, gz.m)));
       TRY(run_solve(h, gh, gz, gst, h->zeros, t.x, t.u, corr));
       TRY(run_mult(h, gh, gz, gst, t.x, t.u, t.lam, t.mu, t.eta, t.alpha));
       // trial point w + dw, its residual, and the choice
@@ -950,7 +950,7 @@ int eclqr_set_costs(eclqr_handle *h, const eclqr_data *data, void *stream) {
     g.A = data->A; g.B = data->B; g.c = data->c; g.C = data->C; g.D = data->D; g.d = data->d;
     g.E = data->E; g.e = data->e; g.Q = data->Q; g.M = data->M; g.R = data->R; g.qv = data->qv; g.rv = data->rv;
     g.active = nullptr;
-    TRY(launch(h, k_set_costs, g.nstage, 0, group_stream(h, gh, st), g, 0));
+    TRY(launch(h, k_set_costs, g.nstage, smem_set_costs(g.n, g.m), group_stream(h, gh, st), g, smem_set_costs(g.n, g.m)));
   }
   TRY(join_groups(h, st));
   h->solved = false;

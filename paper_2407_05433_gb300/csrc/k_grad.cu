@@ -80,6 +80,9 @@ __global__ void k_param_grads(Group g, Sol w, Sol wb, GradOut o) {
 
 namespace eclqr {
 
+// shared memory of k_set_costs: the stage factor L' (at most (n + m)^2)
+__host__ int smem_set_costs(int n, int m) { return (n + m) * (n + m) + 8; }
+
 // New linear costs with zero affine offsets (c = d = e = 0), on the factors of
 // the last build -- the adjoint problem of the gradient above.  With h_i = 0
 // every suffix domain is a subspace, so t = y = 0 and cbar = 0; the reduced
@@ -126,18 +129,35 @@ __global__ void k_set_costs(Group g, int per_task) {
       for (int l = 0; l < m; l++) s0 = fma(Z[l * m + a], r[l], s0);
       ws[g.ws.rb + a] = s0;
     }
-    tsync();
-    if (!last && tid == 0) {
-      const int kh = nb + mb, ldh = n + m;
+    // lt = L^{-1} [rbar; qbar] (order (v, z), L = LT'), by the first warp: L' is staged in
+    // shared memory, lane a holds rows a and a + 32, and step l fixes lt[l] and takes its
+    // column out of the rows below it (the same operations, in the same order, as the row
+    // by row substitution)
+    const int kh = nb + mb, ldh = n + m;
+    double *Ls = team_smem(per_task);
+    if (!last) {
       const double *LT = ws + g.ws.LT;
-      double *lt = ws + g.ws.lt;
-      for (int a = 0; a < kh; a++) {
-        double s0 = (a < mb) ? ws[g.ws.rb + a] : ws[g.ws.qb + (a - mb)];  // order (v, z)
-        for (int l = 0; l < a; l++) s0 = fma(-LT[l * ldh + a], lt[l], s0);
-        lt[a] = s0 / LT[a * ldh + a];
+      for (int idx = tid; idx < kh * kh; idx += TEAM) {
+        const int l = idx / kh, a = idx - l * kh;
+        Ls[l * kh + a] = LT[l * ldh + a];
       }
     }
-    (void)per_task;
+    tsync();
+    if (!last && tid < 32) {
+      const int a0 = tid, a1 = tid + 32;
+      auto rhs = [&](int a) { return (a < mb) ? ws[g.ws.rb + a] : ws[g.ws.qb + (a - mb)]; };
+      double x0 = (a0 < kh) ? rhs(a0) : 0.0, x1 = (a1 < kh) ? rhs(a1) : 0.0;
+      for (int l = 0; l < kh; l++) {
+        const double xl = __shfl_sync(kFull, l < 32 ? x0 : x1, l & 31) / Ls[l * kh + l];
+        if (a0 == l) x0 = xl;
+        if (a1 == l) x1 = xl;
+        if (a0 > l && a0 < kh) x0 = fma(-Ls[l * kh + a0], xl, x0);
+        if (a1 > l && a1 < kh) x1 = fma(-Ls[l * kh + a1], xl, x1);
+      }
+      double *lt = ws + g.ws.lt;
+      if (a0 < kh) lt[a0] = x0;
+      if (a1 < kh) lt[a1] = x1;
+    }
   });
 }
 

@@ -733,6 +733,9 @@ __global__ void k_aff_down(Group g, int mode, int fin, int per_task) {
   }
   int s = steps > 0 ? stage_of(0) : 0;
   int dout = steps > 0 ? dout_of(s) : 0;
+  // the output dimension of the next stage, read one stage ahead of its map's entries so
+  // that the two global reads do not follow each other on the chain
+  int dpre = steps > 1 ? dout_of(stage_of(1)) : 0;
   if (steps > 0) load(s, dcur, dout, gr, gvr);
   tsync();
   for (int k = 0; k < steps; k++) {
@@ -745,8 +748,9 @@ __global__ void k_aff_down(Group g, int mode, int fin, int per_task) {
     int sn = s, dn = 0;
     if (k + 1 < steps) {
       sn = stage_of(k + 1);
-      dn = dout_of(sn);
+      dn = dpre;
       load(sn, dout, dn, gn, gvn);
+      if (k + 2 < steps) dpre = dout_of(stage_of(k + 2));
     }
     double acc = 0.0;
 #pragma unroll
