@@ -1064,8 +1064,12 @@ static int solve_once(const orc_problem *P, const orc_options *opt, double *x,
             co_[(size_t)i * n + a] = s;
           }
         }
+        /* products with T_i = I (ur = 0: x = z, the T' part of the z residual) or T_{i+1} = I
+           are their other factor: not counted as work (as in step 5) */
+        const int tei = ur[i] == 0, ten = i < N && ur[i + 1] == 0;
         ADDF(2.0 * n * ni + 2.0 * m * (ni + mi) + 2.0 * n * nn + 2.0 * n * (2 * n + m) + 2.0 * m * (2 * n + m) +
-             2.0 * ni * (n + m) + 2.0 * mi * m + 2.0 * nn * (ni + mi));
+             2.0 * ni * (n + m) + 2.0 * mi * m + 2.0 * nn * (ni + mi) - (tei ? 4.0 * n * ni : 0.0) -
+             (ten ? 2.0 * n * nn : 0.0));
       }
     }
     free(qo_); free(ro_); free(co_); free(dz); free(dv); free(dpi); free(pv); free(w); free(hu); free(z0);

@@ -443,7 +443,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
           {(const void *)k_riccati_down, smem_riccati(n, m)},
           {(const void *)k_riccati_finish, smem_riccati_finish(n, m)}, {(const void *)k_aff_up, sa},
           {(const void *)k_aff_level, sa}, {(const void *)k_aff_down, sa}, {(const void *)k_resid, 3 * n + 2 * m},
-          {(const void *)k_pcorr, n + m}, {(const void *)k_dual_stage, smem_dual_stage(n, m)},
+          {(const void *)k_pcorr, n + m + m * m}, {(const void *)k_dual_stage, smem_dual_stage(n, m)},
           {(const void *)k_dual_terminal, sdw}, {(const void *)k_dual_up, sdw}, {(const void *)k_dual_down, sdw},
           {(const void *)k_dual_root, sdw}, {(const void *)k_dual_leaf, smem_dual_leaf(n, m, pmax, qmax)}};
       int optin = 0;
@@ -641,7 +641,7 @@ int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, 
   int src = 0;
   for (int k = 0; k < gh.levels; k++, src ^= 1)
     TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
-  TRY(launch(h, k_primal_down, g.nslot, sw, gst, g, src, sw));
+  TRY(launch_sweep(h, gh.queue, k_primal_down, g.nslot, sw, gst, g, src, sw));
   const int sp = smem_param(n), se = smem_elim(n, m, pm);
   TRY(launch(h, k_param, g.nstage, sp, gst, g, sp));
   TRY(launch(h, k_elim, g.nstage, se, gst, g, se));
@@ -678,7 +678,7 @@ int run_solve(eclqr_handle *h, const GroupHost &gh, const Group &g, cudaStream_t
     const int sres = 3 * g.n + 2 * g.m;
     TRY(launch(h, k_resid, g.nstage, sres, gst, g, sres));
     TRY(aff_scan(h, gh, g, AFF_PLIN_, gst));
-    const int sc = g.n + g.m;
+    const int sc = g.n + g.m + g.m * g.m;
     TRY(launch(h, k_pcorr, g.nstage, sc, gst, g, sc));
     TRY(aff_scan(h, gh, g, AFF_CROLL_, gst));
     TRY(launch(h, k_post_roll, g.nstage, 0, gst, g, 1));

@@ -884,9 +884,13 @@ __global__ void k_resid(Group g, int per_task) {
     const double *Y = ws + g.ws.Y, *Z = ws + g.ws.Z, *Ab = ws + g.ws.Ab, *Bb = ws + g.ws.Bb;
     double *sm = team_smem(per_task);
     double *xs = sm, *us = xs + n, *lh = us + m, *ga = lh + n, *gb = ga + n;
+    // T_i = I, t_i = 0 (te) or T_{i+1} = I (tne): the products with them are their other factor
+    const bool te = wi[SI_TEYE] != 0, tne = !last && stage_wi(g, s + 1)[SI_TEYE] != 0;
     for (int a = tid; a < n; a += TEAM) {
       double s0 = ws[g.ws.t + a];
-      for (int j = 0; j < nx; j++) s0 = fma(T[a * n + j], z[j], s0);
+      if (te) s0 = z[a];
+      else
+        for (int j = 0; j < nx; j++) s0 = fma(T[a * n + j], z[j], s0);
       xs[a] = s0;
     }
     if (!last) {
@@ -898,7 +902,9 @@ __global__ void k_resid(Group g, int per_task) {
       }
       for (int l = tid; l < n; l += TEAM) {
         double s0 = 0.0;
-        for (int j = 0; j < ny; j++) s0 = fma(Tn[l * n + j], pin[j], s0);
+        if (tne) s0 = pin[l];
+        else
+          for (int j = 0; j < ny; j++) s0 = fma(Tn[l * n + j], pin[j], s0);
         lh[l] = s0;                                               // T_{i+1} pi_{i+1}
       }
     }
@@ -927,7 +933,9 @@ __global__ void k_resid(Group g, int per_task) {
     tsync();
     for (int r = tid; r < nx; r += TEAM) {
       double s0 = -pi[r];
-      for (int l = 0; l < n; l++) s0 = fma(T[l * n + r], ga[l], s0);
+      if (te) s0 = ga[r] - pi[r];
+      else
+        for (int l = 0; l < n; l++) s0 = fma(T[l * n + r], ga[l], s0);
       if (!last)
         for (int l = 0; l < m; l++) s0 = fma(Y[l * n + r], gb[l], s0);
       ws[g.ws.rq + r] = s0;
@@ -959,8 +967,12 @@ __global__ void k_pcorr(Group g, int per_task) {
     const double *wn = stage_ws(g, s + 1);
     const int mu = stage_wi(g, s)[SI_MBAR], ny = stage_wi(g, s + 1)[SI_NBAR];
     double *sm = team_smem(per_task);
-    double *w = sm, *hu = sm + n;
+    double *w = sm, *hu = sm + n, *Ls = hu + m;  // Ls: chol(H_uu), mu x mu (ld m)
     const double *Pn = wn + g.ws.P, *ppn = wn + g.ws.pp, *rc = ws + g.ws.rc, *Bb = ws + g.ws.Bb;
+    for (int idx = tid; idx < mu * mu; idx += TEAM) {
+      const int a = idx / mu, l = idx - a * mu;
+      Ls[a * m + l] = ws[g.ws.Lh + a * m + l];
+    }
     for (int b = tid; b < ny; b += TEAM) {
       double s0 = ppn[b];
       for (int l = 0; l < ny; l++) s0 = fma(Pn[b * n + l], rc[l], s0);
@@ -973,19 +985,22 @@ __global__ void k_pcorr(Group g, int per_task) {
       hu[a] = s0;
     }
     tsync();
-    if (tid == 0) {
-      const double *Lh = ws + g.ws.Lh;  // lower triangular, ld m
-      for (int a = 0; a < mu; a++) {
-        double s0 = hu[a];
-        for (int l = 0; l < a; l++) s0 = fma(-Lh[a * m + l], hu[l], s0);
-        hu[a] = s0 / Lh[a * m + a];
+    // dv = -H_uu^{-1} hu with H_uu = L L' (L = Ls, lower): forward then backward
+    // substitution by the first warp, lane a holding row a (mu <= 16), column by column
+    if (tid < 32) {
+      const int a = tid;
+      double x = (a < mu) ? hu[a] : 0.0;
+      for (int l = 0; l < mu; l++) {
+        const double xl = __shfl_sync(kFull, x, l) / Ls[l * m + l];
+        if (a == l) x = xl;
+        else if (a > l && a < mu) x = fma(-Ls[a * m + l], xl, x);
       }
-      for (int a = mu - 1; a >= 0; a--) {
-        double s0 = hu[a];
-        for (int l = a + 1; l < mu; l++) s0 = fma(-Lh[l * m + a], hu[l], s0);
-        hu[a] = s0 / Lh[a * m + a];
+      for (int l = mu - 1; l >= 0; l--) {
+        const double xl = __shfl_sync(kFull, x, l) / Ls[l * m + l];
+        if (a == l) x = xl;
+        else if (a < l) x = fma(-Ls[l * m + a], xl, x);
       }
-      for (int a = 0; a < mu; a++) ws[g.ws.dv + a] = -hu[a];
+      if (a < mu) ws[g.ws.dv + a] = -x;
     }
   });
 }

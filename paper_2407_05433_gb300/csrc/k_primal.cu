@@ -302,8 +302,12 @@ __device__ int primal_down_stage(const Group &g, const ProbInfo &P, int i, doubl
 // up to rounding, and a stage whose domain was derived from one set while the
 // next stage's basis comes from the other leaves U_b'(A T + B Y) at that
 // rounding level, which the multipliers of Sec. 7 multiply by |nu_b|.
-__global__ void k_primal_down(Group g, int fin, int per_task) {
-  const int t = team_task();
+static __device__ void primal_down_task(const Group &g, int fin, int t, int per_task);
+__global__ void k_primal_down(Group g, int fin, int per_task, int *queue) {
+  for_tasks(g.nslot, queue, [&](int t) { primal_down_task(g, fin, t, per_task); });
+}
+
+static __device__ void primal_down_task(const Group &g, int fin, int t, int per_task) {
   if (t >= g.nslot) return;
   const ChunkInfo ci = g.chunk[t];
   const ProbInfo &P = g.prob[ci.prob];
