@@ -56,7 +56,7 @@ PHASE_KERNELS = {"k_primal_down": 0, "k_param": 1, "k_elim": 2, "k_riccati_down"
 # kernels that carry the rest of the same phase (their time counts with the phase's kernel)
 # (phase 5's forward substitution of nu also runs in k_aff_down, whose launches serve the rollout too and
 # are left out, so the multipliers' rate is an upper bound)
-PHASE_PARTNERS = {"k_riccati_down": ("k_riccati_finish",),
+PHASE_PARTNERS = {"k_riccati_down": ("k_riccati_finish",), "k_primal_down": ("k_primal_stage",),
                   "k_dual_down": ("k_dual_stage", "k_dual_leaf", "k_dual_root", "k_dual_terminal", "k_dual_up")}
 
 

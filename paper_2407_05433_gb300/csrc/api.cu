@@ -110,6 +110,7 @@ int team_for(const eclqr_handle *h, const void *kern, int ntasks, int n) {
       {(const void *)k_riccati_down, 1, 24, 2},  {(const void *)k_riccati_down_f32, 1, 0, 1},
       {(const void *)k_riccati_finish, 1, 0, 1}, {(const void *)k_elim, 1, 16, 4},
       {(const void *)k_primal_down, 1, 24, 2},   {(const void *)k_dual_down, 1, 0, 1},
+      {(const void *)k_primal_stage, 1, 24, 2},
       {(const void *)k_aff_down, 2, 24, 8},      {(const void *)k_dual_leaf, 1, 0, 1},
       {(const void *)k_aff_prep, 1, 0, 1},       {(const void *)k_stage_lists, 1, 0, 1},
       {(const void *)k_dual_stage, 2, 0, 2},     {(const void *)k_param, 1, 0, 1},
@@ -174,7 +175,7 @@ bool stage_list_kernel(const void *kern) {
       (const void *)k_riccati_finish, (const void *)k_aff_prep,  (const void *)k_post_roll,
       (const void *)k_resid,      (const void *)k_pcorr,         (const void *)k_recover,
       (const void *)k_dual_stage, (const void *)k_dual_leaf,     (const void *)k_set_costs,
-      (const void *)k_refine_trial, (const void *)k_refine_accept};
+      (const void *)k_refine_trial, (const void *)k_refine_accept, (const void *)k_primal_stage};
   for (const void *k : table)
     if (k == kern) return true;
   return false;
@@ -437,7 +438,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       const int sdw = smem_dual_sweep(n, m, pmax, qmax);
       const struct { const void *fn; int dyn; } kk[] = {
           {(const void *)k_scan_check, smem_scan_check(n, m, pmax)}, {(const void *)k_terminal, sw},
-          {(const void *)k_primal_up, sw}, {(const void *)k_primal_down, sw}, {(const void *)k_rel_level, sl},
+          {(const void *)k_primal_up, sw}, {(const void *)k_primal_down, sw}, {(const void *)k_primal_stage, sw}, {(const void *)k_rel_level, sl},
           {(const void *)k_param, smem_param(n)}, {(const void *)k_elim, smem_elim(n, m, pmax)},
           {(const void *)k_lqr_up, smem_lqr_up(n, m)}, {(const void *)k_lqr_level, smem_lqr_level(n)},
           {(const void *)k_riccati_down, smem_riccati(n, m)},
@@ -641,6 +642,7 @@ int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, 
   int src = 0;
   for (int k = 0; k < gh.levels; k++, src ^= 1)
     TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
+  TRY(launch(h, k_primal_stage, g.nstage, sw, gst, g, sw));
   TRY(launch_sweep(h, gh.queue, k_primal_down, g.nslot, sw, gst, g, src, sw));
   const int sp = smem_param(n), se = smem_elim(n, m, pm);
   TRY(launch(h, k_param, g.nstage, sp, gst, g, sp));
@@ -1043,7 +1045,7 @@ int eclqr_time_kernel(eclqr_handle *h, const char *name) {
   }
   static const struct { const char *name; const void *fn; } table[] = {
       {"k_scan_check", (const void *)k_scan_check}, {"k_terminal", (const void *)k_terminal}, {"k_primal_up", (const void *)k_primal_up},
-      {"k_rel_level", (const void *)k_rel_level}, {"k_primal_down", (const void *)k_primal_down},
+      {"k_rel_level", (const void *)k_rel_level}, {"k_primal_down", (const void *)k_primal_down}, {"k_primal_stage", (const void *)k_primal_stage},
       {"k_param", (const void *)k_param}, {"k_elim", (const void *)k_elim},
       {"k_lqr_up", (const void *)k_lqr_up}, {"k_lqr_level", (const void *)k_lqr_level},
       {"k_riccati_down", (const void *)k_riccati_down}, {"k_riccati_finish", (const void *)k_riccati_finish},

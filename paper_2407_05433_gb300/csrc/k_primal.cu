@@ -302,6 +302,32 @@ __device__ int primal_down_stage(const Group &g, const ProbInfo &P, int i, doubl
 // up to rounding, and a stage whose domain was derived from one set while the
 // next stage's basis comes from the other leaves U_b'(A T + B Y) at that
 // rounding level, which the multipliers of Sec. 7 multiply by |nu_b|.
+// The stage's own rows (mixed and state-only) projected onto x_i, for every stage at
+// once: the down-sweep's step at a stage whose successor domain X_{i+1} is the whole
+// space (no rows) is this projection, the same call on the same matrix, so the sweep
+// takes the stored result there instead of computing it on its sequential chain.
+__global__ void k_primal_stage(Group g, int per_task) {
+  for_stages(g, [&](const int s) {
+    const StageInfo S = g.st[s];
+    const ProbInfo &P = g.prob[S.prob];
+    if (skipped_by_mask(g, S.prob)) return;
+    if (S.i >= P.N || scan_skipped(g, S.prob)) return;
+    const int n = g.n, m = g.m, tid = team_rank();
+    const int ldh = n + 1, ldm = m + n + 1;
+    double *sm = team_smem(per_task);
+    double *Hs = sm, *M = Hs + n * ldh, *scr = M + (n + g.pmax + g.qmax) * ldm;
+    int inc = 0;
+    const int rr = primal_down_stage(g, P, S.i, Hs, 0, M, scr, &inc);
+    double *Hp = stage_ws(g, s) + g.ws.Hpre;
+    for (int idx = tid; idx < rr * ldh; idx += TEAM) Hp[idx] = Hs[idx];
+    if (tid == 0) {
+      int *wi = stage_wi(g, s);
+      wi[SI_PRE] = rr;
+      wi[SI_PREINC] = inc;
+    }
+  });
+}
+
 static __device__ void primal_down_task(const Group &g, int fin, int t, int per_task);
 __global__ void k_primal_down(Group g, int fin, int per_task, int *queue) {
   for_tasks(g.nslot, queue, [&](int t) { primal_down_task(g, fin, t, per_task); });
@@ -336,7 +362,16 @@ static __device__ void primal_down_task(const Group &g, int fin, int t, int per_
   tsync();
   for (int i = start - 1; i >= a; --i) {
     int inc = 0;
-    rr = primal_down_stage(g, P, i, Hs, rr, M, scr, &inc);
+    if (rr == 0) {  // X_{i+1} = R^n: the stage's own projection, formed by k_primal_stage
+      const int *wi = stage_wi(g, P.st0 + i);
+      const double *Hp = stage_ws(g, P.st0 + i) + g.ws.Hpre;
+      rr = wi[SI_PRE];
+      inc = wi[SI_PREINC];
+      for (int idx = tid; idx < rr * ldh; idx += TEAM) Hs[idx] = Hp[idx];
+      tsync();
+    } else {
+      rr = primal_down_stage(g, P, i, Hs, rr, M, scr, &inc);
+    }
     if (i >= b) continue;  // the next chunk's stage: stored by that chunk
     const int s = P.st0 + i;
     double *H = stage_ws(g, s) + g.ws.H;

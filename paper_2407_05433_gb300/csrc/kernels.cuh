@@ -28,6 +28,7 @@ __global__ void k_terminal(Group g, int per_task);
 __global__ void k_primal_up(Group g, int per_task);
 __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task);
 __global__ void k_primal_down(Group g, int fin, int per_task, int *queue);
+__global__ void k_primal_stage(Group g, int per_task);
 __global__ void k_param(Group g, int per_task);
 __global__ void k_elim(Group g, int per_task);
 

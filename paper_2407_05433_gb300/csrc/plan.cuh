@@ -45,6 +45,7 @@ struct WsLayout {
                 // triangular (L L' = [Rbar Mbar'; Mbar Qbar]), and L^{-1} [rbar; qbar]
   int Rv;       // the Riccati QR's rows of the minimiser, (R_vv | R_vz | o_v), ld n + m + 1
   int gv;       // offset of the affine chain's stage map (k_aff_prep), n
+  int Hpre;     // the stage's own rows projected onto x_i (k_primal_stage), n x (n + 1)
   int stride;
 };
 
@@ -95,13 +96,16 @@ __host__ __device__ inline WsLayout make_ws_layout(int n, int m, int pmax, int q
   L.lt = take(n + m);
   L.Rv = take(m * (n + m + 1));
   L.gv = take(n);
+  L.Hpre = take(n * (n + 1));
   L.stride = (o + 3) & ~3;
   return L;
 }
 
 // per-stage ints
-// SI_TEYE: 1 when T_i is the identity and t_i = 0, bit for bit (X_i = R^n)
-enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_TEYE = 5, SI_STRIDE = 8 };
+// SI_TEYE: 1 when T_i is the identity and t_i = 0, bit for bit (X_i = R^n);
+// SI_PRE, SI_PREINC: rows and inconsistency of the stage's own rows projected onto x_i
+enum { SI_HROWS = 0, SI_UR = 1, SI_NBAR = 2, SI_MBAR = 3, SI_NUROWS = 4, SI_TEYE = 5, SI_PRE = 6, SI_PREINC = 7,
+       SI_STRIDE = 8 };
 // per-chunk-slot ints: rows, left dim, right dim (0 = unary/value)
 enum { CI_ROWS = 0, CI_NA = 1, CI_NB = 2, CI_ROWS2 = 3, CI_STRIDE = 4 };
 
