@@ -438,7 +438,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       const int sdw = smem_dual_sweep(n, m, pmax, qmax);
       const struct { const void *fn; int dyn; } kk[] = {
           {(const void *)k_scan_check, smem_scan_check(n, m, pmax)}, {(const void *)k_terminal, sw},
-          {(const void *)k_primal_up, sw}, {(const void *)k_primal_down, sw}, {(const void *)k_primal_stage, sw}, {(const void *)k_rel_level, sl},
+          {(const void *)k_primal_up, sw}, {(const void *)k_primal_down, sw}, {(const void *)k_primal_stage, smem_primal_stage(n, m, pmax, qmax)}, {(const void *)k_rel_level, sl},
           {(const void *)k_param, smem_param(n)}, {(const void *)k_elim, smem_elim(n, m, pmax)},
           {(const void *)k_lqr_up, smem_lqr_up(n, m)}, {(const void *)k_lqr_level, smem_lqr_level(n)},
           {(const void *)k_riccati_down, smem_riccati(n, m)},
@@ -642,7 +642,8 @@ int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, 
   int src = 0;
   for (int k = 0; k < gh.levels; k++, src ^= 1)
     TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
-  TRY(launch(h, k_primal_stage, g.nstage, sw, gst, g, sw));
+  const int sps = smem_primal_stage(n, m, pm, qm);
+  TRY(launch(h, k_primal_stage, g.nstage, sps, gst, g, sps));
   TRY(launch_sweep(h, gh.queue, k_primal_down, g.nslot, sw, gst, g, src, sw));
   const int sp = smem_param(n), se = smem_elim(n, m, pm);
   TRY(launch(h, k_param, g.nstage, sp, gst, g, sp));

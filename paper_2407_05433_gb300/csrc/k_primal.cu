@@ -22,6 +22,11 @@ __host__ int smem_primal_sweep(int n, int m, int pmax, int qmax) {
   int rows = 2 * n + pmax + qmax, ldm = m + 2 * n + 1;
   return 2 * n * (2 * n + 1) + rows * ldm + rows + 2 * ldm + 8;
 }
+// k_primal_stage: the output rows, the stage's own rows and wproject's scratch
+__host__ int smem_primal_stage(int n, int m, int pmax, int qmax) {
+  const int rows = pmax + qmax, ldm = m + n + 1;
+  return n * (n + 1) + rows * ldm + 2 * ldm + rows + ldm / 2 + 16;
+}
 __host__ int smem_rel_level(int n, int pmax, int qmax) {
   int nmax = n;  // relation endpoint dimensions never exceed n
   int rows = 4 * nmax, ldm = 3 * nmax + 1;
@@ -315,7 +320,7 @@ __global__ void k_primal_stage(Group g, int per_task) {
     const int n = g.n, m = g.m, tid = team_rank();
     const int ldh = n + 1, ldm = m + n + 1;
     double *sm = team_smem(per_task);
-    double *Hs = sm, *M = Hs + n * ldh, *scr = M + (n + g.pmax + g.qmax) * ldm;
+    double *Hs = sm, *M = Hs + n * ldh, *scr = M + (g.pmax + g.qmax) * ldm;
     int inc = 0;
     const int rr = primal_down_stage(g, P, S.i, Hs, 0, M, scr, &inc);
     double *Hp = stage_ws(g, s) + g.ws.Hpre;

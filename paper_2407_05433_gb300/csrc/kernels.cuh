@@ -15,6 +15,7 @@ __host__ int smem_lqr_level(int n);
 __host__ int smem_riccati(int n, int m);
 __host__ int smem_riccati_finish(int n, int m);
 __host__ int smem_set_costs(int n, int m);
+__host__ int smem_primal_stage(int n, int m, int pmax, int qmax);
 __host__ int smem_aff(int n, int m);
 __host__ int smem_dual_stage(int n, int m);
 __host__ int smem_dual_sweep(int n, int m, int pmax, int qmax);
