@@ -1165,7 +1165,10 @@ static int solve_once(const orc_problem *P, const orc_options *opt, double *x,
           ru[(size_t)i * m + a] = s;
         }
       }
-      ADDF((double)N * (2.0 * n * n + 2.0 * n * (n + m)));
+      /* T_{i+1} pi_{i+1} with T_{i+1} = I (ur = 0) is pi_{i+1}: not counted (as in step 5) */
+      int eye1 = 0;
+      for (int i = 0; i < N; i++) eye1 += ur[i + 1] == 0;
+      ADDF((double)N * (2.0 * n * n + 2.0 * n * (n + m)) - 2.0 * n * n * eye1);
       free(tp);
     }
     int wr = n + m + n;
@@ -1379,7 +1382,10 @@ static int solve_once(const orc_problem *P, const orc_options *opt, double *x,
           for (int a = 0; a < ur[i]; a++) s += UX(i, l, a) * nus[(size_t)i * n + a];
           lam[(size_t)i * n + l] = s;
         }
-      ADDF(2.0 * (N + 1) * n * n);
+      /* lambda_i = pi_i where T_i = I and nu_i has no coordinates (ur = 0): not counted */
+      int eye0 = 0;
+      for (int i = 0; i <= N; i++) eye0 += ur[i] == 0;
+      ADDF(2.0 * (N + 1) * n * n - 2.0 * n * n * eye0);
       for (int l = 0; l < n; l++) alpha[l] = -lam[l];
     }
 #undef STAGE_BLOCKS

@@ -90,13 +90,16 @@ __global__ void k_dual_stage(Group g, const double *x, const double *u, int per_
     const int r1 = win[SI_UR], nb1 = n - r1;
     const double *U1 = wn + g.ws.UT, *T1 = wn + g.ws.UT + r1, *pi1 = wn + g.ws.pi;
     // objective gradients (eq. objective-gradients) and T_{i+1} pi_{i+1}
+    const bool tne = win[SI_TEYE] != 0;  // T_{i+1} = I: T_{i+1} pi_{i+1} = pi_{i+1}
     for (int a = tid; a < n; a += TEAM) {
       double v = q[a];
       for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
       for (int j = 0; j < m; j++) v = fma(Mm[a * m + j], ui[j], v);
       gx[a] = v;
       double t = 0.0;
-      for (int j = 0; j < nb1; j++) t = fma(T1[a * n + j], pi1[j], t);
+      if (tne) t = pi1[a];
+      else
+        for (int j = 0; j < nb1; j++) t = fma(T1[a * n + j], pi1[j], t);
       tp[a] = t;
     }
     for (int a = tid; a < m; a += TEAM) {
@@ -407,10 +410,15 @@ __global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, doubl
     // lambda_i = T_i pi_i + U_i nu_i
     const double *UT = ws + g.ws.UT, *pi = ws + g.ws.pi;
     bool bad = false;
+    const bool te = stage_wi(g, s)[SI_TEYE] != 0;  // T_i = I, no nu_i: lambda_i = pi_i
     for (int a = tid; a < n; a += TEAM) {
       double v = 0.0;
-      for (int j = 0; j < r0; j++) v = fma(UT[a * n + j], nu0[j], v);
-      for (int j = 0; j < nb; j++) v = fma(UT[a * n + r0 + j], pi[j], v);
+      if (te) {
+        v = pi[a];
+      } else {
+        for (int j = 0; j < r0; j++) v = fma(UT[a * n + j], nu0[j], v);
+        for (int j = 0; j < nb; j++) v = fma(UT[a * n + r0 + j], pi[j], v);
+      }
       lam[P.olam + (size_t)i * n + a] = v;
       if (i == 0) alpha[P.oalpha + a] = -v;
       bad = bad || !isfinite(v);
