@@ -47,7 +47,7 @@ __host__ int smem_dual_leaf(int n, int m, int pmax, int qmax) {
 }
 
 // ---------------------------------------------------------------- per-stage blocks
-__global__ void k_dual_stage(Group g, const double *x, const double *u, int per_task) {
+__global__ void __launch_bounds__(256, 3) k_dual_stage(Group g, const double *x, const double *u, int per_task) {
   for_stages(g, [&](const int s) {
     const StageInfo S = g.st[s];
     const ProbInfo &P = g.prob[S.prob];
@@ -397,7 +397,7 @@ __global__ void k_dual_root(Group g, int per_task) {
 }
 
 // ---------------------------------------------------------------- leaves: mu_i, eta_i, lambda_i, alpha, eta_N
-__global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task) {
+__global__ void __launch_bounds__(256, 4) k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task) {
   for_stages(g, [&](const int s) {
     const StageInfo S = g.st[s];
     const ProbInfo &P = g.prob[S.prob];

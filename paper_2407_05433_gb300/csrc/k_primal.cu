@@ -449,7 +449,9 @@ __global__ void k_param(Group g, int per_task) {
 }
 
 // ----------------------------------------------------------- stage elimination (Sec. 5)
-__global__ void k_elim(Group g, int per_task) {
+// at most 64 registers a thread: with four-warp teams (n >= 16) 80 registers left 6 CTAs
+// per SM where 64 leave 8 (n = 16: 40 ms against 45 over the group)
+__global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task) {
   for_stages(g, [&](const int s) {
     const StageInfo S = g.st[s];
     const ProbInfo &P = g.prob[S.prob];

@@ -31,7 +31,7 @@ __global__ void k_rel_level(Group g, int src, int d, int fail_code, int per_task
 __global__ void k_primal_down(Group g, int fin, int per_task, int *queue);
 __global__ void k_primal_stage(Group g, int per_task);
 __global__ void k_param(Group g, int per_task);
-__global__ void k_elim(Group g, int per_task);
+__global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task);
 
 // reduced LQR, affine chains, recovery (k_lqr.cu)
 enum { AFF_ROLL_ = 0, AFF_CROLL_ = 1, AFF_PLIN_ = 2, AFF_NU_ = 3 };
@@ -52,12 +52,12 @@ __global__ void k_recover(Group g, double *x, double *u);
 __global__ void k_dims(Group g, int *nbar, int *mbar);
 
 // multipliers and residual (k_dual.cu)
-__global__ void k_dual_stage(Group g, const double *x, const double *u, int per_task);
+__global__ void __launch_bounds__(256, 3) k_dual_stage(Group g, const double *x, const double *u, int per_task);
 __global__ void k_dual_terminal(Group g, int per_task);
 __global__ void k_dual_up(Group g, int per_task);
 __global__ void k_dual_down(Group g, int fin, int per_task);
 __global__ void k_dual_root(Group g, int per_task);
-__global__ void k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task);
+__global__ void __launch_bounds__(256, 4) k_dual_leaf(Group g, double *lam, double *mu, double *eta, double *alpha, int per_task);
 __global__ void k_param_grads(Group g, Sol w, Sol wb, GradOut o);
 __global__ void k_set_costs(Group g, int per_task);
 __global__ void k_kkt(Group g, const double *s0, const double *x, const double *u, const double *lam,
