@@ -117,8 +117,8 @@ typedef struct {
                        * 0 (default) = per kernel: 4 when a launch has fewer tasks than
                        * SMs; with at least 4 tasks per SM the kernel's measured best for
                        * the group's n (1 for the per-problem sweeps and the small
-                       * per-stage kernels, 1 or 4 for the stage elimination, 8 for the
-                       * affine-chain sweep); in between that but at least 2            */
+                       * per-stage kernels, 1 or 4 for the stage elimination, 2 or 8 for
+                       * the affine-chain sweep); in between that but at least 2          */
   int32_t scan_skip;  /* 1 (default): take the shortcut of Sec. 6 (complete algorithm and
                        * complexity) where it applies: a problem without state-only or
                        * terminal rows whose every stage's mixed rows leave no row on x_i
