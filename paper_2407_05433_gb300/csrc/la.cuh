@@ -1371,9 +1371,71 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
     if (fabs(M[i * ld + off]) > tau_inc * om) bad = 1;
   res.inconsistent = __syncthreads_or(bad);
   wnorm_rows_out(M, ld, res.k1, res.kc, ne, nk, off, outC, ldo);
-  // E: compress the remaining cost rows over the kept columns (no pivoting)
+  // E: compress the remaining cost rows over the kept columns (no pivoting).  Rows with
+  // no entry in the first kept columns (cost rows of an operand that the eliminated
+  // variables never touched) are moved last, ordered by their first nonzero kept column
+  // (exact zeros, compared as bit patterns), and each Householder step works only on
+  // the rows with an entry in its column or before it: the others are zero there and a
+  // reflector would leave them unchanged.  The rows' order does not change the factor
+  // beyond rounding and row signs.  The rows move in place, one thread per column
+  // following the permutation's cycles.
   int ke = kk;
-  ke = hh_diag_steps(M, ld, ke, r, ne, off, nc, v, w, 0.0, false);
+  const int R = r - kk;
+  if (R > 1 && nk > 0) {
+    int *lead = (int *)v, *rank = lead + R;  // v holds r doubles: 2 r ints
+    for (int i = tid; i < R; i += TEAM) {
+      int c = nk;
+      for (int j = 0; j < nk; j++)
+        if ((__double_as_longlong(M[(kk + i) * ld + ne + j]) << 1) != 0) { c = j; break; }
+      lead[i] = c;
+    }
+    tsync();
+    for (int i = tid; i < R; i += TEAM) {
+      int rk = 0;
+      for (int j = 0; j < R; j++) rk += (lead[j] < lead[i] || (lead[j] == lead[i] && j < i)) ? 1 : 0;
+      rank[i] = rk;  // row i moves to position rank[i]
+    }
+    for (int c = tid; c < nk; c += TEAM) {
+      int cnt = 0;
+      for (int i = 0; i < R; i++) cnt += lead[i] <= c ? 1 : 0;
+      done[c] = kk + cnt;  // rows [kk, done[c]) may have an entry in kept column c
+    }
+    tsync();
+    for (int i = tid; i < R; i += TEAM) {  // lead[i] <- i leads its cycle (its smallest index)
+      int j = rank[i];
+      bool first = true;
+      while (j != i) {
+        if (j < i) first = false;
+        j = rank[j];
+      }
+      lead[i] = first ? 1 : 0;
+    }
+    tsync();
+    for (int c = tid; c <= nk; c += TEAM) {
+      double *col = M + (size_t)kk * ld + ne + c;
+      for (int i = 0; i < R; i++) {
+        if (!lead[i]) continue;
+        double carry = col[(size_t)i * ld];
+        int j = rank[i];
+        while (j != i) {
+          const double t = col[(size_t)j * ld];
+          col[(size_t)j * ld] = carry;
+          carry = t;
+          j = rank[j];
+        }
+        col[(size_t)i * ld] = carry;
+      }
+    }
+    tsync();
+    for (int col = ne; col < off && ke < r; col++) {
+      const int re = done[col - ne];
+      if (re <= ke) continue;  // no row from ke on has an entry in this column
+      HHLayout L = hh_layout(nc - col, re - ke);
+      if (hh_core(M, ld, ke, re, col, nullptr, col, nc - col, L, v, w, 0.0) > 0.0) ke++;
+    }
+  } else {
+    ke = hh_diag_steps(M, ld, ke, r, ne, off, nc, v, w, 0.0, false);
+  }
   res.kq = ke - kk;
   for (int idx = tid; idx < res.kq * (nk + 1); idx += TEAM) {
     int a = idx / (nk + 1), j = idx - a * (nk + 1);
