@@ -1315,6 +1315,45 @@ struct LseResult {
   int k1, k2, kc, kq, inconsistent;
 };
 
+// Stable in-place reorder of the rows [r0, r0 + R) of M, columns [c0, c1), by key[i]
+// ascending (ties keep their order): each thread moves whole columns along the cycles of
+// the permutation.  key and rank are scratch of R ints each (key is overwritten).
+static __device__ void rows_by_key(double *M, int ld, int r0, int R, int c0, int c1, int *key, int *rank) {
+  const int tid = team_rank();
+  for (int i = tid; i < R; i += TEAM) {
+    int rk = 0;
+    for (int j = 0; j < R; j++) rk += (key[j] < key[i] || (key[j] == key[i] && j < i)) ? 1 : 0;
+    rank[i] = rk;  // row i moves to position rank[i]
+  }
+  tsync();
+  for (int i = tid; i < R; i += TEAM) {  // key[i] <- i leads its cycle (its smallest index)
+    int j = rank[i];
+    bool first = true;
+    while (j != i) {
+      if (j < i) first = false;
+      j = rank[j];
+    }
+    key[i] = first ? 1 : 0;
+  }
+  tsync();
+  for (int c = c0 + tid; c < c1; c += TEAM) {
+    double *col = M + (size_t)r0 * ld + c;
+    for (int i = 0; i < R; i++) {
+      if (!key[i]) continue;
+      double carry = col[(size_t)i * ld];
+      int j = rank[i];
+      while (j != i) {
+        const double t = col[(size_t)j * ld];
+        col[(size_t)j * ld] = carry;
+        carry = t;
+        j = rank[j];
+      }
+      col[(size_t)i * ld] = carry;
+    }
+  }
+  tsync();
+}
+
 static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne, int nk, double tau_rank,
                                       double tau_inc, double *outC, double *outQ, int ldo, double *scr) {
   const int tid = team_rank();
@@ -1357,11 +1396,29 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
       tsync();
     }
   }
-  // C
+  // C, on the cost rows with an entry in an eliminated column: the others (cost rows of
+  // an operand that never involved these variables) are moved after them, unchanged by
+  // the steps, which would leave them as they are
+  int rce = r;
+  if (rq > 1 && ne > 0) {
+    int *has = (int *)v, *rank = has + rq;  // v holds r doubles
+    for (int i = tid; i < rq; i += TEAM) {
+      int h = 1;
+      for (int j = 0; j < ne; j++)
+        if ((__double_as_longlong(M[(rc + i) * ld + j]) << 1) != 0) { h = 0; break; }
+      has[i] = h;  // 0: has an entry in an eliminated column (sorts first)
+    }
+    tsync();
+    int cnt = 0;
+    for (int i = 0; i < rq; i++) cnt += has[i] == 0 ? 1 : 0;
+    rce = rc + cnt;
+    tsync();
+    if (cnt < rq) rows_by_key(M, ld, rc, rq, 0, nc, has, rank);
+  }
   double nuq2, om_unused;
-  wcol_max(M, ld, rc, r, ne, done, -1, nuq2, om_unused);
+  wcol_max(M, ld, rc, rce, ne, done, -1, nuq2, om_unused);
   const double nuq = sqrt(nuq2);
-  res.k2 = hh_pivoted(M, ld, rc, r, 0, ne, 0, nc, done, nullptr, tau_rank * nuq, v, w);
+  res.k2 = hh_pivoted(M, ld, rc, rce, 0, ne, 0, nc, done, nullptr, tau_rank * nuq, v, w);
   const int kk = rc + res.k2;
   // D
   res.kc = hh_pivoted(M, ld, res.k1, rc, ne, off, ne, nc, done, nullptr, thr, v, w);
@@ -1390,43 +1447,12 @@ static __device__ LseResult wlse_elim(double *M, int ld, int rc, int rq, int ne,
       lead[i] = c;
     }
     tsync();
-    for (int i = tid; i < R; i += TEAM) {
-      int rk = 0;
-      for (int j = 0; j < R; j++) rk += (lead[j] < lead[i] || (lead[j] == lead[i] && j < i)) ? 1 : 0;
-      rank[i] = rk;  // row i moves to position rank[i]
-    }
     for (int c = tid; c < nk; c += TEAM) {
       int cnt = 0;
       for (int i = 0; i < R; i++) cnt += lead[i] <= c ? 1 : 0;
       done[c] = kk + cnt;  // rows [kk, done[c]) may have an entry in kept column c
     }
-    tsync();
-    for (int i = tid; i < R; i += TEAM) {  // lead[i] <- i leads its cycle (its smallest index)
-      int j = rank[i];
-      bool first = true;
-      while (j != i) {
-        if (j < i) first = false;
-        j = rank[j];
-      }
-      lead[i] = first ? 1 : 0;
-    }
-    tsync();
-    for (int c = tid; c <= nk; c += TEAM) {
-      double *col = M + (size_t)kk * ld + ne + c;
-      for (int i = 0; i < R; i++) {
-        if (!lead[i]) continue;
-        double carry = col[(size_t)i * ld];
-        int j = rank[i];
-        while (j != i) {
-          const double t = col[(size_t)j * ld];
-          col[(size_t)j * ld] = carry;
-          carry = t;
-          j = rank[j];
-        }
-        col[(size_t)i * ld] = carry;
-      }
-    }
-    tsync();
+    rows_by_key(M, ld, kk, R, ne, nc, lead, rank);
     for (int col = ne; col < off && ke < r; col++) {
       const int re = done[col - ne];
       if (re <= ke) continue;  // no row from ke on has an entry in this column
