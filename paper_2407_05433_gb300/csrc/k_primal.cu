@@ -40,12 +40,14 @@ __host__ int smem_scan_check(int n, int m, int pmax) {
 __host__ int smem_param(int n) { return n * (n + 1) + n * n + n * n + n + n + 4 * n + 8 + n; }
 // k_elim's shared memory: the blocks live through the whole stage (A T, Q_m, Y, the
 // vectors, the QR scratch and permutation) and one region that three phases use in
-// turn: Lemma 4's solve (H_{i+1}, Gamma, [Phi | gamma], the factor and the solution),
-// the substitution products, and the bordered stage Hessian.
+// turn: Lemma 4's solve (Gamma, whose block the solve's scratch reuses once the QR has
+// copied it, [Phi | gamma], the factor and the solution), the substitution products,
+// and the bordered stage Hessian.  H_{i+1} is read where it lies in the workspace.
 __host__ __device__ inline int elim_union(int n, int m, int pmax) {
   const int rows = pmax + n;
-  const int ab = n * (n + 1) + rows * m + rows * (n + 1) + m * rows + 2 * m * (n + 1);
-  const int c = 2 * n * n + 3 * n * m + m * m;
+  const int gx = rows * m > m * (n + 1) ? rows * m : m * (n + 1);
+  const int ab = gx + rows * (n + 1) + m * rows + m * (n + 1);
+  const int c = n * n + 3 * n * m + m * m;
   const int d = (n + m + 1) * (n + m + 1);
   return ab > c ? (ab > d ? ab : d) : (c > d ? c : d);
 }
@@ -484,16 +486,16 @@ __global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task) {
     double *ys = Ry + m, *scr = ys + m;    // scratch >= 2n + 2 rows
     double *U = vec + 12 * n + 8 * m + 2 * rmax + 16;  // the phases' region
     // Lemma 4's solve
-    double *Hs = U;                        // n x (n+1)
-    double *Gm = Hs + n * (n + 1);         // rmax x m
-    double *Rh = Gm + rmax * m;            // rmax x (n+1)
+    const int gx = rmax * m > m * (n + 1) ? rmax * m : m * (n + 1);
+    double *Gm = U;                        // rmax x m: Gamma, copied into Wt by the QR
+    double *X1 = Gm;                       // m x (n+1) scratch for the min-norm solve, after the QR
+    double *Rh = Gm + gx;                  // rmax x (n+1)
     double *Wt = Rh + rmax * (n + 1);      // m x rmax
     double *Sol = Wt + m * rmax;           // m x (n+1)
-    double *X1 = Sol + m * (n + 1);        // m x (n+1) scratch for the min-norm solve
     // the substitution products
-    double *QT = U;                        // n x n
-    double *X2 = QT + n * n;               // n x n  scratch
-    double *Mz = X2 + n * n;               // n x m
+    double *QT = U;                        // n x n: Q T, read only by Q^z
+    double *X2 = QT;                       // n x n: M^z Y, after Q^z
+    double *Mz = QT + n * n;               // n x m
     double *RY = Mz + n * m;               // m x n
     double *BZ = RY + n * m;               // n x m
     double *RZ = BZ + n * m;               // m x m
@@ -510,14 +512,12 @@ __global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task) {
         Atc[l] = s0;
       }
     }
-    for (int idx = tid; idx < r1 * (n + 1); idx += TEAM) Hs[idx] = Hn[idx];
-    tsync();
     // Gamma = [D; Hn B],  [Phi | gamma] = [C T | C t + d; Hn A T | Hn (A t + c) + hn]
     for (int idx = tid; idx < S.p * m; idx += TEAM) {
       int a = idx / m, j = idx - a * m;
       Gm[a * m + j] = g.D[P.oD + (size_t)(S.prow + a) * m + j];
     }
-    wgemm<false, false>(r1, m, n, 1.0, Hs, n + 1, B, m, 0.0, Gm + S.p * m, m);
+    wgemm<false, false>(r1, m, n, 1.0, Hn, n + 1, B, m, 0.0, Gm + S.p * m, m);
     for (int idx = tid; idx < S.p * (nb + 1); idx += TEAM) {
       int a = idx / (nb + 1), j = idx - a * (nb + 1);
       const double *Cr = g.C + P.oC + (size_t)(S.prow + a) * n;
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task) {
     }
     for (int idx = tid; idx < r1 * (nb + 1); idx += TEAM) {
       int a = idx / (nb + 1), j = idx - a * (nb + 1);
-      const double *hr = Hs + a * (n + 1);
+      const double *hr = Hn + a * (n + 1);
       double s0 = 0.0;
       if (j < nb) {
         for (int l = 0; l < n; l++) s0 = fma(hr[l], AT[l * n + j], s0);
