@@ -40,20 +40,26 @@ __host__ int smem_scan_check(int n, int m, int pmax) {
 __host__ int smem_param(int n) { return n * (n + 1) + n * n + n * n + n + n + 4 * n + 8 + n; }
 // k_elim's shared memory: the blocks live through the whole stage (A T, Q_m, Y, the
 // vectors, the QR scratch and permutation) and one region that three phases use in
-// turn: Lemma 4's solve (Gamma, whose block the solve's scratch reuses once the QR has
-// copied it, [Phi | gamma], the factor and the solution), the substitution products,
-// and the bordered stage Hessian.  H_{i+1} is read where it lies in the workspace.
+// turn: Lemma 4's solve (Gamma, then [Phi | gamma] in the same block once the QR has
+// copied Gamma; the factor, the solution and the solve's scratch), the substitution
+// products, and the bordered stage Hessian.  H_{i+1} is read where it lies in the
+// workspace.
+__host__ __device__ inline int elim_vec(int n, int m, int pmax) {
+  const int rows = pmax + n;
+  // A t + c, c_v, Q t + q, q^z (n each); r^z, R y + r^z, y (m each); the QR's scratch
+  // (m + max(m, rows)); the permutation (rows ints)
+  return 4 * n + 4 * m + (m > rows ? m : rows) + (rows + 1) / 2 + 2;
+}
 __host__ __device__ inline int elim_union(int n, int m, int pmax) {
   const int rows = pmax + n;
-  const int gx = rows * m > m * (n + 1) ? rows * m : m * (n + 1);
-  const int ab = gx + rows * (n + 1) + m * rows + m * (n + 1);
+  const int gr = rows * m > rows * (n + 1) ? rows * m : rows * (n + 1);
+  const int ab = gr + m * rows + 2 * m * (n + 1);
   const int c = n * n + 3 * n * m + m * m;
   const int d = (n + m + 1) * (n + m + 1);
   return ab > c ? (ab > d ? ab : d) : (c > d ? c : d);
 }
 __host__ int smem_elim(int n, int m, int pmax) {
-  const int rows = pmax + n;
-  return n * n + m * m + n * m + 12 * n + 8 * m + 2 * rows + 16 + elim_union(n, m, pmax) + 8;
+  return n * n + m * m + n * m + elim_vec(n, m, pmax) + elim_union(n, m, pmax) + 8;
 }
 
 // ----------------------------------------------------------- shortcut test (Sec. 6)
@@ -481,17 +487,18 @@ __global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task) {
     double *AT = sm;                       // n x n (ld n)
     double *Qm = AT + n * n;               // m x m: Q of Gamma' (Z = its last columns)
     double *Yw = Qm + m * m;               // m x n  (ld n): Y
-    double *vec = Yw + n * m;              // 12 n + 8 m
+    double *vec = Yw + n * m;              // elim_vec doubles
     double *Atc = vec, *cv = Atc + n, *Qtq = cv + n, *qz = Qtq + n, *rz = qz + n, *Ry = rz + m;
-    double *ys = Ry + m, *scr = ys + m;    // scratch >= 2n + 2 rows
-    double *U = vec + 12 * n + 8 * m + 2 * rmax + 16;  // the phases' region
+    double *ys = Ry + m, *scr = ys + m;    // the QR's scratch: m + max(m, rmax)
+    int *perm = (int *)(scr + m + (m > rmax ? m : rmax));
+    double *U = vec + elim_vec(n, m, g.pmax);  // the phases' region
     // Lemma 4's solve
-    const int gx = rmax * m > m * (n + 1) ? rmax * m : m * (n + 1);
+    const int gr = rmax * m > rmax * (n + 1) ? rmax * m : rmax * (n + 1);
     double *Gm = U;                        // rmax x m: Gamma, copied into Wt by the QR
-    double *X1 = Gm;                       // m x (n+1) scratch for the min-norm solve, after the QR
-    double *Rh = Gm + gx;                  // rmax x (n+1)
-    double *Wt = Rh + rmax * (n + 1);      // m x rmax
+    double *Rh = U;                        // rmax x (n+1): [Phi | gamma], formed after the QR
+    double *Wt = U + gr;                   // m x rmax
     double *Sol = Wt + m * rmax;           // m x (n+1)
+    double *X1 = Sol + m * (n + 1);        // m x (n+1) scratch for the min-norm solve
     // the substitution products
     double *QT = U;                        // n x n: Q T, read only by Q^z
     double *X2 = QT;                       // n x n: M^z Y, after Q^z
@@ -499,7 +506,6 @@ __global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task) {
     double *RY = Mz + n * m;               // m x n
     double *BZ = RY + n * m;               // n x m
     double *RZ = BZ + n * m;               // m x m
-    int *perm = (int *)(scr + 4 * n + 2 * m + 2 * rmax);
     // A T, A t + c
     if (te) {
       for (int idx = tid; idx < n * n; idx += TEAM) AT[idx] = A[idx];
@@ -512,12 +518,18 @@ __global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task) {
         Atc[l] = s0;
       }
     }
-    // Gamma = [D; Hn B],  [Phi | gamma] = [C T | C t + d; Hn A T | Hn (A t + c) + hn]
+    // Gamma = [D; Hn B]
     for (int idx = tid; idx < S.p * m; idx += TEAM) {
       int a = idx / m, j = idx - a * m;
       Gm[a * m + j] = g.D[P.oD + (size_t)(S.prow + a) * m + j];
     }
     wgemm<false, false>(r1, m, n, 1.0, Hn, n + 1, B, m, 0.0, Gm + S.p * m, m);
+    // Lemma 4: Z = null(Gamma), [Y | y] = -Gamma^- [Phi | gamma] (min norm)
+    // the small form only: this kernel runs many CTAs to an SM, and the large form's
+    // registers and static scratch would cost it occupancy
+    const int rank = wtqr_small(Gm, m, rows, m, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qm, m, perm, scr);
+    // [Phi | gamma] = [C T | C t + d; Hn A T | Hn (A t + c) + hn], in Gamma's block (the QR
+    // has copied Gamma into Wt)
     for (int idx = tid; idx < S.p * (nb + 1); idx += TEAM) {
       int a = idx / (nb + 1), j = idx - a * (nb + 1);
       const double *Cr = g.C + P.oC + (size_t)(S.prow + a) * n;
@@ -545,10 +557,6 @@ __global__ void __launch_bounds__(256, 4) k_elim(Group g, int per_task) {
       Rh[(S.p + a) * (nb + 1) + j] = s0;
     }
     tsync();
-    // Lemma 4: Z = null(Gamma), [Y | y] = -Gamma^- [Phi | gamma] (min norm)
-    // the small form only: this kernel runs many CTAs to an SM, and the large form's
-    // registers and static scratch would cost it occupancy
-    const int rank = wtqr_small(Gm, m, rows, m, g.tau_rank, Wt, (rows > 0 ? rows : 1), Qm, m, perm, scr);
     const double rs = wtqr_solve(Wt, (rows > 0 ? rows : 1), Qm, m, perm, rows, m, rank, Rh, nb + 1, nb + 1,
                                  Sol, nb + 1, X1, nb + 1);
     if (tid == 0 && rs > g.tau_inc) set_status(g, S.prob, ST_RANK_INCONSISTENT);
