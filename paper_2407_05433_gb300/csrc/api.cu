@@ -412,13 +412,18 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
     // longest horizons first: the tasks of a launch are issued in this order, so the
     // longest sweeps start in the first wave instead of finishing alone in the last
     std::stable_sort(gh.ids.begin(), gh.ids.end(), [&](int a, int b) { return d->N[a] > d->N[b]; });
-    int pmax = 0, qmax = 0;
+    int pmax = 0, qmax = 0, wmax = 0;
     for (int j : gh.ids) {
-      for (long long i = 0; i < d->N[j]; i++) pmax = std::max(pmax, d->p[pstage[j] + i]);
+      for (long long i = 0; i < d->N[j]; i++) {
+        pmax = std::max(pmax, d->p[pstage[j] + i]);
+        wmax = std::max(wmax, d->p[pstage[j] + i] + d->q[qstage[j] + i]);
+      }
       for (long long i = 0; i <= d->N[j]; i++) qmax = std::max(qmax, d->q[qstage[j] + i]);
+      wmax = std::max(wmax, d->q[qstage[j] + d->N[j]]);
     }
     g.pmax = pmax;
     g.qmax = qmax;
+    g.wmax = wmax;
     // every kernel's shared memory must fit one task (one CTA)
     {
       const int n = g.n, m = g.m;
@@ -426,7 +431,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
                                  smem_elim(n, m, pmax), smem_lqr_up(n, m), smem_lqr_level(n), smem_riccati(n, m),
                                  smem_riccati_finish(n, m),
                                  smem_aff(n, m), smem_dual_stage(n, m), smem_dual_sweep(n, m, pmax, qmax),
-                                 smem_dual_leaf(n, m, pmax, qmax), smem_scan_check(n, m, pmax)});
+                                 smem_dual_leaf(n, m, wmax), smem_scan_check(n, m, pmax)});
       if ((size_t)need * sizeof(double) > (size_t)kMaxSmemBytes) {
         for (auto &x : h->groups) cudaFree(x.dmem);
         delete h;
@@ -438,7 +443,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
       const int sdw = smem_dual_sweep(n, m, pmax, qmax);
       const struct { const void *fn; int dyn; } kk[] = {
           {(const void *)k_scan_check, smem_scan_check(n, m, pmax)}, {(const void *)k_terminal, sw},
-          {(const void *)k_primal_up, sw}, {(const void *)k_primal_down, sw}, {(const void *)k_primal_stage, smem_primal_stage(n, m, pmax, qmax)}, {(const void *)k_rel_level, sl},
+          {(const void *)k_primal_up, sw}, {(const void *)k_primal_down, sw}, {(const void *)k_primal_stage, smem_primal_stage(n, m, wmax)}, {(const void *)k_rel_level, sl},
           {(const void *)k_param, smem_param(n)}, {(const void *)k_elim, smem_elim(n, m, pmax)},
           {(const void *)k_lqr_up, smem_lqr_up(n, m)}, {(const void *)k_lqr_level, smem_lqr_level(n)},
           {(const void *)k_riccati_down, smem_riccati(n, m)},
@@ -446,7 +451,7 @@ int eclqr_create(const eclqr_desc *d, const eclqr_options *opt, eclqr_handle **o
           {(const void *)k_aff_level, sa}, {(const void *)k_aff_down, sa}, {(const void *)k_resid, 3 * n + 2 * m},
           {(const void *)k_pcorr, n + m + m * m}, {(const void *)k_dual_stage, smem_dual_stage(n, m)},
           {(const void *)k_dual_terminal, sdw}, {(const void *)k_dual_up, sdw}, {(const void *)k_dual_down, sdw},
-          {(const void *)k_dual_root, sdw}, {(const void *)k_dual_leaf, smem_dual_leaf(n, m, pmax, qmax)}};
+          {(const void *)k_dual_root, sdw}, {(const void *)k_dual_leaf, smem_dual_leaf(n, m, wmax)}};
       int optin = 0;
       int rc = (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) == cudaSuccess)
                    ? ECLQR_OK : ECLQR_ECUDA;
@@ -642,7 +647,7 @@ int run_build(eclqr_handle *h, GroupHost &gh, const Group &g, cudaStream_t gst, 
   int src = 0;
   for (int k = 0; k < gh.levels; k++, src ^= 1)
     TRY(launch(h, k_rel_level, g.nslot, sl, gst, g, src, 1 << k, (int)ST_INFEASIBLE_SUFFIX, sl));
-  const int sps = smem_primal_stage(n, m, pm, qm);
+  const int sps = smem_primal_stage(n, m, g.wmax);
   TRY(launch(h, k_primal_stage, g.nstage, sps, gst, g, sps));
   TRY(launch_sweep(h, gh.queue, k_primal_down, g.nslot, sw, gst, g, src, sw));
   const int sp = smem_param(n), se = smem_elim(n, m, pm);
@@ -695,7 +700,7 @@ int run_mult(eclqr_handle *h, const GroupHost &gh, const Group &g, cudaStream_t 
              double *lam, double *mu, double *eta, double *alpha) {
   const int n = g.n, m = g.m, pm = g.pmax, qm = g.qmax;
   const int sd = smem_dual_stage(n, m), sw = smem_dual_sweep(n, m, pm, qm), sl = smem_rel_level(n, pm, qm);
-  const int sf = smem_dual_leaf(n, m, pm, qm);
+  const int sf = smem_dual_leaf(n, m, g.wmax);
   TRY(launch(h, k_dual_stage, g.nstage, sd, gst, g, x, u, sd));
   TRY(launch(h, k_dual_terminal, g.nprob, sw, gst, g, sw));
   TRY(launch(h, k_dual_up, g.nslot, sw, gst, g, sw));

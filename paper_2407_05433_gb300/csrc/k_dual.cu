@@ -41,8 +41,8 @@ __host__ int smem_dual_sweep(int n, int m, int pmax, int qmax) {
   const int solve = dual_solve_scratch(n, rows);
   return base + (solve <= rows * ldm ? 0 : solve) + 16;
 }
-__host__ int smem_dual_leaf(int n, int m, int pmax, int qmax) {
-  int w = pmax + qmax, rows = n + m;
+__host__ int smem_dual_leaf(int n, int m, int wmax) {
+  int w = wmax, rows = n + m;
   return rows * w + rows + w * rows + w * w + w + rows + 2 * (rows + w) + rows + 16;
 }
 
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(256, 4) k_dual_leaf(Group g, double *lam, doub
     const int w = (i < P.N) ? S.p + S.q : S.q;
     if (w == 0) return;
     double *sm = team_smem(per_task);
-    const int wmax = g.pmax + g.qmax, rmax = n + m;
+    const int wmax = g.wmax, rmax = n + m;
     double *F = sm, *rhs = F + rmax * wmax, *Wt = rhs + rmax, *Qf = Wt + wmax * rmax, *X = Qf + wmax * wmax;
     double *Ys = X + wmax, *tq = Ys + rmax;
     int *perm = (int *)(tq + 2 * (rmax + wmax));

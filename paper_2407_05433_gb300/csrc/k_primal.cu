@@ -23,8 +23,8 @@ __host__ int smem_primal_sweep(int n, int m, int pmax, int qmax) {
   return 2 * n * (2 * n + 1) + rows * ldm + rows + 2 * ldm + 8;
 }
 // k_primal_stage: the output rows, the stage's own rows and wproject's scratch
-__host__ int smem_primal_stage(int n, int m, int pmax, int qmax) {
-  const int rows = pmax + qmax, ldm = m + n + 1;
+__host__ int smem_primal_stage(int n, int m, int wmax) {
+  const int rows = wmax, ldm = m + n + 1;
   return n * (n + 1) + rows * ldm + 2 * ldm + rows + ldm / 2 + 16;
 }
 __host__ int smem_rel_level(int n, int pmax, int qmax) {
@@ -328,7 +328,7 @@ __global__ void k_primal_stage(Group g, int per_task) {
     const int n = g.n, m = g.m, tid = team_rank();
     const int ldh = n + 1, ldm = m + n + 1;
     double *sm = team_smem(per_task);
-    double *Hs = sm, *M = Hs + n * ldh, *scr = M + (g.pmax + g.qmax) * ldm;
+    double *Hs = sm, *M = Hs + n * ldh, *scr = M + g.wmax * ldm;
     int inc = 0;
     const int rr = primal_down_stage(g, P, S.i, Hs, 0, M, scr, &inc);
     double *Hp = stage_ws(g, s) + g.ws.Hpre;

@@ -15,11 +15,11 @@ __host__ int smem_lqr_level(int n);
 __host__ int smem_riccati(int n, int m);
 __host__ int smem_riccati_finish(int n, int m);
 __host__ int smem_set_costs(int n, int m);
-__host__ int smem_primal_stage(int n, int m, int pmax, int qmax);
+__host__ int smem_primal_stage(int n, int m, int wmax);
 __host__ int smem_aff(int n, int m);
 __host__ int smem_dual_stage(int n, int m);
 __host__ int smem_dual_sweep(int n, int m, int pmax, int qmax);
-__host__ int smem_dual_leaf(int n, int m, int pmax, int qmax);
+__host__ int smem_dual_leaf(int n, int m, int wmax);
 __host__ int smem_scan_check(int n, int m, int pmax);
 
 // primal scan and elimination (k_primal.cu)

@@ -111,6 +111,7 @@ enum { CI_ROWS = 0, CI_NA = 1, CI_NB = 2, CI_ROWS2 = 3, CI_STRIDE = 4 };
 
 struct Group {
   int n, m, pmax, qmax;
+  int wmax;  // the most rows of one stage: p_i + q_i for i < N, q_N at N
   int nprob, nstage, nslot;
   const ProbInfo *prob;
   const StageInfo *st;
