@@ -510,7 +510,15 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
 // (equality rows divided by max(1, largest |coefficient|, |offset|)) is reduced
 // into resid[id] and, with parts set, into parts[4 id + k] for k = initial,
 // dynamics, equalities, stationarity.  Any NaN in a row reaches the norm.
-__global__ void k_kkt(Group g, const double *s0, const double *x, const double *u, const double *lam,
+// v + sum_j a[j sa] x[j], in order; unrolled by two, so that the residual kernel needs
+// under 80 registers a thread and 25 one-warp CTAs fit an SM (16 at 128 registers)
+__device__ __forceinline__ double kkt_dot(double v, const double *a, int sa, const double *x, int len) {
+#pragma unroll 2
+  for (int j = 0; j < len; j++) v = fma(a[(size_t)j * sa], x[j], v);
+  return v;
+}
+
+__global__ void __launch_bounds__(256, 3) k_kkt(Group g, const double *s0, const double *x, const double *u, const double *lam,
                       const double *mu, const double *eta, const double *alpha, KktRows rows, double *resid,
                       double *parts) {
   for_stages(g, [&](const int s) {
@@ -532,6 +540,7 @@ __global__ void k_kkt(Group g, const double *s0, const double *x, const double *
     for (int k = tid; k < S.q; k += TEAM) {
       const double *Ek = g.E + P.oE + (size_t)(S.qrow + k) * n;
       double e = g.e[P.oe + S.qrow + k], v = e, sc = nanmax(1.0, fabs(e));
+#pragma unroll 2
       for (int j = 0; j < n; j++) { v = fma(Ek[j], xi[j], v); sc = nanmax(sc, fabs(Ek[j])); }
       r2 = nanmax(r2, fabs(v) / sc);
       if (wr) rows.e[P.oe + S.qrow + k] = v;
@@ -545,44 +554,41 @@ __global__ void k_kkt(Group g, const double *s0, const double *x, const double *
       const double *ui = u + P.ou + (size_t)i * m, *xn = x + P.ox + (size_t)(i + 1) * n;
       const double *ln = lam + P.olam + (size_t)(i + 1) * n, *mui = mu + P.omu + S.prow;
       for (int a = tid; a < n; a += TEAM) {
-        double v = c[a] - xn[a];
-        for (int j = 0; j < n; j++) v = fma(A[a * n + j], xi[j], v);
-        for (int j = 0; j < m; j++) v = fma(B[a * m + j], ui[j], v);
+        const double v = kkt_dot(kkt_dot(c[a] - xn[a], A + a * n, 1, xi, n), B + a * m, 1, ui, m);
         r1 = nanmax(r1, fabs(v));
         if (wr) rows.c[P.oc + (size_t)i * n + a] = v;
       }
       for (int k = tid; k < S.p; k += TEAM) {
         const double *Ck = g.C + P.oC + (size_t)(S.prow + k) * n, *Dk = g.D + P.oD + (size_t)(S.prow + k) * m;
         double dd = g.d[P.od + S.prow + k], v = dd, sc = nanmax(1.0, fabs(dd));
+#pragma unroll 2
         for (int j = 0; j < n; j++) { v = fma(Ck[j], xi[j], v); sc = nanmax(sc, fabs(Ck[j])); }
+#pragma unroll 2
         for (int j = 0; j < m; j++) { v = fma(Dk[j], ui[j], v); sc = nanmax(sc, fabs(Dk[j])); }
         r2 = nanmax(r2, fabs(v) / sc);
         if (wr) rows.d[P.od + S.prow + k] = v;
       }
       for (int a = tid; a < m; a += TEAM) {
-        double v = rv[a];
-        for (int j = 0; j < n; j++) v = fma(Mm[j * m + a], xi[j], v);
-        for (int j = 0; j < m; j++) v = fma(R[a * m + j], ui[j], v);
-        for (int j = 0; j < n; j++) v = fma(B[j * m + a], ln[j], v);
-        for (int k = 0; k < S.p; k++) v = fma(g.D[P.oD + (size_t)(S.prow + k) * m + a], mui[k], v);
+        double v = kkt_dot(rv[a], Mm + a, m, xi, n);
+        v = kkt_dot(v, R + a * m, 1, ui, m);
+        v = kkt_dot(v, B + a, m, ln, n);
+        v = kkt_dot(v, g.D + P.oD + (size_t)S.prow * m + a, m, mui, S.p);
         r3 = nanmax(r3, fabs(v));
         if (wr) rows.rv[P.orv + (size_t)i * m + a] = v;
       }
       for (int a = tid; a < n; a += TEAM) {
-        double v = q[a] + ((i == 0) ? alpha[P.oalpha + a] : -li[a]);
-        for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
-        for (int j = 0; j < m; j++) v = fma(Mm[a * m + j], ui[j], v);
-        for (int j = 0; j < n; j++) v = fma(A[j * n + a], ln[j], v);
-        for (int k = 0; k < S.p; k++) v = fma(g.C[P.oC + (size_t)(S.prow + k) * n + a], mui[k], v);
-        for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
+        double v = kkt_dot(q[a] + ((i == 0) ? alpha[P.oalpha + a] : -li[a]), Q + a * n, 1, xi, n);
+        v = kkt_dot(v, Mm + a * m, 1, ui, m);
+        v = kkt_dot(v, A + a, n, ln, n);
+        v = kkt_dot(v, g.C + P.oC + (size_t)S.prow * n + a, n, mui, S.p);
+        v = kkt_dot(v, g.E + P.oE + (size_t)S.qrow * n + a, n, etai, S.q);
         r3 = nanmax(r3, fabs(v));
         if (wr) rows.qv[P.oqv + (size_t)i * n + a] = v;
       }
     } else {
       for (int a = tid; a < n; a += TEAM) {
-        double v = q[a] - li[a];
-        for (int j = 0; j < n; j++) v = fma(Q[a * n + j], xi[j], v);
-        for (int k = 0; k < S.q; k++) v = fma(g.E[P.oE + (size_t)(S.qrow + k) * n + a], etai[k], v);
+        double v = kkt_dot(q[a] - li[a], Q + a * n, 1, xi, n);
+        v = kkt_dot(v, g.E + P.oE + (size_t)S.qrow * n + a, n, etai, S.q);
         r3 = nanmax(r3, fabs(v));
         if (wr) rows.qv[P.oqv + (size_t)i * n + a] = v;
       }
