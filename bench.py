@@ -51,6 +51,9 @@ KKT_GATE = 1e-9
 FLOOR_FACTOR = 4.0
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 PLAIN_SAMPLE = 24
+# reduced refinement passes inside each correction of the refinement on the KKT residual (fewer
+# stall it); the first solve's count is chosen by autotune_refine
+CORR_REFINE = 2
 # kernels whose launches carry one phase of the method alone when every problem is one chunk
 PHASE_KERNELS = {"k_primal_down": 0, "k_param": 1, "k_elim": 2, "k_riccati_down": 3, "k_dual_down": 5}
 # kernels that carry the rest of the same phase (their time counts with the phase's kernel)
@@ -250,22 +253,46 @@ def single_line(name, pb, dev, flush, stream, steps, **kw):
             "gate_passed": bool(r["status"] == 0 and r["resid"] <= KKT_GATE)}
 
 
-def autotune_kkt_refine(pbs, dev, gates, flush, stream, candidates=(2, 3, 4, 8), team_warps=0):
-    """(passes, trials): the smallest candidate whose eager pass leaves as many problems under their
-    gate as the largest candidate; trials = [(passes, ms, passed)]."""
+def autotune_refine(pbs, dev, gates, flush, stream, candidates=(2, 3, 4, 8), team_warps=0):
+    """(refine, kkt_refine, trials).  For one and for two reduced refinement passes in the first
+    solve (the KKT corrections keep two), the smallest KKT pass count whose eager pass leaves as
+    many problems under their gate as the largest; of those pairs that reach the best gate count,
+    the one whose captured step replays fastest.  trials: {"eager": [(refine, passes, ms, passed)],
+    "replay": [(refine, passes, ms)]}."""
     from paper_2407_05433_gb300 import eclqr
-    trials = []
-    for kr in candidates:
-        b = eclqr.Batch(pbs, device=dev, kkt_refine=kr, team_warps=team_warps)
+    eager, pick = [], {}
+    for refine in (1, 2):
+        rows = []
+        for kr in candidates:
+            b = eclqr.Batch(pbs, device=dev, refine=refine, corr_refine=CORR_REFINE, kkt_refine=kr,
+                            team_warps=team_warps)
+            try:
+                b.run()
+                ms = statistics.median(_time_runs(b, 1, flush, stream))
+                passed, _ = gate_report(pbs, b.resid.cpu().numpy(), b.status.cpu().numpy(), gates)
+            finally:
+                b.close()
+            rows.append((refine, kr, round(ms, 1), int(passed.sum())))
+        best = max(r[3] for r in rows)
+        pick[refine] = (min(r[1] for r in rows if r[3] == best), best)
+        eager += rows
+    top = max(p[1] for p in pick.values())
+    replay = []
+    for refine, (kr, passed) in sorted(pick.items()):
+        if passed < top:
+            continue
+        b = eclqr.Batch(pbs, device=dev, refine=refine, corr_refine=CORR_REFINE, kkt_refine=kr,
+                        team_warps=team_warps)
         try:
-            b.run()
-            ms = statistics.median(_time_runs(b, 1, flush, stream))
-            passed, _ = gate_report(pbs, b.resid.cpu().numpy(), b.status.cpu().numpy(), gates)
+            b.capture()
+            for _ in range(2):
+                b.replay()
+            ms = statistics.median(_time_replays(b, 3, flush, stream))
         finally:
             b.close()
-        trials.append((kr, round(ms, 1), int(passed.sum())))
-    best = max(t[2] for t in trials)
-    return min(t[0] for t in trials if t[2] == best), trials
+        replay.append((refine, kr, round(ms, 1)))
+    refine, kr, _ = min(replay, key=lambda r: r[2])
+    return refine, kr, {"eager": eager, "replay": replay}
 
 
 def measure_plain(pbs, dev, flush, stream):
@@ -290,7 +317,7 @@ def measure_plain(pbs, dev, flush, stream):
                       f"warps sweeps every stage), median of 2 passes each"}
 
 
-def measure_kernels(pbs, dev, flush, stream, flops):
+def measure_kernels(pbs, dev, flush, stream, flops, refine=2):
     """Per-kernel device time of one pass over the batch (without the refinement on the KKT
     residual), one (n, m) group at a time (groups run on concurrent streams in the batch itself,
     where one kernel's events would also cover the others' work).
@@ -312,7 +339,7 @@ def measure_kernels(pbs, dev, flush, stream, flops):
         # the group alone still takes one chunk per problem (its longest horizon fits an SM's share).
         # Without the refinement on the KKT residual every kernel launches once per phase, so the
         # phase's flops and the kernel's time describe the same work.
-        b = eclqr.Batch(gp, device=dev, kkt_refine=0)
+        b = eclqr.Batch(gp, device=dev, refine=refine, kkt_refine=0)
         try:
             b.run()
             for name in names:
@@ -338,11 +365,11 @@ def measure_kernels(pbs, dev, flush, stream, flops):
     return out
 
 
-def measure_without_kkt_refine(pbs, dev, flush, stream, gates, steps=2):
+def measure_without_kkt_refine(pbs, dev, flush, stream, gates, refine=2, steps=2):
     """The same batch and step without the refinement on the KKT residual (kkt_refine = 0), eager:
     what the refinement costs and what it buys."""
     from paper_2407_05433_gb300 import eclqr
-    b = eclqr.Batch(pbs, device=dev, kkt_refine=0)
+    b = eclqr.Batch(pbs, device=dev, refine=refine, kkt_refine=0)
     try:
         b.run()
         ms = statistics.median(_time_runs(b, steps, flush, stream))
@@ -585,10 +612,12 @@ def run_gpu(args):
     stages = int(sum(p.N for p in pbs))
 
     # untimed setup: the fewest refinement passes on the KKT residual that leave as many problems
-    # under their gate as the library default (8); a captured step records every pass, so passes
-    # that no problem needs still cost their launches and the sweeps of slow-converging problems
-    kkt_refine, kr_trials = autotune_kkt_refine(pbs, dev, gates, flush, stream, team_warps=args.team_warps)
-    batch = eclqr.Batch(pbs, device=dev, kkt_refine=kkt_refine, team_warps=args.team_warps)
+    # under their gate as the library default (8), for one or two reduced passes in the first
+    # solve; a captured step records every pass, so passes that no problem needs still cost their
+    # launches and the sweeps of slow-converging problems
+    refine, kkt_refine, kr_trials = autotune_refine(pbs, dev, gates, flush, stream, team_warps=args.team_warps)
+    batch = eclqr.Batch(pbs, device=dev, refine=refine, corr_refine=CORR_REFINE, kkt_refine=kkt_refine,
+                        team_warps=args.team_warps)
     per_replay = batch.capture()            # eager pass on a side stream, then one captured pass
     for _ in range(max(3, args.warmup)):
         batch.replay()
@@ -653,17 +682,18 @@ def run_gpu(args):
         return 0
 
     flops_all = workload_flops()
-    fl = flops_all.get(WORKLOAD) if (args.problems == PROBLEMS and args.state_dim is None
-                                     and args.max_horizon is None) else None
+    # the oracle's count for the same number of reduced refinement passes in the first solve
+    fl = flops_all.get(WORKLOAD + ("" if refine == 2 else "_refine%d" % refine)) if (
+        args.problems == PROBLEMS and args.state_dim is None and args.max_horizon is None) else None
     peak = eclqr.eclqr_probe_fp64_peak()
     extras = {}
     kern = None
     if not args.no_extra:
         extras["plain"] = measure_plain(pbs, dev, flush, stream)
         extras["plain"]["speedup_batched_vs_plain"] = value / extras["plain"]["value"]
-        kern = measure_kernels(pbs, dev, flush, stream, fl)
+        kern = measure_kernels(pbs, dev, flush, stream, fl, refine)
         extras["kernels"] = kern
-        extras["without_kkt_refine"] = measure_without_kkt_refine(pbs, dev, flush, stream, gates)
+        extras["without_kkt_refine"] = measure_without_kkt_refine(pbs, dev, flush, stream, gates, refine)
     batch.close()
     roofline = None
     if fl:
@@ -736,7 +766,8 @@ def run_gpu(args):
                    "team_warps": args.team_warps or "per kernel", "state_dim": args.state_dim,
                    "max_horizon": args.max_horizon,
                    "step": "graph replay of eclqr_build + eclqr_solve + eclqr_multipliers + eclqr_refine",
-                   "refine": 2, "kkt_refine": kkt_refine, "kkt_refine_autotune": kr_trials,
+                   "refine": refine, "corr_refine": CORR_REFINE, "kkt_refine": kkt_refine,
+                   "refine_autotune": kr_trials,
                    "refine_tol": 5e-10, "generation_s": round(t_gen, 1)},
         "gate": gate, "gate_passed": all_ok,
         "e2e": {"value": e2e_solved / (e2e_ms * 1e-3), "unit": "stages/s", "h2d_bytes_per_step": h2d,

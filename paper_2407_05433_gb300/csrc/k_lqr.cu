@@ -30,9 +30,11 @@ __host__ int smem_lqr_level(int n) {
   const int rows = 8 * n, ldm = 3 * n + 1;
   return rows * ldm + 2 * rows + 2 * (ldm + rows) + n + 16;
 }
+// V, the stacked rows, and the reflector's two vectors; the FP32 sweep's blocks (the same
+// ones in floats, its gains and the stage data) fit in the same bytes
 __host__ int smem_riccati(int n, int m) {
   const int rows = 2 * n + m, ld = n + m + 1;
-  return n * (n + 1) + rows * ld + rows + ld + 2 * m * (n + 1) + 8;
+  return n * (n + 1) + rows * ld + rows + ld + 8;
 }
 __host__ int smem_riccati_finish(int n, int m) { return m * (n + m + 1) + n * (n + 1) + m * (n + 1) + 8; }
 __host__ int smem_aff(int n, int m) { return 2 * (n * n + n) + n * n + 5 * n + 2 * m + 8; }

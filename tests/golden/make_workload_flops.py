@@ -7,6 +7,8 @@ parameterisation, 2 stage elimination (Sec. 5), 3 Riccati factors (Sec. 6), 4 ro
 refinement on the reduced residual and recovery, 5 multipliers (Sec. 7), 6 KKT residual (Sec. 9);
 phase 7 is the refinement on the original KKT residual, counted separately and not as useful
 work.  Scan overhead of the GPU path (chunk aggregates, compositions) is not counted.
+"batched_uneven_refine1" is the uneven batch with one reduced refinement pass in phase 4
+instead of two, the count the benchmark's autotuner may choose for the first solve.
 
     python tests/golden/make_workload_flops.py [--procs 8]
 
@@ -31,10 +33,10 @@ OUT = os.path.join(HERE, "workload_flops.json")
 def _flops(job):
     import oracle
     from paper_2407_05433_gb300 import synth
-    name, kw = job
+    name, kw, refine = job
     pb = synth.config(name, **kw)
-    s = oracle.solve(pb)
-    return name, kw, pb.N, [float(v) for v in s.phase_flops] + [max(0.0, float(s.flops - sum(s.phase_flops)))]
+    s = oracle.solve(pb, refine=refine)
+    return name + ("_refine%d" % refine if refine != 2 else ""), kw, pb.N, [float(v) for v in s.phase_flops] + [max(0.0, float(s.flops - sum(s.phase_flops)))]
 
 
 def main():
@@ -43,15 +45,15 @@ def main():
     args = ap.parse_args()
     import oracle
     oracle.build_oracle()
-    jobs = [("batched_uneven", {"index": j}) for j in range(4096)]
-    jobs += [("diff_batch", {"index": j}) for j in range(1024)]
-    jobs += [("single_n4", {}), ("degenerate_n12", {}), ("long_n16", {}), ("mixed_only_n12", {})]
-    jobs += [("table1", {"N": N}) for N in (1024, 4096, 16384)]
+    jobs = [("batched_uneven", {"index": j}, r) for r in (2, 1) for j in range(4096)]
+    jobs += [("diff_batch", {"index": j}, 2) for j in range(1024)]
+    jobs += [(k, {}, 2) for k in ("single_n4", "degenerate_n12", "long_n16", "mixed_only_n12")]
+    jobs += [("table1", {"N": N}, 2) for N in (1024, 4096, 16384)]
     with get_context("spawn").Pool(args.procs) as pool:
         rows = pool.map(_flops, jobs, chunksize=8)
     out = {}
     for name, kw, N, ph in rows:
-        key = name if name in ("batched_uneven", "diff_batch") else name + ("_N%d" % kw["N"] if "N" in kw else "")
+        key = name if name.startswith(("batched_uneven", "diff_batch")) else name + ("_N%d" % kw["N"] if "N" in kw else "")
         e = out.setdefault(key, {"problems": 0, "stages": 0, "phase_flops": [0.0] * 8})
         e["problems"] += 1
         e["stages"] += N
